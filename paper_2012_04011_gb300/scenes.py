@@ -1,0 +1,155 @@
+"""Seeded synthetic inputs: grids, obstacle scenes and the initial value V0.
+
+This module builds inputs only.  It holds none of the numerical scheme: no
+differences, Hamiltonian, dissipation, time step or BRT min.  Both the CUDA
+path and the FP64 oracle consume the V0 arrays it produces, so the two sides
+always start from the same bytes.
+
+V0 follows Sec. IV-A, Eq. (init_V): the signed xy-distance to a round
+obstacle, sqrt((x - x_o)^2 + (y - y_o)^2) - R, replicated over v and theta.
+Several obstacles combine by a pointwise min (the union of the target sets
+{V0 <= 0}).  Axis-aligned rectangles (used by the 128x128x64x96 workload, not
+in the paper) use the exact rectangle signed distance.
+
+Workloads (the paper's lab scenes are not published, so seeded random
+obstacles stand in for them; Sec. IV-A, Fig. 4):
+  car4d_31x31x11x16   6 circles, T = 1.0 s
+  car4d_60x60x20x36   12 circles, T = 2.0 s (the paper's grid size)
+  car4d_128x128x64x96 28 circles + 4 rectangles, T = 2.0 s
+  batch64             64 instances, uneven grids, 4-16 circles, T = 1.5 s
+Domain for all: x, y in [-5, 5], v in [0, 4], theta in [-pi, pi) periodic;
+a_max = 1.5, w_max = 1.0, CFL 0.8.  Circles: centres uniform in [-4, 4]^2,
+radii uniform in [0.3, 1.0].  Rectangles: centres uniform in [-4, 4]^2,
+half-sizes uniform in [0.2, 1.0].
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+SEED_BASE = 2012040110
+
+DOMAIN_LO = (-5.0, -5.0, 0.0, -math.pi)
+DOMAIN_HI = (5.0, 5.0, 4.0, math.pi)
+PERIODIC_THETA = 0b1000  # bit 3: theta wraps
+A_MAX = 1.5
+W_MAX = 1.0
+CFL = 0.8
+
+
+@dataclass
+class GridSpec:
+    """Points per axis (x, y, v, theta) and the axis bounds."""
+    n: tuple
+    lo: tuple = DOMAIN_LO
+    hi: tuple = DOMAIN_HI
+    periodic: int = PERIODIC_THETA
+
+    @property
+    def ncell(self) -> int:
+        return int(np.prod(self.n))
+
+    def axis(self, d: int) -> np.ndarray:
+        """Grid states on axis d: lo + i*h, h = (hi-lo)/(N-1), or (hi-lo)/N if periodic."""
+        N = self.n[d]
+        h = (self.hi[d] - self.lo[d]) / (N if (self.periodic >> d) & 1 else N - 1)
+        return self.lo[d] + np.arange(N, dtype=np.float64) * h
+
+
+@dataclass
+class Scene:
+    """Obstacles: circles (x_o, y_o, R) and axis-aligned rectangles (cx, cy, hx, hy)."""
+    circles: np.ndarray = field(default_factory=lambda: np.zeros((0, 3)))
+    rects: np.ndarray = field(default_factory=lambda: np.zeros((0, 4)))
+
+    def copy(self) -> "Scene":
+        return Scene(self.circles.copy(), self.rects.copy())
+
+
+@dataclass
+class Workload:
+    name: str
+    grid: GridSpec
+    scene: Scene
+    T: float
+    seed: int
+    a_max: float = A_MAX
+    w_max: float = W_MAX
+    cfl: float = CFL
+
+
+def random_scene(rng: np.random.Generator, n_circles: int, n_rects: int = 0) -> Scene:
+    c = np.empty((n_circles, 3))
+    c[:, 0:2] = rng.uniform(-4.0, 4.0, size=(n_circles, 2))
+    c[:, 2] = rng.uniform(0.3, 1.0, size=n_circles)
+    r = np.empty((n_rects, 4))
+    r[:, 0:2] = rng.uniform(-4.0, 4.0, size=(n_rects, 2))
+    r[:, 2:4] = rng.uniform(0.2, 1.0, size=(n_rects, 2))
+    return Scene(c, r)
+
+
+def signed_distance_xy(grid: GridSpec, scene: Scene) -> np.ndarray:
+    """min over obstacles of the signed xy-distance on the (N1, N2) plane."""
+    x = grid.axis(0)[:, None]
+    y = grid.axis(1)[None, :]
+    sd = np.full((grid.n[0], grid.n[1]), np.inf)
+    for xo, yo, R in scene.circles:
+        sd = np.minimum(sd, np.sqrt((x - xo) ** 2 + (y - yo) ** 2) - R)
+    for cx, cy, hx, hy in scene.rects:
+        qx = np.abs(x - cx) - hx
+        qy = np.abs(y - cy) - hy
+        outside = np.sqrt(np.maximum(qx, 0.0) ** 2 + np.maximum(qy, 0.0) ** 2)
+        inside = np.minimum(np.maximum(qx, qy), 0.0)
+        sd = np.minimum(sd, outside + inside)
+    if not np.all(np.isfinite(sd)):
+        raise ValueError("scene has no obstacles")
+    return sd
+
+
+def initial_value(grid: GridSpec, scene: Scene) -> np.ndarray:
+    """V0[i, j, k, l] (FP64, C order, theta fastest) from Eq. (init_V)."""
+    sd = signed_distance_xy(grid, scene)
+    v0 = np.broadcast_to(sd[:, :, None, None], grid.n)
+    return np.ascontiguousarray(v0, dtype=np.float64)
+
+
+def _single(name: str, n, n_circles: int, n_rects: int, T: float, seed: int) -> Workload:
+    rng = np.random.default_rng(seed)
+    return Workload(name, GridSpec(tuple(n)), random_scene(rng, n_circles, n_rects), T, seed)
+
+
+def workload(name: str) -> Workload:
+    """The named single-instance workloads."""
+    if name == "car4d_31x31x11x16":
+        return _single(name, (31, 31, 11, 16), 6, 0, 1.0, SEED_BASE + 0)
+    if name == "car4d_60x60x20x36":
+        return _single(name, (60, 60, 20, 36), 12, 0, 2.0, SEED_BASE + 1)
+    if name == "car4d_128x128x64x96":
+        return _single(name, (128, 128, 64, 96), 28, 4, 2.0, SEED_BASE + 3)
+    raise KeyError(name)
+
+
+WORKLOADS = ("car4d_31x31x11x16", "car4d_60x60x20x36", "car4d_128x128x64x96")
+
+
+def batch_workloads(count: int = 64, seed: int = SEED_BASE + 2):
+    """Independent instances with uneven grids: N1, N2 in {40, 50, 60}, N3 in
+    [16, 24], N4 in [24, 36], 4-16 circles each, T = 1.5 s."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for b in range(count):
+        n = (int(rng.choice([40, 50, 60])), int(rng.choice([40, 50, 60])),
+             int(rng.integers(16, 25)), int(rng.integers(24, 37)))
+        sc = random_scene(rng, int(rng.integers(4, 17)))
+        out.append(Workload(f"batch{b}", GridSpec(n), sc, 1.5, seed))
+    return out
+
+
+def custom_workload(n, n_circles: int = 4, n_rects: int = 0, T: float = 0.5, seed: int = SEED_BASE + 99,
+                    a_max: float = A_MAX, w_max: float = W_MAX, cfl: float = CFL) -> Workload:
+    """Seeded scene on an arbitrary grid (tests use it for ragged and tiny shapes)."""
+    rng = np.random.default_rng(seed)
+    return Workload(f"custom{tuple(n)}", GridSpec(tuple(int(x) for x in n)), random_scene(rng, n_circles, n_rects),
+                    T, seed, a_max, w_max, cfl)
