@@ -1,0 +1,195 @@
+/*
+ * libhj — GB300 (sm_103a) time stepping of the Hamilton-Jacobi reachability
+ * PDE on a dense 4D grid, computing the Backward Reachable Tube (BRT) of the
+ * 4D car of arxiv 2012.04011 ("Real-Time Formal Verification of Autonomous
+ * Systems With An FPGA").
+ *
+ * Plain C ABI: status codes returned by value, plain pointers and sizes, no
+ * C++ or framework types.  No exception and no exit() crosses this boundary.
+ *
+ * Problem (Sec. II-A): dynamics z' = f(z, u) (Eq. main_ode, no disturbance),
+ * target set T = {z : V0(z) <= 0} given by an implicit surface V0
+ * (Sec. II-A; Eq. init_V for round obstacles), and the BRT as the sub-zero
+ * level set of the value function V of Eq. eq3, the viscosity solution of the
+ * HJ variational inequality (Eq. HJ_variational_inequality).
+ *
+ * Scheme (Sec. II-B): one-sided differences D-, D+ and their mean on every
+ * axis (Eq. central_diff) with extrapolated points at the ends of
+ * non-periodic axes; u_opt = argmax_u grad(V).f (bang-bang); Lax-Friedrichs
+ * Hamiltonian with the local dissipation alpha_d = |xdot_d| (Algorithm 2);
+ * CFL step dt = CFL / sum_d alpha_d^max / dx_d from max reductions over the
+ * grid (Algorithm 1); forward Euler; V <- min(V0, V) after every step
+ * (Algorithms 1-2).  Time runs from t = 0 to the horizon T; the last step is
+ * cut so that t lands on T.
+ *
+ * Grid layout everywhere in this API: row-major [N1][N2][N3][N4] over the
+ * axes (x, y, v, theta), theta (axis 4) fastest, matching the loop order
+ * i, j, k, l of Algorithms 1-2.  Non-periodic axes include both end points:
+ * x_i = lo + i (hi - lo)/(N - 1).  A periodic axis of N points covers
+ * [lo, hi): x_i = lo + i (hi - lo)/N.
+ *
+ * Call order: hj_create_grid -> hj_set_dynamics -> hj_set_initial_value[_device]
+ * -> hj_solve_brt / hj_advance_brt (repeatable: each call continues from the
+ * current (V, t)) -> hj_read_value[_device] -> hj_destroy_grid.
+ *
+ * Threading: a grid is not thread safe; different grids may be used from
+ * different host threads.  All device work of a grid runs on the grid's
+ * stream.  The calls below block until their device work is complete unless
+ * stated otherwise.
+ */
+#ifndef HJ_H
+#define HJ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define HJ_API __attribute__((visibility("default")))
+#else
+#define HJ_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hj_grid hj_grid; /* opaque; created and freed by the library */
+
+typedef enum {
+    HJ_OK = 0,
+    HJ_ERR_INVALID_ARG = 1, /* a bad size, bound, pointer, count or a non-finite value */
+    HJ_ERR_STATE = 2,       /* call out of order (e.g. solving before V0 is set) */
+    HJ_ERR_OOM = 3,         /* device or host allocation failed */
+    HJ_ERR_CUDA = 4,        /* a CUDA runtime or driver call failed (message: hj_last_error) */
+    HJ_ERR_UNSTABLE = 5,    /* the CFL step came out non-finite or non-positive */
+    HJ_ERR_TIMEOUT = 6,     /* a device-side wait ran out of time; the grid must be destroyed */
+    HJ_ERR_UNSUPPORTED = 7  /* valid request this build does not implement */
+} hj_status;
+
+typedef enum { HJ_FP64 = 0, HJ_FP32 = 1 } hj_precision;
+
+typedef enum {
+    /* Sec. IV-A car with the heading rate as a bounded control:
+     * x' = v cos(th), y' = v sin(th), v' = a, th' = w; |a| <= p[0] (a_max),
+     * |w| <= p[1] (w_max).  Axes must be (x, y, v, theta). */
+    HJ_DYN_CAR4D = 0,
+    /* Constant velocity xdot = (p[0], p[1], p[2], p[3]), no control
+     * (closed-form test cases). */
+    HJ_DYN_CONST = 1
+} hj_dynamics;
+
+/* Step-kernel selection (HJ_KERNEL_AUTO picks the fastest one that supports
+ * the grid). */
+typedef enum {
+    HJ_KERNEL_AUTO = 0,
+    HJ_KERNEL_GENERIC = 1, /* one thread per cell, loads through L1/L2 */
+    HJ_KERNEL_TILED = 2    /* FP32: TMA-staged 4D tiles streamed along x */
+} hj_kernel;
+
+typedef struct {
+    int64_t steps;         /* steps taken by this call */
+    int64_t total_steps;   /* steps since the last hj_set_initial_value */
+    double t_final;        /* simulated time reached */
+    double dt_first;       /* dt of the first step of this call (0 if none) */
+    double dt_last;        /* dt of the last step of this call (0 if none) */
+    double alpha_max[4];   /* alpha_d^max reduced by the last step (|xdot_d| maxima) */
+    double device_ms;      /* device time of the whole call (CUDA events) */
+    double loop_ms;        /* device time of the time loop only (step kernels) */
+    int32_t kernel;        /* hj_kernel actually used */
+    int32_t launches;      /* kernels launched by this call */
+} hj_solve_stats;
+
+typedef struct {
+    int32_t n[4];
+    int32_t pitch4;        /* internal row pitch along theta (N4 rounded up) */
+    int32_t precision;     /* hj_precision */
+    int32_t kernel;        /* hj_kernel that hj_solve_brt will use */
+    double lo[4], hi[4], dx[4];
+    uint32_t periodic_mask;
+    int32_t has_value;     /* V0 has been set */
+    int64_t total_steps;
+    double t;
+    size_t device_bytes;   /* device memory held by the grid */
+} hj_grid_info;
+
+/* Create a grid of n[0]*n[1]*n[2]*n[3] cells on the current CUDA device.
+ *   n:             points per axis; N_d >= 3 on every axis; N4 <= 4096.
+ *   lo, hi:        axis bounds, finite, hi > lo.
+ *   periodic_mask: bit d set makes axis d periodic (bit 3 = theta).
+ *   prec:          arithmetic of the value function on the device; the
+ *                  simulated time and dt are always FP64.
+ *   cuda_stream:   a cudaStream_t to run on (e.g. a PyTorch stream), or NULL
+ *                  for a stream owned by the grid.  The caller keeps a passed
+ *                  stream alive until hj_destroy_grid.
+ *   out:           receives the grid; written only on HJ_OK.
+ * Allocates three device arrays (V0 and two ping-pong buffers) of
+ * n1*n2*n3*pitch4 values each. */
+HJ_API hj_status hj_create_grid(const int32_t n[4], const double lo[4], const double hi[4],
+                         uint32_t periodic_mask, hj_precision prec, void *cuda_stream,
+                         hj_grid **out);
+
+/* Set the dynamics (Eq. main_ode; car: Eq. car_dynamics of Sec. IV-A with
+ * th' = w).  params: HJ_DYN_CAR4D {a_max >= 0, w_max >= 0};
+ * HJ_DYN_CONST {c1, c2, c3, c4}.  nparams must match (2 or 4), values finite.
+ * Uploads the (v, theta) state tables once (Sec. III-A keeps the state
+ * vectors and cos/sin of theta in small on-chip look-up tables). */
+HJ_API hj_status hj_set_dynamics(hj_grid *g, hj_dynamics kind, const double *params, int32_t nparams);
+
+/* Initial value V0 (Sec. II-A, target set {V0 <= 0}) from a HOST array of
+ * count = N1*N2*N3*N4 doubles in the layout above.  The library copies it
+ * (the caller keeps ownership) and resets t = 0, V = V0.  Non-finite values
+ * give HJ_ERR_INVALID_ARG (checked on the device).  Pinned host memory makes
+ * the copy faster; pageable memory works. */
+HJ_API hj_status hj_set_initial_value(hj_grid *g, const double *v0, size_t count);
+
+/* As hj_set_initial_value, from a DEVICE array (dtype HJ_FP64 = double,
+ * HJ_FP32 = float) of count values on the grid's device, dense layout
+ * above.  The array is read on the grid's stream; the caller keeps
+ * ownership. */
+HJ_API hj_status hj_set_initial_value_device(hj_grid *g, const void *v0_device, hj_precision dtype,
+                                      size_t count);
+
+/* Integrate from the current time to the horizon T (T >= 0, finite) with
+ * Courant number cfl (0 < cfl <= 1).  T <= current t is a no-op returning
+ * HJ_OK.  stats may be NULL.  HJ_ERR_STATE without dynamics or V0. */
+HJ_API hj_status hj_solve_brt(hj_grid *g, double T, double cfl, hj_solve_stats *stats);
+
+/* As hj_solve_brt but takes at most max_steps (>= 0) steps toward T; a later
+ * call continues.  Lets a caller bound the work of one call. */
+HJ_API hj_status hj_advance_brt(hj_grid *g, double T, double cfl, int64_t max_steps,
+                         hj_solve_stats *stats);
+
+/* Copy the current V into a HOST buffer of count = N1*N2*N3*N4 doubles
+ * (caller-owned), layout above. */
+HJ_API hj_status hj_read_value(const hj_grid *g, double *out, size_t count);
+
+/* Copy the current V into a DEVICE buffer of count values of dtype
+ * (HJ_FP64 or HJ_FP32), layout above; caller-owned.  Runs on the grid's
+ * stream; returns once the copy is queued and completed. */
+HJ_API hj_status hj_read_value_device(const hj_grid *g, void *out_device, hj_precision dtype,
+                               size_t count);
+
+/* Choose the step kernel.  HJ_KERNEL_TILED on a grid that it does not
+ * support returns HJ_ERR_UNSUPPORTED and leaves the choice unchanged. */
+HJ_API hj_status hj_set_kernel(hj_grid *g, hj_kernel kernel);
+
+/* Describe the grid (sizes, spacings, time, memory). */
+HJ_API hj_status hj_get_info(const hj_grid *g, hj_grid_info *info);
+
+/* Free all device and host resources of the grid (NULL is a no-op). */
+HJ_API void hj_destroy_grid(hj_grid *g);
+
+/* Static string naming a status code. */
+HJ_API const char *hj_status_string(hj_status s);
+
+/* Message of the last error raised on the calling host thread ("" if none). */
+HJ_API const char *hj_last_error(void);
+
+/* Library version as major*10000 + minor*100 + patch. */
+HJ_API int32_t hj_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HJ_H */

@@ -1,0 +1,708 @@
+// C-ABI implementation of libhj (declarations and documentation: hj.h).
+//
+// Host side of the HJ reachability solver for arxiv 2012.04011: grid and
+// buffer management, the (v, theta) state tables (Sec. III-A), V0 ingest,
+// the time loop driving the step kernels (Algorithms 1-2, Sec. II-B), and
+// readback.  Simulated time and dt live on the device in FP64 and are
+// advanced by the step kernels themselves (fused alpha^max reduction and
+// finaliser, hj_device.cuh); the host only launches steps and reads the
+// state back to know when the horizon is reached.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "hj_device.cuh"
+
+#define HJ_VERSION 10000
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+hj_status set_err(hj_status s, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return s;
+}
+
+#define HJ_CUDA(call)                                                                                 \
+    do {                                                                                              \
+        cudaError_t e_ = (call);                                                                      \
+        if (e_ != cudaSuccess)                                                                        \
+            return set_err(e_ == cudaErrorMemoryAllocation ? HJ_ERR_OOM : HJ_ERR_CUDA, "%s: %s (%s:%d)", \
+                           #call, cudaGetErrorString(e_), __FILE__, __LINE__);                        \
+    } while (0)
+
+// ---------------------------------------------------------------- kernels
+
+// Dense row-major [N1][N2][N3][N4] (any of double/float) -> internal layout
+// (rows padded to p4, pad lanes zero).  Flags non-finite input.
+template <typename Tin, typename T>
+__global__ void ingest_kernel(const Tin *__restrict__ src, T *__restrict__ dst, int n4, int p4, long long nrows,
+                              int *nonfinite)
+{
+    long long total = nrows * p4;
+    int bad = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        long long row = i / p4;
+        int l = (int)(i - row * p4);
+        T v = T(0);
+        if (l < n4) {
+            double x = (double)src[row * n4 + l];
+            if (!isfinite(x)) bad = 1;
+            v = (T)x;
+        }
+        dst[i] = v;
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(nonfinite, 1);
+}
+
+// Internal layout -> dense (rows [row0, row0 + nrows)), converting type.
+template <typename T, typename Tout>
+__global__ void readback_kernel(const T *__restrict__ src, Tout *__restrict__ dst, int n4, int p4, long long row0,
+                                long long nrows)
+{
+    long long total = nrows * n4;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        long long row = i / n4;
+        int l = (int)(i - row * n4);
+        dst[i] = (Tout)src[(row0 + row) * p4 + l];
+    }
+}
+
+// Start of a solve call: horizon, Courant number and the dt of the first
+// step.  Right after V0 is set (n == 0), alpha^max is reduced over the
+// (v, theta) table, which holds |xdot_1|, |xdot_2| of every cell (the car's
+// velocity depends only on v and theta).
+template <typename T>
+__global__ void prologue_kernel(HjDevState *st, const HjGeom g, const HjCoef<T> *__restrict__ coef, int ncoef,
+                                double T_end, double cfl)
+{
+    __shared__ unsigned long long scratch[64];
+    unsigned long long a1 = 0ull, a2 = 0ull;
+    const bool fresh = st->n == 0;
+    if (fresh)
+        for (int i = threadIdx.x; i < ncoef; i += blockDim.x) {
+            unsigned long long b1 = hj_abits((double)coef[i].a1), b2 = hj_abits((double)coef[i].a2);
+            a1 = a1 > b1 ? a1 : b1;
+            a2 = a2 > b2 ? a2 : b2;
+        }
+    a1 = hj_warp_max_u64(a1);
+    a2 = hj_warp_max_u64(a2);
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        scratch[warp] = a1;
+        scratch[32 + warp] = a2;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+            a1 = a1 > scratch[w] ? a1 : scratch[w];
+            a2 = a2 > scratch[32 + w] ? a2 : scratch[32 + w];
+        }
+        st->T = T_end;
+        st->cfl = cfl;
+        double a[4];
+        if (fresh) {
+            a[0] = __longlong_as_double((long long)a1);
+            a[1] = __longlong_as_double((long long)a2);
+            a[2] = g.alpha3;
+            a[3] = g.alpha4;
+            for (int d = 0; d < 4; ++d) st->alpha_prev[d] = a[d];
+        } else {
+            for (int d = 0; d < 4; ++d) a[d] = st->alpha_prev[d];
+        }
+        st->alpha_bits[0] = 0ull;
+        st->alpha_bits[1] = 0ull;
+        st->blocks_done = 0u;
+        if (st->status == HJ_OK)
+            hj_next_dt(st, g, a, st->t);
+        else
+            st->done = 1;
+    }
+}
+
+int grid_blocks(long long work, int threads)
+{
+    long long b = (work + threads - 1) / threads;
+    if (b > 152 * 16) b = 152 * 16;
+    return b < 1 ? 1 : (int)b;
+}
+
+bool finite_all(const double *p, int n)
+{
+    for (int i = 0; i < n; ++i)
+        if (!isfinite(p[i])) return false;
+    return true;
+}
+
+hj_status check_grid(const hj_grid *g)
+{
+    if (!g) return set_err(HJ_ERR_INVALID_ARG, "grid is NULL");
+    return HJ_OK;
+}
+
+hj_status activate(const hj_grid *g)
+{
+    int cur = -1;
+    HJ_CUDA(cudaGetDevice(&cur));
+    if (cur != g->device) HJ_CUDA(cudaSetDevice(g->device));
+    return HJ_OK;
+}
+
+hj_status pull_state(hj_grid *g)
+{
+    HJ_CUDA(cudaMemcpyAsync(g->hstate, g->dstate, sizeof(HjDevState), cudaMemcpyDeviceToHost, g->stream));
+    HJ_CUDA(cudaStreamSynchronize(g->stream));
+    return HJ_OK;
+}
+
+hj_status upload_tables(hj_grid *g)
+{
+    const int N3 = g->n[2], N4 = g->n[3], P4 = g->p4;
+    const bool car = g->dyn == HJ_DYN_CAR4D;
+    // per-(v, theta) coefficients in FP64: xdot_1 = v cos(theta), xdot_2 = v sin(theta)
+    size_t nco = (size_t)N3 * N4;
+    double *f1 = (double *)malloc(sizeof(double) * nco), *f2 = (double *)malloc(sizeof(double) * nco);
+    float *tab = (float *)calloc((size_t)N3 + 2 * (size_t)P4, sizeof(float));
+    if (!f1 || !f2 || !tab) {
+        free(f1);
+        free(f2);
+        free(tab);
+        return set_err(HJ_ERR_OOM, "host allocation failed");
+    }
+    for (int k = 0; k < N3; ++k) {
+        double v = g->lo[2] + (double)k * g->h[2];
+        tab[k] = (float)v;
+        for (int l = 0; l < N4; ++l) {
+            double th = g->lo[3] + (double)l * g->h[3];
+            f1[(size_t)k * N4 + l] = car ? v * cos(th) : g->params[0];
+            f2[(size_t)k * N4 + l] = car ? v * sin(th) : g->params[1];
+        }
+    }
+    for (int l = 0; l < N4; ++l) {
+        double th = g->lo[3] + (double)l * g->h[3];
+        tab[N3 + l] = (float)(cos(th) / g->h[0]);
+        tab[N3 + P4 + l] = (float)(sin(th) / g->h[1]);
+    }
+    const double k3 = g->geom.k3, k4 = g->geom.k4;
+    hj_status st = HJ_OK;
+    if (g->prec == HJ_FP64) {
+        HjCoef<double> *c = (HjCoef<double> *)malloc(sizeof(HjCoef<double>) * nco);
+        if (!c) st = set_err(HJ_ERR_OOM, "host allocation failed");
+        for (size_t i = 0; c && i < nco; ++i) {
+            c[i].c1 = f1[i] / g->h[0];
+            c[i].c2 = f2[i] / g->h[1];
+            c[i].ks = fabs(c[i].c1) + fabs(c[i].c2) + k3 + k4;
+            c[i].a1 = fabs(f1[i]);
+            c[i].a2 = fabs(f2[i]);
+        }
+        if (c) {
+            cudaError_t e = cudaMemcpy(g->coef, c, sizeof(HjCoef<double>) * nco, cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) st = set_err(HJ_ERR_CUDA, "table upload: %s", cudaGetErrorString(e));
+        }
+        free(c);
+    } else {
+        HjCoef<float> *c = (HjCoef<float> *)malloc(sizeof(HjCoef<float>) * nco);
+        if (!c) st = set_err(HJ_ERR_OOM, "host allocation failed");
+        for (size_t i = 0; c && i < nco; ++i) {
+            double c1 = f1[i] / g->h[0], c2 = f2[i] / g->h[1];
+            c[i].c1 = (float)c1;
+            c[i].c2 = (float)c2;
+            c[i].ks = (float)(fabs(c1) + fabs(c2) + k3 + k4);
+            c[i].a1 = (float)fabs(f1[i]);
+            c[i].a2 = (float)fabs(f2[i]);
+        }
+        if (c) {
+            cudaError_t e = cudaMemcpy(g->coef, c, sizeof(HjCoef<float>) * nco, cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) st = set_err(HJ_ERR_CUDA, "table upload: %s", cudaGetErrorString(e));
+        }
+        free(c);
+    }
+    if (st == HJ_OK) {
+        cudaError_t e = cudaMemcpy(g->tab_tiled, tab, sizeof(float) * ((size_t)N3 + 2 * (size_t)P4),
+                                   cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) st = set_err(HJ_ERR_CUDA, "table upload: %s", cudaGetErrorString(e));
+    }
+    free(f1);
+    free(f2);
+    free(tab);
+    return st;
+}
+
+hj_status reset_state(hj_grid *g)
+{
+    memset(g->hstate, 0, sizeof(HjDevState));
+    g->hstate->status = HJ_OK;
+    HJ_CUDA(cudaMemcpyAsync(g->dstate, g->hstate, sizeof(HjDevState), cudaMemcpyHostToDevice, g->stream));
+    return HJ_OK;
+}
+
+hj_kernel effective_kernel(const hj_grid *g)
+{
+    if (g->kernel_req == HJ_KERNEL_GENERIC) return HJ_KERNEL_GENERIC;
+    return g->tiled_ok ? HJ_KERNEL_TILED : HJ_KERNEL_GENERIC;
+}
+
+hj_status launch_step(hj_grid *g, hj_kernel k)
+{
+    cudaError_t e = (k == HJ_KERNEL_TILED) ? hj_launch_step_tiled(g) : hj_launch_step_generic(g);
+    if (e != cudaSuccess) return set_err(HJ_ERR_CUDA, "step launch: %s", cudaGetErrorString(e));
+    return HJ_OK;
+}
+
+void free_grid(hj_grid *g)
+{
+    if (!g) return;
+    if (g->v0) cudaFree(g->v0);
+    if (g->buf) cudaFree(g->buf);
+    if (g->coef) cudaFree(g->coef);
+    if (g->tab_tiled) cudaFree(g->tab_tiled);
+    if (g->dstate) cudaFree(g->dstate);
+    if (g->hstate) cudaFreeHost(g->hstate);
+    for (int i = 0; i < 4; ++i)
+        if (g->ev[i]) cudaEventDestroy(g->ev[i]);
+    if (g->own_stream && g->stream) cudaStreamDestroy(g->stream);
+    delete g;
+}
+
+}  // namespace
+
+// ==================================================================== C ABI
+
+extern "C" {
+
+int32_t hj_version(void) { return HJ_VERSION; }
+
+const char *hj_last_error(void) { return g_err; }
+
+const char *hj_status_string(hj_status s)
+{
+    switch (s) {
+    case HJ_OK: return "HJ_OK";
+    case HJ_ERR_INVALID_ARG: return "HJ_ERR_INVALID_ARG";
+    case HJ_ERR_STATE: return "HJ_ERR_STATE";
+    case HJ_ERR_OOM: return "HJ_ERR_OOM";
+    case HJ_ERR_CUDA: return "HJ_ERR_CUDA";
+    case HJ_ERR_UNSTABLE: return "HJ_ERR_UNSTABLE";
+    case HJ_ERR_TIMEOUT: return "HJ_ERR_TIMEOUT";
+    case HJ_ERR_UNSUPPORTED: return "HJ_ERR_UNSUPPORTED";
+    }
+    return "HJ_ERR_UNKNOWN";
+}
+
+hj_status hj_create_grid(const int32_t n[4], const double lo[4], const double hi[4], uint32_t periodic_mask,
+                         hj_precision prec, void *cuda_stream, hj_grid **out)
+{
+    g_err[0] = 0;
+    if (!n || !lo || !hi || !out) return set_err(HJ_ERR_INVALID_ARG, "NULL argument");
+    if (prec != HJ_FP64 && prec != HJ_FP32) return set_err(HJ_ERR_INVALID_ARG, "unknown precision %d", (int)prec);
+    if (periodic_mask & ~0xFu) return set_err(HJ_ERR_INVALID_ARG, "periodic_mask has bits above 3");
+    long long ncell = 1;
+    for (int d = 0; d < 4; ++d) {
+        if (n[d] < 3) return set_err(HJ_ERR_INVALID_ARG, "N%d = %d < 3", d + 1, n[d]);
+        if (!isfinite(lo[d]) || !isfinite(hi[d]) || !(hi[d] > lo[d]))
+            return set_err(HJ_ERR_INVALID_ARG, "axis %d bounds must be finite with hi > lo", d + 1);
+        ncell *= n[d];
+    }
+    if (n[3] > 4096) return set_err(HJ_ERR_INVALID_ARG, "N4 = %d > 4096", n[3]);
+    if (ncell > (1LL << 33)) return set_err(HJ_ERR_INVALID_ARG, "grid of %lld cells is too large", ncell);
+
+    hj_grid *g = new (std::nothrow) hj_grid();
+    if (!g) return set_err(HJ_ERR_OOM, "host allocation failed");
+    memset(g, 0, sizeof(*g));
+    for (int d = 0; d < 4; ++d) {
+        g->n[d] = n[d];
+        g->lo[d] = lo[d];
+        g->hi[d] = hi[d];
+        bool per = (periodic_mask >> d) & 1u;
+        g->h[d] = (hi[d] - lo[d]) / (double)(per ? n[d] : n[d] - 1);
+    }
+    g->p4 = (n[3] + 3) / 4 * 4;
+    g->periodic = periodic_mask;
+    g->prec = prec;
+    g->esize = prec == HJ_FP64 ? 8 : 4;
+    g->ncell = ncell;
+    g->nint = (long long)n[0] * n[1] * n[2] * g->p4;
+    g->kernel_req = HJ_KERNEL_AUTO;
+
+    cudaError_t e = cudaGetDevice(&g->device);
+    if (e == cudaSuccess && cuda_stream) {
+        g->stream = (cudaStream_t)cuda_stream;
+    } else if (e == cudaSuccess) {
+        e = cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking);
+        g->own_stream = e == cudaSuccess;
+    }
+    size_t arr = (size_t)g->nint * g->esize;
+    size_t ncoef = (size_t)n[2] * n[3];
+    if (e == cudaSuccess) e = cudaMalloc(&g->v0, arr);
+    if (e == cudaSuccess) e = cudaMalloc(&g->buf, 2 * arr);
+    if (e == cudaSuccess) e = cudaMalloc(&g->coef, ncoef * (prec == HJ_FP64 ? sizeof(HjCoef<double>) : sizeof(HjCoef<float>)));
+    if (e == cudaSuccess) e = cudaMalloc(&g->tab_tiled, sizeof(float) * ((size_t)n[2] + 2 * (size_t)g->p4));
+    if (e == cudaSuccess) e = cudaMalloc(&g->dstate, sizeof(HjDevState));
+    if (e == cudaSuccess) e = cudaHostAlloc(&g->hstate, sizeof(HjDevState), cudaHostAllocDefault);
+    for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaEventCreate(&g->ev[i]);
+    if (e != cudaSuccess) {
+        hj_status s = set_err(e == cudaErrorMemoryAllocation ? HJ_ERR_OOM : HJ_ERR_CUDA, "hj_create_grid: %s",
+                              cudaGetErrorString(e));
+        free_grid(g);
+        return s;
+    }
+    g->device_bytes = 3 * arr + ncoef * (prec == HJ_FP64 ? sizeof(HjCoef<double>) : sizeof(HjCoef<float>)) +
+                      sizeof(HjDevState);
+    hj_status s = reset_state(g);
+    if (s == HJ_OK) {
+        cudaError_t e2 = cudaStreamSynchronize(g->stream);
+        if (e2 != cudaSuccess) s = set_err(HJ_ERR_CUDA, "hj_create_grid: %s", cudaGetErrorString(e2));
+    }
+    if (s != HJ_OK) {
+        free_grid(g);
+        return s;
+    }
+    *out = g;
+    return HJ_OK;
+}
+
+void hj_destroy_grid(hj_grid *g)
+{
+    if (!g) return;
+    if (activate(g) == HJ_OK && g->stream) cudaStreamSynchronize(g->stream);
+    free_grid(g);
+}
+
+hj_status hj_set_dynamics(hj_grid *g, hj_dynamics kind, const double *params, int32_t nparams)
+{
+    g_err[0] = 0;
+    hj_status s = check_grid(g);
+    if (s != HJ_OK) return s;
+    if (!params) return set_err(HJ_ERR_INVALID_ARG, "params is NULL");
+    if (kind == HJ_DYN_CAR4D) {
+        if (nparams != 2) return set_err(HJ_ERR_INVALID_ARG, "car dynamics take 2 parameters (a_max, w_max)");
+        if (!finite_all(params, 2) || params[0] < 0 || params[1] < 0)
+            return set_err(HJ_ERR_INVALID_ARG, "a_max and w_max must be finite and >= 0");
+    } else if (kind == HJ_DYN_CONST) {
+        if (nparams != 4) return set_err(HJ_ERR_INVALID_ARG, "constant dynamics take 4 parameters");
+        if (!finite_all(params, 4)) return set_err(HJ_ERR_INVALID_ARG, "parameters must be finite");
+    } else {
+        return set_err(HJ_ERR_INVALID_ARG, "unknown dynamics %d", (int)kind);
+    }
+    if ((s = activate(g)) != HJ_OK) return s;
+    HJ_CUDA(cudaStreamSynchronize(g->stream));
+    g->dyn = kind;
+    for (int i = 0; i < 4; ++i) g->params[i] = i < nparams ? params[i] : 0.0;
+
+    HjGeom &G = g->geom;
+    memset(&G, 0, sizeof(G));
+    G.n1 = g->n[0];
+    G.n2 = g->n[1];
+    G.n3 = g->n[2];
+    G.n4 = g->n[3];
+    G.p4 = g->p4;
+    G.periodic = (int32_t)g->periodic;
+    for (int d = 0; d < 4; ++d) G.h[d] = g->h[d];
+    if (kind == HJ_DYN_CAR4D) {
+        G.mode3 = HJ_AXIS_CONTROL;
+        G.mode4 = HJ_AXIS_CONTROL;
+        G.alpha3 = params[0];
+        G.alpha4 = params[1];
+    } else {
+        G.mode3 = params[2] >= 0 ? HJ_AXIS_PLUS : HJ_AXIS_MINUS;
+        G.mode4 = params[3] >= 0 ? HJ_AXIS_PLUS : HJ_AXIS_MINUS;
+        G.alpha3 = fabs(params[2]);
+        G.alpha4 = fabs(params[3]);
+    }
+    G.k3 = G.alpha3 / g->h[2];
+    G.k4 = G.alpha4 / g->h[3];
+    if ((s = upload_tables(g)) != HJ_OK) return s;
+    g->has_dyn = true;
+    char why[160];
+    g->tiled_ok = hj_tiled_setup(g, why, sizeof(why));
+    if (g->kernel_req == HJ_KERNEL_TILED && !g->tiled_ok) g->kernel_req = HJ_KERNEL_AUTO;
+    // a previously set V0 stays; the next solve continues with the new dynamics
+    return HJ_OK;
+}
+
+static hj_status finish_ingest(hj_grid *g)
+{
+    HJ_CUDA(cudaGetLastError());
+    HJ_CUDA(cudaStreamSynchronize(g->stream));
+    HJ_CUDA(cudaMemcpy(g->hstate, g->dstate, sizeof(HjDevState), cudaMemcpyDeviceToHost));
+    if (g->hstate->nonfinite) {
+        g->has_value = false;
+        reset_state(g);
+        cudaStreamSynchronize(g->stream);
+        return set_err(HJ_ERR_INVALID_ARG, "V0 contains NaN or Inf");
+    }
+    g->has_value = true;
+    return HJ_OK;
+}
+
+hj_status hj_set_initial_value(hj_grid *g, const double *v0, size_t count)
+{
+    g_err[0] = 0;
+    hj_status s = check_grid(g);
+    if (s != HJ_OK) return s;
+    if (!v0) return set_err(HJ_ERR_INVALID_ARG, "v0 is NULL");
+    if (count != (size_t)g->ncell)
+        return set_err(HJ_ERR_INVALID_ARG, "count %zu != N1*N2*N3*N4 = %lld", count, g->ncell);
+    if ((s = activate(g)) != HJ_OK) return s;
+    if ((s = reset_state(g)) != HJ_OK) return s;
+    // stage the dense FP64 array in the ping-pong region (2 * nint * esize >= ncell * 8 bytes)
+    double *staging = (double *)g->buf;
+    HJ_CUDA(cudaMemcpyAsync(staging, v0, sizeof(double) * (size_t)g->ncell, cudaMemcpyHostToDevice, g->stream));
+    long long nrows = (long long)g->n[0] * g->n[1] * g->n[2];
+    int *flag = &g->dstate->nonfinite;
+    int blocks = grid_blocks(g->nint, 256);
+    if (g->prec == HJ_FP64)
+        ingest_kernel<double, double><<<blocks, 256, 0, g->stream>>>(staging, (double *)g->v0, g->n[3], g->p4, nrows, flag);
+    else
+        ingest_kernel<double, float><<<blocks, 256, 0, g->stream>>>(staging, (float *)g->v0, g->n[3], g->p4, nrows, flag);
+    return finish_ingest(g);
+}
+
+hj_status hj_set_initial_value_device(hj_grid *g, const void *v0_device, hj_precision dtype, size_t count)
+{
+    g_err[0] = 0;
+    hj_status s = check_grid(g);
+    if (s != HJ_OK) return s;
+    if (!v0_device) return set_err(HJ_ERR_INVALID_ARG, "v0_device is NULL");
+    if (dtype != HJ_FP64 && dtype != HJ_FP32) return set_err(HJ_ERR_INVALID_ARG, "unknown dtype");
+    if (count != (size_t)g->ncell)
+        return set_err(HJ_ERR_INVALID_ARG, "count %zu != N1*N2*N3*N4 = %lld", count, g->ncell);
+    if ((s = activate(g)) != HJ_OK) return s;
+    if ((s = reset_state(g)) != HJ_OK) return s;
+    long long nrows = (long long)g->n[0] * g->n[1] * g->n[2];
+    int *flag = &g->dstate->nonfinite;
+    int blocks = grid_blocks(g->nint, 256);
+    if (g->prec == HJ_FP64) {
+        if (dtype == HJ_FP64)
+            ingest_kernel<double, double><<<blocks, 256, 0, g->stream>>>((const double *)v0_device, (double *)g->v0,
+                                                                         g->n[3], g->p4, nrows, flag);
+        else
+            ingest_kernel<float, double><<<blocks, 256, 0, g->stream>>>((const float *)v0_device, (double *)g->v0,
+                                                                        g->n[3], g->p4, nrows, flag);
+    } else {
+        if (dtype == HJ_FP64)
+            ingest_kernel<double, float><<<blocks, 256, 0, g->stream>>>((const double *)v0_device, (float *)g->v0,
+                                                                        g->n[3], g->p4, nrows, flag);
+        else
+            ingest_kernel<float, float><<<blocks, 256, 0, g->stream>>>((const float *)v0_device, (float *)g->v0,
+                                                                       g->n[3], g->p4, nrows, flag);
+    }
+    return finish_ingest(g);
+}
+
+hj_status hj_advance_brt(hj_grid *g, double T, double cfl, int64_t max_steps, hj_solve_stats *stats)
+{
+    g_err[0] = 0;
+    hj_status s = check_grid(g);
+    if (s != HJ_OK) return s;
+    if (!isfinite(T) || T < 0) return set_err(HJ_ERR_INVALID_ARG, "T must be finite and >= 0");
+    if (!isfinite(cfl) || !(cfl > 0) || cfl > 1) return set_err(HJ_ERR_INVALID_ARG, "cfl must be in (0, 1]");
+    if (max_steps < 0) return set_err(HJ_ERR_INVALID_ARG, "max_steps must be >= 0");
+    if (!g->has_dyn) return set_err(HJ_ERR_STATE, "hj_set_dynamics has not been called");
+    if (!g->has_value) return set_err(HJ_ERR_STATE, "no initial value (hj_set_initial_value)");
+    if ((s = activate(g)) != HJ_OK) return s;
+
+    const hj_kernel kern = effective_kernel(g);
+    int launches = 0;
+    HJ_CUDA(cudaEventRecord(g->ev[0], g->stream));
+    const int ncoef = g->n[2] * g->n[3];
+    if (g->prec == HJ_FP64)
+        prologue_kernel<double><<<1, 256, 0, g->stream>>>(g->dstate, g->geom, (const HjCoef<double> *)g->coef, ncoef, T, cfl);
+    else
+        prologue_kernel<float><<<1, 256, 0, g->stream>>>(g->dstate, g->geom, (const HjCoef<float> *)g->coef, ncoef, T, cfl);
+    ++launches;
+    HJ_CUDA(cudaGetLastError());
+    if ((s = pull_state(g)) != HJ_OK) return s;
+    const long long n_start = g->hstate->n;
+    const double dt_first = g->hstate->done ? 0.0 : g->hstate->dt;
+    long long taken = 0;
+    bool loop_started = false;
+    while (!g->hstate->done && g->hstate->status == HJ_OK && taken < max_steps) {
+        // predicted steps to the horizon (dt is constant until the cut last step)
+        const HjDevState &h = *g->hstate;
+        long long k = 1;
+        if (!h.last && h.dt > 0) {
+            double r = ceil((h.T - h.t) / h.dt);
+            k = r > 1 ? (r < 1e15 ? (long long)r : (long long)1e15) : 1;
+        }
+        if (k > max_steps - taken) k = max_steps - taken;
+        if (!loop_started) {
+            HJ_CUDA(cudaEventRecord(g->ev[1], g->stream));
+            loop_started = true;
+        }
+        for (long long i = 0; i < k; ++i) {
+            if ((s = launch_step(g, kern)) != HJ_OK) return s;
+            ++launches;
+        }
+        HJ_CUDA(cudaEventRecord(g->ev[2], g->stream));
+        if ((s = pull_state(g)) != HJ_OK) return s;
+        taken = g->hstate->n - n_start;
+    }
+    HJ_CUDA(cudaEventRecord(g->ev[3], g->stream));
+    HJ_CUDA(cudaEventSynchronize(g->ev[3]));
+    const HjDevState &h = *g->hstate;
+    if (h.status != HJ_OK)
+        return set_err((hj_status)h.status, "device reported %s", hj_status_string((hj_status)h.status));
+    if (stats) {
+        memset(stats, 0, sizeof(*stats));
+        stats->steps = h.n - n_start;
+        stats->total_steps = h.n;
+        stats->t_final = h.t;
+        stats->dt_first = stats->steps > 0 ? dt_first : 0.0;
+        stats->dt_last = stats->steps > 0 ? h.dt_prev : 0.0;
+        for (int d = 0; d < 4; ++d) stats->alpha_max[d] = h.alpha_prev[d];
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, g->ev[0], g->ev[3]);
+        stats->device_ms = ms;
+        if (loop_started) {
+            cudaEventElapsedTime(&ms, g->ev[1], g->ev[2]);
+            stats->loop_ms = ms;
+        }
+        stats->kernel = kern;
+        stats->launches = launches;
+    }
+    return HJ_OK;
+}
+
+hj_status hj_solve_brt(hj_grid *g, double T, double cfl, hj_solve_stats *stats)
+{
+    return hj_advance_brt(g, T, cfl, INT64_MAX, stats);
+}
+
+hj_status hj_read_value(const hj_grid *gc, double *out, size_t count)
+{
+    g_err[0] = 0;
+    hj_grid *g = (hj_grid *)gc;
+    hj_status s = check_grid(g);
+    if (s != HJ_OK) return s;
+    if (!out) return set_err(HJ_ERR_INVALID_ARG, "out is NULL");
+    if (count != (size_t)g->ncell)
+        return set_err(HJ_ERR_INVALID_ARG, "count %zu != N1*N2*N3*N4 = %lld", count, g->ncell);
+    if (!g->has_value) return set_err(HJ_ERR_STATE, "no initial value (hj_set_initial_value)");
+    if ((s = activate(g)) != HJ_OK) return s;
+    if ((s = pull_state(g)) != HJ_OK) return s;
+    const long long n = g->hstate->n;
+    const void *src = hj_value_ptr(g, n);
+    if (g->prec == HJ_FP64 && g->p4 == g->n[3]) {
+        HJ_CUDA(cudaMemcpyAsync(out, src, sizeof(double) * (size_t)g->ncell, cudaMemcpyDeviceToHost, g->stream));
+        HJ_CUDA(cudaStreamSynchronize(g->stream));
+        return HJ_OK;
+    }
+    // convert in chunks of rows into a free buffer, then copy each chunk out
+    void *free_buf;
+    size_t free_bytes;
+    if (n == 0) {
+        free_buf = g->buf;
+        free_bytes = 2 * (size_t)g->nint * g->esize;
+    } else {
+        free_buf = (char *)g->buf + (size_t)(n & 1) * g->nint * g->esize;  // the buffer the next step writes
+        free_bytes = (size_t)g->nint * g->esize;
+    }
+    const long long nrows = (long long)g->n[0] * g->n[1] * g->n[2];
+    long long rows_per_chunk = (long long)(free_bytes / (sizeof(double) * (size_t)g->n[3]));
+    if (rows_per_chunk < 1) return set_err(HJ_ERR_STATE, "no room to stage the readback");
+    for (long long r0 = 0; r0 < nrows; r0 += rows_per_chunk) {
+        long long nr = nrows - r0 < rows_per_chunk ? nrows - r0 : rows_per_chunk;
+        int blocks = grid_blocks(nr * g->n[3], 256);
+        if (g->prec == HJ_FP64)
+            readback_kernel<double, double><<<blocks, 256, 0, g->stream>>>((const double *)src, (double *)free_buf,
+                                                                           g->n[3], g->p4, r0, nr);
+        else
+            readback_kernel<float, double><<<blocks, 256, 0, g->stream>>>((const float *)src, (double *)free_buf,
+                                                                          g->n[3], g->p4, r0, nr);
+        HJ_CUDA(cudaGetLastError());
+        HJ_CUDA(cudaMemcpyAsync(out + r0 * g->n[3], free_buf, sizeof(double) * (size_t)(nr * g->n[3]),
+                                cudaMemcpyDeviceToHost, g->stream));
+    }
+    HJ_CUDA(cudaStreamSynchronize(g->stream));
+    return HJ_OK;
+}
+
+hj_status hj_read_value_device(const hj_grid *gc, void *out_device, hj_precision dtype, size_t count)
+{
+    g_err[0] = 0;
+    hj_grid *g = (hj_grid *)gc;
+    hj_status s = check_grid(g);
+    if (s != HJ_OK) return s;
+    if (!out_device) return set_err(HJ_ERR_INVALID_ARG, "out_device is NULL");
+    if (dtype != HJ_FP64 && dtype != HJ_FP32) return set_err(HJ_ERR_INVALID_ARG, "unknown dtype");
+    if (count != (size_t)g->ncell)
+        return set_err(HJ_ERR_INVALID_ARG, "count %zu != N1*N2*N3*N4 = %lld", count, g->ncell);
+    if (!g->has_value) return set_err(HJ_ERR_STATE, "no initial value (hj_set_initial_value)");
+    if ((s = activate(g)) != HJ_OK) return s;
+    if ((s = pull_state(g)) != HJ_OK) return s;
+    const void *src = hj_value_ptr(g, g->hstate->n);
+    const long long nrows = (long long)g->n[0] * g->n[1] * g->n[2];
+    int blocks = grid_blocks(g->ncell, 256);
+    if (g->prec == HJ_FP64) {
+        if (dtype == HJ_FP64)
+            readback_kernel<double, double><<<blocks, 256, 0, g->stream>>>((const double *)src, (double *)out_device,
+                                                                           g->n[3], g->p4, 0, nrows);
+        else
+            readback_kernel<double, float><<<blocks, 256, 0, g->stream>>>((const double *)src, (float *)out_device,
+                                                                          g->n[3], g->p4, 0, nrows);
+    } else {
+        if (dtype == HJ_FP64)
+            readback_kernel<float, double><<<blocks, 256, 0, g->stream>>>((const float *)src, (double *)out_device,
+                                                                          g->n[3], g->p4, 0, nrows);
+        else
+            readback_kernel<float, float><<<blocks, 256, 0, g->stream>>>((const float *)src, (float *)out_device,
+                                                                         g->n[3], g->p4, 0, nrows);
+    }
+    HJ_CUDA(cudaGetLastError());
+    HJ_CUDA(cudaStreamSynchronize(g->stream));
+    return HJ_OK;
+}
+
+hj_status hj_set_kernel(hj_grid *g, hj_kernel kernel)
+{
+    g_err[0] = 0;
+    hj_status s = check_grid(g);
+    if (s != HJ_OK) return s;
+    if (kernel != HJ_KERNEL_AUTO && kernel != HJ_KERNEL_GENERIC && kernel != HJ_KERNEL_TILED)
+        return set_err(HJ_ERR_INVALID_ARG, "unknown kernel %d", (int)kernel);
+    if (kernel == HJ_KERNEL_TILED && !g->tiled_ok)
+        return set_err(HJ_ERR_UNSUPPORTED, "the tiled kernel does not support this grid (FP32 car grids with "
+                                           "periodic theta only; set the dynamics first)");
+    g->kernel_req = kernel;
+    return HJ_OK;
+}
+
+hj_status hj_get_info(const hj_grid *g, hj_grid_info *info)
+{
+    g_err[0] = 0;
+    hj_status s = check_grid(g);
+    if (s != HJ_OK) return s;
+    if (!info) return set_err(HJ_ERR_INVALID_ARG, "info is NULL");
+    if ((s = activate(g)) != HJ_OK) return s;
+    if ((s = pull_state((hj_grid *)g)) != HJ_OK) return s;
+    memset(info, 0, sizeof(*info));
+    for (int d = 0; d < 4; ++d) {
+        info->n[d] = g->n[d];
+        info->lo[d] = g->lo[d];
+        info->hi[d] = g->hi[d];
+        info->dx[d] = g->h[d];
+    }
+    info->pitch4 = g->p4;
+    info->precision = g->prec;
+    info->kernel = effective_kernel(g);
+    info->periodic_mask = g->periodic;
+    info->has_value = g->has_value;
+    info->total_steps = g->hstate->n;
+    info->t = g->hstate->t;
+    info->device_bytes = g->device_bytes;
+    return HJ_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,129 @@
+// Device helpers shared by the step kernels of libhj: order-preserving
+// min/max, the fused alpha^max reduction, and the CFL/time-loop finaliser
+// that the last CTA of every step runs.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "hj_internal.h"
+
+// ---------------------------------------------------------------- min / max
+// FP64 min/max are slow on this GPU (they run on the FP64 unit).  For finite
+// doubles, flipping the magnitude bits of negative values gives an integer
+// key with the same order, so min/max become integer compares plus a select.
+__device__ __forceinline__ long long hj_key(double x)
+{
+    long long b = __double_as_longlong(x);
+    return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ double hj_max(double a, double b) { return hj_key(a) >= hj_key(b) ? a : b; }
+__device__ __forceinline__ double hj_min(double a, double b) { return hj_key(a) <= hj_key(b) ? a : b; }
+__device__ __forceinline__ float hj_max(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ float hj_min(float a, float b) { return fminf(a, b); }
+
+// Non-negative doubles order like their bit patterns read as unsigned.
+__device__ __forceinline__ unsigned long long hj_abits(double a) { return (unsigned long long)__double_as_longlong(a); }
+
+__device__ __forceinline__ unsigned long long hj_warp_max_u64(unsigned long long v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+        v = v > w ? v : w;
+    }
+    return v;
+}
+
+// ---------------------------------------------------------------- time loop
+
+// dt for the next step from alpha^max (Algorithm 1: dt = CFL / sum_d
+// alpha_d^max / dx_d), cut so that t lands on the horizon.  Same operation
+// order as the oracle's FP64 arithmetic, with explicit round-to-nearest
+// intrinsics so that no contraction can change a bit.
+__device__ __forceinline__ void hj_next_dt(HjDevState *st, const HjGeom &g, const double a[4], double t)
+{
+    double T = st->T;
+    if (!(t < T)) {
+        st->done = 1;
+        st->last = 0;
+        return;
+    }
+    double S = 0.0;
+#pragma unroll
+    for (int d = 0; d < 4; ++d)
+        S = __dadd_rn(S, __ddiv_rn(a[d], g.h[d]));
+    double dt = (S == 0.0) ? 0.0 : __ddiv_rn(st->cfl, S);
+    if (!(dt >= 0.0) || isinf(dt)) {
+        st->status = HJ_ERR_UNSTABLE;
+        st->done = 1;
+        return;
+    }
+    int last = (dt == 0.0) || (__dadd_rn(t, dt) >= T);
+    if (last) dt = __dadd_rn(T, -t);
+    st->dt = dt;
+    st->last = last;
+    st->done = 0;
+}
+
+// Run by one thread of the last CTA to finish a step: publish alpha^max,
+// advance t and n, compute the next dt, reset the per-step accumulators.
+__device__ __forceinline__ void hj_finalise(HjDevState *st, const HjGeom &g)
+{
+    __threadfence();
+    double a[4];
+    a[0] = __longlong_as_double((long long)atomicAdd(&st->alpha_bits[0], 0ull));
+    a[1] = __longlong_as_double((long long)atomicAdd(&st->alpha_bits[1], 0ull));
+    a[2] = g.alpha3;  // |a_opt| = a_max at every cell (bang-bang), |c3| for constant dynamics
+    a[3] = g.alpha4;
+#pragma unroll
+    for (int d = 0; d < 4; ++d) st->alpha_prev[d] = a[d];
+    double t = st->t, dt = st->dt;
+    double tn = st->last ? st->T : __dadd_rn(t, dt);
+    st->dt_prev = dt;
+    st->t = tn;
+    st->n = st->n + 1;
+    if (st->status == HJ_OK)
+        hj_next_dt(st, g, a, tn);
+    else
+        st->done = 1;
+    st->alpha_bits[0] = 0ull;
+    st->alpha_bits[1] = 0ull;
+    st->blocks_done = 0u;
+    __threadfence();
+}
+
+// Block-wide max of the CTA's |xdot_1|, |xdot_2| partials (bit patterns of
+// non-negative doubles), then the grid-wide atomic max and the last-CTA
+// finaliser.  Every thread of the block must call it.  `scratch` holds at
+// least 2 * 32 unsigned long long.
+__device__ __forceinline__ void hj_step_epilogue(HjDevState *st, const HjGeom &g, unsigned long long a1,
+                                                 unsigned long long a2, unsigned long long *scratch)
+{
+    a1 = hj_warp_max_u64(a1);
+    a2 = hj_warp_max_u64(a2);
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = (blockDim.x + 31) >> 5;
+    if (lane == 0) {
+        scratch[warp] = a1;
+        scratch[32 + warp] = a2;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < nwarp; ++w) {
+            a1 = a1 > scratch[w] ? a1 : scratch[w];
+            a2 = a2 > scratch[32 + w] ? a2 : scratch[32 + w];
+        }
+        atomicMax(&st->alpha_bits[0], a1);
+        atomicMax(&st->alpha_bits[1], a2);
+        __threadfence();
+        unsigned int prev = atomicAdd(&st->blocks_done, 1u);
+        if (prev == gridDim.x - 1) hj_finalise(st, g);
+    }
+}
+
+// Selects V after n steps' input and output buffers.
+template <typename T>
+__device__ __forceinline__ void hj_io_buffers(const T *v0, T *buf, long long nint, long long n, const T *&vin, T *&vout)
+{
+    vin = (n == 0) ? v0 : buf + ((n - 1) & 1) * nint;
+    vout = buf + (n & 1) * nint;
+}

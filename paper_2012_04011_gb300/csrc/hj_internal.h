@@ -1,0 +1,104 @@
+// Internal declarations of libhj shared by its translation units.
+// Nothing here is part of the C ABI (include/hj.h).
+#pragma once
+
+#include <cuda.h>  // CUtensorMap (type only; the driver is reached through cudaGetDriverEntryPointByVersion)
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "hj.h"
+
+// Per-axis treatment of the upwind side on axes 3 and 4 (v and theta).
+enum HjAxisMode : int32_t {
+    HJ_AXIS_CONTROL = 0,  // bang-bang control: u_opt follows the sign of the costate, so the
+                          // upwind value is max(V+, V-)  (Alg. 2, u_opt = argmax)
+    HJ_AXIS_PLUS = 1,     // fixed velocity >= 0: upwind value is V+
+    HJ_AXIS_MINUS = 2     // fixed velocity < 0: upwind value is V-
+};
+
+// Device-resident time-loop state of one grid.  Written by the prologue
+// kernel and by the last CTA of every step kernel ("finaliser"), read by the
+// next kernel on the same stream.
+struct HjDevState {
+    double t;                          // simulated time at the start of the next step
+    double dt;                         // size of the next step
+    double dt_prev;                    // size of the step just taken
+    double T;                          // horizon of the current call
+    double cfl;                        // Courant number of the current call
+    long long n;                       // steps since V0 was set
+    int last;                          // the next step is cut to land on T
+    int done;                          // t has reached T: step kernels exit at once
+    unsigned long long alpha_bits[2];  // running max of |xdot_1|, |xdot_2| of this step (FP64 bit patterns)
+    double alpha_prev[4];              // alpha_d^max reduced by the last step (or the prologue)
+    unsigned int blocks_done;          // CTAs of the current step that have finished
+    int status;                        // hj_status raised on the device (HJ_OK if none)
+    int nonfinite;                     // ingest saw a NaN or Inf
+    int pad_;
+};
+
+// Grid geometry handed to kernels by value.
+struct HjGeom {
+    int32_t n1, n2, n3, n4;  // points per axis
+    int32_t p4;              // internal row pitch along theta (n4 rounded up to a multiple of 4)
+    int32_t periodic;        // bit d: axis d periodic
+    int32_t mode3, mode4;    // HjAxisMode of axes 3 and 4
+    double h[4];             // grid spacing dx_d (FP64, as the API defines it)
+    double k3, k4;           // |xdot_3|/dx_3 and |xdot_4|/dx_4 (constant over the grid)
+    double alpha3, alpha4;   // |xdot_3|, |xdot_4| (constant over the grid)
+};
+
+// Per-(v, theta) coefficients: c1 = xdot_1/dx_1, c2 = xdot_2/dx_2 (signed),
+// ks = |c1| + |c2| + k3 + k4, a1 = |xdot_1|, a2 = |xdot_2|.
+template <typename T>
+struct HjCoef {
+    T c1, c2, ks, a1, a2;
+};
+
+struct hj_grid {
+    int32_t n[4];
+    int32_t p4;
+    double lo[4], hi[4], h[4];
+    uint32_t periodic;
+    hj_precision prec;
+    size_t esize;          // bytes per value on the device
+    long long ncell;       // n1*n2*n3*n4
+    long long nint;        // n1*n2*n3*p4 (internal values per array)
+    cudaStream_t stream;
+    bool own_stream;
+    int device;
+
+    void *v0;              // V0 (internal layout)
+    void *buf;             // two ping-pong buffers, back to back (2*nint values)
+    void *coef;            // HjCoef<T>[n3*n4]
+    float *tab_tiled;      // tiled-kernel tables: v_k [n3], cos/dx1 [p4], sin/dx2 [p4], |cos| [p4], |sin| [p4]
+    HjDevState *dstate;
+    HjDevState *hstate;    // pinned host mirror
+
+    bool has_dyn, has_value;
+    hj_dynamics dyn;
+    double params[4];
+    HjGeom geom;
+
+    hj_kernel kernel_req;  // requested by hj_set_kernel
+    bool tiled_ok;         // the tiled kernel supports this grid
+    CUtensorMap tmap[3];   // V0, buffer A, buffer B (tiled kernel, FP32 only)
+    int32_t tile_ty, tile_tv, tile_xc, tile_rg, tile_stages;
+    int32_t tiled_ctas;
+
+    cudaEvent_t ev[4];
+    size_t device_bytes;
+};
+
+// Launchers (each returns the CUDA error of its launch).
+cudaError_t hj_launch_step_generic(hj_grid *g);
+cudaError_t hj_launch_step_tiled(hj_grid *g);
+// Set up the tiled kernel for g (tensor maps, tile shape); false if unsupported.
+bool hj_tiled_setup(hj_grid *g, char *why, size_t why_len);
+
+// Pointer of the value buffer that holds V after n steps.
+inline void *hj_value_ptr(const hj_grid *g, long long n)
+{
+    if (n == 0) return g->v0;
+    char *base = (char *)g->buf;
+    return base + ((n - 1) & 1) * (size_t)g->nint * g->esize;
+}

@@ -1,0 +1,139 @@
+// Generic HJ step kernel: one thread per cell (grid-stride), neighbours read
+// through L1/L2.  Supports every grid, both precisions and any periodic
+// mask.  It is the FP64 path (which is bound by the FP64 ALU on this GPU,
+// not by HBM) and the FP32 fallback for grids the tiled kernel rejects.
+//
+// Per cell it computes one step of Algorithm 2 (Sec. II-B of arxiv
+// 2012.04011) in upwind form.  With the local dissipation alpha_d = |xdot_d|
+// the Lax-Friedrichs rate of one axis,
+//     xdot_d (D+ + D-)/2 + |xdot_d| (D+ - D-)/2,
+// equals xdot_d D+ when xdot_d >= 0 and xdot_d D- otherwise, i.e.
+//     (|xdot_d| / dx_d) (V_up - V_c)
+// with V_up the neighbour on the side the flow comes from.  On a control
+// axis the bang-bang u_opt takes the sign of the costate, so V_up is
+// max(V+, V-).  Summing over axes:
+//     V_new = min(V0, V_c + dt * (sum_d K_d V_up,d - K_sum V_c)),
+// with K_d = |xdot_d| / dx_d.  In FP64 that is 1 DMUL + 5 DFMA per cell; the
+// FP32 variant keeps the differences (V_up - V_c) for accuracy.
+#include "hj_device.cuh"
+
+namespace {
+
+template <typename T>
+struct Neigh {
+    T m, p;  // values at index - 1 and + 1 along one axis (ghosts already applied)
+};
+
+// Neighbours along one axis of a cell at offset o with index i of N and
+// stride s.  Ends: periodic wrap, or linear extrapolation
+// V_{-1} = 2 V_0 - V_1, V_N = 2 V_{N-1} - V_{N-2} (the "extrapolated points"
+// of Sec. II-B).
+template <typename T>
+__device__ __forceinline__ Neigh<T> axis_neighbours(const T *__restrict__ v, long long o, int i, int N, long long s,
+                                                    bool periodic, T vc)
+{
+    Neigh<T> r;
+    if (i > 0)
+        r.m = v[o - s];
+    else
+        r.m = periodic ? v[o + (long long)(N - 1) * s] : T(2) * vc - v[o + s];
+    if (i < N - 1)
+        r.p = v[o + s];
+    else
+        r.p = periodic ? v[o - (long long)(N - 1) * s] : T(2) * vc - v[o - s];
+    return r;
+}
+
+template <typename T>
+__device__ __forceinline__ T upwind_value(const Neigh<T> &nb, int mode)
+{
+    if (mode == HJ_AXIS_CONTROL) return hj_max(nb.p, nb.m);
+    return mode == HJ_AXIS_PLUS ? nb.p : nb.m;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) hj_step_generic_kernel(const T *__restrict__ v0, T *__restrict__ buf,
+                                                               const HjCoef<T> *__restrict__ coef, HjDevState *st,
+                                                               const HjGeom g, long long nint)
+{
+    __shared__ unsigned long long scratch[64];
+    if (st->done) return;  // uniform: written by the previous kernel on this stream
+    const long long n = st->n;
+    const T dt = (T)st->dt;
+    const T *vin;
+    T *vout;
+    hj_io_buffers<T>(v0, buf, nint, n, vin, vout);
+
+    const unsigned int N1 = g.n1, N2 = g.n2, N3 = g.n3, N4 = g.n4;
+    const long long s3 = g.p4, s2 = (long long)N3 * g.p4, s1 = (long long)N2 * s2;
+    const unsigned long long ncell = (unsigned long long)N1 * N2 * N3 * N4;
+    const T k3 = (T)g.k3, k4 = (T)g.k4;
+    unsigned long long am1 = 0ull, am2 = 0ull;
+
+    for (unsigned long long c = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; c < ncell;
+         c += (unsigned long long)gridDim.x * blockDim.x) {
+        const unsigned long long row = c / N4;
+        const int l = (int)(c - row * N4);
+        const unsigned long long r2 = row / N3;
+        const int k = (int)(row - r2 * N3);
+        const int i = (int)(r2 / N2);
+        const int j = (int)(r2 - (unsigned long long)i * N2);
+        const long long o = (long long)row * g.p4 + l;
+
+        const T vc = vin[o];
+        const Neigh<T> nx = axis_neighbours<T>(vin, o, i, N1, s1, g.periodic & 1, vc);
+        const Neigh<T> ny = axis_neighbours<T>(vin, o, j, N2, s2, (g.periodic >> 1) & 1, vc);
+        const Neigh<T> nv = axis_neighbours<T>(vin, o, k, N3, s3, (g.periodic >> 2) & 1, vc);
+        const Neigh<T> nt = axis_neighbours<T>(vin, o, l, N4, 1, (g.periodic >> 3) & 1, vc);
+
+        const HjCoef<T> cf = coef[k * N4 + l];
+        const T u1 = cf.c1 >= T(0) ? nx.p : nx.m;
+        const T u2 = cf.c2 >= T(0) ? ny.p : ny.m;
+        const T u3 = upwind_value<T>(nv, g.mode3);
+        const T u4 = upwind_value<T>(nt, g.mode4);
+        const T K1 = cf.c1 >= T(0) ? cf.c1 : -cf.c1;
+        const T K2 = cf.c2 >= T(0) ? cf.c2 : -cf.c2;
+        T vn;
+        if constexpr (sizeof(T) == 8) {
+            T r = -cf.ks * vc;
+            r = fma(K1, u1, r);
+            r = fma(K2, u2, r);
+            r = fma(k3, u3, r);
+            r = fma(k4, u4, r);
+            vn = fma(dt, r, vc);
+        } else {
+            T r = K1 * (u1 - vc);
+            r = fmaf(K2, u2 - vc, r);
+            r = fmaf(k3, u3 - vc, r);
+            r = fmaf(k4, u4 - vc, r);
+            vn = fmaf(dt, r, vc);
+        }
+        vout[o] = hj_min(v0[o], vn);  // BRT min with the target (Algorithm 2)
+
+        // alpha_d^max: the largest |xdot_d| among the cells this thread updated
+        const unsigned long long b1 = hj_abits((double)cf.a1), b2 = hj_abits((double)cf.a2);
+        am1 = am1 > b1 ? am1 : b1;
+        am2 = am2 > b2 ? am2 : b2;
+    }
+    hj_step_epilogue(st, g, am1, am2, scratch);
+}
+
+}  // namespace
+
+cudaError_t hj_launch_step_generic(hj_grid *g)
+{
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);
+    const int threads = 256;
+    long long want = (g->ncell + threads - 1) / threads;
+    long long cap = (long long)(sms > 0 ? sms : 1) * 8;
+    int blocks = (int)(want < cap ? want : cap);
+    if (blocks < 1) blocks = 1;
+    if (g->prec == HJ_FP64)
+        hj_step_generic_kernel<double><<<blocks, threads, 0, g->stream>>>(
+            (const double *)g->v0, (double *)g->buf, (const HjCoef<double> *)g->coef, g->dstate, g->geom, g->nint);
+    else
+        hj_step_generic_kernel<float><<<blocks, threads, 0, g->stream>>>(
+            (const float *)g->v0, (float *)g->buf, (const HjCoef<float> *)g->coef, g->dstate, g->geom, g->nint);
+    return cudaGetLastError();
+}

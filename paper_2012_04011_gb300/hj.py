@@ -1,0 +1,282 @@
+"""Thin ctypes binding of libhj (include/hj.h): argument marshalling only.
+
+Every function keeps the C name and returns what the C call writes to its
+out-parameters; a status other than HJ_OK raises HjError with the library's
+message.  All computation happens in the CUDA library; there is no Python
+or CPU fallback: if libhj.so cannot be loaded, importing the binding raises.
+
+Device arrays may be passed as PyTorch CUDA tensors (PyTorch is used only for
+device memory and streams) or as raw integer device pointers.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import _build
+
+HJ_OK, HJ_ERR_INVALID_ARG, HJ_ERR_STATE, HJ_ERR_OOM, HJ_ERR_CUDA, HJ_ERR_UNSTABLE, HJ_ERR_TIMEOUT, \
+    HJ_ERR_UNSUPPORTED = range(8)
+HJ_FP64, HJ_FP32 = 0, 1
+HJ_DYN_CAR4D, HJ_DYN_CONST = 0, 1
+HJ_KERNEL_AUTO, HJ_KERNEL_GENERIC, HJ_KERNEL_TILED = 0, 1, 2
+PERIODIC_THETA = 0b1000
+
+
+class HjError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{status_name(status)}: {message}")
+        self.status = status
+
+
+class hj_solve_stats(ctypes.Structure):
+    _fields_ = [
+        ("steps", ctypes.c_int64),
+        ("total_steps", ctypes.c_int64),
+        ("t_final", ctypes.c_double),
+        ("dt_first", ctypes.c_double),
+        ("dt_last", ctypes.c_double),
+        ("alpha_max", ctypes.c_double * 4),
+        ("device_ms", ctypes.c_double),
+        ("loop_ms", ctypes.c_double),
+        ("kernel", ctypes.c_int32),
+        ("launches", ctypes.c_int32),
+    ]
+
+    def as_dict(self) -> dict:
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["alpha_max"] = list(self.alpha_max)
+        return d
+
+
+class hj_grid_info(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int32 * 4),
+        ("pitch4", ctypes.c_int32),
+        ("precision", ctypes.c_int32),
+        ("kernel", ctypes.c_int32),
+        ("lo", ctypes.c_double * 4),
+        ("hi", ctypes.c_double * 4),
+        ("dx", ctypes.c_double * 4),
+        ("periodic_mask", ctypes.c_uint32),
+        ("has_value", ctypes.c_int32),
+        ("total_steps", ctypes.c_int64),
+        ("t", ctypes.c_double),
+        ("device_bytes", ctypes.c_size_t),
+    ]
+
+    def as_dict(self) -> dict:
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        for k in ("n", "lo", "hi", "dx"):
+            d[k] = list(d[k])
+        return d
+
+
+# symbol -> (restype, argtypes); the exported C ABI
+_VP = ctypes.c_void_p
+_SIGS = {
+    "hj_create_grid": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(ctypes.c_double), ctypes.c_uint32, ctypes.c_int, _VP,
+                                      ctypes.POINTER(_VP)]),
+    "hj_set_dynamics": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_int32]),
+    "hj_set_initial_value": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.c_size_t]),
+    "hj_set_initial_value_device": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_size_t]),
+    "hj_solve_brt": (ctypes.c_int, [_VP, ctypes.c_double, ctypes.c_double, ctypes.POINTER(hj_solve_stats)]),
+    "hj_advance_brt": (ctypes.c_int, [_VP, ctypes.c_double, ctypes.c_double, ctypes.c_int64,
+                                      ctypes.POINTER(hj_solve_stats)]),
+    "hj_read_value": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.c_size_t]),
+    "hj_read_value_device": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_size_t]),
+    "hj_set_kernel": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "hj_get_info": (ctypes.c_int, [_VP, ctypes.POINTER(hj_grid_info)]),
+    "hj_destroy_grid": (None, [_VP]),
+    "hj_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "hj_last_error": (ctypes.c_char_p, []),
+    "hj_version": (ctypes.c_int32, []),
+}
+SYMBOLS = tuple(_SIGS)
+
+
+def _load() -> ctypes.CDLL:
+    path = _build.LIB_PATH
+    if not os.path.exists(path):
+        raise ImportError(f"libhj.so is not built ({path}); run __graft_entry__.build() or "
+                          f"python -m paper_2012_04011_gb300._build")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+def status_name(s: int) -> str:
+    return lib.hj_status_string(int(s)).decode()
+
+
+def _check(status: int):
+    if status != HJ_OK:
+        raise HjError(status, lib.hj_last_error().decode())
+
+
+def _dptr(x) -> int:
+    """Device pointer of a torch CUDA tensor (or an int pointer)."""
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        if not x.is_cuda:
+            raise ValueError("expected a CUDA tensor")
+        if not x.is_contiguous():
+            raise ValueError("expected a contiguous tensor")
+        return int(x.data_ptr())
+    raise TypeError(f"cannot take a device pointer of {type(x)}")
+
+
+def _dtype_code(x) -> int:
+    name = str(getattr(x, "dtype", ""))
+    if name.endswith("float64"):
+        return HJ_FP64
+    if name.endswith("float32"):
+        return HJ_FP32
+    raise TypeError(f"unsupported dtype {name}")
+
+
+# ------------------------------------------------------------- C-named calls
+
+def hj_version() -> int:
+    return int(lib.hj_version())
+
+
+def hj_create_grid(n, lo, hi, periodic_mask: int = PERIODIC_THETA, prec: int = HJ_FP32, cuda_stream=None):
+    """Returns the opaque grid handle (an int)."""
+    cn = (ctypes.c_int32 * 4)(*[int(v) for v in n])
+    clo = (ctypes.c_double * 4)(*[float(v) for v in lo])
+    chi = (ctypes.c_double * 4)(*[float(v) for v in hi])
+    out = _VP()
+    stream = None if cuda_stream is None else ctypes.c_void_p(int(cuda_stream))
+    _check(lib.hj_create_grid(cn, clo, chi, int(periodic_mask), int(prec), stream, ctypes.byref(out)))
+    return out.value
+
+
+def hj_set_dynamics(g, kind: int, params):
+    p = np.ascontiguousarray(np.asarray(params, dtype=np.float64))
+    _check(lib.hj_set_dynamics(g, int(kind), p.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(p.size)))
+
+
+def hj_set_initial_value(g, v0: np.ndarray):
+    a = np.ascontiguousarray(v0, dtype=np.float64)
+    _check(lib.hj_set_initial_value(g, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), a.size))
+
+
+def hj_set_initial_value_device(g, v0_device, count: int | None = None, dtype: int | None = None):
+    cnt = int(v0_device.numel()) if count is None else int(count)
+    code = _dtype_code(v0_device) if dtype is None else int(dtype)
+    _check(lib.hj_set_initial_value_device(g, ctypes.c_void_p(_dptr(v0_device)), code, cnt))
+
+
+def hj_solve_brt(g, T: float, cfl: float = 0.8) -> hj_solve_stats:
+    st = hj_solve_stats()
+    _check(lib.hj_solve_brt(g, float(T), float(cfl), ctypes.byref(st)))
+    return st
+
+
+def hj_advance_brt(g, T: float, cfl: float, max_steps: int) -> hj_solve_stats:
+    st = hj_solve_stats()
+    _check(lib.hj_advance_brt(g, float(T), float(cfl), int(max_steps), ctypes.byref(st)))
+    return st
+
+
+def hj_read_value(g, out: np.ndarray | None = None, shape=None) -> np.ndarray:
+    info = hj_get_info(g)
+    n = tuple(info.n)
+    if out is None:
+        out = np.empty(n if shape is None else shape, dtype=np.float64)
+    if out.dtype != np.float64 or not out.flags.c_contiguous:
+        raise ValueError("out must be a C-contiguous float64 array")
+    _check(lib.hj_read_value(g, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), out.size))
+    return out
+
+
+def hj_read_value_device(g, out_device, count: int | None = None, dtype: int | None = None):
+    cnt = int(out_device.numel()) if count is None else int(count)
+    code = _dtype_code(out_device) if dtype is None else int(dtype)
+    _check(lib.hj_read_value_device(g, ctypes.c_void_p(_dptr(out_device)), code, cnt))
+    return out_device
+
+
+def hj_set_kernel(g, kernel: int):
+    _check(lib.hj_set_kernel(g, int(kernel)))
+
+
+def hj_get_info(g) -> hj_grid_info:
+    info = hj_grid_info()
+    _check(lib.hj_get_info(g, ctypes.byref(info)))
+    return info
+
+
+def hj_destroy_grid(g):
+    lib.hj_destroy_grid(g)
+
+
+# ------------------------------------------------------------- convenience
+
+class Grid:
+    """Owns one hj_grid; the methods are the C calls above."""
+
+    def __init__(self, n, lo, hi, periodic_mask=PERIODIC_THETA, prec=HJ_FP32, cuda_stream=None):
+        self.n = tuple(int(v) for v in n)
+        self.handle = hj_create_grid(n, lo, hi, periodic_mask, prec, cuda_stream)
+
+    @classmethod
+    def for_workload(cls, w, prec=HJ_FP32, cuda_stream=None):
+        g = cls(w.grid.n, w.grid.lo, w.grid.hi, w.grid.periodic, prec, cuda_stream)
+        g.set_dynamics(HJ_DYN_CAR4D, (w.a_max, w.w_max))
+        return g
+
+    def set_dynamics(self, kind, params):
+        hj_set_dynamics(self.handle, kind, params)
+
+    def set_initial_value(self, v0):
+        if hasattr(v0, "is_cuda") and v0.is_cuda:
+            hj_set_initial_value_device(self.handle, v0)
+        else:
+            hj_set_initial_value(self.handle, np.asarray(v0))
+
+    def solve_brt(self, T, cfl=0.8) -> hj_solve_stats:
+        return hj_solve_brt(self.handle, T, cfl)
+
+    def advance_brt(self, T, cfl, max_steps) -> hj_solve_stats:
+        return hj_advance_brt(self.handle, T, cfl, max_steps)
+
+    def read_value(self, out=None) -> np.ndarray:
+        return hj_read_value(self.handle, out)
+
+    def read_value_device(self, out):
+        return hj_read_value_device(self.handle, out)
+
+    def set_kernel(self, kernel):
+        hj_set_kernel(self.handle, kernel)
+
+    def info(self) -> hj_grid_info:
+        return hj_get_info(self.handle)
+
+    def close(self):
+        if self.handle:
+            hj_destroy_grid(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
