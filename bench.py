@@ -1,0 +1,395 @@
+"""Benchmark: 4D HJ reachability BRT solves on GB300 through libhj.
+
+One benchmark step is one whole BRT solve of the 128x128x64x96 car workload
+(seeded obstacles, T = 2.0 s, CFL 0.8, 352 time steps): V0 ingest from a
+device-resident array, the full time loop, and the readback of V into a
+device-resident array.  Throughput is cell-updates/s (cells x time steps /
+s); the dominant kernel's roofline is the HBM bound (12 algorithmic bytes per
+FP32 cell-update: read V_n, read V0, write V_{n+1}).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank solves its own replica (no data-path
+collective); the JSON line reports the whole-job rate.  --impl reference
+times the FP64 CPU oracle on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "4D HJ cell-updates/s (fraction of HBM peak) + p99 re-solve latency vs FP64 path"
+UNIT = "cell-updates/s"
+WORKLOAD = "car4d_128x128x64x96"
+BYTES_PER_UPDATE = {"f32": 12, "f64": 24}
+PROFILE = os.path.join(ROOT, "profiles", "hj_step_tiled_car4d_128x128x64x96.md")
+KERNEL_SOURCES = ["hj_step_tiled.cu", "hj_device.cuh", "hj_internal.h"]
+
+
+# ------------------------------------------------------------------ helpers
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2012_04011_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the tiled step kernel from the committed ncu
+    summary, if it was taken on the current kernel source; else None."""
+    try:
+        text = open(PROFILE).read()
+    except OSError:
+        return None
+    m_hash = re.search(r"kernel_source_sha256:\s*([0-9a-f]+)", text)
+    m_tr = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if not m_hash or not m_tr or m_hash.group(1) != kernel_hash():
+        return None
+    return float(m_tr.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.gpu)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.thread.join(timeout=2)
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def visible_gpu_index(local_rank: int) -> int:
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    ids = [v for v in vis.split(",") if v.strip() != ""]
+    if ids and ids[local_rank % len(ids)].strip().isdigit():
+        return int(ids[local_rank % len(ids)])
+    return local_rank
+
+
+# ------------------------------------------------------------------ oracle (CPU baseline)
+
+def oracle_sample(w, V0, steps: int, nthreads: int):
+    """Time `steps` oracle time steps of the workload (the whole per-step hot
+    path: alpha reduction, CFL step, stencil update, BRT min)."""
+    import oracle
+    P = oracle.Problem(w.grid.n, w.grid.lo, w.grid.hi, w.grid.periodic, oracle.DYN_CAR4D, (w.a_max, w.w_max))
+    t0 = time.perf_counter()
+    _, _, dts = oracle.advance(P, V0, V0, 0.0, w.T, w.cfl, max_steps=steps, nthreads=nthreads)
+    el = time.perf_counter() - t0
+    return len(dts) * V0.size / el, el, len(dts)
+
+
+def cpu_threads() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+# ------------------------------------------------------------------ reference arm
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_2012_04011_gb300 import scenes
+    w = scenes.workload(WORKLOAD)
+    V0 = scenes.initial_value(w.grid, w.scene)
+    nthreads = cpu_threads()
+    per_step = args.cpu_sample_steps
+    for _ in range(args.warmup):
+        oracle_sample(w, V0, per_step, nthreads)
+    updates, elapsed = 0, 0.0
+    for _ in range(args.steps):
+        _, el, nst = oracle_sample(w, V0, per_step, nthreads)
+        updates += nst * V0.size
+        elapsed += el
+    value = updates / elapsed
+    sample = (f"{per_step} oracle time steps of the {WORKLOAD} solve per benchmark step "
+              f"({per_step * V0.size:.3e} cell-updates), FP64, OpenMP over x")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded obstacles)",
+        "config": {"workload": WORKLOAD, "grid": list(w.grid.n), "horizon_s": w.T, "cfl": w.cfl,
+                   "sample_time_steps_per_step": per_step},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": nthreads, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ our arm
+
+def run_ours(args):
+    import torch
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2012_04011_gb300 import hj, scenes
+
+    w = scenes.workload(WORKLOAD)
+    V0 = scenes.initial_value(w.grid, w.scene)
+    ncell = V0.size
+    stream = torch.cuda.current_stream()
+    V0_dev = torch.from_numpy(V0).to("cuda")
+    out32 = torch.empty(ncell, dtype=torch.float32, device="cuda")
+    out64 = torch.empty(ncell, dtype=torch.float64, device="cuda")
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x: float) -> float:
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    def solve_once(g, out):
+        hj.hj_set_initial_value_device(g.handle, V0_dev)
+        st = hj.hj_solve_brt(g.handle, w.T, w.cfl)
+        hj.hj_read_value_device(g.handle, out)
+        return st
+
+    results = {}
+    for prec_name, prec, out, K, W in (("f32", hj.HJ_FP32, out32, args.steps, args.warmup),
+                                       ("f64", hj.HJ_FP64, out64, max(1, min(args.steps, args.fp64_steps)), 1)):
+        if prec_name == "f64" and args.no_fp64:
+            continue
+        g = hj.Grid(w.grid.n, w.grid.lo, w.grid.hi, w.grid.periodic, prec, stream.cuda_stream)
+        g.set_dynamics(hj.HJ_DYN_CAR4D, (w.a_max, w.w_max))
+        tuned = None
+        if prec == hj.HJ_FP32 and not args.no_autotune:
+            # pick the tile shape by timing candidates (outside the timed region)
+            hj.hj_set_initial_value_device(g.handle, V0_dev)
+            tried = g.autotune(8)
+            tuned = {"shape": list(g.info().tile), "ctas": g.info().tile_ctas,
+                     "tried": [t.as_dict() for t in tried]}
+        for _ in range(W):
+            solve_once(g, out)
+        barrier()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        lat, loop_ms, steps_total, launches = [], 0.0, 0, 0
+        sampler = ClockSampler(visible_gpu_index(local)) if prec_name == "f32" else None
+        if sampler:
+            sampler.__enter__()
+        ev0.record(stream)
+        for _ in range(K):
+            e_a, e_b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e_a.record(stream)
+            st = solve_once(g, out)
+            e_b.record(stream)
+            e_b.synchronize()
+            lat.append(e_a.elapsed_time(e_b))
+            loop_ms += st.loop_ms
+            steps_total += st.steps
+            launches += st.launches + 2  # + ingest and readback kernels
+        ev1.record(stream)
+        barrier()
+        if sampler:
+            sampler.__exit__(None, None, None)
+        ms = max_over_ranks(ev0.elapsed_time(ev1))
+        kernel = g.info().kernel
+        g.close()
+        updates = world * ncell * steps_total  # all ranks
+        results[prec_name] = {
+            "ms_total": ms, "K": K, "value": updates / (ms * 1e-3), "ms_per_step": ms / K,
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+            "avg_step_kernel_ms": loop_ms / steps_total, "time_steps_per_solve": steps_total // K,
+            "launches": launches, "kernel": kernel, "clocks": sampler.summary() if sampler else None,
+            "tile": tuned,
+        }
+
+    # end to end through the C ABI with host buffers (pinned), copies timed
+    e2e = None
+    if not args.no_e2e:
+        h_v0 = torch.from_numpy(V0).pin_memory()
+        h_out = torch.empty(ncell, dtype=torch.float64).pin_memory()
+        g = hj.Grid(w.grid.n, w.grid.lo, w.grid.hi, w.grid.periodic, hj.HJ_FP32, stream.cuda_stream)
+        g.set_dynamics(hj.HJ_DYN_CAR4D, (w.a_max, w.w_max))
+        if results["f32"]["tile"]:
+            g.set_tile_shape(results["f32"]["tile"]["shape"])
+        v0_np, out_np = h_v0.numpy(), h_out.numpy()
+
+        def e2e_once():
+            hj.hj_set_initial_value(g.handle, v0_np)
+            st = hj.hj_solve_brt(g.handle, w.T, w.cfl)
+            hj.hj_read_value(g.handle, out_np.reshape(V0.shape))
+            return st
+
+        for _ in range(max(1, args.warmup)):
+            e2e_once()
+        barrier()
+        t0 = time.perf_counter()
+        st_steps = 0
+        Ke = max(1, min(args.steps, args.e2e_steps))
+        for _ in range(Ke):
+            st_steps += e2e_once().steps
+        barrier()
+        el = max_over_ranks(time.perf_counter() - t0)
+        g.close()
+        e2e = {"value": world * ncell * st_steps / el, "unit": UNIT,
+               "h2d_bytes_per_step": int(V0.nbytes), "d2h_bytes_per_step": int(h_out.numel() * 8),
+               "ms_per_step": 1e3 * el / Ke}
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return 0
+
+    r32 = results["f32"]
+    peak, peak_kind = measured_peaks()
+    achieved = BYTES_PER_UPDATE["f32"] * ncell / (r32["avg_step_kernel_ms"] * 1e-3) / 1e9
+    traffic = profiled_traffic()
+    line = {
+        "metric": METRIC, "value": r32["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": r32["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded obstacles)",
+        "config": {"workload": WORKLOAD, "grid": list(w.grid.n), "horizon_s": w.T, "cfl": w.cfl,
+                   "time_steps_per_solve": r32["time_steps_per_solve"],
+                   "step": "one BRT solve: V0 ingest from HBM, full time loop, V readback to HBM",
+                   "l2": "no flush needed: V0 and both V buffers are 403 MB each (> 129 MB L2)",
+                   "parallelism": f"replicas x{world}",
+                   "tile": r32["tile"]},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "hj_step_tiled_kernel", "peak_source": f"{peak_kind} hbm_gbs",
+                     "bytes_per_update": BYTES_PER_UPDATE["f32"],
+                     "avg_launch_ms": r32["avg_step_kernel_ms"]},
+        "latency_ms": r32["latency_ms"],
+        "clocks": r32["clocks"],
+        "gpu_launches": r32["launches"],
+        "e2e": e2e,
+    }
+    if "f64" in results:
+        r64 = results["f64"]
+        # the FP64 path is bound by the FP64 ALU on this GPU, not by HBM
+        line["fp64_path"] = {
+            "value": r64["value"], "unit": UNIT, "ms_per_step": r64["ms_per_step"], "steps": r64["K"],
+            "latency_ms": r64["latency_ms"], "avg_step_kernel_ms": r64["avg_step_kernel_ms"],
+            "hbm_frac": BYTES_PER_UPDATE["f64"] * ncell / (r64["avg_step_kernel_ms"] * 1e-3) / 1e9 / peak,
+            "speedup_fp32_over_fp64": r32["value"] / r64["value"],
+        }
+    if world == 1 and not args.no_cpu_baseline:
+        nthreads = cpu_threads()
+        rate, el, nst = oracle_sample(w, V0, args.cpu_sample_steps, nthreads)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": nthreads, "kind": "oracle",
+                                "sample": f"{nst} oracle time steps of the {WORKLOAD} solve "
+                                          f"({nst * ncell:.3e} cell-updates, {el:.1f} s), FP64, OpenMP over x"}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--cpu-sample-steps", type=int, default=8)
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        print("note: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -99,6 +99,14 @@ typedef struct {
     int32_t launches;      /* kernels launched by this call */
 } hj_solve_stats;
 
+/* One tile shape of the tiled kernel and its measured step time. */
+typedef struct {
+    int32_t shape[4];      /* rows along y, rows along v, x planes per work item, smem ring stages */
+    int32_t threads;       /* threads per CTA */
+    int32_t ctas;          /* CTAs per launch */
+    double ms_per_step;    /* mean device time of one step kernel (CUDA events) */
+} hj_tile_result;
+
 typedef struct {
     int32_t n[4];
     int32_t pitch4;        /* internal row pitch along theta (N4 rounded up) */
@@ -110,6 +118,8 @@ typedef struct {
     int64_t total_steps;
     double t;
     size_t device_bytes;   /* device memory held by the grid */
+    int32_t tile[4];       /* tiled kernel shape in use (zeros if the tiled kernel is unavailable) */
+    int32_t tile_ctas;     /* CTAs per tiled step launch */
 } hj_grid_info;
 
 /* Create a grid of n[0]*n[1]*n[2]*n[3] cells on the current CUDA device.
@@ -172,6 +182,23 @@ HJ_API hj_status hj_read_value_device(const hj_grid *g, void *out_device, hj_pre
 /* Choose the step kernel.  HJ_KERNEL_TILED on a grid that it does not
  * support returns HJ_ERR_UNSUPPORTED and leaves the choice unchanged. */
 HJ_API hj_status hj_set_kernel(hj_grid *g, hj_kernel kernel);
+
+/* Tile shape of the tiled kernel: shape = {rows along y, rows along v, x
+ * planes per work item, shared-memory stages}; a 0 entry is chosen
+ * automatically.  HJ_ERR_UNSUPPORTED if the grid has no tiled kernel or the
+ * shape does not fit (the previous shape then stays). */
+HJ_API hj_status hj_set_tile_shape(hj_grid *g, const int32_t shape[4]);
+
+/* Autotune the tiled kernel: time steps_per_trial (>= 1) step launches for
+ * each candidate tile shape and keep the fastest.  Must be called right
+ * after hj_set_initial_value[_device] (no step taken yet): trial steps read
+ * V0 and write only the ping-pong buffers, and the time-loop state is put
+ * back afterwards, so the next solve is unchanged.  results (may be NULL)
+ * receives up to max_results candidates in the order tried, *nresults (may
+ * be NULL) their count.  HJ_ERR_UNSUPPORTED without a tiled kernel,
+ * HJ_ERR_STATE after a step. */
+HJ_API hj_status hj_autotune(hj_grid *g, int32_t steps_per_trial, hj_tile_result *results, int32_t max_results,
+                             int32_t *nresults);
 
 /* Describe the grid (sizes, spacings, time, memory). */
 HJ_API hj_status hj_get_info(const hj_grid *g, hj_grid_info *info);

@@ -679,6 +679,155 @@ hj_status hj_set_kernel(hj_grid *g, hj_kernel kernel)
     return HJ_OK;
 }
 
+hj_status hj_set_tile_shape(hj_grid *g, const int32_t shape[4])
+{
+    g_err[0] = 0;
+    hj_status s = check_grid(g);
+    if (s != HJ_OK) return s;
+    if (!shape) return set_err(HJ_ERR_INVALID_ARG, "shape is NULL");
+    for (int i = 0; i < 4; ++i)
+        if (shape[i] < 0 || shape[i] > 4096) return set_err(HJ_ERR_INVALID_ARG, "shape entries must be in [0, 4096]");
+    if (!g->tiled_ok) return set_err(HJ_ERR_UNSUPPORTED, "this grid has no tiled kernel");
+    if ((s = activate(g)) != HJ_OK) return s;
+    HJ_CUDA(cudaStreamSynchronize(g->stream));
+    int32_t old[4];
+    memcpy(old, g->tile_req, sizeof(old));
+    memcpy(g->tile_req, shape, sizeof(old));
+    char why[160];
+    if (!hj_tiled_setup(g, why, sizeof(why))) {
+        memcpy(g->tile_req, old, sizeof(old));
+        hj_tiled_setup(g, why, sizeof(why));
+        return set_err(HJ_ERR_UNSUPPORTED, "tile shape rejected: %s", why);
+    }
+    return HJ_OK;
+}
+
+hj_status hj_autotune(hj_grid *g, int32_t steps_per_trial, hj_tile_result *results, int32_t max_results,
+                      int32_t *nresults)
+{
+    g_err[0] = 0;
+    hj_status s = check_grid(g);
+    if (s != HJ_OK) return s;
+    if (steps_per_trial < 1) return set_err(HJ_ERR_INVALID_ARG, "steps_per_trial must be >= 1");
+    if (max_results < 0) return set_err(HJ_ERR_INVALID_ARG, "max_results must be >= 0");
+    if (!g->tiled_ok) return set_err(HJ_ERR_UNSUPPORTED, "this grid has no tiled kernel");
+    if (!g->has_value) return set_err(HJ_ERR_STATE, "no initial value (hj_set_initial_value)");
+    if ((s = activate(g)) != HJ_OK) return s;
+    if ((s = pull_state(g)) != HJ_OK) return s;
+    if (g->hstate->n != 0) return set_err(HJ_ERR_STATE, "autotune must run before the first step");
+    HjDevState saved = *g->hstate;
+    int32_t keep[4];
+    memcpy(keep, g->tile_req, sizeof(keep));
+
+    // candidate (ty, tv): one consumer thread per (row, theta quad), 8 to 24
+    // warps, ranked by the halo reads per row
+    struct Cand {
+        int ty, tv;
+        double halo;
+    } cands[64];
+    int nc = 0;
+    for (int ty = 1; ty <= 16; ++ty)
+        for (int tv = 1; tv <= 16; ++tv) {
+            if (ty > g->n[1] || tv > g->n[2]) continue;
+            int th = hj_tiled_threads(g, ty, tv);
+            if (th == 0 || th < 288) continue;
+            double halo = (double)(ty + 2) * (tv + 2) / (ty * tv);
+            if (nc < 64) cands[nc++] = {ty, tv, halo};
+            else {
+                int worst = 0;
+                for (int i = 1; i < nc; ++i)
+                    if (cands[i].halo > cands[worst].halo) worst = i;
+                if (halo < cands[worst].halo) cands[worst] = {ty, tv, halo};
+            }
+        }
+    for (int i = 0; i < nc; ++i)  // best halo ratio first
+        for (int j = i + 1; j < nc; ++j)
+            if (cands[j].halo < cands[i].halo) {
+                Cand t = cands[i];
+                cands[i] = cands[j];
+                cands[j] = t;
+            }
+    if (nc > 12) nc = 12;
+    if (nc == 0) {  // tiny grids: whatever the default shape is
+        cands[0] = {0, 0, 0.0};
+        nc = 1;
+    }
+
+    const int ncoef = g->n[2] * g->n[3];
+    auto run_steps = [&](int k) -> hj_status {
+        *g->hstate = saved;
+        HJ_CUDA(cudaMemcpyAsync(g->dstate, g->hstate, sizeof(HjDevState), cudaMemcpyHostToDevice, g->stream));
+        prologue_kernel<float><<<1, 256, 0, g->stream>>>(g->dstate, g->geom, (const HjCoef<float> *)g->coef, ncoef,
+                                                         1e300, 0.8);
+        HJ_CUDA(cudaGetLastError());
+        HJ_CUDA(cudaEventRecord(g->ev[1], g->stream));
+        for (int i = 0; i < k; ++i) {
+            hj_status r = launch_step(g, HJ_KERNEL_TILED);
+            if (r != HJ_OK) return r;
+        }
+        HJ_CUDA(cudaEventRecord(g->ev[2], g->stream));
+        HJ_CUDA(cudaEventSynchronize(g->ev[2]));
+        return HJ_OK;
+    };
+    double best = 1e300;
+    int32_t best_req[4] = {0, 0, 0, 0};
+    int32_t count = 0;
+    char why[160];
+    for (int c = 0; c < nc; ++c) {
+        int auto_xc = -1;
+        for (int xc_mode = 0; xc_mode < 2; ++xc_mode) {
+            g->tile_req[0] = cands[c].ty;
+            g->tile_req[1] = cands[c].tv;
+            g->tile_req[2] = xc_mode == 0 ? 0 : g->n[0];  // automatic chunks, or one chunk per column
+            g->tile_req[3] = 0;
+            if (!hj_tiled_setup(g, why, sizeof(why))) continue;
+            if (xc_mode == 0) auto_xc = g->tile_xc;
+            else if (g->tile_xc == auto_xc) continue;  // the automatic choice already was one chunk
+            if ((s = run_steps(2)) != HJ_OK) break;  // warm-up
+            if ((s = run_steps(steps_per_trial)) != HJ_OK) break;
+            pull_state(g);
+            if (g->hstate->status != HJ_OK) {
+                s = set_err((hj_status)g->hstate->status, "device reported %s during autotune",
+                            hj_status_string((hj_status)g->hstate->status));
+                break;
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, g->ev[1], g->ev[2]);
+            const double per = ms / steps_per_trial;
+            if (results && count < max_results) {
+                hj_tile_result &r = results[count];
+                r.shape[0] = g->tile_ty;
+                r.shape[1] = g->tile_tv;
+                r.shape[2] = g->tile_xc;
+                r.shape[3] = g->tile_stages;
+                r.threads = hj_tiled_threads(g, g->tile_ty, g->tile_tv);
+                r.ctas = g->tiled_ctas;
+                r.ms_per_step = per;
+            }
+            ++count;
+            if (per < best) {
+                best = per;
+                best_req[0] = g->tile_ty;
+                best_req[1] = g->tile_tv;
+                best_req[2] = g->tile_xc;
+                best_req[3] = g->tile_stages;
+            }
+        }
+        if (s != HJ_OK) break;
+    }
+    // keep the winner (or the previous shape if nothing ran), restore the state
+    if (best < 1e300)
+        memcpy(g->tile_req, best_req, sizeof(best_req));
+    else
+        memcpy(g->tile_req, keep, sizeof(keep));
+    hj_tiled_setup(g, why, sizeof(why));
+    *g->hstate = saved;
+    cudaMemcpyAsync(g->dstate, g->hstate, sizeof(HjDevState), cudaMemcpyHostToDevice, g->stream);
+    cudaStreamSynchronize(g->stream);
+    if (nresults) *nresults = count;
+    return s;
+}
+
 hj_status hj_get_info(const hj_grid *g, hj_grid_info *info)
 {
     g_err[0] = 0;
@@ -702,6 +851,13 @@ hj_status hj_get_info(const hj_grid *g, hj_grid_info *info)
     info->total_steps = g->hstate->n;
     info->t = g->hstate->t;
     info->device_bytes = g->device_bytes;
+    if (g->tiled_ok) {
+        info->tile[0] = g->tile_ty;
+        info->tile[1] = g->tile_tv;
+        info->tile[2] = g->tile_xc;
+        info->tile[3] = g->tile_stages;
+        info->tile_ctas = g->tiled_ctas;
+    }
     return HJ_OK;
 }
 

@@ -82,8 +82,9 @@ struct hj_grid {
     hj_kernel kernel_req;  // requested by hj_set_kernel
     bool tiled_ok;         // the tiled kernel supports this grid
     CUtensorMap tmap[3];   // V0, buffer A, buffer B (tiled kernel, FP32 only)
+    int32_t tile_req[4];   // requested (ty, tv, xc, stages); 0 = choose automatically
     int32_t tile_ty, tile_tv, tile_xc, tile_rg, tile_stages;
-    int32_t tiled_ctas;
+    int32_t tiled_ctas, tiled_per_sm;
 
     cudaEvent_t ev[4];
     size_t device_bytes;
@@ -94,6 +95,9 @@ cudaError_t hj_launch_step_generic(hj_grid *g);
 cudaError_t hj_launch_step_tiled(hj_grid *g);
 // Set up the tiled kernel for g (tensor maps, tile shape); false if unsupported.
 bool hj_tiled_setup(hj_grid *g, char *why, size_t why_len);
+// Consumer threads a tile of ty x tv rows needs (one per row and theta quad),
+// and whether that shape can run at all.
+int hj_tiled_threads(const hj_grid *g, int ty, int tv);
 
 // Pointer of the value buffer that holds V after n steps.
 inline void *hj_value_ptr(const hj_grid *g, long long n)

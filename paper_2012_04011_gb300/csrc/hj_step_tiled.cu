@@ -29,12 +29,17 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <type_traits>
+
 #include "hj_device.cuh"
 
 namespace {
 
-constexpr int MAXR = 4;                 // rows per consumer thread
 constexpr int MAX_STAGES = 8;
+constexpr int MAX_CONSUMERS = 768;      // consumer threads per CTA (+ one producer warp)
+// Two launch-bound variants: up to 512 consumers (120 registers a thread) and
+// up to 768 (80 registers); a shape uses the smaller one that holds it.
+constexpr int SMALL_CONSUMERS = 512;
 constexpr unsigned long long WAIT_NS = 4000000000ull;  // 4 s per wait: far beyond any healthy wait
 
 struct TiledParams {
@@ -144,13 +149,12 @@ __device__ __forceinline__ ItemGeom item_geom(const TiledParams &P, const HjGeom
     return it;
 }
 
-__global__ void __launch_bounds__(256) hj_step_tiled_kernel(const __grid_constant__ CUtensorMap map_v0,
-                                                             const __grid_constant__ CUtensorMap map_a,
-                                                             const __grid_constant__ CUtensorMap map_b,
-                                                             const float *__restrict__ v0, float *__restrict__ buf,
-                                                             const HjCoef<float> *__restrict__ coef,
-                                                             const float *__restrict__ tab, HjDevState *st,
-                                                             const HjGeom g, const TiledParams P, long long nint)
+template <bool PADDED, int MAXC>
+__global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
+    const __grid_constant__ CUtensorMap map_v0, const __grid_constant__ CUtensorMap map_a,
+    const __grid_constant__ CUtensorMap map_b, const float *__restrict__ v0, float *__restrict__ buf,
+    const HjCoef<float> *__restrict__ coef, const float *__restrict__ tab, HjDevState *st, const HjGeom g,
+    const TiledParams P, long long nint)
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     if (st->done) return;  // uniform across the grid
@@ -160,8 +164,7 @@ __global__ void __launch_bounds__(256) hj_step_tiled_kernel(const __grid_constan
     uint64_t *full = (uint64_t *)(smem_raw + (size_t)P.stages * P.stage_bytes);
     uint64_t *empty = full + MAX_STAGES;
     unsigned long long *scratch = (unsigned long long *)(empty + MAX_STAGES);
-    float *vtab = (float *)(scratch + 64);
-    volatile int *abort_flag = (volatile int *)(vtab + g.n3);
+    volatile int *abort_flag = (volatile int *)(scratch + 64);
 
     const long long n = st->n;
     const float dt = (float)st->dt;
@@ -181,11 +184,10 @@ __global__ void __launch_bounds__(256) hj_step_tiled_kernel(const __grid_constan
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
-    for (int k = tid; k < g.n3; k += blockDim.x) vtab[k] = tab[k];
     __syncthreads();
 
     const unsigned long long deadline = global_ns() + WAIT_NS;
-    unsigned long long am1 = 0ull, am2 = 0ull;
+    float am1 = 0.f, am2 = 0.f;  // this thread's max |xdot_1|, |xdot_2| (non-negative)
 
     if (tid >= P.nconsumer) {
         // ------------------------------------------------------------ producer
@@ -225,26 +227,35 @@ __global__ void __launch_bounds__(256) hj_step_tiled_kernel(const __grid_constan
         }
     } else {
         // ------------------------------------------------------------ consumers
+        // Thread t owns theta quad q = t % q4 of tile row r = t / q4 (row r is
+        // (y0 + r / tv, v0 + r % tv)) for the whole kernel.
         const int lane = tid & 31;
-        const bool active = tid < P.q4 * P.rg;
         const int q = tid % P.q4;
-        const int rgid = tid / P.q4;
+        const int r = tid / P.q4;
         const int N1 = g.n1, N2 = g.n2, N3 = g.n3, N4 = g.n4, P4 = g.p4;
-        const int rows = P.ty * P.tv;
         const int srow = P.tv + 2;  // smem rows per y row
-        const float k3 = (float)g.k3, k4 = (float)g.k4;
-        const long long s1 = (long long)N2 * N3 * P4, s2 = (long long)N3 * P4;
+        const int jy = r / P.tv, kv = r - (r / P.tv) * P.tv;
+        const bool inrow = r < P.ty * P.tv;
+        const int rsm = inrow ? ((jy + 1) * srow + (kv + 1)) * P4 + 4 * q : (srow + 1) * P4;
+        const float k3 = (float)g.k3, k4 = (float)g.k4, k34 = (float)(g.k3 + g.k4);
+        const uint32_t s1 = (uint32_t)N2 * N3 * P4;  // plane stride (the grid has < 2^31 values)
 
-        // this thread's theta states: cos/dx1 and sin/dx2 of its quad
-        float ch[4], sh[4];
+        // Upwind weights of the x and y terms for this quad: xdot_1/dx_1 =
+        // v cos(th)/dx_1 splits into a part that takes V(x+1) (cos >= 0) and
+        // one that takes V(x-1) (cos < 0); likewise y with sin.
+        float cp[4], cm[4], sp[4], sm[4], cs[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-            ch[e] = tab[N3 + 4 * q + e];
-            sh[e] = tab[N3 + P4 + 4 * q + e];
+            const float c = tab[N3 + 4 * q + e], s = tab[N3 + P4 + 4 * q + e];
+            cp[e] = fmaxf(c, 0.f);
+            cm[e] = fmaxf(-c, 0.f);
+            sp[e] = fmaxf(s, 0.f);
+            sm[e] = fmaxf(-s, 0.f);
+            cs[e] = fabsf(c) + fabsf(s);
         }
-        const int lm = (4 * q - 1 + N4) % N4;    // theta index left of the quad
-        const int lp = (4 * q + 4) % N4;         // right of the quad
-        const int lreal = min(4, N4 - 4 * q);    // real lanes in the quad (< 4 only in a padded last quad)
+        const int lm = (4 * q - 1 + N4) % N4;  // theta index left of the quad
+        const int lp = (4 * q + 4) % N4;       // right of the quad
+        const int lreal = min(4, N4 - 4 * q);  // real lanes (< 4 only in a padded last quad)
 
         uint32_t seq = 0;
         bool ok = true;
@@ -252,155 +263,121 @@ __global__ void __launch_bounds__(256) hj_step_tiled_kernel(const __grid_constan
             const ItemGeom it = item_geom(P, g, item);
             const uint32_t seq0 = seq;
             seq += (uint32_t)(it.pl1 - it.pl0 + 1);
+            const bool edge = it.y0 == 0 || it.y0 + P.ty >= N2 || it.v0 == 0 || it.v0 + P.tv >= N3;
+            const int y = it.y0 + jy, v = it.v0 + kv;
+            const bool rok = inrow && y < N2 && v < N3;
+            const uint32_t rbase = rok ? ((uint32_t)y * N3 + v) * P4 + 4 * q : 0u;
+            const float vk = rok ? tab[v] : 0.f;
+            // ghosts this row needs: 1 y-1, 2 y+1, 4 v-1, 8 v+1
+            const uint32_t gmask = (y == 0 ? 1u : 0u) | (y == N2 - 1 ? 2u : 0u) | (v == 0 ? 4u : 0u) |
+                                   (v == N3 - 1 ? 8u : 0u);
+            if (rok)
+                for (int e = 0; e < lreal; ++e) {
+                    // alpha partials over this thread's (v, theta) states
+                    const HjCoef<float> c = coef[v * N4 + 4 * q + e];
+                    am1 = fmaxf(am1, c.a1);
+                    am2 = fmaxf(am2, c.a2);
+                }
 
-            // rows of this thread
-            int rsm[MAXR];       // smem row index of the centre
-            int ry[MAXR], rv[MAXR];
-            bool rok[MAXR];
-#pragma unroll
-            for (int m = 0; m < MAXR; ++m) {
-                int r = rgid + P.rg * m;
-                int jy = r / P.tv, kv = r - jy * P.tv;
-                ry[m] = it.y0 + jy;
-                rv[m] = it.v0 + kv;
-                rok[m] = active && r < rows && ry[m] < N2 && rv[m] < N3;
-                // rows this thread does not own read a harmless in-tile row
-                rsm[m] = rok[m] ? (jy + 1) * srow + (kv + 1) : srow + 1;
-            }
-            // alpha partials over this thread's (v, theta) states
-#pragma unroll
-            for (int m = 0; m < MAXR; ++m)
-                if (rok[m])
-                    for (int e = 0; e < lreal; ++e) {
-                        const HjCoef<float> c = coef[rv[m] * N4 + 4 * q + e];
-                        unsigned long long b1 = hj_abits((double)c.a1), b2 = hj_abits((double)c.a2);
-                        am1 = am1 > b1 ? am1 : b1;
-                        am2 = am2 > b2 ? am2 : b2;
-                    }
+            // plane p of this item sits in ring slot (seq0 + p - pl0) % stages
+#define HJ_SEQ(p) (seq0 + (uint32_t)((p) - it.pl0))
+#define HJ_STAGE(p) (stages + (size_t)(HJ_SEQ(p) % P.stages) * (P.stage_bytes / 4))
+#define HJ_WAIT(p) mbar_wait_warp(&full[HJ_SEQ(p) % P.stages], (HJ_SEQ(p) / P.stages) & 1u, deadline)
+#define HJ_RELEASE(p)                                          \
+    do {                                                       \
+        __syncwarp();                                          \
+        if (lane == 0) mbar_arrive(&empty[HJ_SEQ(p) % P.stages]); \
+    } while (0)
 
-            auto stage_of = [&](int p) -> float * {
-                return stages + (size_t)((seq0 + (uint32_t)(p - it.pl0)) % P.stages) * (P.stage_bytes / 4);
-            };
-            auto wait_plane = [&](int p) -> bool {
-                uint32_t sq = seq0 + (uint32_t)(p - it.pl0);
-                return mbar_wait_warp(&full[sq % P.stages], (sq / P.stages) & 1u, deadline);
-            };
-            auto release_plane = [&](int p) {
-                uint32_t sq = seq0 + (uint32_t)(p - it.pl0);
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&empty[sq % P.stages]);
-            };
-
-            float4 prev[MAXR], cur[MAXR], nxt[MAXR], v0c[MAXR], v0n[MAXR];
+            float4 prev, cur, nxt, v0c, v0n = make_float4(0.f, 0.f, 0.f, 0.f);
             // item prologue: planes x0-1 (if any) and x0
-            if (!wait_plane(it.pl0)) ok = false;
-            if (ok && it.x0 > it.pl0 && !wait_plane(it.x0)) ok = false;
+            if (!HJ_WAIT(it.pl0)) ok = false;
+            if (ok && it.x0 > it.pl0 && !HJ_WAIT(it.x0)) ok = false;
             if (!ok) break;
-            {
-                const float *sc = stage_of(it.x0);
-                const float *sp = stage_of(it.pl0);
-#pragma unroll
-                for (int m = 0; m < MAXR; ++m) {
-                    cur[m] = *(const float4 *)(sc + rsm[m] * P4 + 4 * q);
-                    prev[m] = *(const float4 *)(sp + rsm[m] * P4 + 4 * q);  // == cur when x0 == 0 (ghost set below)
-                    const long long o = ((long long)it.x0 * N2 + ry[m]) * s2 + (long long)rv[m] * P4 + 4 * q;
-                    v0c[m] = rok[m] ? __ldcs((const float4 *)(v0 + o)) : make_float4(0.f, 0.f, 0.f, 0.f);
-                }
-            }
-            if (it.x0 > it.pl0) release_plane(it.pl0);
+            cur = *(const float4 *)(HJ_STAGE(it.x0) + rsm);
+            prev = *(const float4 *)(HJ_STAGE(it.pl0) + rsm);  // replaced by the ghost when x0 == 0
+            v0c = rok ? __ldcs((const float4 *)(v0 + (uint32_t)it.x0 * s1 + rbase)) : make_float4(0.f, 0.f, 0.f, 0.f);
+            if (it.x0 > it.pl0) HJ_RELEASE(it.pl0);
 
-            for (int x = it.x0; x < it.x1; ++x) {
-                if (__any_sync(0xffffffffu, *abort_flag != 0)) {
-                    ok = false;
-                    break;
-                }
-                const float *sx = stage_of(x);
-                // centre of plane x+1, or the extrapolated ghost past the end
-                if (x + 1 <= N1 - 1) {
-                    if (!wait_plane(x + 1)) {
+            {
+                for (int x = it.x0; x < it.x1; ++x) {
+                    if (__any_sync(0xffffffffu, *abort_flag != 0)) {
                         ok = false;
                         break;
                     }
-                    const float *sn = stage_of(x + 1);
-#pragma unroll
-                    for (int m = 0; m < MAXR; ++m) nxt[m] = *(const float4 *)(sn + rsm[m] * P4 + 4 * q);
-                } else {
-#pragma unroll
-                    for (int m = 0; m < MAXR; ++m) nxt[m] = f4ghost(cur[m], prev[m]);
-                }
-                if (x == 0) {
-#pragma unroll
-                    for (int m = 0; m < MAXR; ++m) prev[m] = f4ghost(cur[m], nxt[m]);
-                }
-                // V0 one plane ahead
-                if (x + 1 < it.x1) {
-#pragma unroll
-                    for (int m = 0; m < MAXR; ++m) {
-                        const long long o = ((long long)(x + 1) * N2 + ry[m]) * s2 + (long long)rv[m] * P4 + 4 * q;
-                        v0n[m] = rok[m] ? __ldcs((const float4 *)(v0 + o)) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    const float *sx = HJ_STAGE(x);
+                    // V0 one plane ahead
+                    if (rok && x + 1 < it.x1) v0n = __ldcs((const float4 *)(v0 + (uint32_t)(x + 1) * s1 + rbase));
+                    // centre of plane x+1, or the extrapolated ghost past the end
+                    if (x + 1 <= N1 - 1) {
+                        if (!HJ_WAIT(x + 1)) {
+                            ok = false;
+                            break;
+                        }
+                        nxt = *(const float4 *)(HJ_STAGE(x + 1) + rsm);
+                    } else {
+                        nxt = f4ghost(cur, prev);
                     }
-                }
+                    if (x == 0) prev = f4ghost(cur, nxt);
+                    if (rok) {
+                        const float *row = sx + rsm;
+                        float4 ym = *(const float4 *)(row - srow * P4);
+                        float4 yp = *(const float4 *)(row + srow * P4);
+                        float4 vm = *(const float4 *)(row - P4);
+                        float4 vp = *(const float4 *)(row + P4);
+                        if (edge && gmask) {
+                            // extrapolated points past the y / v ends (Sec. II-B)
+                            if (gmask & 1u) ym = f4ghost(cur, yp);
+                            if (gmask & 2u) yp = f4ghost(cur, ym);
+                            if (gmask & 4u) vm = f4ghost(cur, vp);
+                            if (gmask & 8u) vp = f4ghost(cur, vm);
+                        }
+                        const float *row0 = row - 4 * q;
+                        const float tl = row0[lm], tr = row0[lp];
+                        float t0 = 0.f;
+                        if (PADDED) t0 = row0[0];
+                        float4 out;
 #pragma unroll
-                for (int m = 0; m < MAXR; ++m) {
-                    if (!rok[m]) continue;
-                    const float *row = sx + rsm[m] * P4;
-                    const float4 c = cur[m];
-                    float4 ym = *(const float4 *)(row - srow * P4 + 4 * q);
-                    float4 yp = *(const float4 *)(row + srow * P4 + 4 * q);
-                    float4 vm = *(const float4 *)(row - P4 + 4 * q);
-                    float4 vp = *(const float4 *)(row + P4 + 4 * q);
-                    if (ry[m] == 0) ym = f4ghost(c, yp);
-                    if (ry[m] == N2 - 1) yp = f4ghost(c, ym);
-                    if (rv[m] == 0) vm = f4ghost(c, vp);
-                    if (rv[m] == N3 - 1) vp = f4ghost(c, vm);
-                    const float tl = row[lm], tr = row[lp], t0 = row[0];
-                    const float vk = vtab[rv[m]];
-                    float4 out;
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const float vc = f4get(c, e);
-                        const float tm = e == 0 ? tl : f4get(c, e - 1);
-                        float tp = e == 3 ? tr : f4get(c, e + 1);
-                        if (e == lreal - 1 && lreal < 4) tp = t0;  // wrap of a padded last quad
-                        const float C1 = vk * ch[e], C2 = vk * sh[e];
-                        const float u1 = C1 >= 0.f ? f4get(nxt[m], e) : f4get(prev[m], e);
-                        const float u2 = C2 >= 0.f ? f4get(yp, e) : f4get(ym, e);
-                        const float u3 = fmaxf(f4get(vp, e), f4get(vm, e));
-                        const float u4 = fmaxf(tp, tm);
-                        float r = fabsf(C1) * (u1 - vc);
-                        r = fmaf(fabsf(C2), u2 - vc, r);
-                        r = fmaf(k3, u3 - vc, r);
-                        r = fmaf(k4, u4 - vc, r);
-                        float vn = fminf(f4get(v0c[m], e), fmaf(dt, r, vc));
-                        f4set(out, e, e < lreal ? vn : 0.f);
+                        for (int e = 0; e < 4; ++e) {
+                            const float vc = f4get(cur, e);
+                            const float tm = e == 0 ? tl : f4get(cur, e - 1);
+                            float tp = e == 3 ? tr : f4get(cur, e + 1);
+                            if (PADDED && lreal < 4 && e == lreal - 1) tp = t0;  // wrap of a padded last quad
+                            // x and y: upwind differences folded into weights (no selects)
+                            float in = cp[e] * f4get(nxt, e);
+                            in = fmaf(cm[e], f4get(prev, e), in);
+                            in = fmaf(sp[e], f4get(yp, e), in);
+                            in = fmaf(sm[e], f4get(ym, e), in);
+                            in = fmaf(-cs[e], vc, in);
+                            // v and theta: the bang-bang control takes the larger neighbour
+                            float acc = fmaf(k3, fmaxf(f4get(vp, e), f4get(vm, e)), -k34 * vc);
+                            acc = fmaf(k4, fmaxf(tp, tm), acc);
+                            acc = fmaf(vk, in, acc);
+                            float vn = fminf(f4get(v0c, e), fmaf(dt, acc, vc));
+                            if (PADDED && e >= lreal) vn = 0.f;
+                            f4set(out, e, vn);
+                        }
+                        *(float4 *)(vout + (uint32_t)x * s1 + rbase) = out;
                     }
-                    const long long o = ((long long)x * N2 + ry[m]) * s2 + (long long)rv[m] * P4 + 4 * q;
-                    *(float4 *)(vout + o) = out;
-                }
-                release_plane(x);
-#pragma unroll
-                for (int m = 0; m < MAXR; ++m) {
-                    prev[m] = cur[m];
-                    cur[m] = nxt[m];
-                    v0c[m] = v0n[m];
+                    HJ_RELEASE(x);
+                    prev = cur;
+                    cur = nxt;
+                    v0c = v0n;
                 }
             }
             if (!ok) break;
-            if (it.x1 <= it.pl1) release_plane(it.x1);
+            if (it.x1 <= it.pl1) HJ_RELEASE(it.x1);
+#undef HJ_SEQ
+#undef HJ_STAGE
+#undef HJ_WAIT
+#undef HJ_RELEASE
         }
         if (!ok) {
             st->status = HJ_ERR_TIMEOUT;
             *abort_flag = 1;
         }
-        (void)s1;
     }
-    hj_step_epilogue(st, g, am1, am2, scratch);
-}
-
-size_t tiled_smem_bytes(const TiledParams &P, int n3)
-{
-    return (size_t)P.stages * P.stage_bytes + 2 * MAX_STAGES * sizeof(uint64_t) + 64 * sizeof(unsigned long long) +
-           (size_t)n3 * sizeof(float) + 16;
+    hj_step_epilogue(st, g, hj_abits((double)am1), hj_abits((double)am2), scratch);
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
@@ -423,7 +400,7 @@ EncodeTiledFn get_encode_fn()
     return fn;
 }
 
-TiledParams make_params(const hj_grid *g, int ty, int tv, int stages, int slots)
+TiledParams make_params(const hj_grid *g, int ty, int tv, int stages, int xc)
 {
     TiledParams P;
     memset(&P, 0, sizeof(P));
@@ -432,32 +409,61 @@ TiledParams make_params(const hj_grid *g, int ty, int tv, int stages, int slots)
     P.stages = stages;
     P.q4 = g->p4 / 4;
     int rows = ty * tv;
-    P.rg = (rows + MAXR - 1) / MAXR;
-    P.nconsumer = ((P.q4 * P.rg + 31) / 32) * 32;
+    P.rg = rows;
+    P.nconsumer = ((P.q4 * rows + 31) / 32) * 32;
     P.ncol_v = (g->n[2] + tv - 1) / tv;
     P.ncol = ((g->n[1] + ty - 1) / ty) * P.ncol_v;
     P.stage_floats = g->p4 * (tv + 2) * (ty + 2);
     P.stage_bytes = ((P.stage_floats * 4 + 127) / 128) * 128;
-    // enough work items to fill every CTA slot, but at least 4 planes per item
-    int nchunk = 1;
-    if (P.ncol * 4 < slots * 3) nchunk = (slots + P.ncol - 1) / P.ncol;
-    int xc = (g->n[0] + nchunk - 1) / nchunk;
-    if (xc < 4) xc = 4;
-    P.xc = xc;
-    P.nchunk = (g->n[0] + xc - 1) / xc;
+    P.xc = xc < 1 ? g->n[0] : (xc > g->n[0] ? g->n[0] : xc);
+    P.nchunk = (g->n[0] + P.xc - 1) / P.xc;
     P.nitems = P.ncol * P.nchunk;
     return P;
 }
 
+// Planes per work item: all CTAs sweep x concurrently, so the time of a step
+// is about (rounds of items) x (planes one item loads, halo planes included).
+// Pick the chunk length that minimises it.
+int best_chunk(const hj_grid *g, int ncol, int slots)
+{
+    const int n1 = g->n[0];
+    int best_xc = n1;
+    double best = 1e300;
+    for (int nchunk = 1; nchunk <= n1 / 4 || nchunk == 1; ++nchunk) {
+        const int xc = (n1 + nchunk - 1) / nchunk;
+        const int nch = (n1 + xc - 1) / xc;
+        const long long items = (long long)ncol * nch;
+        const long long rounds = (items + slots - 1) / slots;
+        const double cost = (double)rounds * (xc + (nch > 1 ? 2 : 0));
+        if (cost < best - 1e-9) {
+            best = cost;
+            best_xc = xc;
+        }
+    }
+    return best_xc;
+}
+
+const void *kernel_fn(bool padded, int nconsumer)
+{
+    const bool small = nconsumer <= SMALL_CONSUMERS;
+    if (padded) return small ? (const void *)hj_step_tiled_kernel<true, SMALL_CONSUMERS>
+                             : (const void *)hj_step_tiled_kernel<true, MAX_CONSUMERS>;
+    return small ? (const void *)hj_step_tiled_kernel<false, SMALL_CONSUMERS>
+                 : (const void *)hj_step_tiled_kernel<false, MAX_CONSUMERS>;
+}
+
+size_t tiled_smem_bytes(const TiledParams &P, int n3)
+{
+    (void)n3;
+    return (size_t)P.stages * P.stage_bytes + 2 * MAX_STAGES * sizeof(uint64_t) + 64 * sizeof(unsigned long long) + 16;
+}
+
 }  // namespace
 
-static TiledParams params_of(const hj_grid *g)
+int hj_tiled_threads(const hj_grid *g, int ty, int tv)
 {
-    TiledParams P = make_params(g, g->tile_ty, g->tile_tv, g->tile_stages, 0);
-    P.xc = g->tile_xc;
-    P.nchunk = (g->n[0] + P.xc - 1) / P.xc;
-    P.nitems = P.ncol * P.nchunk;
-    return P;
+    const int nc = ((g->p4 / 4) * ty * tv + 31) / 32 * 32;
+    return nc <= MAX_CONSUMERS ? nc + 32 : 0;
 }
 
 bool hj_tiled_setup(hj_grid *g, char *why, size_t why_len)
@@ -470,6 +476,7 @@ bool hj_tiled_setup(hj_grid *g, char *why, size_t why_len)
     if (g->periodic != 0x8u) return fail("tiled kernel needs theta (axis 4) periodic and x, y, v not");
     if (!g->has_dyn || g->dyn != HJ_DYN_CAR4D) return fail("tiled kernel needs the car dynamics");
     if (g->p4 > 256) return fail("theta rows longer than 256 points");
+    if (g->nint >= (1LL << 31)) return fail("grid too large for 32-bit offsets");
     EncodeTiledFn enc = get_encode_fn();
     if (!enc) return fail("cuTensorMapEncodeTiled unavailable");
 
@@ -477,38 +484,39 @@ bool hj_tiled_setup(hj_grid *g, char *why, size_t why_len)
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);
     cudaDeviceGetAttribute(&maxsmem, cudaDevAttrMaxSharedMemoryPerBlockOptin, g->device);
 
-    // tile shape: by default 8 x 4 rows of (y, v) (32 rows, MAXR per thread)
-    // and a four-stage ring; at most 224 consumer threads (+ the producer warp)
+    // tile shape: by default 8 x 4 rows of (y, v) and as many stages as fit;
+    // one consumer thread per (row, theta quad), at most MAX_CONSUMERS (+ the
+    // producer warp)
     const int q4 = g->p4 / 4;
-    const int max_rows = (224 / q4) * MAXR;
+    const int max_rows = MAX_CONSUMERS / q4;
     if (max_rows < 1) return fail("theta rows too long for one CTA");
-    int ty = g->tile_ty > 0 ? g->tile_ty : 8;
-    int tv = g->tile_tv > 0 ? g->tile_tv : 4;
+    int ty = g->tile_req[0] > 0 ? g->tile_req[0] : 8;
+    int tv = g->tile_req[1] > 0 ? g->tile_req[1] : 4;
     if (tv > g->n[2]) tv = g->n[2];
     if (ty > g->n[1]) ty = g->n[1];
     while (ty * tv > max_rows && ty > 1) --ty;
     while (ty * tv > max_rows && tv > 1) --tv;
-    int stages = g->tile_stages > 0 ? g->tile_stages : 4;
+    int stages = g->tile_req[3];
+    if (stages <= 0) {  // as many as fit in shared memory, up to MAX_STAGES
+        TiledParams P1 = make_params(g, ty, tv, 1, 0);
+        stages = (int)((maxsmem - 2048) / P1.stage_bytes);
+        if (stages > MAX_STAGES) stages = MAX_STAGES;
+    }
     if (stages < 3 || stages > MAX_STAGES) return fail("stage count out of range");
-    TiledParams P = make_params(g, ty, tv, stages, 1);
-    if (P.nconsumer + 32 > 256) return fail("tile needs more than 256 threads");
+    TiledParams P = make_params(g, ty, tv, stages, 0);
+    if (P.nconsumer > MAX_CONSUMERS) return fail("tile needs too many threads");
     size_t smem = tiled_smem_bytes(P, g->n[2]);
     if ((int)smem > maxsmem) return fail("tile does not fit in shared memory");
-    if (cudaFuncSetAttribute(hj_step_tiled_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess)
+    const void *fn = kernel_fn(g->p4 != g->n[3], P.nconsumer);
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return fail("cannot raise the shared-memory limit");
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hj_step_tiled_kernel, P.nconsumer + 32, smem) !=
-            cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, P.nconsumer + 32, smem) != cudaSuccess ||
         per_sm < 1)
         return fail("tile shape does not fit on an SM");
-    int slots = sms * per_sm;
-    P = make_params(g, ty, tv, stages, slots);
-    if (g->tile_xc > 0) {
-        P.xc = g->tile_xc;
-        P.nchunk = (g->n[0] + P.xc - 1) / P.xc;
-        P.nitems = P.ncol * P.nchunk;
-    }
+    const int slots = sms * per_sm;
+    const int xc = g->tile_req[2] > 0 ? g->tile_req[2] : best_chunk(g, P.ncol, slots);
+    P = make_params(g, ty, tv, stages, xc);
 
     // tensor maps over V0 and the two ping-pong buffers: dims (p4, n3, n2, n1)
     cuuint64_t dims[4] = {(cuuint64_t)g->p4, (cuuint64_t)g->n[2], (cuuint64_t)g->n[1], (cuuint64_t)g->n[0]};
@@ -532,15 +540,24 @@ bool hj_tiled_setup(hj_grid *g, char *why, size_t why_len)
     g->tile_rg = P.rg;
     g->tile_stages = stages;
     g->tiled_ctas = P.nitems < slots ? P.nitems : slots;
+    g->tiled_per_sm = per_sm;
     return true;
 }
 
 cudaError_t hj_launch_step_tiled(hj_grid *g)
 {
-    TiledParams P = params_of(g);
+    TiledParams P = make_params(g, g->tile_ty, g->tile_tv, g->tile_stages, g->tile_xc);
     size_t smem = tiled_smem_bytes(P, g->n[2]);
-    hj_step_tiled_kernel<<<g->tiled_ctas, P.nconsumer + 32, smem, g->stream>>>(
-        g->tmap[0], g->tmap[1], g->tmap[2], (const float *)g->v0, (float *)g->buf, (const HjCoef<float> *)g->coef,
-        g->tab_tiled, g->dstate, g->geom, P, g->nint);
+    const bool padded = g->p4 != g->n[3];
+    const bool small = P.nconsumer <= SMALL_CONSUMERS;
+#define HJ_LAUNCH(PAD, MC)                                                                                  \
+    hj_step_tiled_kernel<PAD, MC><<<g->tiled_ctas, P.nconsumer + 32, smem, g->stream>>>(                    \
+        g->tmap[0], g->tmap[1], g->tmap[2], (const float *)g->v0, (float *)g->buf, (const HjCoef<float> *)g->coef, \
+        g->tab_tiled, g->dstate, g->geom, P, g->nint)
+    if (padded && small) HJ_LAUNCH(true, SMALL_CONSUMERS);
+    else if (padded) HJ_LAUNCH(true, MAX_CONSUMERS);
+    else if (small) HJ_LAUNCH(false, SMALL_CONSUMERS);
+    else HJ_LAUNCH(false, MAX_CONSUMERS);
+#undef HJ_LAUNCH
     return cudaGetLastError();
 }

@@ -51,6 +51,19 @@ class hj_solve_stats(ctypes.Structure):
         return d
 
 
+class hj_tile_result(ctypes.Structure):
+    _fields_ = [
+        ("shape", ctypes.c_int32 * 4),
+        ("threads", ctypes.c_int32),
+        ("ctas", ctypes.c_int32),
+        ("ms_per_step", ctypes.c_double),
+    ]
+
+    def as_dict(self) -> dict:
+        return {"shape": list(self.shape), "threads": self.threads, "ctas": self.ctas,
+                "ms_per_step": self.ms_per_step}
+
+
 class hj_grid_info(ctypes.Structure):
     _fields_ = [
         ("n", ctypes.c_int32 * 4),
@@ -65,11 +78,13 @@ class hj_grid_info(ctypes.Structure):
         ("total_steps", ctypes.c_int64),
         ("t", ctypes.c_double),
         ("device_bytes", ctypes.c_size_t),
+        ("tile", ctypes.c_int32 * 4),
+        ("tile_ctas", ctypes.c_int32),
     ]
 
     def as_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_}
-        for k in ("n", "lo", "hi", "dx"):
+        for k in ("n", "lo", "hi", "dx", "tile"):
             d[k] = list(d[k])
         return d
 
@@ -89,6 +104,9 @@ _SIGS = {
     "hj_read_value": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.c_size_t]),
     "hj_read_value_device": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_size_t]),
     "hj_set_kernel": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "hj_set_tile_shape": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int32)]),
+    "hj_autotune": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.POINTER(hj_tile_result), ctypes.c_int32,
+                                   ctypes.POINTER(ctypes.c_int32)]),
     "hj_get_info": (ctypes.c_int, [_VP, ctypes.POINTER(hj_grid_info)]),
     "hj_destroy_grid": (None, [_VP]),
     "hj_status_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -212,6 +230,19 @@ def hj_set_kernel(g, kernel: int):
     _check(lib.hj_set_kernel(g, int(kernel)))
 
 
+def hj_set_tile_shape(g, shape):
+    arr = (ctypes.c_int32 * 4)(*[int(v) for v in shape])
+    _check(lib.hj_set_tile_shape(g, arr))
+
+
+def hj_autotune(g, steps_per_trial: int = 8, max_results: int = 32):
+    """Returns the list of tried shapes (hj_tile_result) in the order tried."""
+    res = (hj_tile_result * max_results)()
+    cnt = ctypes.c_int32(0)
+    _check(lib.hj_autotune(g, int(steps_per_trial), res, int(max_results), ctypes.byref(cnt)))
+    return [res[i] for i in range(min(cnt.value, max_results))]
+
+
 def hj_get_info(g) -> hj_grid_info:
     info = hj_grid_info()
     _check(lib.hj_get_info(g, ctypes.byref(info)))
@@ -260,6 +291,12 @@ class Grid:
 
     def set_kernel(self, kernel):
         hj_set_kernel(self.handle, kernel)
+
+    def set_tile_shape(self, shape):
+        hj_set_tile_shape(self.handle, shape)
+
+    def autotune(self, steps_per_trial=8):
+        return hj_autotune(self.handle, steps_per_trial)
 
     def info(self) -> hj_grid_info:
         return hj_get_info(self.handle)

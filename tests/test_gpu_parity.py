@@ -306,3 +306,52 @@ def test_full_size_sampled_step_parity(hj, prec):
             assert st.t_final == w.T
             V = g.read_value()
             assert np.all(V <= V0d) and np.all(np.isfinite(V))
+
+
+# ---------------------------------------------------------------- tile shapes and the autotuner
+
+@pytest.mark.parametrize("name", ["car4d_31x31x11x16", "car4d_60x60x20x36"])
+def test_every_tile_shape_gives_identical_bits(hj, name):
+    """The per-cell arithmetic does not depend on the tiling, so every tile
+    shape (ragged tiles, x chunks with halo planes, ring depth) must produce
+    exactly the same values."""
+    w = scenes.workload(name)
+    V0 = scenes.initial_value(w.grid, w.scene)
+    ref = None
+    shapes = [(0, 0, 0, 0), (8, 4, 0, 4), (3, 5, 7, 3), (1, 7, 5, 5), (5, 3, 0, 8), (2, 2, 4, 0)]
+    for shape in shapes:
+        with hj.Grid.for_workload(w, hj.HJ_FP32) as g:
+            try:
+                g.set_tile_shape(shape)
+            except hj.HjError as e:
+                assert e.status == hj.HJ_ERR_UNSUPPORTED
+                continue
+            g.set_initial_value(V0)
+            g.solve_brt(w.T, w.cfl)
+            V = g.read_value()
+        if ref is None:
+            ref = V
+        else:
+            assert np.array_equal(V, ref), shape
+
+
+def test_autotune_keeps_results_and_state(hj):
+    w = scenes.workload("car4d_60x60x20x36")
+    V0 = scenes.initial_value(w.grid, w.scene)
+    with hj.Grid.for_workload(w, hj.HJ_FP32) as g:
+        g.set_initial_value(V0)
+        V_ref_st = g.solve_brt(w.T, w.cfl)
+        V_ref = g.read_value()
+        g.set_initial_value(V0)
+        tried = g.autotune(4)
+        assert len(tried) >= 1 and all(t.ms_per_step > 0 for t in tried)
+        info = g.info()
+        best = min(tried, key=lambda t: t.ms_per_step)
+        assert list(info.tile) == list(best.shape)
+        assert info.total_steps == 0 and info.t == 0.0
+        st = g.solve_brt(w.T, w.cfl)
+        assert st.steps == V_ref_st.steps
+        assert np.array_equal(g.read_value(), V_ref)
+        with pytest.raises(hj.HjError) as e:
+            g.autotune(2)  # after steps: refused
+        assert e.value.status == hj.HJ_ERR_STATE
