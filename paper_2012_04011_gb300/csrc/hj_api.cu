@@ -719,35 +719,37 @@ hj_status hj_autotune(hj_grid *g, int32_t steps_per_trial, hj_tile_result *resul
     int32_t keep[4];
     memcpy(keep, g->tile_req, sizeof(keep));
 
-    // candidate (ty, tv): one consumer thread per (row, theta quad), 8 to 24
-    // warps, ranked by the halo reads per row
+    // candidate (ty, tv): one consumer thread per (row, theta quad), at least
+    // 8 warps; the 4 shapes with the fewest halo reads per row from each
+    // launch-bound class (<= 384, 512, 640, 768 consumer threads)
     struct Cand {
         int ty, tv;
         double halo;
-    } cands[64];
+    } cands[16];
     int nc = 0;
-    for (int ty = 1; ty <= 16; ++ty)
-        for (int tv = 1; tv <= 16; ++tv) {
-            if (ty > g->n[1] || tv > g->n[2]) continue;
-            int th = hj_tiled_threads(g, ty, tv);
-            if (th == 0 || th < 288) continue;
-            double halo = (double)(ty + 2) * (tv + 2) / (ty * tv);
-            if (nc < 64) cands[nc++] = {ty, tv, halo};
-            else {
-                int worst = 0;
-                for (int i = 1; i < nc; ++i)
-                    if (cands[i].halo > cands[worst].halo) worst = i;
-                if (halo < cands[worst].halo) cands[worst] = {ty, tv, halo};
+    const int class_hi[4] = {384, 512, 640, 768};
+    for (int cls = 0; cls < 4; ++cls) {
+        Cand top[4];
+        int nt = 0;
+        for (int ty = 1; ty <= 16; ++ty)
+            for (int tv = 1; tv <= 16; ++tv) {
+                if (ty > g->n[1] || tv > g->n[2]) continue;
+                const int th = hj_tiled_threads(g, ty, tv);
+                if (th == 0) continue;
+                const int cons = th - 32;
+                if (cons < 256 || cons > class_hi[cls] || (cls > 0 && cons <= class_hi[cls - 1])) continue;
+                const Cand c = {ty, tv, (double)(ty + 2) * (tv + 2) / (ty * tv)};
+                if (nt < 4) {
+                    top[nt++] = c;
+                } else {
+                    int worst = 0;
+                    for (int i = 1; i < nt; ++i)
+                        if (top[i].halo > top[worst].halo) worst = i;
+                    if (c.halo < top[worst].halo) top[worst] = c;
+                }
             }
-        }
-    for (int i = 0; i < nc; ++i)  // best halo ratio first
-        for (int j = i + 1; j < nc; ++j)
-            if (cands[j].halo < cands[i].halo) {
-                Cand t = cands[i];
-                cands[i] = cands[j];
-                cands[j] = t;
-            }
-    if (nc > 12) nc = 12;
+        for (int i = 0; i < nt; ++i) cands[nc++] = top[i];
+    }
     if (nc == 0) {  // tiny grids: whatever the default shape is
         cands[0] = {0, 0, 0.0};
         nc = 1;

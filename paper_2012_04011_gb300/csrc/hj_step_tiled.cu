@@ -37,9 +37,9 @@ namespace {
 
 constexpr int MAX_STAGES = 8;
 constexpr int MAX_CONSUMERS = 768;      // consumer threads per CTA (+ one producer warp)
-// Two launch-bound variants: up to 512 consumers (120 registers a thread) and
-// up to 768 (80 registers); a shape uses the smaller one that holds it.
-constexpr int SMALL_CONSUMERS = 512;
+// Launch-bound variants: up to 384, 512, 640 or 768 consumer threads (152,
+// 120, 96 or 80 registers a thread); a shape uses the smallest that holds it.
+constexpr int VARIANTS[4] = {384, 512, 640, 768};
 constexpr unsigned long long WAIT_NS = 4000000000ull;  // 4 s per wait: far beyond any healthy wait
 
 struct TiledParams {
@@ -53,6 +53,7 @@ struct TiledParams {
     int nchunk, nitems;   // x chunks per column; work items = ncol * nchunk
     int stage_floats;     // p4 * (tv + 2) * (ty + 2)
     int stage_bytes;      // stage_floats * 4 rounded up to 128
+    float k3, k4, mk34;   // |xdot_3|/dx_3, |xdot_4|/dx_4, -(k3 + k4): constant-bank operands
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -97,12 +98,12 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, unsign
 }
 // Warp-uniform version for consumer warps: every lane observes the phase,
 // and the timeout decision is the same for the whole warp.
-__device__ __forceinline__ bool mbar_wait_warp(uint64_t *bar, uint32_t parity, unsigned long long deadline)
+__device__ __forceinline__ bool mbar_wait_warp(uint64_t *bar, uint32_t parity, const unsigned long long *deadline)
 {
     while (true) {
         bool done = mbar_try_wait(bar, parity);
         if (__all_sync(0xffffffffu, done)) return true;
-        bool late = global_ns() > deadline;
+        bool late = global_ns() > *deadline;
         if (__any_sync(0xffffffffu, late)) return false;
     }
 }
@@ -165,6 +166,7 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
     uint64_t *empty = full + MAX_STAGES;
     unsigned long long *scratch = (unsigned long long *)(empty + MAX_STAGES);
     volatile int *abort_flag = (volatile int *)(scratch + 64);
+    unsigned long long *deadline_p = (unsigned long long *)(scratch + 65);
 
     const long long n = st->n;
     const float dt = (float)st->dt;
@@ -181,27 +183,31 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
             mbar_init(&empty[s], nconsumer_warps);
         }
         *abort_flag = 0;
+        *deadline_p = global_ns() + WAIT_NS;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     __syncthreads();
 
-    const unsigned long long deadline = global_ns() + WAIT_NS;
+    const unsigned long long deadline = *deadline_p;
     float am1 = 0.f, am2 = 0.f;  // this thread's max |xdot_1|, |xdot_2| (non-negative)
 
     if (tid >= P.nconsumer) {
         // ------------------------------------------------------------ producer
         if (tid == P.nconsumer) {
-            uint32_t seq = 0;
-            int last_seq[MAX_STAGES];
-            for (int s = 0; s < MAX_STAGES; ++s) last_seq[s] = -1;
+            // ring cursor: slot of the next load and the parity of its use
+            int slot = 0;
+            uint32_t phase = 0;
+            uint32_t issued = 0;      // loads issued so far
+            uint32_t used_mask = 0;   // slots that received a load
+            uint32_t last_phase = 0;  // bit s: parity of the last load into slot s
+            const uint32_t tx = (uint32_t)(P.stage_floats * 4);
             bool ok = true;
             for (int item = blockIdx.x; item < P.nitems && ok; item += gridDim.x) {
                 ItemGeom it = item_geom(P, g, item);
-                for (int p = it.pl0; p <= it.pl1; ++p, ++seq) {
-                    int s = seq % P.stages;
-                    uint32_t ph = (seq / P.stages) & 1u;
-                    if (seq >= (uint32_t)P.stages && !mbar_wait(&empty[s], ph ^ 1u, deadline)) {
+                for (int p = it.pl0; p <= it.pl1; ++p) {
+                    // the slot's previous contents must have been released
+                    if (issued >= (uint32_t)P.stages && !mbar_wait(&empty[slot], phase ^ 1u, deadline)) {
                         ok = false;
                         break;
                     }
@@ -209,10 +215,16 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
                         ok = false;
                         break;
                     }
-                    mbar_arrive_expect_tx(&full[s], (uint32_t)(P.stage_floats * 4));
-                    tma_load_4d(stages + (size_t)s * (P.stage_bytes / 4), map_in, &full[s], 0, it.v0 - 1,
+                    mbar_arrive_expect_tx(&full[slot], tx);
+                    tma_load_4d(stages + (size_t)slot * (P.stage_bytes / 4), map_in, &full[slot], 0, it.v0 - 1,
                                 it.y0 - 1, p);
-                    last_seq[s] = (int)seq;
+                    used_mask |= 1u << slot;
+                    last_phase = (last_phase & ~(1u << slot)) | (phase << slot);
+                    ++issued;
+                    if (++slot == P.stages) {
+                        slot = 0;
+                        phase ^= 1u;
+                    }
                 }
             }
             if (!ok) {
@@ -222,7 +234,7 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
             // drain: every copy this CTA issued must land before the CTA exits
             const unsigned long long drain_deadline = global_ns() + WAIT_NS;
             for (int s = 0; s < P.stages; ++s)
-                if (last_seq[s] >= 0 && !mbar_wait(&full[s], ((uint32_t)last_seq[s] / P.stages) & 1u, drain_deadline))
+                if (((used_mask >> s) & 1u) && !mbar_wait(&full[s], (last_phase >> s) & 1u, drain_deadline))
                     st->status = HJ_ERR_TIMEOUT;
         }
     } else {
@@ -237,7 +249,6 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
         const int jy = r / P.tv, kv = r - (r / P.tv) * P.tv;
         const bool inrow = r < P.ty * P.tv;
         const int rsm = inrow ? ((jy + 1) * srow + (kv + 1)) * P4 + 4 * q : (srow + 1) * P4;
-        const float k3 = (float)g.k3, k4 = (float)g.k4, k34 = (float)(g.k3 + g.k4);
         const uint32_t s1 = (uint32_t)N2 * N3 * P4;  // plane stride (the grid has < 2^31 values)
 
         // Upwind weights of the x and y terms for this quad: xdot_1/dx_1 =
@@ -257,12 +268,17 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
         const int lp = (4 * q + 4) % N4;       // right of the quad
         const int lreal = min(4, N4 - 4 * q);  // real lanes (< 4 only in a padded last quad)
 
-        uint32_t seq = 0;
+        // Ring cursors.  Planes are waited for and released in load order, so
+        // one cursor walks the slots to wait on (with the phase parity) and
+        // one walks the slots to release; plane x is always the oldest plane
+        // not yet released.
+        int wslot = 0, rslot = 0;
+        uint32_t wphase = 0;
+        const int nst = P.stages;
+        const int sfl = P.stage_bytes / 4;
         bool ok = true;
         for (int item = blockIdx.x; item < P.nitems && ok; item += gridDim.x) {
             const ItemGeom it = item_geom(P, g, item);
-            const uint32_t seq0 = seq;
-            seq += (uint32_t)(it.pl1 - it.pl0 + 1);
             const bool edge = it.y0 == 0 || it.y0 + P.ty >= N2 || it.v0 == 0 || it.v0 + P.tv >= N3;
             const int y = it.y0 + jy, v = it.v0 + kv;
             const bool rok = inrow && y < N2 && v < N3;
@@ -271,110 +287,133 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
             // ghosts this row needs: 1 y-1, 2 y+1, 4 v-1, 8 v+1
             const uint32_t gmask = (y == 0 ? 1u : 0u) | (y == N2 - 1 ? 2u : 0u) | (v == 0 ? 4u : 0u) |
                                    (v == N3 - 1 ? 8u : 0u);
-            if (rok)
-                for (int e = 0; e < lreal; ++e) {
-                    // alpha partials over this thread's (v, theta) states
-                    const HjCoef<float> c = coef[v * N4 + 4 * q + e];
-                    am1 = fmaxf(am1, c.a1);
-                    am2 = fmaxf(am2, c.a2);
-                }
 
-            // plane p of this item sits in ring slot (seq0 + p - pl0) % stages
-#define HJ_SEQ(p) (seq0 + (uint32_t)((p) - it.pl0))
-#define HJ_STAGE(p) (stages + (size_t)(HJ_SEQ(p) % P.stages) * (P.stage_bytes / 4))
-#define HJ_WAIT(p) mbar_wait_warp(&full[HJ_SEQ(p) % P.stages], (HJ_SEQ(p) / P.stages) & 1u, deadline)
-#define HJ_RELEASE(p)                                          \
-    do {                                                       \
-        __syncwarp();                                          \
-        if (lane == 0) mbar_arrive(&empty[HJ_SEQ(p) % P.stages]); \
+            // wait for the next plane in load order; returns its slot or -1
+#define HJ_WAIT_NEXT(slot_out)                                         \
+    do {                                                               \
+        if (!mbar_wait_warp(&full[wslot], wphase, deadline_p)) {       \
+            slot_out = -1;                                             \
+        } else {                                                       \
+            slot_out = wslot;                                          \
+            if (++wslot == nst) {                                      \
+                wslot = 0;                                             \
+                wphase ^= 1u;                                          \
+            }                                                          \
+        }                                                              \
+    } while (0)
+            // release the oldest plane still held
+#define HJ_RELEASE_OLDEST()                                            \
+    do {                                                               \
+        __syncwarp();                                                  \
+        if (lane == 0) mbar_arrive(&empty[rslot]);                     \
+        if (++rslot == nst) rslot = 0;                                 \
     } while (0)
 
-            float4 prev, cur, nxt, v0c, v0n = make_float4(0.f, 0.f, 0.f, 0.f);
-            // item prologue: planes x0-1 (if any) and x0
-            if (!HJ_WAIT(it.pl0)) ok = false;
-            if (ok && it.x0 > it.pl0 && !HJ_WAIT(it.x0)) ok = false;
-            if (!ok) break;
-            cur = *(const float4 *)(HJ_STAGE(it.x0) + rsm);
-            prev = *(const float4 *)(HJ_STAGE(it.pl0) + rsm);  // replaced by the ghost when x0 == 0
-            v0c = rok ? __ldcs((const float4 *)(v0 + (uint32_t)it.x0 * s1 + rbase)) : make_float4(0.f, 0.f, 0.f, 0.f);
-            if (it.x0 > it.pl0) HJ_RELEASE(it.pl0);
+            // Planes held in the ring while plane x is updated: x-1 (if
+            // loaded), x and x+1; plane x-1 is released after the update.
+            float4 cur, nxt;
+            int s_first, s_x;
+            HJ_WAIT_NEXT(s_first);
+            s_x = s_first;
+            if (s_first >= 0 && it.x0 > it.pl0) HJ_WAIT_NEXT(s_x);
+            if (s_first < 0 || s_x < 0) {
+                ok = false;
+                break;
+            }
+            cur = *(const float4 *)(stages + (size_t)s_x * sfl + rsm);
+            int s_prev = it.x0 > it.pl0 ? s_first : -1;  // slot of plane x-1, -1 at x = 0
 
-            {
-                for (int x = it.x0; x < it.x1; ++x) {
-                    if (__any_sync(0xffffffffu, *abort_flag != 0)) {
+            for (int x = it.x0; x < it.x1; ++x) {
+                if (__any_sync(0xffffffffu, *abort_flag != 0)) {
+                    ok = false;
+                    break;
+                }
+                // V0 of this plane (used last, so its latency overlaps the rest)
+                const float4 v0c = rok ? __ldcs((const float4 *)(v0 + (uint32_t)x * s1 + rbase))
+                                       : make_float4(0.f, 0.f, 0.f, 0.f);
+                const float *sx = stages + (size_t)s_x * sfl;
+                // centre of plane x+1, or the extrapolated ghost past the end
+                int s_n = -1;
+                float4 prev;
+                if (x + 1 <= N1 - 1) {
+                    HJ_WAIT_NEXT(s_n);
+                    if (s_n < 0) {
                         ok = false;
                         break;
                     }
-                    const float *sx = HJ_STAGE(x);
-                    // V0 one plane ahead
-                    if (rok && x + 1 < it.x1) v0n = __ldcs((const float4 *)(v0 + (uint32_t)(x + 1) * s1 + rbase));
-                    // centre of plane x+1, or the extrapolated ghost past the end
-                    if (x + 1 <= N1 - 1) {
-                        if (!HJ_WAIT(x + 1)) {
-                            ok = false;
-                            break;
-                        }
-                        nxt = *(const float4 *)(HJ_STAGE(x + 1) + rsm);
-                    } else {
-                        nxt = f4ghost(cur, prev);
-                    }
-                    if (x == 0) prev = f4ghost(cur, nxt);
-                    if (rok) {
-                        const float *row = sx + rsm;
-                        float4 ym = *(const float4 *)(row - srow * P4);
-                        float4 yp = *(const float4 *)(row + srow * P4);
-                        float4 vm = *(const float4 *)(row - P4);
-                        float4 vp = *(const float4 *)(row + P4);
-                        if (edge && gmask) {
-                            // extrapolated points past the y / v ends (Sec. II-B)
-                            if (gmask & 1u) ym = f4ghost(cur, yp);
-                            if (gmask & 2u) yp = f4ghost(cur, ym);
-                            if (gmask & 4u) vm = f4ghost(cur, vp);
-                            if (gmask & 8u) vp = f4ghost(cur, vm);
-                        }
-                        const float *row0 = row - 4 * q;
-                        const float tl = row0[lm], tr = row0[lp];
-                        float t0 = 0.f;
-                        if (PADDED) t0 = row0[0];
-                        float4 out;
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            const float vc = f4get(cur, e);
-                            const float tm = e == 0 ? tl : f4get(cur, e - 1);
-                            float tp = e == 3 ? tr : f4get(cur, e + 1);
-                            if (PADDED && lreal < 4 && e == lreal - 1) tp = t0;  // wrap of a padded last quad
-                            // x and y: upwind differences folded into weights (no selects)
-                            float in = cp[e] * f4get(nxt, e);
-                            in = fmaf(cm[e], f4get(prev, e), in);
-                            in = fmaf(sp[e], f4get(yp, e), in);
-                            in = fmaf(sm[e], f4get(ym, e), in);
-                            in = fmaf(-cs[e], vc, in);
-                            // v and theta: the bang-bang control takes the larger neighbour
-                            float acc = fmaf(k3, fmaxf(f4get(vp, e), f4get(vm, e)), -k34 * vc);
-                            acc = fmaf(k4, fmaxf(tp, tm), acc);
-                            acc = fmaf(vk, in, acc);
-                            float vn = fminf(f4get(v0c, e), fmaf(dt, acc, vc));
-                            if (PADDED && e >= lreal) vn = 0.f;
-                            f4set(out, e, vn);
-                        }
-                        *(float4 *)(vout + (uint32_t)x * s1 + rbase) = out;
-                    }
-                    HJ_RELEASE(x);
-                    prev = cur;
-                    cur = nxt;
-                    v0c = v0n;
+                    nxt = *(const float4 *)(stages + (size_t)s_n * sfl + rsm);
+                    prev = s_prev >= 0 ? *(const float4 *)(stages + (size_t)s_prev * sfl + rsm) : f4ghost(cur, nxt);
+                } else {
+                    prev = s_prev >= 0 ? *(const float4 *)(stages + (size_t)s_prev * sfl + rsm) : cur;
+                    nxt = f4ghost(cur, prev);
                 }
+                if (rok) {
+                    const float *row = sx + rsm;
+                    float4 ym = *(const float4 *)(row - srow * P4);
+                    float4 yp = *(const float4 *)(row + srow * P4);
+                    float4 vm = *(const float4 *)(row - P4);
+                    float4 vp = *(const float4 *)(row + P4);
+                    if (edge && gmask) {
+                        // extrapolated points past the y / v ends (Sec. II-B)
+                        if (gmask & 1u) ym = f4ghost(cur, yp);
+                        if (gmask & 2u) yp = f4ghost(cur, ym);
+                        if (gmask & 4u) vm = f4ghost(cur, vp);
+                        if (gmask & 8u) vp = f4ghost(cur, vm);
+                    }
+                    const float *row0 = row - 4 * q;
+                    const float tl = row0[lm], tr = row0[lp];
+                    float t0 = 0.f;
+                    if (PADDED) t0 = row0[0];
+                    float4 out;
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const float vc = f4get(cur, e);
+                        const float tm = e == 0 ? tl : f4get(cur, e - 1);
+                        float tp = e == 3 ? tr : f4get(cur, e + 1);
+                        if (PADDED && lreal < 4 && e == lreal - 1) tp = t0;  // wrap of a padded last quad
+                        // x and y: upwind differences folded into weights (no selects)
+                        float in = cp[e] * f4get(nxt, e);
+                        in = fmaf(cm[e], f4get(prev, e), in);
+                        in = fmaf(sp[e], f4get(yp, e), in);
+                        in = fmaf(sm[e], f4get(ym, e), in);
+                        in = fmaf(-cs[e], vc, in);
+                        // v and theta: the bang-bang control takes the larger neighbour
+                        float acc = fmaf(P.k3, fmaxf(f4get(vp, e), f4get(vm, e)), P.mk34 * vc);
+                        acc = fmaf(P.k4, fmaxf(tp, tm), acc);
+                        acc = fmaf(vk, in, acc);
+                        float vn = fminf(f4get(v0c, e), fmaf(dt, acc, vc));
+                        if (PADDED && e >= lreal) vn = 0.f;
+                        f4set(out, e, vn);
+                    }
+                    *(float4 *)(vout + (uint32_t)x * s1 + rbase) = out;
+                }
+                if (s_prev >= 0) HJ_RELEASE_OLDEST();  // plane x-1
+                s_prev = s_x;
+                s_x = s_n;
+                cur = nxt;
             }
             if (!ok) break;
-            if (it.x1 <= it.pl1) HJ_RELEASE(it.x1);
-#undef HJ_SEQ
-#undef HJ_STAGE
-#undef HJ_WAIT
-#undef HJ_RELEASE
+            // still held: plane x1-1 and, if loaded, the halo plane x1
+            HJ_RELEASE_OLDEST();
+            if (it.x1 <= it.pl1) HJ_RELEASE_OLDEST();
+#undef HJ_WAIT_NEXT
+#undef HJ_RELEASE_OLDEST
         }
         if (!ok) {
             st->status = HJ_ERR_TIMEOUT;
             *abort_flag = 1;
+        }
+        // alpha^max partials over the (v, theta) states of the cells this
+        // thread updated (the car's xdot_1, xdot_2 depend only on v, theta)
+        for (int item = blockIdx.x; item < P.nitems; item += gridDim.x) {
+            const ItemGeom it = item_geom(P, g, item);
+            const int y = it.y0 + jy, v = it.v0 + kv;
+            if (inrow && y < N2 && v < N3)
+                for (int e = 0; e < lreal; ++e) {
+                    const HjCoef<float> c = coef[v * N4 + 4 * q + e];
+                    am1 = fmaxf(am1, c.a1);
+                    am2 = fmaxf(am2, c.a2);
+                }
         }
     }
     hj_step_epilogue(st, g, hj_abits((double)am1), hj_abits((double)am2), scratch);
@@ -418,6 +457,9 @@ TiledParams make_params(const hj_grid *g, int ty, int tv, int stages, int xc)
     P.xc = xc < 1 ? g->n[0] : (xc > g->n[0] ? g->n[0] : xc);
     P.nchunk = (g->n[0] + P.xc - 1) / P.xc;
     P.nitems = P.ncol * P.nchunk;
+    P.k3 = (float)g->geom.k3;
+    P.k4 = (float)g->geom.k4;
+    P.mk34 = (float)(-(g->geom.k3 + g->geom.k4));
     return P;
 }
 
@@ -443,13 +485,18 @@ int best_chunk(const hj_grid *g, int ncol, int slots)
     return best_xc;
 }
 
+template <bool PADDED>
+const void *kernel_fn_p(int nconsumer)
+{
+    if (nconsumer <= VARIANTS[0]) return (const void *)hj_step_tiled_kernel<PADDED, VARIANTS[0]>;
+    if (nconsumer <= VARIANTS[1]) return (const void *)hj_step_tiled_kernel<PADDED, VARIANTS[1]>;
+    if (nconsumer <= VARIANTS[2]) return (const void *)hj_step_tiled_kernel<PADDED, VARIANTS[2]>;
+    return (const void *)hj_step_tiled_kernel<PADDED, VARIANTS[3]>;
+}
+
 const void *kernel_fn(bool padded, int nconsumer)
 {
-    const bool small = nconsumer <= SMALL_CONSUMERS;
-    if (padded) return small ? (const void *)hj_step_tiled_kernel<true, SMALL_CONSUMERS>
-                             : (const void *)hj_step_tiled_kernel<true, MAX_CONSUMERS>;
-    return small ? (const void *)hj_step_tiled_kernel<false, SMALL_CONSUMERS>
-                 : (const void *)hj_step_tiled_kernel<false, MAX_CONSUMERS>;
+    return padded ? kernel_fn_p<true>(nconsumer) : kernel_fn_p<false>(nconsumer);
 }
 
 size_t tiled_smem_bytes(const TiledParams &P, int n3)
@@ -502,7 +549,7 @@ bool hj_tiled_setup(hj_grid *g, char *why, size_t why_len)
         stages = (int)((maxsmem - 2048) / P1.stage_bytes);
         if (stages > MAX_STAGES) stages = MAX_STAGES;
     }
-    if (stages < 3 || stages > MAX_STAGES) return fail("stage count out of range");
+    if (stages < 4 || stages > MAX_STAGES) return fail("stage count out of range");
     TiledParams P = make_params(g, ty, tv, stages, 0);
     if (P.nconsumer > MAX_CONSUMERS) return fail("tile needs too many threads");
     size_t smem = tiled_smem_bytes(P, g->n[2]);
@@ -549,15 +596,14 @@ cudaError_t hj_launch_step_tiled(hj_grid *g)
     TiledParams P = make_params(g, g->tile_ty, g->tile_tv, g->tile_stages, g->tile_xc);
     size_t smem = tiled_smem_bytes(P, g->n[2]);
     const bool padded = g->p4 != g->n[3];
-    const bool small = P.nconsumer <= SMALL_CONSUMERS;
-#define HJ_LAUNCH(PAD, MC)                                                                                  \
-    hj_step_tiled_kernel<PAD, MC><<<g->tiled_ctas, P.nconsumer + 32, smem, g->stream>>>(                    \
-        g->tmap[0], g->tmap[1], g->tmap[2], (const float *)g->v0, (float *)g->buf, (const HjCoef<float> *)g->coef, \
-        g->tab_tiled, g->dstate, g->geom, P, g->nint)
-    if (padded && small) HJ_LAUNCH(true, SMALL_CONSUMERS);
-    else if (padded) HJ_LAUNCH(true, MAX_CONSUMERS);
-    else if (small) HJ_LAUNCH(false, SMALL_CONSUMERS);
-    else HJ_LAUNCH(false, MAX_CONSUMERS);
-#undef HJ_LAUNCH
+    // the variant's launch bound is a template argument; pick it through the
+    // same table as the set-up
+    typedef void (*KernelFn)(const CUtensorMap, const CUtensorMap, const CUtensorMap, const float *, float *,
+                             const HjCoef<float> *, const float *, HjDevState *, const HjGeom, const TiledParams,
+                             long long);
+    KernelFn fn = (KernelFn)kernel_fn(padded, P.nconsumer);
+    fn<<<g->tiled_ctas, P.nconsumer + 32, smem, g->stream>>>(g->tmap[0], g->tmap[1], g->tmap[2], (const float *)g->v0,
+                                                             (float *)g->buf, (const HjCoef<float> *)g->coef,
+                                                             g->tab_tiled, g->dstate, g->geom, P, g->nint);
     return cudaGetLastError();
 }
