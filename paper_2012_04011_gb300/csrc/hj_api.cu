@@ -173,7 +173,7 @@ hj_status upload_tables(hj_grid *g)
     // per-(v, theta) coefficients in FP64: xdot_1 = v cos(theta), xdot_2 = v sin(theta)
     size_t nco = (size_t)N3 * N4;
     double *f1 = (double *)malloc(sizeof(double) * nco), *f2 = (double *)malloc(sizeof(double) * nco);
-    float *tab = (float *)calloc((size_t)N3 + 2 * (size_t)P4, sizeof(float));
+    float *tab = (float *)calloc((size_t)N3 + 3 * (size_t)P4, sizeof(float));
     if (!f1 || !f2 || !tab) {
         free(f1);
         free(f2);
@@ -229,7 +229,7 @@ hj_status upload_tables(hj_grid *g)
         free(c);
     }
     if (st == HJ_OK) {
-        cudaError_t e = cudaMemcpy(g->tab_tiled, tab, sizeof(float) * ((size_t)N3 + 2 * (size_t)P4),
+        cudaError_t e = cudaMemcpy(g->tab_tiled, tab, sizeof(float) * ((size_t)N3 + 3 * (size_t)P4),
                                    cudaMemcpyHostToDevice);
         if (e != cudaSuccess) st = set_err(HJ_ERR_CUDA, "table upload: %s", cudaGetErrorString(e));
     }
@@ -347,7 +347,7 @@ hj_status hj_create_grid(const int32_t n[4], const double lo[4], const double hi
     if (e == cudaSuccess) e = cudaMalloc(&g->v0, arr);
     if (e == cudaSuccess) e = cudaMalloc(&g->buf, 2 * arr);
     if (e == cudaSuccess) e = cudaMalloc(&g->coef, ncoef * (prec == HJ_FP64 ? sizeof(HjCoef<double>) : sizeof(HjCoef<float>)));
-    if (e == cudaSuccess) e = cudaMalloc(&g->tab_tiled, sizeof(float) * ((size_t)n[2] + 2 * (size_t)g->p4));
+    if (e == cudaSuccess) e = cudaMalloc(&g->tab_tiled, sizeof(float) * ((size_t)n[2] + 3 * (size_t)g->p4));
     if (e == cudaSuccess) e = cudaMalloc(&g->dstate, sizeof(HjDevState));
     if (e == cudaSuccess) e = cudaHostAlloc(&g->hstate, sizeof(HjDevState), cudaHostAllocDefault);
     for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaEventCreate(&g->ev[i]);

@@ -70,7 +70,7 @@ struct hj_grid {
     void *v0;              // V0 (internal layout)
     void *buf;             // two ping-pong buffers, back to back (2*nint values)
     void *coef;            // HjCoef<T>[n3*n4]
-    float *tab_tiled;      // tiled-kernel tables: v_k [n3], cos/dx1 [p4], sin/dx2 [p4], |cos| [p4], |sin| [p4]
+    float *tab_tiled;      // tiled-kernel tables: v_k [n3], cos/dx1 [p4], sin/dx2 [p4], quad signs [p4]
     HjDevState *dstate;
     HjDevState *hstate;    // pinned host mirror
 
@@ -81,10 +81,11 @@ struct hj_grid {
 
     hj_kernel kernel_req;  // requested by hj_set_kernel
     bool tiled_ok;         // the tiled kernel supports this grid
-    CUtensorMap tmap[3];   // V0, buffer A, buffer B (tiled kernel, FP32 only)
+    CUtensorMap tmap[4];   // V0, buffer A, buffer B with the halo box; V0 with the tile box (tiled kernel)
     int32_t tile_req[4];   // requested (ty, tv, xc, stages); 0 = choose automatically
-    int32_t tile_ty, tile_tv, tile_xc, tile_rg, tile_stages;
+    int32_t tile_ty, tile_tv, tile_xc, tile_stages;
     int32_t tiled_ctas, tiled_per_sm;
+    bool tiled_usign;      // every theta quad has one sign of cos and of sin
 
     cudaEvent_t ev[4];
     size_t device_bytes;

@@ -5,20 +5,22 @@
 // bandwidth:
 //   * A CTA owns a column of the grid: TY rows of y x TV rows of v x the full
 //     theta row (so the periodic wrap stays inside the tile), and streams it
-//     along x (the slowest axis), plane by plane.
-//   * A producer warp loads each plane's tile plus its one-cell y/v halo as
-//     one 4D TMA box (cp.async.bulk.tensor.4d) into a ring of shared-memory
-//     stages guarded by mbarriers (full: bytes landed, empty: consumers done).
+//     along x (the slowest axis), plane by plane.  Long columns may be split
+//     into x chunks (work items) to balance the SMs.
+//   * A producer warp loads, per plane, the tile plus its one-cell y/v halo
+//     of V_n and the halo-free tile of V0 as two 4D TMA boxes
+//     (cp.async.bulk.tensor.4d) into one stage of a shared-memory ring
+//     guarded by mbarriers (full: bytes landed, empty: consumers done).
 //     Out-of-range halo rows come back zero-filled and are replaced by
 //     extrapolated ghosts.
-//   * Consumer threads each own a theta quad (float4) of up to MAXR rows; the
-//     x-1 / x / x+1 centres stay in registers, y/v/theta neighbours come from
-//     the plane's stage.  V0 is streamed with float4 loads one plane ahead,
-//     V_new is written with float4 stores.  Every V value is read from HBM
-//     once per step; halos are served by shared memory and L2.
-//   * All CTAs of a step sweep x concurrently (one column per CTA when there
-//     are enough columns), so y/v halo rows of neighbouring columns are in
-//     L2 when they are needed.
+//   * Each consumer thread owns one (y, v) row of the tile and one theta quad
+//     (float4) for the whole kernel.  It holds planes x-1, x, x+1 in the ring
+//     (x-1 and x+1 give the x neighbours), reads y/v/theta neighbours and V0
+//     from the stage of plane x, and writes V_{n+1} with one float4 store.
+//     Every V and V0 value is read from HBM once per step; halos are served
+//     by shared memory and L2.
+//   * All CTAs of a step sweep x concurrently, so y/v halo rows of
+//     neighbouring columns are in L2 when they are needed.
 //   * alpha^max partials (|xdot_1|, |xdot_2| over the (v, theta) states of the
 //     cells each thread updates) are reduced by warp shuffles and a block
 //     reduction, and the last CTA computes the next CFL step (fused; no extra
@@ -26,34 +28,34 @@
 // Every mbarrier wait is bounded by %globaltimer; on timeout the kernel
 // records HJ_ERR_TIMEOUT in the device state, stops issuing work, waits
 // (bounded) for its own copies in flight and returns.
+#include <math.h>
 #include <stdio.h>
 #include <string.h>
-
-#include <type_traits>
 
 #include "hj_device.cuh"
 
 namespace {
 
 constexpr int MAX_STAGES = 8;
-constexpr int MAX_CONSUMERS = 768;      // consumer threads per CTA (+ one producer warp)
+constexpr int MAX_CONSUMERS = 768;  // consumer threads per CTA (+ one producer warp)
 // Launch-bound variants: up to 384, 512, 640 or 768 consumer threads (152,
 // 120, 96 or 80 registers a thread); a shape uses the smallest that holds it.
 constexpr int VARIANTS[4] = {384, 512, 640, 768};
 constexpr unsigned long long WAIT_NS = 4000000000ull;  // 4 s per wait: far beyond any healthy wait
 
 struct TiledParams {
-    int ty, tv;           // tile rows along y and v
-    int xc;               // planes per work item
-    int q4;               // float4 per theta row (p4 / 4)
-    int rg;               // row groups: consumer thread t owns quad t % q4 of rows t / q4 + rg * m
-    int nconsumer;        // consumer threads (multiple of 32)
-    int stages;           // shared-memory ring depth
-    int ncol_v, ncol;     // tiles along v; columns in total
-    int nchunk, nitems;   // x chunks per column; work items = ncol * nchunk
-    int stage_floats;     // p4 * (tv + 2) * (ty + 2)
-    int stage_bytes;      // stage_floats * 4 rounded up to 128
-    float k3, k4, mk34;   // |xdot_3|/dx_3, |xdot_4|/dx_4, -(k3 + k4): constant-bank operands
+    int ty, tv;          // tile rows along y and v
+    int xc;              // planes per work item
+    int q4;              // float4 per theta row (p4 / 4)
+    int nconsumer;       // consumer threads (multiple of 32)
+    int stages;          // shared-memory ring depth
+    int ncol_v, ncol;    // tiles along v; columns in total
+    int nchunk, nitems;  // x chunks per column; work items = ncol * nchunk
+    int halo_box;        // floats in the V box with halo: p4 * (tv + 2) * (ty + 2)
+    int halo_floats;     // its room in a stage: halo_box rounded up to 32 floats (V0 box 128-byte aligned)
+    int v0_floats;       // V0 box: p4 * tv * ty
+    int stage_bytes;     // (halo_floats + v0_floats) * 4 rounded up to 128
+    float k3, k4, mk34;  // |xdot_3|/dx_3, |xdot_4|/dx_4, -(k3 + k4): constant-bank operands
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -97,7 +99,8 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, unsign
     return true;
 }
 // Warp-uniform version for consumer warps: every lane observes the phase,
-// and the timeout decision is the same for the whole warp.
+// and the timeout decision is the same for the whole warp.  The deadline is
+// read (from shared memory) only when the phase is not complete yet.
 __device__ __forceinline__ bool mbar_wait_warp(uint64_t *bar, uint32_t parity, const unsigned long long *deadline)
 {
     while (true) {
@@ -150,12 +153,15 @@ __device__ __forceinline__ ItemGeom item_geom(const TiledParams &P, const HjGeom
     return it;
 }
 
-template <bool PADDED, int MAXC>
+// PADDED: N4 is not a multiple of 4 (the last quad of a row has pad lanes).
+// USIGN: cos(theta) and sin(theta) have one sign (up to negligible values)
+// across every theta quad, so each thread picks its x and y upwind sides once.
+template <bool PADDED, bool USIGN, int MAXC>
 __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
     const __grid_constant__ CUtensorMap map_v0, const __grid_constant__ CUtensorMap map_a,
-    const __grid_constant__ CUtensorMap map_b, const float *__restrict__ v0, float *__restrict__ buf,
-    const HjCoef<float> *__restrict__ coef, const float *__restrict__ tab, HjDevState *st, const HjGeom g,
-    const TiledParams P, long long nint)
+    const __grid_constant__ CUtensorMap map_b, const __grid_constant__ CUtensorMap map_v0_tile,
+    float *__restrict__ buf, const HjCoef<float> *__restrict__ coef, const float *__restrict__ tab, HjDevState *st,
+    const HjGeom g, const TiledParams P, long long nint)
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     if (st->done) return;  // uniform across the grid
@@ -170,9 +176,7 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
 
     const long long n = st->n;
     const float dt = (float)st->dt;
-    const float *vin_unused;
-    float *vout;
-    hj_io_buffers<float>(v0, buf, nint, n, vin_unused, vout);
+    float *vout = buf + (n & 1) * nint;
     const CUtensorMap *map_in = (n == 0) ? &map_v0 : (((n - 1) & 1) ? &map_b : &map_a);
 
     const int tid = threadIdx.x;
@@ -189,19 +193,20 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
     }
     __syncthreads();
 
-    const unsigned long long deadline = *deadline_p;
     float am1 = 0.f, am2 = 0.f;  // this thread's max |xdot_1|, |xdot_2| (non-negative)
 
     if (tid >= P.nconsumer) {
         // ------------------------------------------------------------ producer
         if (tid == P.nconsumer) {
+            const unsigned long long deadline = *deadline_p;
             // ring cursor: slot of the next load and the parity of its use
             int slot = 0;
             uint32_t phase = 0;
             uint32_t issued = 0;      // loads issued so far
             uint32_t used_mask = 0;   // slots that received a load
             uint32_t last_phase = 0;  // bit s: parity of the last load into slot s
-            const uint32_t tx = (uint32_t)(P.stage_floats * 4);
+            // bytes each box delivers (the exact box sizes, not the padded room)
+            const uint32_t tx_halo = (uint32_t)(P.halo_box * 4), tx_v0 = (uint32_t)(P.v0_floats * 4);
             bool ok = true;
             for (int item = blockIdx.x; item < P.nitems && ok; item += gridDim.x) {
                 ItemGeom it = item_geom(P, g, item);
@@ -215,9 +220,11 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
                         ok = false;
                         break;
                     }
-                    mbar_arrive_expect_tx(&full[slot], tx);
-                    tma_load_4d(stages + (size_t)slot * (P.stage_bytes / 4), map_in, &full[slot], 0, it.v0 - 1,
-                                it.y0 - 1, p);
+                    const bool interior = p >= it.x0 && p < it.x1;  // V0 is needed on updated planes only
+                    float *dst = stages + (size_t)slot * (P.stage_bytes / 4);
+                    mbar_arrive_expect_tx(&full[slot], tx_halo + (interior ? tx_v0 : 0u));
+                    tma_load_4d(dst, map_in, &full[slot], 0, it.v0 - 1, it.y0 - 1, p);
+                    if (interior) tma_load_4d(dst + P.halo_floats, &map_v0_tile, &full[slot], 0, it.v0, it.y0, p);
                     used_mask |= 1u << slot;
                     last_phase = (last_phase & ~(1u << slot)) | (phase << slot);
                     ++issued;
@@ -249,20 +256,32 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
         const int jy = r / P.tv, kv = r - (r / P.tv) * P.tv;
         const bool inrow = r < P.ty * P.tv;
         const int rsm = inrow ? ((jy + 1) * srow + (kv + 1)) * P4 + 4 * q : (srow + 1) * P4;
+        const int r0sm = P.halo_floats + (inrow ? (jy * P.tv + kv) * P4 + 4 * q : 0);  // V0 in the stage
         const uint32_t s1 = (uint32_t)N2 * N3 * P4;  // plane stride (the grid has < 2^31 values)
 
-        // Upwind weights of the x and y terms for this quad: xdot_1/dx_1 =
-        // v cos(th)/dx_1 splits into a part that takes V(x+1) (cos >= 0) and
-        // one that takes V(x-1) (cos < 0); likewise y with sin.
-        float cp[4], cm[4], sp[4], sm[4], cs[4];
+        // x and y upwind weights of this quad: xdot_1/dx_1 = v cos(th)/dx_1
+        // takes V(x+1) where cos >= 0 and V(x-1) where cos < 0; likewise y.
+        float wx[4], wy[4], cs[4], wxm[4], wym[4];
+        bool xplus = true, yplus = true;
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             const float c = tab[N3 + 4 * q + e], s = tab[N3 + P4 + 4 * q + e];
-            cp[e] = fmaxf(c, 0.f);
-            cm[e] = fmaxf(-c, 0.f);
-            sp[e] = fmaxf(s, 0.f);
-            sm[e] = fmaxf(-s, 0.f);
             cs[e] = fabsf(c) + fabsf(s);
+            if (USIGN) {
+                wx[e] = fabsf(c);
+                wy[e] = fabsf(s);
+                wxm[e] = wym[e] = 0.f;
+            } else {
+                wx[e] = fmaxf(c, 0.f);
+                wxm[e] = fmaxf(-c, 0.f);
+                wy[e] = fmaxf(s, 0.f);
+                wym[e] = fmaxf(-s, 0.f);
+            }
+        }
+        if (USIGN) {  // the side of the quad's dominant lane (the host checked the others agree or vanish)
+            // scalar loads: the sign table starts at float N3 + 2 P4, not 16-byte aligned in general
+            xplus = tab[N3 + 2 * P4 + 4 * q] >= 0.f;
+            yplus = tab[N3 + 2 * P4 + 4 * q + 1] >= 0.f;
         }
         const int lm = (4 * q - 1 + N4) % N4;  // theta index left of the quad
         const int lp = (4 * q + 4) % N4;       // right of the quad
@@ -270,13 +289,30 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
 
         // Ring cursors.  Planes are waited for and released in load order, so
         // one cursor walks the slots to wait on (with the phase parity) and
-        // one walks the slots to release; plane x is always the oldest plane
-        // not yet released.
+        // one walks the slots to release.
         int wslot = 0, rslot = 0;
         uint32_t wphase = 0;
         const int nst = P.stages;
         const int sfl = P.stage_bytes / 4;
         bool ok = true;
+#define HJ_WAIT_NEXT(slot_out)                                   \
+    do {                                                         \
+        if (!mbar_wait_warp(&full[wslot], wphase, deadline_p)) { \
+            slot_out = -1;                                       \
+        } else {                                                 \
+            slot_out = wslot;                                    \
+            if (++wslot == nst) {                                \
+                wslot = 0;                                       \
+                wphase ^= 1u;                                    \
+            }                                                    \
+        }                                                        \
+    } while (0)
+#define HJ_RELEASE_OLDEST()                            \
+    do {                                               \
+        __syncwarp();                                  \
+        if (lane == 0) mbar_arrive(&empty[rslot]);     \
+        if (++rslot == nst) rslot = 0;                 \
+    } while (0)
         for (int item = blockIdx.x; item < P.nitems && ok; item += gridDim.x) {
             const ItemGeom it = item_geom(P, g, item);
             const bool edge = it.y0 == 0 || it.y0 + P.ty >= N2 || it.v0 == 0 || it.v0 + P.tv >= N3;
@@ -288,30 +324,8 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
             const uint32_t gmask = (y == 0 ? 1u : 0u) | (y == N2 - 1 ? 2u : 0u) | (v == 0 ? 4u : 0u) |
                                    (v == N3 - 1 ? 8u : 0u);
 
-            // wait for the next plane in load order; returns its slot or -1
-#define HJ_WAIT_NEXT(slot_out)                                         \
-    do {                                                               \
-        if (!mbar_wait_warp(&full[wslot], wphase, deadline_p)) {       \
-            slot_out = -1;                                             \
-        } else {                                                       \
-            slot_out = wslot;                                          \
-            if (++wslot == nst) {                                      \
-                wslot = 0;                                             \
-                wphase ^= 1u;                                          \
-            }                                                          \
-        }                                                              \
-    } while (0)
-            // release the oldest plane still held
-#define HJ_RELEASE_OLDEST()                                            \
-    do {                                                               \
-        __syncwarp();                                                  \
-        if (lane == 0) mbar_arrive(&empty[rslot]);                     \
-        if (++rslot == nst) rslot = 0;                                 \
-    } while (0)
-
-            // Planes held in the ring while plane x is updated: x-1 (if
-            // loaded), x and x+1; plane x-1 is released after the update.
-            float4 cur, nxt;
+            // Planes held while plane x is updated: x-1 (if loaded), x and
+            // x+1; plane x-1 is released after the update.
             int s_first, s_x;
             HJ_WAIT_NEXT(s_first);
             s_x = s_first;
@@ -320,7 +334,7 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
                 ok = false;
                 break;
             }
-            cur = *(const float4 *)(stages + (size_t)s_x * sfl + rsm);
+            float4 cur = *(const float4 *)(stages + (size_t)s_x * sfl + rsm);
             int s_prev = it.x0 > it.pl0 ? s_first : -1;  // slot of plane x-1, -1 at x = 0
 
             for (int x = it.x0; x < it.x1; ++x) {
@@ -328,13 +342,10 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
                     ok = false;
                     break;
                 }
-                // V0 of this plane (used last, so its latency overlaps the rest)
-                const float4 v0c = rok ? __ldcs((const float4 *)(v0 + (uint32_t)x * s1 + rbase))
-                                       : make_float4(0.f, 0.f, 0.f, 0.f);
                 const float *sx = stages + (size_t)s_x * sfl;
                 // centre of plane x+1, or the extrapolated ghost past the end
                 int s_n = -1;
-                float4 prev;
+                float4 prev, nxt;
                 if (x + 1 <= N1 - 1) {
                     HJ_WAIT_NEXT(s_n);
                     if (s_n < 0) {
@@ -364,6 +375,12 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
                     const float tl = row0[lm], tr = row0[lp];
                     float t0 = 0.f;
                     if (PADDED) t0 = row0[0];
+                    const float4 v0c = *(const float4 *)(sx + r0sm);
+                    float4 xu = nxt, yu = yp;  // upwind x / y neighbours (USIGN)
+                    if (USIGN) {
+                        if (!xplus) xu = prev;
+                        if (!yplus) yu = ym;
+                    }
                     float4 out;
 #pragma unroll
                     for (int e = 0; e < 4; ++e) {
@@ -371,11 +388,16 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
                         const float tm = e == 0 ? tl : f4get(cur, e - 1);
                         float tp = e == 3 ? tr : f4get(cur, e + 1);
                         if (PADDED && lreal < 4 && e == lreal - 1) tp = t0;  // wrap of a padded last quad
-                        // x and y: upwind differences folded into weights (no selects)
-                        float in = cp[e] * f4get(nxt, e);
-                        in = fmaf(cm[e], f4get(prev, e), in);
-                        in = fmaf(sp[e], f4get(yp, e), in);
-                        in = fmaf(sm[e], f4get(ym, e), in);
+                        float in;
+                        if (USIGN) {
+                            in = wx[e] * f4get(xu, e);
+                            in = fmaf(wy[e], f4get(yu, e), in);
+                        } else {  // upwind differences folded into weights (no selects)
+                            in = wx[e] * f4get(nxt, e);
+                            in = fmaf(wxm[e], f4get(prev, e), in);
+                            in = fmaf(wy[e], f4get(yp, e), in);
+                            in = fmaf(wym[e], f4get(ym, e), in);
+                        }
                         in = fmaf(-cs[e], vc, in);
                         // v and theta: the bang-bang control takes the larger neighbour
                         float acc = fmaf(P.k3, fmaxf(f4get(vp, e), f4get(vm, e)), P.mk34 * vc);
@@ -396,9 +418,9 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
             // still held: plane x1-1 and, if loaded, the halo plane x1
             HJ_RELEASE_OLDEST();
             if (it.x1 <= it.pl1) HJ_RELEASE_OLDEST();
+        }
 #undef HJ_WAIT_NEXT
 #undef HJ_RELEASE_OLDEST
-        }
         if (!ok) {
             st->status = HJ_ERR_TIMEOUT;
             *abort_flag = 1;
@@ -417,6 +439,25 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
         }
     }
     hj_step_epilogue(st, g, hj_abits((double)am1), hj_abits((double)am2), scratch);
+}
+
+typedef void (*KernelFn)(const CUtensorMap, const CUtensorMap, const CUtensorMap, const CUtensorMap, float *,
+                         const HjCoef<float> *, const float *, HjDevState *, const HjGeom, const TiledParams,
+                         long long);
+
+template <bool PADDED, bool USIGN>
+KernelFn kernel_fn_pu(int nconsumer)
+{
+    if (nconsumer <= VARIANTS[0]) return hj_step_tiled_kernel<PADDED, USIGN, VARIANTS[0]>;
+    if (nconsumer <= VARIANTS[1]) return hj_step_tiled_kernel<PADDED, USIGN, VARIANTS[1]>;
+    if (nconsumer <= VARIANTS[2]) return hj_step_tiled_kernel<PADDED, USIGN, VARIANTS[2]>;
+    return hj_step_tiled_kernel<PADDED, USIGN, VARIANTS[3]>;
+}
+
+KernelFn kernel_fn(bool padded, bool usign, int nconsumer)
+{
+    if (padded) return usign ? kernel_fn_pu<true, true>(nconsumer) : kernel_fn_pu<true, false>(nconsumer);
+    return usign ? kernel_fn_pu<false, true>(nconsumer) : kernel_fn_pu<false, false>(nconsumer);
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
@@ -447,13 +488,13 @@ TiledParams make_params(const hj_grid *g, int ty, int tv, int stages, int xc)
     P.tv = tv;
     P.stages = stages;
     P.q4 = g->p4 / 4;
-    int rows = ty * tv;
-    P.rg = rows;
-    P.nconsumer = ((P.q4 * rows + 31) / 32) * 32;
+    P.nconsumer = ((P.q4 * ty * tv + 31) / 32) * 32;
     P.ncol_v = (g->n[2] + tv - 1) / tv;
     P.ncol = ((g->n[1] + ty - 1) / ty) * P.ncol_v;
-    P.stage_floats = g->p4 * (tv + 2) * (ty + 2);
-    P.stage_bytes = ((P.stage_floats * 4 + 127) / 128) * 128;
+    P.halo_box = g->p4 * (tv + 2) * (ty + 2);
+    P.halo_floats = (P.halo_box + 31) / 32 * 32;
+    P.v0_floats = g->p4 * tv * ty;
+    P.stage_bytes = ((P.halo_floats + P.v0_floats) * 4 + 127) / 128 * 128;
     P.xc = xc < 1 ? g->n[0] : (xc > g->n[0] ? g->n[0] : xc);
     P.nchunk = (g->n[0] + P.xc - 1) / P.xc;
     P.nitems = P.ncol * P.nchunk;
@@ -485,24 +526,45 @@ int best_chunk(const hj_grid *g, int ncol, int slots)
     return best_xc;
 }
 
-template <bool PADDED>
-const void *kernel_fn_p(int nconsumer)
+size_t tiled_smem_bytes(const TiledParams &P)
 {
-    if (nconsumer <= VARIANTS[0]) return (const void *)hj_step_tiled_kernel<PADDED, VARIANTS[0]>;
-    if (nconsumer <= VARIANTS[1]) return (const void *)hj_step_tiled_kernel<PADDED, VARIANTS[1]>;
-    if (nconsumer <= VARIANTS[2]) return (const void *)hj_step_tiled_kernel<PADDED, VARIANTS[2]>;
-    return (const void *)hj_step_tiled_kernel<PADDED, VARIANTS[3]>;
+    return (size_t)P.stages * P.stage_bytes + 2 * MAX_STAGES * sizeof(uint64_t) + 64 * sizeof(unsigned long long) +
+           32;
 }
 
-const void *kernel_fn(bool padded, int nconsumer)
+// Whether every theta quad has one sign of cos and of sin, up to values that
+// are negligible (|x| <= 1e-6 max|x|) and contribute nothing measurable in
+// FP32; also writes the quads' dominant signs into tab_sign[4 * q].
+bool sign_uniform(const hj_grid *g, float *tab_sign)
 {
-    return padded ? kernel_fn_p<true>(nconsumer) : kernel_fn_p<false>(nconsumer);
-}
-
-size_t tiled_smem_bytes(const TiledParams &P, int n3)
-{
-    (void)n3;
-    return (size_t)P.stages * P.stage_bytes + 2 * MAX_STAGES * sizeof(uint64_t) + 64 * sizeof(unsigned long long) + 16;
+    const int N4 = g->n[3];
+    double cmax = 0, smax = 0;
+    for (int l = 0; l < N4; ++l) {
+        const double th = g->lo[3] + (double)l * g->h[3];
+        cmax = fmax(cmax, fabs(cos(th)));
+        smax = fmax(smax, fabs(sin(th)));
+    }
+    bool ok = true;
+    for (int q = 0; q < g->p4 / 4; ++q) {
+        double bc = 0, bs = 0;
+        int sc = 1, ss = 1;
+        for (int e = 0; e < 4 && 4 * q + e < N4; ++e) {
+            const double th = g->lo[3] + (double)(4 * q + e) * g->h[3];
+            if (fabs(cos(th)) > bc) bc = fabs(cos(th)), sc = cos(th) >= 0 ? 1 : -1;
+            if (fabs(sin(th)) > bs) bs = fabs(sin(th)), ss = sin(th) >= 0 ? 1 : -1;
+        }
+        for (int e = 0; e < 4 && 4 * q + e < N4; ++e) {
+            const double th = g->lo[3] + (double)(4 * q + e) * g->h[3];
+            const double c = cos(th), s = sin(th);
+            if ((c >= 0 ? 1 : -1) != sc && fabs(c) > 1e-6 * cmax) ok = false;
+            if ((s >= 0 ? 1 : -1) != ss && fabs(s) > 1e-6 * smax) ok = false;
+        }
+        tab_sign[4 * q + 0] = (float)sc;
+        tab_sign[4 * q + 1] = (float)ss;
+        tab_sign[4 * q + 2] = 0.f;
+        tab_sign[4 * q + 3] = 0.f;
+    }
+    return ok;
 }
 
 }  // namespace
@@ -531,6 +593,15 @@ bool hj_tiled_setup(hj_grid *g, char *why, size_t why_len)
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);
     cudaDeviceGetAttribute(&maxsmem, cudaDevAttrMaxSharedMemoryPerBlockOptin, g->device);
 
+    // quad signs: tab_tiled holds v_k [n3], cos/dx1 [p4], sin/dx2 [p4], then
+    // the (cos, sin) sign of each quad's dominant lane [p4]
+    float *sgn = (float *)calloc((size_t)g->p4, sizeof(float));
+    if (!sgn) return fail("host allocation failed");
+    const bool usign = sign_uniform(g, sgn);
+    cudaError_t e = cudaMemcpy(g->tab_tiled + g->n[2] + 2 * g->p4, sgn, sizeof(float) * g->p4, cudaMemcpyHostToDevice);
+    free(sgn);
+    if (e != cudaSuccess) return fail("sign table upload failed");
+
     // tile shape: by default 8 x 4 rows of (y, v) and as many stages as fit;
     // one consumer thread per (row, theta quad), at most MAX_CONSUMERS (+ the
     // producer warp)
@@ -552,9 +623,9 @@ bool hj_tiled_setup(hj_grid *g, char *why, size_t why_len)
     if (stages < 4 || stages > MAX_STAGES) return fail("stage count out of range");
     TiledParams P = make_params(g, ty, tv, stages, 0);
     if (P.nconsumer > MAX_CONSUMERS) return fail("tile needs too many threads");
-    size_t smem = tiled_smem_bytes(P, g->n[2]);
+    size_t smem = tiled_smem_bytes(P);
     if ((int)smem > maxsmem) return fail("tile does not fit in shared memory");
-    const void *fn = kernel_fn(g->p4 != g->n[3], P.nconsumer);
+    const void *fn = (const void *)kernel_fn(g->p4 != g->n[3], usign, P.nconsumer);
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return fail("cannot raise the shared-memory limit");
     int per_sm = 0;
@@ -565,17 +636,19 @@ bool hj_tiled_setup(hj_grid *g, char *why, size_t why_len)
     const int xc = g->tile_req[2] > 0 ? g->tile_req[2] : best_chunk(g, P.ncol, slots);
     P = make_params(g, ty, tv, stages, xc);
 
-    // tensor maps over V0 and the two ping-pong buffers: dims (p4, n3, n2, n1)
+    // tensor maps, dims (p4, n3, n2, n1): V0 / buffer A / buffer B with the
+    // halo box, and V0 with the halo-free box
     cuuint64_t dims[4] = {(cuuint64_t)g->p4, (cuuint64_t)g->n[2], (cuuint64_t)g->n[1], (cuuint64_t)g->n[0]};
     cuuint64_t strides[3] = {(cuuint64_t)g->p4 * 4, (cuuint64_t)g->p4 * g->n[2] * 4,
                              (cuuint64_t)g->p4 * g->n[2] * g->n[1] * 4};
-    cuuint32_t box[4] = {(cuuint32_t)g->p4, (cuuint32_t)(tv + 2), (cuuint32_t)(ty + 2), 1};
+    cuuint32_t box_halo[4] = {(cuuint32_t)g->p4, (cuuint32_t)(tv + 2), (cuuint32_t)(ty + 2), 1};
+    cuuint32_t box_tile[4] = {(cuuint32_t)g->p4, (cuuint32_t)tv, (cuuint32_t)ty, 1};
     cuuint32_t estr[4] = {1, 1, 1, 1};
-    void *bases[3] = {g->v0, g->buf, (char *)g->buf + (size_t)g->nint * 4};
-    for (int i = 0; i < 3; ++i) {
-        CUresult r = enc(&g->tmap[i], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, bases[i], dims, strides, box, estr,
-                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    void *bases[4] = {g->v0, g->buf, (char *)g->buf + (size_t)g->nint * 4, g->v0};
+    for (int i = 0; i < 4; ++i) {
+        CUresult r = enc(&g->tmap[i], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, bases[i], dims, strides,
+                         i < 3 ? box_halo : box_tile, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) {
             snprintf(why, why_len, "cuTensorMapEncodeTiled failed (%d)", (int)r);
             return false;
@@ -584,26 +657,19 @@ bool hj_tiled_setup(hj_grid *g, char *why, size_t why_len)
     g->tile_ty = ty;
     g->tile_tv = tv;
     g->tile_xc = P.xc;
-    g->tile_rg = P.rg;
     g->tile_stages = stages;
     g->tiled_ctas = P.nitems < slots ? P.nitems : slots;
     g->tiled_per_sm = per_sm;
+    g->tiled_usign = usign;
     return true;
 }
 
 cudaError_t hj_launch_step_tiled(hj_grid *g)
 {
-    TiledParams P = make_params(g, g->tile_ty, g->tile_tv, g->tile_stages, g->tile_xc);
-    size_t smem = tiled_smem_bytes(P, g->n[2]);
-    const bool padded = g->p4 != g->n[3];
-    // the variant's launch bound is a template argument; pick it through the
-    // same table as the set-up
-    typedef void (*KernelFn)(const CUtensorMap, const CUtensorMap, const CUtensorMap, const float *, float *,
-                             const HjCoef<float> *, const float *, HjDevState *, const HjGeom, const TiledParams,
-                             long long);
-    KernelFn fn = (KernelFn)kernel_fn(padded, P.nconsumer);
-    fn<<<g->tiled_ctas, P.nconsumer + 32, smem, g->stream>>>(g->tmap[0], g->tmap[1], g->tmap[2], (const float *)g->v0,
-                                                             (float *)g->buf, (const HjCoef<float> *)g->coef,
-                                                             g->tab_tiled, g->dstate, g->geom, P, g->nint);
+    const TiledParams P = make_params(g, g->tile_ty, g->tile_tv, g->tile_stages, g->tile_xc);
+    KernelFn fn = kernel_fn(g->p4 != g->n[3], g->tiled_usign, P.nconsumer);
+    fn<<<g->tiled_ctas, P.nconsumer + 32, tiled_smem_bytes(P), g->stream>>>(
+        g->tmap[0], g->tmap[1], g->tmap[2], g->tmap[3], (float *)g->buf, (const HjCoef<float> *)g->coef,
+        g->tab_tiled, g->dstate, g->geom, P, g->nint);
     return cudaGetLastError();
 }
