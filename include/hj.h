@@ -200,6 +200,37 @@ HJ_API hj_status hj_set_tile_shape(hj_grid *g, const int32_t shape[4]);
 HJ_API hj_status hj_autotune(hj_grid *g, int32_t steps_per_trial, hj_tile_result *results, int32_t max_results,
                              int32_t *nresults);
 
+/* One time step on caller-owned DEVICE arrays, allocating nothing.  The paper
+ * has no counterpart: this entry point exists for callers that cannot
+ * allocate device memory, such as code whose device memory all belongs to a
+ * host framework's own pool, code on a memory budget fixed at start-up, or
+ * code that must not call cudaMalloc (which can synchronise the device) at
+ * the moment it steps.
+ *
+ * Computes v_out = min(v0, v_in + dt * rate(v_in)) for every cell: the same
+ * step as hj_advance_brt, with the dt the caller gives (>= 0, finite).
+ * Arrays are dense [N1][N2][N3][N4] of double (HJ_FP64) or float (HJ_FP32)
+ * on the current device; v_out must not overlap v_in.  Grid, periodic mask
+ * and dynamics are as for hj_create_grid and hj_set_dynamics.
+ * alpha_max_out (host, may be NULL) receives alpha_d^max over the grid, from
+ * which a caller forms the next CFL step (dt = CFL / sum_d alpha_d^max/dx_d).
+ *
+ * It calls no cudaMalloc, cudaFree or other allocating routine.  Its working
+ * data (the per-(v, theta) coefficient table and the alpha^max accumulators)
+ * live in a fixed device array of 640 KiB that every GPU which loads the
+ * library holds until the process exits; N3 * N4 may therefore be at most
+ * 16384 (HJ_ERR_INVALID_ARG beyond).  The first call on a device looks up
+ * that array's device address (cudaGetSymbolAddress); make that first call
+ * before any stream capture.  All calls share the array and it keeps the
+ * last call's contents (each call clears what must start at zero), so calls
+ * whose work overlaps on the GPU race with one another: serialise them on
+ * one stream.  Runs on cuda_stream (NULL: the legacy default stream) and
+ * returns when the step is complete. */
+HJ_API hj_status hj_step_noalloc(const int32_t n[4], const double lo[4], const double hi[4], uint32_t periodic_mask,
+                                 hj_precision prec, hj_dynamics kind, const double *params, int32_t nparams,
+                                 const void *v_in, const void *v0, void *v_out, double dt, void *cuda_stream,
+                                 double alpha_max_out[4]);
+
 /* Describe the grid (sizes, spacings, time, memory). */
 HJ_API hj_status hj_get_info(const hj_grid *g, hj_grid_info *info);
 

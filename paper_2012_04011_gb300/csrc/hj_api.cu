@@ -277,6 +277,8 @@ void free_grid(hj_grid *g)
 
 }  // namespace
 
+void hj_internal_set_error(const char *msg) { snprintf(g_err, sizeof(g_err), "%s", msg); }
+
 // ==================================================================== C ABI
 
 extern "C" {

@@ -100,6 +100,9 @@ bool hj_tiled_setup(hj_grid *g, char *why, size_t why_len);
 // and whether that shape can run at all.
 int hj_tiled_threads(const hj_grid *g, int ty, int tv);
 
+// Sets the message hj_last_error() returns on this host thread.
+void hj_internal_set_error(const char *msg);
+
 // Pointer of the value buffer that holds V after n steps.
 inline void *hj_value_ptr(const hj_grid *g, long long n)
 {

@@ -107,6 +107,10 @@ _SIGS = {
     "hj_set_tile_shape": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int32)]),
     "hj_autotune": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.POINTER(hj_tile_result), ctypes.c_int32,
                                    ctypes.POINTER(ctypes.c_int32)]),
+    "hj_step_noalloc": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_double), ctypes.c_uint32, ctypes.c_int, ctypes.c_int,
+                                       ctypes.POINTER(ctypes.c_double), ctypes.c_int32, _VP, _VP, _VP,
+                                       ctypes.c_double, _VP, ctypes.POINTER(ctypes.c_double)]),
     "hj_get_info": (ctypes.c_int, [_VP, ctypes.POINTER(hj_grid_info)]),
     "hj_destroy_grid": (None, [_VP]),
     "hj_status_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -241,6 +245,20 @@ def hj_autotune(g, steps_per_trial: int = 8, max_results: int = 32):
     cnt = ctypes.c_int32(0)
     _check(lib.hj_autotune(g, int(steps_per_trial), res, int(max_results), ctypes.byref(cnt)))
     return [res[i] for i in range(min(cnt.value, max_results))]
+
+
+def hj_step_noalloc(n, lo, hi, periodic_mask, prec, kind, params, v_in, v0, v_out, dt, cuda_stream=None):
+    """One step on caller-owned device arrays without any allocation; returns alpha^max (4 values)."""
+    cn = (ctypes.c_int32 * 4)(*[int(v) for v in n])
+    clo = (ctypes.c_double * 4)(*[float(v) for v in lo])
+    chi = (ctypes.c_double * 4)(*[float(v) for v in hi])
+    p = (ctypes.c_double * len(params))(*[float(v) for v in params])
+    alpha = (ctypes.c_double * 4)()
+    stream = None if cuda_stream is None else ctypes.c_void_p(int(cuda_stream))
+    _check(lib.hj_step_noalloc(cn, clo, chi, int(periodic_mask), int(prec), int(kind), p, len(params),
+                               ctypes.c_void_p(_dptr(v_in)), ctypes.c_void_p(_dptr(v0)), ctypes.c_void_p(_dptr(v_out)),
+                               float(dt), stream, alpha))
+    return list(alpha)
 
 
 def hj_get_info(g) -> hj_grid_info:
