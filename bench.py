@@ -35,7 +35,12 @@ UNIT = "cell-updates/s"
 WORKLOAD = "car4d_128x128x64x96"
 BYTES_PER_UPDATE = {"f32": 12, "f64": 24}
 PROFILE = os.path.join(ROOT, "profiles", "hj_step_tiled_car4d_128x128x64x96.md")
-KERNEL_SOURCES = ["hj_step_tiled.cu", "hj_device.cuh", "hj_internal.h"]
+KERNEL_SOURCES = ["hj_step_tiled.cu", "hj_device.cuh"]
+# FP64 path: bound by the FP64 unit.  Algorithmic FP64 flops per cell-update:
+# 1 DMUL + 5 DFMA = 11; nominal GB300 FP64 rate 1.25 TFLOP/s (no measured FP64
+# figure in MEASURED_PEAKS.json).
+FP64_FLOPS_PER_UPDATE = 11
+FP64_PEAK_TFLOPS = 1.25
 
 
 # ------------------------------------------------------------------ helpers
@@ -247,7 +252,10 @@ def run_ours(args):
         g = hj.Grid(w.grid.n, w.grid.lo, w.grid.hi, w.grid.periodic, prec, stream.cuda_stream)
         g.set_dynamics(hj.HJ_DYN_CAR4D, (w.a_max, w.w_max))
         tuned = None
-        if prec == hj.HJ_FP32 and not args.no_autotune:
+        if prec == hj.HJ_FP32 and args.tile:
+            g.set_tile_shape([int(v) for v in args.tile.split(",")])
+            tuned = {"shape": list(g.info().tile), "ctas": g.info().tile_ctas, "tried": []}
+        elif prec == hj.HJ_FP32 and not args.no_autotune:
             # pick the tile shape by timing candidates (outside the timed region)
             hj.hj_set_initial_value_device(g.handle, V0_dev)
             tried = g.autotune(8)
@@ -356,6 +364,13 @@ def run_ours(args):
             "value": r64["value"], "unit": UNIT, "ms_per_step": r64["ms_per_step"], "steps": r64["K"],
             "latency_ms": r64["latency_ms"], "avg_step_kernel_ms": r64["avg_step_kernel_ms"],
             "hbm_frac": BYTES_PER_UPDATE["f64"] * ncell / (r64["avg_step_kernel_ms"] * 1e-3) / 1e9 / peak,
+            "roofline": {"bound": "alu", "kernel": "hj_step_generic_kernel<double>",
+                         "achieved": FP64_FLOPS_PER_UPDATE * ncell / (r64["avg_step_kernel_ms"] * 1e-3) / 1e12,
+                         "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": FP64_FLOPS_PER_UPDATE * ncell / (r64["avg_step_kernel_ms"] * 1e-3) / 1e12
+                         / FP64_PEAK_TFLOPS,
+                         "peak_source": "nominal GB300 FP64 rate (profiling recipe table)",
+                         "flops_per_update": FP64_FLOPS_PER_UPDATE},
             "speedup_fp32_over_fp64": r32["value"] / r64["value"],
         }
     if world == 1 and not args.no_cpu_baseline:
@@ -383,6 +398,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--tile", default="", help="fixed tile shape ty,tv,xc,stages instead of autotuning")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("note: fewer than 3 warm-up steps", file=sys.stderr)

@@ -19,6 +19,44 @@
 
 namespace {
 
+// Division of 32-bit unsigned integers by an invariant divisor d >= 1 with a
+// multiply-high and shifts (Granlund and Montgomery, "Division by Invariant
+// Integers using Multiplication", PLDI 1994, Sec. 4): with l = ceil(log2 d)
+// and m = floor(2^32 (2^l - d) / d) + 1, q = (t + ((n - t) >> min(l, 1)))
+// >> max(l - 1, 0) where t = mulhi(m, n), exact for every 32-bit n.  A
+// runtime integer division is a long instruction sequence on this GPU (part
+// of it on the FP64 unit, which the FP64 path needs for its arithmetic).
+struct FastDiv {
+    uint32_t d, m, s1, s2;
+};
+
+FastDiv make_fastdiv(uint32_t d)
+{
+    FastDiv f;
+    int l = 0;
+    while ((1ull << l) < d) ++l;
+    f.d = d;
+    f.m = (uint32_t)((((1ull << 32) * ((1ull << l) - d)) / d) + 1);
+    f.s1 = l > 0 ? 1u : 0u;
+    f.s2 = l > 0 ? (uint32_t)(l - 1) : 0u;
+    return f;
+}
+
+__device__ __forceinline__ uint32_t fast_div(uint32_t n, const FastDiv &f)
+{
+    const uint32_t t = __umulhi(n, f.m);
+    return (t + ((n - t) >> f.s1)) >> f.s2;
+}
+
+struct Divisors {
+    FastDiv n4, n3, n2;
+};
+
+// Sign and magnitude of a coefficient without the FP64 unit: the sign bit
+// is in the high word.
+__device__ __forceinline__ bool nonneg(double x) { return __double2hiint(x) >= 0; }
+__device__ __forceinline__ bool nonneg(float x) { return __float_as_int(x) >= 0; }
+
 template <typename T>
 struct Neigh {
     T m, p;  // values at index - 1 and + 1 along one axis (ghosts already applied)
@@ -51,10 +89,10 @@ __device__ __forceinline__ T upwind_value(const Neigh<T> &nb, int mode)
     return mode == HJ_AXIS_PLUS ? nb.p : nb.m;
 }
 
-template <typename T>
+template <typename T, bool FAST32>
 __global__ void __launch_bounds__(256) hj_step_generic_kernel(const T *__restrict__ v0, T *__restrict__ buf,
                                                                const HjCoef<T> *__restrict__ coef, HjDevState *st,
-                                                               const HjGeom g, long long nint)
+                                                               const HjGeom g, long long nint, const Divisors dv)
 {
     __shared__ unsigned long long scratch[64];
     if (st->done) return;  // uniform: written by the previous kernel on this stream
@@ -69,15 +107,29 @@ __global__ void __launch_bounds__(256) hj_step_generic_kernel(const T *__restric
     const unsigned long long ncell = (unsigned long long)N1 * N2 * N3 * N4;
     const T k3 = (T)g.k3, k4 = (T)g.k4;
     unsigned long long am1 = 0ull, am2 = 0ull;
+    float am1f = 0.f, am2f = 0.f;
 
     for (unsigned long long c = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; c < ncell;
          c += (unsigned long long)gridDim.x * blockDim.x) {
-        const unsigned long long row = c / N4;
-        const int l = (int)(c - row * N4);
-        const unsigned long long r2 = row / N3;
-        const int k = (int)(row - r2 * N3);
-        const int i = (int)(r2 / N2);
-        const int j = (int)(r2 - (unsigned long long)i * N2);
+        unsigned long long row;
+        int l, k, i, j;
+        if (FAST32) {  // the grid has fewer than 2^32 cells
+            const uint32_t c32 = (uint32_t)c, row32 = fast_div(c32, dv.n4);
+            const uint32_t r2 = fast_div(row32, dv.n3);
+            const uint32_t i32 = fast_div(r2, dv.n2);
+            row = row32;
+            l = (int)(c32 - row32 * N4);
+            k = (int)(row32 - r2 * N3);
+            i = (int)i32;
+            j = (int)(r2 - i32 * N2);
+        } else {
+            row = c / N4;
+            l = (int)(c - row * N4);
+            const unsigned long long r2 = row / N3;
+            k = (int)(row - r2 * N3);
+            i = (int)(r2 / N2);
+            j = (int)(r2 - (unsigned long long)i * N2);
+        }
         const long long o = (long long)row * g.p4 + l;
 
         const T vc = vin[o];
@@ -87,12 +139,11 @@ __global__ void __launch_bounds__(256) hj_step_generic_kernel(const T *__restric
         const Neigh<T> nt = axis_neighbours<T>(vin, o, l, N4, 1, (g.periodic >> 3) & 1, vc);
 
         const HjCoef<T> cf = coef[k * N4 + l];
-        const T u1 = cf.c1 >= T(0) ? nx.p : nx.m;
-        const T u2 = cf.c2 >= T(0) ? ny.p : ny.m;
+        const T u1 = nonneg(cf.c1) ? nx.p : nx.m;
+        const T u2 = nonneg(cf.c2) ? ny.p : ny.m;
         const T u3 = upwind_value<T>(nv, g.mode3);
         const T u4 = upwind_value<T>(nt, g.mode4);
-        const T K1 = cf.c1 >= T(0) ? cf.c1 : -cf.c1;
-        const T K2 = cf.c2 >= T(0) ? cf.c2 : -cf.c2;
+        const T K1 = fabs(cf.c1), K2 = fabs(cf.c2);  // |.| is an operand modifier, no extra instruction
         T vn;
         if constexpr (sizeof(T) == 8) {
             T r = -cf.ks * vc;
@@ -111,9 +162,19 @@ __global__ void __launch_bounds__(256) hj_step_generic_kernel(const T *__restric
         vout[o] = hj_min(v0[o], vn);  // BRT min with the target (Algorithm 2)
 
         // alpha_d^max: the largest |xdot_d| among the cells this thread updated
-        const unsigned long long b1 = hj_abits((double)cf.a1), b2 = hj_abits((double)cf.a2);
-        am1 = am1 > b1 ? am1 : b1;
-        am2 = am2 > b2 ? am2 : b2;
+        // (FP64: integer max of the bit patterns; FP32: float max, widened once)
+        if constexpr (sizeof(T) == 8) {
+            const unsigned long long b1 = hj_abits((double)cf.a1), b2 = hj_abits((double)cf.a2);
+            am1 = am1 > b1 ? am1 : b1;
+            am2 = am2 > b2 ? am2 : b2;
+        } else {
+            am1f = fmaxf(am1f, (float)cf.a1);
+            am2f = fmaxf(am2f, (float)cf.a2);
+        }
+    }
+    if constexpr (sizeof(T) == 4) {
+        am1 = hj_abits((double)am1f);
+        am2 = hj_abits((double)am2f);
     }
     hj_step_epilogue(st, g, am1, am2, scratch);
 }
@@ -129,11 +190,22 @@ cudaError_t hj_launch_step_generic(hj_grid *g)
     long long cap = (long long)(sms > 0 ? sms : 1) * 8;
     int blocks = (int)(want < cap ? want : cap);
     if (blocks < 1) blocks = 1;
-    if (g->prec == HJ_FP64)
-        hj_step_generic_kernel<double><<<blocks, threads, 0, g->stream>>>(
-            (const double *)g->v0, (double *)g->buf, (const HjCoef<double> *)g->coef, g->dstate, g->geom, g->nint);
-    else
-        hj_step_generic_kernel<float><<<blocks, threads, 0, g->stream>>>(
-            (const float *)g->v0, (float *)g->buf, (const HjCoef<float> *)g->coef, g->dstate, g->geom, g->nint);
+    Divisors dv;
+    dv.n4 = make_fastdiv((uint32_t)g->n[3]);
+    dv.n3 = make_fastdiv((uint32_t)g->n[2]);
+    dv.n2 = make_fastdiv((uint32_t)g->n[1]);
+    const bool fast = g->ncell < (1LL << 32);
+#define HJ_LAUNCH(T, F)                                                                                          \
+    hj_step_generic_kernel<T, F><<<blocks, threads, 0, g->stream>>>((const T *)g->v0, (T *)g->buf,              \
+                                                                    (const HjCoef<T> *)g->coef, g->dstate, g->geom, \
+                                                                    g->nint, dv)
+    if (g->prec == HJ_FP64) {
+        if (fast) HJ_LAUNCH(double, true);
+        else HJ_LAUNCH(double, false);
+    } else {
+        if (fast) HJ_LAUNCH(float, true);
+        else HJ_LAUNCH(float, false);
+    }
+#undef HJ_LAUNCH
     return cudaGetLastError();
 }
