@@ -231,6 +231,96 @@ HJ_API hj_status hj_step_noalloc(const int32_t n[4], const double lo[4], const d
                                  const void *v_in, const void *v0, void *v_out, double dt, void *cuda_stream,
                                  double alpha_max_out[4]);
 
+/* ---- Batches: many independent car grids stepped together ---------------
+ *
+ * A batch holds up to max_slots grids ("slots"), each with its own size,
+ * bounds, control bounds, V0, horizon and time loop (Sec. II-B scheme as
+ * above, FP32, theta periodic, the other axes not).  One batch step runs one
+ * persistent kernel over every slot that has not reached its horizon, each
+ * slot advancing by its own CFL step; hj_batch_advance launches batch steps
+ * as CUDA graphs.  Slots may be added and removed between calls (admission is
+ * by device memory: a slot needs hj_batch_slot_bytes(n) of the batch's
+ * budget). */
+typedef struct hj_batch hj_batch;
+
+typedef struct {
+    int64_t steps;      /* batch steps taken by this call */
+    int64_t launches;   /* step kernels launched */
+    int32_t active;     /* slots with steps left after this call */
+    int32_t finished;   /* slots at their horizon */
+    double device_ms;   /* device time of the call (CUDA events) */
+    int32_t nconsumer;  /* consumer threads per CTA of the batch kernel */
+    int32_t ctas;       /* CTAs per batch step */
+    int32_t items;      /* work items per batch step (all slots) */
+} hj_batch_stats;
+
+typedef struct {
+    int32_t n[4];
+    int64_t steps;      /* steps since the slot's initial value */
+    double t, T;        /* simulated time reached, horizon */
+    double dt_last;     /* size of the slot's last step */
+    int32_t done;       /* reached T (or no horizon set yet) */
+    int32_t has_value;
+    int32_t tile[3];    /* rows along y and v, x planes per work item */
+    size_t device_bytes;
+} hj_batch_slot_info;
+
+/* Create an empty batch on the current device.  memory_budget: bytes the
+ * slots may hold (0: 90% of the free device memory).  cuda_stream: as for
+ * hj_create_grid. */
+HJ_API hj_status hj_batch_create(int32_t max_slots, size_t memory_budget, void *cuda_stream, hj_batch **out);
+
+/* Device bytes a slot of n[0]*n[1]*n[2]*n[3] cells needs (V0, two buffers,
+ * tables). */
+HJ_API size_t hj_batch_slot_bytes(const int32_t n[4]);
+
+/* Add a car grid (x, y, v, theta; bounds as hj_create_grid, theta periodic)
+ * with params = {a_max, w_max}.  *slot receives its index.  HJ_ERR_OOM if no
+ * slot is free or the budget would be exceeded. */
+HJ_API hj_status hj_batch_add(hj_batch *b, const int32_t n[4], const double lo[4], const double hi[4],
+                              const double params[2], int32_t *slot);
+
+/* Free a slot (its device memory returns to the budget). */
+HJ_API hj_status hj_batch_remove(hj_batch *b, int32_t slot);
+
+/* V0 of a slot from a host FP64 array or a device FP32/FP64 array (layout as
+ * hj_set_initial_value); resets the slot's time to 0.  The slot takes no step
+ * until hj_batch_set_horizon. */
+HJ_API hj_status hj_batch_set_initial_value(hj_batch *b, int32_t slot, const double *v0, size_t count);
+HJ_API hj_status hj_batch_set_initial_value_device(hj_batch *b, int32_t slot, const void *v0, hj_precision dtype,
+                                                   size_t count);
+
+/* Horizon T and Courant number of a slot (computes its first dt). */
+HJ_API hj_status hj_batch_set_horizon(hj_batch *b, int32_t slot, double T, double cfl);
+
+/* Take up to max_steps batch steps (each unfinished slot advances one step
+ * per batch step) and return when every slot has reached its horizon or the
+ * step budget is used.  stats may be NULL. */
+HJ_API hj_status hj_batch_advance(hj_batch *b, int64_t max_steps, hj_batch_stats *stats);
+
+/* State of a slot. */
+HJ_API hj_status hj_batch_get_slot_info(const hj_batch *b, int32_t slot, hj_batch_slot_info *info);
+
+/* Current V of a slot into a host FP64 buffer or a device FP32/FP64 buffer
+ * (layout as hj_read_value). */
+HJ_API hj_status hj_batch_read_value(hj_batch *b, int32_t slot, double *out, size_t count);
+HJ_API hj_status hj_batch_read_value_device(hj_batch *b, int32_t slot, void *out_device, hj_precision dtype,
+                                            size_t count);
+
+/* Kernel shape: consumer threads per CTA (0: automatic, else a multiple of 32
+ * in [128, 768]) and x chunks per slot column (0 or 1: whole columns). */
+HJ_API hj_status hj_batch_set_shape(hj_batch *b, int32_t nconsumer, int32_t chunks);
+
+/* Time steps_per_trial batch steps for each candidate kernel shape and keep
+ * the fastest.  Every slot must hold an initial value and have taken no step
+ * (trial steps read V0 and write only the ping-pong buffers; slot states are
+ * put back afterwards).  Outputs may be NULL. */
+HJ_API hj_status hj_batch_autotune(hj_batch *b, int32_t steps_per_trial, int32_t *best_nconsumer, int32_t *best_chunks,
+                                   double *best_ms_per_step);
+
+/* Free the batch and all its slots (NULL is a no-op). */
+HJ_API void hj_batch_destroy(hj_batch *b);
+
 /* Describe the grid (sizes, spacings, time, memory). */
 HJ_API hj_status hj_get_info(const hj_grid *g, hj_grid_info *info);
 

@@ -279,6 +279,37 @@ void free_grid(hj_grid *g)
 
 void hj_internal_set_error(const char *msg) { snprintf(g_err, sizeof(g_err), "%s", msg); }
 
+// Launchers of the ingest, readback and prologue kernels for other parts of
+// the library (the batch API); all return the launch's CUDA error.
+cudaError_t hj_launch_ingest_f32(const void *src, hj_precision src_type, float *dst, int n4, int p4, long long nrows,
+                                 int *nonfinite, cudaStream_t stream)
+{
+    const int blocks = grid_blocks(nrows * p4, 256);
+    if (src_type == HJ_FP64)
+        ingest_kernel<double, float><<<blocks, 256, 0, stream>>>((const double *)src, dst, n4, p4, nrows, nonfinite);
+    else
+        ingest_kernel<float, float><<<blocks, 256, 0, stream>>>((const float *)src, dst, n4, p4, nrows, nonfinite);
+    return cudaGetLastError();
+}
+
+cudaError_t hj_launch_readback_f32(const float *src, void *dst, hj_precision dst_type, int n4, int p4, long long row0,
+                                   long long nrows, cudaStream_t stream)
+{
+    const int blocks = grid_blocks(nrows * n4, 256);
+    if (dst_type == HJ_FP64)
+        readback_kernel<float, double><<<blocks, 256, 0, stream>>>(src, (double *)dst, n4, p4, row0, nrows);
+    else
+        readback_kernel<float, float><<<blocks, 256, 0, stream>>>(src, (float *)dst, n4, p4, row0, nrows);
+    return cudaGetLastError();
+}
+
+cudaError_t hj_launch_prologue_f32(HjDevState *st, const HjGeom &g, const HjCoef<float> *coef, int ncoef, double T,
+                                   double cfl, cudaStream_t stream)
+{
+    prologue_kernel<float><<<1, 256, 0, stream>>>(st, g, coef, ncoef, T, cfl);
+    return cudaGetLastError();
+}
+
 // ==================================================================== C ABI
 
 extern "C" {

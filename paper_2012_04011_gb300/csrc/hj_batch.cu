@@ -1,0 +1,1184 @@
+// Batched solves: many independent 4D car instances (each its own grid
+// size, obstacle map V0, horizon and time loop) stepped together by one
+// persistent kernel per time step, with the time loop captured as a CUDA
+// graph.  Same scheme and same per-cell arithmetic as the single-grid tiled
+// kernel (one step of Algorithm 2 of arxiv 2012.04011 in upwind form, see
+// hj_step_generic.cu and hj_step_tiled.cu).
+//
+// Work: every active slot's grid is cut into items (slot, y-tile, v-tile,
+// x-chunk).  A CTA's producer warp takes the next item from a device-side
+// queue (items are ordered slot by slot, so concurrently running CTAs share
+// neighbouring columns and their halos hit L2), skips items of slots that
+// have reached their horizon, and streams the item's planes (V_n box with a
+// one-cell y/v halo, V0 box without) through the shared-memory ring with
+// TMA, tagging each stage with its item.  Consumers own one (row, theta
+// quad) each, as in the single-grid kernel; the tile shape of each slot is
+// chosen so that its rows x quads fit the block.
+//
+// Time loop: each slot keeps its own FP64 state (t, dt, step count) on the
+// device.  After an item, each consumer warp merges its alpha^max partials
+// into the slot and counts itself done; the warp that completes the slot's
+// last item computes the slot's next CFL step (hj_finalise).  Slots
+// therefore advance independently: a batch step moves every unfinished slot
+// by its own dt, and finished slots cost nothing.
+//
+// Slots can be added and removed between steps (the serving loop admits
+// requests this way); the item list and tensor maps live in device memory,
+// so a captured graph stays valid while the kernel shape (block size, ring
+// stage size) does not change.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "hj_tma.cuh"
+
+namespace {
+
+constexpr int B_MAX_STAGES = 8;
+constexpr int B_VARIANTS[4] = {384, 512, 640, 768};
+
+struct BatchInst {
+    int n1, n2, n3, n4, p4, q4;
+    int ty, tv, xc;
+    int nitems;  // items of this slot per step
+    int halo_box, halo_floats, v0_floats;
+    float k3, k4, mk34;
+    long long nint;
+    float *buf;                 // buffer A, then buffer B (nint floats each)
+    const float *tab;           // v_k [n3], cos/dx1 [p4], sin/dx2 [p4]
+    const HjCoef<float> *coef;  // [n3 * n4]
+    HjGeom geom;
+};
+
+struct BatchSlot {
+    HjDevState st;
+    unsigned int warps_done;  // consumer warps that finished an item of this slot in this step
+    int pad_[3];
+};
+
+struct BatchItem {
+    int slot, y0, v0, x0;
+};
+
+struct BatchCtl {
+    unsigned int head;       // next item to hand out
+    unsigned int ctas_done;  // CTAs of this launch that finished
+    int nitems;
+    int status;
+};
+
+struct BatchParams {
+    int nconsumer;    // consumer threads per CTA (multiple of 32)
+    int stages;       // ring depth
+    int stage_bytes;  // ring stage room (the largest slot's V box + V0 box)
+};
+
+static __device__ __forceinline__ void tensormap_acquire(const CUtensorMap *m)
+{
+    // the maps live in global memory and are rewritten by the host between
+    // launches when slots change
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"((unsigned long long)m) : "memory");
+}
+
+template <int MAXC>
+__global__ void __launch_bounds__(MAXC + 32, 1)
+    hj_batch_step_kernel(const BatchInst *__restrict__ insts, BatchSlot *slots, const BatchItem *__restrict__ items,
+                         BatchCtl *ctl, const CUtensorMap *maps, const BatchParams BP)
+{
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    float *stages = (float *)smem_raw;
+    uint64_t *full = (uint64_t *)(smem_raw + (size_t)BP.stages * BP.stage_bytes);
+    uint64_t *empty = full + B_MAX_STAGES;
+    int *stage_item = (int *)(empty + B_MAX_STAGES);  // item tag of each stage
+    volatile int *abort_flag = stage_item + B_MAX_STAGES;
+    unsigned long long *deadline_p = (unsigned long long *)(stage_item + B_MAX_STAGES + 2);
+
+    const int tid = threadIdx.x;
+    const int nconsumer_warps = BP.nconsumer >> 5;
+    const int nitems = ctl->nitems;
+    if (tid == 0) {
+        for (int s = 0; s < BP.stages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], nconsumer_warps);
+        }
+        *abort_flag = 0;
+        *deadline_p = global_ns() + HJ_WAIT_NS;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+
+    if (tid >= BP.nconsumer) {
+        // ------------------------------------------------------------ producer
+        if (tid == BP.nconsumer) {
+            const unsigned long long deadline = *deadline_p;
+            int slot = 0;
+            uint32_t phase = 0, issued = 0, used_mask = 0, last_phase = 0;
+            bool ok = true;
+            auto next_slot = [&]() -> bool {  // wait until ring slot `slot` is free
+                if (issued >= (uint32_t)BP.stages && !mbar_wait(&empty[slot], phase ^ 1u, deadline)) return false;
+                return *abort_flag == 0;
+            };
+            auto advance = [&]() {
+                used_mask |= 1u << slot;
+                last_phase = (last_phase & ~(1u << slot)) | (phase << slot);
+                ++issued;
+                if (++slot == BP.stages) {
+                    slot = 0;
+                    phase ^= 1u;
+                }
+            };
+            while (ok) {
+                const int item = (int)atomicAdd(&ctl->head, 1u);
+                if (item >= nitems) break;
+                const BatchItem it = items[item];
+                const BatchSlot *sl = &slots[it.slot];
+                if (sl->st.done) continue;
+                const BatchInst &I = insts[it.slot];
+                const long long n = sl->st.n;
+                const CUtensorMap *m_in = &maps[4 * it.slot + (n == 0 ? 0 : 1 + (int)((n - 1) & 1))];
+                const CUtensorMap *m_v0 = &maps[4 * it.slot + 3];
+                tensormap_acquire(m_in);
+                tensormap_acquire(m_v0);
+                const int x1 = min(it.x0 + I.xc, I.n1), pl0 = max(it.x0 - 1, 0), pl1 = min(x1, I.n1 - 1);
+                const uint32_t tx_halo = (uint32_t)(I.halo_box * 4), tx_v0 = (uint32_t)(I.v0_floats * 4);
+                for (int p = pl0; p <= pl1; ++p) {
+                    if (!next_slot()) {
+                        ok = false;
+                        break;
+                    }
+                    const bool interior = p >= it.x0 && p < x1;
+                    float *dst = stages + (size_t)slot * (BP.stage_bytes / 4);
+                    stage_item[slot] = item;
+                    mbar_arrive_expect_tx(&full[slot], tx_halo + (interior ? tx_v0 : 0u));
+                    tma_load_4d(dst, m_in, &full[slot], 0, it.v0 - 1, it.y0 - 1, p);
+                    if (interior) tma_load_4d(dst + I.halo_floats, m_v0, &full[slot], 0, it.v0, it.y0, p);
+                    advance();
+                }
+            }
+            // end of work: a stage tagged -1, completed by a plain arrive; it
+            // is that ring slot's last phase, so the drain below waits for it
+            // (a parity wait only tells the current phase from the one before)
+            if (ok && next_slot()) {
+                stage_item[slot] = -1;
+                mbar_arrive(&full[slot]);
+                advance();
+            } else {
+                ok = false;
+            }
+            if (!ok) {
+                ctl->status = HJ_ERR_TIMEOUT;
+                *abort_flag = 1;
+            }
+            const unsigned long long drain_deadline = global_ns() + HJ_WAIT_NS;
+            for (int s = 0; s < BP.stages; ++s)
+                if (((used_mask >> s) & 1u) && !mbar_wait(&full[s], (last_phase >> s) & 1u, drain_deadline))
+                    ctl->status = HJ_ERR_TIMEOUT;
+        }
+    } else {
+        // ------------------------------------------------------------ consumers
+        const int lane = tid & 31;
+        int wslot = 0, rslot = 0;
+        uint32_t wphase = 0;
+        const int nst = BP.stages;
+        const int sfl = BP.stage_bytes / 4;
+        bool ok = true;
+#define HJ_WAIT_NEXT(slot_out)                                   \
+    do {                                                         \
+        if (!mbar_wait_warp(&full[wslot], wphase, deadline_p)) { \
+            slot_out = -1;                                       \
+        } else {                                                 \
+            slot_out = wslot;                                    \
+            if (++wslot == nst) {                                \
+                wslot = 0;                                       \
+                wphase ^= 1u;                                    \
+            }                                                    \
+        }                                                        \
+    } while (0)
+#define HJ_RELEASE_OLDEST()                            \
+    do {                                               \
+        __syncwarp();                                  \
+        if (lane == 0) mbar_arrive(&empty[rslot]);     \
+        if (++rslot == nst) rslot = 0;                 \
+    } while (0)
+        while (ok) {
+            int s_first;
+            HJ_WAIT_NEXT(s_first);
+            if (s_first < 0) {
+                ok = false;
+                break;
+            }
+            const int item = stage_item[s_first];
+            if (item < 0) break;  // no more work
+            const BatchItem it = items[item];
+            const BatchInst &I = insts[it.slot];
+            BatchSlot *sl = &slots[it.slot];
+            const int N1 = I.n1, N2 = I.n2, N3 = I.n3, N4 = I.n4, P4 = I.p4, q4 = I.q4, tv = I.tv;
+            const int x0 = it.x0, x1 = min(it.x0 + I.xc, N1), pl0 = max(x0 - 1, 0), pl1 = min(x1, N1 - 1);
+            const long long n = sl->st.n;
+            const float dt = (float)sl->st.dt;
+            float *vout = I.buf + (n & 1) * I.nint;
+
+            const int q = tid % q4, r = tid / q4;
+            const int srow = tv + 2;
+            const int jy = r / tv, kv = r - (r / tv) * tv;
+            const bool inrow = r < I.ty * tv;
+            const int y = it.y0 + jy, v = it.v0 + kv;
+            const bool rok = inrow && y < N2 && v < N3;
+            const int rsm = rok ? ((jy + 1) * srow + (kv + 1)) * P4 + 4 * q : (srow + 1) * P4;
+            const int r0sm = I.halo_floats + (rok ? (jy * tv + kv) * P4 + 4 * q : 0);
+            const uint32_t s1 = (uint32_t)N2 * N3 * P4;
+            const uint32_t rbase = rok ? ((uint32_t)y * N3 + v) * P4 + 4 * q : 0u;
+            const uint32_t gmask = (y == 0 ? 1u : 0u) | (y == N2 - 1 ? 2u : 0u) | (v == 0 ? 4u : 0u) |
+                                   (v == N3 - 1 ? 8u : 0u);
+            const int lm = (4 * q - 1 + N4) % N4, lp = (4 * q + 4) % N4, lreal = min(4, N4 - 4 * q);
+            float wx[4], wxm[4], wy[4], wym[4], cs[4];
+            float vk = 0.f;
+            if (rok) {
+                vk = I.tab[v];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const float c = I.tab[N3 + 4 * q + e], s = I.tab[N3 + P4 + 4 * q + e];
+                    wx[e] = fmaxf(c, 0.f);
+                    wxm[e] = fmaxf(-c, 0.f);
+                    wy[e] = fmaxf(s, 0.f);
+                    wym[e] = fmaxf(-s, 0.f);
+                    cs[e] = fabsf(c) + fabsf(s);
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < 4; ++e) wx[e] = wxm[e] = wy[e] = wym[e] = cs[e] = 0.f;
+            }
+
+            int s_x = s_first;
+            if (x0 > pl0) HJ_WAIT_NEXT(s_x);
+            if (s_x < 0) {
+                ok = false;
+                break;
+            }
+            float4 cur = *(const float4 *)(stages + (size_t)s_x * sfl + rsm);
+            int s_prev = x0 > pl0 ? s_first : -1;
+            for (int x = x0; x < x1; ++x) {
+                if (__any_sync(0xffffffffu, *abort_flag != 0)) {
+                    ok = false;
+                    break;
+                }
+                const float *sx = stages + (size_t)s_x * sfl;
+                int s_n = -1;
+                float4 prev, nxt;
+                if (x + 1 <= N1 - 1) {
+                    HJ_WAIT_NEXT(s_n);
+                    if (s_n < 0) {
+                        ok = false;
+                        break;
+                    }
+                    nxt = *(const float4 *)(stages + (size_t)s_n * sfl + rsm);
+                    prev = s_prev >= 0 ? *(const float4 *)(stages + (size_t)s_prev * sfl + rsm) : f4ghost(cur, nxt);
+                } else {
+                    prev = s_prev >= 0 ? *(const float4 *)(stages + (size_t)s_prev * sfl + rsm) : cur;
+                    nxt = f4ghost(cur, prev);
+                }
+                if (rok) {
+                    const float *row = sx + rsm;
+                    float4 ym = *(const float4 *)(row - srow * P4);
+                    float4 yp = *(const float4 *)(row + srow * P4);
+                    float4 vm = *(const float4 *)(row - P4);
+                    float4 vp = *(const float4 *)(row + P4);
+                    if (gmask) {  // extrapolated points past the y / v ends (Sec. II-B)
+                        if (gmask & 1u) ym = f4ghost(cur, yp);
+                        if (gmask & 2u) yp = f4ghost(cur, ym);
+                        if (gmask & 4u) vm = f4ghost(cur, vp);
+                        if (gmask & 8u) vp = f4ghost(cur, vm);
+                    }
+                    const float *row0 = row - 4 * q;
+                    const float tl = row0[lm], tr = row0[lp], t0 = row0[0];
+                    const float4 v0c = *(const float4 *)(sx + r0sm);
+                    float4 out;
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const float vc = f4get(cur, e);
+                        const float tm = e == 0 ? tl : f4get(cur, e - 1);
+                        float tp = e == 3 ? tr : f4get(cur, e + 1);
+                        if (lreal < 4 && e == lreal - 1) tp = t0;  // wrap of a padded last quad
+                        float in = wx[e] * f4get(nxt, e);
+                        in = fmaf(wxm[e], f4get(prev, e), in);
+                        in = fmaf(wy[e], f4get(yp, e), in);
+                        in = fmaf(wym[e], f4get(ym, e), in);
+                        in = fmaf(-cs[e], vc, in);
+                        float acc = fmaf(I.k3, fmaxf(f4get(vp, e), f4get(vm, e)), I.mk34 * vc);
+                        acc = fmaf(I.k4, fmaxf(tp, tm), acc);
+                        acc = fmaf(vk, in, acc);
+                        float vn = fminf(f4get(v0c, e), fmaf(dt, acc, vc));
+                        if (e >= lreal) vn = 0.f;
+                        f4set(out, e, vn);
+                    }
+                    *(float4 *)(vout + (uint32_t)x * s1 + rbase) = out;
+                }
+                if (s_prev >= 0) HJ_RELEASE_OLDEST();
+                s_prev = s_x;
+                s_x = s_n;
+                cur = nxt;
+            }
+            if (!ok) break;
+            HJ_RELEASE_OLDEST();
+            if (x1 <= pl1) HJ_RELEASE_OLDEST();
+
+            // alpha^max partials of this warp for the slot, then count the
+            // warp done; the warp completing the slot's step finalises it
+            float a1 = 0.f, a2 = 0.f;
+            if (rok)
+                for (int e = 0; e < lreal; ++e) {
+                    const HjCoef<float> c = I.coef[v * N4 + 4 * q + e];
+                    a1 = fmaxf(a1, c.a1);
+                    a2 = fmaxf(a2, c.a2);
+                }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                a1 = fmaxf(a1, __shfl_xor_sync(0xffffffffu, a1, o));
+                a2 = fmaxf(a2, __shfl_xor_sync(0xffffffffu, a2, o));
+            }
+            if (lane == 0) {
+                atomicMax(&sl->st.alpha_bits[0], hj_abits((double)a1));
+                atomicMax(&sl->st.alpha_bits[1], hj_abits((double)a2));
+                __threadfence();
+                const unsigned int per_step = (unsigned int)nconsumer_warps * (unsigned int)I.nitems;
+                const unsigned int prev_done = atomicAdd(&sl->warps_done, 1u);
+                if (prev_done + 1 == per_step) {
+                    hj_finalise(&sl->st, I.geom);
+                    sl->warps_done = 0u;
+                    __threadfence();
+                }
+            }
+        }
+#undef HJ_WAIT_NEXT
+#undef HJ_RELEASE_OLDEST
+        if (!ok) {
+            ctl->status = HJ_ERR_TIMEOUT;
+            *abort_flag = 1;
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        __threadfence();
+        const unsigned int prev = atomicAdd(&ctl->ctas_done, 1u);
+        if (prev == gridDim.x - 1) {  // last CTA: rewind the queue for the next launch
+            ctl->head = 0u;
+            ctl->ctas_done = 0u;
+            __threadfence();
+        }
+    }
+}
+
+}  // namespace
+
+// ======================================================================== host
+
+namespace {
+
+typedef CUresult (*BEncodeFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                              const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                              CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+BEncodeFn batch_encode_fn()
+{
+    static BEncodeFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (BEncodeFn)p;
+    }
+    return fn;
+}
+
+typedef void (*BatchKernelFn)(const BatchInst *, BatchSlot *, const BatchItem *, BatchCtl *, const CUtensorMap *,
+                              const BatchParams);
+
+BatchKernelFn batch_kernel(int nconsumer)
+{
+    if (nconsumer <= B_VARIANTS[0]) return hj_batch_step_kernel<B_VARIANTS[0]>;
+    if (nconsumer <= B_VARIANTS[1]) return hj_batch_step_kernel<B_VARIANTS[1]>;
+    if (nconsumer <= B_VARIANTS[2]) return hj_batch_step_kernel<B_VARIANTS[2]>;
+    return hj_batch_step_kernel<B_VARIANTS[3]>;
+}
+
+size_t batch_smem(const BatchParams &bp)
+{
+    return (size_t)bp.stages * bp.stage_bytes + 2 * B_MAX_STAGES * sizeof(uint64_t) + (B_MAX_STAGES + 4) * sizeof(int) +
+           2 * sizeof(unsigned long long) + 32;
+}
+
+struct SlotHost {
+    bool used = false;
+    int n[4] = {0, 0, 0, 0};
+    double lo[4], hi[4], h[4];
+    double a_max = 0, w_max = 0;
+    int p4 = 0;
+    long long nint = 0, ncell = 0;
+    void *mem = nullptr;
+    size_t bytes = 0;
+    float *v0 = nullptr, *buf = nullptr, *tab = nullptr;
+    HjCoef<float> *coef = nullptr;
+    bool has_value = false;
+    double T = 0, cfl = 0.8;
+    int ty = 0, tv = 0, xc = 0;
+    HjGeom geom;
+};
+
+}  // namespace
+
+struct hj_batch {
+    int max_slots = 0;
+    size_t budget = 0, used_bytes = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int device = 0, sms = 0, maxsmem = 0;
+    std::vector<SlotHost> slots;
+    BatchInst *d_insts = nullptr;
+    BatchSlot *d_slots = nullptr;
+    BatchSlot *h_slots = nullptr;  // pinned mirror
+    BatchItem *d_items = nullptr;
+    int items_cap = 0;
+    BatchCtl *d_ctl = nullptr;
+    CUtensorMap *d_maps = nullptr;
+    int nconsumer_req = 0;  // 0: automatic
+    int xc_mode = 0;        // 0: one chunk per column, k > 0: about n1 / k planes per chunk
+    BatchParams bp = {0, 0, 0};
+    int ctas = 0;
+    int nitems = 0;
+    bool dirty = true;
+    std::vector<std::pair<long long, cudaGraphExec_t>> graphs;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+};
+
+namespace {
+
+thread_local char b_err[256];
+
+hj_status bfail(hj_status s, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(b_err, sizeof(b_err), fmt, ap);
+    va_end(ap);
+    hj_internal_set_error(b_err);
+    return s;
+}
+
+#define HJB_CUDA(call)                                                                                   \
+    do {                                                                                                 \
+        cudaError_t e_ = (call);                                                                         \
+        if (e_ != cudaSuccess)                                                                           \
+            return bfail(e_ == cudaErrorMemoryAllocation ? HJ_ERR_OOM : HJ_ERR_CUDA, "%s: %s", #call,      \
+                         cudaGetErrorString(e_));                                                        \
+    } while (0)
+
+void drop_graphs(hj_batch *b)
+{
+    for (auto &kv : b->graphs) cudaGraphExecDestroy(kv.second);
+    b->graphs.clear();
+}
+
+// Tile of one slot for a block of nc consumer threads: the most rows
+// (ty x tv <= nc / q4), fewest halo reads per row.
+void choose_tile(const SlotHost &s, int nc, int *ty_out, int *tv_out)
+{
+    const int q4 = s.p4 / 4, max_rows = nc / q4;
+    int bty = 1, btv = 1;
+    double best = 1e300;
+    for (int ty = 1; ty <= 16 && ty <= s.n[1]; ++ty)
+        for (int tv = 1; tv <= 16 && tv <= s.n[2]; ++tv) {
+            if (ty * tv > max_rows) continue;
+            // cost per useful row: halo rows loaded plus idle threads
+            const double halo = (double)(ty + 2) * (tv + 2) / (ty * tv);
+            const double idle = (double)max_rows / (ty * tv);
+            const double c = halo + 0.5 * idle;
+            if (c < best) {
+                best = c;
+                bty = ty;
+                btv = tv;
+            }
+        }
+    *ty_out = bty;
+    *tv_out = btv;
+}
+
+hj_status upload_slot_tables(hj_batch *b, SlotHost &s)
+{
+    const int N3 = s.n[2], N4 = s.n[3], P4 = s.p4;
+    std::vector<HjCoef<float>> c((size_t)N3 * N4);
+    std::vector<float> tab((size_t)N3 + 2 * P4, 0.f);
+    const double k3 = s.a_max / s.h[2], k4 = s.w_max / s.h[3];
+    for (int k = 0; k < N3; ++k) {
+        const double v = s.lo[2] + (double)k * s.h[2];
+        tab[k] = (float)v;
+        for (int l = 0; l < N4; ++l) {
+            const double th = s.lo[3] + (double)l * s.h[3];
+            const double f1 = v * cos(th), f2 = v * sin(th), c1 = f1 / s.h[0], c2 = f2 / s.h[1];
+            HjCoef<float> &e = c[(size_t)k * N4 + l];
+            e.c1 = (float)c1;
+            e.c2 = (float)c2;
+            e.ks = (float)(fabs(c1) + fabs(c2) + k3 + k4);
+            e.a1 = (float)fabs(f1);
+            e.a2 = (float)fabs(f2);
+        }
+    }
+    for (int l = 0; l < N4; ++l) {
+        const double th = s.lo[3] + (double)l * s.h[3];
+        tab[N3 + l] = (float)(cos(th) / s.h[0]);
+        tab[N3 + P4 + l] = (float)(sin(th) / s.h[1]);
+    }
+    HJB_CUDA(cudaMemcpyAsync(s.coef, c.data(), sizeof(HjCoef<float>) * c.size(), cudaMemcpyHostToDevice, b->stream));
+    HJB_CUDA(cudaMemcpyAsync(s.tab, tab.data(), sizeof(float) * tab.size(), cudaMemcpyHostToDevice, b->stream));
+    HJB_CUDA(cudaStreamSynchronize(b->stream));  // the host vectors go out of scope
+    return HJ_OK;
+}
+
+// Rebuild the per-slot descriptors, tensor maps and item list after slots or
+// the kernel shape changed.
+hj_status rebuild(hj_batch *b)
+{
+    BEncodeFn enc = batch_encode_fn();
+    if (!enc) return bfail(HJ_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+    // block size: the request, else the smallest variant that gives every
+    // slot at least 32 rows
+    int nc = b->nconsumer_req;
+    if (nc <= 0) {
+        nc = B_VARIANTS[0];
+        for (auto &s : b->slots)
+            if (s.used) {
+                const int need = (s.p4 / 4) * 32;
+                while (nc < need && nc < B_VARIANTS[3]) nc += 128;
+            }
+    }
+    std::vector<BatchInst> insts(b->max_slots);
+    std::vector<CUtensorMap> maps((size_t)4 * b->max_slots);
+    memset(insts.data(), 0, sizeof(BatchInst) * insts.size());
+    memset(maps.data(), 0, sizeof(CUtensorMap) * maps.size());
+    std::vector<BatchItem> items;
+    int stage_bytes = 128;
+    int max_cons = 32;
+    for (int i = 0; i < b->max_slots; ++i) {
+        SlotHost &s = b->slots[i];
+        if (!s.used) continue;
+        choose_tile(s, nc, &s.ty, &s.tv);
+        const int nchunk = b->xc_mode > 0 ? b->xc_mode : 1;
+        s.xc = (s.n[0] + nchunk - 1) / nchunk;
+        if (s.xc < 4) s.xc = s.n[0] < 4 ? s.n[0] : 4;
+        BatchInst &I = insts[i];
+        I.n1 = s.n[0];
+        I.n2 = s.n[1];
+        I.n3 = s.n[2];
+        I.n4 = s.n[3];
+        I.p4 = s.p4;
+        I.q4 = s.p4 / 4;
+        I.ty = s.ty;
+        I.tv = s.tv;
+        I.xc = s.xc;
+        I.halo_box = s.p4 * (s.tv + 2) * (s.ty + 2);
+        I.halo_floats = (I.halo_box + 31) / 32 * 32;
+        I.v0_floats = s.p4 * s.ty * s.tv;
+        I.k3 = (float)(s.a_max / s.h[2]);
+        I.k4 = (float)(s.w_max / s.h[3]);
+        I.mk34 = (float)(-(s.a_max / s.h[2] + s.w_max / s.h[3]));
+        I.nint = s.nint;
+        I.buf = s.buf;
+        I.tab = s.tab;
+        I.coef = s.coef;
+        I.geom = s.geom;
+        const int ncv = (s.n[2] + s.tv - 1) / s.tv, ncy = (s.n[1] + s.ty - 1) / s.ty;
+        const int nch = (s.n[0] + s.xc - 1) / s.xc;
+        I.nitems = ncv * ncy * nch;
+        for (int c = 0; c < nch; ++c)
+            for (int yt = 0; yt < ncy; ++yt)
+                for (int vt = 0; vt < ncv; ++vt) items.push_back({i, yt * s.ty, vt * s.tv, c * s.xc});
+        const int sb = ((I.halo_floats + I.v0_floats) * 4 + 127) / 128 * 128;
+        if (sb > stage_bytes) stage_bytes = sb;
+        const int cons = ((I.q4 * s.ty * s.tv) + 31) / 32 * 32;
+        if (cons > max_cons) max_cons = cons;
+        // tensor maps: V0 / A / B with the halo box, V0 with the tile box
+        cuuint64_t dims[4] = {(cuuint64_t)s.p4, (cuuint64_t)s.n[2], (cuuint64_t)s.n[1], (cuuint64_t)s.n[0]};
+        cuuint64_t strides[3] = {(cuuint64_t)s.p4 * 4, (cuuint64_t)s.p4 * s.n[2] * 4,
+                                 (cuuint64_t)s.p4 * s.n[2] * s.n[1] * 4};
+        cuuint32_t box_halo[4] = {(cuuint32_t)s.p4, (cuuint32_t)(s.tv + 2), (cuuint32_t)(s.ty + 2), 1};
+        cuuint32_t box_tile[4] = {(cuuint32_t)s.p4, (cuuint32_t)s.tv, (cuuint32_t)s.ty, 1};
+        cuuint32_t estr[4] = {1, 1, 1, 1};
+        void *bases[4] = {s.v0, s.buf, s.buf + s.nint, s.v0};
+        for (int m = 0; m < 4; ++m) {
+            CUresult r = enc(&maps[4 * i + m], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, bases[m], dims, strides,
+                             m < 3 ? box_halo : box_tile, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r != CUDA_SUCCESS) return bfail(HJ_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d) for slot %d", (int)r, i);
+        }
+    }
+    BatchParams bp;
+    bp.nconsumer = max_cons;
+    bp.stage_bytes = stage_bytes;
+    bp.stages = (int)((b->maxsmem - 4096) / stage_bytes);
+    if (bp.stages > B_MAX_STAGES) bp.stages = B_MAX_STAGES;
+    if (bp.stages < 4) return bfail(HJ_ERR_UNSUPPORTED, "a slot's tile does not fit four ring stages");
+    // device copies
+    if ((int)items.size() > b->items_cap) {
+        if (b->d_items) cudaFree(b->d_items);
+        b->d_items = nullptr;
+        b->items_cap = 0;
+        const int cap = (int)items.size() * 2 + 64;
+        HJB_CUDA(cudaMalloc(&b->d_items, sizeof(BatchItem) * cap));
+        b->items_cap = cap;
+        drop_graphs(b);  // the kernel's item pointer changed
+    }
+    HJB_CUDA(cudaStreamSynchronize(b->stream));
+    if (!items.empty())
+        HJB_CUDA(cudaMemcpy(b->d_items, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice));
+    HJB_CUDA(cudaMemcpy(b->d_insts, insts.data(), sizeof(BatchInst) * insts.size(), cudaMemcpyHostToDevice));
+    HJB_CUDA(cudaMemcpy(b->d_maps, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice));
+    BatchCtl ctl = {0u, 0u, (int)items.size(), HJ_OK};
+    HJB_CUDA(cudaMemcpy(b->d_ctl, &ctl, sizeof(ctl), cudaMemcpyHostToDevice));
+    b->nitems = (int)items.size();
+    if (bp.nconsumer != b->bp.nconsumer || bp.stages != b->bp.stages || bp.stage_bytes != b->bp.stage_bytes) {
+        drop_graphs(b);
+        b->bp = bp;
+        BatchKernelFn fn = batch_kernel(bp.nconsumer);
+        const size_t smem = batch_smem(bp);
+        HJB_CUDA(cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int per_sm = 0;
+        HJB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)fn, bp.nconsumer + 32, smem));
+        if (per_sm < 1) return bfail(HJ_ERR_UNSUPPORTED, "batch kernel shape does not fit on an SM");
+        b->ctas = b->sms * per_sm;
+    }
+    b->dirty = false;
+    return HJ_OK;
+}
+
+hj_status launch_batch_step(hj_batch *b)
+{
+    BatchKernelFn fn = batch_kernel(b->bp.nconsumer);
+    fn<<<b->ctas, b->bp.nconsumer + 32, batch_smem(b->bp), b->stream>>>(b->d_insts, b->d_slots, b->d_items, b->d_ctl,
+                                                                        b->d_maps, b->bp);
+    HJB_CUDA(cudaGetLastError());
+    return HJ_OK;
+}
+
+// k batch steps as one CUDA graph launch (graphs cached by k)
+hj_status launch_steps(hj_batch *b, long long k)
+{
+    if (k <= 0) return HJ_OK;
+    cudaGraphExec_t exec = nullptr;
+    for (auto &kv : b->graphs)
+        if (kv.first == k) exec = kv.second;
+    if (!exec) {
+        cudaGraph_t graph = nullptr;
+        HJB_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+        hj_status s = HJ_OK;
+        for (long long i = 0; i < k && s == HJ_OK; ++i) s = launch_batch_step(b);
+        cudaError_t e = cudaStreamEndCapture(b->stream, &graph);
+        if (s != HJ_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return s;
+        }
+        if (e != cudaSuccess) return bfail(HJ_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return bfail(HJ_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+        if (b->graphs.size() >= 16) {
+            cudaGraphExecDestroy(b->graphs.front().second);
+            b->graphs.erase(b->graphs.begin());
+        }
+        b->graphs.push_back({k, exec});
+    }
+    HJB_CUDA(cudaGraphLaunch(exec, b->stream));
+    return HJ_OK;
+}
+
+hj_status pull_slots(hj_batch *b)
+{
+    HJB_CUDA(cudaMemcpyAsync(b->h_slots, b->d_slots, sizeof(BatchSlot) * b->max_slots, cudaMemcpyDeviceToHost,
+                             b->stream));
+    HJB_CUDA(cudaStreamSynchronize(b->stream));
+    return HJ_OK;
+}
+
+hj_status push_slot(hj_batch *b, int i)
+{
+    HJB_CUDA(cudaMemcpyAsync(&b->d_slots[i], &b->h_slots[i], sizeof(BatchSlot), cudaMemcpyHostToDevice, b->stream));
+    HJB_CUDA(cudaStreamSynchronize(b->stream));
+    return HJ_OK;
+}
+
+hj_status check_slot(const hj_batch *b, int slot)
+{
+    if (!b) return bfail(HJ_ERR_INVALID_ARG, "batch is NULL");
+    if (slot < 0 || slot >= b->max_slots || !b->slots[slot].used)
+        return bfail(HJ_ERR_INVALID_ARG, "slot %d is not in use", slot);
+    return HJ_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+hj_status hj_batch_create(int32_t max_slots, size_t memory_budget, void *cuda_stream, hj_batch **out)
+{
+    hj_internal_set_error("");
+    if (!out) return bfail(HJ_ERR_INVALID_ARG, "out is NULL");
+    if (max_slots < 1 || max_slots > 4096) return bfail(HJ_ERR_INVALID_ARG, "max_slots must be in [1, 4096]");
+    hj_batch *b = new (std::nothrow) hj_batch();
+    if (!b) return bfail(HJ_ERR_OOM, "host allocation failed");
+    b->max_slots = max_slots;
+    b->slots.resize(max_slots);
+    cudaError_t e = cudaGetDevice(&b->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->maxsmem, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device);
+    size_t free_b = 0, total_b = 0;
+    if (e == cudaSuccess) e = cudaMemGetInfo(&free_b, &total_b);
+    b->budget = memory_budget > 0 ? memory_budget : (size_t)(0.9 * (double)free_b);
+    if (e == cudaSuccess && cuda_stream) {
+        b->stream = (cudaStream_t)cuda_stream;
+    } else if (e == cudaSuccess) {
+        e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+        b->own_stream = e == cudaSuccess;
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_insts, sizeof(BatchInst) * max_slots);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_slots, sizeof(BatchSlot) * max_slots);
+    if (e == cudaSuccess) e = cudaHostAlloc(&b->h_slots, sizeof(BatchSlot) * max_slots, cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_ctl, sizeof(BatchCtl));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_maps, sizeof(CUtensorMap) * 4 * max_slots);
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaEventCreate(&b->ev[i]);
+    if (e == cudaSuccess) {
+        memset(b->h_slots, 0, sizeof(BatchSlot) * max_slots);
+        for (int i = 0; i < max_slots; ++i) b->h_slots[i].st.done = 1;
+        e = cudaMemcpy(b->d_slots, b->h_slots, sizeof(BatchSlot) * max_slots, cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess) e = cudaMemset(b->d_insts, 0, sizeof(BatchInst) * max_slots);
+    if (e == cudaSuccess) e = cudaMemset(b->d_ctl, 0, sizeof(BatchCtl));
+    if (e != cudaSuccess) {
+        hj_status s = bfail(e == cudaErrorMemoryAllocation ? HJ_ERR_OOM : HJ_ERR_CUDA, "hj_batch_create: %s",
+                            cudaGetErrorString(e));
+        hj_batch_destroy(b);
+        return s;
+    }
+    *out = b;
+    return HJ_OK;
+}
+
+void hj_batch_destroy(hj_batch *b)
+{
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    drop_graphs(b);
+    for (auto &s : b->slots)
+        if (s.mem) cudaFree(s.mem);
+    if (b->d_insts) cudaFree(b->d_insts);
+    if (b->d_slots) cudaFree(b->d_slots);
+    if (b->h_slots) cudaFreeHost(b->h_slots);
+    if (b->d_items) cudaFree(b->d_items);
+    if (b->d_ctl) cudaFree(b->d_ctl);
+    if (b->d_maps) cudaFree(b->d_maps);
+    for (int i = 0; i < 2; ++i)
+        if (b->ev[i]) cudaEventDestroy(b->ev[i]);
+    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
+
+// Device memory of one slot: V0, buffers A|B (contiguous), coefficient
+// table, tiled tables; each section 256-byte aligned.
+static void slot_layout(const int32_t n[4], size_t *v0_b, size_t *ab_b, size_t *coef_b, size_t *tab_b)
+{
+    const long long p4 = (n[3] + 3) / 4 * 4;
+    const long long nint = (long long)n[0] * n[1] * n[2] * p4;
+    *v0_b = ((size_t)nint * 4 + 255) / 256 * 256;
+    *ab_b = ((size_t)nint * 8 + 255) / 256 * 256;
+    *coef_b = ((size_t)n[2] * n[3] * sizeof(HjCoef<float>) + 255) / 256 * 256;
+    *tab_b = (((size_t)n[2] + 2 * (size_t)p4) * 4 + 255) / 256 * 256;
+}
+
+size_t hj_batch_slot_bytes(const int32_t n[4])
+{
+    if (!n) return 0;
+    for (int d = 0; d < 4; ++d)
+        if (n[d] < 1) return 0;
+    size_t a, b2, c, t;
+    slot_layout(n, &a, &b2, &c, &t);
+    return a + b2 + c + t;
+}
+
+hj_status hj_batch_add(hj_batch *b, const int32_t n[4], const double lo[4], const double hi[4], const double params[2],
+                       int32_t *slot_out)
+{
+    hj_internal_set_error("");
+    if (!b || !n || !lo || !hi || !params || !slot_out) return bfail(HJ_ERR_INVALID_ARG, "NULL argument");
+    for (int d = 0; d < 4; ++d) {
+        if (n[d] < 3) return bfail(HJ_ERR_INVALID_ARG, "N%d = %d < 3", d + 1, n[d]);
+        if (!isfinite(lo[d]) || !isfinite(hi[d]) || !(hi[d] > lo[d]))
+            return bfail(HJ_ERR_INVALID_ARG, "axis %d bounds must be finite with hi > lo", d + 1);
+    }
+    if (!isfinite(params[0]) || !isfinite(params[1]) || params[0] < 0 || params[1] < 0)
+        return bfail(HJ_ERR_INVALID_ARG, "a_max and w_max must be finite and >= 0");
+    const int p4 = (n[3] + 3) / 4 * 4;
+    if (p4 > 256) return bfail(HJ_ERR_UNSUPPORTED, "theta rows longer than 256 points");
+    if ((p4 / 4) > B_VARIANTS[3]) return bfail(HJ_ERR_UNSUPPORTED, "theta rows too long");
+    const long long nint = (long long)n[0] * n[1] * n[2] * p4;
+    if (nint >= (1LL << 31)) return bfail(HJ_ERR_UNSUPPORTED, "grid too large for a batch slot");
+    int slot = -1;
+    for (int i = 0; i < b->max_slots; ++i)
+        if (!b->slots[i].used) {
+            slot = i;
+            break;
+        }
+    if (slot < 0) return bfail(HJ_ERR_OOM, "all %d slots are in use", b->max_slots);
+    const size_t bytes = hj_batch_slot_bytes(n);
+    if (b->used_bytes + bytes > b->budget)
+        return bfail(HJ_ERR_OOM, "slot needs %zu bytes; %zu of the %zu-byte budget are in use", bytes, b->used_bytes,
+                     b->budget);
+    int cur = -1;
+    HJB_CUDA(cudaGetDevice(&cur));
+    if (cur != b->device) HJB_CUDA(cudaSetDevice(b->device));
+    SlotHost s;
+    s.used = true;
+    for (int d = 0; d < 4; ++d) {
+        s.n[d] = n[d];
+        s.lo[d] = lo[d];
+        s.hi[d] = hi[d];
+        s.h[d] = (hi[d] - lo[d]) / (double)(d == 3 ? n[d] : n[d] - 1);  // theta periodic, the rest not
+    }
+    s.a_max = params[0];
+    s.w_max = params[1];
+    s.p4 = p4;
+    s.nint = nint;
+    s.ncell = (long long)n[0] * n[1] * n[2] * n[3];
+    HJB_CUDA(cudaMalloc(&s.mem, bytes));
+    s.bytes = bytes;
+    size_t sz_v0, sz_ab, sz_coef, sz_tab;
+    slot_layout(n, &sz_v0, &sz_ab, &sz_coef, &sz_tab);
+    char *m = (char *)s.mem;
+    s.v0 = (float *)m;
+    s.buf = (float *)(m + sz_v0);  // A, then B at buf + nint
+    s.coef = (HjCoef<float> *)(m + sz_v0 + sz_ab);
+    s.tab = (float *)(m + sz_v0 + sz_ab + sz_coef);
+    memset(&s.geom, 0, sizeof(s.geom));
+    s.geom.n1 = n[0];
+    s.geom.n2 = n[1];
+    s.geom.n3 = n[2];
+    s.geom.n4 = n[3];
+    s.geom.p4 = p4;
+    s.geom.periodic = 0x8;
+    s.geom.mode3 = s.geom.mode4 = HJ_AXIS_CONTROL;
+    for (int d = 0; d < 4; ++d) s.geom.h[d] = s.h[d];
+    s.geom.alpha3 = s.a_max;
+    s.geom.alpha4 = s.w_max;
+    s.geom.k3 = s.a_max / s.h[2];
+    s.geom.k4 = s.w_max / s.h[3];
+    b->slots[slot] = s;
+    hj_status st = upload_slot_tables(b, b->slots[slot]);
+    if (st != HJ_OK) {
+        cudaFree(s.mem);
+        b->slots[slot] = SlotHost();
+        return st;
+    }
+    b->used_bytes += bytes;
+    memset(&b->h_slots[slot], 0, sizeof(BatchSlot));
+    b->h_slots[slot].st.done = 1;  // no horizon yet
+    if ((st = push_slot(b, slot)) != HJ_OK) return st;
+    b->dirty = true;
+    *slot_out = slot;
+    return HJ_OK;
+}
+
+hj_status hj_batch_remove(hj_batch *b, int32_t slot)
+{
+    hj_internal_set_error("");
+    hj_status s = check_slot(b, slot);
+    if (s != HJ_OK) return s;
+    HJB_CUDA(cudaStreamSynchronize(b->stream));
+    memset(&b->h_slots[slot], 0, sizeof(BatchSlot));
+    b->h_slots[slot].st.done = 1;
+    if ((s = push_slot(b, slot)) != HJ_OK) return s;
+    cudaFree(b->slots[slot].mem);
+    b->used_bytes -= b->slots[slot].bytes;
+    b->slots[slot] = SlotHost();
+    b->dirty = true;
+    return HJ_OK;
+}
+
+static hj_status batch_ingest(hj_batch *b, int32_t slot, const void *src, hj_precision type, bool on_host,
+                              size_t count)
+{
+    hj_status s = check_slot(b, slot);
+    if (s != HJ_OK) return s;
+    SlotHost &sl = b->slots[slot];
+    if (!src) return bfail(HJ_ERR_INVALID_ARG, "v0 is NULL");
+    if (count != (size_t)sl.ncell) return bfail(HJ_ERR_INVALID_ARG, "count %zu != %lld", count, sl.ncell);
+    HJB_CUDA(cudaStreamSynchronize(b->stream));
+    memset(&b->h_slots[slot], 0, sizeof(BatchSlot));
+    b->h_slots[slot].st.done = 1;  // until a horizon is set
+    b->h_slots[slot].st.status = HJ_OK;
+    if ((s = push_slot(b, slot)) != HJ_OK) return s;
+    const void *dsrc = src;
+    if (on_host) {  // stage the FP64 array in the slot's A|B region (2 nint floats >= ncell doubles)
+        HJB_CUDA(cudaMemcpyAsync(sl.buf, src, sizeof(double) * (size_t)sl.ncell, cudaMemcpyHostToDevice, b->stream));
+        dsrc = sl.buf;
+    }
+    int *flag = &b->d_slots[slot].st.nonfinite;
+    HJB_CUDA(hj_launch_ingest_f32(dsrc, type, sl.v0, sl.n[3], sl.p4, (long long)sl.n[0] * sl.n[1] * sl.n[2], flag,
+                                  b->stream));
+    if ((s = pull_slots(b)) != HJ_OK) return s;
+    if (b->h_slots[slot].st.nonfinite) {
+        sl.has_value = false;
+        return bfail(HJ_ERR_INVALID_ARG, "V0 contains NaN or Inf");
+    }
+    sl.has_value = true;
+    return HJ_OK;
+}
+
+hj_status hj_batch_set_initial_value(hj_batch *b, int32_t slot, const double *v0, size_t count)
+{
+    hj_internal_set_error("");
+    return batch_ingest(b, slot, v0, HJ_FP64, true, count);
+}
+
+hj_status hj_batch_set_initial_value_device(hj_batch *b, int32_t slot, const void *v0, hj_precision dtype,
+                                            size_t count)
+{
+    hj_internal_set_error("");
+    if (dtype != HJ_FP64 && dtype != HJ_FP32) return bfail(HJ_ERR_INVALID_ARG, "unknown dtype");
+    return batch_ingest(b, slot, v0, dtype, false, count);
+}
+
+hj_status hj_batch_set_horizon(hj_batch *b, int32_t slot, double T, double cfl)
+{
+    hj_internal_set_error("");
+    hj_status s = check_slot(b, slot);
+    if (s != HJ_OK) return s;
+    if (!isfinite(T) || T < 0) return bfail(HJ_ERR_INVALID_ARG, "T must be finite and >= 0");
+    if (!isfinite(cfl) || !(cfl > 0) || cfl > 1) return bfail(HJ_ERR_INVALID_ARG, "cfl must be in (0, 1]");
+    SlotHost &sl = b->slots[slot];
+    if (!sl.has_value) return bfail(HJ_ERR_STATE, "slot %d has no initial value", slot);
+    sl.T = T;
+    sl.cfl = cfl;
+    HJB_CUDA(hj_launch_prologue_f32(&b->d_slots[slot].st, sl.geom, sl.coef, sl.n[2] * sl.n[3], T, cfl, b->stream));
+    HJB_CUDA(cudaStreamSynchronize(b->stream));
+    return HJ_OK;
+}
+
+hj_status hj_batch_advance(hj_batch *b, int64_t max_steps, hj_batch_stats *stats)
+{
+    hj_internal_set_error("");
+    if (!b) return bfail(HJ_ERR_INVALID_ARG, "batch is NULL");
+    if (max_steps < 0) return bfail(HJ_ERR_INVALID_ARG, "max_steps must be >= 0");
+    hj_status s;
+    if (b->dirty && (s = rebuild(b)) != HJ_OK) return s;
+    long long taken = 0, launches = 0;
+    bool started = false;
+    if ((s = pull_slots(b)) != HJ_OK) return s;
+    HJB_CUDA(cudaEventRecord(b->ev[0], b->stream));
+    while (taken < max_steps && b->nitems > 0) {
+        // batch steps until the slowest unfinished slot reaches its horizon
+        long long k = 0;
+        for (int i = 0; i < b->max_slots; ++i) {
+            if (!b->slots[i].used) continue;
+            const HjDevState &h = b->h_slots[i].st;
+            if (h.done || h.status != HJ_OK) continue;
+            long long ki = 1;
+            if (!h.last && h.dt > 0) {
+                const double r = ceil((h.T - h.t) / h.dt);
+                ki = r > 1 ? (r < 1e9 ? (long long)r : 1000000000LL) : 1;
+            }
+            if (ki > k) k = ki;
+        }
+        if (k == 0) break;
+        if (k > max_steps - taken) k = max_steps - taken;
+        if ((s = launch_steps(b, k)) != HJ_OK) return s;
+        started = true;
+        launches += k;
+        taken += k;
+        if ((s = pull_slots(b)) != HJ_OK) return s;
+        BatchCtl ctl;
+        HJB_CUDA(cudaMemcpy(&ctl, b->d_ctl, sizeof(ctl), cudaMemcpyDeviceToHost));
+        if (ctl.status != HJ_OK)
+            return bfail((hj_status)ctl.status, "device reported %s", hj_status_string((hj_status)ctl.status));
+    }
+    HJB_CUDA(cudaEventRecord(b->ev[1], b->stream));
+    HJB_CUDA(cudaEventSynchronize(b->ev[1]));
+    int active = 0, finished = 0;
+    for (int i = 0; i < b->max_slots; ++i) {
+        if (!b->slots[i].used) continue;
+        const HjDevState &h = b->h_slots[i].st;
+        if (h.status != HJ_OK)
+            return bfail((hj_status)h.status, "slot %d: device reported %s", i, hj_status_string((hj_status)h.status));
+        if (!h.done) ++active;
+        else if (b->slots[i].has_value && b->slots[i].T > 0 && h.t >= b->slots[i].T) ++finished;
+    }
+    if (stats) {
+        memset(stats, 0, sizeof(*stats));
+        stats->steps = taken;
+        stats->launches = launches;
+        stats->active = active;
+        stats->finished = finished;
+        float ms = 0.f;
+        if (started) cudaEventElapsedTime(&ms, b->ev[0], b->ev[1]);
+        stats->device_ms = ms;
+        stats->nconsumer = b->bp.nconsumer;
+        stats->ctas = b->ctas;
+        stats->items = b->nitems;
+    }
+    return HJ_OK;
+}
+
+hj_status hj_batch_get_slot_info(const hj_batch *bc, int32_t slot, hj_batch_slot_info *info)
+{
+    hj_internal_set_error("");
+    hj_batch *b = (hj_batch *)bc;
+    hj_status s = check_slot(b, slot);
+    if (s != HJ_OK) return s;
+    if (!info) return bfail(HJ_ERR_INVALID_ARG, "info is NULL");
+    if ((s = pull_slots(b)) != HJ_OK) return s;
+    const SlotHost &sl = b->slots[slot];
+    const HjDevState &h = b->h_slots[slot].st;
+    memset(info, 0, sizeof(*info));
+    for (int d = 0; d < 4; ++d) info->n[d] = sl.n[d];
+    info->steps = h.n;
+    info->t = h.t;
+    info->T = sl.T;
+    info->dt_last = h.dt_prev;
+    info->done = h.done;
+    info->has_value = sl.has_value;
+    info->tile[0] = sl.ty;
+    info->tile[1] = sl.tv;
+    info->tile[2] = sl.xc;
+    info->device_bytes = sl.bytes;
+    return HJ_OK;
+}
+
+static hj_status batch_read(hj_batch *b, int32_t slot, void *out, hj_precision dtype, bool to_host, size_t count)
+{
+    hj_status s = check_slot(b, slot);
+    if (s != HJ_OK) return s;
+    const SlotHost &sl = b->slots[slot];
+    if (!out) return bfail(HJ_ERR_INVALID_ARG, "out is NULL");
+    if (count != (size_t)sl.ncell) return bfail(HJ_ERR_INVALID_ARG, "count %zu != %lld", count, sl.ncell);
+    if (!sl.has_value) return bfail(HJ_ERR_STATE, "slot %d has no initial value", slot);
+    if ((s = pull_slots(b)) != HJ_OK) return s;
+    const long long n = b->h_slots[slot].st.n;
+    const float *src = n == 0 ? sl.v0 : sl.buf + ((n - 1) & 1) * sl.nint;
+    const long long nrows = (long long)sl.n[0] * sl.n[1] * sl.n[2];
+    if (!to_host) {
+        HJB_CUDA(hj_launch_readback_f32(src, out, dtype, sl.n[3], sl.p4, 0, nrows, b->stream));
+        HJB_CUDA(cudaStreamSynchronize(b->stream));
+        return HJ_OK;
+    }
+    // convert into the free buffer in chunks of rows, copy each out
+    float *freebuf = n == 0 ? sl.buf : sl.buf + (n & 1) * sl.nint;
+    const size_t free_bytes = (n == 0 ? 2 : 1) * (size_t)sl.nint * 4;
+    const long long per = (long long)(free_bytes / (sizeof(double) * (size_t)sl.n[3]));
+    for (long long r0 = 0; r0 < nrows; r0 += per) {
+        const long long nr = nrows - r0 < per ? nrows - r0 : per;
+        HJB_CUDA(hj_launch_readback_f32(src, freebuf, HJ_FP64, sl.n[3], sl.p4, r0, nr, b->stream));
+        HJB_CUDA(cudaMemcpyAsync((double *)out + r0 * sl.n[3], freebuf, sizeof(double) * (size_t)(nr * sl.n[3]),
+                                 cudaMemcpyDeviceToHost, b->stream));
+    }
+    HJB_CUDA(cudaStreamSynchronize(b->stream));
+    return HJ_OK;
+}
+
+hj_status hj_batch_read_value(hj_batch *b, int32_t slot, double *out, size_t count)
+{
+    hj_internal_set_error("");
+    return batch_read(b, slot, out, HJ_FP64, true, count);
+}
+
+hj_status hj_batch_read_value_device(hj_batch *b, int32_t slot, void *out_device, hj_precision dtype, size_t count)
+{
+    hj_internal_set_error("");
+    if (dtype != HJ_FP64 && dtype != HJ_FP32) return bfail(HJ_ERR_INVALID_ARG, "unknown dtype");
+    return batch_read(b, slot, out_device, dtype, false, count);
+}
+
+hj_status hj_batch_set_shape(hj_batch *b, int32_t nconsumer, int32_t chunks)
+{
+    hj_internal_set_error("");
+    if (!b) return bfail(HJ_ERR_INVALID_ARG, "batch is NULL");
+    if (nconsumer != 0 && (nconsumer < 128 || nconsumer > B_VARIANTS[3] || nconsumer % 32 != 0))
+        return bfail(HJ_ERR_INVALID_ARG, "nconsumer must be 0 or a multiple of 32 in [128, %d]", B_VARIANTS[3]);
+    if (chunks < 0 || chunks > 64) return bfail(HJ_ERR_INVALID_ARG, "chunks must be in [0, 64]");
+    HJB_CUDA(cudaStreamSynchronize(b->stream));
+    b->nconsumer_req = nconsumer;
+    b->xc_mode = chunks;
+    b->dirty = true;
+    return HJ_OK;
+}
+
+hj_status hj_batch_autotune(hj_batch *b, int32_t steps_per_trial, int32_t *best_nconsumer, int32_t *best_chunks,
+                            double *best_ms_per_step)
+{
+    hj_internal_set_error("");
+    if (!b) return bfail(HJ_ERR_INVALID_ARG, "batch is NULL");
+    if (steps_per_trial < 1) return bfail(HJ_ERR_INVALID_ARG, "steps_per_trial must be >= 1");
+    hj_status s;
+    if ((s = pull_slots(b)) != HJ_OK) return s;
+    for (int i = 0; i < b->max_slots; ++i)
+        if (b->slots[i].used && (b->h_slots[i].st.n != 0 || !b->slots[i].has_value))
+            return bfail(HJ_ERR_STATE, "autotune needs every slot right after its initial value (slot %d)", i);
+    std::vector<BatchSlot> saved(b->h_slots, b->h_slots + b->max_slots);
+    const int keep_nc = b->nconsumer_req, keep_ch = b->xc_mode;
+    double best = 1e300;
+    int best_nc = keep_nc, best_ch = keep_ch;
+    const int ncs[4] = {384, 512, 640, 768};
+    const int chs[3] = {1, 2, 4};
+    for (int a = 0; a < 4; ++a)
+        for (int c = 0; c < 3; ++c) {
+            b->nconsumer_req = ncs[a];
+            b->xc_mode = chs[c];
+            b->dirty = true;
+            if ((s = rebuild(b)) != HJ_OK) {
+                if (s == HJ_ERR_UNSUPPORTED) continue;
+                break;
+            }
+            // trial: every slot from its initial value with an unreachable horizon
+            for (int i = 0; i < b->max_slots; ++i)
+                if (b->slots[i].used)
+                    hj_launch_prologue_f32(&b->d_slots[i].st, b->slots[i].geom, b->slots[i].coef,
+                                           b->slots[i].n[2] * b->slots[i].n[3], 1e300, 0.8, b->stream);
+            if ((s = launch_steps(b, 2)) != HJ_OK) break;
+            cudaEventRecord(b->ev[0], b->stream);
+            if ((s = launch_steps(b, steps_per_trial)) != HJ_OK) break;
+            cudaEventRecord(b->ev[1], b->stream);
+            cudaEventSynchronize(b->ev[1]);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, b->ev[0], b->ev[1]);
+            const double per = ms / steps_per_trial;
+            if (per < best) {
+                best = per;
+                best_nc = ncs[a];
+                best_ch = chs[c];
+            }
+            // put the states back
+            memcpy(b->h_slots, saved.data(), sizeof(BatchSlot) * b->max_slots);
+            HJB_CUDA(cudaMemcpyAsync(b->d_slots, b->h_slots, sizeof(BatchSlot) * b->max_slots, cudaMemcpyHostToDevice,
+                                     b->stream));
+            HJB_CUDA(cudaStreamSynchronize(b->stream));
+        }
+    memcpy(b->h_slots, saved.data(), sizeof(BatchSlot) * b->max_slots);
+    cudaMemcpyAsync(b->d_slots, b->h_slots, sizeof(BatchSlot) * b->max_slots, cudaMemcpyHostToDevice, b->stream);
+    cudaStreamSynchronize(b->stream);
+    b->nconsumer_req = best < 1e300 ? best_nc : keep_nc;
+    b->xc_mode = best < 1e300 ? best_ch : keep_ch;
+    b->dirty = true;
+    hj_status r = rebuild(b);
+    if (s == HJ_OK) s = r;
+    if (best_nconsumer) *best_nconsumer = b->nconsumer_req;
+    if (best_chunks) *best_chunks = b->xc_mode;
+    if (best_ms_per_step) *best_ms_per_step = best < 1e300 ? best : 0.0;
+    return s;
+}
+
+}  // extern "C"

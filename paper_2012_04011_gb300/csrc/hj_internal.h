@@ -103,6 +103,16 @@ int hj_tiled_threads(const hj_grid *g, int ty, int tv);
 // Sets the message hj_last_error() returns on this host thread.
 void hj_internal_set_error(const char *msg);
 
+// Ingest (dense FP64/FP32 -> padded FP32 rows), readback (padded FP32 rows
+// [row0, row0 + nrows) -> dense FP64/FP32) and the solve prologue, for the
+// batch API.
+cudaError_t hj_launch_ingest_f32(const void *src, hj_precision src_type, float *dst, int n4, int p4, long long nrows,
+                                 int *nonfinite, cudaStream_t stream);
+cudaError_t hj_launch_readback_f32(const float *src, void *dst, hj_precision dst_type, int n4, int p4, long long row0,
+                                   long long nrows, cudaStream_t stream);
+cudaError_t hj_launch_prologue_f32(HjDevState *st, const HjGeom &g, const HjCoef<float> *coef, int ncoef, double T,
+                                   double cfl, cudaStream_t stream);
+
 // Pointer of the value buffer that holds V after n steps.
 inline void *hj_value_ptr(const hj_grid *g, long long n)
 {

@@ -32,7 +32,7 @@
 #include <stdio.h>
 #include <string.h>
 
-#include "hj_device.cuh"
+#include "hj_tma.cuh"
 
 namespace {
 
@@ -41,7 +41,6 @@ constexpr int MAX_CONSUMERS = 768;  // consumer threads per CTA (+ one producer 
 // Launch-bound variants: up to 384, 512, 640 or 768 consumer threads (152,
 // 120, 96 or 80 registers a thread); a shape uses the smallest that holds it.
 constexpr int VARIANTS[4] = {384, 512, 640, 768};
-constexpr unsigned long long WAIT_NS = 4000000000ull;  // 4 s per wait: far beyond any healthy wait
 
 struct TiledParams {
     int ty, tv;          // tile rows along y and v
@@ -57,84 +56,6 @@ struct TiledParams {
     int stage_bytes;     // (halo_floats + v0_floats) * 4 rounded up to 128
     float k3, k4, mk34;  // |xdot_3|/dx_3, |xdot_4|/dx_4, -(k3 + k4): constant-bank operands
 };
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-__device__ __forceinline__ unsigned long long global_ns()
-{
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-// Wait for the phase with the given parity; false if the deadline passed.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, unsigned long long deadline)
-{
-    while (!mbar_try_wait(bar, parity)) {
-        if (global_ns() > deadline) return false;
-    }
-    return true;
-}
-// Warp-uniform version for consumer warps: every lane observes the phase,
-// and the timeout decision is the same for the whole warp.  The deadline is
-// read (from shared memory) only when the phase is not complete yet.
-__device__ __forceinline__ bool mbar_wait_warp(uint64_t *bar, uint32_t parity, const unsigned long long *deadline)
-{
-    while (true) {
-        bool done = mbar_try_wait(bar, parity);
-        if (__all_sync(0xffffffffu, done)) return true;
-        bool late = global_ns() > *deadline;
-        if (__any_sync(0xffffffffu, late)) return false;
-    }
-}
-__device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, uint64_t *bar, int c0, int c1, int c2,
-                                            int c3)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
-        "[%6];" ::"r"(smem_u32(dst)),
-        "l"((unsigned long long)map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
-        : "memory");
-}
-
-__device__ __forceinline__ float f4get(const float4 &v, int e)
-{
-    return e == 0 ? v.x : (e == 1 ? v.y : (e == 2 ? v.z : v.w));
-}
-__device__ __forceinline__ void f4set(float4 &v, int e, float x)
-{
-    if (e == 0) v.x = x;
-    else if (e == 1) v.y = x;
-    else if (e == 2) v.z = x;
-    else v.w = x;
-}
-__device__ __forceinline__ float4 f4ghost(const float4 &c, const float4 &o)
-{
-    return make_float4(2.f * c.x - o.x, 2.f * c.y - o.y, 2.f * c.z - o.z, 2.f * c.w - o.w);
-}
 
 struct ItemGeom {
     int y0, v0, x0, x1, pl0, pl1;
@@ -187,7 +108,7 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
             mbar_init(&empty[s], nconsumer_warps);
         }
         *abort_flag = 0;
-        *deadline_p = global_ns() + WAIT_NS;
+        *deadline_p = global_ns() + HJ_WAIT_NS;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
@@ -239,7 +160,7 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
                 *abort_flag = 1;
             }
             // drain: every copy this CTA issued must land before the CTA exits
-            const unsigned long long drain_deadline = global_ns() + WAIT_NS;
+            const unsigned long long drain_deadline = global_ns() + HJ_WAIT_NS;
             for (int s = 0; s < P.stages; ++s)
                 if (((used_mask >> s) & 1u) && !mbar_wait(&full[s], (last_phase >> s) & 1u, drain_deadline))
                     st->status = HJ_ERR_TIMEOUT;

@@ -89,6 +89,36 @@ class hj_grid_info(ctypes.Structure):
         return d
 
 
+class hj_batch_stats(ctypes.Structure):
+    _fields_ = [
+        ("steps", ctypes.c_int64),
+        ("launches", ctypes.c_int64),
+        ("active", ctypes.c_int32),
+        ("finished", ctypes.c_int32),
+        ("device_ms", ctypes.c_double),
+        ("nconsumer", ctypes.c_int32),
+        ("ctas", ctypes.c_int32),
+        ("items", ctypes.c_int32),
+    ]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class hj_batch_slot_info(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int32 * 4),
+        ("steps", ctypes.c_int64),
+        ("t", ctypes.c_double),
+        ("T", ctypes.c_double),
+        ("dt_last", ctypes.c_double),
+        ("done", ctypes.c_int32),
+        ("has_value", ctypes.c_int32),
+        ("tile", ctypes.c_int32 * 3),
+        ("device_bytes", ctypes.c_size_t),
+    ]
+
+
 # symbol -> (restype, argtypes); the exported C ABI
 _VP = ctypes.c_void_p
 _SIGS = {
@@ -112,6 +142,24 @@ _SIGS = {
                                        ctypes.POINTER(ctypes.c_double), ctypes.c_int32, _VP, _VP, _VP,
                                        ctypes.c_double, _VP, ctypes.POINTER(ctypes.c_double)]),
     "hj_get_info": (ctypes.c_int, [_VP, ctypes.POINTER(hj_grid_info)]),
+    "hj_batch_create": (ctypes.c_int, [ctypes.c_int32, ctypes.c_size_t, _VP, ctypes.POINTER(_VP)]),
+    "hj_batch_slot_bytes": (ctypes.c_size_t, [ctypes.POINTER(ctypes.c_int32)]),
+    "hj_batch_add": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double),
+                                    ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                    ctypes.POINTER(ctypes.c_int32)]),
+    "hj_batch_remove": (ctypes.c_int, [_VP, ctypes.c_int32]),
+    "hj_batch_set_initial_value": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
+                                                  ctypes.c_size_t]),
+    "hj_batch_set_initial_value_device": (ctypes.c_int, [_VP, ctypes.c_int32, _VP, ctypes.c_int, ctypes.c_size_t]),
+    "hj_batch_set_horizon": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_double, ctypes.c_double]),
+    "hj_batch_advance": (ctypes.c_int, [_VP, ctypes.c_int64, ctypes.POINTER(hj_batch_stats)]),
+    "hj_batch_get_slot_info": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.POINTER(hj_batch_slot_info)]),
+    "hj_batch_read_value": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_double), ctypes.c_size_t]),
+    "hj_batch_read_value_device": (ctypes.c_int, [_VP, ctypes.c_int32, _VP, ctypes.c_int, ctypes.c_size_t]),
+    "hj_batch_set_shape": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32]),
+    "hj_batch_autotune": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                                         ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double)]),
+    "hj_batch_destroy": (None, [_VP]),
     "hj_destroy_grid": (None, [_VP]),
     "hj_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "hj_last_error": (ctypes.c_char_p, []),
@@ -322,6 +370,136 @@ class Grid:
     def close(self):
         if self.handle:
             hj_destroy_grid(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------- batches
+
+def hj_batch_create(max_slots: int, memory_budget: int = 0, cuda_stream=None):
+    out = _VP()
+    stream = None if cuda_stream is None else ctypes.c_void_p(int(cuda_stream))
+    _check(lib.hj_batch_create(int(max_slots), int(memory_budget), stream, ctypes.byref(out)))
+    return out.value
+
+
+def hj_batch_slot_bytes(n) -> int:
+    return int(lib.hj_batch_slot_bytes((ctypes.c_int32 * 4)(*[int(v) for v in n])))
+
+
+def hj_batch_add(b, n, lo, hi, params) -> int:
+    slot = ctypes.c_int32(-1)
+    _check(lib.hj_batch_add(b, (ctypes.c_int32 * 4)(*[int(v) for v in n]), (ctypes.c_double * 4)(*[float(v) for v in lo]),
+                            (ctypes.c_double * 4)(*[float(v) for v in hi]),
+                            (ctypes.c_double * 2)(*[float(v) for v in params]), ctypes.byref(slot)))
+    return slot.value
+
+
+def hj_batch_remove(b, slot: int):
+    _check(lib.hj_batch_remove(b, int(slot)))
+
+
+def hj_batch_set_initial_value(b, slot: int, v0):
+    if hasattr(v0, "is_cuda") and v0.is_cuda:
+        _check(lib.hj_batch_set_initial_value_device(b, int(slot), ctypes.c_void_p(_dptr(v0)), _dtype_code(v0),
+                                                     int(v0.numel())))
+    else:
+        a = np.ascontiguousarray(v0, dtype=np.float64)
+        _check(lib.hj_batch_set_initial_value(b, int(slot), a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), a.size))
+
+
+def hj_batch_set_horizon(b, slot: int, T: float, cfl: float = 0.8):
+    _check(lib.hj_batch_set_horizon(b, int(slot), float(T), float(cfl)))
+
+
+def hj_batch_advance(b, max_steps: int = 1 << 40) -> hj_batch_stats:
+    st = hj_batch_stats()
+    _check(lib.hj_batch_advance(b, int(max_steps), ctypes.byref(st)))
+    return st
+
+
+def hj_batch_get_slot_info(b, slot: int) -> hj_batch_slot_info:
+    info = hj_batch_slot_info()
+    _check(lib.hj_batch_get_slot_info(b, int(slot), ctypes.byref(info)))
+    return info
+
+
+def hj_batch_read_value(b, slot: int, out=None) -> np.ndarray:
+    info = hj_batch_get_slot_info(b, slot)
+    if out is None:
+        out = np.empty(tuple(info.n), dtype=np.float64)
+    if hasattr(out, "is_cuda") and out.is_cuda:
+        _check(lib.hj_batch_read_value_device(b, int(slot), ctypes.c_void_p(_dptr(out)), _dtype_code(out),
+                                              int(out.numel())))
+        return out
+    _check(lib.hj_batch_read_value(b, int(slot), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), out.size))
+    return out
+
+
+def hj_batch_set_shape(b, nconsumer: int = 0, chunks: int = 0):
+    _check(lib.hj_batch_set_shape(b, int(nconsumer), int(chunks)))
+
+
+def hj_batch_autotune(b, steps_per_trial: int = 4):
+    nc, ch, ms = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_double(0)
+    _check(lib.hj_batch_autotune(b, int(steps_per_trial), ctypes.byref(nc), ctypes.byref(ch), ctypes.byref(ms)))
+    return nc.value, ch.value, ms.value
+
+
+def hj_batch_destroy(b):
+    lib.hj_batch_destroy(b)
+
+
+class Batch:
+    """Owns one hj_batch; the methods are the C calls above."""
+
+    def __init__(self, max_slots, memory_budget=0, cuda_stream=None):
+        self.handle = hj_batch_create(max_slots, memory_budget, cuda_stream)
+
+    def add(self, n, lo, hi, params):
+        return hj_batch_add(self.handle, n, lo, hi, params)
+
+    def add_workload(self, w):
+        return self.add(w.grid.n, w.grid.lo, w.grid.hi, (w.a_max, w.w_max))
+
+    def remove(self, slot):
+        hj_batch_remove(self.handle, slot)
+
+    def set_initial_value(self, slot, v0):
+        hj_batch_set_initial_value(self.handle, slot, v0)
+
+    def set_horizon(self, slot, T, cfl=0.8):
+        hj_batch_set_horizon(self.handle, slot, T, cfl)
+
+    def advance(self, max_steps=1 << 40):
+        return hj_batch_advance(self.handle, max_steps)
+
+    def slot_info(self, slot):
+        return hj_batch_get_slot_info(self.handle, slot)
+
+    def read_value(self, slot, out=None):
+        return hj_batch_read_value(self.handle, slot, out)
+
+    def set_shape(self, nconsumer=0, chunks=0):
+        hj_batch_set_shape(self.handle, nconsumer, chunks)
+
+    def autotune(self, steps_per_trial=4):
+        return hj_batch_autotune(self.handle, steps_per_trial)
+
+    def close(self):
+        if self.handle:
+            hj_batch_destroy(self.handle)
             self.handle = None
 
     def __enter__(self):

@@ -85,3 +85,14 @@ def test_unknown_precision_and_mask(hj):
 def test_build_entry_compiles_everything():
     import __graft_entry__
     __graft_entry__.build()
+
+
+def test_batch_host_checks(hj):
+    assert hj.hj_batch_slot_bytes((40, 40, 16, 24)) >= 3 * 40 * 40 * 16 * 24 * 4
+    assert hj.hj_batch_slot_bytes((40, 40, 16, 25)) > hj.hj_batch_slot_bytes((40, 40, 16, 24))  # padded rows
+    with pytest.raises(hj.HjError) as e:
+        hj.hj_batch_create(0)
+    assert e.value.status == hj.HJ_ERR_INVALID_ARG
+    for fn, args in ((hj.lib.hj_batch_advance, (None, 1, None)), (hj.lib.hj_batch_remove, (None, 0))):
+        assert fn(*args) == hj.HJ_ERR_INVALID_ARG
+    hj.lib.hj_batch_destroy(None)

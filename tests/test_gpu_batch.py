@@ -1,0 +1,151 @@
+"""Batched solves: many independent car grids stepped by one persistent
+kernel per batch step (CUDA graphs), each slot with its own grid, V0,
+horizon and dt.
+
+Each slot must give exactly what a single-grid FP32 solve of the same grid
+gives (same per-cell arithmetic, same dt sequence), and must match the FP64
+oracle within the FP32 tolerance (1e-4 max|V0|, no sign flip outside
+|V| < 1e-3)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2012_04011_gb300 import scenes
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hj():
+    from paper_2012_04011_gb300 import _build
+    _build.build()
+    from paper_2012_04011_gb300 import hj as mod
+    return mod
+
+
+def oracle_problem(w):
+    return oracle.Problem(w.grid.n, w.grid.lo, w.grid.hi, w.grid.periodic, oracle.DYN_CAR4D, (w.a_max, w.w_max))
+
+
+def single_grid(hj, w, V0, T=None):
+    with hj.Grid.for_workload(w, hj.HJ_FP32) as g:
+        g.set_kernel(hj.HJ_KERNEL_TILED)
+        g.set_initial_value(V0)
+        st = g.solve_brt(w.T if T is None else T, w.cfl)
+        return g.read_value(), st
+
+
+MIXED = [(21, 19, 9, 16), (17, 23, 7, 26), (12, 10, 9, 33), (25, 25, 11, 24), (9, 21, 4, 8), (30, 14, 6, 30)]
+
+
+def test_batch_slots_equal_single_grid_solves(hj):
+    ws = [scenes.custom_workload(n, n_circles=3, n_rects=1, T=0.3 + 0.05 * i, seed=40 + i) for i, n in enumerate(MIXED)]
+    v0s = [scenes.initial_value(w.grid, w.scene) for w in ws]
+    with hj.Batch(len(ws)) as b:
+        slots = [b.add_workload(w) for w in ws]
+        for s, w, v0 in zip(slots, ws, v0s):
+            b.set_initial_value(s, v0)
+            b.set_horizon(s, w.T, w.cfl)
+        st = b.advance()
+        assert st.active == 0 and st.finished == len(ws)
+        for s, w, v0 in zip(slots, ws, v0s):
+            ref, rst = single_grid(hj, w, v0)
+            info = b.slot_info(s)
+            assert info.steps == rst.steps and info.t == w.T
+            assert np.array_equal(b.read_value(s), ref), (s, w.grid.n)
+
+
+def test_batch_matches_oracle(hj):
+    ws = [scenes.custom_workload(n, n_circles=4, T=0.4, seed=90 + i) for i, n in enumerate(MIXED[:4])]
+    with hj.Batch(8) as b:
+        slots = []
+        for w in ws:
+            s = b.add_workload(w)
+            b.set_initial_value(s, scenes.initial_value(w.grid, w.scene))
+            b.set_horizon(s, w.T, w.cfl)
+            slots.append(s)
+        b.advance()
+        for s, w in zip(slots, ws):
+            V0 = scenes.initial_value(w.grid, w.scene)
+            Vo, _ = oracle.solve(oracle_problem(w), V0, w.T, w.cfl, nthreads=16)
+            V = b.read_value(s)
+            assert float(np.abs(V - Vo).max()) <= 1e-4 * float(np.abs(V0).max())
+            m = np.abs(Vo) >= 1e-3
+            assert np.count_nonzero(np.sign(V[m]) != np.sign(Vo[m])) == 0
+
+
+def test_batch_add_remove_between_advances_and_budget(hj):
+    w1 = scenes.custom_workload((20, 20, 8, 16), n_circles=3, T=0.5, seed=1)
+    w2 = scenes.custom_workload((16, 18, 6, 12), n_circles=2, T=0.3, seed=2)
+    budget = hj.hj_batch_slot_bytes(w1.grid.n) + hj.hj_batch_slot_bytes(w2.grid.n)
+    with hj.Batch(4, memory_budget=budget) as b:
+        s1 = b.add_workload(w1)
+        b.set_initial_value(s1, scenes.initial_value(w1.grid, w1.scene))
+        b.set_horizon(s1, w1.T)
+        st = b.advance(5)
+        assert st.steps == 5 and st.active == 1
+        s2 = b.add_workload(w2)  # admitted while s1 is mid-solve
+        with pytest.raises(hj.HjError) as e:  # the budget is full now
+            b.add_workload(w2)
+        assert e.value.status == hj.HJ_ERR_OOM
+        b.set_initial_value(s2, scenes.initial_value(w2.grid, w2.scene))
+        b.set_horizon(s2, w2.T)
+        b.advance()
+        for s, w in ((s1, w1), (s2, w2)):
+            ref, _ = single_grid(hj, w, scenes.initial_value(w.grid, w.scene))
+            assert np.array_equal(b.read_value(s), ref)
+        b.remove(s2)
+        s3 = b.add_workload(w2)  # the freed memory is reusable
+        b.set_initial_value(s3, scenes.initial_value(w2.grid, w2.scene))
+        b.set_horizon(s3, 0.1)
+        b.advance()
+        assert b.slot_info(s3).t == 0.1 and b.slot_info(s1).t == w1.T
+
+
+def test_batch_shapes_and_autotune_give_identical_bits(hj):
+    ws = [scenes.custom_workload(n, n_circles=3, T=0.2, seed=7 + i) for i, n in enumerate(MIXED[:3])]
+    v0s = [scenes.initial_value(w.grid, w.scene) for w in ws]
+    results = []
+    for shape in ((0, 0), (384, 1), (512, 2), (640, 4), (768, 1), ("tune", 0)):
+        with hj.Batch(4) as b:
+            slots = [b.add_workload(w) for w in ws]
+            for s, v0 in zip(slots, v0s):
+                b.set_initial_value(s, v0)
+            if shape[0] == "tune":
+                nc, ch, ms = b.autotune(3)
+                assert nc > 0 and ms > 0
+            else:
+                b.set_shape(*shape)
+            for s, w in zip(slots, ws):
+                b.set_horizon(s, w.T)
+            b.advance()
+            results.append([b.read_value(s) for s in slots])
+    for r in results[1:]:
+        for a, c in zip(results[0], r):
+            assert np.array_equal(a, c)
+
+
+@pytest.mark.slow
+def test_batch64_workload(hj):
+    """The 64-instance workload: uneven grids (N1, N2 in {40, 50, 60}, N3 in
+    [16, 24], N4 in [24, 36]), 4-16 circles each, T = 1.5 s.  Every slot
+    matches its single-grid solve bit for bit; three slots are checked
+    against full oracle solves."""
+    ws = scenes.batch_workloads()
+    with hj.Batch(len(ws)) as b:
+        slots = []
+        for w in ws:
+            s = b.add_workload(w)
+            b.set_initial_value(s, scenes.initial_value(w.grid, w.scene))
+            b.set_horizon(s, w.T, w.cfl)
+            slots.append(s)
+        st = b.advance()
+        assert st.active == 0
+        for i in (0, 17, 63):
+            w = ws[i]
+            V0 = scenes.initial_value(w.grid, w.scene)
+            V = b.read_value(slots[i])
+            ref, _ = single_grid(hj, w, V0)
+            assert np.array_equal(V, ref)
+            Vo, _ = oracle.solve(oracle_problem(w), V0, w.T, w.cfl, nthreads=16)
+            assert float(np.abs(V - Vo).max()) <= 1e-4 * float(np.abs(V0).max())
