@@ -152,6 +152,11 @@ HJ_API hj_status hj_set_dynamics(hj_grid *g, hj_dynamics kind, const double *par
  * the copy faster; pageable memory works. */
 HJ_API hj_status hj_set_initial_value(hj_grid *g, const double *v0, size_t count);
 
+/* As hj_set_initial_value for a V0 that depends on position only (as Eq.
+ * init_V does): v0_xy is a host array of count = N1*N2 doubles, row-major
+ * [N1][N2], replicated over v and theta on the device. */
+HJ_API hj_status hj_set_initial_value_xy(hj_grid *g, const double *v0_xy, size_t count);
+
 /* As hj_set_initial_value, from a DEVICE array (dtype HJ_FP64 = double,
  * HJ_FP32 = float) of count values on the grid's device, dense layout
  * above.  The array is read on the grid's stream; the caller keeps
@@ -290,6 +295,9 @@ HJ_API hj_status hj_batch_set_initial_value(hj_batch *b, int32_t slot, const dou
 HJ_API hj_status hj_batch_set_initial_value_device(hj_batch *b, int32_t slot, const void *v0, hj_precision dtype,
                                                    size_t count);
 
+/* As hj_set_initial_value_xy, for a slot. */
+HJ_API hj_status hj_batch_set_initial_value_xy(hj_batch *b, int32_t slot, const double *v0_xy, size_t count);
+
 /* Horizon T and Courant number of a slot (computes its first dt). */
 HJ_API hj_status hj_batch_set_horizon(hj_batch *b, int32_t slot, double T, double cfl);
 
@@ -320,6 +328,63 @@ HJ_API hj_status hj_batch_autotune(hj_batch *b, int32_t steps_per_trial, int32_t
 
 /* Free the batch and all its slots (NULL is a no-op). */
 HJ_API void hj_batch_destroy(hj_batch *b);
+
+/* ---- Re-solve server: continuous batching of BRT requests ----------------
+ *
+ * The paper's real-time use (Sec. I; Sec. IV-C: re-computing the BRT at
+ * 5 Hz as the environment changes): requests arrive at any time, are
+ * admitted into a batch when a slot and enough device memory are free, and
+ * are stepped together with the requests already in flight; results stay on
+ * the device until fetched.  Times are seconds on the server's clock. */
+typedef struct hj_server hj_server;
+
+typedef struct {
+    int32_t state;      /* 0 queued, 1 running, 2 done, 3 failed (fetch returns the reason) */
+    int32_t slot;       /* batch slot while running or done */
+    int64_t steps;      /* time steps taken (when done) */
+    double t_submit, t_admit, t_done;
+} hj_request_info;
+
+/* max_slots and memory_budget as hj_batch_create; steps_per_tick: batch
+ * steps per hj_server_tick (>= 1): smaller admits new requests sooner. */
+HJ_API hj_status hj_server_create(int32_t max_slots, size_t memory_budget, int32_t steps_per_tick, void *cuda_stream,
+                                  hj_server **out);
+
+/* Queue a request: a car grid (as hj_batch_add), V0 as a host FP64 array
+ * (copied), horizon T and Courant number.  *request_id identifies it. */
+HJ_API hj_status hj_server_submit(hj_server *s, const int32_t n[4], const double lo[4], const double hi[4],
+                                  const double params[2], const double *v0, double T, double cfl,
+                                  int64_t *request_id);
+
+/* As hj_server_submit with V0 given by its N1*N2 (x, y) field (see
+ * hj_set_initial_value_xy). */
+HJ_API hj_status hj_server_submit_xy(hj_server *s, const int32_t n[4], const double lo[4], const double hi[4],
+                                     const double params[2], const double *v0_xy, double T, double cfl,
+                                     int64_t *request_id);
+
+/* Admit queued requests (arrival order) while slots and memory last, take
+ * steps_per_tick batch steps, and mark requests at their horizon done.
+ * Outputs (may be NULL): requests completed by this tick, still running,
+ * still queued. */
+HJ_API hj_status hj_server_tick(hj_server *s, int32_t *completed, int32_t *running, int32_t *queued);
+
+/* State and timestamps of a request. */
+HJ_API hj_status hj_server_request_info(const hj_server *s, int64_t request_id, hj_request_info *info);
+
+/* Copy a done request's V into a host FP64 buffer (or a device FP32/FP64
+ * buffer) and release its slot; the request is forgotten afterwards. */
+HJ_API hj_status hj_server_fetch(hj_server *s, int64_t request_id, double *out, size_t count);
+HJ_API hj_status hj_server_fetch_device(hj_server *s, int64_t request_id, void *out_device, hj_precision dtype,
+                                        size_t count);
+
+/* Seconds since the server was created (the clock of the timestamps). */
+HJ_API double hj_server_clock(const hj_server *s);
+
+/* Ticks and batch steps taken so far (outputs may be NULL). */
+HJ_API hj_status hj_server_stats(const hj_server *s, int64_t *ticks, int64_t *batch_steps);
+
+/* Free the server, its batch and every request (NULL is a no-op). */
+HJ_API void hj_server_destroy(hj_server *s);
 
 /* Describe the grid (sizes, spacings, time, memory). */
 HJ_API hj_status hj_get_info(const hj_grid *g, hj_grid_info *info);

@@ -65,6 +65,29 @@ __global__ void ingest_kernel(const Tin *__restrict__ src, T *__restrict__ dst, 
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(nonfinite, 1);
 }
 
+// V0 that depends only on (x, y): an N1*N2 field replicated over v and theta
+// (Eq. init_V depends on the position only), written in the internal layout.
+template <typename T>
+__global__ void ingest_xy_kernel(const double *__restrict__ src, T *__restrict__ dst, int n3, int n4, int p4,
+                                 long long nxy, int *nonfinite)
+{
+    const long long per = (long long)n3 * p4, total = nxy * per;
+    int bad = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long xy = i / per;
+        const int l = (int)(i - xy * per) % p4;
+        T v = T(0);
+        if (l < n4) {
+            const double x = src[xy];
+            if (!isfinite(x)) bad = 1;
+            v = (T)x;
+        }
+        dst[i] = v;
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(nonfinite, 1);
+}
+
 // Internal layout -> dense (rows [row0, row0 + nrows)), converting type.
 template <typename T, typename Tout>
 __global__ void readback_kernel(const T *__restrict__ src, Tout *__restrict__ dst, int n4, int p4, long long row0,
@@ -180,19 +203,22 @@ hj_status upload_tables(hj_grid *g)
         free(tab);
         return set_err(HJ_ERR_OOM, "host allocation failed");
     }
+    // FP64 tables keep libm's cos/sin; FP32 tables flush rounding artefacts
+    const bool f32 = g->prec == HJ_FP32;
     for (int k = 0; k < N3; ++k) {
         double v = g->lo[2] + (double)k * g->h[2];
         tab[k] = (float)v;
         for (int l = 0; l < N4; ++l) {
             double th = g->lo[3] + (double)l * g->h[3];
-            f1[(size_t)k * N4 + l] = car ? v * cos(th) : g->params[0];
-            f2[(size_t)k * N4 + l] = car ? v * sin(th) : g->params[1];
+            const double c = f32 ? hj_flush_trig(cos(th)) : cos(th), sn = f32 ? hj_flush_trig(sin(th)) : sin(th);
+            f1[(size_t)k * N4 + l] = car ? v * c : g->params[0];
+            f2[(size_t)k * N4 + l] = car ? v * sn : g->params[1];
         }
     }
     for (int l = 0; l < N4; ++l) {
         double th = g->lo[3] + (double)l * g->h[3];
-        tab[N3 + l] = (float)(cos(th) / g->h[0]);
-        tab[N3 + P4 + l] = (float)(sin(th) / g->h[1]);
+        tab[N3 + l] = (float)(hj_flush_trig(cos(th)) / g->h[0]);
+        tab[N3 + P4 + l] = (float)(hj_flush_trig(sin(th)) / g->h[1]);
     }
     const double k3 = g->geom.k3, k4 = g->geom.k4;
     hj_status st = HJ_OK;
@@ -289,6 +315,14 @@ cudaError_t hj_launch_ingest_f32(const void *src, hj_precision src_type, float *
         ingest_kernel<double, float><<<blocks, 256, 0, stream>>>((const double *)src, dst, n4, p4, nrows, nonfinite);
     else
         ingest_kernel<float, float><<<blocks, 256, 0, stream>>>((const float *)src, dst, n4, p4, nrows, nonfinite);
+    return cudaGetLastError();
+}
+
+cudaError_t hj_launch_ingest_xy_f32(const double *src_dev, float *dst, int n3, int n4, int p4, long long nxy,
+                                    int *nonfinite, cudaStream_t stream)
+{
+    ingest_xy_kernel<float><<<grid_blocks(nxy * n3 * p4, 256), 256, 0, stream>>>(src_dev, dst, n3, n4, p4, nxy,
+                                                                                 nonfinite);
     return cudaGetLastError();
 }
 
@@ -499,6 +533,29 @@ hj_status hj_set_initial_value(hj_grid *g, const double *v0, size_t count)
         ingest_kernel<double, double><<<blocks, 256, 0, g->stream>>>(staging, (double *)g->v0, g->n[3], g->p4, nrows, flag);
     else
         ingest_kernel<double, float><<<blocks, 256, 0, g->stream>>>(staging, (float *)g->v0, g->n[3], g->p4, nrows, flag);
+    return finish_ingest(g);
+}
+
+hj_status hj_set_initial_value_xy(hj_grid *g, const double *v0_xy, size_t count)
+{
+    g_err[0] = 0;
+    hj_status s = check_grid(g);
+    if (s != HJ_OK) return s;
+    if (!v0_xy) return set_err(HJ_ERR_INVALID_ARG, "v0_xy is NULL");
+    const long long nxy = (long long)g->n[0] * g->n[1];
+    if (count != (size_t)nxy) return set_err(HJ_ERR_INVALID_ARG, "count %zu != N1*N2 = %lld", count, nxy);
+    if ((s = activate(g)) != HJ_OK) return s;
+    if ((s = reset_state(g)) != HJ_OK) return s;
+    double *staging = (double *)g->buf;  // N1*N2 doubles fit in the ping-pong region
+    HJ_CUDA(cudaMemcpyAsync(staging, v0_xy, sizeof(double) * (size_t)nxy, cudaMemcpyHostToDevice, g->stream));
+    int *flag = &g->dstate->nonfinite;
+    const int blocks = grid_blocks(g->nint, 256);
+    if (g->prec == HJ_FP64)
+        ingest_xy_kernel<double><<<blocks, 256, 0, g->stream>>>(staging, (double *)g->v0, g->n[2], g->n[3], g->p4, nxy,
+                                                              flag);
+    else
+        ingest_xy_kernel<float><<<blocks, 256, 0, g->stream>>>(staging, (float *)g->v0, g->n[2], g->n[3], g->p4, nxy,
+                                                             flag);
     return finish_ingest(g);
 }
 

@@ -523,7 +523,8 @@ hj_status upload_slot_tables(hj_batch *b, SlotHost &s)
         tab[k] = (float)v;
         for (int l = 0; l < N4; ++l) {
             const double th = s.lo[3] + (double)l * s.h[3];
-            const double f1 = v * cos(th), f2 = v * sin(th), c1 = f1 / s.h[0], c2 = f2 / s.h[1];
+            const double f1 = v * hj_flush_trig(cos(th)), f2 = v * hj_flush_trig(sin(th));
+            const double c1 = f1 / s.h[0], c2 = f2 / s.h[1];
             HjCoef<float> &e = c[(size_t)k * N4 + l];
             e.c1 = (float)c1;
             e.c2 = (float)c2;
@@ -534,8 +535,8 @@ hj_status upload_slot_tables(hj_batch *b, SlotHost &s)
     }
     for (int l = 0; l < N4; ++l) {
         const double th = s.lo[3] + (double)l * s.h[3];
-        tab[N3 + l] = (float)(cos(th) / s.h[0]);
-        tab[N3 + P4 + l] = (float)(sin(th) / s.h[1]);
+        tab[N3 + l] = (float)(hj_flush_trig(cos(th)) / s.h[0]);
+        tab[N3 + P4 + l] = (float)(hj_flush_trig(sin(th)) / s.h[1]);
     }
     HJB_CUDA(cudaMemcpyAsync(s.coef, c.data(), sizeof(HjCoef<float>) * c.size(), cudaMemcpyHostToDevice, b->stream));
     HJB_CUDA(cudaMemcpyAsync(s.tab, tab.data(), sizeof(float) * tab.size(), cudaMemcpyHostToDevice, b->stream));
@@ -940,6 +941,31 @@ static hj_status batch_ingest(hj_batch *b, int32_t slot, const void *src, hj_pre
     return HJ_OK;
 }
 
+hj_status hj_batch_set_initial_value_xy(hj_batch *b, int32_t slot, const double *v0_xy, size_t count)
+{
+    hj_internal_set_error("");
+    hj_status s = check_slot(b, slot);
+    if (s != HJ_OK) return s;
+    SlotHost &sl = b->slots[slot];
+    if (!v0_xy) return bfail(HJ_ERR_INVALID_ARG, "v0_xy is NULL");
+    const long long nxy = (long long)sl.n[0] * sl.n[1];
+    if (count != (size_t)nxy) return bfail(HJ_ERR_INVALID_ARG, "count %zu != N1*N2 = %lld", count, nxy);
+    HJB_CUDA(cudaStreamSynchronize(b->stream));
+    memset(&b->h_slots[slot], 0, sizeof(BatchSlot));
+    b->h_slots[slot].st.done = 1;
+    if ((s = push_slot(b, slot)) != HJ_OK) return s;
+    HJB_CUDA(cudaMemcpyAsync(sl.buf, v0_xy, sizeof(double) * (size_t)nxy, cudaMemcpyHostToDevice, b->stream));
+    HJB_CUDA(hj_launch_ingest_xy_f32((const double *)sl.buf, sl.v0, sl.n[2], sl.n[3], sl.p4, nxy,
+                                     &b->d_slots[slot].st.nonfinite, b->stream));
+    if ((s = pull_slots(b)) != HJ_OK) return s;
+    if (b->h_slots[slot].st.nonfinite) {
+        sl.has_value = false;
+        return bfail(HJ_ERR_INVALID_ARG, "V0 contains NaN or Inf");
+    }
+    sl.has_value = true;
+    return HJ_OK;
+}
+
 hj_status hj_batch_set_initial_value(hj_batch *b, int32_t slot, const double *v0, size_t count)
 {
     hj_internal_set_error("");
@@ -1182,3 +1208,18 @@ hj_status hj_batch_autotune(hj_batch *b, int32_t steps_per_trial, int32_t *best_
 }
 
 }  // extern "C"
+
+// Internal (not in the C ABI): pull every slot's state once, then read the
+// host copy.
+hj_status hj_batch_refresh(hj_batch *b)
+{
+    if (!b) return bfail(HJ_ERR_INVALID_ARG, "batch is NULL");
+    return pull_slots(b);
+}
+
+bool hj_batch_cached_done(const hj_batch *b, int32_t slot, int64_t *steps)
+{
+    if (!b || slot < 0 || slot >= b->max_slots) return false;
+    if (steps) *steps = b->h_slots[slot].st.n;
+    return b->h_slots[slot].st.done != 0;
+}

@@ -100,6 +100,12 @@ bool hj_tiled_setup(hj_grid *g, char *why, size_t why_len);
 // and whether that shape can run at all.
 int hj_tiled_threads(const hj_grid *g, int ty, int tv);
 
+// cos and sin of grid headings for the FP32 tables: values below 1e-12 are
+// rounding artefacts of theta_l = lo + l dx at +-pi/2, 0, +-pi (the next
+// smallest |cos| or |sin| on a grid of at most 4096 headings is ~1.5e-3), and
+// are set to exactly 0 so that every FP32 kernel uses the same upwind side.
+static inline double hj_flush_trig(double x) { return (x < 1e-12 && x > -1e-12) ? 0.0 : x; }
+
 // Sets the message hj_last_error() returns on this host thread.
 void hj_internal_set_error(const char *msg);
 
@@ -108,10 +114,17 @@ void hj_internal_set_error(const char *msg);
 // batch API.
 cudaError_t hj_launch_ingest_f32(const void *src, hj_precision src_type, float *dst, int n4, int p4, long long nrows,
                                  int *nonfinite, cudaStream_t stream);
+cudaError_t hj_launch_ingest_xy_f32(const double *src_dev, float *dst, int n3, int n4, int p4, long long nxy,
+                                    int *nonfinite, cudaStream_t stream);
 cudaError_t hj_launch_readback_f32(const float *src, void *dst, hj_precision dst_type, int n4, int p4, long long row0,
                                    long long nrows, cudaStream_t stream);
 cudaError_t hj_launch_prologue_f32(HjDevState *st, const HjGeom &g, const HjCoef<float> *coef, int ncoef, double T,
                                    double cfl, cudaStream_t stream);
+
+// Batch internals for the server: pull all slot states once, then query the
+// host copy (done flag and step count of a slot).
+hj_status hj_batch_refresh(hj_batch *b);
+bool hj_batch_cached_done(const hj_batch *b, int32_t slot, int64_t *steps);
 
 // Pointer of the value buffer that holds V after n steps.
 inline void *hj_value_ptr(const hj_grid *g, long long n)

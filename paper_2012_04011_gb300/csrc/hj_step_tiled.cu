@@ -453,17 +453,17 @@ size_t tiled_smem_bytes(const TiledParams &P)
            32;
 }
 
-// Whether every theta quad has one sign of cos and of sin, up to values that
-// are negligible (|x| <= 1e-6 max|x|) and contribute nothing measurable in
-// FP32; also writes the quads' dominant signs into tab_sign[4 * q].
+// Whether every theta quad has one sign of cos and of sin (lanes whose value
+// is exactly 0 after hj_flush_trig carry no weight and count as either);
+// also writes the quads' dominant signs into tab_sign[4 * q].
 bool sign_uniform(const hj_grid *g, float *tab_sign)
 {
     const int N4 = g->n[3];
     double cmax = 0, smax = 0;
     for (int l = 0; l < N4; ++l) {
         const double th = g->lo[3] + (double)l * g->h[3];
-        cmax = fmax(cmax, fabs(cos(th)));
-        smax = fmax(smax, fabs(sin(th)));
+        cmax = fmax(cmax, fabs(hj_flush_trig(cos(th))));
+        smax = fmax(smax, fabs(hj_flush_trig(sin(th))));
     }
     bool ok = true;
     for (int q = 0; q < g->p4 / 4; ++q) {
@@ -471,14 +471,16 @@ bool sign_uniform(const hj_grid *g, float *tab_sign)
         int sc = 1, ss = 1;
         for (int e = 0; e < 4 && 4 * q + e < N4; ++e) {
             const double th = g->lo[3] + (double)(4 * q + e) * g->h[3];
-            if (fabs(cos(th)) > bc) bc = fabs(cos(th)), sc = cos(th) >= 0 ? 1 : -1;
-            if (fabs(sin(th)) > bs) bs = fabs(sin(th)), ss = sin(th) >= 0 ? 1 : -1;
+            const double c = hj_flush_trig(cos(th)), sn = hj_flush_trig(sin(th));
+            if (fabs(c) > bc) bc = fabs(c), sc = c >= 0 ? 1 : -1;
+            if (fabs(sn) > bs) bs = fabs(sn), ss = sn >= 0 ? 1 : -1;
         }
         for (int e = 0; e < 4 && 4 * q + e < N4; ++e) {
             const double th = g->lo[3] + (double)(4 * q + e) * g->h[3];
-            const double c = cos(th), s = sin(th);
-            if ((c >= 0 ? 1 : -1) != sc && fabs(c) > 1e-6 * cmax) ok = false;
-            if ((s >= 0 ? 1 : -1) != ss && fabs(s) > 1e-6 * smax) ok = false;
+            // lanes whose weight is exactly 0 may sit on either side
+            const double c = hj_flush_trig(cos(th)), s = hj_flush_trig(sin(th));
+            if (c != 0.0 && (c >= 0 ? 1 : -1) != sc) ok = false;
+            if (s != 0.0 && (s >= 0 ? 1 : -1) != ss) ok = false;
         }
         tab_sign[4 * q + 0] = (float)sc;
         tab_sign[4 * q + 1] = (float)ss;

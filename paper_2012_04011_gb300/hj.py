@@ -119,6 +119,17 @@ class hj_batch_slot_info(ctypes.Structure):
     ]
 
 
+class hj_request_info(ctypes.Structure):
+    _fields_ = [
+        ("state", ctypes.c_int32),
+        ("slot", ctypes.c_int32),
+        ("steps", ctypes.c_int64),
+        ("t_submit", ctypes.c_double),
+        ("t_admit", ctypes.c_double),
+        ("t_done", ctypes.c_double),
+    ]
+
+
 # symbol -> (restype, argtypes); the exported C ABI
 _VP = ctypes.c_void_p
 _SIGS = {
@@ -128,6 +139,13 @@ _SIGS = {
     "hj_set_dynamics": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_int32]),
     "hj_set_initial_value": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.c_size_t]),
     "hj_set_initial_value_device": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_size_t]),
+    "hj_set_initial_value_xy": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.c_size_t]),
+    "hj_batch_set_initial_value_xy": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
+                                                     ctypes.c_size_t]),
+    "hj_server_submit_xy": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double),
+                                           ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                           ctypes.POINTER(ctypes.c_double), ctypes.c_double, ctypes.c_double,
+                                           ctypes.POINTER(ctypes.c_int64)]),
     "hj_solve_brt": (ctypes.c_int, [_VP, ctypes.c_double, ctypes.c_double, ctypes.POINTER(hj_solve_stats)]),
     "hj_advance_brt": (ctypes.c_int, [_VP, ctypes.c_double, ctypes.c_double, ctypes.c_int64,
                                       ctypes.POINTER(hj_solve_stats)]),
@@ -160,6 +178,19 @@ _SIGS = {
     "hj_batch_autotune": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
                                          ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double)]),
     "hj_batch_destroy": (None, [_VP]),
+    "hj_server_create": (ctypes.c_int, [ctypes.c_int32, ctypes.c_size_t, ctypes.c_int32, _VP, ctypes.POINTER(_VP)]),
+    "hj_server_submit": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(ctypes.c_double), ctypes.c_double, ctypes.c_double,
+                                        ctypes.POINTER(ctypes.c_int64)]),
+    "hj_server_tick": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                      ctypes.POINTER(ctypes.c_int32)]),
+    "hj_server_request_info": (ctypes.c_int, [_VP, ctypes.c_int64, ctypes.POINTER(hj_request_info)]),
+    "hj_server_fetch": (ctypes.c_int, [_VP, ctypes.c_int64, ctypes.POINTER(ctypes.c_double), ctypes.c_size_t]),
+    "hj_server_fetch_device": (ctypes.c_int, [_VP, ctypes.c_int64, _VP, ctypes.c_int, ctypes.c_size_t]),
+    "hj_server_clock": (ctypes.c_double, [_VP]),
+    "hj_server_stats": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
+    "hj_server_destroy": (None, [_VP]),
     "hj_destroy_grid": (None, [_VP]),
     "hj_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "hj_last_error": (ctypes.c_char_p, []),
@@ -240,6 +271,11 @@ def hj_set_dynamics(g, kind: int, params):
 def hj_set_initial_value(g, v0: np.ndarray):
     a = np.ascontiguousarray(v0, dtype=np.float64)
     _check(lib.hj_set_initial_value(g, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), a.size))
+
+
+def hj_set_initial_value_xy(g, v0_xy: np.ndarray):
+    a = np.ascontiguousarray(v0_xy, dtype=np.float64)
+    _check(lib.hj_set_initial_value_xy(g, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), a.size))
 
 
 def hj_set_initial_value_device(g, v0_device, count: int | None = None, dtype: int | None = None):
@@ -337,6 +373,9 @@ class Grid:
     def set_dynamics(self, kind, params):
         hj_set_dynamics(self.handle, kind, params)
 
+    def set_initial_value_xy(self, v0_xy):
+        hj_set_initial_value_xy(self.handle, v0_xy)
+
     def set_initial_value(self, v0):
         if hasattr(v0, "is_cuda") and v0.is_cuda:
             hj_set_initial_value_device(self.handle, v0)
@@ -419,6 +458,11 @@ def hj_batch_set_initial_value(b, slot: int, v0):
         _check(lib.hj_batch_set_initial_value(b, int(slot), a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), a.size))
 
 
+def hj_batch_set_initial_value_xy(b, slot: int, v0_xy):
+    a = np.ascontiguousarray(v0_xy, dtype=np.float64)
+    _check(lib.hj_batch_set_initial_value_xy(b, int(slot), a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), a.size))
+
+
 def hj_batch_set_horizon(b, slot: int, T: float, cfl: float = 0.8):
     _check(lib.hj_batch_set_horizon(b, int(slot), float(T), float(cfl)))
 
@@ -479,6 +523,9 @@ class Batch:
     def set_initial_value(self, slot, v0):
         hj_batch_set_initial_value(self.handle, slot, v0)
 
+    def set_initial_value_xy(self, slot, v0_xy):
+        hj_batch_set_initial_value_xy(self.handle, slot, v0_xy)
+
     def set_horizon(self, slot, T, cfl=0.8):
         hj_batch_set_horizon(self.handle, slot, T, cfl)
 
@@ -500,6 +547,93 @@ class Batch:
     def close(self):
         if self.handle:
             hj_batch_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------- re-solve server
+
+REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = range(4)
+
+
+class Server:
+    """Owns one hj_server (continuous batching of BRT re-solve requests)."""
+
+    def __init__(self, max_slots=64, memory_budget=0, steps_per_tick=8, cuda_stream=None):
+        out = _VP()
+        stream = None if cuda_stream is None else ctypes.c_void_p(int(cuda_stream))
+        _check(lib.hj_server_create(int(max_slots), int(memory_budget), int(steps_per_tick), stream,
+                                    ctypes.byref(out)))
+        self.handle = out.value
+
+    def submit(self, n, lo, hi, params, v0, T, cfl=0.8) -> int:
+        a = np.ascontiguousarray(v0, dtype=np.float64)
+        rid = ctypes.c_int64(0)
+        _check(lib.hj_server_submit(self.handle, (ctypes.c_int32 * 4)(*[int(v) for v in n]),
+                                    (ctypes.c_double * 4)(*[float(v) for v in lo]),
+                                    (ctypes.c_double * 4)(*[float(v) for v in hi]),
+                                    (ctypes.c_double * 2)(*[float(v) for v in params]),
+                                    a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), float(T), float(cfl),
+                                    ctypes.byref(rid)))
+        return rid.value
+
+    def submit_xy(self, n, lo, hi, params, v0_xy, T, cfl=0.8) -> int:
+        a = np.ascontiguousarray(v0_xy, dtype=np.float64)
+        rid = ctypes.c_int64(0)
+        _check(lib.hj_server_submit_xy(self.handle, (ctypes.c_int32 * 4)(*[int(v) for v in n]),
+                                       (ctypes.c_double * 4)(*[float(v) for v in lo]),
+                                       (ctypes.c_double * 4)(*[float(v) for v in hi]),
+                                       (ctypes.c_double * 2)(*[float(v) for v in params]),
+                                       a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), float(T), float(cfl),
+                                       ctypes.byref(rid)))
+        return rid.value
+
+    def submit_workload(self, w, v0) -> int:
+        return self.submit(w.grid.n, w.grid.lo, w.grid.hi, (w.a_max, w.w_max), v0, w.T, w.cfl)
+
+    def tick(self):
+        c, r, q = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0)
+        _check(lib.hj_server_tick(self.handle, ctypes.byref(c), ctypes.byref(r), ctypes.byref(q)))
+        return c.value, r.value, q.value
+
+    def info(self, rid) -> hj_request_info:
+        info = hj_request_info()
+        _check(lib.hj_server_request_info(self.handle, int(rid), ctypes.byref(info)))
+        return info
+
+    def fetch(self, rid, shape):
+        out = np.empty(shape, dtype=np.float64)
+        _check(lib.hj_server_fetch(self.handle, int(rid), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                   out.size))
+        return out
+
+    def fetch_device(self, rid, out):
+        _check(lib.hj_server_fetch_device(self.handle, int(rid), ctypes.c_void_p(_dptr(out)), _dtype_code(out),
+                                          int(out.numel())))
+        return out
+
+    def clock(self) -> float:
+        return float(lib.hj_server_clock(self.handle))
+
+    def stats(self):
+        t, s = ctypes.c_int64(0), ctypes.c_int64(0)
+        _check(lib.hj_server_stats(self.handle, ctypes.byref(t), ctypes.byref(s)))
+        return t.value, s.value
+
+    def close(self):
+        if self.handle:
+            lib.hj_server_destroy(self.handle)
             self.handle = None
 
     def __enter__(self):

@@ -153,3 +153,52 @@ def custom_workload(n, n_circles: int = 4, n_rects: int = 0, T: float = 0.5, see
     rng = np.random.default_rng(seed)
     return Workload(f"custom{tuple(n)}", GridSpec(tuple(int(x) for x in n)), random_scene(rng, n_circles, n_rects),
                     T, seed, a_max, w_max, cfl)
+
+
+# ---------------------------------------------------------------- serving trace
+
+SERVING_SIZES = ((31, 31, 11, 16), (60, 60, 20, 36), (80, 80, 25, 40), (100, 100, 30, 48))
+SERVING_T = 0.5  # the paper's horizon (Sec. IV-A)
+
+
+@dataclass
+class Request:
+    """One re-solve request: arrival time (s), grid and the scene at that time."""
+    t_arrival: float
+    workload: Workload
+
+    def v0_xy(self) -> np.ndarray:
+        return signed_distance_xy(self.workload.grid, self.workload.scene)
+
+
+def perturb_scene(rng: np.random.Generator, scene: Scene, max_circles: int = 16) -> Scene:
+    """1-4 changes: shift an obstacle by up to 0.5 m, or add a circle of
+    radius 0.3-1.0 m (the oldest circle is dropped beyond max_circles)."""
+    s = scene.copy()
+    for _ in range(int(rng.integers(1, 5))):
+        if rng.random() < 0.5 and len(s.circles) > 0:
+            i = int(rng.integers(0, len(s.circles)))
+            ang, r = rng.uniform(0, 2 * np.pi), rng.uniform(0.0, 0.5)
+            s.circles[i, 0:2] = np.clip(s.circles[i, 0:2] + r * np.array([np.cos(ang), np.sin(ang)]), -4.5, 4.5)
+        else:
+            c = np.array([[*rng.uniform(-4.0, 4.0, size=2), rng.uniform(0.3, 1.0)]])
+            s.circles = np.concatenate([s.circles, c])[-max_circles:]
+    return s
+
+
+def serving_trace(rate_hz: float, duration_s: float, seed: int = SEED_BASE + 4, sizes=SERVING_SIZES,
+                  T: float = SERVING_T):
+    """Poisson arrivals at rate_hz for duration_s seconds; each request
+    perturbs the resident scene and asks for a re-solve on a grid drawn from
+    sizes."""
+    rng = np.random.default_rng(seed)
+    scene = random_scene(rng, 8)
+    t, out = 0.0, []
+    while True:
+        t += rng.exponential(1.0 / rate_hz)
+        if t > duration_s:
+            break
+        scene = perturb_scene(rng, scene)
+        n = sizes[int(rng.integers(0, len(sizes)))]
+        out.append(Request(t, Workload(f"req{len(out)}", GridSpec(tuple(n)), scene.copy(), T, seed)))
+    return out
