@@ -35,7 +35,7 @@ UNIT = "cell-updates/s"
 WORKLOAD = "car4d_128x128x64x96"
 BYTES_PER_UPDATE = {"f32": 12, "f64": 24}
 PROFILE = os.path.join(ROOT, "profiles", "hj_step_tiled_car4d_128x128x64x96.md")
-KERNEL_SOURCES = ["hj_step_tiled.cu", "hj_device.cuh"]
+KERNEL_SOURCES = ["hj_step_tiled.cu", "hj_device.cuh", "hj_tma.cuh"]
 # FP64 path: bound by the FP64 unit.  Algorithmic FP64 flops per cell-update:
 # 1 DMUL + 5 DFMA = 11; nominal GB300 FP64 rate 1.25 TFLOP/s (no measured FP64
 # figure in MEASURED_PEAKS.json).
@@ -296,6 +296,69 @@ def run_ours(args):
             "tile": tuned,
         }
 
+    # batched solves: the 64-instance workload (uneven grids, own obstacles,
+    # T = 1.5 s), V0 already on the device, one persistent kernel per batch step
+    batch = None
+    if not args.no_batch:
+        ws = scenes.batch_workloads()
+        v0d = [torch.from_numpy(scenes.initial_value(bw.grid, bw.scene)).to("cuda").reshape(-1) for bw in ws]
+        b = hj.Batch(len(ws), cuda_stream=stream.cuda_stream)
+        slots = [b.add_workload(bw) for bw in ws]
+        for sl, v in zip(slots, v0d):
+            hj.hj_batch_set_initial_value(b.handle, sl, v)
+        if args.batch_shape:
+            nc, ch = [int(v) for v in args.batch_shape.split(",")]
+            b.set_shape(nc, ch)
+        else:
+            nc, ch, _ = b.autotune(4)
+
+        def batch_solve():
+            for sl, v, bw in zip(slots, v0d, ws):
+                hj.hj_batch_set_initial_value(b.handle, sl, v)
+                b.set_horizon(sl, bw.T, bw.cfl)
+            return b.advance()
+
+        for _ in range(2):
+            batch_solve()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        kb = max(1, min(args.steps, 5))
+        e0.record(stream)
+        upd, adv_ms, bsteps = 0, 0.0, 0
+        for _ in range(kb):
+            st = batch_solve()
+            adv_ms += st.device_ms
+            bsteps += st.steps
+            upd += sum(int(np.prod(bw.grid.n)) * b.slot_info(sl).steps for sl, bw in zip(slots, ws))
+        e1.record(stream)
+        barrier()
+        bms = max_over_ranks(e0.elapsed_time(e1))
+        cells = sum(int(np.prod(bw.grid.n)) for bw in ws)
+        b.close()
+        batch = {"workload": "batch64: 64 car instances, N1,N2 in {40,50,60}, N3 in [16,24], N4 in [24,36], "
+                             "4-16 circles, T = 1.5 s, FP32",
+                 "value": world * upd / (bms * 1e-3), "unit": UNIT, "ms_per_solve": bms / kb,
+                 "cells": cells, "batch_steps_per_solve": bsteps // kb, "nconsumer": nc, "chunks": ch,
+                 "hbm_frac": 12 * (upd / kb) / (adv_ms / kb * 1e-3) / 1e9 / measured_peaks()[0]}
+
+    # serving: Poisson re-solve requests (each moves or adds 1-4 obstacles of
+    # a resident scene), T = 0.5 s, continuous batching vs the plain FP64 path
+    serving = None
+    if not args.no_serving and world == 1:
+        from paper_2012_04011_gb300 import serving as srv_mod
+        tr = scenes.serving_trace(args.serving_rate, args.serving_seconds, sizes=((60, 60, 20, 36),))
+        s32 = srv_mod.run_server(tr, cuda_stream=stream.cuda_stream)
+        s64 = srv_mod.run_plain_fp64(tr, cuda_stream=stream.cuda_stream)
+        mixed = srv_mod.run_server(scenes.serving_trace(args.serving_rate, args.serving_seconds),
+                                   cuda_stream=stream.cuda_stream)
+        serving = {"workload": f"60x60x20x36 re-solves, T = 0.5 s, Poisson {args.serving_rate:g} req/s for "
+                               f"{args.serving_seconds:g} s", "deadline_ms": 200.0,
+                   "fp32_batched": {k: s32[k] for k in ("requests", "latency_ms", "cell_updates_per_s")},
+                   "fp64_plain": {k: s64[k] for k in ("requests", "latency_ms", "cell_updates_per_s")},
+                   "mixed_sizes_fp32_batched": {"sizes": "31x31x11x16, 60x60x20x36, 80x80x25x40, 100x100x30x48",
+                                                **{k: mixed[k] for k in ("requests", "latency_ms",
+                                                                         "cell_updates_per_s")}}}
+
     # end to end through the C ABI with host buffers (pinned), copies timed
     e2e = None
     if not args.no_e2e:
@@ -356,6 +419,8 @@ def run_ours(args):
         "clocks": r32["clocks"],
         "gpu_launches": r32["launches"],
         "e2e": e2e,
+        "batch64": batch,
+        "serving": serving,
     }
     if "f64" in results:
         r64 = results["f64"]
@@ -399,6 +464,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--tile", default="", help="fixed tile shape ty,tv,xc,stages instead of autotuning")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--batch-shape", default="", help="fixed batch kernel shape nconsumer,chunks instead of autotuning")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serving-rate", type=float, default=40.0)
+    ap.add_argument("--serving-seconds", type=float, default=4.0)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("note: fewer than 3 warm-up steps", file=sys.stderr)
