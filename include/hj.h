@@ -105,6 +105,7 @@ typedef struct {
     int32_t threads;       /* threads per CTA */
     int32_t ctas;          /* CTAs per launch */
     double ms_per_step;    /* mean device time of one step kernel (CUDA events) */
+    double ms_retimed;     /* the second, longer trial's time (0: not re-timed) */
 } hj_tile_result;
 
 typedef struct {
@@ -195,7 +196,9 @@ HJ_API hj_status hj_set_kernel(hj_grid *g, hj_kernel kernel);
 HJ_API hj_status hj_set_tile_shape(hj_grid *g, const int32_t shape[4]);
 
 /* Autotune the tiled kernel: time steps_per_trial (>= 1) step launches for
- * each candidate tile shape and keep the fastest.  Must be called right
+ * each candidate tile shape, re-time the three fastest with three times the
+ * steps (their ms_retimed; this second pass needs results), and keep the
+ * fastest of those.  Must be called right
  * after hj_set_initial_value[_device] (no step taken yet): trial steps read
  * V0 and write only the ping-pong buffers, and the time-loop state is put
  * back afterwards, so the next solve is unchanged.  results (may be NULL)

@@ -33,7 +33,16 @@ struct HjDevState {
     unsigned int blocks_done;          // CTAs of the current step that have finished
     int status;                        // hj_status raised on the device (HJ_OK if none)
     int nonfinite;                     // ingest saw a NaN or Inf
-    int pad_;
+    int alpha_stale;                   // dynamics changed: the next prologue re-reduces alpha^max
+    double dt_scaled;                  // dt the FP64 dt-scaled coefficient table holds (0: none yet)
+};
+
+// FP64 coefficients with dt folded in (per (v, theta)): w1 = dt xdot_1/dx_1,
+// w2 = dt xdot_2/dx_2 (signed: the sign picks the upwind side), w0 = 1 - dt
+// (|xdot_1|/dx_1 + |xdot_2|/dx_2 + k3 + k4).  V_new = w0 V_c + |w1| V_up1 +
+// |w2| V_up2 + dt k3 V_up3 + dt k4 V_up4.
+struct HjScaledCoef {
+    double w1, w2, w0;
 };
 
 // Grid geometry handed to kernels by value.
@@ -70,6 +79,7 @@ struct hj_grid {
     void *v0;              // V0 (internal layout)
     void *buf;             // two ping-pong buffers, back to back (2*nint values)
     void *coef;            // HjCoef<T>[n3*n4]
+    HjScaledCoef *scaled;  // FP64 grids: dt-scaled coefficients [n3*n4]
     float *tab_tiled;      // tiled-kernel tables: v_k [n3], cos/dx1 [p4], sin/dx2 [p4], quad signs [p4]
     HjDevState *dstate;
     HjDevState *hstate;    // pinned host mirror
@@ -120,6 +130,20 @@ cudaError_t hj_launch_readback_f32(const float *src, void *dst, hj_precision dst
                                    long long nrows, cudaStream_t stream);
 cudaError_t hj_launch_prologue_f32(HjDevState *st, const HjGeom &g, const HjCoef<float> *coef, int ncoef, double T,
                                    double cfl, cudaStream_t stream);
+
+// Rescale the FP64 coefficient table for dt (all threads of one block call
+// it; the table covers ncoef entries).
+__device__ __forceinline__ void hj_rescale_table(HjScaledCoef *sc, const HjCoef<double> *coef, int ncoef, double dt)
+{
+    for (int i = threadIdx.x; i < ncoef; i += blockDim.x) {
+        const HjCoef<double> c = coef[i];
+        HjScaledCoef o;
+        o.w1 = dt * c.c1;
+        o.w2 = dt * c.c2;
+        o.w0 = 1.0 - dt * c.ks;
+        sc[i] = o;
+    }
+}
 
 // Batch internals for the server: pull all slot states once, then query the
 // host copy (done flag and step count of a slot).

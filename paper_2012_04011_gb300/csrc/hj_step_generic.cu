@@ -13,8 +13,10 @@
 // axis the bang-bang u_opt takes the sign of the costate, so V_up is
 // max(V+, V-).  Summing over axes:
 //     V_new = min(V0, V_c + dt * (sum_d K_d V_up,d - K_sum V_c)),
-// with K_d = |xdot_d| / dx_d.  In FP64 that is 1 DMUL + 5 DFMA per cell; the
-// FP32 variant keeps the differences (V_up - V_c) for accuracy.
+// with K_d = |xdot_d| / dx_d.  The FP64 variant folds dt into a per-(v, theta)
+// table (w0 = 1 - dt K_sum, w_d = dt K_d): 1 DMUL + 4 DFMA per cell, the
+// table rescaled by the last CTA only when dt changes.  The FP32 variant
+// keeps the differences (V_up - V_c) for accuracy.
 #include "hj_device.cuh"
 
 namespace {
@@ -89,10 +91,17 @@ __device__ __forceinline__ T upwind_value(const Neigh<T> &nb, int mode)
     return mode == HJ_AXIS_PLUS ? nb.p : nb.m;
 }
 
+// Magnitude without the FP64 unit: clear the sign bit.
+__device__ __forceinline__ double mag(double x)
+{
+    return __longlong_as_double(__double_as_longlong(x) & 0x7fffffffffffffffLL);
+}
+
 template <typename T, bool FAST32>
 __global__ void __launch_bounds__(256) hj_step_generic_kernel(const T *__restrict__ v0, T *__restrict__ buf,
-                                                               const HjCoef<T> *__restrict__ coef, HjDevState *st,
-                                                               const HjGeom g, long long nint, const Divisors dv)
+                                                               const HjCoef<T> *__restrict__ coef,
+                                                               HjScaledCoef *scaled, HjDevState *st, const HjGeom g,
+                                                               long long nint, const Divisors dv)
 {
     __shared__ unsigned long long scratch[64];
     if (st->done) return;  // uniform: written by the previous kernel on this stream
@@ -106,6 +115,9 @@ __global__ void __launch_bounds__(256) hj_step_generic_kernel(const T *__restric
     const long long s3 = g.p4, s2 = (long long)N3 * g.p4, s1 = (long long)N2 * s2;
     const unsigned long long ncell = (unsigned long long)N1 * N2 * N3 * N4;
     const T k3 = (T)g.k3, k4 = (T)g.k4;
+    // FP64: dt is folded into the per-(v, theta) table; the v/theta weights
+    // need it once per thread
+    const double k3dt = g.k3 * st->dt, k4dt = g.k4 * st->dt;
     unsigned long long am1 = 0ull, am2 = 0ull;
     float am1f = 0.f, am2f = 0.f;
 
@@ -139,20 +151,24 @@ __global__ void __launch_bounds__(256) hj_step_generic_kernel(const T *__restric
         const Neigh<T> nt = axis_neighbours<T>(vin, o, l, N4, 1, (g.periodic >> 3) & 1, vc);
 
         const HjCoef<T> cf = coef[k * N4 + l];
-        const T u1 = nonneg(cf.c1) ? nx.p : nx.m;
-        const T u2 = nonneg(cf.c2) ? ny.p : ny.m;
         const T u3 = upwind_value<T>(nv, g.mode3);
         const T u4 = upwind_value<T>(nt, g.mode4);
-        const T K1 = fabs(cf.c1), K2 = fabs(cf.c2);  // |.| is an operand modifier, no extra instruction
         T vn;
         if constexpr (sizeof(T) == 8) {
-            T r = -cf.ks * vc;
-            r = fma(K1, u1, r);
-            r = fma(K2, u2, r);
-            r = fma(k3, u3, r);
-            r = fma(k4, u4, r);
-            vn = fma(dt, r, vc);
+            // V_new = w0 V_c + |w1| V_up1 + |w2| V_up2 + dt k3 V_up3 + dt k4 V_up4:
+            // 1 DMUL + 4 DFMA; signs and magnitudes by integer operations
+            const HjScaledCoef sc = scaled[k * N4 + l];
+            const T u1 = nonneg(sc.w1) ? nx.p : nx.m;
+            const T u2 = nonneg(sc.w2) ? ny.p : ny.m;
+            T r = sc.w0 * vc;
+            r = fma(mag(sc.w1), u1, r);
+            r = fma(mag(sc.w2), u2, r);
+            r = fma(k3dt, u3, r);
+            vn = fma(k4dt, u4, r);
         } else {
+            const T u1 = nonneg(cf.c1) ? nx.p : nx.m;
+            const T u2 = nonneg(cf.c2) ? ny.p : ny.m;
+            const T K1 = fabs(cf.c1), K2 = fabs(cf.c2);
             T r = K1 * (u1 - vc);
             r = fmaf(K2, u2 - vc, r);
             r = fmaf(k3, u3 - vc, r);
@@ -175,8 +191,45 @@ __global__ void __launch_bounds__(256) hj_step_generic_kernel(const T *__restric
     if constexpr (sizeof(T) == 4) {
         am1 = hj_abits((double)am1f);
         am2 = hj_abits((double)am2f);
+        hj_step_epilogue(st, g, am1, am2, scratch);
+    } else {
+        // as hj_step_epilogue, and the last CTA also rescales the table when
+        // the next dt differs (the first step and the cut last step)
+        __shared__ int s_last;
+        am1 = hj_warp_max_u64(am1);
+        am2 = hj_warp_max_u64(am2);
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = (blockDim.x + 31) >> 5;
+        if (lane == 0) {
+            scratch[warp] = am1;
+            scratch[32 + warp] = am2;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int w = 1; w < nwarp; ++w) {
+                am1 = am1 > scratch[w] ? am1 : scratch[w];
+                am2 = am2 > scratch[32 + w] ? am2 : scratch[32 + w];
+            }
+            atomicMax(&st->alpha_bits[0], am1);
+            atomicMax(&st->alpha_bits[1], am2);
+            __threadfence();
+            const unsigned int prev = atomicAdd(&st->blocks_done, 1u);
+            s_last = prev == gridDim.x - 1;
+            if (s_last) hj_finalise(st, g);
+        }
+        __syncthreads();
+        if (s_last) {
+            const volatile HjDevState *vs = st;
+            const double dtn = vs->dt;
+            if (!vs->done && dtn != vs->dt_scaled) {
+                hj_rescale_table(scaled, (const HjCoef<double> *)coef, N3 * N4, dtn);
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    st->dt_scaled = dtn;
+                    __threadfence();
+                }
+            }
+        }
     }
-    hj_step_epilogue(st, g, am1, am2, scratch);
 }
 
 }  // namespace
@@ -196,9 +249,8 @@ cudaError_t hj_launch_step_generic(hj_grid *g)
     dv.n2 = make_fastdiv((uint32_t)g->n[1]);
     const bool fast = g->ncell < (1LL << 32);
 #define HJ_LAUNCH(T, F)                                                                                          \
-    hj_step_generic_kernel<T, F><<<blocks, threads, 0, g->stream>>>((const T *)g->v0, (T *)g->buf,              \
-                                                                    (const HjCoef<T> *)g->coef, g->dstate, g->geom, \
-                                                                    g->nint, dv)
+    hj_step_generic_kernel<T, F><<<blocks, threads, 0, g->stream>>>(                                       \
+        (const T *)g->v0, (T *)g->buf, (const HjCoef<T> *)g->coef, g->scaled, g->dstate, g->geom, g->nint, dv)
     if (g->prec == HJ_FP64) {
         if (fast) HJ_LAUNCH(double, true);
         else HJ_LAUNCH(double, false);

@@ -57,11 +57,12 @@ class hj_tile_result(ctypes.Structure):
         ("threads", ctypes.c_int32),
         ("ctas", ctypes.c_int32),
         ("ms_per_step", ctypes.c_double),
+        ("ms_retimed", ctypes.c_double),
     ]
 
     def as_dict(self) -> dict:
         return {"shape": list(self.shape), "threads": self.threads, "ctas": self.ctas,
-                "ms_per_step": self.ms_per_step}
+                "ms_per_step": self.ms_per_step, "ms_retimed": self.ms_retimed}
 
 
 class hj_grid_info(ctypes.Structure):

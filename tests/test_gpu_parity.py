@@ -186,6 +186,36 @@ def test_resume_equals_single_call(hj):
         assert np.array_equal(Va, Vb)
 
 
+def test_dynamics_change_mid_solve(hj):
+    """set_dynamics between two solve calls: the solve continues from V(t1)
+    under the new control bounds, with alpha^max and dt taken from the new
+    Hamiltonian (Alg. 2), as the oracle's advance does."""
+    w = scenes.workload("car4d_31x31x11x16")
+    V0 = scenes.initial_value(w.grid, w.scene)
+    t1, new = 0.37, (2.5, 0.4)
+    P1, P2 = oracle_problem(w), oracle_problem(w, params=new)
+    V1, _, d1 = oracle.advance(P1, V0, V0, 0.0, t1, w.cfl)
+    Vo, _, d2 = oracle.advance(P2, V0, V1, t1, w.T, w.cfl)
+    for prec in (hj.HJ_FP64, hj.HJ_FP32):
+        kernels = (hj.HJ_KERNEL_GENERIC,) if prec == hj.HJ_FP64 else (hj.HJ_KERNEL_GENERIC, hj.HJ_KERNEL_TILED)
+        for k in kernels:
+            with hj.Grid.for_workload(w, prec) as g:
+                g.set_kernel(k)
+                g.set_initial_value(V0)
+                g.solve_brt(t1, w.cfl)
+                g.set_dynamics(hj.HJ_DYN_CAR4D, new)
+                st = g.solve_brt(w.T, w.cfl)
+                V = g.read_value()
+            assert st.t_final == w.T
+            if prec == hj.HJ_FP64:
+                assert st.steps == len(d2) and st.dt_first == d2[0] and st.dt_last == d2[-1]
+                assert float(np.abs(V - Vo).max()) <= 1e-12
+            else:
+                assert abs(st.steps - len(d2)) <= 1
+                assert float(np.abs(V - Vo).max()) <= fp32_tol(V0)
+                assert sign_flips(V, Vo) == 0
+
+
 def test_zero_horizon_and_zero_dynamics(hj):
     w = scenes.workload("car4d_31x31x11x16")
     V0 = scenes.initial_value(w.grid, w.scene)
@@ -346,7 +376,13 @@ def test_autotune_keeps_results_and_state(hj):
         tried = g.autotune(4)
         assert len(tried) >= 1 and all(t.ms_per_step > 0 for t in tried)
         info = g.info()
-        best = min(tried, key=lambda t: t.ms_per_step)
+        # the kept shape is the fastest of the re-timed ones, which are the
+        # fastest of the first pass
+        retimed = [t for t in tried if t.ms_retimed > 0]
+        assert 1 <= len(retimed) <= 3
+        first = sorted(t.ms_per_step for t in tried)
+        assert all(t.ms_per_step <= first[len(retimed) - 1] for t in retimed)
+        best = min(retimed, key=lambda t: t.ms_retimed)
         assert list(info.tile) == list(best.shape)
         assert info.total_steps == 0 and info.t == 0.0
         st = g.solve_brt(w.T, w.cfl)
