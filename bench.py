@@ -52,6 +52,23 @@ def dist_env():
     return world, rank, local
 
 
+def rank_max(x: float, world: int, device: str = "cpu") -> float:
+    """Max of x over all ranks (each rank times its own replica; the job
+    takes as long as the slowest)."""
+    if world == 1:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world: int, units_per_rank: float, seconds_max: float) -> float:
+    """Whole-job rate: every rank processed units_per_rank (replicas, weak
+    scaling) in at most seconds_max."""
+    return world * units_per_rank / seconds_max
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -232,11 +249,7 @@ def run_ours(args):
         torch.cuda.synchronize()
 
     def max_over_ranks(x: float) -> float:
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return float(t.item())
+        return rank_max(x, world, "cuda")
 
     def solve_once(g, out):
         hj.hj_set_initial_value_device(g.handle, V0_dev)
@@ -287,9 +300,8 @@ def run_ours(args):
         ms = max_over_ranks(ev0.elapsed_time(ev1))
         kernel = g.info().kernel
         g.close()
-        updates = world * ncell * steps_total  # all ranks
         results[prec_name] = {
-            "ms_total": ms, "K": K, "value": updates / (ms * 1e-3), "ms_per_step": ms / K,
+            "ms_total": ms, "K": K, "value": job_throughput(world, ncell * steps_total, ms * 1e-3), "ms_per_step": ms / K,
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
             "avg_step_kernel_ms": loop_ms / steps_total, "time_steps_per_solve": steps_total // K,
             "launches": launches, "kernel": kernel, "clocks": sampler.summary() if sampler else None,
@@ -337,7 +349,7 @@ def run_ours(args):
         b.close()
         batch = {"workload": "batch64: 64 car instances, N1,N2 in {40,50,60}, N3 in [16,24], N4 in [24,36], "
                              "4-16 circles, T = 1.5 s, FP32",
-                 "value": world * upd / (bms * 1e-3), "unit": UNIT, "ms_per_solve": bms / kb,
+                 "value": job_throughput(world, upd, bms * 1e-3), "unit": UNIT, "ms_per_solve": bms / kb,
                  "cells": cells, "batch_steps_per_solve": bsteps // kb, "nconsumer": nc, "chunks": ch,
                  "hbm_frac": 12 * (upd / kb) / (adv_ms / kb * 1e-3) / 1e9 / measured_peaks()[0]}
 
@@ -387,7 +399,7 @@ def run_ours(args):
         barrier()
         el = max_over_ranks(time.perf_counter() - t0)
         g.close()
-        e2e = {"value": world * ncell * st_steps / el, "unit": UNIT,
+        e2e = {"value": job_throughput(world, ncell * st_steps, el), "unit": UNIT,
                "h2d_bytes_per_step": int(V0.nbytes), "d2h_bytes_per_step": int(h_out.numel() * 8),
                "ms_per_step": 1e3 * el / Ke}
 
