@@ -12,8 +12,10 @@ results).  This module only compiles it with gcc and marshals numpy arrays
 through ctypes.
 
 Parity status of each entry point (how it is pinned) is listed in the tests
-``tests/test_oracle_pins.py``; every function here is pinned by at least one
-closed form, invariant, textbook special case or paper number.
+``tests/test_oracle_pins.py`` (FP64 scheme) and
+``tests/test_oracle_q527_pins.py`` (Q5.27 fixed-point variant of Sec. III-C /
+Sec. IV-B); every function here is pinned by at least one closed form,
+invariant, textbook special case or paper number.
 """
 from __future__ import annotations
 
@@ -82,6 +84,16 @@ def _load():
         lib.hjo_advance.argtypes = [P, dp, dp, dp, ctypes.c_double, ctypes.c_double, ctypes.c_int64,
                                     dp, ctypes.c_int]
         lib.hjo_advance.restype = ctypes.c_int64
+        i32p = ctypes.POINTER(ctypes.c_int32)
+        lib.hjo_to_q527.argtypes = [dp, ctypes.c_int64, i32p]
+        lib.hjo_to_q527.restype = ctypes.c_int
+        lib.hjo_from_q527.argtypes = [i32p, ctypes.c_int64, dp]
+        lib.hjo_from_q527.restype = None
+        lib.hjo_advance_q527.argtypes = [P, i32p, i32p, dp, ctypes.c_double, ctypes.c_double, ctypes.c_int64,
+                                         dp, ctypes.c_int]
+        lib.hjo_advance_q527.restype = ctypes.c_int64
+        lib.hjo_step_cells_q527.argtypes = [P, i32p, i32p, ctypes.c_double, i64p, ctypes.c_int64, i32p]
+        lib.hjo_step_cells_q527.restype = ctypes.c_int
         lib.hjo_max_threads.argtypes = []
         lib.hjo_max_threads.restype = ctypes.c_int
         _lib = lib
@@ -200,3 +212,76 @@ def solve(P: Problem, V0, T: float, cfl: float = 0.8, nthreads: int = 1, max_ste
     """Whole BRT solve from t = 0 to T.  Returns (V(T), dts)."""
     V, _, dts = advance(P, V0, V0, 0.0, T, cfl, max_steps, nthreads)
     return V, dts
+
+
+# ---------------------------------------------------------------- Q5.27 fixed point
+# Sec. III-C / Sec. IV-B: V as 32-bit fixed point, 5 integer bits (sign
+# included) and 27 fractional bits.  The readings of the arithmetic are listed
+# in hj_oracle.c ("Q5.27 fixed-point variant").
+
+Q527_ULP = 2.0 ** -27
+
+
+def _ipt(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+
+
+def to_q527(x) -> np.ndarray:
+    """int32 codes of x: nearest (ties to even), saturated to the int32 range."""
+    x = np.ascontiguousarray(np.asarray(x, dtype=np.float64))
+    q = np.empty(x.shape, dtype=np.int32)
+    if _load().hjo_to_q527(_dptr(x), x.size, _ipt(q)):
+        raise ValueError("NaN or Inf cannot be converted to Q5.27")
+    return q
+
+
+def from_q527(q) -> np.ndarray:
+    """Exact FP64 values q * 2^-27."""
+    q = np.ascontiguousarray(np.asarray(q, dtype=np.int32))
+    x = np.empty(q.shape, dtype=np.float64)
+    _load().hjo_from_q527(_ipt(q), q.size, _dptr(x))
+    return x
+
+
+def _as_qgrid(P: Problem, a) -> np.ndarray:
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.int32))
+    if a.size != P.ncell:
+        raise ValueError(f"array has {a.size} values, grid has {P.ncell}")
+    return a.reshape(P.n)
+
+
+def advance_q527(P: Problem, Q0, Q, t: float, T: float, cfl: float = 0.8, max_steps: int = 1 << 40,
+                 nthreads: int = 1):
+    """Fixed-point advance of the int32 grid Q from t toward T.  Returns
+    (Q_new, t_new, dts)."""
+    Q0 = _as_qgrid(P, Q0)
+    Qw = _as_qgrid(P, Q).copy()
+    cap = int(min(max_steps, 1 << 20))
+    dts = np.zeros(cap)
+    tt = ctypes.c_double(float(t))
+    steps = _load().hjo_advance_q527(ctypes.byref(P._s), _ipt(Q0), _ipt(Qw), ctypes.byref(tt), float(T),
+                                     float(cfl), cap, _dptr(dts), int(nthreads))
+    if steps < 0:
+        raise MemoryError("oracle allocation failed")
+    return Qw, float(tt.value), dts[:steps].copy()
+
+
+def solve_q527(P: Problem, V0, T: float, cfl: float = 0.8, nthreads: int = 1, max_steps: int = 1 << 40):
+    """Fixed-point BRT solve from the FP64 V0 (converted to Q5.27) to T.
+    Returns (Q(T) as int32 codes, dts)."""
+    Q0 = to_q527(V0)
+    Q, _, dts = advance_q527(P, Q0, Q0, 0.0, T, cfl, max_steps, nthreads)
+    return Q, dts
+
+
+def step_cells_q527(P: Problem, Q, Q0, dt: float, cells) -> np.ndarray:
+    """One fixed-point step of size dt at flat cell indices."""
+    Q = _as_qgrid(P, Q)
+    Q0 = _as_qgrid(P, Q0)
+    cells = np.ascontiguousarray(np.asarray(cells, dtype=np.int64))
+    out = np.empty(cells.size, dtype=np.int32)
+    rc = _load().hjo_step_cells_q527(ctypes.byref(P._s), _ipt(Q), _ipt(Q0), float(dt),
+                                     cells.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), cells.size, _ipt(out))
+    if rc:
+        raise MemoryError("oracle allocation failed")
+    return out

@@ -358,3 +358,209 @@ int hjo_max_threads(void)
     return 1;
 #endif
 }
+
+/* ---- Q5.27 fixed-point variant ------------------------------------------
+ *
+ * Sec. III-C and Sec. IV-B: the FPGA holds V in 32-bit two's-complement
+ * fixed point with 5 integer bits (sign included) and 27 fractional bits,
+ * value = q * 2^-27, range [-16, 16), resolution 2^-27.  The paper fixes the
+ * data format only; the arithmetic inside the processing element is not
+ * given.  Readings (each a single place below):
+ *   - conversion from FP64: nearest, ties to even, saturated to the int32
+ *     range; NaN and Inf are rejected                         (hjo_to_q527)
+ *   - time step: the FP64 dt sequence of the FP64 scheme (the paper computes
+ *     dt once on the host, Sec. II-B); t stays FP64
+ *   - coefficients: each axis enters Algorithm 2 through dt |xdot_d| / dx_d
+ *     (D+-_d carry 1/dx_d, the Euler step carries dt), held as an unsigned
+ *     fixed-point weight with 30 fractional bits,
+ *     W_d = nearest-even(2^30 * (dt * (|xdot_d| / dx_d))),
+ *     and the sign of xdot_d                                  (q_weight)
+ *   - arithmetic: differences, H and the dissipation are exact integers in
+ *     units of 2^-27 * 2^-30 (nothing is rounded inside the cell); the Euler
+ *     increment dt (H + diss) is rounded once to 2^-27, half up
+ *     (floor(x + 1/2))                                        (q_cell)
+ *   - ghosts: the linear extrapolation of the FP64 scheme, exact in integers
+ *   - the BRT min against the converted V0, then saturation to the int32
+ *     range.
+ */
+
+typedef __int128 hjo_i128;
+
+/* floor(a / b) for b > 0 */
+static hjo_i128 floor_div(hjo_i128 a, hjo_i128 b)
+{
+    hjo_i128 q = a / b;
+    if (a % b != 0 && a < 0)
+        q -= 1;
+    return q;
+}
+
+/* Q5.27 code of x: nearest (ties to even), saturated.  Returns -1 for NaN
+ * or Inf, else 0. */
+int hjo_to_q527(const double *x, int64_t m, int32_t *q)
+{
+    for (int64_t i = 0; i < m; ++i) {
+        if (!isfinite(x[i]))
+            return -1;
+        double s = nearbyint(ldexp(x[i], 27));
+        if (s >= 2147483647.0)
+            q[i] = INT32_MAX;
+        else if (s <= -2147483648.0)
+            q[i] = INT32_MIN;
+        else
+            q[i] = (int32_t)s;
+    }
+    return 0;
+}
+
+void hjo_from_q527(const int32_t *q, int64_t m, double *x)
+{
+    for (int64_t i = 0; i < m; ++i)
+        x[i] = ldexp((double)q[i], -27);
+}
+
+/* Fixed-point weight of one axis: dt |xdot_d| / dx_d with 30 fractional bits. */
+static int64_t q_weight(double dt, double xdot_abs, double h)
+{
+    return (int64_t)nearbyint(ldexp(dt * (xdot_abs / h), 30));
+}
+
+static int64_t q_ghost_value(const hjo_problem *P, const hjo_tables *T, const int32_t *Q,
+                             int64_t c, const int idx[4], int d, int dir)
+{
+    int i = idx[d] + dir;
+    int N = P->n[d];
+    if (i >= 0 && i < N)
+        return Q[c + dir * T->stride[d]];
+    if (is_periodic(P, d)) {
+        int w = (i + N) % N;
+        return Q[c + (int64_t)(w - idx[d]) * T->stride[d]];
+    }
+    return 2 * (int64_t)Q[c] - (int64_t)Q[c - dir * T->stride[d]];
+}
+
+/* xdot_d of one cell before the control is chosen (the car's v, theta
+ * components; the constant field) and |xdot_d| for the CFL sum. */
+static void q_xdot_abs(const hjo_problem *P, const hjo_tables *T, const int idx[4], double a[4])
+{
+    if (P->dyn == HJO_DYN_CAR4D) {
+        double v = T->v[idx[2]];
+        a[0] = fabs(v * T->cos_th[idx[3]]);
+        a[1] = fabs(v * T->sin_th[idx[3]]);
+        a[2] = P->p[0];
+        a[3] = P->p[1];
+    } else {
+        for (int d = 0; d < 4; ++d)
+            a[d] = fabs(P->p[d]);
+    }
+}
+
+/* Algorithm 2, lines 3-9 for one cell in fixed point: returns V_{t+1}. */
+static int32_t q_cell(const hjo_problem *P, const hjo_tables *T, const int32_t *Q, const int32_t *Q0,
+                      int64_t c, const int idx[4], double dt)
+{
+    int64_t Vc = Q[c];
+    hjo_i128 twice = 0; /* 2 (H + diss) dt, units 2^-57 */
+    double xa[4];
+    q_xdot_abs(P, T, idx, xa);
+    for (int d = 0; d < 4; ++d) {
+        int64_t dm = Vc - q_ghost_value(P, T, Q, c, idx, d, -1); /* dx_d D-_d */
+        int64_t dp = q_ghost_value(P, T, Q, c, idx, d, +1) - Vc; /* dx_d D+_d */
+        int64_t W = q_weight(dt, xa[d], T->h[d]);                /* dt |xdot_d| / dx_d */
+        int sgn;                                                  /* sign of xdot_d */
+        if (P->dyn == HJO_DYN_CAR4D) {
+            if (d == 0)
+                sgn = T->v[idx[2]] * T->cos_th[idx[3]] >= 0.0 ? 1 : -1;
+            else if (d == 1)
+                sgn = T->v[idx[2]] * T->sin_th[idx[3]] >= 0.0 ? 1 : -1;
+            else /* bang-bang control: the bound with the sign of p_d (tie: upper) */
+                sgn = (dp + dm) >= 0 ? 1 : -1;
+        } else {
+            sgn = P->p[d] >= 0.0 ? 1 : -1;
+        }
+        /* H term p_d xdot_d = sgn W (D+ + D-)/2, dissipation W (D+ - D-)/2 */
+        twice += (hjo_i128)sgn * W * (dp + dm);
+        twice += (hjo_i128)W * (dp - dm);
+    }
+    /* twice is even: each axis contributes 2 W dp or -2 W dm */
+    hjo_i128 inc = floor_div(twice / 2 + ((hjo_i128)1 << 29), (hjo_i128)1 << 30);
+    hjo_i128 vn = (hjo_i128)Vc + inc;
+    if (vn > Q0[c])
+        vn = Q0[c];
+    if (vn < INT32_MIN)
+        vn = INT32_MIN;
+    return (int32_t)vn;
+}
+
+/* Advance the Q5.27 grid Q (in place) from *t toward T_end, at most
+ * max_steps steps; dts as in hjo_advance.  Returns the steps taken, or -1 on
+ * allocation failure. */
+int64_t hjo_advance_q527(const hjo_problem *P, const int32_t *Q0, int32_t *Q, double *t, double T_end,
+                         double cfl, int64_t max_steps, double *dts, int nthreads)
+{
+    int64_t ncell = hjo_cell_count(P);
+    hjo_tables T;
+    int32_t *Qn = (int32_t *)malloc(sizeof(int32_t) * (size_t)ncell);
+    if (!Qn || tables_init(P, &T)) {
+        free(Qn);
+        tables_free(&T);
+        return -1;
+    }
+    int N1 = P->n[0], N2 = P->n[1], N3 = P->n[2], N4 = P->n[3];
+    (void)nthreads;
+    int64_t s = 0;
+    while (*t < T_end && s < max_steps) {
+        /* alpha_d^max over the grid (Algorithm 1); |xdot_d| of the car does
+         * not depend on V */
+        double am[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int k = 0; k < N3; ++k)
+            for (int l = 0; l < N4; ++l) {
+                int idx[4] = {0, 0, k, l};
+                double xa[4];
+                q_xdot_abs(P, &T, idx, xa);
+                for (int d = 0; d < 4; ++d)
+                    am[d] = fmax(am[d], xa[d]);
+            }
+        double dt = hjo_cfl_dt(P, am, cfl);
+        int last = (dt == 0.0) || (*t + dt >= T_end);
+        if (last)
+            dt = T_end - *t;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) num_threads(nthreads > 0 ? nthreads : 1)
+#endif
+        for (int i = 0; i < N1; ++i)
+            for (int j = 0; j < N2; ++j)
+                for (int k = 0; k < N3; ++k)
+                    for (int l = 0; l < N4; ++l) {
+                        int idx[4] = {i, j, k, l};
+                        int64_t c = ((((int64_t)i * N2 + j) * N3 + k) * N4) + l;
+                        Qn[c] = q_cell(P, &T, Q, Q0, c, idx, dt);
+                    }
+        memcpy(Q, Qn, sizeof(int32_t) * (size_t)ncell);
+        if (dts)
+            dts[s] = dt;
+        *t = last ? T_end : *t + dt;
+        ++s;
+    }
+    free(Qn);
+    tables_free(&T);
+    return s;
+}
+
+/* One fixed-point step of size dt at the listed cells (sampled parity). */
+int hjo_step_cells_q527(const hjo_problem *P, const int32_t *Q, const int32_t *Q0, double dt,
+                        const int64_t *cells, int64_t m, int32_t *out)
+{
+    hjo_tables T;
+    if (tables_init(P, &T)) {
+        tables_free(&T);
+        return -1;
+    }
+    for (int64_t q = 0; q < m; ++q) {
+        int idx[4];
+        unflatten(P, cells[q], idx);
+        out[q] = q_cell(P, &T, Q, Q0, cells[q], idx, dt);
+    }
+    tables_free(&T);
+    return 0;
+}
