@@ -66,7 +66,20 @@ typedef enum {
     HJ_ERR_UNSUPPORTED = 7  /* valid request this build does not implement */
 } hj_status;
 
-typedef enum { HJ_FP64 = 0, HJ_FP32 = 1 } hj_precision;
+/* Arithmetic of the value function on the device (and the element type of
+ * device arrays passed with a dtype).
+ *   HJ_FP64, HJ_FP32: IEEE double / float.
+ *   HJ_Q527: the FPGA's fixed-point format (Sec. III-C, Sec. IV-B): int32
+ *     codes q with value q * 2^-27 (5 integer bits including the sign, 27
+ *     fractional bits; range [-16, 16), resolution 2^-27).  Conversion from
+ *     floating point: nearest, ties to even, saturated to the int32 range;
+ *     conversion back is exact.  One step per cell: the upwind differences,
+ *     H and the dissipation of Algorithm 2 are exact integers; each axis is
+ *     weighted by dt |xdot_d| / dx_d held with 30 fractional bits (nearest,
+ *     ties to even, from the FP64 dt); the Euler increment is rounded once
+ *     to 2^-27, half up; then the BRT min with V0 and saturation.  dt and t
+ *     are FP64 as for the other precisions. */
+typedef enum { HJ_FP64 = 0, HJ_FP32 = 1, HJ_Q527 = 2 } hj_precision;
 
 typedef enum {
     /* Sec. IV-A car with the heading rate as a bounded control:
@@ -83,7 +96,7 @@ typedef enum {
 typedef enum {
     HJ_KERNEL_AUTO = 0,
     HJ_KERNEL_GENERIC = 1, /* one thread per cell, loads through L1/L2 */
-    HJ_KERNEL_TILED = 2    /* FP32: TMA-staged 4D tiles streamed along x */
+    HJ_KERNEL_TILED = 2    /* FP32, Q5.27: TMA-staged 4D tiles streamed along x */
 } hj_kernel;
 
 typedef struct {
@@ -159,9 +172,9 @@ HJ_API hj_status hj_set_initial_value(hj_grid *g, const double *v0, size_t count
 HJ_API hj_status hj_set_initial_value_xy(hj_grid *g, const double *v0_xy, size_t count);
 
 /* As hj_set_initial_value, from a DEVICE array (dtype HJ_FP64 = double,
- * HJ_FP32 = float) of count values on the grid's device, dense layout
- * above.  The array is read on the grid's stream; the caller keeps
- * ownership. */
+ * HJ_FP32 = float, HJ_Q527 = int32 codes) of count values on the grid's
+ * device, dense layout above, converted to the grid's precision.  The array
+ * is read on the grid's stream; the caller keeps ownership. */
 HJ_API hj_status hj_set_initial_value_device(hj_grid *g, const void *v0_device, hj_precision dtype,
                                       size_t count);
 
@@ -176,12 +189,13 @@ HJ_API hj_status hj_advance_brt(hj_grid *g, double T, double cfl, int64_t max_st
                          hj_solve_stats *stats);
 
 /* Copy the current V into a HOST buffer of count = N1*N2*N3*N4 doubles
- * (caller-owned), layout above. */
+ * (caller-owned), layout above (exact for every precision). */
 HJ_API hj_status hj_read_value(const hj_grid *g, double *out, size_t count);
 
 /* Copy the current V into a DEVICE buffer of count values of dtype
- * (HJ_FP64 or HJ_FP32), layout above; caller-owned.  Runs on the grid's
- * stream; returns once the copy is queued and completed. */
+ * (HJ_FP64, HJ_FP32 or HJ_Q527), layout above, converted from the grid's
+ * precision as for the ingest; caller-owned.  Runs on the grid's stream;
+ * returns once the copy is queued and completed. */
 HJ_API hj_status hj_read_value_device(const hj_grid *g, void *out_device, hj_precision dtype,
                                size_t count);
 

@@ -14,6 +14,7 @@
 #include <string.h>
 
 #include <new>
+#include <type_traits>
 
 #include "hj_device.cuh"
 
@@ -42,6 +43,22 @@ hj_status set_err(hj_status s, const char *fmt, ...)
 
 // ---------------------------------------------------------------- kernels
 
+// Element conversions of the ingest and readback kernels: int32_t stands for
+// Q5.27 codes (nearest-even and saturating from FP64, exact back to FP64).
+template <typename T>
+__device__ __forceinline__ double elem_to_f64(T v)
+{
+    if constexpr (std::is_same<T, int32_t>::value) return hj_q527_to_f64(v);
+    else return (double)v;
+}
+
+template <typename T>
+__device__ __forceinline__ T elem_from_f64(double x)
+{
+    if constexpr (std::is_same<T, int32_t>::value) return hj_q527_from_f64(x);
+    else return (T)x;
+}
+
 // Dense row-major [N1][N2][N3][N4] (any of double/float) -> internal layout
 // (rows padded to p4, pad lanes zero).  Flags non-finite input.
 template <typename Tin, typename T>
@@ -56,9 +73,9 @@ __global__ void ingest_kernel(const Tin *__restrict__ src, T *__restrict__ dst, 
         int l = (int)(i - row * p4);
         T v = T(0);
         if (l < n4) {
-            double x = (double)src[row * n4 + l];
+            double x = elem_to_f64<Tin>(src[row * n4 + l]);
             if (!isfinite(x)) bad = 1;
-            v = (T)x;
+            v = elem_from_f64<T>(x);
         }
         dst[i] = v;
     }
@@ -81,7 +98,7 @@ __global__ void ingest_xy_kernel(const double *__restrict__ src, T *__restrict__
         if (l < n4) {
             const double x = src[xy];
             if (!isfinite(x)) bad = 1;
-            v = (T)x;
+            v = elem_from_f64<T>(x);
         }
         dst[i] = v;
     }
@@ -98,7 +115,7 @@ __global__ void readback_kernel(const T *__restrict__ src, Tout *__restrict__ ds
          i += (long long)gridDim.x * blockDim.x) {
         long long row = i / n4;
         int l = (int)(i - row * n4);
-        dst[i] = (Tout)src[(row0 + row) * p4 + l];
+        dst[i] = elem_from_f64<Tout>(elem_to_f64<T>(src[(row0 + row) * p4 + l]));
     }
 }
 
@@ -108,7 +125,7 @@ __global__ void readback_kernel(const T *__restrict__ src, Tout *__restrict__ ds
 // velocity depends only on v and theta).
 template <typename T>
 __global__ void prologue_kernel(HjDevState *st, const HjGeom g, const HjCoef<T> *__restrict__ coef, int ncoef,
-                                double T_end, double cfl, HjScaledCoef *scaled = nullptr)
+                                double T_end, double cfl, HjScaledCoef *scaled = nullptr, int32_t *qw = nullptr)
 {
     __shared__ unsigned long long scratch[64];
     unsigned long long a1 = 0ull, a2 = 0ull;
@@ -153,12 +170,13 @@ __global__ void prologue_kernel(HjDevState *st, const HjGeom g, const HjCoef<T> 
         else
             st->done = 1;
     }
-    if (scaled) {  // FP64 grids: the dt-scaled table must match the first dt
+    if (scaled || qw) {  // FP64 / Q5.27 grids: the dt-scaled tables must match the first dt
         __syncthreads();
         const volatile HjDevState *vs = st;
         const double dt = vs->dt;
         if (!vs->done && dt != vs->dt_scaled) {
-            hj_rescale_table(scaled, (const HjCoef<double> *)coef, ncoef, dt);
+            if (scaled) hj_rescale_table(scaled, (const HjCoef<double> *)coef, ncoef, dt);
+            else hj_rescale_qweights(qw, (const HjCoef<double> *)coef, g.n3, g.n4, g.p4, g.k3, g.k4, dt);
             __syncthreads();
             if (threadIdx.x == 0) st->dt_scaled = dt;
         }
@@ -233,7 +251,7 @@ hj_status upload_tables(hj_grid *g)
     }
     const double k3 = g->geom.k3, k4 = g->geom.k4;
     hj_status st = HJ_OK;
-    if (g->prec == HJ_FP64) {
+    if (g->prec != HJ_FP32) {
         HjCoef<double> *c = (HjCoef<double> *)malloc(sizeof(HjCoef<double>) * nco);
         if (!c) st = set_err(HJ_ERR_OOM, "host allocation failed");
         for (size_t i = 0; c && i < nco; ++i) {
@@ -297,6 +315,31 @@ hj_status launch_step(hj_grid *g, hj_kernel k)
     return HJ_OK;
 }
 
+// Calls f with a value of the grid element type: double, float or int32_t
+// (Q5.27 codes).
+template <typename F>
+void with_elem(hj_precision p, F &&f)
+{
+    if (p == HJ_FP64) f(double(0));
+    else if (p == HJ_FP32) f(float(0));
+    else f(int32_t(0));
+}
+
+bool valid_prec(hj_precision p) { return p == HJ_FP64 || p == HJ_FP32 || p == HJ_Q527; }
+
+// Start of a solve call (horizon, Courant number, first dt, and the FP64 /
+// fixed-point tables scaled for it).
+void launch_prologue(hj_grid *g, double T, double cfl)
+{
+    const int ncoef = g->n[2] * g->n[3];
+    if (g->prec == HJ_FP32)
+        prologue_kernel<float><<<1, 256, 0, g->stream>>>(g->dstate, g->geom, (const HjCoef<float> *)g->coef, ncoef, T,
+                                                         cfl);
+    else
+        prologue_kernel<double><<<1, 256, 0, g->stream>>>(g->dstate, g->geom, (const HjCoef<double> *)g->coef, ncoef,
+                                                          T, cfl, g->scaled, g->qw);
+}
+
 void free_grid(hj_grid *g)
 {
     if (!g) return;
@@ -305,6 +348,7 @@ void free_grid(hj_grid *g)
     if (g->coef) cudaFree(g->coef);
     if (g->tab_tiled) cudaFree(g->tab_tiled);
     if (g->scaled) cudaFree(g->scaled);
+    if (g->qw) cudaFree(g->qw);
     if (g->dstate) cudaFree(g->dstate);
     if (g->hstate) cudaFreeHost(g->hstate);
     for (int i = 0; i < 4; ++i)
@@ -384,7 +428,7 @@ hj_status hj_create_grid(const int32_t n[4], const double lo[4], const double hi
 {
     g_err[0] = 0;
     if (!n || !lo || !hi || !out) return set_err(HJ_ERR_INVALID_ARG, "NULL argument");
-    if (prec != HJ_FP64 && prec != HJ_FP32) return set_err(HJ_ERR_INVALID_ARG, "unknown precision %d", (int)prec);
+    if (!valid_prec(prec)) return set_err(HJ_ERR_INVALID_ARG, "unknown precision %d", (int)prec);
     if (periodic_mask & ~0xFu) return set_err(HJ_ERR_INVALID_ARG, "periodic_mask has bits above 3");
     long long ncell = 1;
     for (int d = 0; d < 4; ++d) {
@@ -409,7 +453,7 @@ hj_status hj_create_grid(const int32_t n[4], const double lo[4], const double hi
     g->p4 = (n[3] + 3) / 4 * 4;
     g->periodic = periodic_mask;
     g->prec = prec;
-    g->esize = prec == HJ_FP64 ? 8 : 4;
+    g->esize = prec == HJ_FP64 ? 8 : 4;  // FP32 and Q5.27: 4 bytes
     g->ncell = ncell;
     g->nint = (long long)n[0] * n[1] * n[2] * g->p4;
     g->kernel_req = HJ_KERNEL_AUTO;
@@ -425,9 +469,13 @@ hj_status hj_create_grid(const int32_t n[4], const double lo[4], const double hi
     size_t ncoef = (size_t)n[2] * n[3];
     if (e == cudaSuccess) e = cudaMalloc(&g->v0, arr);
     if (e == cudaSuccess) e = cudaMalloc(&g->buf, 2 * arr);
-    if (e == cudaSuccess) e = cudaMalloc(&g->coef, ncoef * (prec == HJ_FP64 ? sizeof(HjCoef<double>) : sizeof(HjCoef<float>)));
+    // FP64 coefficients for FP64 and Q5.27 grids (alpha^max and dt are FP64)
+    const size_t coef_bytes = ncoef * (prec == HJ_FP32 ? sizeof(HjCoef<float>) : sizeof(HjCoef<double>));
+    const size_t qw_bytes = prec == HJ_Q527 ? sizeof(int32_t) * (2 * (size_t)n[2] * g->p4 + 4) : 0;
+    if (e == cudaSuccess) e = cudaMalloc(&g->coef, coef_bytes);
     if (e == cudaSuccess) e = cudaMalloc(&g->tab_tiled, sizeof(float) * ((size_t)n[2] + 3 * (size_t)g->p4));
     if (e == cudaSuccess && prec == HJ_FP64) e = cudaMalloc(&g->scaled, ncoef * sizeof(HjScaledCoef));
+    if (e == cudaSuccess && prec == HJ_Q527) e = cudaMalloc(&g->qw, qw_bytes);
     if (e == cudaSuccess) e = cudaMalloc(&g->dstate, sizeof(HjDevState));
     if (e == cudaSuccess) e = cudaHostAlloc(&g->hstate, sizeof(HjDevState), cudaHostAllocDefault);
     for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaEventCreate(&g->ev[i]);
@@ -437,7 +485,7 @@ hj_status hj_create_grid(const int32_t n[4], const double lo[4], const double hi
         free_grid(g);
         return s;
     }
-    g->device_bytes = 3 * arr + ncoef * (prec == HJ_FP64 ? sizeof(HjCoef<double>) : sizeof(HjCoef<float>)) +
+    g->device_bytes = 3 * arr + coef_bytes + qw_bytes + (prec == HJ_FP64 ? ncoef * sizeof(HjScaledCoef) : 0) +
                       sizeof(HjDevState);
     hj_status s = reset_state(g);
     if (s == HJ_OK) {
@@ -547,10 +595,10 @@ hj_status hj_set_initial_value(hj_grid *g, const double *v0, size_t count)
     long long nrows = (long long)g->n[0] * g->n[1] * g->n[2];
     int *flag = &g->dstate->nonfinite;
     int blocks = grid_blocks(g->nint, 256);
-    if (g->prec == HJ_FP64)
-        ingest_kernel<double, double><<<blocks, 256, 0, g->stream>>>(staging, (double *)g->v0, g->n[3], g->p4, nrows, flag);
-    else
-        ingest_kernel<double, float><<<blocks, 256, 0, g->stream>>>(staging, (float *)g->v0, g->n[3], g->p4, nrows, flag);
+    with_elem(g->prec, [&](auto e) {
+        using T = decltype(e);
+        ingest_kernel<double, T><<<blocks, 256, 0, g->stream>>>(staging, (T *)g->v0, g->n[3], g->p4, nrows, flag);
+    });
     return finish_ingest(g);
 }
 
@@ -568,12 +616,10 @@ hj_status hj_set_initial_value_xy(hj_grid *g, const double *v0_xy, size_t count)
     HJ_CUDA(cudaMemcpyAsync(staging, v0_xy, sizeof(double) * (size_t)nxy, cudaMemcpyHostToDevice, g->stream));
     int *flag = &g->dstate->nonfinite;
     const int blocks = grid_blocks(g->nint, 256);
-    if (g->prec == HJ_FP64)
-        ingest_xy_kernel<double><<<blocks, 256, 0, g->stream>>>(staging, (double *)g->v0, g->n[2], g->n[3], g->p4, nxy,
-                                                              flag);
-    else
-        ingest_xy_kernel<float><<<blocks, 256, 0, g->stream>>>(staging, (float *)g->v0, g->n[2], g->n[3], g->p4, nxy,
-                                                             flag);
+    with_elem(g->prec, [&](auto e) {
+        using T = decltype(e);
+        ingest_xy_kernel<T><<<blocks, 256, 0, g->stream>>>(staging, (T *)g->v0, g->n[2], g->n[3], g->p4, nxy, flag);
+    });
     return finish_ingest(g);
 }
 
@@ -583,7 +629,7 @@ hj_status hj_set_initial_value_device(hj_grid *g, const void *v0_device, hj_prec
     hj_status s = check_grid(g);
     if (s != HJ_OK) return s;
     if (!v0_device) return set_err(HJ_ERR_INVALID_ARG, "v0_device is NULL");
-    if (dtype != HJ_FP64 && dtype != HJ_FP32) return set_err(HJ_ERR_INVALID_ARG, "unknown dtype");
+    if (!valid_prec(dtype)) return set_err(HJ_ERR_INVALID_ARG, "unknown dtype");
     if (count != (size_t)g->ncell)
         return set_err(HJ_ERR_INVALID_ARG, "count %zu != N1*N2*N3*N4 = %lld", count, g->ncell);
     if ((s = activate(g)) != HJ_OK) return s;
@@ -591,21 +637,14 @@ hj_status hj_set_initial_value_device(hj_grid *g, const void *v0_device, hj_prec
     long long nrows = (long long)g->n[0] * g->n[1] * g->n[2];
     int *flag = &g->dstate->nonfinite;
     int blocks = grid_blocks(g->nint, 256);
-    if (g->prec == HJ_FP64) {
-        if (dtype == HJ_FP64)
-            ingest_kernel<double, double><<<blocks, 256, 0, g->stream>>>((const double *)v0_device, (double *)g->v0,
-                                                                         g->n[3], g->p4, nrows, flag);
-        else
-            ingest_kernel<float, double><<<blocks, 256, 0, g->stream>>>((const float *)v0_device, (double *)g->v0,
-                                                                        g->n[3], g->p4, nrows, flag);
-    } else {
-        if (dtype == HJ_FP64)
-            ingest_kernel<double, float><<<blocks, 256, 0, g->stream>>>((const double *)v0_device, (float *)g->v0,
-                                                                        g->n[3], g->p4, nrows, flag);
-        else
-            ingest_kernel<float, float><<<blocks, 256, 0, g->stream>>>((const float *)v0_device, (float *)g->v0,
-                                                                       g->n[3], g->p4, nrows, flag);
-    }
+    with_elem(dtype, [&](auto ein) {
+        with_elem(g->prec, [&](auto e) {
+            using Tin = decltype(ein);
+            using T = decltype(e);
+            ingest_kernel<Tin, T><<<blocks, 256, 0, g->stream>>>((const Tin *)v0_device, (T *)g->v0, g->n[3], g->p4,
+                                                                 nrows, flag);
+        });
+    });
     return finish_ingest(g);
 }
 
@@ -624,12 +663,7 @@ hj_status hj_advance_brt(hj_grid *g, double T, double cfl, int64_t max_steps, hj
     const hj_kernel kern = effective_kernel(g);
     int launches = 0;
     HJ_CUDA(cudaEventRecord(g->ev[0], g->stream));
-    const int ncoef = g->n[2] * g->n[3];
-    if (g->prec == HJ_FP64)
-        prologue_kernel<double><<<1, 256, 0, g->stream>>>(g->dstate, g->geom, (const HjCoef<double> *)g->coef, ncoef, T, cfl,
-                                                          g->scaled);
-    else
-        prologue_kernel<float><<<1, 256, 0, g->stream>>>(g->dstate, g->geom, (const HjCoef<float> *)g->coef, ncoef, T, cfl);
+    launch_prologue(g, T, cfl);
     ++launches;
     HJ_CUDA(cudaGetLastError());
     if ((s = pull_state(g)) != HJ_OK) return s;
@@ -724,12 +758,11 @@ hj_status hj_read_value(const hj_grid *gc, double *out, size_t count)
     for (long long r0 = 0; r0 < nrows; r0 += rows_per_chunk) {
         long long nr = nrows - r0 < rows_per_chunk ? nrows - r0 : rows_per_chunk;
         int blocks = grid_blocks(nr * g->n[3], 256);
-        if (g->prec == HJ_FP64)
-            readback_kernel<double, double><<<blocks, 256, 0, g->stream>>>((const double *)src, (double *)free_buf,
-                                                                           g->n[3], g->p4, r0, nr);
-        else
-            readback_kernel<float, double><<<blocks, 256, 0, g->stream>>>((const float *)src, (double *)free_buf,
-                                                                          g->n[3], g->p4, r0, nr);
+        with_elem(g->prec, [&](auto e) {
+            using T = decltype(e);
+            readback_kernel<T, double><<<blocks, 256, 0, g->stream>>>((const T *)src, (double *)free_buf, g->n[3],
+                                                                      g->p4, r0, nr);
+        });
         HJ_CUDA(cudaGetLastError());
         HJ_CUDA(cudaMemcpyAsync(out + r0 * g->n[3], free_buf, sizeof(double) * (size_t)(nr * g->n[3]),
                                 cudaMemcpyDeviceToHost, g->stream));
@@ -745,7 +778,7 @@ hj_status hj_read_value_device(const hj_grid *gc, void *out_device, hj_precision
     hj_status s = check_grid(g);
     if (s != HJ_OK) return s;
     if (!out_device) return set_err(HJ_ERR_INVALID_ARG, "out_device is NULL");
-    if (dtype != HJ_FP64 && dtype != HJ_FP32) return set_err(HJ_ERR_INVALID_ARG, "unknown dtype");
+    if (!valid_prec(dtype)) return set_err(HJ_ERR_INVALID_ARG, "unknown dtype");
     if (count != (size_t)g->ncell)
         return set_err(HJ_ERR_INVALID_ARG, "count %zu != N1*N2*N3*N4 = %lld", count, g->ncell);
     if (!g->has_value) return set_err(HJ_ERR_STATE, "no initial value (hj_set_initial_value)");
@@ -754,21 +787,14 @@ hj_status hj_read_value_device(const hj_grid *gc, void *out_device, hj_precision
     const void *src = hj_value_ptr(g, g->hstate->n);
     const long long nrows = (long long)g->n[0] * g->n[1] * g->n[2];
     int blocks = grid_blocks(g->ncell, 256);
-    if (g->prec == HJ_FP64) {
-        if (dtype == HJ_FP64)
-            readback_kernel<double, double><<<blocks, 256, 0, g->stream>>>((const double *)src, (double *)out_device,
-                                                                           g->n[3], g->p4, 0, nrows);
-        else
-            readback_kernel<double, float><<<blocks, 256, 0, g->stream>>>((const double *)src, (float *)out_device,
-                                                                          g->n[3], g->p4, 0, nrows);
-    } else {
-        if (dtype == HJ_FP64)
-            readback_kernel<float, double><<<blocks, 256, 0, g->stream>>>((const float *)src, (double *)out_device,
-                                                                          g->n[3], g->p4, 0, nrows);
-        else
-            readback_kernel<float, float><<<blocks, 256, 0, g->stream>>>((const float *)src, (float *)out_device,
-                                                                         g->n[3], g->p4, 0, nrows);
-    }
+    with_elem(g->prec, [&](auto e) {
+        with_elem(dtype, [&](auto eout) {
+            using T = decltype(e);
+            using Tout = decltype(eout);
+            readback_kernel<T, Tout><<<blocks, 256, 0, g->stream>>>((const T *)src, (Tout *)out_device, g->n[3], g->p4,
+                                                                    0, nrows);
+        });
+    });
     HJ_CUDA(cudaGetLastError());
     HJ_CUDA(cudaStreamSynchronize(g->stream));
     return HJ_OK;
@@ -782,8 +808,8 @@ hj_status hj_set_kernel(hj_grid *g, hj_kernel kernel)
     if (kernel != HJ_KERNEL_AUTO && kernel != HJ_KERNEL_GENERIC && kernel != HJ_KERNEL_TILED)
         return set_err(HJ_ERR_INVALID_ARG, "unknown kernel %d", (int)kernel);
     if (kernel == HJ_KERNEL_TILED && !g->tiled_ok)
-        return set_err(HJ_ERR_UNSUPPORTED, "the tiled kernel does not support this grid (FP32 car grids with "
-                                           "periodic theta only; set the dynamics first)");
+        return set_err(HJ_ERR_UNSUPPORTED, "the tiled kernel does not support this grid (FP32 or Q5.27 car grids "
+                                           "with periodic theta only; set the dynamics first)");
     g->kernel_req = kernel;
     return HJ_OK;
 }
@@ -868,8 +894,7 @@ hj_status hj_autotune(hj_grid *g, int32_t steps_per_trial, hj_tile_result *resul
     auto run_steps = [&](int k) -> hj_status {
         *g->hstate = saved;
         HJ_CUDA(cudaMemcpyAsync(g->dstate, g->hstate, sizeof(HjDevState), cudaMemcpyHostToDevice, g->stream));
-        prologue_kernel<float><<<1, 256, 0, g->stream>>>(g->dstate, g->geom, (const HjCoef<float> *)g->coef, ncoef,
-                                                         1e300, 0.8);
+        launch_prologue(g, 1e300, 0.8);
         HJ_CUDA(cudaGetLastError());
         HJ_CUDA(cudaEventRecord(g->ev[1], g->stream));
         for (int i = 0; i < k; ++i) {

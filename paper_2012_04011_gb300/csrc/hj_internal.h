@@ -80,6 +80,7 @@ struct hj_grid {
     void *buf;             // two ping-pong buffers, back to back (2*nint values)
     void *coef;            // HjCoef<T>[n3*n4]
     HjScaledCoef *scaled;  // FP64 grids: dt-scaled coefficients [n3*n4]
+    int32_t *qw;           // Q5.27 grids: fixed-point axis weights (hj_rescale_qweights)
     float *tab_tiled;      // tiled-kernel tables: v_k [n3], cos/dx1 [p4], sin/dx2 [p4], quad signs [p4]
     HjDevState *dstate;
     HjDevState *hstate;    // pinned host mirror
@@ -143,6 +144,71 @@ __device__ __forceinline__ void hj_rescale_table(HjScaledCoef *sc, const HjCoef<
         o.w0 = 1.0 - dt * c.ks;
         sc[i] = o;
     }
+}
+
+// ---- Q5.27 fixed point (Sec. III-C, Sec. IV-B): int32 codes q, value q 2^-27
+
+constexpr double HJ_Q527_SCALE = 134217728.0;  // 2^27
+constexpr double HJ_QW_SCALE = 1073741824.0;   // 2^30: fractional bits of the axis weights
+
+// Code of x: nearest, ties to even, saturated to the int32 range.
+__device__ __forceinline__ int32_t hj_q527_from_f64(double x)
+{
+    const long long q = __double2ll_rn(__dmul_rn(x, HJ_Q527_SCALE));  // the product is exact
+    return (int32_t)(q > 2147483647LL ? 2147483647LL : (q < -2147483648LL ? -2147483648LL : q));
+}
+
+// Exact value of a code.
+__device__ __forceinline__ double hj_q527_to_f64(int32_t q) { return (double)q * (1.0 / HJ_Q527_SCALE); }
+
+// Axis weight dt k (k = |xdot_d| / dx_d) with 30 fractional bits: nearest,
+// ties to even, of the FP64 product (dt k <= Courant number <= 1).
+__device__ __forceinline__ int32_t hj_qweight(double dt, double k)
+{
+    return (int32_t)__double2ll_rn(__dmul_rn(__dmul_rn(dt, k), HJ_QW_SCALE));
+}
+
+// Fixed-point weights for dt (all threads of one block call it):
+//   qw[k p4 + l]            x weight of (v_k, theta_l), signed with xdot_1
+//   qw[n3 p4 + k p4 + l]    y weight, signed with xdot_2
+//   qw[2 n3 p4 + 0 / 1]     v and theta weights (constant over the grid)
+// Pad lanes (l >= n4) get 0.
+__device__ __forceinline__ void hj_rescale_qweights(int32_t *qw, const HjCoef<double> *coef, int n3, int n4, int p4,
+                                                    double k3, double k4, double dt)
+{
+    const int tot = n3 * p4;
+    for (int i = threadIdx.x; i < tot; i += blockDim.x) {
+        const int k = i / p4, l = i - (i / p4) * p4;
+        int32_t w1 = 0, w2 = 0;
+        if (l < n4) {
+            const HjCoef<double> c = coef[k * n4 + l];
+            w1 = hj_qweight(dt, fabs(c.c1));
+            w2 = hj_qweight(dt, fabs(c.c2));
+            if (c.c1 < 0.0) w1 = -w1;
+            if (c.c2 < 0.0) w2 = -w2;
+        }
+        qw[i] = w1;
+        qw[tot + i] = w2;
+    }
+    if (threadIdx.x == 0) {
+        qw[2 * tot] = hj_qweight(dt, k3);
+        qw[2 * tot + 1] = hj_qweight(dt, k4);
+    }
+}
+
+// One fixed-point cell update from the upwind differences d_d = V_up,d - V_c
+// (exact, int64) and the weight magnitudes: V_c + floor((sum W_d d_d + 2^29)
+// / 2^30), then the BRT min with V0 and saturation below.
+__device__ __forceinline__ int32_t hj_q527_update(int32_t vc, int32_t v0, long long d1, long long d2, long long d3,
+                                                  long long d4, int32_t w1, int32_t w2, int32_t w3, int32_t w4)
+{
+    long long acc = (long long)w1 * d1;
+    acc += (long long)w2 * d2;
+    acc += (long long)w3 * d3;
+    acc += (long long)w4 * d4;
+    long long vn = (long long)vc + ((acc + (1LL << 29)) >> 30);  // arithmetic shift: floor
+    vn = vn < (long long)v0 ? vn : (long long)v0;
+    return (int32_t)(vn < -2147483648LL ? -2147483648LL : vn);
 }
 
 // Batch internals for the server: pull all slot states once, then query the

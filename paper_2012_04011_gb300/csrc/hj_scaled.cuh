@@ -1,0 +1,53 @@
+// Step epilogue of the kernels whose coefficient tables carry dt (the FP64
+// dt-scaled table and the Q5.27 fixed-point weights): as hj_step_epilogue
+// (alpha^max partials, last-CTA finaliser), and the last CTA also rescales
+// the table when the next dt differs from the one it holds, which happens
+// after the first step of a call and before the cut last step.  Every other
+// CTA has finished reading the table by then (it counted itself done after
+// its last cell), and the next step kernel is ordered after this one on the
+// stream.
+#pragma once
+
+#include "hj_device.cuh"
+
+__device__ __forceinline__ void hj_step_epilogue_scaled(HjDevState *st, const HjGeom &g, unsigned long long a1,
+                                                        unsigned long long a2, unsigned long long *scratch,
+                                                        HjScaledCoef *scaled, int32_t *qw,
+                                                        const HjCoef<double> *coef)
+{
+    __shared__ int s_last;
+    a1 = hj_warp_max_u64(a1);
+    a2 = hj_warp_max_u64(a2);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = (blockDim.x + 31) >> 5;
+    if (lane == 0) {
+        scratch[warp] = a1;
+        scratch[32 + warp] = a2;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < nwarp; ++w) {
+            a1 = a1 > scratch[w] ? a1 : scratch[w];
+            a2 = a2 > scratch[32 + w] ? a2 : scratch[32 + w];
+        }
+        atomicMax(&st->alpha_bits[0], a1);
+        atomicMax(&st->alpha_bits[1], a2);
+        __threadfence();
+        const unsigned int prev = atomicAdd(&st->blocks_done, 1u);
+        s_last = prev == gridDim.x - 1;
+        if (s_last) hj_finalise(st, g);
+    }
+    __syncthreads();
+    if (s_last) {
+        const volatile HjDevState *vs = st;
+        const double dtn = vs->dt;
+        if (!vs->done && dtn != vs->dt_scaled) {
+            if (scaled) hj_rescale_table(scaled, coef, g.n3 * g.n4, dtn);
+            else hj_rescale_qweights(qw, coef, g.n3, g.n4, g.p4, g.k3, g.k4, dtn);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                st->dt_scaled = dtn;
+                __threadfence();
+            }
+        }
+    }
+}

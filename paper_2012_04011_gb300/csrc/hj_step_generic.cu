@@ -16,8 +16,10 @@
 // with K_d = |xdot_d| / dx_d.  The FP64 variant folds dt into a per-(v, theta)
 // table (w0 = 1 - dt K_sum, w_d = dt K_d): 1 DMUL + 4 DFMA per cell, the
 // table rescaled by the last CTA only when dt changes.  The FP32 variant
-// keeps the differences (V_up - V_c) for accuracy.
-#include "hj_device.cuh"
+// keeps the differences (V_up - V_c) for accuracy.  The Q5.27 kernel
+// (hj_step_q527_kernel) evaluates the same form in exact integer differences
+// with fixed-point weights.
+#include "hj_scaled.cuh"
 
 namespace {
 
@@ -95,6 +97,98 @@ __device__ __forceinline__ T upwind_value(const Neigh<T> &nb, int mode)
 __device__ __forceinline__ double mag(double x)
 {
     return __longlong_as_double(__double_as_longlong(x) & 0x7fffffffffffffffLL);
+}
+
+// Q5.27 neighbour differences along one axis: V(i-1) - V_c and V(i+1) - V_c
+// in exact integers (ghosts: periodic wrap or the linear extrapolation, whose
+// difference is minus the one on the other side).
+struct QDiff {
+    long long dm, dp;
+};
+
+__device__ __forceinline__ QDiff q_axis(const int32_t *__restrict__ v, long long o, int i, int N, long long s,
+                                        bool periodic, int32_t vc)
+{
+    long long m = 0, p = 0;
+    const bool gm = i == 0 && !periodic, gp = i == N - 1 && !periodic;
+    if (i > 0) m = v[o - s];
+    else if (periodic) m = v[o + (long long)(N - 1) * s];
+    if (i < N - 1) p = v[o + s];
+    else if (periodic) p = v[o - (long long)(N - 1) * s];
+    QDiff d;
+    d.dm = gm ? (long long)vc - p : m - vc;
+    d.dp = gp ? (long long)vc - m : p - vc;
+    return d;
+}
+
+__device__ __forceinline__ long long q_upwind(const QDiff &d, int mode)
+{
+    if (mode == HJ_AXIS_CONTROL) return d.dp > d.dm ? d.dp : d.dm;
+    return mode == HJ_AXIS_PLUS ? d.dp : d.dm;
+}
+
+// One step in Q5.27 for every grid (the tiled kernel covers the car grids it
+// supports): V_c + round_half_up(sum_d W_d (V_up,d - V_c) / 2^30), BRT min,
+// saturation (hj_q527_update).  alpha^max comes from the FP64 table, so the dt
+// sequence is the FP64 one.
+template <bool FAST32>
+__global__ void __launch_bounds__(256) hj_step_q527_kernel(const int32_t *__restrict__ v0, int32_t *__restrict__ buf,
+                                                            const HjCoef<double> *__restrict__ coef, int32_t *qw,
+                                                            HjDevState *st, const HjGeom g, long long nint,
+                                                            const Divisors dv)
+{
+    __shared__ unsigned long long scratch[64];
+    if (st->done) return;
+    const long long n = st->n;
+    const int32_t *vin;
+    int32_t *vout;
+    hj_io_buffers<int32_t>(v0, buf, nint, n, vin, vout);
+
+    const unsigned int N1 = g.n1, N2 = g.n2, N3 = g.n3, N4 = g.n4;
+    const long long s3 = g.p4, s2 = (long long)N3 * g.p4, s1 = (long long)N2 * s2;
+    const unsigned long long ncell = (unsigned long long)N1 * N2 * N3 * N4;
+    const int tot = (int)N3 * g.p4;
+    const int32_t w3 = qw[2 * tot], w4 = qw[2 * tot + 1];
+    unsigned long long am1 = 0ull, am2 = 0ull;
+
+    for (unsigned long long c = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; c < ncell;
+         c += (unsigned long long)gridDim.x * blockDim.x) {
+        unsigned long long row;
+        int l, k, i, j;
+        if (FAST32) {
+            const uint32_t c32 = (uint32_t)c, row32 = fast_div(c32, dv.n4);
+            const uint32_t r2 = fast_div(row32, dv.n3);
+            const uint32_t i32 = fast_div(r2, dv.n2);
+            row = row32;
+            l = (int)(c32 - row32 * N4);
+            k = (int)(row32 - r2 * N3);
+            i = (int)i32;
+            j = (int)(r2 - i32 * N2);
+        } else {
+            row = c / N4;
+            l = (int)(c - row * N4);
+            const unsigned long long r2 = row / N3;
+            k = (int)(row - r2 * N3);
+            i = (int)(r2 / N2);
+            j = (int)(r2 - (unsigned long long)i * N2);
+        }
+        const long long o = (long long)row * g.p4 + l;
+        const int32_t vc = vin[o];
+        const QDiff dx = q_axis(vin, o, i, N1, s1, g.periodic & 1, vc);
+        const QDiff dy = q_axis(vin, o, j, N2, s2, (g.periodic >> 1) & 1, vc);
+        const QDiff dv3 = q_axis(vin, o, k, N3, s3, (g.periodic >> 2) & 1, vc);
+        const QDiff dv4 = q_axis(vin, o, l, N4, 1, (g.periodic >> 3) & 1, vc);
+        const int32_t w1 = qw[k * g.p4 + l], w2 = qw[tot + k * g.p4 + l];
+        const long long d1 = w1 >= 0 ? dx.dp : dx.dm;
+        const long long d2 = w2 >= 0 ? dy.dp : dy.dm;
+        vout[o] = hj_q527_update(vc, v0[o], d1, d2, q_upwind(dv3, g.mode3), q_upwind(dv4, g.mode4), abs(w1), abs(w2),
+                                 w3, w4);
+        const HjCoef<double> cf = coef[k * N4 + l];
+        const unsigned long long b1 = hj_abits(cf.a1), b2 = hj_abits(cf.a2);
+        am1 = am1 > b1 ? am1 : b1;
+        am2 = am2 > b2 ? am2 : b2;
+    }
+    hj_step_epilogue_scaled(st, g, am1, am2, scratch, nullptr, qw, coef);
 }
 
 template <typename T, bool FAST32>
@@ -193,42 +287,7 @@ __global__ void __launch_bounds__(256) hj_step_generic_kernel(const T *__restric
         am2 = hj_abits((double)am2f);
         hj_step_epilogue(st, g, am1, am2, scratch);
     } else {
-        // as hj_step_epilogue, and the last CTA also rescales the table when
-        // the next dt differs (the first step and the cut last step)
-        __shared__ int s_last;
-        am1 = hj_warp_max_u64(am1);
-        am2 = hj_warp_max_u64(am2);
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = (blockDim.x + 31) >> 5;
-        if (lane == 0) {
-            scratch[warp] = am1;
-            scratch[32 + warp] = am2;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            for (int w = 1; w < nwarp; ++w) {
-                am1 = am1 > scratch[w] ? am1 : scratch[w];
-                am2 = am2 > scratch[32 + w] ? am2 : scratch[32 + w];
-            }
-            atomicMax(&st->alpha_bits[0], am1);
-            atomicMax(&st->alpha_bits[1], am2);
-            __threadfence();
-            const unsigned int prev = atomicAdd(&st->blocks_done, 1u);
-            s_last = prev == gridDim.x - 1;
-            if (s_last) hj_finalise(st, g);
-        }
-        __syncthreads();
-        if (s_last) {
-            const volatile HjDevState *vs = st;
-            const double dtn = vs->dt;
-            if (!vs->done && dtn != vs->dt_scaled) {
-                hj_rescale_table(scaled, (const HjCoef<double> *)coef, N3 * N4, dtn);
-                __syncthreads();
-                if (threadIdx.x == 0) {
-                    st->dt_scaled = dtn;
-                    __threadfence();
-                }
-            }
-        }
+        hj_step_epilogue_scaled(st, g, am1, am2, scratch, scaled, nullptr, (const HjCoef<double> *)coef);
     }
 }
 
@@ -251,7 +310,16 @@ cudaError_t hj_launch_step_generic(hj_grid *g)
 #define HJ_LAUNCH(T, F)                                                                                          \
     hj_step_generic_kernel<T, F><<<blocks, threads, 0, g->stream>>>(                                       \
         (const T *)g->v0, (T *)g->buf, (const HjCoef<T> *)g->coef, g->scaled, g->dstate, g->geom, g->nint, dv)
-    if (g->prec == HJ_FP64) {
+    if (g->prec == HJ_Q527) {
+        if (fast)
+            hj_step_q527_kernel<true><<<blocks, threads, 0, g->stream>>>(
+                (const int32_t *)g->v0, (int32_t *)g->buf, (const HjCoef<double> *)g->coef, g->qw, g->dstate, g->geom,
+                g->nint, dv);
+        else
+            hj_step_q527_kernel<false><<<blocks, threads, 0, g->stream>>>(
+                (const int32_t *)g->v0, (int32_t *)g->buf, (const HjCoef<double> *)g->coef, g->qw, g->dstate, g->geom,
+                g->nint, dv);
+    } else if (g->prec == HJ_FP64) {
         if (fast) HJ_LAUNCH(double, true);
         else HJ_LAUNCH(double, false);
     } else {

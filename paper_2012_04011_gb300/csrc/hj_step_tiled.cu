@@ -1,4 +1,4 @@
-// Tiled FP32 HJ step kernel for sm_103a (the HBM-bound fast path).
+// Tiled FP32 / Q5.27 HJ step kernel for sm_103a (the HBM-bound fast path).
 //
 // Same per-cell arithmetic as the generic kernel (one step of Algorithm 2 of
 // arxiv 2012.04011 in upwind form, see hj_step_generic.cu), organised for
@@ -25,6 +25,11 @@
 //     cells each thread updates) are reduced by warp shuffles and a block
 //     reduction, and the last CTA computes the next CFL step (fused; no extra
 //     pass over the grid).
+// The Q5.27 variant (FIXED) moves the same 4-byte values through the same
+// ring and evaluates the fixed-point update of hj_q527_update per lane:
+// exact integer upwind differences (ghosts by flag, as minus the difference
+// on the other side), per-(v, theta) weights from the fixed-point table, and
+// the FP64 coefficient table for alpha^max.
 // Every mbarrier wait is bounded by %globaltimer; on timeout the kernel
 // records HJ_ERR_TIMEOUT in the device state, stops issuing work, waits
 // (bounded) for its own copies in flight and returns.
@@ -32,6 +37,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include "hj_scaled.cuh"
 #include "hj_tma.cuh"
 
 namespace {
@@ -74,16 +80,21 @@ __device__ __forceinline__ ItemGeom item_geom(const TiledParams &P, const HjGeom
     return it;
 }
 
+__device__ __forceinline__ int32_t f4geti(const float4 &v, int e) { return __float_as_int(f4get(v, e)); }
+
+// FIXED: Q5.27 values (the ring and the buffers hold int32 codes).
 // PADDED: N4 is not a multiple of 4 (the last quad of a row has pad lanes).
 // USIGN: cos(theta) and sin(theta) have one sign (up to negligible values)
 // across every theta quad, so each thread picks its x and y upwind sides once.
-template <bool PADDED, bool USIGN, int MAXC>
+template <bool FIXED, bool PADDED, bool USIGN, int MAXC>
 __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
     const __grid_constant__ CUtensorMap map_v0, const __grid_constant__ CUtensorMap map_a,
     const __grid_constant__ CUtensorMap map_b, const __grid_constant__ CUtensorMap map_v0_tile,
-    float *__restrict__ buf, const HjCoef<float> *__restrict__ coef, const float *__restrict__ tab, HjDevState *st,
-    const HjGeom g, const TiledParams P, long long nint)
+    float *__restrict__ buf, const void *__restrict__ coefv, const float *__restrict__ tab,
+    int32_t *__restrict__ qw, HjDevState *st, const HjGeom g, const TiledParams P, long long nint)
 {
+    const HjCoef<float> *coef = (const HjCoef<float> *)coefv;     // FP32 grids
+    const HjCoef<double> *coefd = (const HjCoef<double> *)coefv;  // Q5.27 grids
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     if (st->done) return;  // uniform across the grid
 
@@ -115,6 +126,7 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
     __syncthreads();
 
     float am1 = 0.f, am2 = 0.f;  // this thread's max |xdot_1|, |xdot_2| (non-negative)
+    unsigned long long ab1 = 0ull, ab2 = 0ull;  // the same as FP64 bit patterns (FIXED)
 
     if (tid >= P.nconsumer) {
         // ------------------------------------------------------------ producer
@@ -185,7 +197,7 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
         float wx[4], wy[4], cs[4], wxm[4], wym[4];
         bool xplus = true, yplus = true;
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
+        for (int e = 0; e < 4 && !FIXED; ++e) {
             const float c = tab[N3 + 4 * q + e], s = tab[N3 + P4 + 4 * q + e];
             cs[e] = fabsf(c) + fabsf(s);
             if (USIGN) {
@@ -199,7 +211,7 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
                 wym[e] = fmaxf(-s, 0.f);
             }
         }
-        if (USIGN) {  // the side of the quad's dominant lane (the host checked the others agree or vanish)
+        if (USIGN && !FIXED) {  // the side of the quad's dominant lane (the host checked the others agree or vanish)
             // scalar loads: the sign table starts at float N3 + 2 P4, not 16-byte aligned in general
             xplus = tab[N3 + 2 * P4 + 4 * q] >= 0.f;
             yplus = tab[N3 + 2 * P4 + 4 * q + 1] >= 0.f;
@@ -207,6 +219,12 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
         const int lm = (4 * q - 1 + N4) % N4;  // theta index left of the quad
         const int lp = (4 * q + 4) % N4;       // right of the quad
         const int lreal = min(4, N4 - 4 * q);  // real lanes (< 4 only in a padded last quad)
+        const int qtot = N3 * P4;
+        int32_t qw3 = 0, qw4 = 0;  // fixed-point v and theta weights
+        if (FIXED) {
+            qw3 = qw[2 * qtot];
+            qw4 = qw[2 * qtot + 1];
+        }
 
         // Ring cursors.  Planes are waited for and released in load order, so
         // one cursor walks the slots to wait on (with the phase parity) and
@@ -240,7 +258,12 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
             const int y = it.y0 + jy, v = it.v0 + kv;
             const bool rok = inrow && y < N2 && v < N3;
             const uint32_t rbase = rok ? ((uint32_t)y * N3 + v) * P4 + 4 * q : 0u;
-            const float vk = rok ? tab[v] : 0.f;
+            const float vk = (rok && !FIXED) ? tab[v] : 0.f;
+            int4 qw1 = make_int4(0, 0, 0, 0), qw2 = make_int4(0, 0, 0, 0);  // signed x / y weights of the quad
+            if (FIXED && rok) {
+                qw1 = *(const int4 *)(qw + v * P4 + 4 * q);
+                qw2 = *(const int4 *)(qw + qtot + v * P4 + 4 * q);
+            }
             // ghosts this row needs: 1 y-1, 2 y+1, 4 v-1, 8 v+1
             const uint32_t gmask = (y == 0 ? 1u : 0u) | (y == N2 - 1 ? 2u : 0u) | (v == 0 ? 4u : 0u) |
                                    (v == N3 - 1 ? 8u : 0u);
@@ -274,10 +297,11 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
                         break;
                     }
                     nxt = *(const float4 *)(stages + (size_t)s_n * sfl + rsm);
-                    prev = s_prev >= 0 ? *(const float4 *)(stages + (size_t)s_prev * sfl + rsm) : f4ghost(cur, nxt);
+                    prev = s_prev >= 0 ? *(const float4 *)(stages + (size_t)s_prev * sfl + rsm)
+                                       : (FIXED ? cur : f4ghost(cur, nxt));
                 } else {
                     prev = s_prev >= 0 ? *(const float4 *)(stages + (size_t)s_prev * sfl + rsm) : cur;
-                    nxt = f4ghost(cur, prev);
+                    nxt = FIXED ? cur : f4ghost(cur, prev);
                 }
                 if (rok) {
                     const float *row = sx + rsm;
@@ -285,7 +309,7 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
                     float4 yp = *(const float4 *)(row + srow * P4);
                     float4 vm = *(const float4 *)(row - P4);
                     float4 vp = *(const float4 *)(row + P4);
-                    if (edge && gmask) {
+                    if (!FIXED && edge && gmask) {
                         // extrapolated points past the y / v ends (Sec. II-B)
                         if (gmask & 1u) ym = f4ghost(cur, yp);
                         if (gmask & 2u) yp = f4ghost(cur, ym);
@@ -303,6 +327,32 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
                         if (!yplus) yu = ym;
                     }
                     float4 out;
+                    if constexpr (FIXED) {
+                        // ghost flags: x-1 (x = 0), x+1 (x = N1-1), y-1, y+1, v-1, v+1
+                        const bool gxm = s_prev < 0, gxp = x == N1 - 1;
+                        const bool gym = gmask & 1u, gyp = gmask & 2u, gvm = gmask & 4u, gvp = gmask & 8u;
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const long long vc = f4geti(cur, e);
+                            const long long xm = f4geti(prev, e), xp = f4geti(nxt, e);
+                            const long long ym_ = f4geti(ym, e), yp_ = f4geti(yp, e);
+                            const long long vm_ = f4geti(vm, e), vp_ = f4geti(vp, e);
+                            const int32_t tm = e == 0 ? __float_as_int(tl) : f4geti(cur, e - 1);
+                            int32_t tp = e == 3 ? __float_as_int(tr) : f4geti(cur, e + 1);
+                            if (PADDED && lreal < 4 && e == lreal - 1) tp = __float_as_int(t0);
+                            // V(i -+ 1) - V_c with the extrapolated ghosts (Sec. II-B)
+                            const long long dxm = gxm ? vc - xp : xm - vc, dxp = gxp ? vc - xm : xp - vc;
+                            const long long dym = gym ? vc - yp_ : ym_ - vc, dyp = gyp ? vc - ym_ : yp_ - vc;
+                            const long long dvm = gvm ? vc - vp_ : vm_ - vc, dvp = gvp ? vc - vm_ : vp_ - vc;
+                            const int32_t w1 = e == 0 ? qw1.x : e == 1 ? qw1.y : e == 2 ? qw1.z : qw1.w;
+                            const int32_t w2 = e == 0 ? qw2.x : e == 1 ? qw2.y : e == 2 ? qw2.z : qw2.w;
+                            int32_t vn = hj_q527_update((int32_t)vc, f4geti(v0c, e), w1 >= 0 ? dxp : dxm,
+                                                        w2 >= 0 ? dyp : dym, dvp > dvm ? dvp : dvm,
+                                                        (long long)max(tp, tm) - vc, abs(w1), abs(w2), qw3, qw4);
+                            if (PADDED && e >= lreal) vn = 0;
+                            f4set(out, e, __int_as_float(vn));
+                        }
+                    } else {
 #pragma unroll
                     for (int e = 0; e < 4; ++e) {
                         const float vc = f4get(cur, e);
@@ -327,6 +377,7 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
                         float vn = fminf(f4get(v0c, e), fmaf(dt, acc, vc));
                         if (PADDED && e >= lreal) vn = 0.f;
                         f4set(out, e, vn);
+                    }
                     }
                     *(float4 *)(vout + (uint32_t)x * s1 + rbase) = out;
                 }
@@ -353,32 +404,45 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
             const int y = it.y0 + jy, v = it.v0 + kv;
             if (inrow && y < N2 && v < N3)
                 for (int e = 0; e < lreal; ++e) {
-                    const HjCoef<float> c = coef[v * N4 + 4 * q + e];
-                    am1 = fmaxf(am1, c.a1);
-                    am2 = fmaxf(am2, c.a2);
+                    if constexpr (FIXED) {
+                        const HjCoef<double> c = coefd[v * N4 + 4 * q + e];
+                        const unsigned long long b1 = hj_abits(c.a1), b2 = hj_abits(c.a2);
+                        ab1 = ab1 > b1 ? ab1 : b1;
+                        ab2 = ab2 > b2 ? ab2 : b2;
+                    } else {
+                        const HjCoef<float> c = coef[v * N4 + 4 * q + e];
+                        am1 = fmaxf(am1, c.a1);
+                        am2 = fmaxf(am2, c.a2);
+                    }
                 }
         }
     }
-    hj_step_epilogue(st, g, hj_abits((double)am1), hj_abits((double)am2), scratch);
+    if constexpr (FIXED)
+        hj_step_epilogue_scaled(st, g, ab1, ab2, scratch, nullptr, qw, coefd);
+    else
+        hj_step_epilogue(st, g, hj_abits((double)am1), hj_abits((double)am2), scratch);
 }
 
 typedef void (*KernelFn)(const CUtensorMap, const CUtensorMap, const CUtensorMap, const CUtensorMap, float *,
-                         const HjCoef<float> *, const float *, HjDevState *, const HjGeom, const TiledParams,
+                         const void *, const float *, int32_t *, HjDevState *, const HjGeom, const TiledParams,
                          long long);
 
-template <bool PADDED, bool USIGN>
+template <bool FIXED, bool PADDED, bool USIGN>
 KernelFn kernel_fn_pu(int nconsumer)
 {
-    if (nconsumer <= VARIANTS[0]) return hj_step_tiled_kernel<PADDED, USIGN, VARIANTS[0]>;
-    if (nconsumer <= VARIANTS[1]) return hj_step_tiled_kernel<PADDED, USIGN, VARIANTS[1]>;
-    if (nconsumer <= VARIANTS[2]) return hj_step_tiled_kernel<PADDED, USIGN, VARIANTS[2]>;
-    return hj_step_tiled_kernel<PADDED, USIGN, VARIANTS[3]>;
+    if (nconsumer <= VARIANTS[0]) return hj_step_tiled_kernel<FIXED, PADDED, USIGN, VARIANTS[0]>;
+    if (nconsumer <= VARIANTS[1]) return hj_step_tiled_kernel<FIXED, PADDED, USIGN, VARIANTS[1]>;
+    if (nconsumer <= VARIANTS[2]) return hj_step_tiled_kernel<FIXED, PADDED, USIGN, VARIANTS[2]>;
+    return hj_step_tiled_kernel<FIXED, PADDED, USIGN, VARIANTS[3]>;
 }
 
-KernelFn kernel_fn(bool padded, bool usign, int nconsumer)
+// The fixed-point variant selects the upwind side per lane (no USIGN form).
+KernelFn kernel_fn(bool fixed, bool padded, bool usign, int nconsumer)
 {
-    if (padded) return usign ? kernel_fn_pu<true, true>(nconsumer) : kernel_fn_pu<true, false>(nconsumer);
-    return usign ? kernel_fn_pu<false, true>(nconsumer) : kernel_fn_pu<false, false>(nconsumer);
+    if (fixed) return padded ? kernel_fn_pu<true, true, false>(nconsumer) : kernel_fn_pu<true, false, false>(nconsumer);
+    if (padded)
+        return usign ? kernel_fn_pu<false, true, true>(nconsumer) : kernel_fn_pu<false, true, false>(nconsumer);
+    return usign ? kernel_fn_pu<false, false, true>(nconsumer) : kernel_fn_pu<false, false, false>(nconsumer);
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
@@ -504,7 +568,8 @@ bool hj_tiled_setup(hj_grid *g, char *why, size_t why_len)
         snprintf(why, why_len, "%s", m);
         return false;
     };
-    if (g->prec != HJ_FP32) return fail("tiled kernel is FP32 only");
+    if (g->prec != HJ_FP32 && g->prec != HJ_Q527) return fail("tiled kernel is FP32 or Q5.27 only");
+    const bool fixed = g->prec == HJ_Q527;
     if (g->periodic != 0x8u) return fail("tiled kernel needs theta (axis 4) periodic and x, y, v not");
     if (!g->has_dyn || g->dyn != HJ_DYN_CAR4D) return fail("tiled kernel needs the car dynamics");
     if (g->p4 > 256) return fail("theta rows longer than 256 points");
@@ -520,7 +585,7 @@ bool hj_tiled_setup(hj_grid *g, char *why, size_t why_len)
     // the (cos, sin) sign of each quad's dominant lane [p4]
     float *sgn = (float *)calloc((size_t)g->p4, sizeof(float));
     if (!sgn) return fail("host allocation failed");
-    const bool usign = sign_uniform(g, sgn);
+    const bool usign = !fixed && sign_uniform(g, sgn);
     cudaError_t e = cudaMemcpy(g->tab_tiled + g->n[2] + 2 * g->p4, sgn, sizeof(float) * g->p4, cudaMemcpyHostToDevice);
     free(sgn);
     if (e != cudaSuccess) return fail("sign table upload failed");
@@ -548,7 +613,7 @@ bool hj_tiled_setup(hj_grid *g, char *why, size_t why_len)
     if (P.nconsumer > MAX_CONSUMERS) return fail("tile needs too many threads");
     size_t smem = tiled_smem_bytes(P);
     if ((int)smem > maxsmem) return fail("tile does not fit in shared memory");
-    const void *fn = (const void *)kernel_fn(g->p4 != g->n[3], usign, P.nconsumer);
+    const void *fn = (const void *)kernel_fn(fixed, g->p4 != g->n[3], usign, P.nconsumer);
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return fail("cannot raise the shared-memory limit");
     int per_sm = 0;
@@ -569,7 +634,8 @@ bool hj_tiled_setup(hj_grid *g, char *why, size_t why_len)
     cuuint32_t estr[4] = {1, 1, 1, 1};
     void *bases[4] = {g->v0, g->buf, (char *)g->buf + (size_t)g->nint * 4, g->v0};
     for (int i = 0; i < 4; ++i) {
-        CUresult r = enc(&g->tmap[i], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, bases[i], dims, strides,
+        CUresult r = enc(&g->tmap[i], fixed ? CU_TENSOR_MAP_DATA_TYPE_INT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4,
+                         bases[i], dims, strides,
                          i < 3 ? box_halo : box_tile, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) {
@@ -590,9 +656,9 @@ bool hj_tiled_setup(hj_grid *g, char *why, size_t why_len)
 cudaError_t hj_launch_step_tiled(hj_grid *g)
 {
     const TiledParams P = make_params(g, g->tile_ty, g->tile_tv, g->tile_stages, g->tile_xc);
-    KernelFn fn = kernel_fn(g->p4 != g->n[3], g->tiled_usign, P.nconsumer);
+    KernelFn fn = kernel_fn(g->prec == HJ_Q527, g->p4 != g->n[3], g->tiled_usign, P.nconsumer);
     fn<<<g->tiled_ctas, P.nconsumer + 32, tiled_smem_bytes(P), g->stream>>>(
-        g->tmap[0], g->tmap[1], g->tmap[2], g->tmap[3], (float *)g->buf, (const HjCoef<float> *)g->coef,
-        g->tab_tiled, g->dstate, g->geom, P, g->nint);
+        g->tmap[0], g->tmap[1], g->tmap[2], g->tmap[3], (float *)g->buf, g->coef, g->tab_tiled, g->qw, g->dstate,
+        g->geom, P, g->nint);
     return cudaGetLastError();
 }

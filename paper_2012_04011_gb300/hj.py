@@ -19,7 +19,7 @@ from . import _build
 
 HJ_OK, HJ_ERR_INVALID_ARG, HJ_ERR_STATE, HJ_ERR_OOM, HJ_ERR_CUDA, HJ_ERR_UNSTABLE, HJ_ERR_TIMEOUT, \
     HJ_ERR_UNSUPPORTED = range(8)
-HJ_FP64, HJ_FP32 = 0, 1
+HJ_FP64, HJ_FP32, HJ_Q527 = 0, 1, 2  # HJ_Q527: int32 codes, value = code * 2^-27
 HJ_DYN_CAR4D, HJ_DYN_CONST = 0, 1
 HJ_KERNEL_AUTO, HJ_KERNEL_GENERIC, HJ_KERNEL_TILED = 0, 1, 2
 PERIODIC_THETA = 0b1000
@@ -244,6 +244,8 @@ def _dtype_code(x) -> int:
         return HJ_FP64
     if name.endswith("float32"):
         return HJ_FP32
+    if name.endswith("int32"):
+        return HJ_Q527
     raise TypeError(f"unsupported dtype {name}")
 
 
