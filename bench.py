@@ -33,9 +33,9 @@ sys.path.insert(0, ROOT)
 METRIC = "4D HJ cell-updates/s (fraction of HBM peak) + p99 re-solve latency vs FP64 path"
 UNIT = "cell-updates/s"
 WORKLOAD = "car4d_128x128x64x96"
-BYTES_PER_UPDATE = {"f32": 12, "f64": 24}
+BYTES_PER_UPDATE = {"f32": 12, "f64": 24, "q527": 12}
 PROFILE = os.path.join(ROOT, "profiles", "hj_step_tiled_car4d_128x128x64x96.md")
-KERNEL_SOURCES = ["hj_step_tiled.cu", "hj_device.cuh", "hj_tma.cuh"]
+KERNEL_SOURCES = ["hj_step_tiled.cu", "hj_device.cuh", "hj_tma.cuh", "hj_scaled.cuh", "hj_internal.h"]
 # FP64 path: bound by the FP64 unit.  Algorithmic FP64 flops per cell-update:
 # 1 DMUL + 5 DFMA = 11; nominal GB300 FP64 rate 1.25 TFLOP/s (no measured FP64
 # figure in MEASURED_PEAKS.json).
@@ -241,6 +241,7 @@ def run_ours(args):
     V0_dev = torch.from_numpy(V0).to("cuda")
     out32 = torch.empty(ncell, dtype=torch.float32, device="cuda")
     out64 = torch.empty(ncell, dtype=torch.float64, device="cuda")
+    outq = torch.empty(ncell, dtype=torch.int32, device="cuda")
 
     def barrier():
         torch.cuda.synchronize()
@@ -259,16 +260,17 @@ def run_ours(args):
 
     results = {}
     for prec_name, prec, out, K, W in (("f32", hj.HJ_FP32, out32, args.steps, args.warmup),
-                                       ("f64", hj.HJ_FP64, out64, max(1, min(args.steps, args.fp64_steps)), 1)):
-        if prec_name == "f64" and args.no_fp64:
+                                       ("f64", hj.HJ_FP64, out64, max(1, min(args.steps, args.fp64_steps)), 1),
+                                       ("q527", hj.HJ_Q527, outq, max(1, min(args.steps, args.q527_steps)), 1)):
+        if (prec_name == "f64" and args.no_fp64) or (prec_name == "q527" and args.no_q527):
             continue
         g = hj.Grid(w.grid.n, w.grid.lo, w.grid.hi, w.grid.periodic, prec, stream.cuda_stream)
         g.set_dynamics(hj.HJ_DYN_CAR4D, (w.a_max, w.w_max))
         tuned = None
-        if prec == hj.HJ_FP32 and args.tile:
+        if prec != hj.HJ_FP64 and args.tile:
             g.set_tile_shape([int(v) for v in args.tile.split(",")])
             tuned = {"shape": list(g.info().tile), "ctas": g.info().tile_ctas, "tried": []}
-        elif prec == hj.HJ_FP32 and not args.no_autotune:
+        elif prec != hj.HJ_FP64 and not args.no_autotune:
             # pick the tile shape by timing candidates (outside the timed region)
             hj.hj_set_initial_value_device(g.handle, V0_dev)
             tried = g.autotune(8)
@@ -450,6 +452,23 @@ def run_ours(args):
                          "flops_per_update": FP64_FLOPS_PER_UPDATE},
             "speedup_fp32_over_fp64": r32["value"] / r64["value"],
         }
+    if "q527" in results:
+        rq = results["q527"]
+        # Q5.27 codes move like FP32 (4 bytes); Sec. IV-B's error table compares
+        # the fixed-point result with a floating-point one
+        err = None
+        if "f64" in results:
+            err = float((outq.double() * 2.0 ** -27 - out64).abs().max().item())
+        aq = BYTES_PER_UPDATE["q527"] * ncell / (rq["avg_step_kernel_ms"] * 1e-3) / 1e9
+        line["q527_path"] = {
+            "value": rq["value"], "unit": UNIT, "ms_per_step": rq["ms_per_step"], "steps": rq["K"],
+            "latency_ms": rq["latency_ms"], "avg_step_kernel_ms": rq["avg_step_kernel_ms"],
+            "kernel": "hj_step_tiled_kernel<FIXED>" if rq["kernel"] == hj.HJ_KERNEL_TILED else "hj_step_q527_kernel",
+            "roofline": {"bound": "hbm", "achieved": aq, "peak": peak, "unit": "GB/s", "frac": aq / peak,
+                         "bytes_per_update": BYTES_PER_UPDATE["q527"], "peak_source": f"{peak_kind} hbm_gbs"},
+            "max_abs_err_vs_fp64": err,
+            "tile": {k: v for k, v in (rq["tile"] or {}).items() if k != "tried"},
+        }
     if world == 1 and not args.no_cpu_baseline:
         nthreads = cpu_threads()
         rate, el, nst = oracle_sample(w, V0, args.cpu_sample_steps, nthreads)
@@ -472,6 +491,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-sample-steps", type=int, default=8)
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--q527-steps", type=int, default=5)
+    ap.add_argument("--no-q527", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")

@@ -196,6 +196,24 @@ __device__ __forceinline__ void hj_rescale_qweights(int32_t *qw, const HjCoef<do
     }
 }
 
+// Interior form of the same update (no extrapolated ghost on any axis):
+// sum_d W_d (V_up,d - V_c) = sum_d W_d V_up,d - S V_c with S = sum_d W_d, all
+// operands int32, so five 32x32->64 multiply-adds give the exact sum.
+// nsum = -S; the rounding offset 2^29 starts the accumulator.
+__device__ __forceinline__ int32_t hj_q527_update_interior(int32_t vc, int32_t v0, int32_t u1, int32_t u2, int32_t u3,
+                                                           int32_t u4, int32_t w1, int32_t w2, int32_t w3, int32_t w4,
+                                                           int32_t nsum)
+{
+    // three short chains instead of one long one (the sum is exact in any order)
+    const long long a = (long long)nsum * vc + (long long)w1 * u1;
+    const long long b = (long long)w2 * u2 + (long long)w3 * u3;
+    const long long c = (long long)w4 * u4 + (1LL << 29);
+    const long long acc = a + b + c;
+    long long vn = (long long)vc + (acc >> 30);
+    vn = vn < (long long)v0 ? vn : (long long)v0;
+    return (int32_t)(vn < -2147483648LL ? -2147483648LL : vn);
+}
+
 // One fixed-point cell update from the upwind differences d_d = V_up,d - V_c
 // (exact, int64) and the weight magnitudes: V_c + floor((sum W_d d_d + 2^29)
 // / 2^30), then the BRT min with V0 and saturation below.

@@ -264,6 +264,21 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
                 qw1 = *(const int4 *)(qw + v * P4 + 4 * q);
                 qw2 = *(const int4 *)(qw + qtot + v * P4 + 4 * q);
             }
+            // per lane: weight magnitudes, upwind sides and -(sum of the four weights)
+            int32_t aw1[4], aw2[4], nsum[4];
+            bool xpos[4], ypos[4];
+            if (FIXED) {
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int32_t w1 = e == 0 ? qw1.x : e == 1 ? qw1.y : e == 2 ? qw1.z : qw1.w;
+                    const int32_t w2 = e == 0 ? qw2.x : e == 1 ? qw2.y : e == 2 ? qw2.z : qw2.w;
+                    xpos[e] = w1 >= 0;
+                    ypos[e] = w2 >= 0;
+                    aw1[e] = abs(w1);
+                    aw2[e] = abs(w2);
+                    nsum[e] = -(aw1[e] + aw2[e] + qw3 + qw4);
+                }
+            }
             // ghosts this row needs: 1 y-1, 2 y+1, 4 v-1, 8 v+1
             const uint32_t gmask = (y == 0 ? 1u : 0u) | (y == N2 - 1 ? 2u : 0u) | (v == 0 ? 4u : 0u) |
                                    (v == N3 - 1 ? 8u : 0u);
@@ -331,26 +346,55 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
                         // ghost flags: x-1 (x = 0), x+1 (x = N1-1), y-1, y+1, v-1, v+1
                         const bool gxm = s_prev < 0, gxp = x == N1 - 1;
                         const bool gym = gmask & 1u, gyp = gmask & 2u, gvm = gmask & 4u, gvp = gmask & 8u;
+                        if (!(gxm || gxp || gmask)) {  // interior row: int32 operands throughout
 #pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            const long long vc = f4geti(cur, e);
-                            const long long xm = f4geti(prev, e), xp = f4geti(nxt, e);
-                            const long long ym_ = f4geti(ym, e), yp_ = f4geti(yp, e);
-                            const long long vm_ = f4geti(vm, e), vp_ = f4geti(vp, e);
-                            const int32_t tm = e == 0 ? __float_as_int(tl) : f4geti(cur, e - 1);
-                            int32_t tp = e == 3 ? __float_as_int(tr) : f4geti(cur, e + 1);
-                            if (PADDED && lreal < 4 && e == lreal - 1) tp = __float_as_int(t0);
-                            // V(i -+ 1) - V_c with the extrapolated ghosts (Sec. II-B)
-                            const long long dxm = gxm ? vc - xp : xm - vc, dxp = gxp ? vc - xm : xp - vc;
-                            const long long dym = gym ? vc - yp_ : ym_ - vc, dyp = gyp ? vc - ym_ : yp_ - vc;
-                            const long long dvm = gvm ? vc - vp_ : vm_ - vc, dvp = gvp ? vc - vm_ : vp_ - vc;
-                            const int32_t w1 = e == 0 ? qw1.x : e == 1 ? qw1.y : e == 2 ? qw1.z : qw1.w;
-                            const int32_t w2 = e == 0 ? qw2.x : e == 1 ? qw2.y : e == 2 ? qw2.z : qw2.w;
-                            int32_t vn = hj_q527_update((int32_t)vc, f4geti(v0c, e), w1 >= 0 ? dxp : dxm,
-                                                        w2 >= 0 ? dyp : dym, dvp > dvm ? dvp : dvm,
-                                                        (long long)max(tp, tm) - vc, abs(w1), abs(w2), qw3, qw4);
-                            if (PADDED && e >= lreal) vn = 0;
-                            f4set(out, e, __int_as_float(vn));
+                            for (int e = 0; e < 4; ++e) {
+                                const int32_t vc = f4geti(cur, e);
+                                const int32_t tm = e == 0 ? __float_as_int(tl) : f4geti(cur, e - 1);
+                                int32_t tp = e == 3 ? __float_as_int(tr) : f4geti(cur, e + 1);
+                                if (PADDED && lreal < 4 && e == lreal - 1) tp = __float_as_int(t0);
+                                const int32_t u1 = xpos[e] ? f4geti(nxt, e) : f4geti(prev, e);
+                                const int32_t u2 = ypos[e] ? f4geti(yp, e) : f4geti(ym, e);
+                                const int32_t u3 = max(f4geti(vp, e), f4geti(vm, e));
+                                int32_t vn = hj_q527_update_interior(vc, f4geti(v0c, e), u1, u2, u3, max(tp, tm),
+                                                                     aw1[e], aw2[e], qw3, qw4, nsum[e]);
+                                if (PADDED && e >= lreal) vn = 0;
+                                f4set(out, e, __int_as_float(vn));
+                            }
+                        } else {
+                            // an extrapolated ghost on some axis (Sec. II-B): the ghost
+                            // 2 V_c - V_o enters as -W on V_o and +2W on V_c, so the
+                            // operands stay int32 and the sum stays exact
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                const int32_t vc = f4geti(cur, e);
+                                const int32_t xm = f4geti(prev, e), xp = f4geti(nxt, e);
+                                const int32_t ym_ = f4geti(ym, e), yp_ = f4geti(yp, e);
+                                const int32_t vm_ = f4geti(vm, e), vp_ = f4geti(vp, e);
+                                const int32_t tm = e == 0 ? __float_as_int(tl) : f4geti(cur, e - 1);
+                                int32_t tp = e == 3 ? __float_as_int(tr) : f4geti(cur, e + 1);
+                                if (PADDED && lreal < 4 && e == lreal - 1) tp = __float_as_int(t0);
+                                // x, y: the upwind side, and whether it is a ghost
+                                const bool hx = xpos[e] ? gxp : gxm, hy = ypos[e] ? gyp : gym;
+                                const int32_t ux = (xpos[e] != hx) ? xp : xm, uy = (ypos[e] != hy) ? yp_ : ym_;
+                                // v: the larger of V(v+1), V(v-1), either possibly a ghost
+                                bool hv = false;
+                                int32_t uv = max(vp_, vm_);
+                                if (gvp) {
+                                    uv = vm_;
+                                    hv = vc >= vm_;
+                                } else if (gvm) {
+                                    uv = vp_;
+                                    hv = vp_ < vc;
+                                }
+                                const int32_t c0 = nsum[e] + (hx ? 2 * aw1[e] : 0) + (hy ? 2 * aw2[e] : 0) +
+                                                   (hv ? 2 * qw3 : 0);
+                                int32_t vn = hj_q527_update_interior(vc, f4geti(v0c, e), ux, uy, uv, max(tp, tm),
+                                                                     hx ? -aw1[e] : aw1[e], hy ? -aw2[e] : aw2[e],
+                                                                     hv ? -qw3 : qw3, qw4, c0);
+                                if (PADDED && e >= lreal) vn = 0;
+                                f4set(out, e, __int_as_float(vn));
+                            }
                         }
                     } else {
 #pragma unroll
