@@ -33,7 +33,7 @@ sys.path.insert(0, ROOT)
 METRIC = "4D HJ cell-updates/s (fraction of HBM peak) + p99 re-solve latency vs FP64 path"
 UNIT = "cell-updates/s"
 WORKLOAD = "car4d_128x128x64x96"
-BYTES_PER_UPDATE = {"f32": 12, "f64": 24, "q527": 12}
+BYTES_PER_UPDATE = {"f32": 12, "f64": 24, "q527": 12, "f32_bcast": 8}
 PROFILE = os.path.join(ROOT, "profiles", "hj_step_tiled_car4d_128x128x64x96.md")
 KERNEL_SOURCES = ["hj_step_tiled.cu", "hj_device.cuh", "hj_tma.cuh", "hj_scaled.cuh", "hj_internal.h"]
 # FP64 path: bound by the FP64 unit.  Algorithmic FP64 flops per cell-update:
@@ -239,6 +239,7 @@ def run_ours(args):
     ncell = V0.size
     stream = torch.cuda.current_stream()
     V0_dev = torch.from_numpy(V0).to("cuda")
+    V0xy_dev = torch.from_numpy(np.ascontiguousarray(scenes.signed_distance_xy(w.grid, w.scene))).to("cuda")
     out32 = torch.empty(ncell, dtype=torch.float32, device="cuda")
     out64 = torch.empty(ncell, dtype=torch.float64, device="cuda")
     outq = torch.empty(ncell, dtype=torch.int32, device="cuda")
@@ -252,8 +253,11 @@ def run_ours(args):
     def max_over_ranks(x: float) -> float:
         return rank_max(x, world, "cuda")
 
-    def solve_once(g, out):
-        hj.hj_set_initial_value_device(g.handle, V0_dev)
+    def solve_once(g, out, xy=False):
+        if xy:  # V0 from its position-only field: the broadcast-V0 kernel
+            hj.hj_set_initial_value_xy_device(g.handle, V0xy_dev)
+        else:
+            hj.hj_set_initial_value_device(g.handle, V0_dev)
         st = hj.hj_solve_brt(g.handle, w.T, w.cfl)
         hj.hj_read_value_device(g.handle, out)
         return st
@@ -261,9 +265,13 @@ def run_ours(args):
     results = {}
     for prec_name, prec, out, K, W in (("f32", hj.HJ_FP32, out32, args.steps, args.warmup),
                                        ("f64", hj.HJ_FP64, out64, max(1, min(args.steps, args.fp64_steps)), 1),
-                                       ("q527", hj.HJ_Q527, outq, max(1, min(args.steps, args.q527_steps)), 1)):
-        if (prec_name == "f64" and args.no_fp64) or (prec_name == "q527" and args.no_q527):
+                                       ("q527", hj.HJ_Q527, outq, max(1, min(args.steps, args.q527_steps)), 1),
+                                       ("f32_bcast", hj.HJ_FP32, out32, max(1, min(args.steps, args.bcast_steps)),
+                                        1)):
+        if (prec_name == "f64" and args.no_fp64) or (prec_name == "q527" and args.no_q527) or \
+                (prec_name == "f32_bcast" and args.no_bcast):
             continue
+        xy = prec_name == "f32_bcast"
         g = hj.Grid(w.grid.n, w.grid.lo, w.grid.hi, w.grid.periodic, prec, stream.cuda_stream)
         g.set_dynamics(hj.HJ_DYN_CAR4D, (w.a_max, w.w_max))
         tuned = None
@@ -272,12 +280,15 @@ def run_ours(args):
             tuned = {"shape": list(g.info().tile), "ctas": g.info().tile_ctas, "tried": []}
         elif prec != hj.HJ_FP64 and not args.no_autotune:
             # pick the tile shape by timing candidates (outside the timed region)
-            hj.hj_set_initial_value_device(g.handle, V0_dev)
+            if xy:
+                hj.hj_set_initial_value_xy_device(g.handle, V0xy_dev)
+            else:
+                hj.hj_set_initial_value_device(g.handle, V0_dev)
             tried = g.autotune(8)
             tuned = {"shape": list(g.info().tile), "ctas": g.info().tile_ctas,
                      "tried": [t.as_dict() for t in tried]}
         for _ in range(W):
-            solve_once(g, out)
+            solve_once(g, out, xy)
         barrier()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         lat, loop_ms, steps_total, launches = [], 0.0, 0, 0
@@ -288,7 +299,7 @@ def run_ours(args):
         for _ in range(K):
             e_a, e_b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e_a.record(stream)
-            st = solve_once(g, out)
+            st = solve_once(g, out, xy)
             e_b.record(stream)
             e_b.synchronize()
             lat.append(e_a.elapsed_time(e_b))
@@ -469,6 +480,17 @@ def run_ours(args):
             "max_abs_err_vs_fp64": err,
             "tile": {k: v for k, v in (rq["tile"] or {}).items() if k != "tried"},
         }
+    if "f32_bcast" in results:
+        rb = results["f32_bcast"]
+        ab = BYTES_PER_UPDATE["f32_bcast"] * ncell / (rb["avg_step_kernel_ms"] * 1e-3) / 1e9
+        line["broadcast_v0_path"] = {
+            "workload": WORKLOAD + " with V0 given as its 128x128 (x, y) field (Eq. init_V), FP32",
+            "value": rb["value"], "unit": UNIT, "ms_per_step": rb["ms_per_step"], "steps": rb["K"],
+            "avg_step_kernel_ms": rb["avg_step_kernel_ms"],
+            "roofline": {"bound": "hbm", "achieved": ab, "peak": peak, "unit": "GB/s", "frac": ab / peak,
+                         "bytes_per_update": BYTES_PER_UPDATE["f32_bcast"], "peak_source": f"{peak_kind} hbm_gbs"},
+            "tile": {k: v for k, v in (rb["tile"] or {}).items() if k != "tried"},
+        }
     if world == 1 and not args.no_cpu_baseline:
         nthreads = cpu_threads()
         rate, el, nst = oracle_sample(w, V0, args.cpu_sample_steps, nthreads)
@@ -493,6 +515,8 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--q527-steps", type=int, default=5)
     ap.add_argument("--no-q527", action="store_true")
+    ap.add_argument("--bcast-steps", type=int, default=5)
+    ap.add_argument("--no-bcast", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")

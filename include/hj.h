@@ -134,6 +134,7 @@ typedef struct {
     size_t device_bytes;   /* device memory held by the grid */
     int32_t tile[4];       /* tiled kernel shape in use (zeros if the tiled kernel is unavailable) */
     int32_t tile_ctas;     /* CTAs per tiled step launch */
+    int32_t v0_broadcast;  /* 1: V0 was set from its (x, y) field and the tiled kernel reads that field */
 } hj_grid_info;
 
 /* Create a grid of n[0]*n[1]*n[2]*n[3] cells on the current CUDA device.
@@ -168,8 +169,18 @@ HJ_API hj_status hj_set_initial_value(hj_grid *g, const double *v0, size_t count
 
 /* As hj_set_initial_value for a V0 that depends on position only (as Eq.
  * init_V does): v0_xy is a host array of count = N1*N2 doubles, row-major
- * [N1][N2], replicated over v and theta on the device. */
+ * [N1][N2], replicated over v and theta on the device.  The grid also keeps
+ * the field itself, and the tiled step kernel then reads V0 from it
+ * (8 instead of 12 bytes of HBM traffic per FP32 / Q5.27 cell-update; same
+ * results bit for bit).  Any other hj_set_initial_value* call switches back
+ * to the full 4D V0. */
 HJ_API hj_status hj_set_initial_value_xy(hj_grid *g, const double *v0_xy, size_t count);
+
+/* As hj_set_initial_value_xy from a DEVICE array of count = N1*N2 values of
+ * dtype (HJ_FP64, HJ_FP32 or HJ_Q527 codes) on the grid's device; read on
+ * the grid's stream; the caller keeps ownership. */
+HJ_API hj_status hj_set_initial_value_xy_device(hj_grid *g, const void *v0_xy_device, hj_precision dtype,
+                                                size_t count);
 
 /* As hj_set_initial_value, from a DEVICE array (dtype HJ_FP64 = double,
  * HJ_FP32 = float, HJ_Q527 = int32 codes) of count values on the grid's

@@ -84,8 +84,8 @@ __global__ void ingest_kernel(const Tin *__restrict__ src, T *__restrict__ dst, 
 
 // V0 that depends only on (x, y): an N1*N2 field replicated over v and theta
 // (Eq. init_V depends on the position only), written in the internal layout.
-template <typename T>
-__global__ void ingest_xy_kernel(const double *__restrict__ src, T *__restrict__ dst, int n3, int n4, int p4,
+template <typename Tin, typename T>
+__global__ void ingest_xy_kernel(const Tin *__restrict__ src, T *__restrict__ dst, int n3, int n4, int p4,
                                  long long nxy, int *nonfinite)
 {
     const long long per = (long long)n3 * p4, total = nxy * per;
@@ -96,7 +96,7 @@ __global__ void ingest_xy_kernel(const double *__restrict__ src, T *__restrict__
         const int l = (int)(i - xy * per) % p4;
         T v = T(0);
         if (l < n4) {
-            const double x = src[xy];
+            const double x = elem_to_f64<Tin>(src[xy]);
             if (!isfinite(x)) bad = 1;
             v = elem_from_f64<T>(x);
         }
@@ -349,6 +349,7 @@ void free_grid(hj_grid *g)
     if (g->tab_tiled) cudaFree(g->tab_tiled);
     if (g->scaled) cudaFree(g->scaled);
     if (g->qw) cudaFree(g->qw);
+    if (g->v0xy) cudaFree(g->v0xy);
     if (g->dstate) cudaFree(g->dstate);
     if (g->hstate) cudaFreeHost(g->hstate);
     for (int i = 0; i < 4; ++i)
@@ -377,7 +378,7 @@ cudaError_t hj_launch_ingest_f32(const void *src, hj_precision src_type, float *
 cudaError_t hj_launch_ingest_xy_f32(const double *src_dev, float *dst, int n3, int n4, int p4, long long nxy,
                                     int *nonfinite, cudaStream_t stream)
 {
-    ingest_xy_kernel<float><<<grid_blocks(nxy * n3 * p4, 256), 256, 0, stream>>>(src_dev, dst, n3, n4, p4, nxy,
+    ingest_xy_kernel<double, float><<<grid_blocks(nxy * n3 * p4, 256), 256, 0, stream>>>(src_dev, dst, n3, n4, p4, nxy,
                                                                                  nonfinite);
     return cudaGetLastError();
 }
@@ -476,6 +477,8 @@ hj_status hj_create_grid(const int32_t n[4], const double lo[4], const double hi
     if (e == cudaSuccess) e = cudaMalloc(&g->tab_tiled, sizeof(float) * ((size_t)n[2] + 3 * (size_t)g->p4));
     if (e == cudaSuccess && prec == HJ_FP64) e = cudaMalloc(&g->scaled, ncoef * sizeof(HjScaledCoef));
     if (e == cudaSuccess && prec == HJ_Q527) e = cudaMalloc(&g->qw, qw_bytes);
+    const size_t xy_bytes = (size_t)n[0] * n[1] * g->esize;
+    if (e == cudaSuccess) e = cudaMalloc(&g->v0xy, xy_bytes);
     if (e == cudaSuccess) e = cudaMalloc(&g->dstate, sizeof(HjDevState));
     if (e == cudaSuccess) e = cudaHostAlloc(&g->hstate, sizeof(HjDevState), cudaHostAllocDefault);
     for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaEventCreate(&g->ev[i]);
@@ -486,7 +489,7 @@ hj_status hj_create_grid(const int32_t n[4], const double lo[4], const double hi
         return s;
     }
     g->device_bytes = 3 * arr + coef_bytes + qw_bytes + (prec == HJ_FP64 ? ncoef * sizeof(HjScaledCoef) : 0) +
-                      sizeof(HjDevState);
+                      xy_bytes + sizeof(HjDevState);
     hj_status s = reset_state(g);
     if (s == HJ_OK) {
         cudaError_t e2 = cudaStreamSynchronize(g->stream);
@@ -564,6 +567,42 @@ hj_status hj_set_dynamics(hj_grid *g, hj_dynamics kind, const double *params, in
     return HJ_OK;
 }
 
+// The tiled kernel's stage layout depends on whether V0 is broadcast from the
+// (x, y) field; redo its setup when that changes.
+static void set_v0_mode(hj_grid *g, bool bcast)
+{
+    if (g->v0_bcast == bcast) return;
+    g->v0_bcast = bcast;
+    if (g->has_dyn) {
+        char why[160];
+        g->tiled_ok = hj_tiled_setup(g, why, sizeof(why));
+        if (g->kernel_req == HJ_KERNEL_TILED && !g->tiled_ok) g->kernel_req = HJ_KERNEL_AUTO;
+    }
+}
+
+static hj_status finish_ingest(hj_grid *g);
+
+// V0 from its (x, y) field on the device (src: nxy values of dtype): the 4D
+// V0 (replicated over v and theta) and the field itself for the
+// broadcast-V0 step kernel, with the same conversion.
+static hj_status ingest_xy(hj_grid *g, const void *src, hj_precision dtype, long long nxy)
+{
+    int *flag = &g->dstate->nonfinite;
+    const int blocks = grid_blocks(g->nint, 256);
+    with_elem(dtype, [&](auto ein) {
+        with_elem(g->prec, [&](auto e) {
+            using Tin = decltype(ein);
+            using T = decltype(e);
+            ingest_xy_kernel<Tin, T><<<blocks, 256, 0, g->stream>>>((const Tin *)src, (T *)g->v0, g->n[2], g->n[3],
+                                                                    g->p4, nxy, flag);
+            ingest_kernel<Tin, T><<<grid_blocks(nxy, 256), 256, 0, g->stream>>>((const Tin *)src, (T *)g->v0xy,
+                                                                                (int)nxy, (int)nxy, 1, flag);
+        });
+    });
+    set_v0_mode(g, true);
+    return finish_ingest(g);
+}
+
 static hj_status finish_ingest(hj_grid *g)
 {
     HJ_CUDA(cudaGetLastError());
@@ -599,6 +638,7 @@ hj_status hj_set_initial_value(hj_grid *g, const double *v0, size_t count)
         using T = decltype(e);
         ingest_kernel<double, T><<<blocks, 256, 0, g->stream>>>(staging, (T *)g->v0, g->n[3], g->p4, nrows, flag);
     });
+    set_v0_mode(g, false);
     return finish_ingest(g);
 }
 
@@ -614,13 +654,21 @@ hj_status hj_set_initial_value_xy(hj_grid *g, const double *v0_xy, size_t count)
     if ((s = reset_state(g)) != HJ_OK) return s;
     double *staging = (double *)g->buf;  // N1*N2 doubles fit in the ping-pong region
     HJ_CUDA(cudaMemcpyAsync(staging, v0_xy, sizeof(double) * (size_t)nxy, cudaMemcpyHostToDevice, g->stream));
-    int *flag = &g->dstate->nonfinite;
-    const int blocks = grid_blocks(g->nint, 256);
-    with_elem(g->prec, [&](auto e) {
-        using T = decltype(e);
-        ingest_xy_kernel<T><<<blocks, 256, 0, g->stream>>>(staging, (T *)g->v0, g->n[2], g->n[3], g->p4, nxy, flag);
-    });
-    return finish_ingest(g);
+    return ingest_xy(g, staging, HJ_FP64, nxy);
+}
+
+hj_status hj_set_initial_value_xy_device(hj_grid *g, const void *v0_xy_device, hj_precision dtype, size_t count)
+{
+    g_err[0] = 0;
+    hj_status s = check_grid(g);
+    if (s != HJ_OK) return s;
+    if (!v0_xy_device) return set_err(HJ_ERR_INVALID_ARG, "v0_xy_device is NULL");
+    if (!valid_prec(dtype)) return set_err(HJ_ERR_INVALID_ARG, "unknown dtype");
+    const long long nxy = (long long)g->n[0] * g->n[1];
+    if (count != (size_t)nxy) return set_err(HJ_ERR_INVALID_ARG, "count %zu != N1*N2 = %lld", count, nxy);
+    if ((s = activate(g)) != HJ_OK) return s;
+    if ((s = reset_state(g)) != HJ_OK) return s;
+    return ingest_xy(g, v0_xy_device, dtype, nxy);
 }
 
 hj_status hj_set_initial_value_device(hj_grid *g, const void *v0_device, hj_precision dtype, size_t count)
@@ -645,6 +693,7 @@ hj_status hj_set_initial_value_device(hj_grid *g, const void *v0_device, hj_prec
                                                                  nrows, flag);
         });
     });
+    set_v0_mode(g, false);
     return finish_ingest(g);
 }
 
@@ -986,7 +1035,14 @@ hj_status hj_autotune(hj_grid *g, int32_t steps_per_trial, hj_tile_result *resul
         memcpy(g->tile_req, best_req, sizeof(best_req));
     else
         memcpy(g->tile_req, keep, sizeof(keep));
-    hj_tiled_setup(g, why, sizeof(why));
+    if (!hj_tiled_setup(g, why, sizeof(why)) && s == HJ_OK)
+        s = set_err(HJ_ERR_CUDA, "autotune: the chosen tile shape (%d, %d, %d, %d) was rejected: %s", g->tile_req[0],
+                    g->tile_req[1], g->tile_req[2], g->tile_req[3], why);
+    else if (s == HJ_OK && best < 1e300 &&
+             (g->tile_ty != best_req[0] || g->tile_tv != best_req[1] || g->tile_xc != best_req[2] ||
+              g->tile_stages != best_req[3]))
+        s = set_err(HJ_ERR_CUDA, "autotune: tile shape (%d, %d, %d, %d) came out as (%d, %d, %d, %d)", best_req[0],
+                    best_req[1], best_req[2], best_req[3], g->tile_ty, g->tile_tv, g->tile_xc, g->tile_stages);
     *g->hstate = saved;
     cudaMemcpyAsync(g->dstate, g->hstate, sizeof(HjDevState), cudaMemcpyHostToDevice, g->stream);
     cudaStreamSynchronize(g->stream);
@@ -1011,6 +1067,7 @@ hj_status hj_get_info(const hj_grid *g, hj_grid_info *info)
     }
     info->pitch4 = g->p4;
     info->precision = g->prec;
+    info->v0_broadcast = g->v0_bcast ? 1 : 0;
     info->kernel = effective_kernel(g);
     info->periodic_mask = g->periodic;
     info->has_value = g->has_value;

@@ -81,6 +81,8 @@ struct hj_grid {
     void *coef;            // HjCoef<T>[n3*n4]
     HjScaledCoef *scaled;  // FP64 grids: dt-scaled coefficients [n3*n4]
     int32_t *qw;           // Q5.27 grids: fixed-point axis weights (hj_rescale_qweights)
+    void *v0xy;            // V0 as an N1 x N2 field (element type of the grid), when V0 depends on x, y only
+    bool v0_bcast;         // V0 was set from the (x, y) field: the tiled kernel reads v0xy
     float *tab_tiled;      // tiled-kernel tables: v_k [n3], cos/dx1 [p4], sin/dx2 [p4], quad signs [p4]
     HjDevState *dstate;
     HjDevState *hstate;    // pinned host mirror

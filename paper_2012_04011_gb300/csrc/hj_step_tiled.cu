@@ -30,6 +30,10 @@
 // exact integer upwind differences (ghosts by flag, as minus the difference
 // on the other side), per-(v, theta) weights from the fixed-point table, and
 // the FP64 coefficient table for alpha^max.
+// Broadcast V0 (BCAST): when V0 depends on (x, y) only (Eq. init_V), the
+// grid keeps its N1 x N2 field and the kernel reads V0 from it (one scalar
+// per row and plane, an L1/L2 hit) instead of a V0 box per plane: 8
+// algorithmic bytes per cell-update instead of 12.
 // Every mbarrier wait is bounded by %globaltimer; on timeout the kernel
 // records HJ_ERR_TIMEOUT in the device state, stops issuing work, waits
 // (bounded) for its own copies in flight and returns.
@@ -58,7 +62,7 @@ struct TiledParams {
     int nchunk, nitems;  // x chunks per column; work items = ncol * nchunk
     int halo_box;        // floats in the V box with halo: p4 * (tv + 2) * (ty + 2)
     int halo_floats;     // its room in a stage: halo_box rounded up to 32 floats (V0 box 128-byte aligned)
-    int v0_floats;       // V0 box: p4 * tv * ty
+    int v0_floats;       // V0 box: p4 * tv * ty (0 with the broadcast V0)
     int stage_bytes;     // (halo_floats + v0_floats) * 4 rounded up to 128
     float k3, k4, mk34;  // |xdot_3|/dx_3, |xdot_4|/dx_4, -(k3 + k4): constant-bank operands
 };
@@ -86,12 +90,14 @@ __device__ __forceinline__ int32_t f4geti(const float4 &v, int e) { return __flo
 // PADDED: N4 is not a multiple of 4 (the last quad of a row has pad lanes).
 // USIGN: cos(theta) and sin(theta) have one sign (up to negligible values)
 // across every theta quad, so each thread picks its x and y upwind sides once.
-template <bool FIXED, bool PADDED, bool USIGN, int MAXC>
+// BCAST: V0 comes from the N1 x N2 field v0xy.
+template <bool FIXED, bool PADDED, bool USIGN, bool BCAST, int MAXC>
 __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
     const __grid_constant__ CUtensorMap map_v0, const __grid_constant__ CUtensorMap map_a,
     const __grid_constant__ CUtensorMap map_b, const __grid_constant__ CUtensorMap map_v0_tile,
     float *__restrict__ buf, const void *__restrict__ coefv, const float *__restrict__ tab,
-    int32_t *__restrict__ qw, HjDevState *st, const HjGeom g, const TiledParams P, long long nint)
+    int32_t *__restrict__ qw, const float *__restrict__ v0xy, HjDevState *st, const HjGeom g, const TiledParams P,
+    long long nint)
 {
     const HjCoef<float> *coef = (const HjCoef<float> *)coefv;     // FP32 grids
     const HjCoef<double> *coefd = (const HjCoef<double> *)coefv;  // Q5.27 grids
@@ -153,7 +159,8 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
                         ok = false;
                         break;
                     }
-                    const bool interior = p >= it.x0 && p < it.x1;  // V0 is needed on updated planes only
+                    // V0 is needed on updated planes only (and never as a box with the broadcast V0)
+                    const bool interior = !BCAST && p >= it.x0 && p < it.x1;
                     float *dst = stages + (size_t)slot * (P.stage_bytes / 4);
                     mbar_arrive_expect_tx(&full[slot], tx_halo + (interior ? tx_v0 : 0u));
                     tma_load_4d(dst, map_in, &full[slot], 0, it.v0 - 1, it.y0 - 1, p);
@@ -279,6 +286,8 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
                     nsum[e] = -(aw1[e] + aw2[e] + qw3 + qw4);
                 }
             }
+            float v0next = 0.f;  // broadcast V0 of the next plane (loaded one plane ahead)
+            if (BCAST && rok) v0next = __ldg(v0xy + (size_t)it.x0 * N2 + y);
             // ghosts this row needs: 1 y-1, 2 y+1, 4 v-1, 8 v+1
             const uint32_t gmask = (y == 0 ? 1u : 0u) | (y == N2 - 1 ? 2u : 0u) | (v == 0 ? 4u : 0u) |
                                    (v == N3 - 1 ? 8u : 0u);
@@ -302,6 +311,11 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
                     break;
                 }
                 const float *sx = stages + (size_t)s_x * sfl;
+                float v0s = 0.f;
+                if (BCAST) {
+                    v0s = v0next;
+                    if (rok && x + 1 < it.x1) v0next = __ldg(v0xy + (size_t)(x + 1) * N2 + y);
+                }
                 // centre of plane x+1, or the extrapolated ghost past the end
                 int s_n = -1;
                 float4 prev, nxt;
@@ -335,7 +349,7 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
                     const float tl = row0[lm], tr = row0[lp];
                     float t0 = 0.f;
                     if (PADDED) t0 = row0[0];
-                    const float4 v0c = *(const float4 *)(sx + r0sm);
+                    const float4 v0c = BCAST ? make_float4(v0s, v0s, v0s, v0s) : *(const float4 *)(sx + r0sm);
                     float4 xu = nxt, yu = yp;  // upwind x / y neighbours (USIGN)
                     if (USIGN) {
                         if (!xplus) xu = prev;
@@ -468,25 +482,36 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
 }
 
 typedef void (*KernelFn)(const CUtensorMap, const CUtensorMap, const CUtensorMap, const CUtensorMap, float *,
-                         const void *, const float *, int32_t *, HjDevState *, const HjGeom, const TiledParams,
-                         long long);
+                         const void *, const float *, int32_t *, const float *, HjDevState *, const HjGeom,
+                         const TiledParams, long long);
 
-template <bool FIXED, bool PADDED, bool USIGN>
+template <bool FIXED, bool PADDED, bool USIGN, bool BCAST>
 KernelFn kernel_fn_pu(int nconsumer)
 {
-    if (nconsumer <= VARIANTS[0]) return hj_step_tiled_kernel<FIXED, PADDED, USIGN, VARIANTS[0]>;
-    if (nconsumer <= VARIANTS[1]) return hj_step_tiled_kernel<FIXED, PADDED, USIGN, VARIANTS[1]>;
-    if (nconsumer <= VARIANTS[2]) return hj_step_tiled_kernel<FIXED, PADDED, USIGN, VARIANTS[2]>;
-    return hj_step_tiled_kernel<FIXED, PADDED, USIGN, VARIANTS[3]>;
+    if (nconsumer <= VARIANTS[0]) return hj_step_tiled_kernel<FIXED, PADDED, USIGN, BCAST, VARIANTS[0]>;
+    if (nconsumer <= VARIANTS[1]) return hj_step_tiled_kernel<FIXED, PADDED, USIGN, BCAST, VARIANTS[1]>;
+    if (nconsumer <= VARIANTS[2]) return hj_step_tiled_kernel<FIXED, PADDED, USIGN, BCAST, VARIANTS[2]>;
+    return hj_step_tiled_kernel<FIXED, PADDED, USIGN, BCAST, VARIANTS[3]>;
 }
 
-// The fixed-point variant selects the upwind side per lane (no USIGN form).
-KernelFn kernel_fn(bool fixed, bool padded, bool usign, int nconsumer)
+template <bool BCAST>
+KernelFn kernel_fn_b(bool fixed, bool padded, bool usign, int nconsumer)
 {
-    if (fixed) return padded ? kernel_fn_pu<true, true, false>(nconsumer) : kernel_fn_pu<true, false, false>(nconsumer);
+    // the fixed-point variant selects the upwind side per lane (no USIGN form)
+    if (fixed)
+        return padded ? kernel_fn_pu<true, true, false, BCAST>(nconsumer)
+                      : kernel_fn_pu<true, false, false, BCAST>(nconsumer);
     if (padded)
-        return usign ? kernel_fn_pu<false, true, true>(nconsumer) : kernel_fn_pu<false, true, false>(nconsumer);
-    return usign ? kernel_fn_pu<false, false, true>(nconsumer) : kernel_fn_pu<false, false, false>(nconsumer);
+        return usign ? kernel_fn_pu<false, true, true, BCAST>(nconsumer)
+                     : kernel_fn_pu<false, true, false, BCAST>(nconsumer);
+    return usign ? kernel_fn_pu<false, false, true, BCAST>(nconsumer)
+                 : kernel_fn_pu<false, false, false, BCAST>(nconsumer);
+}
+
+KernelFn kernel_fn(bool fixed, bool padded, bool usign, bool bcast, int nconsumer)
+{
+    return bcast ? kernel_fn_b<true>(fixed, padded, usign, nconsumer)
+                 : kernel_fn_b<false>(fixed, padded, usign, nconsumer);
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
@@ -522,7 +547,7 @@ TiledParams make_params(const hj_grid *g, int ty, int tv, int stages, int xc)
     P.ncol = ((g->n[1] + ty - 1) / ty) * P.ncol_v;
     P.halo_box = g->p4 * (tv + 2) * (ty + 2);
     P.halo_floats = (P.halo_box + 31) / 32 * 32;
-    P.v0_floats = g->p4 * tv * ty;
+    P.v0_floats = g->v0_bcast ? 0 : g->p4 * tv * ty;
     P.stage_bytes = ((P.halo_floats + P.v0_floats) * 4 + 127) / 128 * 128;
     P.xc = xc < 1 ? g->n[0] : (xc > g->n[0] ? g->n[0] : xc);
     P.nchunk = (g->n[0] + P.xc - 1) / P.xc;
@@ -657,7 +682,7 @@ bool hj_tiled_setup(hj_grid *g, char *why, size_t why_len)
     if (P.nconsumer > MAX_CONSUMERS) return fail("tile needs too many threads");
     size_t smem = tiled_smem_bytes(P);
     if ((int)smem > maxsmem) return fail("tile does not fit in shared memory");
-    const void *fn = (const void *)kernel_fn(fixed, g->p4 != g->n[3], usign, P.nconsumer);
+    const void *fn = (const void *)kernel_fn(fixed, g->p4 != g->n[3], usign, g->v0_bcast, P.nconsumer);
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return fail("cannot raise the shared-memory limit");
     int per_sm = 0;
@@ -700,9 +725,9 @@ bool hj_tiled_setup(hj_grid *g, char *why, size_t why_len)
 cudaError_t hj_launch_step_tiled(hj_grid *g)
 {
     const TiledParams P = make_params(g, g->tile_ty, g->tile_tv, g->tile_stages, g->tile_xc);
-    KernelFn fn = kernel_fn(g->prec == HJ_Q527, g->p4 != g->n[3], g->tiled_usign, P.nconsumer);
+    KernelFn fn = kernel_fn(g->prec == HJ_Q527, g->p4 != g->n[3], g->tiled_usign, g->v0_bcast, P.nconsumer);
     fn<<<g->tiled_ctas, P.nconsumer + 32, tiled_smem_bytes(P), g->stream>>>(
-        g->tmap[0], g->tmap[1], g->tmap[2], g->tmap[3], (float *)g->buf, g->coef, g->tab_tiled, g->qw, g->dstate,
-        g->geom, P, g->nint);
+        g->tmap[0], g->tmap[1], g->tmap[2], g->tmap[3], (float *)g->buf, g->coef, g->tab_tiled, g->qw,
+        (const float *)g->v0xy, g->dstate, g->geom, P, g->nint);
     return cudaGetLastError();
 }

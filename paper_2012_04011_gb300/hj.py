@@ -81,6 +81,7 @@ class hj_grid_info(ctypes.Structure):
         ("device_bytes", ctypes.c_size_t),
         ("tile", ctypes.c_int32 * 4),
         ("tile_ctas", ctypes.c_int32),
+        ("v0_broadcast", ctypes.c_int32),
     ]
 
     def as_dict(self) -> dict:
@@ -140,6 +141,7 @@ _SIGS = {
     "hj_set_dynamics": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_int32]),
     "hj_set_initial_value": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.c_size_t]),
     "hj_set_initial_value_device": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_size_t]),
+    "hj_set_initial_value_xy_device": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_size_t]),
     "hj_set_initial_value_xy": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.c_size_t]),
     "hj_batch_set_initial_value_xy": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
                                                      ctypes.c_size_t]),
@@ -279,6 +281,12 @@ def hj_set_initial_value(g, v0: np.ndarray):
 def hj_set_initial_value_xy(g, v0_xy: np.ndarray):
     a = np.ascontiguousarray(v0_xy, dtype=np.float64)
     _check(lib.hj_set_initial_value_xy(g, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), a.size))
+
+
+def hj_set_initial_value_xy_device(g, v0_xy_device, count: int | None = None, dtype: int | None = None):
+    cnt = int(v0_xy_device.numel()) if count is None else int(count)
+    code = _dtype_code(v0_xy_device) if dtype is None else int(dtype)
+    _check(lib.hj_set_initial_value_xy_device(g, ctypes.c_void_p(_dptr(v0_xy_device)), code, cnt))
 
 
 def hj_set_initial_value_device(g, v0_device, count: int | None = None, dtype: int | None = None):
