@@ -33,6 +33,7 @@ _LIB_PATH = os.path.join(_OUT_DIR, "libhj_oracle.so")
 
 DYN_CAR4D = 0  # params (a_max, w_max): x'=v cos th, y'=v sin th, v'=a, th'=w
 DYN_CONST = 1  # params (c1, c2, c3, c4): xdot = c, no control
+DYN_CAR4D_STEER = 2  # params (a_max, delta_max, L): th' = v tan(delta) / L (Eq. car_dynamics)
 
 _lock = threading.Lock()
 _lib = None

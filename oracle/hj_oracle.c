@@ -38,7 +38,10 @@
  *                                                             (hjo_spacing)
  *   - car dynamics of the experiments (Sec. IV-A, Eq. car_dynamics) with the
  *     heading rate used as a bounded control w: x' = v cos th, y' = v sin th,
- *     v' = a, th' = w, |a| <= a_max, |w| <= w_max, no disturbance.
+ *     v' = a, th' = w, |a| <= a_max, |w| <= w_max, no disturbance; and the
+ *     paper's own steering form th' = v tan(delta) / L, |delta| <= delta_max
+ *     (Eq. car_dynamics as printed: a in [-1.5, 1.5], delta in
+ *     [-pi/18, pi/18], L = 0.3 m).
  *
  * Compiled with -O2 -ffp-contract=off (no fused multiply-add), scalar code,
  * optional OpenMP over the slowest axis only: the only cross-cell reduction
@@ -55,6 +58,7 @@
 
 #define HJO_DYN_CAR4D 0 /* params {a_max, w_max} */
 #define HJO_DYN_CONST 1 /* params {c1, c2, c3, c4}: xdot = c, no control */
+#define HJO_DYN_CAR4D_STEER 2 /* params {a_max, delta_max, L}: th' = v tan(delta) / L */
 
 typedef struct {
     int32_t n[4];       /* grid points per axis, axis 4 (theta) fastest */
@@ -176,6 +180,18 @@ static double cell_rate(const hjo_problem *P, const hjo_tables *T, const double 
         xdot[1] = v * T->sin_th[idx[3]];
         xdot[2] = a_opt;
         xdot[3] = w_opt;
+    } else if (P->dyn == HJO_DYN_CAR4D_STEER) {
+        double a_max = P->p[0], d_max = P->p[1], L = P->p[2];
+        double v = T->v[idx[2]];
+        /* p_4 v tan(delta) / L is increasing in delta when p_4 v >= 0 (tan
+         * is increasing on (-pi/2, pi/2)): delta_opt is the bound with the
+         * sign of p_4 v. */
+        double a_opt = (p[2] >= 0.0) ? a_max : -a_max;
+        double d_opt = (p[3] * v >= 0.0) ? d_max : -d_max;
+        xdot[0] = v * T->cos_th[idx[3]];
+        xdot[1] = v * T->sin_th[idx[3]];
+        xdot[2] = a_opt;
+        xdot[3] = v * tan(d_opt) / L;
     } else {
         for (int d = 0; d < 4; ++d)
             xdot[d] = P->p[d];
@@ -443,12 +459,12 @@ static int64_t q_ghost_value(const hjo_problem *P, const hjo_tables *T, const in
  * components; the constant field) and |xdot_d| for the CFL sum. */
 static void q_xdot_abs(const hjo_problem *P, const hjo_tables *T, const int idx[4], double a[4])
 {
-    if (P->dyn == HJO_DYN_CAR4D) {
+    if (P->dyn == HJO_DYN_CAR4D || P->dyn == HJO_DYN_CAR4D_STEER) {
         double v = T->v[idx[2]];
         a[0] = fabs(v * T->cos_th[idx[3]]);
         a[1] = fabs(v * T->sin_th[idx[3]]);
         a[2] = P->p[0];
-        a[3] = P->p[1];
+        a[3] = P->dyn == HJO_DYN_CAR4D ? P->p[1] : fabs(v) * tan(P->p[1]) / P->p[2];
     } else {
         for (int d = 0; d < 4; ++d)
             a[d] = fabs(P->p[d]);
@@ -468,7 +484,7 @@ static int32_t q_cell(const hjo_problem *P, const hjo_tables *T, const int32_t *
         int64_t dp = q_ghost_value(P, T, Q, c, idx, d, +1) - Vc; /* dx_d D+_d */
         int64_t W = q_weight(dt, xa[d], T->h[d]);                /* dt |xdot_d| / dx_d */
         int sgn;                                                  /* sign of xdot_d */
-        if (P->dyn == HJO_DYN_CAR4D) {
+        if (P->dyn == HJO_DYN_CAR4D || P->dyn == HJO_DYN_CAR4D_STEER) {
             if (d == 0)
                 sgn = T->v[idx[2]] * T->cos_th[idx[3]] >= 0.0 ? 1 : -1;
             else if (d == 1)

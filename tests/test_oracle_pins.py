@@ -369,3 +369,65 @@ def test_car_cfl_step(oracle_mod, name, steps):
     dt = 0.8 / (4 / h[0] + 4 / h[1] + 1.5 / h[2] + 1 / h[3])
     assert oracle.cfl_dt(P, am, 0.8) == pytest.approx(dt, rel=1e-15)
     assert math.ceil(w.T / dt) == steps
+
+
+# ---------------------------------------------------------------- steering form (Eq. car_dynamics)
+
+STEER = (1.5, math.pi / 18, 0.3)  # a in [-1.5, 1.5], delta in [-pi/18, pi/18], L = 0.3 m (Sec. IV-A)
+
+
+def steer_problem(grid, a_max=STEER[0], d_max=STEER[1], L=STEER[2]):
+    return oracle.Problem(grid.n, grid.lo, grid.hi, grid.periodic, oracle.DYN_CAR4D_STEER, (a_max, d_max, L))
+
+
+def test_steer_zero_angle_is_car_without_turning(oracle_mod):
+    """delta_max = 0: th' = 0 for every control, which is the heading-rate car
+    with w_max = 0, bit for bit."""
+    w = scenes.custom_workload((13, 11, 7, 12), n_circles=3, T=0.5, seed=4)
+    V0 = scenes.initial_value(w.grid, w.scene)
+    Vs, ds = oracle.solve(steer_problem(w.grid, d_max=0.0), V0, w.T)
+    Vc, dc = oracle.solve(car_problem(w.grid, scenes.A_MAX, 0.0), V0, w.T)
+    assert np.array_equal(ds, dc) and np.array_equal(Vs, Vc)
+
+
+def test_steer_slice_is_car_with_speed_dependent_turn_rate(oracle_mod):
+    """With a_max = 0 no cell moves in v, so on the slice v = v_k the steering
+    car is the heading-rate car with w_max = v_k tan(delta_max) / L: one step
+    of the same dt agrees bit for bit on that slice.  A missing v factor, a
+    wrong L, sin for tan or an argmin steering angle breaks it."""
+    w = scenes.custom_workload((9, 10, 6, 16), n_circles=3, seed=8)
+    V0 = scenes.initial_value(w.grid, w.scene)
+    rng = np.random.default_rng(3)
+    V = V0 + 0.05 * rng.standard_normal(V0.shape)  # a V that depends on theta too
+    Ps = steer_problem(w.grid, a_max=0.0)
+    dt = 0.01
+    for k in (0, 2, 5):
+        vk = Ps.coord(2, k)
+        Pc = car_problem(w.grid, 0.0, vk * math.tan(STEER[1]) / STEER[2])
+        cells = np.array([((i * 10 + j) * 6 + k) * 16 + l for i in range(9) for j in range(10) for l in range(16)])
+        assert np.array_equal(oracle.step_cells(Ps, V, V0, dt, cells), oracle.step_cells(Pc, V, V0, dt, cells)), k
+
+
+def test_steer_cfl_alpha_closed_form(oracle_mod):
+    """alpha^max of the steering car: (max|v cos|, max|v sin|, a_max,
+    v_max tan(delta_max) / L)."""
+    grid = scenes.GridSpec((5, 5, 9, 8))
+    P = steer_problem(grid)
+    _, am = oracle.rate(P, np.zeros(grid.n))
+    vmax = P.coord(2, grid.n[2] - 1)
+    assert am[0] == vmax and am[2] == STEER[0]
+    assert am[3] == vmax * math.tan(STEER[1]) / STEER[2]
+    assert abs(am[1] - vmax) < 1e-12  # sin reaches 1 at theta = -pi/2 up to rounding
+
+
+def test_steer_mirror_symmetry(oracle_mod):
+    """y -> -y with th -> -th maps the steering car onto itself (delta -> -delta)."""
+    N4 = 16
+    w = scenes.custom_workload((17, 17, 5, N4), n_circles=3, T=0.5, seed=31)
+    P = steer_problem(w.grid)
+    V0 = scenes.initial_value(w.grid, w.scene)
+    V, _ = oracle.solve(P, V0, w.T, nthreads=4)
+    l = np.arange(N4)
+    f = lambda A: A[:, ::-1, :, :][..., (N4 - l) % N4]
+    Vm, _ = oracle.solve(P, np.ascontiguousarray(f(V0)), w.T, nthreads=4)
+    assert np.abs(Vm - f(V)).max() <= 1e-12 * np.abs(V0).max()

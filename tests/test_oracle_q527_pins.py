@@ -175,3 +175,22 @@ def test_solve_within_accumulated_bound_of_fp64(oracle_mod, name):
     bound = 0.5 + len(dv) * _per_step_bound_codes(np.abs(V0).max())
     assert err <= bound, (err, bound)
     assert err * ULP < 1e-6
+
+
+def test_steer_q527_within_bound_of_fp64(oracle_mod):
+    """The fixed-point variant of the steering car (per-speed heading weight)
+    stays within the accumulated per-step bound of the FP64 steering solve."""
+    w = scenes.custom_workload((21, 19, 9, 16), n_circles=4, T=0.6, seed=12)
+    P = oracle.Problem(w.grid.n, w.grid.lo, w.grid.hi, w.grid.periodic, oracle.DYN_CAR4D_STEER,
+                       (1.5, math.pi / 18, 0.3))
+    V0 = scenes.initial_value(w.grid, w.scene)
+    Q, dq = oracle.solve_q527(P, V0, w.T, w.cfl)
+    V, dv = oracle.solve(P, V0, w.T, w.cfl)
+    assert np.array_equal(dq, dv)
+    err = np.abs(oracle.from_q527(Q) - V).max() / ULP
+    assert err <= 0.5 + len(dv) * _per_step_bound_codes(np.abs(V0).max()), err
+    # one step from the same data: half a code plus the weight quantisation
+    Q1, _, d1 = oracle.advance_q527(P, oracle.to_q527(V0), Q, 0.0, 10.0, max_steps=1)
+    ref = oracle.step_cells(P, oracle.from_q527(Q), oracle.from_q527(oracle.to_q527(V0)), d1[0], np.arange(Q.size))
+    e1 = np.abs(oracle.from_q527(Q1).ravel() - ref) / ULP
+    assert e1.max() <= _per_step_bound_codes(np.abs(V0).max()) + 1e-6
