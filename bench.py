@@ -18,6 +18,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import re
 import subprocess
@@ -33,6 +34,7 @@ sys.path.insert(0, ROOT)
 METRIC = "4D HJ cell-updates/s (fraction of HBM peak) + p99 re-solve latency vs FP64 path"
 UNIT = "cell-updates/s"
 WORKLOAD = "car4d_128x128x64x96"
+STEER = (1.5, math.pi / 18, 0.3)  # Sec. IV-A: a in [-1.5, 1.5], delta in [-pi/18, pi/18], L = 0.3 m
 BYTES_PER_UPDATE = {"f32": 12, "f64": 24, "q527": 12, "f32_bcast": 8}
 PROFILE = os.path.join(ROOT, "profiles", "hj_step_tiled_car4d_128x128x64x96.md")
 KERNEL_SOURCES = ["hj_step_tiled.cu", "hj_device.cuh", "hj_tma.cuh", "hj_scaled.cuh", "hj_internal.h"]
@@ -267,13 +269,18 @@ def run_ours(args):
                                        ("f64", hj.HJ_FP64, out64, max(1, min(args.steps, args.fp64_steps)), 1),
                                        ("q527", hj.HJ_Q527, outq, max(1, min(args.steps, args.q527_steps)), 1),
                                        ("f32_bcast", hj.HJ_FP32, out32, max(1, min(args.steps, args.bcast_steps)),
+                                        1),
+                                       ("f32_steer", hj.HJ_FP32, out32, max(1, min(args.steps, args.steer_steps)),
                                         1)):
         if (prec_name == "f64" and args.no_fp64) or (prec_name == "q527" and args.no_q527) or \
-                (prec_name == "f32_bcast" and args.no_bcast):
+                (prec_name == "f32_bcast" and args.no_bcast) or (prec_name == "f32_steer" and args.no_steer):
             continue
         xy = prec_name == "f32_bcast"
         g = hj.Grid(w.grid.n, w.grid.lo, w.grid.hi, w.grid.periodic, prec, stream.cuda_stream)
-        g.set_dynamics(hj.HJ_DYN_CAR4D, (w.a_max, w.w_max))
+        if prec_name == "f32_steer":  # Eq. car_dynamics as printed: th' = v tan(delta) / L
+            g.set_dynamics(hj.HJ_DYN_CAR4D_STEER, STEER)
+        else:
+            g.set_dynamics(hj.HJ_DYN_CAR4D, (w.a_max, w.w_max))
         tuned = None
         if prec != hj.HJ_FP64 and args.tile:
             g.set_tile_shape([int(v) for v in args.tile.split(",")])
@@ -491,6 +498,17 @@ def run_ours(args):
                          "bytes_per_update": BYTES_PER_UPDATE["f32_bcast"], "peak_source": f"{peak_kind} hbm_gbs"},
             "tile": {k: v for k, v in (rb["tile"] or {}).items() if k != "tried"},
         }
+    if "f32_steer" in results:
+        rs = results["f32_steer"]
+        a_s = BYTES_PER_UPDATE["f32"] * ncell / (rs["avg_step_kernel_ms"] * 1e-3) / 1e9
+        line["steer_path"] = {
+            "workload": WORKLOAD + " with the steering car (a_max 1.5, delta_max pi/18, L 0.3 m), FP32",
+            "value": rs["value"], "unit": UNIT, "ms_per_step": rs["ms_per_step"], "steps": rs["K"],
+            "time_steps_per_solve": rs["time_steps_per_solve"], "avg_step_kernel_ms": rs["avg_step_kernel_ms"],
+            "roofline": {"bound": "hbm", "achieved": a_s, "peak": peak, "unit": "GB/s", "frac": a_s / peak,
+                         "bytes_per_update": BYTES_PER_UPDATE["f32"], "peak_source": f"{peak_kind} hbm_gbs"},
+            "tile": {k: v for k, v in (rs["tile"] or {}).items() if k != "tried"},
+        }
     if world == 1 and not args.no_cpu_baseline:
         nthreads = cpu_threads()
         rate, el, nst = oracle_sample(w, V0, args.cpu_sample_steps, nthreads)
@@ -517,6 +535,8 @@ def main():
     ap.add_argument("--no-q527", action="store_true")
     ap.add_argument("--bcast-steps", type=int, default=5)
     ap.add_argument("--no-bcast", action="store_true")
+    ap.add_argument("--steer-steps", type=int, default=3)
+    ap.add_argument("--no-steer", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")

@@ -88,7 +88,14 @@ typedef enum {
     HJ_DYN_CAR4D = 0,
     /* Constant velocity xdot = (p[0], p[1], p[2], p[3]), no control
      * (closed-form test cases). */
-    HJ_DYN_CONST = 1
+    HJ_DYN_CONST = 1,
+    /* The car of Eq. car_dynamics as printed in Sec. IV-A, steered by the
+     * wheel angle: x' = v cos(th), y' = v sin(th), v' = a,
+     * th' = v tan(delta) / L; |a| <= p[0] (a_max), |delta| <= p[1]
+     * (delta_max, 0 <= delta_max < pi/2), p[2] = L > 0 (the paper: 1.5,
+     * pi/18, 0.3 m).  The heading rate bound is |v| tan(delta_max) / L, so
+     * the theta dissipation varies with the speed. */
+    HJ_DYN_CAR4D_STEER = 2
 } hj_dynamics;
 
 /* Step-kernel selection (HJ_KERNEL_AUTO picks the fastest one that supports
@@ -154,8 +161,10 @@ HJ_API hj_status hj_create_grid(const int32_t n[4], const double lo[4], const do
                          hj_grid **out);
 
 /* Set the dynamics (Eq. main_ode; car: Eq. car_dynamics of Sec. IV-A with
- * th' = w).  params: HJ_DYN_CAR4D {a_max >= 0, w_max >= 0};
- * HJ_DYN_CONST {c1, c2, c3, c4}.  nparams must match (2 or 4), values finite.
+ * th' = w, or with the steering angle).  params: HJ_DYN_CAR4D {a_max >= 0,
+ * w_max >= 0}; HJ_DYN_CONST {c1, c2, c3, c4}; HJ_DYN_CAR4D_STEER {a_max >= 0,
+ * 0 <= delta_max < pi/2, L > 0}.  nparams must match (2, 4 or 3), values
+ * finite.
  * Uploads the (v, theta) state tables once (Sec. III-A keeps the state
  * vectors and cos/sin of theta in small on-chip look-up tables). */
 HJ_API hj_status hj_set_dynamics(hj_grid *g, hj_dynamics kind, const double *params, int32_t nparams);
@@ -244,7 +253,8 @@ HJ_API hj_status hj_autotune(hj_grid *g, int32_t steps_per_trial, hj_tile_result
  * step as hj_advance_brt, with the dt the caller gives (>= 0, finite).
  * Arrays are dense [N1][N2][N3][N4] of double (HJ_FP64) or float (HJ_FP32)
  * on the current device; v_out must not overlap v_in.  Grid, periodic mask
- * and dynamics are as for hj_create_grid and hj_set_dynamics.
+ * and dynamics are as for hj_create_grid and hj_set_dynamics (HJ_DYN_CAR4D
+ * and HJ_DYN_CONST; other kinds give HJ_ERR_INVALID_ARG).
  * alpha_max_out (host, may be NULL) receives alpha_d^max over the grid, from
  * which a caller forms the next CFL step (dt = CFL / sum_d alpha_d^max/dx_d).
  *

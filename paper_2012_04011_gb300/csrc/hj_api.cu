@@ -125,7 +125,8 @@ __global__ void readback_kernel(const T *__restrict__ src, Tout *__restrict__ ds
 // velocity depends only on v and theta).
 template <typename T>
 __global__ void prologue_kernel(HjDevState *st, const HjGeom g, const HjCoef<T> *__restrict__ coef, int ncoef,
-                                double T_end, double cfl, HjScaledCoef *scaled = nullptr, int32_t *qw = nullptr)
+                                double T_end, double cfl, HjScaledCoef *scaled = nullptr, int32_t *qw = nullptr,
+                                const double *k4 = nullptr)
 {
     __shared__ unsigned long long scratch[64];
     unsigned long long a1 = 0ull, a2 = 0ull;
@@ -175,8 +176,8 @@ __global__ void prologue_kernel(HjDevState *st, const HjGeom g, const HjCoef<T> 
         const volatile HjDevState *vs = st;
         const double dt = vs->dt;
         if (!vs->done && dt != vs->dt_scaled) {
-            if (scaled) hj_rescale_table(scaled, (const HjCoef<double> *)coef, ncoef, dt);
-            else hj_rescale_qweights(qw, (const HjCoef<double> *)coef, g.n3, g.n4, g.p4, g.k3, g.k4, dt);
+            if (scaled) hj_rescale_table(scaled, (const HjCoef<double> *)coef, k4, g.n3, g.n4, dt);
+            else hj_rescale_qweights(qw, (const HjCoef<double> *)coef, g.n3, g.n4, g.p4, g.k3, k4, dt);
             __syncthreads();
             if (threadIdx.x == 0) st->dt_scaled = dt;
         }
@@ -221,7 +222,7 @@ hj_status pull_state(hj_grid *g)
 hj_status upload_tables(hj_grid *g)
 {
     const int N3 = g->n[2], N4 = g->n[3], P4 = g->p4;
-    const bool car = g->dyn == HJ_DYN_CAR4D;
+    const bool car = g->dyn == HJ_DYN_CAR4D || g->dyn == HJ_DYN_CAR4D_STEER;
     // per-(v, theta) coefficients in FP64: xdot_1 = v cos(theta), xdot_2 = v sin(theta)
     size_t nco = (size_t)N3 * N4;
     double *f1 = (double *)malloc(sizeof(double) * nco), *f2 = (double *)malloc(sizeof(double) * nco);
@@ -249,15 +250,36 @@ hj_status upload_tables(hj_grid *g)
         tab[N3 + l] = (float)(hj_flush_trig(cos(th)) / g->h[0]);
         tab[N3 + P4 + l] = (float)(hj_flush_trig(sin(th)) / g->h[1]);
     }
-    const double k3 = g->geom.k3, k4 = g->geom.k4;
+    // theta coefficient per speed, |xdot_4| / dx_4: the steering car's heading
+    // rate bound is |v| tan(delta_max) / L; the other dynamics have one value
+    double *k4v = (double *)malloc(sizeof(double) * (size_t)N3);
+    float *k4f = (float *)malloc(2 * sizeof(float) * (size_t)N3);
+    const double k3 = g->geom.k3;
     hj_status st = HJ_OK;
+    if (!k4v || !k4f) st = set_err(HJ_ERR_OOM, "host allocation failed");
+    for (int k = 0; st == HJ_OK && k < N3; ++k) {
+        if (g->dyn == HJ_DYN_CAR4D_STEER) {
+            const double v = g->lo[2] + (double)k * g->h[2];
+            k4v[k] = (fabs(v) * tan(g->params[1])) / g->params[2] / g->h[3];
+        } else {
+            k4v[k] = g->geom.k4;
+        }
+        k4f[2 * k] = (float)k4v[k];
+        k4f[2 * k + 1] = (float)(-(k3 + k4v[k]));
+    }
+    if (st == HJ_OK) {
+        cudaError_t e = cudaMemcpy(g->k4tab, g->prec == HJ_FP32 ? (const void *)k4f : (const void *)k4v,
+                                   g->prec == HJ_FP32 ? 2 * sizeof(float) * N3 : sizeof(double) * N3,
+                                   cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) st = set_err(HJ_ERR_CUDA, "table upload: %s", cudaGetErrorString(e));
+    }
     if (g->prec != HJ_FP32) {
         HjCoef<double> *c = (HjCoef<double> *)malloc(sizeof(HjCoef<double>) * nco);
         if (!c) st = set_err(HJ_ERR_OOM, "host allocation failed");
         for (size_t i = 0; c && i < nco; ++i) {
             c[i].c1 = f1[i] / g->h[0];
             c[i].c2 = f2[i] / g->h[1];
-            c[i].ks = fabs(c[i].c1) + fabs(c[i].c2) + k3 + k4;
+            c[i].ks = fabs(c[i].c1) + fabs(c[i].c2) + k3 + k4v[i / N4];
             c[i].a1 = fabs(f1[i]);
             c[i].a2 = fabs(f2[i]);
         }
@@ -273,7 +295,7 @@ hj_status upload_tables(hj_grid *g)
             double c1 = f1[i] / g->h[0], c2 = f2[i] / g->h[1];
             c[i].c1 = (float)c1;
             c[i].c2 = (float)c2;
-            c[i].ks = (float)(fabs(c1) + fabs(c2) + k3 + k4);
+            c[i].ks = (float)(fabs(c1) + fabs(c2) + k3 + k4v[i / N4]);
             c[i].a1 = (float)fabs(f1[i]);
             c[i].a2 = (float)fabs(f2[i]);
         }
@@ -291,6 +313,8 @@ hj_status upload_tables(hj_grid *g)
     free(f1);
     free(f2);
     free(tab);
+    free(k4v);
+    free(k4f);
     return st;
 }
 
@@ -337,7 +361,7 @@ void launch_prologue(hj_grid *g, double T, double cfl)
                                                          cfl);
     else
         prologue_kernel<double><<<1, 256, 0, g->stream>>>(g->dstate, g->geom, (const HjCoef<double> *)g->coef, ncoef,
-                                                          T, cfl, g->scaled, g->qw);
+                                                          T, cfl, g->scaled, g->qw, (const double *)g->k4tab);
 }
 
 void free_grid(hj_grid *g)
@@ -350,6 +374,7 @@ void free_grid(hj_grid *g)
     if (g->scaled) cudaFree(g->scaled);
     if (g->qw) cudaFree(g->qw);
     if (g->v0xy) cudaFree(g->v0xy);
+    if (g->k4tab) cudaFree(g->k4tab);
     if (g->dstate) cudaFree(g->dstate);
     if (g->hstate) cudaFreeHost(g->hstate);
     for (int i = 0; i < 4; ++i)
@@ -472,13 +497,15 @@ hj_status hj_create_grid(const int32_t n[4], const double lo[4], const double hi
     if (e == cudaSuccess) e = cudaMalloc(&g->buf, 2 * arr);
     // FP64 coefficients for FP64 and Q5.27 grids (alpha^max and dt are FP64)
     const size_t coef_bytes = ncoef * (prec == HJ_FP32 ? sizeof(HjCoef<float>) : sizeof(HjCoef<double>));
-    const size_t qw_bytes = prec == HJ_Q527 ? sizeof(int32_t) * (2 * (size_t)n[2] * g->p4 + 4) : 0;
+    const size_t qw_bytes = prec == HJ_Q527 ? sizeof(int32_t) * (2 * (size_t)n[2] * g->p4 + HJ_QW_TAIL + n[2]) : 0;
+    const size_t k4_bytes = (size_t)n[2] * (prec == HJ_FP32 ? 2 * sizeof(float) : sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&g->coef, coef_bytes);
     if (e == cudaSuccess) e = cudaMalloc(&g->tab_tiled, sizeof(float) * ((size_t)n[2] + 3 * (size_t)g->p4));
     if (e == cudaSuccess && prec == HJ_FP64) e = cudaMalloc(&g->scaled, ncoef * sizeof(HjScaledCoef));
     if (e == cudaSuccess && prec == HJ_Q527) e = cudaMalloc(&g->qw, qw_bytes);
     const size_t xy_bytes = (size_t)n[0] * n[1] * g->esize;
     if (e == cudaSuccess) e = cudaMalloc(&g->v0xy, xy_bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&g->k4tab, k4_bytes);
     if (e == cudaSuccess) e = cudaMalloc(&g->dstate, sizeof(HjDevState));
     if (e == cudaSuccess) e = cudaHostAlloc(&g->hstate, sizeof(HjDevState), cudaHostAllocDefault);
     for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaEventCreate(&g->ev[i]);
@@ -489,7 +516,7 @@ hj_status hj_create_grid(const int32_t n[4], const double lo[4], const double hi
         return s;
     }
     g->device_bytes = 3 * arr + coef_bytes + qw_bytes + (prec == HJ_FP64 ? ncoef * sizeof(HjScaledCoef) : 0) +
-                      xy_bytes + sizeof(HjDevState);
+                      xy_bytes + k4_bytes + sizeof(HjDevState);
     hj_status s = reset_state(g);
     if (s == HJ_OK) {
         cudaError_t e2 = cudaStreamSynchronize(g->stream);
@@ -523,6 +550,12 @@ hj_status hj_set_dynamics(hj_grid *g, hj_dynamics kind, const double *params, in
     } else if (kind == HJ_DYN_CONST) {
         if (nparams != 4) return set_err(HJ_ERR_INVALID_ARG, "constant dynamics take 4 parameters");
         if (!finite_all(params, 4)) return set_err(HJ_ERR_INVALID_ARG, "parameters must be finite");
+    } else if (kind == HJ_DYN_CAR4D_STEER) {
+        if (nparams != 3)
+            return set_err(HJ_ERR_INVALID_ARG, "steering dynamics take 3 parameters (a_max, delta_max, L)");
+        if (!finite_all(params, 3) || params[0] < 0 || params[1] < 0 || !(params[1] < 1.5707963267948966) ||
+            !(params[2] > 0))
+            return set_err(HJ_ERR_INVALID_ARG, "need a_max >= 0, 0 <= delta_max < pi/2 and L > 0");
     } else {
         return set_err(HJ_ERR_INVALID_ARG, "unknown dynamics %d", (int)kind);
     }
@@ -545,6 +578,14 @@ hj_status hj_set_dynamics(hj_grid *g, hj_dynamics kind, const double *params, in
         G.mode4 = HJ_AXIS_CONTROL;
         G.alpha3 = params[0];
         G.alpha4 = params[1];
+    } else if (kind == HJ_DYN_CAR4D_STEER) {
+        // alpha_4^max = max_k |v_k| tan(delta_max) / L (the end points of the v axis)
+        G.mode3 = HJ_AXIS_CONTROL;
+        G.mode4 = HJ_AXIS_CONTROL;
+        G.alpha3 = params[0];
+        double vmax = 0.0;
+        for (int k = 0; k < g->n[2]; ++k) vmax = fmax(vmax, fabs(g->lo[2] + (double)k * g->h[2]));
+        G.alpha4 = (vmax * tan(params[1])) / params[2];
     } else {
         G.mode3 = params[2] >= 0 ? HJ_AXIS_PLUS : HJ_AXIS_MINUS;
         G.mode4 = params[3] >= 0 ? HJ_AXIS_PLUS : HJ_AXIS_MINUS;

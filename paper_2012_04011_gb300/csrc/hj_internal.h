@@ -39,10 +39,10 @@ struct HjDevState {
 
 // FP64 coefficients with dt folded in (per (v, theta)): w1 = dt xdot_1/dx_1,
 // w2 = dt xdot_2/dx_2 (signed: the sign picks the upwind side), w0 = 1 - dt
-// (|xdot_1|/dx_1 + |xdot_2|/dx_2 + k3 + k4).  V_new = w0 V_c + |w1| V_up1 +
-// |w2| V_up2 + dt k3 V_up3 + dt k4 V_up4.
+// (|xdot_1|/dx_1 + |xdot_2|/dx_2 + k3 + k4(v)), w4 = dt k4(v).  V_new = w0 V_c +
+// |w1| V_up1 + |w2| V_up2 + dt k3 V_up3 + w4 V_up4.
 struct HjScaledCoef {
-    double w1, w2, w0;
+    double w1, w2, w0, w4;  // w4 = dt |xdot_4| / dx_4 (depends on v for the steering car)
 };
 
 // Grid geometry handed to kernels by value.
@@ -81,6 +81,8 @@ struct hj_grid {
     void *coef;            // HjCoef<T>[n3*n4]
     HjScaledCoef *scaled;  // FP64 grids: dt-scaled coefficients [n3*n4]
     int32_t *qw;           // Q5.27 grids: fixed-point axis weights (hj_rescale_qweights)
+    void *k4tab;           // theta coefficient per speed: |xdot_4|/dx_4 (double[n3]; FP32 grids: float2[n3] of
+                           // (k4, -(k3 + k4)))
     void *v0xy;            // V0 as an N1 x N2 field (element type of the grid), when V0 depends on x, y only
     bool v0_bcast;         // V0 was set from the (x, y) field: the tiled kernel reads v0xy
     float *tab_tiled;      // tiled-kernel tables: v_k [n3], cos/dx1 [p4], sin/dx2 [p4], quad signs [p4]
@@ -135,15 +137,18 @@ cudaError_t hj_launch_prologue_f32(HjDevState *st, const HjGeom &g, const HjCoef
                                    double cfl, cudaStream_t stream);
 
 // Rescale the FP64 coefficient table for dt (all threads of one block call
-// it; the table covers ncoef entries).
-__device__ __forceinline__ void hj_rescale_table(HjScaledCoef *sc, const HjCoef<double> *coef, int ncoef, double dt)
+// it; the table covers n3 * n4 entries; k4 holds the theta coefficient of
+// each speed).
+__device__ __forceinline__ void hj_rescale_table(HjScaledCoef *sc, const HjCoef<double> *coef, const double *k4,
+                                                 int n3, int n4, double dt)
 {
-    for (int i = threadIdx.x; i < ncoef; i += blockDim.x) {
+    for (int i = threadIdx.x; i < n3 * n4; i += blockDim.x) {
         const HjCoef<double> c = coef[i];
         HjScaledCoef o;
         o.w1 = dt * c.c1;
         o.w2 = dt * c.c2;
         o.w0 = 1.0 - dt * c.ks;
+        o.w4 = dt * k4[i / n4];
         sc[i] = o;
     }
 }
@@ -173,10 +178,12 @@ __device__ __forceinline__ int32_t hj_qweight(double dt, double k)
 // Fixed-point weights for dt (all threads of one block call it):
 //   qw[k p4 + l]            x weight of (v_k, theta_l), signed with xdot_1
 //   qw[n3 p4 + k p4 + l]    y weight, signed with xdot_2
-//   qw[2 n3 p4 + 0 / 1]     v and theta weights (constant over the grid)
+//   qw[2 n3 p4]             v weight (constant over the grid)
+//   qw[2 n3 p4 + 4 + k]     theta weight of speed v_k
 // Pad lanes (l >= n4) get 0.
+constexpr int HJ_QW_TAIL = 4;  // entries between the y weights and the per-speed theta weights
 __device__ __forceinline__ void hj_rescale_qweights(int32_t *qw, const HjCoef<double> *coef, int n3, int n4, int p4,
-                                                    double k3, double k4, double dt)
+                                                    double k3, const double *k4, double dt)
 {
     const int tot = n3 * p4;
     for (int i = threadIdx.x; i < tot; i += blockDim.x) {
@@ -192,9 +199,10 @@ __device__ __forceinline__ void hj_rescale_qweights(int32_t *qw, const HjCoef<do
         qw[i] = w1;
         qw[tot + i] = w2;
     }
+    for (int k = threadIdx.x; k < n3; k += blockDim.x) qw[2 * tot + HJ_QW_TAIL + k] = hj_qweight(dt, k4[k]);
     if (threadIdx.x == 0) {
         qw[2 * tot] = hj_qweight(dt, k3);
-        qw[2 * tot + 1] = hj_qweight(dt, k4);
+        qw[2 * tot + 1] = 0;
     }
 }
 

@@ -13,7 +13,7 @@
 __device__ __forceinline__ void hj_step_epilogue_scaled(HjDevState *st, const HjGeom &g, unsigned long long a1,
                                                         unsigned long long a2, unsigned long long *scratch,
                                                         HjScaledCoef *scaled, int32_t *qw,
-                                                        const HjCoef<double> *coef)
+                                                        const HjCoef<double> *coef, const double *k4)
 {
     __shared__ int s_last;
     a1 = hj_warp_max_u64(a1);
@@ -41,8 +41,8 @@ __device__ __forceinline__ void hj_step_epilogue_scaled(HjDevState *st, const Hj
         const volatile HjDevState *vs = st;
         const double dtn = vs->dt;
         if (!vs->done && dtn != vs->dt_scaled) {
-            if (scaled) hj_rescale_table(scaled, coef, g.n3 * g.n4, dtn);
-            else hj_rescale_qweights(qw, coef, g.n3, g.n4, g.p4, g.k3, g.k4, dtn);
+            if (scaled) hj_rescale_table(scaled, coef, k4, g.n3, g.n4, dtn);
+            else hj_rescale_qweights(qw, coef, g.n3, g.n4, g.p4, g.k3, k4, dtn);
             __syncthreads();
             if (threadIdx.x == 0) {
                 st->dt_scaled = dtn;

@@ -134,8 +134,8 @@ __device__ __forceinline__ long long q_upwind(const QDiff &d, int mode)
 template <bool FAST32>
 __global__ void __launch_bounds__(256) hj_step_q527_kernel(const int32_t *__restrict__ v0, int32_t *__restrict__ buf,
                                                             const HjCoef<double> *__restrict__ coef, int32_t *qw,
-                                                            HjDevState *st, const HjGeom g, long long nint,
-                                                            const Divisors dv)
+                                                            const double *__restrict__ k4tab, HjDevState *st,
+                                                            const HjGeom g, long long nint, const Divisors dv)
 {
     __shared__ unsigned long long scratch[64];
     if (st->done) return;
@@ -148,7 +148,8 @@ __global__ void __launch_bounds__(256) hj_step_q527_kernel(const int32_t *__rest
     const long long s3 = g.p4, s2 = (long long)N3 * g.p4, s1 = (long long)N2 * s2;
     const unsigned long long ncell = (unsigned long long)N1 * N2 * N3 * N4;
     const int tot = (int)N3 * g.p4;
-    const int32_t w3 = qw[2 * tot], w4 = qw[2 * tot + 1];
+    const int32_t w3 = qw[2 * tot];
+    const int32_t *w4tab = qw + 2 * tot + HJ_QW_TAIL;  // theta weight per speed
     unsigned long long am1 = 0ull, am2 = 0ull;
 
     for (unsigned long long c = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; c < ncell;
@@ -182,20 +183,21 @@ __global__ void __launch_bounds__(256) hj_step_q527_kernel(const int32_t *__rest
         const long long d1 = w1 >= 0 ? dx.dp : dx.dm;
         const long long d2 = w2 >= 0 ? dy.dp : dy.dm;
         vout[o] = hj_q527_update(vc, v0[o], d1, d2, q_upwind(dv3, g.mode3), q_upwind(dv4, g.mode4), abs(w1), abs(w2),
-                                 w3, w4);
+                                 w3, w4tab[k]);
         const HjCoef<double> cf = coef[k * N4 + l];
         const unsigned long long b1 = hj_abits(cf.a1), b2 = hj_abits(cf.a2);
         am1 = am1 > b1 ? am1 : b1;
         am2 = am2 > b2 ? am2 : b2;
     }
-    hj_step_epilogue_scaled(st, g, am1, am2, scratch, nullptr, qw, coef);
+    hj_step_epilogue_scaled(st, g, am1, am2, scratch, nullptr, qw, coef, k4tab);
 }
 
 template <typename T, bool FAST32>
 __global__ void __launch_bounds__(256) hj_step_generic_kernel(const T *__restrict__ v0, T *__restrict__ buf,
                                                                const HjCoef<T> *__restrict__ coef,
-                                                               HjScaledCoef *scaled, HjDevState *st, const HjGeom g,
-                                                               long long nint, const Divisors dv)
+                                                               HjScaledCoef *scaled, const void *__restrict__ k4tab,
+                                                               HjDevState *st, const HjGeom g, long long nint,
+                                                               const Divisors dv)
 {
     __shared__ unsigned long long scratch[64];
     if (st->done) return;  // uniform: written by the previous kernel on this stream
@@ -208,10 +210,10 @@ __global__ void __launch_bounds__(256) hj_step_generic_kernel(const T *__restric
     const unsigned int N1 = g.n1, N2 = g.n2, N3 = g.n3, N4 = g.n4;
     const long long s3 = g.p4, s2 = (long long)N3 * g.p4, s1 = (long long)N2 * s2;
     const unsigned long long ncell = (unsigned long long)N1 * N2 * N3 * N4;
-    const T k3 = (T)g.k3, k4 = (T)g.k4;
-    // FP64: dt is folded into the per-(v, theta) table; the v/theta weights
-    // need it once per thread
-    const double k3dt = g.k3 * st->dt, k4dt = g.k4 * st->dt;
+    const T k3 = (T)g.k3;
+    // FP64: dt is folded into the per-(v, theta) table; the v weight needs it
+    // once per thread
+    const double k3dt = g.k3 * st->dt;
     unsigned long long am1 = 0ull, am2 = 0ull;
     float am1f = 0.f, am2f = 0.f;
 
@@ -258,7 +260,7 @@ __global__ void __launch_bounds__(256) hj_step_generic_kernel(const T *__restric
             r = fma(mag(sc.w1), u1, r);
             r = fma(mag(sc.w2), u2, r);
             r = fma(k3dt, u3, r);
-            vn = fma(k4dt, u4, r);
+            vn = fma(sc.w4, u4, r);
         } else {
             const T u1 = nonneg(cf.c1) ? nx.p : nx.m;
             const T u2 = nonneg(cf.c2) ? ny.p : ny.m;
@@ -266,7 +268,7 @@ __global__ void __launch_bounds__(256) hj_step_generic_kernel(const T *__restric
             T r = K1 * (u1 - vc);
             r = fmaf(K2, u2 - vc, r);
             r = fmaf(k3, u3 - vc, r);
-            r = fmaf(k4, u4 - vc, r);
+            r = fmaf(((const float2 *)k4tab)[k].x, u4 - vc, r);  // theta coefficient of this speed
             vn = fmaf(dt, r, vc);
         }
         vout[o] = hj_min(v0[o], vn);  // BRT min with the target (Algorithm 2)
@@ -287,7 +289,8 @@ __global__ void __launch_bounds__(256) hj_step_generic_kernel(const T *__restric
         am2 = hj_abits((double)am2f);
         hj_step_epilogue(st, g, am1, am2, scratch);
     } else {
-        hj_step_epilogue_scaled(st, g, am1, am2, scratch, scaled, nullptr, (const HjCoef<double> *)coef);
+        hj_step_epilogue_scaled(st, g, am1, am2, scratch, scaled, nullptr, (const HjCoef<double> *)coef,
+                                (const double *)k4tab);
     }
 }
 
@@ -309,16 +312,17 @@ cudaError_t hj_launch_step_generic(hj_grid *g)
     const bool fast = g->ncell < (1LL << 32);
 #define HJ_LAUNCH(T, F)                                                                                          \
     hj_step_generic_kernel<T, F><<<blocks, threads, 0, g->stream>>>(                                       \
-        (const T *)g->v0, (T *)g->buf, (const HjCoef<T> *)g->coef, g->scaled, g->dstate, g->geom, g->nint, dv)
+        (const T *)g->v0, (T *)g->buf, (const HjCoef<T> *)g->coef, g->scaled, g->k4tab, g->dstate, g->geom, \
+        g->nint, dv)
     if (g->prec == HJ_Q527) {
         if (fast)
             hj_step_q527_kernel<true><<<blocks, threads, 0, g->stream>>>(
-                (const int32_t *)g->v0, (int32_t *)g->buf, (const HjCoef<double> *)g->coef, g->qw, g->dstate, g->geom,
-                g->nint, dv);
+                (const int32_t *)g->v0, (int32_t *)g->buf, (const HjCoef<double> *)g->coef, g->qw,
+                (const double *)g->k4tab, g->dstate, g->geom, g->nint, dv);
         else
             hj_step_q527_kernel<false><<<blocks, threads, 0, g->stream>>>(
-                (const int32_t *)g->v0, (int32_t *)g->buf, (const HjCoef<double> *)g->coef, g->qw, g->dstate, g->geom,
-                g->nint, dv);
+                (const int32_t *)g->v0, (int32_t *)g->buf, (const HjCoef<double> *)g->coef, g->qw,
+                (const double *)g->k4tab, g->dstate, g->geom, g->nint, dv);
     } else if (g->prec == HJ_FP64) {
         if (fast) HJ_LAUNCH(double, true);
         else HJ_LAUNCH(double, false);

@@ -96,8 +96,8 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
     const __grid_constant__ CUtensorMap map_v0, const __grid_constant__ CUtensorMap map_a,
     const __grid_constant__ CUtensorMap map_b, const __grid_constant__ CUtensorMap map_v0_tile,
     float *__restrict__ buf, const void *__restrict__ coefv, const float *__restrict__ tab,
-    int32_t *__restrict__ qw, const float *__restrict__ v0xy, HjDevState *st, const HjGeom g, const TiledParams P,
-    long long nint)
+    int32_t *__restrict__ qw, const float *__restrict__ v0xy, const void *__restrict__ k4tab, HjDevState *st,
+    const HjGeom g, const TiledParams P, long long nint)
 {
     const HjCoef<float> *coef = (const HjCoef<float> *)coefv;     // FP32 grids
     const HjCoef<double> *coefd = (const HjCoef<double> *)coefv;  // Q5.27 grids
@@ -227,11 +227,8 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
         const int lp = (4 * q + 4) % N4;       // right of the quad
         const int lreal = min(4, N4 - 4 * q);  // real lanes (< 4 only in a padded last quad)
         const int qtot = N3 * P4;
-        int32_t qw3 = 0, qw4 = 0;  // fixed-point v and theta weights
-        if (FIXED) {
-            qw3 = qw[2 * qtot];
-            qw4 = qw[2 * qtot + 1];
-        }
+        int32_t qw3 = 0;  // fixed-point v weight
+        if (FIXED) qw3 = qw[2 * qtot];
 
         // Ring cursors.  Planes are waited for and released in load order, so
         // one cursor walks the slots to wait on (with the phase parity) and
@@ -266,6 +263,14 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
             const bool rok = inrow && y < N2 && v < N3;
             const uint32_t rbase = rok ? ((uint32_t)y * N3 + v) * P4 + 4 * q : 0u;
             const float vk = (rok && !FIXED) ? tab[v] : 0.f;
+            // theta coefficient of this row's speed (the steering car's heading
+            // rate bound grows with v): (k4, -(k3 + k4)), or the fixed-point weight
+            float2 k4m = make_float2(0.f, 0.f);
+            int32_t qw4 = 0;
+            if (rok) {
+                if (FIXED) qw4 = qw[2 * qtot + HJ_QW_TAIL + v];
+                else k4m = ((const float2 *)k4tab)[v];
+            }
             int4 qw1 = make_int4(0, 0, 0, 0), qw2 = make_int4(0, 0, 0, 0);  // signed x / y weights of the quad
             if (FIXED && rok) {
                 qw1 = *(const int4 *)(qw + v * P4 + 4 * q);
@@ -429,8 +434,8 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
                         }
                         in = fmaf(-cs[e], vc, in);
                         // v and theta: the bang-bang control takes the larger neighbour
-                        float acc = fmaf(P.k3, fmaxf(f4get(vp, e), f4get(vm, e)), P.mk34 * vc);
-                        acc = fmaf(P.k4, fmaxf(tp, tm), acc);
+                        float acc = fmaf(P.k3, fmaxf(f4get(vp, e), f4get(vm, e)), k4m.y * vc);
+                        acc = fmaf(k4m.x, fmaxf(tp, tm), acc);
                         acc = fmaf(vk, in, acc);
                         float vn = fminf(f4get(v0c, e), fmaf(dt, acc, vc));
                         if (PADDED && e >= lreal) vn = 0.f;
@@ -476,14 +481,14 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
         }
     }
     if constexpr (FIXED)
-        hj_step_epilogue_scaled(st, g, ab1, ab2, scratch, nullptr, qw, coefd);
+        hj_step_epilogue_scaled(st, g, ab1, ab2, scratch, nullptr, qw, coefd, (const double *)k4tab);
     else
         hj_step_epilogue(st, g, hj_abits((double)am1), hj_abits((double)am2), scratch);
 }
 
 typedef void (*KernelFn)(const CUtensorMap, const CUtensorMap, const CUtensorMap, const CUtensorMap, float *,
-                         const void *, const float *, int32_t *, const float *, HjDevState *, const HjGeom,
-                         const TiledParams, long long);
+                         const void *, const float *, int32_t *, const float *, const void *, HjDevState *,
+                         const HjGeom, const TiledParams, long long);
 
 template <bool FIXED, bool PADDED, bool USIGN, bool BCAST>
 KernelFn kernel_fn_pu(int nconsumer)
@@ -640,7 +645,8 @@ bool hj_tiled_setup(hj_grid *g, char *why, size_t why_len)
     if (g->prec != HJ_FP32 && g->prec != HJ_Q527) return fail("tiled kernel is FP32 or Q5.27 only");
     const bool fixed = g->prec == HJ_Q527;
     if (g->periodic != 0x8u) return fail("tiled kernel needs theta (axis 4) periodic and x, y, v not");
-    if (!g->has_dyn || g->dyn != HJ_DYN_CAR4D) return fail("tiled kernel needs the car dynamics");
+    if (!g->has_dyn || (g->dyn != HJ_DYN_CAR4D && g->dyn != HJ_DYN_CAR4D_STEER))
+        return fail("tiled kernel needs the car dynamics");
     if (g->p4 > 256) return fail("theta rows longer than 256 points");
     if (g->nint >= (1LL << 31)) return fail("grid too large for 32-bit offsets");
     EncodeTiledFn enc = get_encode_fn();
@@ -728,6 +734,6 @@ cudaError_t hj_launch_step_tiled(hj_grid *g)
     KernelFn fn = kernel_fn(g->prec == HJ_Q527, g->p4 != g->n[3], g->tiled_usign, g->v0_bcast, P.nconsumer);
     fn<<<g->tiled_ctas, P.nconsumer + 32, tiled_smem_bytes(P), g->stream>>>(
         g->tmap[0], g->tmap[1], g->tmap[2], g->tmap[3], (float *)g->buf, g->coef, g->tab_tiled, g->qw,
-        (const float *)g->v0xy, g->dstate, g->geom, P, g->nint);
+        (const float *)g->v0xy, g->k4tab, g->dstate, g->geom, P, g->nint);
     return cudaGetLastError();
 }

@@ -20,7 +20,7 @@ from . import _build
 HJ_OK, HJ_ERR_INVALID_ARG, HJ_ERR_STATE, HJ_ERR_OOM, HJ_ERR_CUDA, HJ_ERR_UNSTABLE, HJ_ERR_TIMEOUT, \
     HJ_ERR_UNSUPPORTED = range(8)
 HJ_FP64, HJ_FP32, HJ_Q527 = 0, 1, 2  # HJ_Q527: int32 codes, value = code * 2^-27
-HJ_DYN_CAR4D, HJ_DYN_CONST = 0, 1
+HJ_DYN_CAR4D, HJ_DYN_CONST, HJ_DYN_CAR4D_STEER = 0, 1, 2
 HJ_KERNEL_AUTO, HJ_KERNEL_GENERIC, HJ_KERNEL_TILED = 0, 1, 2
 PERIODIC_THETA = 0b1000
 
