@@ -85,6 +85,9 @@ def _load():
         lib.hjo_advance.argtypes = [P, dp, dp, dp, ctypes.c_double, ctypes.c_double, ctypes.c_int64,
                                     dp, ctypes.c_int]
         lib.hjo_advance.restype = ctypes.c_int64
+        lib.hjo_advance_converged.argtypes = [P, dp, dp, dp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                              ctypes.c_int64, dp, ctypes.c_int, dp, ctypes.POINTER(ctypes.c_int)]
+        lib.hjo_advance_converged.restype = ctypes.c_int64
         i32p = ctypes.POINTER(ctypes.c_int32)
         lib.hjo_to_q527.argtypes = [dp, ctypes.c_int64, i32p]
         lib.hjo_to_q527.restype = ctypes.c_int
@@ -207,6 +210,26 @@ def advance(P: Problem, V0, V, t: float, T: float, cfl: float = 0.8, max_steps: 
     if steps < 0:
         raise MemoryError("oracle allocation failed")
     return Vw, float(tt.value), dts[:steps].copy()
+
+
+def advance_converged(P: Problem, V0, V, t: float, threshold: float, T: float, cfl: float = 0.8,
+                      max_steps: int = 1 << 40, nthreads: int = 1):
+    """Step from (V, t) until a step changes V by less than threshold in the
+    max norm (Algorithm 2's convergence test), or t reaches T, or max_steps.
+    Returns (V_new, t_new, dts, eps_last, converged)."""
+    V0 = _as_grid(P, V0)
+    Vw = _as_grid(P, V).copy()
+    cap = int(min(max_steps, 1 << 20))
+    dts = np.zeros(cap)
+    tt = ctypes.c_double(float(t))
+    eps = ctypes.c_double(0.0)
+    conv = ctypes.c_int(0)
+    steps = _load().hjo_advance_converged(ctypes.byref(P._s), _dptr(V0), _dptr(Vw), ctypes.byref(tt), float(T),
+                                          float(cfl), float(threshold), cap, _dptr(dts), int(nthreads),
+                                          ctypes.byref(eps), ctypes.byref(conv))
+    if steps < 0:
+        raise MemoryError("oracle allocation failed")
+    return Vw, float(tt.value), dts[:steps].copy(), float(eps.value), bool(conv.value)
 
 
 def solve(P: Problem, V0, T: float, cfl: float = 0.8, nthreads: int = 1, max_steps: int = 1 << 40):

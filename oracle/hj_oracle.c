@@ -356,6 +356,47 @@ int64_t hjo_advance(const hjo_problem *P, const double *V0, double *V, double *t
     return s;
 }
 
+/* Algorithm 2's convergence test (the printed test is inverted; reading:
+ * keep stepping while the step changed V): from (V, *t), take steps as
+ * hjo_advance does and stop after the first step whose largest change
+ * max over the grid of |V_{n+1} - V_n| is below threshold, or at T_end, or
+ * after max_steps steps.  *eps_last receives that largest change of the last
+ * step (0 if none was taken) and *converged whether the test stopped the
+ * loop.  Returns the steps taken, or -1 on allocation failure. */
+int64_t hjo_advance_converged(const hjo_problem *P, const double *V0, double *V, double *t, double T_end,
+                              double cfl, double threshold, int64_t max_steps, double *dts, int nthreads,
+                              double *eps_last, int *converged)
+{
+    int64_t ncell = hjo_cell_count(P);
+    double *Vprev = (double *)malloc(sizeof(double) * (size_t)ncell);
+    if (!Vprev)
+        return -1;
+    int64_t s = 0;
+    *eps_last = 0.0;
+    *converged = 0;
+    while (*t < T_end && s < max_steps) {
+        memcpy(Vprev, V, sizeof(double) * (size_t)ncell);
+        double dt = 0.0;
+        if (hjo_advance(P, V0, V, t, T_end, cfl, 1, &dt, nthreads) != 1) {
+            free(Vprev);
+            return -1;
+        }
+        if (dts)
+            dts[s] = dt;
+        ++s;
+        double eps = 0.0; /* epsilon = |V_{t+1} - V_t| in the max norm */
+        for (int64_t c = 0; c < ncell; ++c)
+            eps = fmax(eps, fabs(V[c] - Vprev[c]));
+        *eps_last = eps;
+        if (eps < threshold) {
+            *converged = 1;
+            break;
+        }
+    }
+    free(Vprev);
+    return s;
+}
+
 /* Whole BRT solve from t = 0: V_out = V(T).  Returns the step count. */
 int64_t hjo_solve(const hjo_problem *P, const double *V0, double T_end, double cfl,
                   double *V_out, int64_t max_steps, double *dts, int nthreads)

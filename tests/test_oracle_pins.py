@@ -431,3 +431,50 @@ def test_steer_mirror_symmetry(oracle_mod):
     f = lambda A: A[:, ::-1, :, :][..., (N4 - l) % N4]
     Vm, _ = oracle.solve(P, np.ascontiguousarray(f(V0)), w.T, nthreads=4)
     assert np.abs(Vm - f(V)).max() <= 1e-12 * np.abs(V0).max()
+
+
+# ---------------------------------------------------------------- convergence test (Algorithm 2)
+
+def test_converged_stops_at_once_when_nothing_changes(oracle_mod):
+    """V0 = slope (v - 2) is a fixed point of the maximising car (see the
+    speed-target test): the first step changes nothing, so the convergence
+    test stops after one step with eps = 0."""
+    grid = scenes.GridSpec((5, 5, 9, 8))
+    P = car_problem(grid)
+    v = P.coords(2)
+    V0 = np.broadcast_to((v - 2.0)[None, None, :, None], grid.n).copy()
+    V, t, dts, eps, conv = oracle.advance_converged(P, V0, V0, 0.0, 1e-9, 50.0)
+    assert conv and eps == 0.0 and len(dts) == 1 and np.array_equal(V, V0)
+
+
+def test_converged_never_stops_on_a_moving_linear_field(oracle_mod):
+    """A linear field advected at constant speed drops by |c| dt every step
+    (closed form), so a threshold below that never triggers: the loop runs to
+    the horizon, and the last change is |c| dt_last."""
+    P2 = const_problem((9, 6, 5, 8), (0.4, 0.0, 0.0, 0.0))
+    x = P2.coords(0)
+    V0 = np.broadcast_to((1.0 - x)[:, None, None, None], P2.n).copy()
+    V, t, dts, eps, conv = oracle.advance_converged(P2, V0, V0, 0.0, 1e-3, 1.0)
+    assert not conv and t == 1.0
+    assert abs(eps - 0.4 * dts[-1]) <= 1e-12
+    Vf, dtf = oracle.solve(P2, V0, 1.0)
+    assert np.array_equal(V, Vf) and np.array_equal(dts, dtf)
+
+
+def test_converged_equals_fixed_steps_and_eps_is_the_max_change(oracle_mod):
+    """The convergence mode takes the same steps as the fixed-horizon loop;
+    eps is the max-norm change of the last step; the car's BRT settles, so a
+    moderate threshold stops it before a long horizon."""
+    w = scenes.custom_workload((15, 15, 7, 12), n_circles=3, seed=21)
+    P = car_problem(w.grid)
+    V0 = scenes.initial_value(w.grid, w.scene)
+    V, t, dts, eps, conv = oracle.advance_converged(P, V0, V0, 0.0, 2e-3, 30.0, nthreads=4)
+    assert conv and eps < 2e-3 and t < 30.0
+    n = len(dts)
+    Vn_1, t1, _ = oracle.advance(P, V0, V0, 0.0, 30.0, max_steps=n - 1, nthreads=4)
+    Vn, _, _ = oracle.advance(P, V0, Vn_1, t1, 30.0, max_steps=1, nthreads=4)
+    assert np.array_equal(Vn, V)
+    assert eps == float(np.abs(Vn - Vn_1).max())
+    # and the step before did not pass the test
+    Vm, _, _ = oracle.advance(P, V0, V0, 0.0, 30.0, max_steps=n - 2, nthreads=4)
+    assert float(np.abs(Vn_1 - Vm).max()) >= 2e-3
