@@ -117,6 +117,8 @@ typedef struct {
     double loop_ms;        /* device time of the time loop only (step kernels) */
     int32_t kernel;        /* hj_kernel actually used */
     int32_t launches;      /* kernels launched by this call */
+    double last_change;    /* hj_solve_converged: max |V_{n+1} - V_n| of the last step (0 otherwise) */
+    int32_t converged;     /* hj_solve_converged: the convergence test ended the loop */
 } hj_solve_stats;
 
 /* One tile shape of the tiled kernel and its measured step time. */
@@ -207,6 +209,17 @@ HJ_API hj_status hj_solve_brt(hj_grid *g, double T, double cfl, hj_solve_stats *
  * call continues.  Lets a caller bound the work of one call. */
 HJ_API hj_status hj_advance_brt(hj_grid *g, double T, double cfl, int64_t max_steps,
                          hj_solve_stats *stats);
+
+/* Algorithm 2's convergence test (the printed test is inverted; read as:
+ * keep stepping while a step changes V): integrate from the current (V, t)
+ * and stop after the first step whose largest change over the grid,
+ * max |V_{n+1} - V_n| (in the grid's precision, exact for Q5.27), is below
+ * threshold (> 0, finite), or when t reaches T_max, or after max_steps
+ * steps.  stats->converged says whether the test ended the loop and
+ * stats->last_change gives that step's largest change.  Same steps, dt and
+ * results as hj_advance_brt otherwise. */
+HJ_API hj_status hj_solve_converged(hj_grid *g, double threshold, double T_max, double cfl, int64_t max_steps,
+                                    hj_solve_stats *stats);
 
 /* Copy the current V into a HOST buffer of count = N1*N2*N3*N4 doubles
  * (caller-owned), layout above (exact for every precision). */

@@ -96,6 +96,10 @@ def _load():
         lib.hjo_advance_q527.argtypes = [P, i32p, i32p, dp, ctypes.c_double, ctypes.c_double, ctypes.c_int64,
                                          dp, ctypes.c_int]
         lib.hjo_advance_q527.restype = ctypes.c_int64
+        lib.hjo_advance_converged_q527.argtypes = [P, i32p, i32p, dp, ctypes.c_double, ctypes.c_double,
+                                                   ctypes.c_double, ctypes.c_int64, dp, ctypes.c_int, dp,
+                                                   ctypes.POINTER(ctypes.c_int)]
+        lib.hjo_advance_converged_q527.restype = ctypes.c_int64
         lib.hjo_step_cells_q527.argtypes = [P, i32p, i32p, ctypes.c_double, i64p, ctypes.c_int64, i32p]
         lib.hjo_step_cells_q527.restype = ctypes.c_int
         lib.hjo_max_threads.argtypes = []
@@ -309,3 +313,22 @@ def step_cells_q527(P: Problem, Q, Q0, dt: float, cells) -> np.ndarray:
     if rc:
         raise MemoryError("oracle allocation failed")
     return out
+
+
+def advance_converged_q527(P: Problem, Q0, Q, t: float, threshold: float, T: float, cfl: float = 0.8,
+                           max_steps: int = 1 << 40, nthreads: int = 1):
+    """advance_converged on the Q5.27 grid.  Returns (Q_new, t_new, dts,
+    eps_last, converged)."""
+    Q0 = _as_qgrid(P, Q0)
+    Qw = _as_qgrid(P, Q).copy()
+    cap = int(min(max_steps, 1 << 20))
+    dts = np.zeros(cap)
+    tt = ctypes.c_double(float(t))
+    eps = ctypes.c_double(0.0)
+    conv = ctypes.c_int(0)
+    steps = _load().hjo_advance_converged_q527(ctypes.byref(P._s), _ipt(Q0), _ipt(Qw), ctypes.byref(tt), float(T),
+                                               float(cfl), float(threshold), cap, _dptr(dts), int(nthreads),
+                                               ctypes.byref(eps), ctypes.byref(conv))
+    if steps < 0:
+        raise MemoryError("oracle allocation failed")
+    return Qw, float(tt.value), dts[:steps].copy(), float(eps.value), bool(conv.value)

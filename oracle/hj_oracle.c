@@ -621,3 +621,45 @@ int hjo_step_cells_q527(const hjo_problem *P, const int32_t *Q, const int32_t *Q
     tables_free(&T);
     return 0;
 }
+
+/* The convergence test of hjo_advance_converged on the Q5.27 grid: the
+ * largest change is max |Q_{n+1} - Q_n| in codes, as the exact value
+ * codes * 2^-27. */
+int64_t hjo_advance_converged_q527(const hjo_problem *P, const int32_t *Q0, int32_t *Q, double *t, double T_end,
+                                   double cfl, double threshold, int64_t max_steps, double *dts, int nthreads,
+                                   double *eps_last, int *converged)
+{
+    int64_t ncell = hjo_cell_count(P);
+    int32_t *Qprev = (int32_t *)malloc(sizeof(int32_t) * (size_t)ncell);
+    if (!Qprev)
+        return -1;
+    int64_t s = 0;
+    *eps_last = 0.0;
+    *converged = 0;
+    while (*t < T_end && s < max_steps) {
+        memcpy(Qprev, Q, sizeof(int32_t) * (size_t)ncell);
+        double dt = 0.0;
+        if (hjo_advance_q527(P, Q0, Q, t, T_end, cfl, 1, &dt, nthreads) != 1) {
+            free(Qprev);
+            return -1;
+        }
+        if (dts)
+            dts[s] = dt;
+        ++s;
+        int64_t m = 0;
+        for (int64_t c = 0; c < ncell; ++c) {
+            int64_t d = (int64_t)Q[c] - (int64_t)Qprev[c];
+            if (d < 0)
+                d = -d;
+            if (d > m)
+                m = d;
+        }
+        *eps_last = ldexp((double)m, -27);
+        if (*eps_last < threshold) {
+            *converged = 1;
+            break;
+        }
+    }
+    free(Qprev);
+    return s;
+}

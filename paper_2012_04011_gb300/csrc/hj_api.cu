@@ -126,7 +126,7 @@ __global__ void readback_kernel(const T *__restrict__ src, Tout *__restrict__ ds
 template <typename T>
 __global__ void prologue_kernel(HjDevState *st, const HjGeom g, const HjCoef<T> *__restrict__ coef, int ncoef,
                                 double T_end, double cfl, HjScaledCoef *scaled = nullptr, int32_t *qw = nullptr,
-                                const double *k4 = nullptr)
+                                const double *k4 = nullptr, double threshold = 0.0)
 {
     __shared__ unsigned long long scratch[64];
     unsigned long long a1 = 0ull, a2 = 0ull;
@@ -152,6 +152,12 @@ __global__ void prologue_kernel(HjDevState *st, const HjGeom g, const HjCoef<T> 
         }
         st->T = T_end;
         st->cfl = cfl;
+        // convergence mode (threshold > 0): the steps reduce max |V_{n+1} - V_n|
+        st->track = threshold > 0.0 ? 1 : 0;
+        st->threshold = threshold;
+        st->converged = 0;
+        st->delta_bits = 0ull;
+        st->delta_last = 0.0;
         double a[4];
         if (fresh) {
             a[0] = __longlong_as_double((long long)a1);
@@ -353,15 +359,16 @@ bool valid_prec(hj_precision p) { return p == HJ_FP64 || p == HJ_FP32 || p == HJ
 
 // Start of a solve call (horizon, Courant number, first dt, and the FP64 /
 // fixed-point tables scaled for it).
-void launch_prologue(hj_grid *g, double T, double cfl)
+void launch_prologue(hj_grid *g, double T, double cfl, double threshold = 0.0)
 {
     const int ncoef = g->n[2] * g->n[3];
     if (g->prec == HJ_FP32)
         prologue_kernel<float><<<1, 256, 0, g->stream>>>(g->dstate, g->geom, (const HjCoef<float> *)g->coef, ncoef, T,
-                                                         cfl);
+                                                         cfl, nullptr, nullptr, nullptr, threshold);
     else
         prologue_kernel<double><<<1, 256, 0, g->stream>>>(g->dstate, g->geom, (const HjCoef<double> *)g->coef, ncoef,
-                                                          T, cfl, g->scaled, g->qw, (const double *)g->k4tab);
+                                                          T, cfl, g->scaled, g->qw, (const double *)g->k4tab,
+                                                          threshold);
 }
 
 void free_grid(hj_grid *g)
@@ -738,11 +745,12 @@ hj_status hj_set_initial_value_device(hj_grid *g, const void *v0_device, hj_prec
     return finish_ingest(g);
 }
 
-hj_status hj_advance_brt(hj_grid *g, double T, double cfl, int64_t max_steps, hj_solve_stats *stats)
+// The time loop of hj_advance_brt and hj_solve_converged (threshold > 0:
+// Algorithm 2's convergence test ends the loop as well).
+static hj_status advance_impl(hj_grid *g, double T, double cfl, int64_t max_steps, double threshold,
+                              hj_solve_stats *stats)
 {
-    g_err[0] = 0;
-    hj_status s = check_grid(g);
-    if (s != HJ_OK) return s;
+    hj_status s = HJ_OK;
     if (!isfinite(T) || T < 0) return set_err(HJ_ERR_INVALID_ARG, "T must be finite and >= 0");
     if (!isfinite(cfl) || !(cfl > 0) || cfl > 1) return set_err(HJ_ERR_INVALID_ARG, "cfl must be in (0, 1]");
     if (max_steps < 0) return set_err(HJ_ERR_INVALID_ARG, "max_steps must be >= 0");
@@ -753,7 +761,7 @@ hj_status hj_advance_brt(hj_grid *g, double T, double cfl, int64_t max_steps, hj
     const hj_kernel kern = effective_kernel(g);
     int launches = 0;
     HJ_CUDA(cudaEventRecord(g->ev[0], g->stream));
-    launch_prologue(g, T, cfl);
+    launch_prologue(g, T, cfl, threshold);
     ++launches;
     HJ_CUDA(cudaGetLastError());
     if ((s = pull_state(g)) != HJ_OK) return s;
@@ -770,6 +778,7 @@ hj_status hj_advance_brt(hj_grid *g, double T, double cfl, int64_t max_steps, hj
             k = r > 1 ? (r < 1e15 ? (long long)r : (long long)1e15) : 1;
         }
         if (k > max_steps - taken) k = max_steps - taken;
+        if (threshold > 0.0 && k > 32) k = 32;  // the test can end the loop at any step: look every 32
         if (!loop_started) {
             HJ_CUDA(cudaEventRecord(g->ev[1], g->stream));
             loop_started = true;
@@ -804,8 +813,28 @@ hj_status hj_advance_brt(hj_grid *g, double T, double cfl, int64_t max_steps, hj
         }
         stats->kernel = kern;
         stats->launches = launches;
+        stats->last_change = h.delta_last;
+        stats->converged = h.converged;
     }
     return HJ_OK;
+}
+
+hj_status hj_advance_brt(hj_grid *g, double T, double cfl, int64_t max_steps, hj_solve_stats *stats)
+{
+    g_err[0] = 0;
+    hj_status s = check_grid(g);
+    if (s != HJ_OK) return s;
+    return advance_impl(g, T, cfl, max_steps, 0.0, stats);
+}
+
+hj_status hj_solve_converged(hj_grid *g, double threshold, double T_max, double cfl, int64_t max_steps,
+                             hj_solve_stats *stats)
+{
+    g_err[0] = 0;
+    hj_status s = check_grid(g);
+    if (s != HJ_OK) return s;
+    if (!isfinite(threshold) || !(threshold > 0)) return set_err(HJ_ERR_INVALID_ARG, "threshold must be finite and > 0");
+    return advance_impl(g, T_max, cfl, max_steps, threshold, stats);
 }
 
 hj_status hj_solve_brt(hj_grid *g, double T, double cfl, hj_solve_stats *stats)

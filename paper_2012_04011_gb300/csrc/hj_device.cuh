@@ -82,42 +82,66 @@ __device__ __forceinline__ void hj_finalise(HjDevState *st, const HjGeom &g)
     st->dt_prev = dt;
     st->t = tn;
     st->n = st->n + 1;
+    if (st->track) {  // Algorithm 2's convergence test on the step just taken
+        const double eps = __longlong_as_double((long long)atomicAdd(&st->delta_bits, 0ull));
+        st->delta_last = eps;
+        st->delta_bits = 0ull;
+        if (eps < st->threshold) st->converged = 1;
+    }
     if (st->status == HJ_OK)
         hj_next_dt(st, g, a, tn);
     else
         st->done = 1;
+    if (st->converged) st->done = 1;
     st->alpha_bits[0] = 0ull;
     st->alpha_bits[1] = 0ull;
     st->blocks_done = 0u;
     __threadfence();
 }
 
-// Block-wide max of the CTA's |xdot_1|, |xdot_2| partials (bit patterns of
-// non-negative doubles), then the grid-wide atomic max and the last-CTA
-// finaliser.  Every thread of the block must call it.  `scratch` holds at
-// least 2 * 32 unsigned long long.
-__device__ __forceinline__ void hj_step_epilogue(HjDevState *st, const HjGeom &g, unsigned long long a1,
-                                                 unsigned long long a2, unsigned long long *scratch)
+// Block-wide max of the CTA's |xdot_1|, |xdot_2| partials and of its largest
+// change |V_{n+1} - V_n| (bit patterns of non-negative doubles; the change
+// is 0 outside the convergence mode), then the grid-wide atomic max and the
+// last-CTA finaliser.  Every thread of the block must call it.  `scratch`
+// holds at least 3 * 32 unsigned long long.  Thread 0 returns whether its
+// CTA was the last one.
+__device__ __forceinline__ bool hj_step_reduce(HjDevState *st, const HjGeom &g, unsigned long long a1,
+                                               unsigned long long a2, unsigned long long d,
+                                               unsigned long long *scratch)
 {
     a1 = hj_warp_max_u64(a1);
     a2 = hj_warp_max_u64(a2);
+    d = hj_warp_max_u64(d);
     int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = (blockDim.x + 31) >> 5;
     if (lane == 0) {
         scratch[warp] = a1;
         scratch[32 + warp] = a2;
+        scratch[64 + warp] = d;
     }
     __syncthreads();
+    bool last = false;
     if (threadIdx.x == 0) {
         for (int w = 1; w < nwarp; ++w) {
             a1 = a1 > scratch[w] ? a1 : scratch[w];
             a2 = a2 > scratch[32 + w] ? a2 : scratch[32 + w];
+            d = d > scratch[64 + w] ? d : scratch[64 + w];
         }
         atomicMax(&st->alpha_bits[0], a1);
         atomicMax(&st->alpha_bits[1], a2);
+        if (d) atomicMax(&st->delta_bits, d);
         __threadfence();
         unsigned int prev = atomicAdd(&st->blocks_done, 1u);
-        if (prev == gridDim.x - 1) hj_finalise(st, g);
+        last = prev == gridDim.x - 1;
+        if (last) hj_finalise(st, g);
     }
+    return last;
+}
+
+__device__ __forceinline__ void hj_step_epilogue(HjDevState *st, const HjGeom &g, unsigned long long a1,
+                                                 unsigned long long a2, unsigned long long d,
+                                                 unsigned long long *scratch)
+{
+    hj_step_reduce(st, g, a1, a2, d, scratch);
 }
 
 // Selects V after n steps' input and output buffers.

@@ -35,6 +35,11 @@ struct HjDevState {
     int nonfinite;                     // ingest saw a NaN or Inf
     int alpha_stale;                   // dynamics changed: the next prologue re-reduces alpha^max
     double dt_scaled;                  // dt the FP64 dt-scaled coefficient table holds (0: none yet)
+    int track;                         // convergence mode: the steps reduce max |V_{n+1} - V_n|
+    int converged;                     // the last step changed V by less than the threshold
+    double threshold;                  // convergence threshold of the current call
+    unsigned long long delta_bits;     // running max |V_{n+1} - V_n| of this step (FP64 bit pattern)
+    double delta_last;                 // max |V_{n+1} - V_n| of the step just taken (convergence mode)
 };
 
 // FP64 coefficients with dt folded in (per (v, theta)): w1 = dt xdot_1/dx_1,

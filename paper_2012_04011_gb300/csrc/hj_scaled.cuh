@@ -11,31 +11,13 @@
 #include "hj_device.cuh"
 
 __device__ __forceinline__ void hj_step_epilogue_scaled(HjDevState *st, const HjGeom &g, unsigned long long a1,
-                                                        unsigned long long a2, unsigned long long *scratch,
-                                                        HjScaledCoef *scaled, int32_t *qw,
-                                                        const HjCoef<double> *coef, const double *k4)
+                                                        unsigned long long a2, unsigned long long d,
+                                                        unsigned long long *scratch, HjScaledCoef *scaled,
+                                                        int32_t *qw, const HjCoef<double> *coef, const double *k4)
 {
     __shared__ int s_last;
-    a1 = hj_warp_max_u64(a1);
-    a2 = hj_warp_max_u64(a2);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = (blockDim.x + 31) >> 5;
-    if (lane == 0) {
-        scratch[warp] = a1;
-        scratch[32 + warp] = a2;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int w = 1; w < nwarp; ++w) {
-            a1 = a1 > scratch[w] ? a1 : scratch[w];
-            a2 = a2 > scratch[32 + w] ? a2 : scratch[32 + w];
-        }
-        atomicMax(&st->alpha_bits[0], a1);
-        atomicMax(&st->alpha_bits[1], a2);
-        __threadfence();
-        const unsigned int prev = atomicAdd(&st->blocks_done, 1u);
-        s_last = prev == gridDim.x - 1;
-        if (s_last) hj_finalise(st, g);
-    }
+    const bool last = hj_step_reduce(st, g, a1, a2, d, scratch);
+    if (threadIdx.x == 0) s_last = last;
     __syncthreads();
     if (s_last) {
         const volatile HjDevState *vs = st;

@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(256) hj_step_q527_kernel(const int32_t *__rest
                                                             const double *__restrict__ k4tab, HjDevState *st,
                                                             const HjGeom g, long long nint, const Divisors dv)
 {
-    __shared__ unsigned long long scratch[64];
+    __shared__ unsigned long long scratch[96];
     if (st->done) return;
     const long long n = st->n;
     const int32_t *vin;
@@ -150,7 +150,8 @@ __global__ void __launch_bounds__(256) hj_step_q527_kernel(const int32_t *__rest
     const int tot = (int)N3 * g.p4;
     const int32_t w3 = qw[2 * tot];
     const int32_t *w4tab = qw + 2 * tot + HJ_QW_TAIL;  // theta weight per speed
-    unsigned long long am1 = 0ull, am2 = 0ull;
+    const bool track = st->track;                      // convergence mode: largest change of V
+    unsigned long long am1 = 0ull, am2 = 0ull, dq = 0ull;
 
     for (unsigned long long c = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; c < ncell;
          c += (unsigned long long)gridDim.x * blockDim.x) {
@@ -182,14 +183,22 @@ __global__ void __launch_bounds__(256) hj_step_q527_kernel(const int32_t *__rest
         const int32_t w1 = qw[k * g.p4 + l], w2 = qw[tot + k * g.p4 + l];
         const long long d1 = w1 >= 0 ? dx.dp : dx.dm;
         const long long d2 = w2 >= 0 ? dy.dp : dy.dm;
-        vout[o] = hj_q527_update(vc, v0[o], d1, d2, q_upwind(dv3, g.mode3), q_upwind(dv4, g.mode4), abs(w1), abs(w2),
-                                 w3, w4tab[k]);
+        const int32_t vn = hj_q527_update(vc, v0[o], d1, d2, q_upwind(dv3, g.mode3), q_upwind(dv4, g.mode4), abs(w1),
+                                          abs(w2), w3, w4tab[k]);
+        vout[o] = vn;
+        if (track) {
+            const long long dd = (long long)vn - vc;
+            const unsigned long long ad = (unsigned long long)(dd < 0 ? -dd : dd);
+            dq = dq > ad ? dq : ad;
+        }
         const HjCoef<double> cf = coef[k * N4 + l];
         const unsigned long long b1 = hj_abits(cf.a1), b2 = hj_abits(cf.a2);
         am1 = am1 > b1 ? am1 : b1;
         am2 = am2 > b2 ? am2 : b2;
     }
-    hj_step_epilogue_scaled(st, g, am1, am2, scratch, nullptr, qw, coef, k4tab);
+    // the largest change in codes, as the FP64 value it stands for (exact)
+    hj_step_epilogue_scaled(st, g, am1, am2, hj_abits((double)dq * (1.0 / HJ_Q527_SCALE)), scratch, nullptr, qw, coef,
+                            k4tab);
 }
 
 template <typename T, bool FAST32>
@@ -199,7 +208,7 @@ __global__ void __launch_bounds__(256) hj_step_generic_kernel(const T *__restric
                                                                HjDevState *st, const HjGeom g, long long nint,
                                                                const Divisors dv)
 {
-    __shared__ unsigned long long scratch[64];
+    __shared__ unsigned long long scratch[96];
     if (st->done) return;  // uniform: written by the previous kernel on this stream
     const long long n = st->n;
     const T dt = (T)st->dt;
@@ -214,8 +223,9 @@ __global__ void __launch_bounds__(256) hj_step_generic_kernel(const T *__restric
     // FP64: dt is folded into the per-(v, theta) table; the v weight needs it
     // once per thread
     const double k3dt = g.k3 * st->dt;
-    unsigned long long am1 = 0ull, am2 = 0ull;
-    float am1f = 0.f, am2f = 0.f;
+    const bool track = st->track;  // convergence mode: largest change of V (Algorithm 2's epsilon)
+    unsigned long long am1 = 0ull, am2 = 0ull, dbits = 0ull;
+    float am1f = 0.f, am2f = 0.f, dmf = 0.f;
 
     for (unsigned long long c = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; c < ncell;
          c += (unsigned long long)gridDim.x * blockDim.x) {
@@ -271,7 +281,16 @@ __global__ void __launch_bounds__(256) hj_step_generic_kernel(const T *__restric
             r = fmaf(((const float2 *)k4tab)[k].x, u4 - vc, r);  // theta coefficient of this speed
             vn = fmaf(dt, r, vc);
         }
-        vout[o] = hj_min(v0[o], vn);  // BRT min with the target (Algorithm 2)
+        vn = hj_min(v0[o], vn);  // BRT min with the target (Algorithm 2)
+        vout[o] = vn;
+        if (track) {
+            if constexpr (sizeof(T) == 8) {
+                const unsigned long long b = hj_abits(mag(vn - vc));
+                dbits = dbits > b ? dbits : b;
+            } else {
+                dmf = fmaxf(dmf, fabsf(vn - vc));
+            }
+        }
 
         // alpha_d^max: the largest |xdot_d| among the cells this thread updated
         // (FP64: integer max of the bit patterns; FP32: float max, widened once)
@@ -287,9 +306,9 @@ __global__ void __launch_bounds__(256) hj_step_generic_kernel(const T *__restric
     if constexpr (sizeof(T) == 4) {
         am1 = hj_abits((double)am1f);
         am2 = hj_abits((double)am2f);
-        hj_step_epilogue(st, g, am1, am2, scratch);
+        hj_step_epilogue(st, g, am1, am2, hj_abits((double)dmf), scratch);
     } else {
-        hj_step_epilogue_scaled(st, g, am1, am2, scratch, scaled, nullptr, (const HjCoef<double> *)coef,
+        hj_step_epilogue_scaled(st, g, am1, am2, dbits, scratch, scaled, nullptr, (const HjCoef<double> *)coef,
                                 (const double *)k4tab);
     }
 }

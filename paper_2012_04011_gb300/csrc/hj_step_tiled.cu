@@ -109,8 +109,8 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
     uint64_t *full = (uint64_t *)(smem_raw + (size_t)P.stages * P.stage_bytes);
     uint64_t *empty = full + MAX_STAGES;
     unsigned long long *scratch = (unsigned long long *)(empty + MAX_STAGES);
-    volatile int *abort_flag = (volatile int *)(scratch + 64);
-    unsigned long long *deadline_p = (unsigned long long *)(scratch + 65);
+    volatile int *abort_flag = (volatile int *)(scratch + 96);
+    unsigned long long *deadline_p = (unsigned long long *)(scratch + 97);
 
     const long long n = st->n;
     const float dt = (float)st->dt;
@@ -133,6 +133,10 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
 
     float am1 = 0.f, am2 = 0.f;  // this thread's max |xdot_1|, |xdot_2| (non-negative)
     unsigned long long ab1 = 0ull, ab2 = 0ull;  // the same as FP64 bit patterns (FIXED)
+    // convergence mode (Algorithm 2's epsilon): this thread's largest |V_{n+1} - V_n|
+    const bool track = st->track;
+    float dmf = 0.f;
+    unsigned int dmq = 0u;  // in codes (FIXED; a change of one step is below 2^32 codes)
 
     if (tid >= P.nconsumer) {
         // ------------------------------------------------------------ producer
@@ -443,6 +447,18 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
                     }
                     }
                     *(float4 *)(vout + (uint32_t)x * s1 + rbase) = out;
+                    if (track) {
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            if constexpr (FIXED) {
+                                const long long dd = (long long)f4geti(out, e) - f4geti(cur, e);
+                                const unsigned long long ad = (unsigned long long)(dd < 0 ? -dd : dd);
+                                dmq = max(dmq, (unsigned int)min(ad, 0xffffffffull));
+                            } else {
+                                dmf = fmaxf(dmf, fabsf(f4get(out, e) - f4get(cur, e)));
+                            }
+                        }
+                    }
                 }
                 if (s_prev >= 0) HJ_RELEASE_OLDEST();  // plane x-1
                 s_prev = s_x;
@@ -481,9 +497,10 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
         }
     }
     if constexpr (FIXED)
-        hj_step_epilogue_scaled(st, g, ab1, ab2, scratch, nullptr, qw, coefd, (const double *)k4tab);
+        hj_step_epilogue_scaled(st, g, ab1, ab2, hj_abits((double)dmq * (1.0 / HJ_Q527_SCALE)), scratch, nullptr, qw,
+                                coefd, (const double *)k4tab);
     else
-        hj_step_epilogue(st, g, hj_abits((double)am1), hj_abits((double)am2), scratch);
+        hj_step_epilogue(st, g, hj_abits((double)am1), hj_abits((double)am2), hj_abits((double)dmf), scratch);
 }
 
 typedef void (*KernelFn)(const CUtensorMap, const CUtensorMap, const CUtensorMap, const CUtensorMap, float *,
@@ -587,7 +604,7 @@ int best_chunk(const hj_grid *g, int ncol, int slots)
 
 size_t tiled_smem_bytes(const TiledParams &P)
 {
-    return (size_t)P.stages * P.stage_bytes + 2 * MAX_STAGES * sizeof(uint64_t) + 64 * sizeof(unsigned long long) +
+    return (size_t)P.stages * P.stage_bytes + 2 * MAX_STAGES * sizeof(uint64_t) + 96 * sizeof(unsigned long long) +
            32;
 }
 

@@ -43,6 +43,8 @@ class hj_solve_stats(ctypes.Structure):
         ("loop_ms", ctypes.c_double),
         ("kernel", ctypes.c_int32),
         ("launches", ctypes.c_int32),
+        ("last_change", ctypes.c_double),
+        ("converged", ctypes.c_int32),
     ]
 
     def as_dict(self) -> dict:
@@ -152,6 +154,8 @@ _SIGS = {
     "hj_solve_brt": (ctypes.c_int, [_VP, ctypes.c_double, ctypes.c_double, ctypes.POINTER(hj_solve_stats)]),
     "hj_advance_brt": (ctypes.c_int, [_VP, ctypes.c_double, ctypes.c_double, ctypes.c_int64,
                                       ctypes.POINTER(hj_solve_stats)]),
+    "hj_solve_converged": (ctypes.c_int, [_VP, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int64,
+                                          ctypes.POINTER(hj_solve_stats)]),
     "hj_read_value": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.c_size_t]),
     "hj_read_value_device": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_size_t]),
     "hj_set_kernel": (ctypes.c_int, [_VP, ctypes.c_int]),
@@ -307,6 +311,13 @@ def hj_advance_brt(g, T: float, cfl: float, max_steps: int) -> hj_solve_stats:
     return st
 
 
+def hj_solve_converged(g, threshold: float, T_max: float, cfl: float = 0.8,
+                       max_steps: int = (1 << 63) - 1) -> hj_solve_stats:
+    st = hj_solve_stats()
+    _check(lib.hj_solve_converged(g, float(threshold), float(T_max), float(cfl), int(max_steps), ctypes.byref(st)))
+    return st
+
+
 def hj_read_value(g, out: np.ndarray | None = None, shape=None) -> np.ndarray:
     info = hj_get_info(g)
     n = tuple(info.n)
@@ -395,6 +406,9 @@ class Grid:
 
     def solve_brt(self, T, cfl=0.8) -> hj_solve_stats:
         return hj_solve_brt(self.handle, T, cfl)
+
+    def solve_converged(self, threshold, T_max, cfl=0.8, max_steps=(1 << 63) - 1) -> hj_solve_stats:
+        return hj_solve_converged(self.handle, threshold, T_max, cfl, max_steps)
 
     def advance_brt(self, T, cfl, max_steps) -> hj_solve_stats:
         return hj_advance_brt(self.handle, T, cfl, max_steps)

@@ -194,3 +194,18 @@ def test_steer_q527_within_bound_of_fp64(oracle_mod):
     ref = oracle.step_cells(P, oracle.from_q527(Q), oracle.from_q527(oracle.to_q527(V0)), d1[0], np.arange(Q.size))
     e1 = np.abs(oracle.from_q527(Q1).ravel() - ref) / ULP
     assert e1.max() <= _per_step_bound_codes(np.abs(V0).max()) + 1e-6
+
+
+def test_converged_q527_matches_fixed_steps(oracle_mod):
+    """The fixed-point convergence loop takes the fixed-point steps; its eps is
+    the largest code change of the last step times 2^-27."""
+    w = scenes.custom_workload((13, 13, 6, 12), n_circles=3, seed=22)
+    P = car_problem(w.grid)
+    Q0 = oracle.to_q527(scenes.initial_value(w.grid, w.scene))
+    Q, t, dts, eps, conv = oracle.advance_converged_q527(P, Q0, Q0, 0.0, 3e-3, 30.0)
+    assert conv and eps < 3e-3
+    n = len(dts)
+    Qa, t1, _ = oracle.advance_q527(P, Q0, Q0, 0.0, 30.0, max_steps=n - 1)
+    Qb, _, _ = oracle.advance_q527(P, Q0, Qa, t1, 30.0, max_steps=1)
+    assert np.array_equal(Qb, Q)
+    assert eps == float(np.abs(Qb.astype(np.int64) - Qa).max()) * ULP
