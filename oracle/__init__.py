@@ -102,6 +102,8 @@ def _load():
         lib.hjo_advance_converged_q527.restype = ctypes.c_int64
         lib.hjo_step_cells_q527.argtypes = [P, i32p, i32p, ctypes.c_double, i64p, ctypes.c_int64, i32p]
         lib.hjo_step_cells_q527.restype = ctypes.c_int
+        lib.hjo_query.argtypes = [P, dp, dp, ctypes.c_int64, dp, dp, dp]
+        lib.hjo_query.restype = ctypes.c_int
         lib.hjo_max_threads.argtypes = []
         lib.hjo_max_threads.restype = ctypes.c_int
         _lib = lib
@@ -234,6 +236,20 @@ def advance_converged(P: Problem, V0, V, t: float, threshold: float, T: float, c
     if steps < 0:
         raise MemoryError("oracle allocation failed")
     return Vw, float(tt.value), dts[:steps].copy(), float(eps.value), bool(conv.value)
+
+
+def query(P: Problem, V, states):
+    """V, grad V (4 per state) and u_opt (2 per state: a and the heading
+    control) at states (m x 4: x, y, v, theta) by multilinear interpolation
+    (Eq. uopt_max; the readings are listed in hj_oracle.c)."""
+    V = _as_grid(P, V)
+    st = np.ascontiguousarray(np.asarray(states, dtype=np.float64).reshape(-1, 4))
+    m = st.shape[0]
+    val = np.empty(m)
+    grad = np.empty((m, 4))
+    ctl = np.empty((m, 2))
+    _load().hjo_query(ctypes.byref(P._s), _dptr(V), _dptr(st), m, _dptr(val), _dptr(grad), _dptr(ctl))
+    return val, grad, ctl
 
 
 def solve(P: Problem, V0, T: float, cfl: float = 0.8, nthreads: int = 1, max_steps: int = 1 << 40):

@@ -663,3 +663,111 @@ int64_t hjo_advance_converged_q527(const hjo_problem *P, const int32_t *Q0, int3
     free(Qprev);
     return s;
 }
+
+/* ---- query: V, grad V and u_opt at arbitrary states -------------------
+ *
+ * Sec. IV-A: near the BRT boundary (Eq. closetoboundary, V < 0.15) the car
+ * applies u_opt = argmax_u grad V(z)^T f(z, u) (Eq. uopt_max) at its
+ * current state z.  Readings (the paper does not say how V and grad V are
+ * evaluated between grid points):
+ *   - V(z): multilinear interpolation of the grid values over the cell that
+ *     contains z (cell index floor((z_d - lo_d) / dx_d), the last cell for
+ *     z_d at the upper end); theta wraps; states beyond a non-periodic axis
+ *     are clamped onto it.
+ *   - grad V(z): the gradient of that interpolant, i.e. on axis d the
+ *     interpolation over the other three axes of (V(i_d + 1) - V(i_d)) / dx_d.
+ *   - u_opt: the bang-bang argmax of Eq. uopt_max; ties (p_d = 0) take the
+ *     upper bound, as in the step. */
+static void query_cell(const hjo_problem *P, int d, double z, int *i0, double *f)
+{
+    int N = P->n[d];
+    double h = hjo_spacing(P, d);
+    double lo = P->lo[d];
+    if (is_periodic(P, d)) {
+        double span = h * (double)N;
+        double u = fmod(z - lo, span);
+        if (u < 0.0)
+            u += span;
+        double r = u / h;
+        int i = (int)floor(r);
+        if (i >= N)
+            i = N - 1;
+        *i0 = i;
+        *f = r - (double)i;
+        return;
+    }
+    double r = (z - lo) / h;
+    if (r <= 0.0) {
+        *i0 = 0;
+        *f = 0.0;
+        return;
+    }
+    if (r >= (double)(N - 1)) {
+        *i0 = N - 2;
+        *f = 1.0;
+        return;
+    }
+    int i = (int)floor(r);
+    if (i > N - 2)
+        i = N - 2;
+    *i0 = i;
+    *f = r - (double)i;
+}
+
+int hjo_query(const hjo_problem *P, const double *V, const double *states, int64_t m, double *value,
+              double *grad, double *control)
+{
+    int64_t stride[4];
+    stride[3] = 1;
+    stride[2] = P->n[3];
+    stride[1] = (int64_t)P->n[2] * P->n[3];
+    stride[0] = (int64_t)P->n[1] * P->n[2] * P->n[3];
+    for (int64_t q = 0; q < m; ++q) {
+        int i0[4], i1[4];
+        double f[4];
+        for (int d = 0; d < 4; ++d) {
+            query_cell(P, d, states[4 * q + d], &i0[d], &f[d]);
+            i1[d] = i0[d] + 1;
+            if (i1[d] >= P->n[d])
+                i1[d] = is_periodic(P, d) ? 0 : P->n[d] - 1;
+        }
+        /* the 16 corners: bit d of c picks i1 on axis d */
+        double val = 0.0, g[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int c = 0; c < 16; ++c) {
+            int64_t off = 0;
+            double w = 1.0;
+            for (int d = 0; d < 4; ++d) {
+                int hi = (c >> d) & 1;
+                off += (int64_t)(hi ? i1[d] : i0[d]) * stride[d];
+                w *= hi ? f[d] : 1.0 - f[d];
+            }
+            val += w * V[off];
+            for (int d = 0; d < 4; ++d) {
+                /* d/dz_d of the weight: the other factors times +-1/dx_d */
+                double wd = ((c >> d) & 1) ? 1.0 : -1.0;
+                for (int e = 0; e < 4; ++e)
+                    if (e != d)
+                        wd *= ((c >> e) & 1) ? f[e] : 1.0 - f[e];
+                g[d] += wd * V[off] / hjo_spacing(P, d);
+            }
+        }
+        value[q] = val;
+        if (grad)
+            for (int d = 0; d < 4; ++d)
+                grad[4 * q + d] = g[d];
+        if (control) {
+            double v = states[4 * q + 2];
+            if (P->dyn == HJO_DYN_CAR4D) {
+                control[2 * q] = g[2] >= 0.0 ? P->p[0] : -P->p[0];
+                control[2 * q + 1] = g[3] >= 0.0 ? P->p[1] : -P->p[1];
+            } else if (P->dyn == HJO_DYN_CAR4D_STEER) {
+                control[2 * q] = g[2] >= 0.0 ? P->p[0] : -P->p[0];
+                control[2 * q + 1] = g[3] * v >= 0.0 ? P->p[1] : -P->p[1];
+            } else {
+                control[2 * q] = 0.0;
+                control[2 * q + 1] = 0.0;
+            }
+        }
+    }
+    return 0;
+}

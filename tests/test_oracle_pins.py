@@ -478,3 +478,88 @@ def test_converged_equals_fixed_steps_and_eps_is_the_max_change(oracle_mod):
     # and the step before did not pass the test
     Vm, _, _ = oracle.advance(P, V0, V0, 0.0, 30.0, max_steps=n - 2, nthreads=4)
     assert float(np.abs(Vn_1 - Vm).max()) >= 2e-3
+
+
+# ---------------------------------------------------------------- query (Eq. uopt_max, Eq. closetoboundary)
+
+def _random_states(P, m, rng):
+    lo, hi = np.array(P.lo), np.array(P.hi)
+    return lo + (hi - lo) * rng.random((m, 4))
+
+
+def test_query_reproduces_grid_values(oracle_mod):
+    w = scenes.custom_workload((7, 6, 5, 8), n_circles=2, seed=2)
+    P = car_problem(w.grid)
+    rng = np.random.default_rng(0)
+    V = rng.standard_normal(w.grid.n)
+    idx = np.array([(i, j, k, l) for i in (0, 3, 6) for j in (0, 5) for k in (0, 2, 4) for l in (0, 7)])
+    states = np.stack([P.coords(d)[idx[:, d]] for d in range(4)], axis=1)
+    val, _, _ = oracle.query(P, V, states)
+    assert np.array_equal(val, V[tuple(idx.T)])
+
+
+def test_query_matches_scipy_linear_interpolation(oracle_mod):
+    """Values: scipy's RegularGridInterpolator (linear) on the same grid, the
+    theta axis closed by repeating its first row at theta = +pi.  Gradients:
+    central differences of that interpolant inside the cell."""
+    interp_mod = pytest.importorskip("scipy.interpolate")
+    w = scenes.custom_workload((9, 8, 6, 10), n_circles=2, seed=3)
+    P = car_problem(w.grid)
+    rng = np.random.default_rng(1)
+    V = rng.standard_normal(w.grid.n)
+    axes = [P.coords(d) for d in range(3)] + [np.append(P.coords(3), math.pi)]
+    Vc = np.concatenate([V, V[..., :1]], axis=3)
+    f = interp_mod.RegularGridInterpolator(axes, Vc, method="linear")
+    states = _random_states(P, 300, rng)
+    val, grad, _ = oracle.query(P, V, states)
+    assert np.abs(val - f(states)).max() <= 1e-12
+    h = [P.spacing(d) for d in range(4)]
+    for d in range(4):
+        # a step well inside the cell: the interpolant is linear along d there
+        frac = ((states[:, d] - P.lo[d]) / h[d]) % 1.0
+        ok = (frac > 0.05) & (frac < 0.95)
+        e = np.zeros(4)
+        e[d] = 0.01 * h[d]
+        fd = (f(states[ok] + e) - f(states[ok] - e)) / (2 * e[d])
+        assert np.abs(grad[ok, d] - fd).max() <= 1e-8, d
+
+
+def test_query_linear_field_gradient_and_controls(oracle_mod):
+    """On V = a x + b y + c v + d th (theta not periodic here) the interpolant
+    is exact and its gradient is (a, b, c, d); the car's u_opt takes
+    a = a_max sign(c), w = w_max sign(d) (the control maximises grad V . f),
+    and the steering car's delta takes the sign of d v."""
+    n = (6, 5, 7, 9)
+    lo, hi = (-5.0, -4.0, 0.0, -1.0), (5.0, 4.0, 4.0, 1.0)
+    coef = (0.3, -0.7, 0.25, -0.4)
+    rng = np.random.default_rng(4)
+    for dyn, params in ((oracle.DYN_CAR4D, (1.5, 1.0)), (oracle.DYN_CAR4D_STEER, (1.5, math.pi / 18, 0.3))):
+        P = oracle.Problem(n, lo, hi, 0, dyn, params)
+        X = np.meshgrid(*[P.coords(d) for d in range(4)], indexing="ij")
+        V = sum(c * x for c, x in zip(coef, X))
+        states = _random_states(P, 200, rng)
+        val, grad, ctl = oracle.query(P, V, states)
+        assert np.abs(val - states @ np.array(coef)).max() <= 1e-12
+        assert np.abs(grad - np.array(coef)).max() <= 1e-12
+        assert np.all(ctl[:, 0] == 1.5)
+        if dyn == oracle.DYN_CAR4D:
+            assert np.all(ctl[:, 1] == -1.0)
+        else:
+            assert np.all(ctl[:, 1] == -math.pi / 18)  # d < 0, v >= 0
+
+
+def test_query_wraps_theta_and_clamps_other_axes(oracle_mod):
+    w = scenes.custom_workload((7, 6, 5, 8), n_circles=2, seed=5)
+    P = car_problem(w.grid)
+    V = np.random.default_rng(6).standard_normal(w.grid.n)
+    s = _random_states(P, 50, np.random.default_rng(7))
+    v0, g0, _ = oracle.query(P, V, s)
+    s2 = s.copy()
+    s2[:, 3] += 2 * math.pi
+    v2, g2, _ = oracle.query(P, V, s2)
+    assert np.abs(v2 - v0).max() <= 1e-12 and np.abs(g2 - g0).max() <= 1e-9
+    s3 = s.copy()
+    s3[:, 0] = P.hi[0] + 3.0
+    s4 = s.copy()
+    s4[:, 0] = P.hi[0]
+    assert np.array_equal(oracle.query(P, V, s3)[0], oracle.query(P, V, s4)[0])
