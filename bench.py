@@ -328,6 +328,40 @@ def run_ours(args):
             "tile": tuned,
         }
 
+    # queries: V, grad V and u_opt at 2^20 random states of the solved grid
+    # (the controller of Sec. IV-A), device arrays, one kernel per call
+    query = None
+    if not args.no_query:
+        g = hj.Grid(w.grid.n, w.grid.lo, w.grid.hi, w.grid.periodic, hj.HJ_FP32, stream.cuda_stream)
+        g.set_dynamics(hj.HJ_DYN_CAR4D, (w.a_max, w.w_max))
+        solve_once(g, out32)
+        mq = 1 << 20
+        rng = np.random.default_rng(scenes.SEED_BASE + 7)
+        lo_, hi_ = np.array(w.grid.lo), np.array(w.grid.hi)
+        sq = torch.from_numpy(lo_ + (hi_ - lo_) * rng.random((mq, 4))).to("cuda")
+        vq = torch.empty(mq, dtype=torch.float64, device="cuda")
+        gq = torch.empty((mq, 4), dtype=torch.float64, device="cuda")
+        cq = torch.empty((mq, 2), dtype=torch.float64, device="cuda")
+        for _ in range(3):
+            hj.hj_query_device(g.handle, sq, vq, gq, cq)
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        kq = 10
+        e0.record(stream)
+        for _ in range(kq):
+            hj.hj_query_device(g.handle, sq, vq, gq, cq)
+        e1.record(stream)
+        barrier()
+        qms = max_over_ranks(e0.elapsed_time(e1)) / kq
+        g.close()
+        qbytes = 32 + 8 + 32 + 16 + 16 * 4  # state in, value, gradient, control out, 16 grid values
+        query = {"workload": f"{mq} random states on the solved {WORKLOAD} FP32 grid: value, gradient, u_opt",
+                 "value": job_throughput(world, mq, qms * 1e-3), "unit": "queries/s", "ms_per_call": qms,
+                 "roofline": {"bound": "hbm", "achieved": qbytes * mq / (qms * 1e-3) / 1e9,
+                              "peak": measured_peaks()[0], "unit": "GB/s",
+                              "frac": qbytes * mq / (qms * 1e-3) / 1e9 / measured_peaks()[0],
+                              "bytes_per_query": qbytes}}
+
     # batched solves: the 64-instance workload (uneven grids, own obstacles,
     # T = 1.5 s), V0 already on the device, one persistent kernel per batch step
     batch = None
@@ -452,6 +486,7 @@ def run_ours(args):
         "gpu_launches": r32["launches"],
         "e2e": e2e,
         "batch64": batch,
+        "query": query,
         "serving": serving,
     }
     if "f64" in results:
@@ -537,6 +572,7 @@ def main():
     ap.add_argument("--no-bcast", action="store_true")
     ap.add_argument("--steer-steps", type=int, default=3)
     ap.add_argument("--no-steer", action="store_true")
+    ap.add_argument("--no-query", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")

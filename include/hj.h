@@ -232,6 +232,28 @@ HJ_API hj_status hj_read_value(const hj_grid *g, double *out, size_t count);
 HJ_API hj_status hj_read_value_device(const hj_grid *g, void *out_device, hj_precision dtype,
                                size_t count);
 
+/* V, grad V and the optimal control at m arbitrary states, from the grid's
+ * current V: the controller of Sec. IV-A, which applies
+ * u_opt = argmax_u grad V^T f (Eq. uopt_max) when V < 0.15 at the car's
+ * state (Eq. closetoboundary).  The paper does not say how V is evaluated
+ * between grid points; here:
+ *   - value[i]: multilinear interpolation of the grid values over the cell
+ *     that contains states[i] (cell floor((z_d - lo_d)/dx_d); theta wraps;
+ *     a coordinate beyond a non-periodic axis is clamped onto it);
+ *   - grad[4i..4i+3] (may be NULL): the gradient of that interpolant;
+ *   - control[2i..2i+1] (may be NULL): u_opt with ties to the upper bound:
+ *     HJ_DYN_CAR4D (a, w), HJ_DYN_CAR4D_STEER (a, delta: the sign of
+ *     dV/dth * v), HJ_DYN_CONST (0, 0).
+ * states: m x 4 doubles (x, y, v, theta), row-major.  FP64 arithmetic; the
+ * grid values are read in the grid's precision.  hj_query takes HOST arrays
+ * (staged through the grid's free ping-pong buffer, nothing allocated);
+ * hj_query_device takes DEVICE arrays on the grid's device.  HJ_ERR_STATE
+ * without V0 (or without dynamics when control is requested). */
+HJ_API hj_status hj_query(const hj_grid *g, const double *states, int64_t m, double *value, double *grad,
+                          double *control);
+HJ_API hj_status hj_query_device(const hj_grid *g, const double *states, int64_t m, double *value, double *grad,
+                                 double *control);
+
 /* Choose the step kernel.  HJ_KERNEL_TILED on a grid that it does not
  * support returns HJ_ERR_UNSUPPORTED and leaves the choice unchanged. */
 HJ_API hj_status hj_set_kernel(hj_grid *g, hj_kernel kernel);

@@ -890,6 +890,67 @@ hj_status hj_read_value(const hj_grid *gc, double *out, size_t count)
     return HJ_OK;
 }
 
+hj_status hj_query_device(const hj_grid *gc, const double *states, int64_t m, double *value, double *grad,
+                          double *control)
+{
+    g_err[0] = 0;
+    hj_grid *g = (hj_grid *)gc;
+    hj_status s = check_grid(g);
+    if (s != HJ_OK) return s;
+    if (m < 0) return set_err(HJ_ERR_INVALID_ARG, "m must be >= 0");
+    if (m > 0 && (!states || !value)) return set_err(HJ_ERR_INVALID_ARG, "states and value must not be NULL");
+    if (!g->has_value) return set_err(HJ_ERR_STATE, "no initial value (hj_set_initial_value)");
+    if (control && !g->has_dyn) return set_err(HJ_ERR_STATE, "the control needs the dynamics (hj_set_dynamics)");
+    if ((s = activate(g)) != HJ_OK) return s;
+    if ((s = pull_state(g)) != HJ_OK) return s;
+    HJ_CUDA(hj_launch_query(g, hj_value_ptr(g, g->hstate->n), states, m, value, grad, control));
+    HJ_CUDA(cudaStreamSynchronize(g->stream));
+    return HJ_OK;
+}
+
+hj_status hj_query(const hj_grid *gc, const double *states, int64_t m, double *value, double *grad, double *control)
+{
+    g_err[0] = 0;
+    hj_grid *g = (hj_grid *)gc;
+    hj_status s = check_grid(g);
+    if (s != HJ_OK) return s;
+    if (m < 0) return set_err(HJ_ERR_INVALID_ARG, "m must be >= 0");
+    if (m > 0 && (!states || !value)) return set_err(HJ_ERR_INVALID_ARG, "states and value must not be NULL");
+    if (!g->has_value) return set_err(HJ_ERR_STATE, "no initial value (hj_set_initial_value)");
+    if (control && !g->has_dyn) return set_err(HJ_ERR_STATE, "the control needs the dynamics (hj_set_dynamics)");
+    if ((s = activate(g)) != HJ_OK) return s;
+    if ((s = pull_state(g)) != HJ_OK) return s;
+    const long long n = g->hstate->n;
+    // stage states and results in the buffer the next step writes (free now)
+    char *free_buf;
+    size_t free_bytes;
+    if (n == 0) {
+        free_buf = (char *)g->buf;
+        free_bytes = 2 * (size_t)g->nint * g->esize;
+    } else {
+        free_buf = (char *)g->buf + (size_t)(n & 1) * g->nint * g->esize;
+        free_bytes = (size_t)g->nint * g->esize;
+    }
+    const long long per = (long long)free_bytes / (11 * (long long)sizeof(double));
+    if (per < 1) return set_err(HJ_ERR_STATE, "no room to stage the query");
+    double *d_states = (double *)free_buf, *d_value = d_states + 4 * per, *d_grad = d_value + per,
+           *d_ctl = d_grad + 4 * per;
+    const void *V = hj_value_ptr(g, n);
+    for (long long q0 = 0; q0 < m; q0 += per) {
+        const long long k = m - q0 < per ? m - q0 : per;
+        HJ_CUDA(cudaMemcpyAsync(d_states, states + 4 * q0, sizeof(double) * 4 * k, cudaMemcpyHostToDevice, g->stream));
+        HJ_CUDA(hj_launch_query(g, V, d_states, k, d_value, grad ? d_grad : nullptr, control ? d_ctl : nullptr));
+        HJ_CUDA(cudaMemcpyAsync(value + q0, d_value, sizeof(double) * k, cudaMemcpyDeviceToHost, g->stream));
+        if (grad)
+            HJ_CUDA(cudaMemcpyAsync(grad + 4 * q0, d_grad, sizeof(double) * 4 * k, cudaMemcpyDeviceToHost, g->stream));
+        if (control)
+            HJ_CUDA(cudaMemcpyAsync(control + 2 * q0, d_ctl, sizeof(double) * 2 * k, cudaMemcpyDeviceToHost,
+                                    g->stream));
+        HJ_CUDA(cudaStreamSynchronize(g->stream));  // the next chunk reuses the staging area
+    }
+    return HJ_OK;
+}
+
 hj_status hj_read_value_device(const hj_grid *gc, void *out_device, hj_precision dtype, size_t count)
 {
     g_err[0] = 0;

@@ -126,6 +126,12 @@ int hj_tiled_threads(const hj_grid *g, int ty, int tv);
 // are set to exactly 0 so that every FP32 kernel uses the same upwind side.
 static inline double hj_flush_trig(double x) { return (x < 1e-12 && x > -1e-12) ? 0.0 : x; }
 
+// Query kernel (hj_query.cu): value, gradient and u_opt of V (the grid's
+// current value array, internal layout) at m states; grad and control may be
+// NULL.  Device pointers; runs on the grid's stream.
+cudaError_t hj_launch_query(const hj_grid *g, const void *V, const double *states, long long m, double *value,
+                            double *grad, double *control);
+
 // Sets the message hj_last_error() returns on this host thread.
 void hj_internal_set_error(const char *msg);
 

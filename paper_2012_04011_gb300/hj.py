@@ -156,6 +156,8 @@ _SIGS = {
                                       ctypes.POINTER(hj_solve_stats)]),
     "hj_solve_converged": (ctypes.c_int, [_VP, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int64,
                                           ctypes.POINTER(hj_solve_stats)]),
+    "hj_query": (ctypes.c_int, [_VP, _VP, ctypes.c_int64, _VP, _VP, _VP]),
+    "hj_query_device": (ctypes.c_int, [_VP, _VP, ctypes.c_int64, _VP, _VP, _VP]),
     "hj_read_value": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.c_size_t]),
     "hj_read_value_device": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_size_t]),
     "hj_set_kernel": (ctypes.c_int, [_VP, ctypes.c_int]),
@@ -316,6 +318,26 @@ def hj_solve_converged(g, threshold: float, T_max: float, cfl: float = 0.8,
     st = hj_solve_stats()
     _check(lib.hj_solve_converged(g, float(threshold), float(T_max), float(cfl), int(max_steps), ctypes.byref(st)))
     return st
+
+
+def hj_query(g, states, want_grad: bool = True, want_control: bool = True):
+    """(value, grad or None, control or None) at host states (m x 4)."""
+    st = np.ascontiguousarray(np.asarray(states, dtype=np.float64).reshape(-1, 4))
+    m = st.shape[0]
+    val = np.empty(m)
+    grad = np.empty((m, 4)) if want_grad else None
+    ctl = np.empty((m, 2)) if want_control else None
+    p = lambda a: None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+    _check(lib.hj_query(g, p(st), m, p(val), p(grad), p(ctl)))
+    return val, grad, ctl
+
+
+def hj_query_device(g, states_device, value_device, grad_device=None, control_device=None):
+    """Device arrays (float64 tensors or pointers): states m x 4, value m,
+    grad m x 4, control m x 2."""
+    m = int(states_device.numel()) // 4 if hasattr(states_device, "numel") else int(value_device.numel())
+    q = lambda a: None if a is None else ctypes.c_void_p(_dptr(a))
+    _check(lib.hj_query_device(g, q(states_device), m, q(value_device), q(grad_device), q(control_device)))
 
 
 def hj_read_value(g, out: np.ndarray | None = None, shape=None) -> np.ndarray:
