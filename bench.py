@@ -37,7 +37,8 @@ WORKLOAD = "car4d_128x128x64x96"
 STEER = (1.5, math.pi / 18, 0.3)  # Sec. IV-A: a in [-1.5, 1.5], delta in [-pi/18, pi/18], L = 0.3 m
 BYTES_PER_UPDATE = {"f32": 12, "f64": 24, "q527": 12, "f32_bcast": 8}
 PROFILE = os.path.join(ROOT, "profiles", "hj_step_tiled_car4d_128x128x64x96.md")
-KERNEL_SOURCES = ["hj_step_tiled.cu", "hj_device.cuh", "hj_tma.cuh", "hj_scaled.cuh", "hj_internal.h"]
+KERNEL_SOURCES = ["hj_tiled_kernel.cuh", "hj_tiled_f32.cu", "hj_device.cuh", "hj_tma.cuh", "hj_scaled.cuh",
+                  "hj_internal.h"]
 # FP64 path: bound by the FP64 unit.  Algorithmic FP64 flops per cell-update:
 # 1 DMUL + 5 DFMA = 11; nominal GB300 FP64 rate 1.25 TFLOP/s (no measured FP64
 # figure in MEASURED_PEAKS.json).

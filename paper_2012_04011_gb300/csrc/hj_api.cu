@@ -747,7 +747,20 @@ hj_status hj_set_initial_value_device(hj_grid *g, const void *v0_device, hj_prec
 
 // The time loop of hj_advance_brt and hj_solve_converged (threshold > 0:
 // Algorithm 2's convergence test ends the loop as well).
+static hj_status advance_loop(hj_grid *g, double T, double cfl, int64_t max_steps, double threshold,
+                              hj_solve_stats *stats);
+
 static hj_status advance_impl(hj_grid *g, double T, double cfl, int64_t max_steps, double threshold,
+                              hj_solve_stats *stats)
+{
+    // the step kernels that also reduce the change run only in this call
+    g->track = threshold > 0.0;
+    const hj_status s = advance_loop(g, T, cfl, max_steps, threshold, stats);
+    g->track = false;
+    return s;
+}
+
+static hj_status advance_loop(hj_grid *g, double T, double cfl, int64_t max_steps, double threshold,
                               hj_solve_stats *stats)
 {
     hj_status s = HJ_OK;

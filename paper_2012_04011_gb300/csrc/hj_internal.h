@@ -90,6 +90,7 @@ struct hj_grid {
                            // (k4, -(k3 + k4)))
     void *v0xy;            // V0 as an N1 x N2 field (element type of the grid), when V0 depends on x, y only
     bool v0_bcast;         // V0 was set from the (x, y) field: the tiled kernel reads v0xy
+    bool track;            // a convergence-mode call is running: launch the kernels that reduce the change
     float *tab_tiled;      // tiled-kernel tables: v_k [n3], cos/dx1 [p4], sin/dx2 [p4], quad signs [p4]
     HjDevState *dstate;
     HjDevState *hstate;    // pinned host mirror

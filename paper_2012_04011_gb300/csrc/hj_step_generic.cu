@@ -131,7 +131,7 @@ __device__ __forceinline__ long long q_upwind(const QDiff &d, int mode)
 // supports): V_c + round_half_up(sum_d W_d (V_up,d - V_c) / 2^30), BRT min,
 // saturation (hj_q527_update).  alpha^max comes from the FP64 table, so the dt
 // sequence is the FP64 one.
-template <bool FAST32>
+template <bool FAST32, bool TRACK>
 __global__ void __launch_bounds__(256) hj_step_q527_kernel(const int32_t *__restrict__ v0, int32_t *__restrict__ buf,
                                                             const HjCoef<double> *__restrict__ coef, int32_t *qw,
                                                             const double *__restrict__ k4tab, HjDevState *st,
@@ -150,7 +150,6 @@ __global__ void __launch_bounds__(256) hj_step_q527_kernel(const int32_t *__rest
     const int tot = (int)N3 * g.p4;
     const int32_t w3 = qw[2 * tot];
     const int32_t *w4tab = qw + 2 * tot + HJ_QW_TAIL;  // theta weight per speed
-    const bool track = st->track;                      // convergence mode: largest change of V
     unsigned long long am1 = 0ull, am2 = 0ull, dq = 0ull;
 
     for (unsigned long long c = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; c < ncell;
@@ -186,7 +185,7 @@ __global__ void __launch_bounds__(256) hj_step_q527_kernel(const int32_t *__rest
         const int32_t vn = hj_q527_update(vc, v0[o], d1, d2, q_upwind(dv3, g.mode3), q_upwind(dv4, g.mode4), abs(w1),
                                           abs(w2), w3, w4tab[k]);
         vout[o] = vn;
-        if (track) {
+        if constexpr (TRACK) {  // convergence mode: largest change of V
             const long long dd = (long long)vn - vc;
             const unsigned long long ad = (unsigned long long)(dd < 0 ? -dd : dd);
             dq = dq > ad ? dq : ad;
@@ -201,7 +200,7 @@ __global__ void __launch_bounds__(256) hj_step_q527_kernel(const int32_t *__rest
                             k4tab);
 }
 
-template <typename T, bool FAST32>
+template <typename T, bool FAST32, bool TRACK>
 __global__ void __launch_bounds__(256) hj_step_generic_kernel(const T *__restrict__ v0, T *__restrict__ buf,
                                                                const HjCoef<T> *__restrict__ coef,
                                                                HjScaledCoef *scaled, const void *__restrict__ k4tab,
@@ -223,7 +222,6 @@ __global__ void __launch_bounds__(256) hj_step_generic_kernel(const T *__restric
     // FP64: dt is folded into the per-(v, theta) table; the v weight needs it
     // once per thread
     const double k3dt = g.k3 * st->dt;
-    const bool track = st->track;  // convergence mode: largest change of V (Algorithm 2's epsilon)
     unsigned long long am1 = 0ull, am2 = 0ull, dbits = 0ull;
     float am1f = 0.f, am2f = 0.f, dmf = 0.f;
 
@@ -283,7 +281,7 @@ __global__ void __launch_bounds__(256) hj_step_generic_kernel(const T *__restric
         }
         vn = hj_min(v0[o], vn);  // BRT min with the target (Algorithm 2)
         vout[o] = vn;
-        if (track) {
+        if constexpr (TRACK) {  // convergence mode: largest change of V (Algorithm 2's epsilon)
             if constexpr (sizeof(T) == 8) {
                 const unsigned long long b = hj_abits(mag(vn - vc));
                 dbits = dbits > b ? dbits : b;
@@ -329,26 +327,38 @@ cudaError_t hj_launch_step_generic(hj_grid *g)
     dv.n3 = make_fastdiv((uint32_t)g->n[2]);
     dv.n2 = make_fastdiv((uint32_t)g->n[1]);
     const bool fast = g->ncell < (1LL << 32);
-#define HJ_LAUNCH(T, F)                                                                                          \
-    hj_step_generic_kernel<T, F><<<blocks, threads, 0, g->stream>>>(                                       \
+#define HJ_LAUNCH_Q(F, K)                                                                                     \
+    hj_step_q527_kernel<F, K><<<blocks, threads, 0, g->stream>>>(                                          \
+        (const int32_t *)g->v0, (int32_t *)g->buf, (const HjCoef<double> *)g->coef, g->qw,                  \
+        (const double *)g->k4tab, g->dstate, g->geom, g->nint, dv)
+#define HJ_LAUNCH(T, F, K)                                                                                    \
+    hj_step_generic_kernel<T, F, K><<<blocks, threads, 0, g->stream>>>(                                    \
         (const T *)g->v0, (T *)g->buf, (const HjCoef<T> *)g->coef, g->scaled, g->k4tab, g->dstate, g->geom, \
         g->nint, dv)
+#define HJ_LAUNCH2(T, F)          \
+    do {                          \
+        if (g->track)             \
+            HJ_LAUNCH(T, F, true);  \
+        else                      \
+            HJ_LAUNCH(T, F, false); \
+    } while (0)
     if (g->prec == HJ_Q527) {
-        if (fast)
-            hj_step_q527_kernel<true><<<blocks, threads, 0, g->stream>>>(
-                (const int32_t *)g->v0, (int32_t *)g->buf, (const HjCoef<double> *)g->coef, g->qw,
-                (const double *)g->k4tab, g->dstate, g->geom, g->nint, dv);
-        else
-            hj_step_q527_kernel<false><<<blocks, threads, 0, g->stream>>>(
-                (const int32_t *)g->v0, (int32_t *)g->buf, (const HjCoef<double> *)g->coef, g->qw,
-                (const double *)g->k4tab, g->dstate, g->geom, g->nint, dv);
+        if (fast) {
+            if (g->track) HJ_LAUNCH_Q(true, true);
+            else HJ_LAUNCH_Q(true, false);
+        } else {
+            if (g->track) HJ_LAUNCH_Q(false, true);
+            else HJ_LAUNCH_Q(false, false);
+        }
     } else if (g->prec == HJ_FP64) {
-        if (fast) HJ_LAUNCH(double, true);
-        else HJ_LAUNCH(double, false);
+        if (fast) HJ_LAUNCH2(double, true);
+        else HJ_LAUNCH2(double, false);
     } else {
-        if (fast) HJ_LAUNCH(float, true);
-        else HJ_LAUNCH(float, false);
+        if (fast) HJ_LAUNCH2(float, true);
+        else HJ_LAUNCH2(float, false);
     }
+#undef HJ_LAUNCH_Q
 #undef HJ_LAUNCH
+#undef HJ_LAUNCH2
     return cudaGetLastError();
 }
