@@ -488,8 +488,10 @@ void drop_graphs(hj_batch *b)
     b->graphs.clear();
 }
 
-// Tile of one slot for a block of nc consumer threads: the most rows
-// (ty x tv <= nc / q4), fewest halo reads per row.
+// Tile of one slot for a block of nc consumer threads (ty x tv <= nc / q4).
+// Every item costs the whole block a pass over its planes, whether its rows
+// fill the block or not (ragged last tiles along y and v), so: the fewest
+// items per column sweep, then the fewest halo reads per row.
 void choose_tile(const SlotHost &s, int nc, int *ty_out, int *tv_out)
 {
     const int q4 = s.p4 / 4, max_rows = nc / q4;
@@ -498,10 +500,9 @@ void choose_tile(const SlotHost &s, int nc, int *ty_out, int *tv_out)
     for (int ty = 1; ty <= 16 && ty <= s.n[1]; ++ty)
         for (int tv = 1; tv <= 16 && tv <= s.n[2]; ++tv) {
             if (ty * tv > max_rows) continue;
-            // cost per useful row: halo rows loaded plus idle threads
+            const double items = (double)((s.n[1] + ty - 1) / ty) * ((s.n[2] + tv - 1) / tv);
             const double halo = (double)(ty + 2) * (tv + 2) / (ty * tv);
-            const double idle = (double)max_rows / (ty * tv);
-            const double c = halo + 0.5 * idle;
+            const double c = items * (1.0 + 0.02 * halo);
             if (c < best) {
                 best = c;
                 bty = ty;
