@@ -1083,7 +1083,6 @@ hj_status hj_autotune(hj_grid *g, int32_t steps_per_trial, hj_tile_result *resul
         nc = 1;
     }
 
-    const int ncoef = g->n[2] * g->n[3];
     auto run_steps = [&](int k) -> hj_status {
         *g->hstate = saved;
         HJ_CUDA(cudaMemcpyAsync(g->dstate, g->hstate, sizeof(HjDevState), cudaMemcpyHostToDevice, g->stream));
