@@ -7,7 +7,10 @@
 // that contains z (theta wraps; the other axes clamp onto the grid), grad
 // V(z) the gradient of that interpolant, and u_opt the bang-bang argmax with
 // ties to the upper bound, as in the step kernels.  One thread per state,
-// FP64 arithmetic; grid values are read in the grid's precision.
+// FP64 arithmetic; grid values are read in the grid's precision.  The
+// interpolant is evaluated as a tensor product, one axis at a time (15
+// linear interpolations for the value, 11 more for the gradient, instead of
+// 16 weighted corners per component).
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
@@ -22,7 +25,7 @@ struct QueryGeom {
     int n[4];
     int p4;
     unsigned int periodic;
-    double lo[4], h[4];
+    double lo[4], h[4], inv_h[4];
     int dyn;
     double p[3];
 };
@@ -67,6 +70,13 @@ __device__ __forceinline__ void query_cell(const QueryGeom &q, int d, double z, 
     f = r - (double)i;
 }
 
+// Linear interpolation a + f (b - a); the difference b - a is returned too.
+__device__ __forceinline__ double lerp(double a, double b, double f, double &diff)
+{
+    diff = b - a;
+    return fma(f, diff, a);
+}
+
 template <typename T>
 __global__ void query_kernel(const T *__restrict__ V, const QueryGeom q, const double *__restrict__ states, long long m,
                              double *__restrict__ value, double *__restrict__ grad, double *__restrict__ control)
@@ -83,40 +93,52 @@ __global__ void query_kernel(const T *__restrict__ V, const QueryGeom q, const d
             i1[d] = i0[d] + 1;
             if (i1[d] >= q.n[d]) i1[d] = ((q.periodic >> d) & 1u) ? 0 : q.n[d] - 1;
         }
-        double val = 0.0, g[4] = {0.0, 0.0, 0.0, 0.0};
-#pragma unroll 4
+        // the 16 corner values, corner index ((a*2 + b)*2 + c)*2 + e for
+        // (x, y, v, theta) = (i_a, j_b, k_c, l_e); all loads issued first
+        double c16[16];
+#pragma unroll
         for (int c = 0; c < 16; ++c) {
             long long off = 0;
-            double w = 1.0;
 #pragma unroll
-            for (int d = 0; d < 4; ++d) {
-                const int hi = (c >> d) & 1;
-                off += (long long)(hi ? i1[d] : i0[d]) * strides[d];
-                w *= hi ? f[d] : 1.0 - f[d];
-            }
-            const double vv = value_at(V, off);
-            val += w * vv;
-#pragma unroll
-            for (int d = 0; d < 4; ++d) {
-                double wd = ((c >> d) & 1) ? 1.0 : -1.0;
-#pragma unroll
-                for (int e = 0; e < 4; ++e)
-                    if (e != d) wd *= ((c >> e) & 1) ? f[e] : 1.0 - f[e];
-                g[d] += wd * vv / q.h[d];
-            }
+            for (int d = 0; d < 4; ++d) off += (long long)(((c >> (3 - d)) & 1) ? i1[d] : i0[d]) * strides[d];
+            c16[c] = value_at(V, off);
         }
-        value[s] = val;
-        if (grad)
+        // the multilinear interpolant, contracted one axis at a time (theta,
+        // v, y, x); the differences along each axis give the gradient
+        double a8[8], d3[8], b4[4], d2[4], c2[2], d1[2], d0;
 #pragma unroll
-            for (int d = 0; d < 4; ++d) grad[4 * s + d] = g[d];
+        for (int k = 0; k < 8; ++k) a8[k] = lerp(c16[2 * k], c16[2 * k + 1], f[3], d3[k]);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) b4[k] = lerp(a8[2 * k], a8[2 * k + 1], f[2], d2[k]);
+#pragma unroll
+        for (int k = 0; k < 2; ++k) c2[k] = lerp(b4[2 * k], b4[2 * k + 1], f[1], d1[k]);
+        value[s] = lerp(c2[0], c2[1], f[0], d0);
+        double t;
+        // dV/dx: d0; dV/dy: d1 interpolated along x; dV/dv: d2 along y, x;
+        // dV/dtheta: d3 along v, y, x
+        const double gy = lerp(d1[0], d1[1], f[0], t);
+        const double e2a = lerp(d2[0], d2[1], f[1], t), e2b = lerp(d2[2], d2[3], f[1], t);
+        const double gv = lerp(e2a, e2b, f[0], t);
+        double e3[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) e3[k] = lerp(d3[2 * k], d3[2 * k + 1], f[2], t);
+        const double e3a = lerp(e3[0], e3[1], f[1], t), e3b = lerp(e3[2], e3[3], f[1], t);
+        const double gt = lerp(e3a, e3b, f[0], t);
+        const double g0 = d0 * q.inv_h[0], g1 = gy * q.inv_h[1], g2 = gv * q.inv_h[2], g3 = gt * q.inv_h[3];
+        if (grad) {
+            grad[4 * s + 0] = g0;
+            grad[4 * s + 1] = g1;
+            grad[4 * s + 2] = g2;
+            grad[4 * s + 3] = g3;
+        }
         if (control) {
             double a = 0.0, u = 0.0;
             if (q.dyn == HJ_DYN_CAR4D) {
-                a = g[2] >= 0.0 ? q.p[0] : -q.p[0];
-                u = g[3] >= 0.0 ? q.p[1] : -q.p[1];
+                a = g2 >= 0.0 ? q.p[0] : -q.p[0];
+                u = g3 >= 0.0 ? q.p[1] : -q.p[1];
             } else if (q.dyn == HJ_DYN_CAR4D_STEER) {
-                a = g[2] >= 0.0 ? q.p[0] : -q.p[0];
-                u = g[3] * states[4 * s + 2] >= 0.0 ? q.p[1] : -q.p[1];
+                a = g2 >= 0.0 ? q.p[0] : -q.p[0];
+                u = g3 * states[4 * s + 2] >= 0.0 ? q.p[1] : -q.p[1];
             }
             control[2 * s] = a;
             control[2 * s + 1] = u;
@@ -132,6 +154,7 @@ QueryGeom make_geom(const hj_grid *g)
         q.n[d] = g->n[d];
         q.lo[d] = g->lo[d];
         q.h[d] = g->h[d];
+        q.inv_h[d] = 1.0 / g->h[d];
     }
     q.p4 = g->p4;
     q.periodic = g->periodic;
