@@ -425,6 +425,18 @@ def run_ours(args):
                    "mixed_sizes_fp32_batched": {"sizes": "31x31x11x16, 60x60x20x36, 80x80x25x40, 100x100x30x48",
                                                 **{k: mixed[k] for k in ("requests", "latency_ms",
                                                                          "cell_updates_per_s")}}}
+        # the arrival rates of the serving workload (5-40 req/s), mixed sizes,
+        # FP32 batched against the plain FP64 path, p50 / p99 latency (ms)
+        sweep = {}
+        for rate in args.serving_sweep:
+            trs = scenes.serving_trace(rate, args.serving_sweep_seconds, seed=scenes.SEED_BASE + 40 + int(rate))
+            a = srv_mod.run_server(trs, cuda_stream=stream.cuda_stream)
+            b = srv_mod.run_plain_fp64(trs, cuda_stream=stream.cuda_stream)
+            sweep[f"{rate:g}"] = {"requests": a["requests"],
+                                  "fp32_batched": {k: a["latency_ms"][k] for k in ("p50", "p99")},
+                                  "fp64_plain": {k: b["latency_ms"][k] for k in ("p50", "p99")}}
+        if sweep:
+            serving["rate_sweep_mixed_sizes"] = {"seconds_per_rate": args.serving_sweep_seconds, "req_per_s": sweep}
 
     # end to end through the C ABI with host buffers (pinned), copies timed
     e2e = None
@@ -583,6 +595,8 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serving-rate", type=float, default=40.0)
     ap.add_argument("--serving-seconds", type=float, default=4.0)
+    ap.add_argument("--serving-sweep", type=float, nargs="*", default=[5.0, 10.0, 20.0, 40.0])
+    ap.add_argument("--serving-sweep-seconds", type=float, default=2.0)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("note: fewer than 3 warm-up steps", file=sys.stderr)
