@@ -462,6 +462,17 @@ HJ_API void hj_server_destroy(hj_server *s);
 /* Describe the grid (sizes, spacings, time, memory). */
 HJ_API hj_status hj_get_info(const hj_grid *g, hj_grid_info *info);
 
+/* Self-test of failure detection (the paper has no counterpart): runs a
+ * kernel whose warps wait, with the same bounded mbarrier wait as the step
+ * kernels, on a barrier phase that nothing completes.  The wait gives up
+ * after limit_ns (1 ms .. 2 s) and the kernel records HJ_ERR_TIMEOUT, the
+ * status a step kernel reports when a wait runs out.  No fault, trap or hang
+ * is involved and the context stays usable.  Returns HJ_OK with *status =
+ * HJ_ERR_TIMEOUT (or HJ_OK if the wait had completed) and *waited_ns (may be
+ * NULL) = the time the kernel waited.  Allocates a few bytes; synchronises
+ * the current device. */
+HJ_API hj_status hj_wait_selftest(int64_t limit_ns, int32_t *status, int64_t *waited_ns);
+
 /* Free all device and host resources of the grid (NULL is a no-op). */
 HJ_API void hj_destroy_grid(hj_grid *g);
 

@@ -1,0 +1,71 @@
+// Self-test of the bounded device-side waits (failure detection without a
+// GPU fault).  Every mbarrier wait of the step kernels gives up at a
+// deadline read from %globaltimer and records HJ_ERR_TIMEOUT instead of
+// spinning forever.  This kernel exercises exactly that path: one producer
+// thread initialises an mbarrier that expects one arrival and never
+// arrives; the consumer warps wait on it with the same warp-uniform bounded
+// wait (mbar_wait_warp) as the step kernels, give up at the deadline and
+// record the status.  Nothing faults, traps or hangs; the context stays
+// usable.
+#include "hj_tma.cuh"
+
+namespace {
+
+__global__ void wait_selftest_kernel(unsigned long long limit_ns, int *status, unsigned long long *waited_ns)
+{
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ unsigned long long deadline;
+    __shared__ unsigned long long t0;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);  // one arrival expected; nothing arrives
+        t0 = global_ns();
+        deadline = t0 + limit_ns;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const bool ok = mbar_wait_warp(&bar, 0u, &deadline);
+    if (!ok && (threadIdx.x & 31) == 0) atomicExch(status, (int)HJ_ERR_TIMEOUT);
+    __syncthreads();
+    if (threadIdx.x == 0) *waited_ns = global_ns() - t0;
+}
+
+}  // namespace
+
+extern "C" hj_status hj_wait_selftest(int64_t limit_ns, int32_t *status, int64_t *waited_ns)
+{
+    hj_internal_set_error("");
+    if (!status) {
+        hj_internal_set_error("status is NULL");
+        return HJ_ERR_INVALID_ARG;
+    }
+    if (limit_ns < 1000000 || limit_ns > 2000000000) {
+        hj_internal_set_error("limit_ns must be in [1 ms, 2 s]");
+        return HJ_ERR_INVALID_ARG;
+    }
+    int *d_status = nullptr;
+    unsigned long long *d_waited = nullptr;
+    cudaError_t e = cudaMalloc(&d_status, sizeof(int) + sizeof(unsigned long long) + 8);
+    if (e != cudaSuccess) {
+        hj_internal_set_error(cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? HJ_ERR_OOM : HJ_ERR_CUDA;
+    }
+    d_waited = (unsigned long long *)((char *)d_status + 8);
+    e = cudaMemset(d_status, 0, sizeof(int));
+    if (e == cudaSuccess) {
+        wait_selftest_kernel<<<1, 64>>>((unsigned long long)limit_ns, d_status, d_waited);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    int h_status = -1;
+    unsigned long long h_waited = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&h_status, d_status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(&h_waited, d_waited, sizeof(h_waited), cudaMemcpyDeviceToHost);
+    cudaFree(d_status);
+    if (e != cudaSuccess) {
+        hj_internal_set_error(cudaGetErrorString(e));
+        return HJ_ERR_CUDA;
+    }
+    *status = h_status;
+    if (waited_ns) *waited_ns = (int64_t)h_waited;
+    return HJ_OK;
+}

@@ -158,6 +158,8 @@ _SIGS = {
                                           ctypes.POINTER(hj_solve_stats)]),
     "hj_query": (ctypes.c_int, [_VP, _VP, ctypes.c_int64, _VP, _VP, _VP]),
     "hj_query_device": (ctypes.c_int, [_VP, _VP, ctypes.c_int64, _VP, _VP, _VP]),
+    "hj_wait_selftest": (ctypes.c_int, [ctypes.c_int64, ctypes.POINTER(ctypes.c_int32),
+                                        ctypes.POINTER(ctypes.c_int64)]),
     "hj_read_value": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.c_size_t]),
     "hj_read_value_device": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_size_t]),
     "hj_set_kernel": (ctypes.c_int, [_VP, ctypes.c_int]),
@@ -338,6 +340,14 @@ def hj_query_device(g, states_device, value_device, grad_device=None, control_de
     m = int(states_device.numel()) // 4 if hasattr(states_device, "numel") else int(value_device.numel())
     q = lambda a: None if a is None else ctypes.c_void_p(_dptr(a))
     _check(lib.hj_query_device(g, q(states_device), m, q(value_device), q(grad_device), q(control_device)))
+
+
+def hj_wait_selftest(limit_ns: int):
+    """(status, waited_ns) of the bounded-wait self-test."""
+    st = ctypes.c_int32(0)
+    waited = ctypes.c_int64(0)
+    _check(lib.hj_wait_selftest(int(limit_ns), ctypes.byref(st), ctypes.byref(waited)))
+    return int(st.value), int(waited.value)
 
 
 def hj_read_value(g, out: np.ndarray | None = None, shape=None) -> np.ndarray:
