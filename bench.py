@@ -363,6 +363,49 @@ def run_ours(args):
                               "frac": qbytes * mq / (qms * 1e-3) / 1e9 / measured_peaks()[0],
                               "bytes_per_query": qbytes}}
 
+    # the small single-instance workloads (both fit in the 129 MB L2, so they
+    # are reported as cell-updates/s only): FP32 (tiled) and FP64 solve times,
+    # and the FP32 result against the FP64 one (which matches the oracle to
+    # 1e-12 in the parity tests): max |difference| and BRT sign flips
+    small = None
+    if not args.no_small:
+        small = {}
+        for name in ("car4d_31x31x11x16", "car4d_60x60x20x36"):
+            ws_ = scenes.workload(name)
+            v0s = torch.from_numpy(scenes.initial_value(ws_.grid, ws_.scene)).to("cuda")
+            res = {}
+            outs = {}
+            for pname, pr in (("f32", hj.HJ_FP32), ("f64", hj.HJ_FP64)):
+                gs = hj.Grid(ws_.grid.n, ws_.grid.lo, ws_.grid.hi, ws_.grid.periodic, pr, stream.cuda_stream)
+                gs.set_dynamics(hj.HJ_DYN_CAR4D, (ws_.a_max, ws_.w_max))
+                o = torch.empty(v0s.numel(), dtype=torch.float64, device="cuda")
+                for _ in range(2):
+                    hj.hj_set_initial_value_device(gs.handle, v0s)
+                    gs.solve_brt(ws_.T, ws_.cfl)
+                ks, ms_, steps, loops = 5, [], 0, []
+                for _ in range(ks):
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    hj.hj_set_initial_value_device(gs.handle, v0s)
+                    st_ = gs.solve_brt(ws_.T, ws_.cfl)
+                    e1.record(stream)
+                    e1.synchronize()
+                    ms_.append(e0.elapsed_time(e1))
+                    steps = st_.steps
+                    loops.append(st_.loop_ms)
+                hj.hj_read_value_device(gs.handle, o)
+                outs[pname] = o
+                res[pname] = {"ms_per_solve_median": float(np.median(ms_)), "time_steps": steps,
+                              "avg_step_ms": float(np.median(loops)) / max(steps, 1),
+                              "value": v0s.numel() * steps / (float(np.median(ms_)) * 1e-3), "unit": UNIT,
+                              "kernel": gs.info().kernel}
+                gs.close()
+            d = (outs["f32"] - outs["f64"]).abs()
+            m = outs["f64"].abs() >= 1e-3
+            flips = int((torch.sign(outs["f32"][m]) != torch.sign(outs["f64"][m])).sum().item())
+            small[name] = {**res, "l2_resident": True, "max_abs_fp32_vs_fp64": float(d.max().item()),
+                           "sign_flips_fp32_vs_fp64": flips}
+
     # batched solves: the 64-instance workload (uneven grids, own obstacles,
     # T = 1.5 s), V0 already on the device, one persistent kernel per batch step
     batch = None
@@ -500,6 +543,7 @@ def run_ours(args):
         "e2e": e2e,
         "batch64": batch,
         "query": query,
+        "small_configs": small,
         "serving": serving,
     }
     if "f64" in results:
@@ -563,6 +607,12 @@ def run_ours(args):
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": nthreads, "kind": "oracle",
                                 "sample": f"{nst} oracle time steps of the {WORKLOAD} solve "
                                           f"({nst * ncell:.3e} cell-updates, {el:.1f} s), FP64, OpenMP over x"}
+        # and the plain single-threaded oracle (one time step)
+        rate1, el1, nst1 = oracle_sample(w, V0, 1, 1)
+        line["cpu_baseline_single_thread"] = {
+            "value": rate1, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{nst1} oracle time step of the {WORKLOAD} solve ({nst1 * ncell:.3e} cell-updates, "
+                      f"{el1:.1f} s), FP64, one thread"}
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -586,6 +636,7 @@ def main():
     ap.add_argument("--steer-steps", type=int, default=3)
     ap.add_argument("--no-steer", action="store_true")
     ap.add_argument("--no-query", action="store_true")
+    ap.add_argument("--no-small", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")

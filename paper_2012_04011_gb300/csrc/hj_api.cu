@@ -345,6 +345,63 @@ hj_status launch_step(hj_grid *g, hj_kernel k)
     return HJ_OK;
 }
 
+// Grids below this many cells take a step in a few microseconds, less than
+// launching it costs, so their time loop replays captured graphs.
+constexpr long long GRAPH_MAX_CELLS = 1LL << 24;
+
+// k step launches as one graph launch (captured on first use, kept in a
+// 4-entry cache); false if a graph cannot be used here (the stream is being
+// captured by the caller, or capture failed), and the caller launches the
+// steps one by one.
+bool launch_steps_graph(hj_grid *g, hj_kernel kern, long long k)
+{
+    if (g->ncell >= GRAPH_MAX_CELLS || k < 4 || k > 4096) return false;
+    cudaStreamCaptureStatus cs;
+    if (cudaStreamIsCapturing(g->stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return false;
+    int hit = -1, victim = 0;
+    for (int i = 0; i < 4; ++i) {
+        const hj_grid::StepGraph &e = g->graphs[i];
+        if (e.exec && e.k == k && e.kernel == (int)kern && e.track == (int)g->track && e.version == g->launch_version)
+            hit = i;
+        if (!g->graphs[i].exec) victim = i;
+    }
+    if (hit < 0) {
+        if (g->graphs[victim].exec) victim = (int)(g->graph_tick++ % 4);
+        hj_grid::StepGraph &e = g->graphs[victim];
+        if (e.exec) {
+            cudaGraphExecDestroy(e.exec);
+            e.exec = nullptr;
+        }
+        cudaGraph_t graph = nullptr;
+        if (cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        bool ok = true;
+        for (long long i = 0; i < k && ok; ++i)
+            ok = ((kern == HJ_KERNEL_TILED) ? hj_launch_step_tiled(g) : hj_launch_step_generic(g)) == cudaSuccess;
+        const cudaError_t ce = cudaStreamEndCapture(g->stream, &graph);
+        if (!ok || ce != cudaSuccess || !graph) {
+            if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
+            return false;
+        }
+        const cudaError_t ie = cudaGraphInstantiate(&e.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ie != cudaSuccess) {
+            e.exec = nullptr;
+            cudaGetLastError();
+            return false;
+        }
+        e.k = k;
+        e.kernel = (int)kern;
+        e.track = (int)g->track;
+        e.version = g->launch_version;
+        hit = victim;
+    }
+    return cudaGraphLaunch(g->graphs[hit].exec, g->stream) == cudaSuccess;
+}
+
 // Calls f with a value of the grid element type: double, float or int32_t
 // (Q5.27 codes).
 template <typename F>
@@ -386,6 +443,8 @@ void free_grid(hj_grid *g)
     if (g->hstate) cudaFreeHost(g->hstate);
     for (int i = 0; i < 4; ++i)
         if (g->ev[i]) cudaEventDestroy(g->ev[i]);
+    for (int i = 0; i < 4; ++i)
+        if (g->graphs[i].exec) cudaGraphExecDestroy(g->graphs[i].exec);
     if (g->own_stream && g->stream) cudaStreamDestroy(g->stream);
     delete g;
 }
@@ -796,9 +855,13 @@ static hj_status advance_loop(hj_grid *g, double T, double cfl, int64_t max_step
             HJ_CUDA(cudaEventRecord(g->ev[1], g->stream));
             loop_started = true;
         }
-        for (long long i = 0; i < k; ++i) {
-            if ((s = launch_step(g, kern)) != HJ_OK) return s;
-            ++launches;
+        if (launch_steps_graph(g, kern, k)) {
+            launches += (int)k;
+        } else {
+            for (long long i = 0; i < k; ++i) {
+                if ((s = launch_step(g, kern)) != HJ_OK) return s;
+                ++launches;
+            }
         }
         HJ_CUDA(cudaEventRecord(g->ev[2], g->stream));
         if ((s = pull_state(g)) != HJ_OK) return s;

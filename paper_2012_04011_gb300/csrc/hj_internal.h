@@ -109,6 +109,17 @@ struct hj_grid {
     bool tiled_usign;      // every theta quad has one sign of cos and of sin
 
     cudaEvent_t ev[4];
+    // CUDA graphs of k back-to-back step launches (small grids, where the
+    // launches cost more than the steps); kernel parameters are captured by
+    // value, so a graph is valid while `launch_version` is unchanged
+    struct StepGraph {
+        long long k;
+        int kernel, track;
+        unsigned version;
+        cudaGraphExec_t exec;
+    } graphs[4];
+    unsigned launch_version;  // bumped whenever a step kernel's parameters may change
+    unsigned graph_tick;
     size_t device_bytes;
 };
 

@@ -132,6 +132,7 @@ int hj_tiled_threads(const hj_grid *g, int ty, int tv)
 
 bool hj_tiled_setup(hj_grid *g, char *why, size_t why_len)
 {
+    ++g->launch_version;  // tile, tensor maps or kernel variant may change: captured step graphs are stale
     auto fail = [&](const char *m) {
         snprintf(why, why_len, "%s", m);
         return false;
