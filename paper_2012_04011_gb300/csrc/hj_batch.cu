@@ -240,10 +240,14 @@ __global__ void __launch_bounds__(MAXC + 32, 1)
             float wx[4], wxm[4], wy[4], wym[4], cs[4];
             float vk = 0.f;
             if (rok) {
+                // xdot_1 = v cos(th), xdot_2 = v sin(th): a negative speed flips
+                // the upwind sides, and the weights take |v|
                 vk = I.tab[v];
+                const float sg = vk < 0.f ? -1.f : 1.f;
+                vk = fabsf(vk);
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
-                    const float c = I.tab[N3 + 4 * q + e], s = I.tab[N3 + P4 + 4 * q + e];
+                    const float c = sg * I.tab[N3 + 4 * q + e], s = sg * I.tab[N3 + P4 + 4 * q + e];
                     wx[e] = fmaxf(c, 0.f);
                     wxm[e] = fmaxf(-c, 0.f);
                     wy[e] = fmaxf(s, 0.f);

@@ -155,7 +155,9 @@ bool hj_tiled_setup(hj_grid *g, char *why, size_t why_len)
     // the (cos, sin) sign of each quad's dominant lane [p4]
     float *sgn = (float *)calloc((size_t)g->p4, sizeof(float));
     if (!sgn) return fail("host allocation failed");
-    const bool usign = !fixed && sign_uniform(g, sgn);
+    // the single-sided (USIGN) form also needs every speed >= 0 (a negative
+    // speed flips the upwind side); otherwise the general form runs
+    const bool usign = !fixed && g->lo[2] >= 0.0 && sign_uniform(g, sgn);
     cudaError_t e = cudaMemcpy(g->tab_tiled + g->n[2] + 2 * g->p4, sgn, sizeof(float) * g->p4, cudaMemcpyHostToDevice);
     free(sgn);
     if (e != cudaSuccess) return fail("sign table upload failed");

@@ -241,8 +241,12 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
         // per step on 128x128x64x96).
         constexpr bool LEAN = BCAST || FIXED;
         constexpr bool YONE = LEAN && USIGN && !FIXED;
+        // (the sides are those of cos and sin: the host takes the USIGN form
+        // only when every speed is >= 0; the general form flips the sides of
+        // a negative-speed row, see below)
         const int yoff = yplus ? srow * P4 : -srow * P4;
         const uint32_t yghost = yplus ? 2u : 1u;
+        bool wswapped = false;  // general form: the +/- weights are exchanged for a negative-speed row
         const int lm = (4 * q - 1 + N4) % N4;  // theta index left of the quad
         const int lp = (4 * q + 4) % N4;       // right of the quad
         const int lreal = min(4, N4 - 4 * q);  // real lanes (< 4 only in a padded last quad)
@@ -288,7 +292,22 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
             const int y = it.y0 + jy, v = it.v0 + kv;
             const bool rok = inrow && y < N2 && v < N3;
             const uint32_t rbase = rok ? ((uint32_t)y * N3 + v) * P4 + 4 * q : 0u;
-            const float vk = (rok && !FIXED) ? tab[v] : 0.f;
+            // xdot_1 = v cos(th), xdot_2 = v sin(th): in the general form a
+            // negative speed flips the upwind sides and the weights take |v|
+            float vk = (rok && !FIXED) ? tab[v] : 0.f;
+            const bool vneg = !USIGN && vk < 0.f;
+            if (vneg) vk = -vk;
+            if (!USIGN && !FIXED && vneg != wswapped) {
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const float tx = wx[e], ty = wy[e];
+                    wx[e] = wxm[e];
+                    wxm[e] = tx;
+                    wy[e] = wym[e];
+                    wym[e] = ty;
+                }
+                wswapped = vneg;
+            }
             // theta coefficient of this row's speed (the steering car's heading
             // rate bound grows with v): (k4, -(k3 + k4)), or the fixed-point weight
             float2 k4m = make_float2(0.f, 0.f);

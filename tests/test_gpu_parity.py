@@ -393,3 +393,63 @@ def test_autotune_keeps_results_and_state(hj):
         with pytest.raises(hj.HjError) as e:
             g.autotune(2)  # after steps: refused
         assert e.value.status == hj.HJ_ERR_STATE
+
+
+# ---------------------------------------------------------------- limits and unusual domains
+
+def test_longest_theta_axis(hj):
+    """N4 = 4096, the largest theta axis the API accepts (the tiled kernel
+    takes rows of at most 256 points, so the generic kernel runs)."""
+    w = scenes.custom_workload((5, 4, 3, 4096), n_circles=2, T=0.05, seed=41)
+    V0 = scenes.initial_value(w.grid, w.scene)
+    P = oracle_problem(w)
+    Vo, dts = oracle.solve(P, V0, w.T, w.cfl)
+    V, st = gpu_solve(hj, w, V0, hj.HJ_FP64, hj.HJ_KERNEL_AUTO)
+    assert st.kernel == hj.HJ_KERNEL_GENERIC and st.steps == len(dts)
+    assert float(np.abs(V - Vo).max()) <= 1e-12
+    V, st = gpu_solve(hj, w, V0, hj.HJ_FP32, hj.HJ_KERNEL_AUTO)
+    assert float(np.abs(V - Vo).max()) <= fp32_tol(V0)
+    with pytest.raises(hj.HjError) as e:
+        hj.hj_create_grid((5, 4, 3, 4097), w.grid.lo, w.grid.hi)
+    assert e.value.status == hj.HJ_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("dyn", ["car", "steer"])
+def test_negative_speeds_and_shifted_domain(hj, dyn):
+    """A speed axis through zero (v in [-1, 3]) and an off-centre x/y domain:
+    the steering car's heading rate changes sign with v, the heading-rate
+    car's does not."""
+    import math
+    g = scenes.GridSpec((23, 19, 9, 16), lo=(-2.0, 1.0, -1.0, -math.pi), hi=(6.0, 7.5, 3.0, math.pi))
+    rng = np.random.default_rng(12)
+    sc = scenes.Scene(np.array([[1.0, 3.0, 0.8], [4.0, 5.5, 0.5]]))
+    V0 = scenes.initial_value(g, sc)
+    if dyn == "car":
+        kind, params, okind = hj.HJ_DYN_CAR4D, (1.5, 1.0), oracle.DYN_CAR4D
+    else:
+        kind, params, okind = hj.HJ_DYN_CAR4D_STEER, (1.5, math.pi / 18, 0.3), oracle.DYN_CAR4D_STEER
+    P = oracle.Problem(g.n, g.lo, g.hi, g.periodic, okind, params)
+    Vo, dts = oracle.solve(P, V0, 0.6, 0.8)
+    for prec, kern in ((hj.HJ_FP64, hj.HJ_KERNEL_GENERIC), (hj.HJ_FP32, hj.HJ_KERNEL_TILED),
+                       (hj.HJ_FP32, hj.HJ_KERNEL_GENERIC)):
+        with hj.Grid(g.n, g.lo, g.hi, g.periodic, prec) as gr:
+            gr.set_dynamics(kind, params)
+            gr.set_kernel(kern)
+            gr.set_initial_value(V0)
+            st = gr.solve_brt(0.6, 0.8)
+            V = gr.read_value()
+        if prec == hj.HJ_FP64:
+            assert st.steps == len(dts) and float(np.abs(V - Vo).max()) <= 1e-12
+        else:
+            assert float(np.abs(V - Vo).max()) <= fp32_tol(V0) and sign_flips(V, Vo) == 0
+    Qo, _ = oracle.solve_q527(P, V0, 0.6, 0.8)
+    import torch
+    for kern in (hj.HJ_KERNEL_GENERIC, hj.HJ_KERNEL_TILED):
+        with hj.Grid(g.n, g.lo, g.hi, g.periodic, hj.HJ_Q527) as gr:
+            gr.set_dynamics(kind, params)
+            gr.set_kernel(kern)
+            gr.set_initial_value(V0)
+            gr.solve_brt(0.6, 0.8)
+            out = torch.empty(V0.size, dtype=torch.int32, device="cuda")
+            gr.read_value_device(out)
+        assert np.array_equal(out.cpu().numpy().reshape(g.n), Qo)
