@@ -149,3 +149,23 @@ def test_batch64_workload(hj):
             assert np.array_equal(V, ref)
             Vo, _ = oracle.solve(oracle_problem(w), V0, w.T, w.cfl, nthreads=16)
             assert float(np.abs(V - Vo).max()) <= 1e-4 * float(np.abs(V0).max())
+
+
+def test_batch_slot_with_negative_speeds(hj):
+    """A slot whose speed axis runs through zero (v in [-1, 3]): x' = v cos(th)
+    flips its upwind side where v < 0.  The slot equals the single-grid solve
+    bit for bit and the oracle within the FP32 tolerance."""
+    import math
+    g = scenes.GridSpec((21, 17, 9, 16), lo=(-5.0, -5.0, -1.0, -math.pi), hi=(5.0, 5.0, 3.0, math.pi))
+    w = scenes.Workload("negv", g, scenes.Scene(np.array([[0.5, -1.0, 0.7], [-2.0, 2.5, 0.9]])), 0.5, 0)
+    V0 = scenes.initial_value(g, w.scene)
+    with hj.Batch(2) as b:
+        s = b.add_workload(w)
+        b.set_initial_value(s, V0)
+        b.set_horizon(s, w.T, w.cfl)
+        b.advance()
+        V = b.read_value(s)
+    ref, _ = single_grid(hj, w, V0)
+    assert np.array_equal(V, ref)
+    Vo, _ = oracle.solve(oracle_problem(w), V0, w.T, w.cfl)
+    assert float(np.abs(V - Vo).max()) <= 1e-4 * float(np.abs(V0).max())
