@@ -162,14 +162,35 @@ bool hj_tiled_setup(hj_grid *g, char *why, size_t why_len)
     free(sgn);
     if (e != cudaSuccess) return fail("sign table upload failed");
 
-    // tile shape: by default 8 x 4 rows of (y, v) and as many stages as fit;
-    // one consumer thread per (row, theta quad), at most MAX_CONSUMERS (+ the
-    // producer warp)
+    // tile shape: one consumer thread per (row, theta quad), at most
+    // MAX_CONSUMERS (+ the producer warp).  By default the rows of (y, v) with
+    // the fewest halo reads per row among the shapes whose block fits the
+    // largest launch-bound class that runs without spills (640 consumer
+    // threads; 512 in fixed point), and as many stages as fit; hj_autotune
+    // measures the candidates instead.
     const int q4 = g->p4 / 4;
     const int max_rows = MAX_CONSUMERS / q4;
     if (max_rows < 1) return fail("theta rows too long for one CTA");
-    int ty = g->tile_req[0] > 0 ? g->tile_req[0] : 8;
-    int tv = g->tile_req[1] > 0 ? g->tile_req[1] : 4;
+    int ty = g->tile_req[0], tv = g->tile_req[1];
+    if (ty <= 0 || tv <= 0) {
+        const int cap = fixed ? 512 : 640;
+        double best = 1e300;
+        int bty = 1, btv = 1;
+        for (int a = 1; a <= 16 && a <= g->n[1]; ++a)
+            for (int b = 1; b <= 16 && b <= g->n[2]; ++b) {
+                if ((ty > 0 && a != ty) || (tv > 0 && b != tv)) continue;
+                const int cons = (a * b * q4 + 31) / 32 * 32;
+                if (cons > cap && !(a == 1 && b == 1)) continue;
+                const double c = (double)(a + 2) * (b + 2) / (a * b) - 1e-6 * a * b;  // ties: more rows
+                if (c < best) {
+                    best = c;
+                    bty = a;
+                    btv = b;
+                }
+            }
+        ty = bty;
+        tv = btv;
+    }
     if (tv > g->n[2]) tv = g->n[2];
     if (ty > g->n[1]) ty = g->n[1];
     while (ty * tv > max_rows && ty > 1) --ty;
