@@ -851,6 +851,7 @@ static hj_status advance_loop(hj_grid *g, double T, double cfl, int64_t max_step
         }
         if (k > max_steps - taken) k = max_steps - taken;
         if (threshold > 0.0 && k > 32) k = 32;  // the test can end the loop at any step: look every 32
+        if (k > (1 << 16)) k = 1 << 16;          // read the device state (and any error) at least this often
         if (!loop_started) {
             HJ_CUDA(cudaEventRecord(g->ev[1], g->stream));
             loop_started = true;
