@@ -1117,7 +1117,7 @@ hj_status hj_autotune(hj_grid *g, int32_t steps_per_trial, hj_tile_result *resul
     struct Cand {
         int ty, tv;
         double halo;
-    } cands[16];
+    } cands[17];
     int nc = 0;
     const int class_hi[4] = {384, 512, 640, 768};
     for (int cls = 0; cls < 4; ++cls) {
@@ -1142,10 +1142,9 @@ hj_status hj_autotune(hj_grid *g, int32_t steps_per_trial, hj_tile_result *resul
             }
         for (int i = 0; i < nt; ++i) cands[nc++] = top[i];
     }
-    if (nc == 0) {  // tiny grids: whatever the default shape is
-        cands[0] = {0, 0, 0.0};
-        nc = 1;
-    }
+    // and the default shape, which on a small grid trades halo reads for more
+    // CTAs (the only candidate on a grid too small for the classes above)
+    cands[nc++] = {0, 0, 0.0};
 
     auto run_steps = [&](int k) -> hj_status {
         *g->hstate = saved;

@@ -166,8 +166,9 @@ bool hj_tiled_setup(hj_grid *g, char *why, size_t why_len)
     // MAX_CONSUMERS (+ the producer warp).  By default the rows of (y, v) with
     // the fewest halo reads per row among the shapes whose block fits the
     // largest launch-bound class that runs without spills (640 consumer
-    // threads; 512 in fixed point), and as many stages as fit; hj_autotune
-    // measures the candidates instead.
+    // threads; 512 in fixed point), discounted by the share of the SMs the
+    // shape can keep busy (a small grid needs small tiles to fill the GPU),
+    // and as many stages as fit; hj_autotune measures the candidates instead.
     const int q4 = g->p4 / 4;
     const int max_rows = MAX_CONSUMERS / q4;
     if (max_rows < 1) return fail("theta rows too long for one CTA");
@@ -181,7 +182,11 @@ bool hj_tiled_setup(hj_grid *g, char *why, size_t why_len)
                 if ((ty > 0 && a != ty) || (tv > 0 && b != tv)) continue;
                 const int cons = (a * b * q4 + 31) / 32 * 32;
                 if (cons > cap && !(a == 1 && b == 1)) continue;
-                const double c = (double)(a + 2) * (b + 2) / (a * b) - 1e-6 * a * b;  // ties: more rows
+                // work items this shape can offer (columns x chunks of >= 4 planes)
+                const double items = (double)((g->n[1] + a - 1) / a) * ((g->n[2] + b - 1) / b) *
+                                     (g->n[0] / 4 > 1 ? g->n[0] / 4 : 1);
+                const double busy = items < sms ? items / (sms > 0 ? sms : 1) : 1.0;
+                const double c = (double)(a + 2) * (b + 2) / (a * b) / busy - 1e-6 * a * b;  // ties: more rows
                 if (c < best) {
                     best = c;
                     bty = a;
