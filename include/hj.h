@@ -103,7 +103,10 @@ typedef enum {
 typedef enum {
     HJ_KERNEL_AUTO = 0,
     HJ_KERNEL_GENERIC = 1, /* one thread per cell, loads through L1/L2 */
-    HJ_KERNEL_TILED = 2    /* FP32, Q5.27: TMA-staged 4D tiles streamed along x */
+    HJ_KERNEL_TILED = 2,   /* FP32, Q5.27: TMA-staged 4D tiles streamed along x */
+    HJ_KERNEL_RESIDENT = 3 /* the generic per-cell update, many steps per cooperative launch
+                            * with a grid barrier between steps (small grids); any
+                            * precision, identical results to HJ_KERNEL_GENERIC */
 } hj_kernel;
 
 typedef struct {
@@ -472,6 +475,14 @@ HJ_API hj_status hj_get_info(const hj_grid *g, hj_grid_info *info);
  * NULL) = the time the kernel waited.  Allocates a few bytes; synchronises
  * the current device. */
 HJ_API hj_status hj_wait_selftest(int64_t limit_ns, int32_t *status, int64_t *waited_ns);
+
+/* The same self-test for the grid barrier of HJ_KERNEL_RESIDENT: a
+ * cooperative launch of two CTAs waits, with the resident kernel's bounded
+ * barrier, for a third CTA that does not exist.  Each wait gives up after
+ * limit_ns (1 ms .. 2 s) and the kernel records HJ_ERR_TIMEOUT, the status
+ * the resident kernel reports when a barrier runs out.  Same outputs and
+ * side effects as hj_wait_selftest. */
+HJ_API hj_status hj_barrier_selftest(int64_t limit_ns, int32_t *status, int64_t *waited_ns);
 
 /* Free all device and host resources of the grid (NULL is a no-op). */
 HJ_API void hj_destroy_grid(hj_grid *g);

@@ -21,7 +21,11 @@ LIB_PATH = os.path.join(OUT_DIR, "libhj.so")
 OBJ_DIR = os.path.join(OUT_DIR, "obj")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fvisibility=hidden",
+# Host code is compiled without floating-point contraction: the coefficient
+# tables (v_k = lo + k dx, theta_l, v cos theta, ...) then round exactly as the
+# plain FP64 arithmetic they restate on every host architecture (GCC contracts
+# a * b + c into an FMA by default where the ISA has one, e.g. on aarch64).
+NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fvisibility=hidden,-ffp-contract=off",
               "-Xptxas", "-v", "--expt-relaxed-constexpr"]
 
 

@@ -332,15 +332,31 @@ hj_status reset_state(hj_grid *g)
     return HJ_OK;
 }
 
+// Whether HJ_KERNEL_AUTO takes the resident kernel: FP32 grids of up to 4 M
+// cells and Q5.27 grids of up to 8 M cells (measured crossovers against the
+// tiled kernel), where a step takes a few microseconds and the per-step
+// launch and last-CTA finaliser of the other kernels cost about as much.
+// Larger grids stream faster through the tiled kernel; FP64 steps are bound
+// by the FP64 unit, where the resident form gains nothing.
+bool resident_auto(const hj_grid *g)
+{
+    const long long cap = g->prec == HJ_FP32 ? (4LL << 20) : (g->prec == HJ_Q527 ? (8LL << 20) : 0);
+    return g->ncell <= cap && hj_resident_supported(g);
+}
+
 hj_kernel effective_kernel(const hj_grid *g)
 {
     if (g->kernel_req == HJ_KERNEL_GENERIC) return HJ_KERNEL_GENERIC;
+    if (g->kernel_req == HJ_KERNEL_RESIDENT) return HJ_KERNEL_RESIDENT;
+    if (g->kernel_req == HJ_KERNEL_AUTO && resident_auto(g)) return HJ_KERNEL_RESIDENT;
     return g->tiled_ok ? HJ_KERNEL_TILED : HJ_KERNEL_GENERIC;
 }
 
 hj_status launch_step(hj_grid *g, hj_kernel k)
 {
-    cudaError_t e = (k == HJ_KERNEL_TILED) ? hj_launch_step_tiled(g) : hj_launch_step_generic(g);
+    cudaError_t e = (k == HJ_KERNEL_TILED)     ? hj_launch_step_tiled(g)
+                    : (k == HJ_KERNEL_RESIDENT) ? hj_launch_step_resident(g, 1)
+                                                : hj_launch_step_generic(g);
     if (e != cudaSuccess) return set_err(HJ_ERR_CUDA, "step launch: %s", cudaGetErrorString(e));
     return HJ_OK;
 }
@@ -439,6 +455,7 @@ void free_grid(hj_grid *g)
     if (g->qw) cudaFree(g->qw);
     if (g->v0xy) cudaFree(g->v0xy);
     if (g->k4tab) cudaFree(g->k4tab);
+    if (g->rsync) cudaFree(g->rsync);
     if (g->dstate) cudaFree(g->dstate);
     if (g->hstate) cudaFreeHost(g->hstate);
     for (int i = 0; i < 4; ++i)
@@ -850,13 +867,18 @@ static hj_status advance_loop(hj_grid *g, double T, double cfl, int64_t max_step
             k = r > 1 ? (r < 1e15 ? (long long)r : (long long)1e15) : 1;
         }
         if (k > max_steps - taken) k = max_steps - taken;
-        if (threshold > 0.0 && k > 32) k = 32;  // the test can end the loop at any step: look every 32
-        if (k > (1 << 16)) k = 1 << 16;          // read the device state (and any error) at least this often
+        // the resident kernel ends the loop itself (horizon, convergence)
+        if (kern == HJ_KERNEL_RESIDENT) k = max_steps - taken;
+        if (threshold > 0.0 && k > 32 && kern != HJ_KERNEL_RESIDENT) k = 32;  // graphs: look every 32 steps
+        if (k > (1 << 16)) k = 1 << 16;  // read the device state (and any error) at least this often
         if (!loop_started) {
             HJ_CUDA(cudaEventRecord(g->ev[1], g->stream));
             loop_started = true;
         }
-        if (launch_steps_graph(g, kern, k)) {
+        if (kern == HJ_KERNEL_RESIDENT) {
+            HJ_CUDA(hj_launch_step_resident(g, k));
+            ++launches;
+        } else if (launch_steps_graph(g, kern, k)) {
             launches += (int)k;
         } else {
             for (long long i = 0; i < k; ++i) {
@@ -1062,8 +1084,11 @@ hj_status hj_set_kernel(hj_grid *g, hj_kernel kernel)
     g_err[0] = 0;
     hj_status s = check_grid(g);
     if (s != HJ_OK) return s;
-    if (kernel != HJ_KERNEL_AUTO && kernel != HJ_KERNEL_GENERIC && kernel != HJ_KERNEL_TILED)
+    if (kernel != HJ_KERNEL_AUTO && kernel != HJ_KERNEL_GENERIC && kernel != HJ_KERNEL_TILED &&
+        kernel != HJ_KERNEL_RESIDENT)
         return set_err(HJ_ERR_INVALID_ARG, "unknown kernel %d", (int)kernel);
+    if (kernel == HJ_KERNEL_RESIDENT && !hj_resident_supported(g))
+        return set_err(HJ_ERR_UNSUPPORTED, "the resident kernel needs cooperative launch and fewer than 2^32 cells");
     if (kernel == HJ_KERNEL_TILED && !g->tiled_ok)
         return set_err(HJ_ERR_UNSUPPORTED, "the tiled kernel does not support this grid (FP32 or Q5.27 car grids "
                                            "with periodic theta only; set the dynamics first)");

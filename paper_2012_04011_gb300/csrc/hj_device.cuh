@@ -65,14 +65,14 @@ __device__ __forceinline__ void hj_next_dt(HjDevState *st, const HjGeom &g, cons
     st->done = 0;
 }
 
-// Run by one thread of the last CTA to finish a step: publish alpha^max,
-// advance t and n, compute the next dt, reset the per-step accumulators.
-__device__ __forceinline__ void hj_finalise(HjDevState *st, const HjGeom &g)
+// The finaliser's arithmetic, given the step's alpha_1^max, alpha_2^max
+// (|xdot_1|, |xdot_2| maxima) and largest change eps: publish alpha^max,
+// advance t and n, run the convergence test, compute the next dt.
+__device__ __forceinline__ void hj_finalise_values(HjDevState *st, const HjGeom &g, double a1, double a2, double eps)
 {
-    __threadfence();
     double a[4];
-    a[0] = __longlong_as_double((long long)atomicAdd(&st->alpha_bits[0], 0ull));
-    a[1] = __longlong_as_double((long long)atomicAdd(&st->alpha_bits[1], 0ull));
+    a[0] = a1;
+    a[1] = a2;
     a[2] = g.alpha3;  // |a_opt| = a_max at every cell (bang-bang), |c3| for constant dynamics
     a[3] = g.alpha4;
 #pragma unroll
@@ -83,9 +83,7 @@ __device__ __forceinline__ void hj_finalise(HjDevState *st, const HjGeom &g)
     st->t = tn;
     st->n = st->n + 1;
     if (st->track) {  // Algorithm 2's convergence test on the step just taken
-        const double eps = __longlong_as_double((long long)atomicAdd(&st->delta_bits, 0ull));
         st->delta_last = eps;
-        st->delta_bits = 0ull;
         if (eps < st->threshold) st->converged = 1;
     }
     if (st->status == HJ_OK)
@@ -93,21 +91,31 @@ __device__ __forceinline__ void hj_finalise(HjDevState *st, const HjGeom &g)
     else
         st->done = 1;
     if (st->converged) st->done = 1;
+}
+
+// Run by one thread of the last CTA to finish a step: read the grid-wide
+// maxima, finalise, reset the per-step accumulators.
+__device__ __forceinline__ void hj_finalise(HjDevState *st, const HjGeom &g)
+{
+    __threadfence();
+    const double a1 = __longlong_as_double((long long)atomicAdd(&st->alpha_bits[0], 0ull));
+    const double a2 = __longlong_as_double((long long)atomicAdd(&st->alpha_bits[1], 0ull));
+    const double eps = st->track ? __longlong_as_double((long long)atomicAdd(&st->delta_bits, 0ull)) : 0.0;
+    hj_finalise_values(st, g, a1, a2, eps);
     st->alpha_bits[0] = 0ull;
     st->alpha_bits[1] = 0ull;
+    st->delta_bits = 0ull;
     st->blocks_done = 0u;
     __threadfence();
 }
 
 // Block-wide max of the CTA's |xdot_1|, |xdot_2| partials and of its largest
 // change |V_{n+1} - V_n| (bit patterns of non-negative doubles; the change
-// is 0 outside the convergence mode), then the grid-wide atomic max and the
-// last-CTA finaliser.  Every thread of the block must call it.  `scratch`
-// holds at least 3 * 32 unsigned long long.  Thread 0 returns whether its
-// CTA was the last one.
-__device__ __forceinline__ bool hj_step_reduce(HjDevState *st, const HjGeom &g, unsigned long long a1,
-                                               unsigned long long a2, unsigned long long d,
-                                               unsigned long long *scratch)
+// is 0 outside the convergence mode).  Every thread of the block must call
+// it; thread 0 returns the CTA's maxima in a1, a2, d.  `scratch` holds at
+// least 3 * 32 unsigned long long.
+__device__ __forceinline__ void hj_block_max3(unsigned long long &a1, unsigned long long &a2, unsigned long long &d,
+                                              unsigned long long *scratch)
 {
     a1 = hj_warp_max_u64(a1);
     a2 = hj_warp_max_u64(a2);
@@ -119,13 +127,25 @@ __device__ __forceinline__ bool hj_step_reduce(HjDevState *st, const HjGeom &g, 
         scratch[64 + warp] = d;
     }
     __syncthreads();
-    bool last = false;
     if (threadIdx.x == 0) {
         for (int w = 1; w < nwarp; ++w) {
             a1 = a1 > scratch[w] ? a1 : scratch[w];
             a2 = a2 > scratch[32 + w] ? a2 : scratch[32 + w];
             d = d > scratch[64 + w] ? d : scratch[64 + w];
         }
+    }
+}
+
+// The CTA's maxima (hj_block_max3), then the grid-wide atomic max and the
+// last-CTA finaliser.  Every thread of the block must call it.  Thread 0
+// returns whether its CTA was the last one.
+__device__ __forceinline__ bool hj_step_reduce(HjDevState *st, const HjGeom &g, unsigned long long a1,
+                                               unsigned long long a2, unsigned long long d,
+                                               unsigned long long *scratch)
+{
+    hj_block_max3(a1, a2, d, scratch);
+    bool last = false;
+    if (threadIdx.x == 0) {
         atomicMax(&st->alpha_bits[0], a1);
         atomicMax(&st->alpha_bits[1], a2);
         if (d) atomicMax(&st->delta_bits, d);

@@ -50,6 +50,16 @@ struct HjScaledCoef {
     double w1, w2, w0, w4;  // w4 = dt |xdot_4| / dx_4 (depends on v for the steering car)
 };
 
+// Device-side bookkeeping of the resident step kernel: the grid barrier's
+// arrival counter and three rotating slots of the per-step largest change
+// of V (convergence mode; FP64 bit patterns).  Zeroed before every resident
+// launch.
+struct HjResidentSync {
+    unsigned int count;
+    unsigned int unused;
+    unsigned long long slot[3];
+};
+
 // Grid geometry handed to kernels by value.
 struct HjGeom {
     int32_t n1, n2, n3, n4;  // points per axis
@@ -120,12 +130,18 @@ struct hj_grid {
     } graphs[4];
     unsigned launch_version;  // bumped whenever a step kernel's parameters may change
     unsigned graph_tick;
+    HjResidentSync *rsync;    // resident kernel bookkeeping (allocated on first use)
     size_t device_bytes;
 };
 
 // Launchers (each returns the CUDA error of its launch).
 cudaError_t hj_launch_step_generic(hj_grid *g);
 cudaError_t hj_launch_step_tiled(hj_grid *g);
+// Up to k steps in one cooperative launch of the resident kernel (it stops
+// early when the time loop is done); allocates g->rsync on first use.
+cudaError_t hj_launch_step_resident(hj_grid *g, long long k);
+// Whether the device can run the resident kernel (cooperative launch).
+bool hj_resident_supported(const hj_grid *g);
 // Set up the tiled kernel for g (tensor maps, tile shape); false if unsupported.
 bool hj_tiled_setup(hj_grid *g, char *why, size_t why_len);
 // Consumer threads a tile of ty x tv rows needs (one per row and theta quad),
@@ -162,18 +178,22 @@ cudaError_t hj_launch_prologue_f32(HjDevState *st, const HjGeom &g, const HjCoef
 // Rescale the FP64 coefficient table for dt (all threads of one block call
 // it; the table covers n3 * n4 entries; k4 holds the theta coefficient of
 // each speed).
+// One entry of that table: coefficients c of a (v, theta), theta
+// coefficient k4 of the speed.
+__device__ __forceinline__ HjScaledCoef hj_scaled_entry(const HjCoef<double> &c, double k4, double dt)
+{
+    HjScaledCoef o;
+    o.w1 = dt * c.c1;
+    o.w2 = dt * c.c2;
+    o.w0 = 1.0 - dt * c.ks;
+    o.w4 = dt * k4;
+    return o;
+}
+
 __device__ __forceinline__ void hj_rescale_table(HjScaledCoef *sc, const HjCoef<double> *coef, const double *k4,
                                                  int n3, int n4, double dt)
 {
-    for (int i = threadIdx.x; i < n3 * n4; i += blockDim.x) {
-        const HjCoef<double> c = coef[i];
-        HjScaledCoef o;
-        o.w1 = dt * c.c1;
-        o.w2 = dt * c.c2;
-        o.w0 = 1.0 - dt * c.ks;
-        o.w4 = dt * k4[i / n4];
-        sc[i] = o;
-    }
+    for (int i = threadIdx.x; i < n3 * n4; i += blockDim.x) sc[i] = hj_scaled_entry(coef[i], k4[i / n4], dt);
 }
 
 // ---- Q5.27 fixed point (Sec. III-C, Sec. IV-B): int32 codes q, value q 2^-27

@@ -6,8 +6,10 @@
 // arrives; the consumer warps wait on it with the same warp-uniform bounded
 // wait (mbar_wait_warp) as the step kernels, give up at the deadline and
 // record the status.  Nothing faults, traps or hangs; the context stays
-// usable.
-#include "hj_tma.cuh"
+// usable.  The grid-barrier self-test does the same for the resident step
+// kernel's barrier (hj_grid_sync): two co-resident CTAs wait for a third
+// arrival that never comes.
+#include "hj_resident.cuh"
 
 namespace {
 
@@ -29,9 +31,25 @@ __global__ void wait_selftest_kernel(unsigned long long limit_ns, int *status, u
     if (threadIdx.x == 0) *waited_ns = global_ns() - t0;
 }
 
-}  // namespace
+// Two CTAs, a barrier that expects three arrivals.
+__global__ void barrier_selftest_kernel(HjResidentSync *sync, unsigned long long limit_ns, int *status,
+                                        unsigned long long *waited_ns)
+{
+    __shared__ int s_ok;
+    const unsigned long long t0 = global_ns();
+    const bool ok = hj_grid_sync(&sync->count, gridDim.x + 1u, limit_ns, &s_ok);
+    if (threadIdx.x == 0) {
+        if (!ok) atomicExch(status, (int)HJ_ERR_TIMEOUT);
+        atomicMax(waited_ns, global_ns() - t0);
+    }
+}
 
-extern "C" hj_status hj_wait_selftest(int64_t limit_ns, int32_t *status, int64_t *waited_ns)
+typedef void (*SelftestLaunch)(unsigned long long limit_ns, int *status, unsigned long long *waited_ns, void *scratch,
+                               cudaError_t *err);
+
+// Runs one self-test kernel with a device status word, waited time and
+// scratch area; copies the results back.
+hj_status run_selftest(int64_t limit_ns, int32_t *status, int64_t *waited_ns, SelftestLaunch launch)
 {
     hj_internal_set_error("");
     if (!status) {
@@ -42,25 +60,23 @@ extern "C" hj_status hj_wait_selftest(int64_t limit_ns, int32_t *status, int64_t
         hj_internal_set_error("limit_ns must be in [1 ms, 2 s]");
         return HJ_ERR_INVALID_ARG;
     }
-    int *d_status = nullptr;
-    unsigned long long *d_waited = nullptr;
-    cudaError_t e = cudaMalloc(&d_status, sizeof(int) + sizeof(unsigned long long) + 8);
+    char *d = nullptr;
+    const size_t bytes = 16 + sizeof(HjResidentSync);
+    cudaError_t e = cudaMalloc(&d, bytes);
     if (e != cudaSuccess) {
         hj_internal_set_error(cudaGetErrorString(e));
         return e == cudaErrorMemoryAllocation ? HJ_ERR_OOM : HJ_ERR_CUDA;
     }
-    d_waited = (unsigned long long *)((char *)d_status + 8);
-    e = cudaMemset(d_status, 0, sizeof(int));
-    if (e == cudaSuccess) {
-        wait_selftest_kernel<<<1, 64>>>((unsigned long long)limit_ns, d_status, d_waited);
-        e = cudaGetLastError();
-    }
+    int *d_status = (int *)d;
+    unsigned long long *d_waited = (unsigned long long *)(d + 8);
+    e = cudaMemset(d, 0, bytes);
+    if (e == cudaSuccess) launch((unsigned long long)limit_ns, d_status, d_waited, d + 16, &e);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     int h_status = -1;
     unsigned long long h_waited = 0;
     if (e == cudaSuccess) e = cudaMemcpy(&h_status, d_status, sizeof(int), cudaMemcpyDeviceToHost);
     if (e == cudaSuccess) e = cudaMemcpy(&h_waited, d_waited, sizeof(h_waited), cudaMemcpyDeviceToHost);
-    cudaFree(d_status);
+    cudaFree(d);
     if (e != cudaSuccess) {
         hj_internal_set_error(cudaGetErrorString(e));
         return HJ_ERR_CUDA;
@@ -68,4 +84,30 @@ extern "C" hj_status hj_wait_selftest(int64_t limit_ns, int32_t *status, int64_t
     *status = h_status;
     if (waited_ns) *waited_ns = (int64_t)h_waited;
     return HJ_OK;
+}
+
+void launch_wait(unsigned long long limit_ns, int *status, unsigned long long *waited_ns, void *, cudaError_t *err)
+{
+    wait_selftest_kernel<<<1, 64>>>(limit_ns, status, waited_ns);
+    *err = cudaGetLastError();
+}
+
+void launch_barrier(unsigned long long limit_ns, int *status, unsigned long long *waited_ns, void *scratch,
+                    cudaError_t *err)
+{
+    HjResidentSync *sync = (HjResidentSync *)scratch;
+    void *args[] = {&sync, &limit_ns, &status, &waited_ns};
+    *err = cudaLaunchCooperativeKernel((const void *)barrier_selftest_kernel, 2, 64, args, 0, 0);
+}
+
+}  // namespace
+
+extern "C" hj_status hj_barrier_selftest(int64_t limit_ns, int32_t *status, int64_t *waited_ns)
+{
+    return run_selftest(limit_ns, status, waited_ns, launch_barrier);
+}
+
+extern "C" hj_status hj_wait_selftest(int64_t limit_ns, int32_t *status, int64_t *waited_ns)
+{
+    return run_selftest(limit_ns, status, waited_ns, launch_wait);
 }

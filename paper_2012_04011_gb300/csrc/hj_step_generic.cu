@@ -19,6 +19,14 @@
 // keeps the differences (V_up - V_c) for accuracy.  The Q5.27 kernel
 // (hj_step_q527_kernel) evaluates the same form in exact integer differences
 // with fixed-point weights.
+//
+// The same per-cell updates also run in a resident form
+// (hj_step_resident_kernel): one cooperative launch takes many steps, with a
+// bounded grid barrier between them instead of a kernel boundary, for grids
+// so small that launching a step costs more than computing it.
+#include <type_traits>
+
+#include "hj_resident.cuh"
 #include "hj_scaled.cuh"
 
 namespace {
@@ -127,10 +135,134 @@ __device__ __forceinline__ long long q_upwind(const QDiff &d, int mode)
     return mode == HJ_AXIS_PLUS ? d.dp : d.dm;
 }
 
+// ---------------------------------------------------------- one cell's update
+// Shared by the per-step and the resident kernels, so that both give the
+// same result bit for bit.
+
+// FP32: V_c + dt (K1 (V_up1 - V_c) + K2 (V_up2 - V_c) + k3 (V_up3 - V_c) +
+// k4 (V_up4 - V_c)), then the BRT min with V0 (Algorithm 2).  c1, c2 are the
+// signed xdot_d / dx_d of the cell's (v, theta).
+__device__ __forceinline__ float cell_value(float vc, float v0c, const Neigh<float> &nx, const Neigh<float> &ny,
+                                            const Neigh<float> &nv, const Neigh<float> &nt, float c1, float c2,
+                                            float k3, float k4, float dt, int mode3, int mode4)
+{
+    const float u3 = upwind_value<float>(nv, mode3);
+    const float u4 = upwind_value<float>(nt, mode4);
+    const float u1 = nonneg(c1) ? nx.p : nx.m;
+    const float u2 = nonneg(c2) ? ny.p : ny.m;
+    const float K1 = fabsf(c1), K2 = fabsf(c2);
+    float r = K1 * (u1 - vc);
+    r = fmaf(K2, u2 - vc, r);
+    r = fmaf(k3, u3 - vc, r);
+    r = fmaf(k4, u4 - vc, r);
+    return hj_min(v0c, fmaf(dt, r, vc));
+}
+
+// FP64: w0 V_c + |w1| V_up1 + |w2| V_up2 + dt k3 V_up3 + w4 V_up4 (1 DMUL +
+// 4 DFMA; signs and magnitudes by integer operations), then the BRT min.
+__device__ __forceinline__ double cell_value(double vc, double v0c, const Neigh<double> &nx, const Neigh<double> &ny,
+                                             const Neigh<double> &nv, const Neigh<double> &nt,
+                                             const HjScaledCoef &sc, double k3dt, int mode3, int mode4)
+{
+    const double u3 = upwind_value<double>(nv, mode3);
+    const double u4 = upwind_value<double>(nt, mode4);
+    const double u1 = nonneg(sc.w1) ? nx.p : nx.m;
+    const double u2 = nonneg(sc.w2) ? ny.p : ny.m;
+    double r = sc.w0 * vc;
+    r = fma(mag(sc.w1), u1, r);
+    r = fma(mag(sc.w2), u2, r);
+    r = fma(k3dt, u3, r);
+    return hj_min(v0c, fma(sc.w4, u4, r));
+}
+
+// Q5.27: V_c + round_half_up(sum_d W_d (V_up,d - V_c) / 2^30), BRT min,
+// saturation (hj_q527_update); w1, w2 signed (the sign picks the side).
+__device__ __forceinline__ int32_t q_cell_value(int32_t vc, int32_t v0c, const QDiff &dx, const QDiff &dy,
+                                                const QDiff &dv3, const QDiff &dv4, int32_t w1, int32_t w2,
+                                                int32_t w3, int32_t w4, int mode3, int mode4)
+{
+    const long long d1 = w1 >= 0 ? dx.dp : dx.dm;
+    const long long d2 = w2 >= 0 ? dy.dp : dy.dm;
+    return hj_q527_update(vc, v0c, d1, d2, q_upwind(dv3, mode3), q_upwind(dv4, mode4), abs(w1), abs(w2), w3, w4);
+}
+
+// A cell's indices (i, j, k, l) and its offset in the padded layout, from
+// its linear index c over the n1 x n2 x n3 x n4 cells.
+struct Cell {
+    long long o;
+    int i, j, k, l;
+};
+
+template <bool FAST32>
+__device__ __forceinline__ Cell cell_at(unsigned long long c, const Divisors &dv, const HjGeom &g)
+{
+    const unsigned int N2 = g.n2, N3 = g.n3, N4 = g.n4;
+    unsigned long long row;
+    Cell r;
+    if (FAST32) {  // the grid has fewer than 2^32 cells
+        const uint32_t c32 = (uint32_t)c, row32 = fast_div(c32, dv.n4);
+        const uint32_t r2 = fast_div(row32, dv.n3);
+        const uint32_t i32 = fast_div(r2, dv.n2);
+        row = row32;
+        r.l = (int)(c32 - row32 * N4);
+        r.k = (int)(row32 - r2 * N3);
+        r.i = (int)i32;
+        r.j = (int)(r2 - i32 * N2);
+    } else {
+        row = c / N4;
+        r.l = (int)(c - row * N4);
+        const unsigned long long r2 = row / N3;
+        r.k = (int)(row - r2 * N3);
+        r.i = (int)(r2 / N2);
+        r.j = (int)(r2 - (unsigned long long)r.i * N2);
+    }
+    r.o = (long long)row * g.p4 + r.l;
+    return r;
+}
+
+// Per-thread maxima of a step: |xdot_1|, |xdot_2| and the change of V.
+struct StepMax {
+    unsigned long long a1 = 0ull, a2 = 0ull, d = 0ull;  // FP64 bit patterns (Q5.27: d in codes)
+    float a1f = 0.f, a2f = 0.f, df = 0.f;               // FP32 kernels
+};
+
+// The maxima as bit patterns of non-negative doubles.
+template <typename T>
+__device__ __forceinline__ void step_max_bits(const StepMax &m, unsigned long long &a1, unsigned long long &a2,
+                                              unsigned long long &d)
+{
+    if constexpr (std::is_same<T, float>::value) {
+        a1 = hj_abits((double)m.a1f);
+        a2 = hj_abits((double)m.a2f);
+        d = hj_abits((double)m.df);
+    } else if constexpr (std::is_same<T, double>::value) {
+        a1 = m.a1;
+        a2 = m.a2;
+        d = m.d;
+    } else {  // the largest change in codes, as the FP64 value it stands for (exact)
+        a1 = m.a1;
+        a2 = m.a2;
+        d = hj_abits((double)m.d * (1.0 / HJ_Q527_SCALE));
+    }
+}
+
+// Largest change of V, per precision (convergence mode).
+__device__ __forceinline__ void track_change(StepMax &m, float vn, float vc) { m.df = fmaxf(m.df, fabsf(vn - vc)); }
+__device__ __forceinline__ void track_change(StepMax &m, double vn, double vc)
+{
+    const unsigned long long b = hj_abits(mag(vn - vc));
+    m.d = m.d > b ? m.d : b;
+}
+__device__ __forceinline__ void track_change(StepMax &m, int32_t vn, int32_t vc)
+{
+    const long long dd = (long long)vn - vc;
+    const unsigned long long ad = (unsigned long long)(dd < 0 ? -dd : dd);
+    m.d = m.d > ad ? m.d : ad;
+}
+
 // One step in Q5.27 for every grid (the tiled kernel covers the car grids it
-// supports): V_c + round_half_up(sum_d W_d (V_up,d - V_c) / 2^30), BRT min,
-// saturation (hj_q527_update).  alpha^max comes from the FP64 table, so the dt
-// sequence is the FP64 one.
+// supports).  alpha^max comes from the FP64 table, so the dt sequence is the
+// FP64 one.
 template <bool FAST32, bool TRACK>
 __global__ void __launch_bounds__(256) hj_step_q527_kernel(const int32_t *__restrict__ v0, int32_t *__restrict__ buf,
                                                             const HjCoef<double> *__restrict__ coef, int32_t *qw,
@@ -144,60 +276,33 @@ __global__ void __launch_bounds__(256) hj_step_q527_kernel(const int32_t *__rest
     int32_t *vout;
     hj_io_buffers<int32_t>(v0, buf, nint, n, vin, vout);
 
-    const unsigned int N1 = g.n1, N2 = g.n2, N3 = g.n3, N4 = g.n4;
-    const long long s3 = g.p4, s2 = (long long)N3 * g.p4, s1 = (long long)N2 * s2;
-    const unsigned long long ncell = (unsigned long long)N1 * N2 * N3 * N4;
-    const int tot = (int)N3 * g.p4;
+    const long long s2 = (long long)g.n3 * g.p4, s1 = (long long)g.n2 * s2;
+    const unsigned long long ncell = (unsigned long long)g.n1 * g.n2 * g.n3 * g.n4;
+    const int tot = g.n3 * g.p4;
     const int32_t w3 = qw[2 * tot];
     const int32_t *w4tab = qw + 2 * tot + HJ_QW_TAIL;  // theta weight per speed
-    unsigned long long am1 = 0ull, am2 = 0ull, dq = 0ull;
-
+    StepMax m;
     for (unsigned long long c = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; c < ncell;
          c += (unsigned long long)gridDim.x * blockDim.x) {
-        unsigned long long row;
-        int l, k, i, j;
-        if (FAST32) {
-            const uint32_t c32 = (uint32_t)c, row32 = fast_div(c32, dv.n4);
-            const uint32_t r2 = fast_div(row32, dv.n3);
-            const uint32_t i32 = fast_div(r2, dv.n2);
-            row = row32;
-            l = (int)(c32 - row32 * N4);
-            k = (int)(row32 - r2 * N3);
-            i = (int)i32;
-            j = (int)(r2 - i32 * N2);
-        } else {
-            row = c / N4;
-            l = (int)(c - row * N4);
-            const unsigned long long r2 = row / N3;
-            k = (int)(row - r2 * N3);
-            i = (int)(r2 / N2);
-            j = (int)(r2 - (unsigned long long)i * N2);
-        }
-        const long long o = (long long)row * g.p4 + l;
+        const Cell cl = cell_at<FAST32>(c, dv, g);
+        const long long o = cl.o;
         const int32_t vc = vin[o];
-        const QDiff dx = q_axis(vin, o, i, N1, s1, g.periodic & 1, vc);
-        const QDiff dy = q_axis(vin, o, j, N2, s2, (g.periodic >> 1) & 1, vc);
-        const QDiff dv3 = q_axis(vin, o, k, N3, s3, (g.periodic >> 2) & 1, vc);
-        const QDiff dv4 = q_axis(vin, o, l, N4, 1, (g.periodic >> 3) & 1, vc);
-        const int32_t w1 = qw[k * g.p4 + l], w2 = qw[tot + k * g.p4 + l];
-        const long long d1 = w1 >= 0 ? dx.dp : dx.dm;
-        const long long d2 = w2 >= 0 ? dy.dp : dy.dm;
-        const int32_t vn = hj_q527_update(vc, v0[o], d1, d2, q_upwind(dv3, g.mode3), q_upwind(dv4, g.mode4), abs(w1),
-                                          abs(w2), w3, w4tab[k]);
+        const QDiff dx = q_axis(vin, o, cl.i, g.n1, s1, g.periodic & 1, vc);
+        const QDiff dy = q_axis(vin, o, cl.j, g.n2, s2, (g.periodic >> 1) & 1, vc);
+        const QDiff dv3 = q_axis(vin, o, cl.k, g.n3, g.p4, (g.periodic >> 2) & 1, vc);
+        const QDiff dv4 = q_axis(vin, o, cl.l, g.n4, 1, (g.periodic >> 3) & 1, vc);
+        const int32_t vn = q_cell_value(vc, v0[o], dx, dy, dv3, dv4, qw[cl.k * g.p4 + cl.l],
+                                        qw[tot + cl.k * g.p4 + cl.l], w3, w4tab[cl.k], g.mode3, g.mode4);
         vout[o] = vn;
-        if constexpr (TRACK) {  // convergence mode: largest change of V
-            const long long dd = (long long)vn - vc;
-            const unsigned long long ad = (unsigned long long)(dd < 0 ? -dd : dd);
-            dq = dq > ad ? dq : ad;
-        }
-        const HjCoef<double> cf = coef[k * N4 + l];
+        if constexpr (TRACK) track_change(m, vn, vc);  // convergence mode: largest change of V
+        const HjCoef<double> cf = coef[cl.k * g.n4 + cl.l];
         const unsigned long long b1 = hj_abits(cf.a1), b2 = hj_abits(cf.a2);
-        am1 = am1 > b1 ? am1 : b1;
-        am2 = am2 > b2 ? am2 : b2;
+        m.a1 = m.a1 > b1 ? m.a1 : b1;
+        m.a2 = m.a2 > b2 ? m.a2 : b2;
     }
-    // the largest change in codes, as the FP64 value it stands for (exact)
-    hj_step_epilogue_scaled(st, g, am1, am2, hj_abits((double)dq * (1.0 / HJ_Q527_SCALE)), scratch, nullptr, qw, coef,
-                            k4tab);
+    unsigned long long a1, a2, d;
+    step_max_bits<int32_t>(m, a1, a2, d);
+    hj_step_epilogue_scaled(st, g, a1, a2, d, scratch, nullptr, qw, coef, k4tab);
 }
 
 template <typename T, bool FAST32, bool TRACK>
@@ -215,103 +320,556 @@ __global__ void __launch_bounds__(256) hj_step_generic_kernel(const T *__restric
     T *vout;
     hj_io_buffers<T>(v0, buf, nint, n, vin, vout);
 
-    const unsigned int N1 = g.n1, N2 = g.n2, N3 = g.n3, N4 = g.n4;
-    const long long s3 = g.p4, s2 = (long long)N3 * g.p4, s1 = (long long)N2 * s2;
-    const unsigned long long ncell = (unsigned long long)N1 * N2 * N3 * N4;
-    const T k3 = (T)g.k3;
+    const long long s2 = (long long)g.n3 * g.p4, s1 = (long long)g.n2 * s2;
+    const unsigned long long ncell = (unsigned long long)g.n1 * g.n2 * g.n3 * g.n4;
     // FP64: dt is folded into the per-(v, theta) table; the v weight needs it
     // once per thread
     const double k3dt = g.k3 * st->dt;
-    unsigned long long am1 = 0ull, am2 = 0ull, dbits = 0ull;
-    float am1f = 0.f, am2f = 0.f, dmf = 0.f;
-
+    StepMax m;
     for (unsigned long long c = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; c < ncell;
          c += (unsigned long long)gridDim.x * blockDim.x) {
-        unsigned long long row;
-        int l, k, i, j;
-        if (FAST32) {  // the grid has fewer than 2^32 cells
-            const uint32_t c32 = (uint32_t)c, row32 = fast_div(c32, dv.n4);
-            const uint32_t r2 = fast_div(row32, dv.n3);
-            const uint32_t i32 = fast_div(r2, dv.n2);
-            row = row32;
-            l = (int)(c32 - row32 * N4);
-            k = (int)(row32 - r2 * N3);
-            i = (int)i32;
-            j = (int)(r2 - i32 * N2);
-        } else {
-            row = c / N4;
-            l = (int)(c - row * N4);
-            const unsigned long long r2 = row / N3;
-            k = (int)(row - r2 * N3);
-            i = (int)(r2 / N2);
-            j = (int)(r2 - (unsigned long long)i * N2);
-        }
-        const long long o = (long long)row * g.p4 + l;
-
+        const Cell cl = cell_at<FAST32>(c, dv, g);
+        const long long o = cl.o;
         const T vc = vin[o];
-        const Neigh<T> nx = axis_neighbours<T>(vin, o, i, N1, s1, g.periodic & 1, vc);
-        const Neigh<T> ny = axis_neighbours<T>(vin, o, j, N2, s2, (g.periodic >> 1) & 1, vc);
-        const Neigh<T> nv = axis_neighbours<T>(vin, o, k, N3, s3, (g.periodic >> 2) & 1, vc);
-        const Neigh<T> nt = axis_neighbours<T>(vin, o, l, N4, 1, (g.periodic >> 3) & 1, vc);
-
-        const HjCoef<T> cf = coef[k * N4 + l];
-        const T u3 = upwind_value<T>(nv, g.mode3);
-        const T u4 = upwind_value<T>(nt, g.mode4);
+        const Neigh<T> nx = axis_neighbours<T>(vin, o, cl.i, g.n1, s1, g.periodic & 1, vc);
+        const Neigh<T> ny = axis_neighbours<T>(vin, o, cl.j, g.n2, s2, (g.periodic >> 1) & 1, vc);
+        const Neigh<T> nv = axis_neighbours<T>(vin, o, cl.k, g.n3, g.p4, (g.periodic >> 2) & 1, vc);
+        const Neigh<T> nt = axis_neighbours<T>(vin, o, cl.l, g.n4, 1, (g.periodic >> 3) & 1, vc);
+        const HjCoef<T> cf = coef[cl.k * g.n4 + cl.l];
         T vn;
-        if constexpr (sizeof(T) == 8) {
-            // V_new = w0 V_c + |w1| V_up1 + |w2| V_up2 + dt k3 V_up3 + dt k4 V_up4:
-            // 1 DMUL + 4 DFMA; signs and magnitudes by integer operations
-            const HjScaledCoef sc = scaled[k * N4 + l];
-            const T u1 = nonneg(sc.w1) ? nx.p : nx.m;
-            const T u2 = nonneg(sc.w2) ? ny.p : ny.m;
-            T r = sc.w0 * vc;
-            r = fma(mag(sc.w1), u1, r);
-            r = fma(mag(sc.w2), u2, r);
-            r = fma(k3dt, u3, r);
-            vn = fma(sc.w4, u4, r);
-        } else {
-            const T u1 = nonneg(cf.c1) ? nx.p : nx.m;
-            const T u2 = nonneg(cf.c2) ? ny.p : ny.m;
-            const T K1 = fabs(cf.c1), K2 = fabs(cf.c2);
-            T r = K1 * (u1 - vc);
-            r = fmaf(K2, u2 - vc, r);
-            r = fmaf(k3, u3 - vc, r);
-            r = fmaf(((const float2 *)k4tab)[k].x, u4 - vc, r);  // theta coefficient of this speed
-            vn = fmaf(dt, r, vc);
-        }
-        vn = hj_min(v0[o], vn);  // BRT min with the target (Algorithm 2)
+        if constexpr (sizeof(T) == 8)
+            vn = cell_value(vc, v0[o], nx, ny, nv, nt, scaled[cl.k * g.n4 + cl.l], k3dt, g.mode3, g.mode4);
+        else  // theta coefficient of this speed: k4tab[k].x
+            vn = cell_value(vc, v0[o], nx, ny, nv, nt, cf.c1, cf.c2, (T)g.k3, ((const float2 *)k4tab)[cl.k].x, dt,
+                            g.mode3, g.mode4);
         vout[o] = vn;
-        if constexpr (TRACK) {  // convergence mode: largest change of V (Algorithm 2's epsilon)
-            if constexpr (sizeof(T) == 8) {
-                const unsigned long long b = hj_abits(mag(vn - vc));
-                dbits = dbits > b ? dbits : b;
-            } else {
-                dmf = fmaxf(dmf, fabsf(vn - vc));
-            }
-        }
+        if constexpr (TRACK) track_change(m, vn, vc);  // convergence mode: Algorithm 2's epsilon
 
         // alpha_d^max: the largest |xdot_d| among the cells this thread updated
         // (FP64: integer max of the bit patterns; FP32: float max, widened once)
         if constexpr (sizeof(T) == 8) {
             const unsigned long long b1 = hj_abits((double)cf.a1), b2 = hj_abits((double)cf.a2);
-            am1 = am1 > b1 ? am1 : b1;
-            am2 = am2 > b2 ? am2 : b2;
+            m.a1 = m.a1 > b1 ? m.a1 : b1;
+            m.a2 = m.a2 > b2 ? m.a2 : b2;
         } else {
-            am1f = fmaxf(am1f, (float)cf.a1);
-            am2f = fmaxf(am2f, (float)cf.a2);
+            m.a1f = fmaxf(m.a1f, (float)cf.a1);
+            m.a2f = fmaxf(m.a2f, (float)cf.a2);
         }
     }
+    unsigned long long a1, a2, d;
+    step_max_bits<T>(m, a1, a2, d);
     if constexpr (sizeof(T) == 4) {
-        am1 = hj_abits((double)am1f);
-        am2 = hj_abits((double)am2f);
-        hj_step_epilogue(st, g, am1, am2, hj_abits((double)dmf), scratch);
+        hj_step_epilogue(st, g, a1, a2, d, scratch);
     } else {
-        hj_step_epilogue_scaled(st, g, am1, am2, dbits, scratch, scaled, nullptr, (const HjCoef<double> *)coef,
+        hj_step_epilogue_scaled(st, g, a1, a2, d, scratch, scaled, nullptr, (const HjCoef<double> *)coef,
                                 (const double *)k4tab);
     }
 }
 
+// ------------------------------------------------------------ resident form
+//
+// Up to ksteps steps of the time loop in one cooperative launch.  Each thread
+// updates theta quads (4 consecutive cells of a row: one 16- or 32-byte load
+// per neighbour row instead of four) with the per-cell functions above, so
+// the results equal the per-step kernels' bit for bit.  Per CTA, in shared
+// memory: the loop state and the per-(v, theta) coefficients of the current
+// dt (rebuilt by the CTA itself when dt changes).  alpha^max does not depend
+// on V, so every CTA reduces it once from the coefficient table (the same
+// maximum as over the grid's cells); each step then needs one grid barrier
+// (plus a max-reduction of the change of V in convergence mode), after which
+// every CTA runs the finaliser on its copy of the state (identical inputs,
+// identical dt).  The state goes back to global memory at the end; a barrier
+// that times out records HJ_ERR_TIMEOUT and ends the launch.
+
+constexpr int RES_THREADS = 256;
+constexpr int RES_MAX_PER_SM = 4;
+constexpr unsigned long long RES_WAIT_NS = 2000000000ull;  // 2 s per barrier wait
+constexpr size_t RES_MAX_TABLE = 160 * 1024;                // shared-memory coefficient table
+
+struct QuadDivisors {
+    FastDiv q4, n3, n2;
+};
+
+template <typename T>
+struct Quad {
+    T v[4];
+};
+
+// Four consecutive values (16-byte aligned) through L2 only: other CTAs
+// wrote them earlier in the same launch, and L1 is not coherent across SMs.
+__device__ __forceinline__ Quad<float> ld_quad(const float *p)
+{
+    const float4 a = __ldcg((const float4 *)p);
+    return {{a.x, a.y, a.z, a.w}};
+}
+__device__ __forceinline__ Quad<int32_t> ld_quad(const int32_t *p)
+{
+    const int4 a = __ldcg((const int4 *)p);
+    return {{a.x, a.y, a.z, a.w}};
+}
+__device__ __forceinline__ Quad<double> ld_quad(const double *p)
+{
+    const double2 a = __ldcg((const double2 *)p), b = __ldcg((const double2 *)p + 1);
+    return {{a.x, a.y, b.x, b.y}};
+}
+// V0 does not change during the launch: the read-only path.
+__device__ __forceinline__ Quad<float> ld_quad_ro(const float *p)
+{
+    const float4 a = __ldg((const float4 *)p);
+    return {{a.x, a.y, a.z, a.w}};
+}
+__device__ __forceinline__ Quad<int32_t> ld_quad_ro(const int32_t *p)
+{
+    const int4 a = __ldg((const int4 *)p);
+    return {{a.x, a.y, a.z, a.w}};
+}
+__device__ __forceinline__ Quad<double> ld_quad_ro(const double *p)
+{
+    const double2 a = __ldg((const double2 *)p), b = __ldg((const double2 *)p + 1);
+    return {{a.x, a.y, b.x, b.y}};
+}
+// The first nv values of a quad (nv < 4 only at the end of a row).
+__device__ __forceinline__ void st_quad(float *p, const Quad<float> &q, int nv)
+{
+    if (nv == 4) {
+        *(float4 *)p = make_float4(q.v[0], q.v[1], q.v[2], q.v[3]);
+    } else {
+#pragma unroll
+        for (int L = 0; L < 4; ++L)
+            if (L < nv) p[L] = q.v[L];
+    }
+}
+__device__ __forceinline__ void st_quad(int32_t *p, const Quad<int32_t> &q, int nv)
+{
+    if (nv == 4) {
+        *(int4 *)p = make_int4(q.v[0], q.v[1], q.v[2], q.v[3]);
+    } else {
+#pragma unroll
+        for (int L = 0; L < 4; ++L)
+            if (L < nv) p[L] = q.v[L];
+    }
+}
+__device__ __forceinline__ void st_quad(double *p, const Quad<double> &q, int nv)
+{
+    if (nv == 4) {
+        *(double2 *)p = make_double2(q.v[0], q.v[1]);
+        *((double2 *)p + 1) = make_double2(q.v[2], q.v[3]);
+    } else {
+#pragma unroll
+        for (int L = 0; L < 4; ++L)
+            if (L < nv) p[L] = q.v[L];
+    }
+}
+
+// The neighbour quads of a quad along one of the axes x, y, v (index i of N,
+// stride s): periodic wrap applied; a side that is an extrapolated ghost is
+// flagged and not loaded.
+template <typename T>
+struct QuadAxis {
+    Quad<T> m, p;
+    bool gm, gp;
+};
+
+template <typename T>
+__device__ __forceinline__ QuadAxis<T> quad_axis(const T *pc, int i, int N, long long s, bool periodic)
+{
+    QuadAxis<T> a;
+    a.gm = i == 0 && !periodic;
+    a.gp = i == N - 1 && !periodic;
+    a.m = {{T(0), T(0), T(0), T(0)}};
+    a.p = a.m;
+    if (i > 0) a.m = ld_quad(pc - s);
+    else if (periodic) a.m = ld_quad(pc + (long long)(N - 1) * s);
+    if (i < N - 1) a.p = ld_quad(pc + s);
+    else if (periodic) a.p = ld_quad(pc - (long long)(N - 1) * s);
+    return a;
+}
+
+// FP32 / FP64: replace an extrapolated side by the ghost of axis_neighbours,
+// V_{-1} = 2 V_0 - V_1 or V_N = 2 V_{N-1} - V_{N-2}, once per quad (the flags
+// are the same for its four lanes; N >= 3, so at most one side is a ghost).
+template <typename T>
+__device__ __forceinline__ void apply_ghosts(QuadAxis<T> &a, const Quad<T> &C)
+{
+    if (a.gm) {
+#pragma unroll
+        for (int L = 0; L < 4; ++L) a.m.v[L] = T(2) * C.v[L] - a.p.v[L];
+    }
+    if (a.gp) {
+#pragma unroll
+        for (int L = 0; L < 4; ++L) a.p.v[L] = T(2) * C.v[L] - a.m.v[L];
+    }
+}
+
+// Q5.27 upwind value on an axis whose neighbours are both grid values (the
+// side with the larger difference is the side with the larger value).
+__device__ __forceinline__ int32_t q_upwind_value(int32_t m, int32_t p, int mode)
+{
+    if (mode == HJ_AXIS_CONTROL) return p > m ? p : m;
+    return mode == HJ_AXIS_PLUS ? p : m;
+}
+
+// Q5.27: lane L's differences with the ghosts of q_axis.
+__device__ __forceinline__ QDiff lane_qdiff(int32_t mraw, int32_t praw, bool gm, bool gp, int32_t vc)
+{
+    QDiff d;
+    d.dm = gm ? (long long)vc - praw : (long long)mraw - vc;
+    d.dp = gp ? (long long)vc - mraw : (long long)praw - vc;
+    return d;
+}
+
+// Shared-memory bytes of a CTA's coefficient tables: per (v, theta) arrays
+// with the rows' pitch p4 (a quad's four entries are one 16- or 32-byte
+// load) and per-speed arrays.
+size_t resident_table_bytes(const hj_grid *g)
+{
+    const size_t n3 = (size_t)g->n[2], p4 = (size_t)g->p4;
+    size_t b;
+    if (g->prec == HJ_FP32) b = 8 * n3 * p4 + 4 * n3;
+    else if (g->prec == HJ_FP64) b = 24 * n3 * p4 + 8 * n3;
+    else b = 4 * (2 * n3 * p4 + HJ_QW_TAIL + n3);
+    return (b + 15) / 16 * 16;
+}
+
+// Four consecutive table entries from shared memory (16-byte aligned).
+__device__ __forceinline__ Quad<float> sm_quad(const float *p)
+{
+    const float4 a = *(const float4 *)p;
+    return {{a.x, a.y, a.z, a.w}};
+}
+__device__ __forceinline__ Quad<int32_t> sm_quad(const int32_t *p)
+{
+    const int4 a = *(const int4 *)p;
+    return {{a.x, a.y, a.z, a.w}};
+}
+__device__ __forceinline__ Quad<double> sm_quad(const double *p)
+{
+    const double2 a = *(const double2 *)p, b = *((const double2 *)p + 1);
+    return {{a.x, a.y, b.x, b.y}};
+}
+
+// FP64 tables for dt: w1, w2, w0 per (v, theta) (hj_scaled_entry), w4 per
+// speed; padding lanes 0.  All threads of the block call it.
+__device__ __forceinline__ void resident_table64(double *w1t, double *w2t, double *w0t, double *w4t,
+                                                 const HjCoef<double> *coef, const double *k4, int n3, int n4,
+                                                 int p4, double dt)
+{
+    for (int e = threadIdx.x; e < n3 * p4; e += blockDim.x) {
+        const int k = e / p4, l = e - k * p4;
+        HjScaledCoef o = {0.0, 0.0, 0.0, 0.0};
+        if (l < n4) o = hj_scaled_entry(coef[k * n4 + l], k4[k], dt);
+        w1t[e] = o.w1;
+        w2t[e] = o.w2;
+        w0t[e] = o.w0;
+    }
+    for (int k = threadIdx.x; k < n3; k += blockDim.x) w4t[k] = hj_scaled_entry(coef[k * n4], k4[k], dt).w4;
+}
+
+// CTAs per SM the register budget is set for (FP32 quads need fewer registers)
+template <typename T>
+constexpr int res_min_blocks()
+{
+    return std::is_same<T, float>::value ? 3 : 2;
+}
+
+template <typename T, bool TRACK>
+__global__ void __launch_bounds__(RES_THREADS, res_min_blocks<T>()) hj_step_resident_kernel(
+    const T *__restrict__ v0, T *buf, const void *__restrict__ coefp, const void *__restrict__ k4tab,
+    HjDevState *st, const HjGeom g, long long nint, const QuadDivisors dv, HjResidentSync *sync, long long ksteps,
+    unsigned long long limit_ns)
+{
+    constexpr bool Q = std::is_same<T, int32_t>::value;
+    constexpr bool F32 = std::is_same<T, float>::value;
+    extern __shared__ __align__(16) unsigned char res_smem[];
+    __shared__ HjDevState s;
+    __shared__ unsigned long long scratch[96];
+    __shared__ double s_alpha[2];
+    __shared__ int s_ok;
+
+    const int N1 = g.n1, N2 = g.n2, N3 = g.n3, N4 = g.n4, P4 = g.p4, tot = N3 * P4;
+    const int per = g.periodic;
+    // the CTA's coefficient tables: FP32 c1, c2 per (v, theta) and k4 per v;
+    // FP64 the dt-scaled w1, w2, w0 per (v, theta) and w4 per v; Q5.27 the
+    // fixed-point weights (qw layout)
+    float *c1t = (float *)res_smem, *c2t = c1t + tot, *k4s = c2t + tot;
+    double *w1t = (double *)res_smem, *w2t = w1t + tot, *w0t = w2t + tot, *w4t = w0t + tot;
+    int32_t *qtab = (int32_t *)res_smem;
+
+    if (threadIdx.x == 0) s = *st;
+    // alpha^max over the coefficient table (= over the grid's cells)
+    unsigned long long a1 = 0ull, a2 = 0ull, dz = 0ull;
+    if constexpr (F32) {
+        const HjCoef<float> *coef = (const HjCoef<float> *)coefp;
+        float m1 = 0.f, m2 = 0.f;
+        for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+            const int k = e / P4, l = e - k * P4;
+            float c1 = 0.f, c2 = 0.f;
+            if (l < N4) {
+                const HjCoef<float> c = coef[k * N4 + l];
+                c1 = c.c1;
+                c2 = c.c2;
+                m1 = fmaxf(m1, (float)c.a1);
+                m2 = fmaxf(m2, (float)c.a2);
+            }
+            c1t[e] = c1;
+            c2t[e] = c2;
+        }
+        for (int k = threadIdx.x; k < N3; k += blockDim.x) k4s[k] = ((const float2 *)k4tab)[k].x;
+        a1 = hj_abits((double)m1);
+        a2 = hj_abits((double)m2);
+    } else {
+        const HjCoef<double> *coef = (const HjCoef<double> *)coefp;
+        for (int e = threadIdx.x; e < N3 * N4; e += blockDim.x) {
+            const unsigned long long b1 = hj_abits(coef[e].a1), b2 = hj_abits(coef[e].a2);
+            a1 = a1 > b1 ? a1 : b1;
+            a2 = a2 > b2 ? a2 : b2;
+        }
+    }
+    hj_block_max3(a1, a2, dz, scratch);
+    if (threadIdx.x == 0) {
+        s_alpha[0] = __longlong_as_double((long long)a1);
+        s_alpha[1] = __longlong_as_double((long long)a2);
+    }
+    __syncthreads();
+    double table_dt = 0.0;  // dt the FP64 / Q5.27 table holds (0: not built)
+    if constexpr (!F32) {
+        if (!s.done) {
+            if constexpr (Q)
+                hj_rescale_qweights(qtab, (const HjCoef<double> *)coefp, N3, N4, P4, g.k3, (const double *)k4tab,
+                                    s.dt);
+            else
+                resident_table64(w1t, w2t, w0t, w4t, (const HjCoef<double> *)coefp, (const double *)k4tab, N3, N4,
+                                 P4, s.dt);
+            table_dt = s.dt;
+            __syncthreads();
+        }
+    }
+
+    const long long s2 = (long long)N3 * P4, s1 = (long long)N2 * s2;
+    const unsigned int Q4 = (unsigned int)(P4 / 4);
+    const unsigned long long nquad = (unsigned long long)N1 * N2 * N3 * Q4;
+    const unsigned long long q0 = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
+    const unsigned long long qstride = (unsigned long long)gridDim.x * blockDim.x;
+    const bool per4 = (per >> 3) & 1;
+    unsigned int barriers = 0;
+    bool aborted = false;
+    for (long long it = 0; it < ksteps && !s.done; ++it) {
+        const T *vin;
+        T *vout;
+        hj_io_buffers<T>(v0, buf, nint, s.n, vin, vout);
+        const T dt = (T)s.dt;
+        const double k3dt = g.k3 * s.dt;
+        StepMax m;
+        for (unsigned long long q = q0; q < nquad; q += qstride) {
+            const uint32_t q32 = (uint32_t)q, row = fast_div(q32, dv.q4);
+            const int l0 = 4 * (int)(q32 - row * Q4);
+            const uint32_t r2 = fast_div(row, dv.n3);
+            const uint32_t i32 = fast_div(r2, dv.n2);
+            const int k = (int)(row - r2 * N3), i = (int)i32, j = (int)(r2 - i32 * N2);
+            const T *rp = vin + (long long)row * P4;
+            const T *pc = rp + l0;
+            const Quad<T> C = ld_quad(pc);
+            QuadAxis<T> ax = quad_axis(pc, i, N1, s1, per & 1);
+            QuadAxis<T> ay = quad_axis(pc, j, N2, s2, (per >> 1) & 1);
+            QuadAxis<T> av = quad_axis(pc, k, N3, P4, (per >> 2) & 1);
+            // theta neighbours outside the quad: before lane 0 and after lane 3
+            // (wrapped on a periodic axis; unused at an extrapolated end)
+            const T em = l0 > 0 ? __ldcg(rp + l0 - 1) : (per4 ? __ldcg(rp + N4 - 1) : T(0));
+            const T ep = l0 + 4 < N4 ? __ldcg(rp + l0 + 4) : (per4 ? __ldcg(rp) : T(0));
+            const Quad<T> Z = ld_quad_ro(v0 + (pc - vin));
+            const int nv = N4 - l0 < 4 ? N4 - l0 : 4;  // lanes of the quad inside the row
+            // the value before lane 0 and after lane nv - 1 (for FP32 / FP64 the
+            // extrapolated ghosts at the row's ends are formed here, once)
+            T lo_m = em, hi_p = ep;
+            if constexpr (!Q) {
+                apply_ghosts(ax, C);
+                apply_ghosts(ay, C);
+                apply_ghosts(av, C);
+                if (l0 == 0 && !per4) lo_m = T(2) * C.v[0] - C.v[1];
+                if (l0 + nv == N4 && !per4) {  // lane nv - 1 holds l = N4 - 1
+                    const T cl = nv == 4 ? C.v[3] : (nv == 3 ? C.v[2] : (nv == 2 ? C.v[1] : C.v[0]));
+                    const T cm = nv == 4 ? C.v[2] : (nv == 3 ? C.v[1] : (nv == 2 ? C.v[0] : em));
+                    hi_p = T(2) * cl - cm;
+                }
+            }
+            // the quad's coefficients (one vector load per table)
+            const int e0 = k * P4 + l0;
+            Quad<float> cq1, cq2;
+            Quad<double> wq1, wq2, wq0;
+            Quad<int32_t> qq1, qq2;
+            if constexpr (F32) {
+                cq1 = sm_quad(c1t + e0);
+                cq2 = sm_quad(c2t + e0);
+            } else if constexpr (Q) {
+                qq1 = sm_quad(qtab + e0);
+                qq2 = sm_quad(qtab + tot + e0);
+            } else {
+                wq1 = sm_quad(w1t + e0);
+                wq2 = sm_quad(w2t + e0);
+                wq0 = sm_quad(w0t + e0);
+            }
+            // Q5.27: no extrapolated ghost among the quad's neighbours
+            const bool qinterior = !(ax.gm || ax.gp || ay.gm || ay.gp || av.gm || av.gp) &&
+                                   (per4 || (l0 > 0 && l0 + nv < N4));
+            Quad<T> out = C;
+#pragma unroll
+            for (int L = 0; L < 4; ++L) {
+                if (L >= nv) continue;
+                const int l = l0 + L;
+                const T vc = C.v[L];
+                const T mraw = L > 0 ? C.v[L > 0 ? L - 1 : 0] : lo_m;
+                const T praw = L < nv - 1 ? C.v[L < 3 ? L + 1 : 3] : hi_p;
+                T vn;
+                if constexpr (Q) {
+                    const int32_t w3 = qtab[2 * tot], w4 = qtab[2 * tot + HJ_QW_TAIL + k];
+                    if (qinterior) {  // every neighbour is a grid value: the int32 form (exact, same sum)
+                        const int32_t w1 = qq1.v[L], w2 = qq2.v[L], a1 = abs(w1), a2 = abs(w2);
+                        const int32_t u1 = w1 >= 0 ? ax.p.v[L] : ax.m.v[L];
+                        const int32_t u2 = w2 >= 0 ? ay.p.v[L] : ay.m.v[L];
+                        const int32_t u3 = q_upwind_value(av.m.v[L], av.p.v[L], g.mode3);
+                        const int32_t u4 = q_upwind_value(mraw, praw, g.mode4);
+                        vn = hj_q527_update_interior(vc, Z.v[L], u1, u2, u3, u4, a1, a2, w3, w4,
+                                                     -(a1 + a2 + w3 + w4));
+                    } else {
+                        const bool gm4 = l == 0 && !per4, gp4 = l == N4 - 1 && !per4;
+                        vn = q_cell_value(vc, Z.v[L], lane_qdiff(ax.m.v[L], ax.p.v[L], ax.gm, ax.gp, vc),
+                                          lane_qdiff(ay.m.v[L], ay.p.v[L], ay.gm, ay.gp, vc),
+                                          lane_qdiff(av.m.v[L], av.p.v[L], av.gm, av.gp, vc),
+                                          lane_qdiff(mraw, praw, gm4, gp4, vc), qq1.v[L], qq2.v[L], w3, w4, g.mode3,
+                                          g.mode4);
+                    }
+                } else {
+                    const Neigh<T> nx = {ax.m.v[L], ax.p.v[L]};
+                    const Neigh<T> ny = {ay.m.v[L], ay.p.v[L]};
+                    const Neigh<T> nvv = {av.m.v[L], av.p.v[L]};
+                    const Neigh<T> nt = {mraw, praw};
+                    if constexpr (F32) {
+                        vn = cell_value(vc, Z.v[L], nx, ny, nvv, nt, cq1.v[L], cq2.v[L], (float)g.k3, k4s[k], dt,
+                                        g.mode3, g.mode4);
+                    } else {
+                        const HjScaledCoef sc = {wq1.v[L], wq2.v[L], wq0.v[L], w4t[k]};
+                        vn = cell_value(vc, Z.v[L], nx, ny, nvv, nt, sc, k3dt, g.mode3, g.mode4);
+                    }
+                }
+                out.v[L] = vn;
+                if constexpr (TRACK) track_change(m, vn, vc);
+            }
+            st_quad(vout + (pc - vin), out, nv);
+        }
+        unsigned long long *slot = &sync->slot[(int)(it % 3)];
+        if constexpr (TRACK) {  // the step's largest change of V, grid-wide
+            unsigned long long u1 = 0ull, u2 = 0ull, d;
+            step_max_bits<T>(m, u1, u2, d);
+            hj_block_max3(u1, u2, d, scratch);
+            if (threadIdx.x == 0 && d) atomicMax(slot, d);
+        }
+        ++barriers;
+        if (!hj_grid_sync(&sync->count, gridDim.x * barriers, limit_ns, &s_ok)) {
+            aborted = true;
+            break;
+        }
+        if (threadIdx.x == 0) {
+            double eps = 0.0;
+            if constexpr (TRACK) {
+                eps = __longlong_as_double((long long)__ldcg(slot));
+                // the slot of step it - 1 is read by every CTA by now: clear it for step it + 2
+                if (blockIdx.x == 0) sync->slot[(int)((it + 2) % 3)] = 0ull;
+            }
+            hj_finalise_values(&s, g, s_alpha[0], s_alpha[1], eps);
+        }
+        __syncthreads();
+        if constexpr (!F32) {
+            if (!s.done && s.dt != table_dt) {  // after the first step and before the cut last one
+                if constexpr (Q)
+                    hj_rescale_qweights(qtab, (const HjCoef<double> *)coefp, N3, N4, P4, g.k3,
+                                        (const double *)k4tab, s.dt);
+                else
+                    resident_table64(w1t, w2t, w0t, w4t, (const HjCoef<double> *)coefp, (const double *)k4tab, N3,
+                                     N4, P4, s.dt);
+                table_dt = s.dt;
+                __syncthreads();
+            }
+        }
+    }
+    if (threadIdx.x != 0) return;
+    if (aborted) {
+        atomicCAS(&st->status, (int)HJ_OK, (int)HJ_ERR_TIMEOUT);
+        return;
+    }
+    if (blockIdx.x == 0) {  // every CTA holds the same state; the global tables were not touched
+        st->t = s.t;
+        st->dt = s.dt;
+        st->dt_prev = s.dt_prev;
+        st->n = s.n;
+        st->last = s.last;
+        st->done = s.done;
+        for (int d = 0; d < 4; ++d) st->alpha_prev[d] = s.alpha_prev[d];
+        st->converged = s.converged;
+        st->delta_last = s.delta_last;
+        if (s.status != HJ_OK) atomicCAS(&st->status, (int)HJ_OK, s.status);
+    }
+}
+
+template <typename T, bool TRACK>
+cudaError_t launch_resident(hj_grid *g, long long k)
+{
+    const void *fn = (const void *)hj_step_resident_kernel<T, TRACK>;
+    const size_t smem = resident_table_bytes(g);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int sms = 0, per_sm = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, RES_THREADS, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1 || sms < 1) return cudaErrorCooperativeLaunchTooLarge;
+    if (per_sm > RES_MAX_PER_SM) per_sm = RES_MAX_PER_SM;
+    const long long nquad = g->nint / 4;
+    const long long want = (nquad + RES_THREADS - 1) / RES_THREADS;
+    const long long cap = (long long)sms * per_sm;
+    const int blocks = (int)(want < cap ? (want > 0 ? want : 1) : cap);
+    QuadDivisors dv;
+    dv.q4 = make_fastdiv((uint32_t)(g->p4 / 4));
+    dv.n3 = make_fastdiv((uint32_t)g->n[2]);
+    dv.n2 = make_fastdiv((uint32_t)g->n[1]);
+    const T *v0 = (const T *)g->v0;
+    T *buf = (T *)g->buf;
+    const void *coef = g->coef;
+    const void *k4 = g->k4tab;
+    HjDevState *st = g->dstate;
+    HjGeom geom = g->geom;
+    long long nint = g->nint;
+    HjResidentSync *sync = g->rsync;
+    long long ksteps = k;
+    unsigned long long limit = RES_WAIT_NS;
+    void *args[] = {&v0, &buf, &coef, &k4, &st, &geom, &nint, &dv, &sync, &ksteps, &limit};
+    return cudaLaunchCooperativeKernel(fn, blocks, RES_THREADS, args, smem, g->stream);
+}
+
 }  // namespace
+
+bool hj_resident_supported(const hj_grid *g)
+{
+    int coop = 0;
+    if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, g->device) != cudaSuccess) return false;
+    return coop != 0 && g->nint < (1LL << 32) && resident_table_bytes(g) <= RES_MAX_TABLE;
+}
+
+cudaError_t hj_launch_step_resident(hj_grid *g, long long k)
+{
+    if (!g->rsync) {
+        cudaError_t e = cudaMalloc(&g->rsync, sizeof(HjResidentSync));
+        if (e != cudaSuccess) {
+            g->rsync = nullptr;
+            return e;
+        }
+        g->device_bytes += sizeof(HjResidentSync);
+    }
+    cudaError_t e = cudaMemsetAsync(g->rsync, 0, sizeof(HjResidentSync), g->stream);
+    if (e != cudaSuccess) return e;
+    if (g->prec == HJ_Q527) return g->track ? launch_resident<int32_t, true>(g, k) : launch_resident<int32_t, false>(g, k);
+    if (g->prec == HJ_FP64) return g->track ? launch_resident<double, true>(g, k) : launch_resident<double, false>(g, k);
+    return g->track ? launch_resident<float, true>(g, k) : launch_resident<float, false>(g, k);
+}
 
 cudaError_t hj_launch_step_generic(hj_grid *g)
 {

@@ -21,7 +21,7 @@ HJ_OK, HJ_ERR_INVALID_ARG, HJ_ERR_STATE, HJ_ERR_OOM, HJ_ERR_CUDA, HJ_ERR_UNSTABL
     HJ_ERR_UNSUPPORTED = range(8)
 HJ_FP64, HJ_FP32, HJ_Q527 = 0, 1, 2  # HJ_Q527: int32 codes, value = code * 2^-27
 HJ_DYN_CAR4D, HJ_DYN_CONST, HJ_DYN_CAR4D_STEER = 0, 1, 2
-HJ_KERNEL_AUTO, HJ_KERNEL_GENERIC, HJ_KERNEL_TILED = 0, 1, 2
+HJ_KERNEL_AUTO, HJ_KERNEL_GENERIC, HJ_KERNEL_TILED, HJ_KERNEL_RESIDENT = 0, 1, 2, 3
 PERIODIC_THETA = 0b1000
 
 
@@ -160,6 +160,8 @@ _SIGS = {
     "hj_query_device": (ctypes.c_int, [_VP, _VP, ctypes.c_int64, _VP, _VP, _VP]),
     "hj_wait_selftest": (ctypes.c_int, [ctypes.c_int64, ctypes.POINTER(ctypes.c_int32),
                                         ctypes.POINTER(ctypes.c_int64)]),
+    "hj_barrier_selftest": (ctypes.c_int, [ctypes.c_int64, ctypes.POINTER(ctypes.c_int32),
+                                           ctypes.POINTER(ctypes.c_int64)]),
     "hj_read_value": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.c_size_t]),
     "hj_read_value_device": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_size_t]),
     "hj_set_kernel": (ctypes.c_int, [_VP, ctypes.c_int]),
@@ -347,6 +349,14 @@ def hj_wait_selftest(limit_ns: int):
     st = ctypes.c_int32(0)
     waited = ctypes.c_int64(0)
     _check(lib.hj_wait_selftest(int(limit_ns), ctypes.byref(st), ctypes.byref(waited)))
+    return int(st.value), int(waited.value)
+
+
+def hj_barrier_selftest(limit_ns: int):
+    """(status, waited_ns) of the bounded grid-barrier self-test."""
+    st = ctypes.c_int32(0)
+    waited = ctypes.c_int64(0)
+    _check(lib.hj_barrier_selftest(int(limit_ns), ctypes.byref(st), ctypes.byref(waited)))
     return int(st.value), int(waited.value)
 
 

@@ -44,11 +44,12 @@ def solve(hj, w, prec, xy, kernel=None, T=None, shape=None):
 def test_broadcast_v0_same_bits_fp32_and_q527(hj, name):
     w = scenes.workload(name)
     for prec in (hj.HJ_FP32, hj.HJ_Q527):
-        a, sta, ia = solve(hj, w, prec, xy=False)
-        b, stb, ib = solve(hj, w, prec, xy=True)
-        assert ia.kernel == ib.kernel == hj.HJ_KERNEL_TILED
-        assert sta.steps == stb.steps
-        assert np.array_equal(a, b)
+        for kern in (hj.HJ_KERNEL_TILED, hj.HJ_KERNEL_RESIDENT):
+            a, sta, ia = solve(hj, w, prec, xy=False, kernel=kern)
+            b, stb, ib = solve(hj, w, prec, xy=True, kernel=kern)
+            assert ia.kernel == ib.kernel == kern
+            assert sta.steps == stb.steps
+            assert np.array_equal(a, b)
 
 
 @pytest.mark.parametrize("n", [(7, 9, 5, 6), (17, 13, 11, 26), (12, 10, 9, 33), (9, 21, 4, 8)])
@@ -67,12 +68,13 @@ def test_broadcast_v0_ragged_grids(hj, n):
 
 def test_broadcast_v0_tile_shapes_and_mode_switch(hj):
     w = scenes.workload("car4d_60x60x20x36")
-    ref, _, _ = solve(hj, w, hj.HJ_FP32, xy=False, T=0.6)
+    ref, _, _ = solve(hj, w, hj.HJ_FP32, xy=False, T=0.6, kernel=hj.HJ_KERNEL_TILED)
     for shape in ([3, 5, 20, 6], [8, 4, 60, 8], [6, 6, 13, 4]):
-        b, _, _ = solve(hj, w, hj.HJ_FP32, xy=True, T=0.6, shape=shape)
+        b, _, _ = solve(hj, w, hj.HJ_FP32, xy=True, T=0.6, shape=shape, kernel=hj.HJ_KERNEL_TILED)
         assert np.array_equal(b, ref), shape
     # switching back to a 4D V0 on the same grid leaves the broadcast mode
     with hj.Grid.for_workload(w, hj.HJ_FP32) as g:
+        g.set_kernel(hj.HJ_KERNEL_TILED)
         g.set_initial_value_xy(scenes.signed_distance_xy(w.grid, w.scene))
         assert g.info().v0_broadcast == 1
         g.set_initial_value(scenes.initial_value(w.grid, w.scene))
@@ -85,8 +87,9 @@ def test_broadcast_v0_device_field(hj):
     import torch
     w = scenes.workload("car4d_31x31x11x16")
     xy = scenes.signed_distance_xy(w.grid, w.scene)
-    a, _, _ = solve(hj, w, hj.HJ_FP32, xy=True)
+    a, _, _ = solve(hj, w, hj.HJ_FP32, xy=True, kernel=hj.HJ_KERNEL_TILED)
     with hj.Grid.for_workload(w, hj.HJ_FP32) as g:
+        g.set_kernel(hj.HJ_KERNEL_TILED)
         hj.hj_set_initial_value_xy_device(g.handle, torch.from_numpy(xy.ravel().copy()).cuda())
         assert g.info().v0_broadcast == 1
         g.solve_brt(w.T, w.cfl)

@@ -3,7 +3,9 @@ returns an error status the host reads, and the context stays usable.
 
 The self-test kernel waits, with the step kernels' own bounded mbarrier
 wait, on a barrier phase that nothing completes (a flag nothing sets); the
-wait gives up at its deadline and records HJ_ERR_TIMEOUT."""
+wait gives up at its deadline and records HJ_ERR_TIMEOUT.  The grid-barrier
+self-test does the same for the resident kernel's barrier: two CTAs wait for
+a third arrival that never comes."""
 import numpy as np
 import pytest
 
@@ -37,8 +39,27 @@ def test_bounded_wait_times_out_and_context_survives(hj):
     assert float(np.abs(V - Vo).max()) <= 1e-12
 
 
+def test_grid_barrier_times_out_and_context_survives(hj):
+    status, waited = hj.hj_barrier_selftest(50_000_000)  # 50 ms
+    assert status == hj.HJ_ERR_TIMEOUT
+    assert 50_000_000 <= waited < 1_000_000_000
+    # a resident solve on the same context completes and matches the oracle
+    w = scenes.workload("car4d_31x31x11x16")
+    V0 = scenes.initial_value(w.grid, w.scene)
+    with hj.Grid.for_workload(w, hj.HJ_FP64) as g:
+        g.set_kernel(hj.HJ_KERNEL_RESIDENT)
+        g.set_initial_value(V0)
+        st = g.solve_brt(w.T, w.cfl)
+        assert st.kernel == hj.HJ_KERNEL_RESIDENT
+        V = g.read_value()
+    P = oracle.Problem(w.grid.n, w.grid.lo, w.grid.hi, w.grid.periodic, oracle.DYN_CAR4D, (w.a_max, w.w_max))
+    Vo, _ = oracle.solve(P, V0, w.T, w.cfl, nthreads=oracle.max_threads())
+    assert float(np.abs(V - Vo).max()) <= 1e-12
+
+
 def test_selftest_limits(hj):
-    for bad in (0, 10, 3_000_000_000):
-        with pytest.raises(hj.HjError) as e:
-            hj.hj_wait_selftest(bad)
-        assert e.value.status == hj.HJ_ERR_INVALID_ARG
+    for fn in (hj.hj_wait_selftest, hj.hj_barrier_selftest):
+        for bad in (0, 10, 3_000_000_000):
+            with pytest.raises(hj.HjError) as e:
+                fn(bad)
+            assert e.value.status == hj.HJ_ERR_INVALID_ARG

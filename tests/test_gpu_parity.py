@@ -109,10 +109,11 @@ def test_small_ragged_grids(hj, n):
     w = scenes.custom_workload(n, n_circles=3, n_rects=1, T=0.4, seed=sum(n))
     V0 = scenes.initial_value(w.grid, w.scene)
     Vo, dts = oracle.solve(oracle_problem(w), V0, w.T, w.cfl)
-    V, st = gpu_solve(hj, w, V0, hj.HJ_FP64, hj.HJ_KERNEL_GENERIC)
-    assert st.steps == len(dts)
-    assert float(np.abs(V - Vo).max()) <= 1e-12
-    for k in (hj.HJ_KERNEL_GENERIC, hj.HJ_KERNEL_TILED):
+    for k in (hj.HJ_KERNEL_GENERIC, hj.HJ_KERNEL_RESIDENT):
+        V, st = gpu_solve(hj, w, V0, hj.HJ_FP64, k)
+        assert st.steps == len(dts) and st.dt_first == dts[0] and st.dt_last == dts[-1]
+        assert float(np.abs(V - Vo).max()) <= 1e-12
+    for k in (hj.HJ_KERNEL_GENERIC, hj.HJ_KERNEL_TILED, hj.HJ_KERNEL_RESIDENT):
         V, st = gpu_solve(hj, w, V0, hj.HJ_FP32, k)
         assert float(np.abs(V - Vo).max()) <= fp32_tol(V0)
         assert sign_flips(V, Vo) == 0
@@ -353,6 +354,7 @@ def test_every_tile_shape_gives_identical_bits(hj, name):
     shapes = [(0, 0, 0, 0), (8, 4, 0, 4), (3, 5, 7, 3), (1, 7, 5, 5), (5, 3, 0, 8), (2, 2, 4, 0)]
     for shape in shapes:
         with hj.Grid.for_workload(w, hj.HJ_FP32) as g:
+            g.set_kernel(hj.HJ_KERNEL_TILED)
             try:
                 g.set_tile_shape(shape)
             except hj.HjError as e:
@@ -371,6 +373,7 @@ def test_autotune_keeps_results_and_state(hj):
     w = scenes.workload("car4d_60x60x20x36")
     V0 = scenes.initial_value(w.grid, w.scene)
     with hj.Grid.for_workload(w, hj.HJ_FP32) as g:
+        g.set_kernel(hj.HJ_KERNEL_TILED)  # the kernel the autotuner shapes
         g.set_initial_value(V0)
         V_ref_st = g.solve_brt(w.T, w.cfl)
         V_ref = g.read_value()
@@ -384,8 +387,9 @@ def test_autotune_keeps_results_and_state(hj):
         assert 1 <= len(retimed) <= 3
         first = sorted(t.ms_per_step for t in tried)
         assert all(t.ms_per_step <= first[len(retimed) - 1] for t in retimed)
-        best = min(retimed, key=lambda t: t.ms_retimed)
-        assert list(info.tile) == list(best.shape)
+        # (two shapes can re-time equal: the kept one is one of the fastest)
+        kept = [t for t in retimed if list(t.shape) == list(info.tile)]
+        assert kept and kept[0].ms_retimed == min(t.ms_retimed for t in retimed)
         assert info.total_steps == 0 and info.t == 0.0
         st = g.solve_brt(w.T, w.cfl)
         assert st.steps == V_ref_st.steps

@@ -94,7 +94,9 @@ def test_q527_all_axes_periodic(hj):
     V0 = scenes.initial_value(w.grid, w.scene)
     Qo, dts = oracle.solve_q527(oracle_problem(w), V0, w.T, w.cfl)
     Q, st, _ = gpu_codes(hj, w, V0, hj.HJ_KERNEL_AUTO)
-    assert st.kernel == hj.HJ_KERNEL_GENERIC
+    assert st.kernel != hj.HJ_KERNEL_TILED  # the tiled kernel needs x, y, v not periodic
+    assert np.array_equal(Q, Qo)
+    Q, st, _ = gpu_codes(hj, w, V0, hj.HJ_KERNEL_GENERIC)
     assert np.array_equal(Q, Qo)
 
 
@@ -105,6 +107,7 @@ def test_q527_every_tile_shape_gives_identical_codes(hj):
     for shape in ([0, 0, 0, 0], [3, 5, 20, 6], [6, 4, 60, 8], [8, 2, 13, 5]):
         with hj.Grid(w.grid.n, w.grid.lo, w.grid.hi, w.grid.periodic, hj.HJ_Q527) as g:
             g.set_dynamics(hj.HJ_DYN_CAR4D, (w.a_max, w.w_max))
+            g.set_kernel(hj.HJ_KERNEL_TILED)
             g.set_tile_shape(shape)
             g.set_initial_value(V0)
             g.solve_brt(0.6, w.cfl)

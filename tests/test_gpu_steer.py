@@ -100,6 +100,7 @@ def test_steer_broadcast_v0_and_zero_angle(hj):
     z, _ = gpu(hj, w, hj.HJ_FP32, hj.HJ_KERNEL_TILED, params=(1.5, 0.0, 0.3), raw=True, T=0.7)
     with hj.Grid(w.grid.n, w.grid.lo, w.grid.hi, w.grid.periodic, hj.HJ_FP32) as g:
         g.set_dynamics(hj.HJ_DYN_CAR4D, (1.5, 0.0))
+        g.set_kernel(hj.HJ_KERNEL_TILED)
         g.set_initial_value(scenes.initial_value(w.grid, w.scene))
         g.solve_brt(0.7, w.cfl)
         assert np.array_equal(g.read_value().astype(np.float32), z)
