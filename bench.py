@@ -36,6 +36,7 @@ UNIT = "cell-updates/s"
 WORKLOAD = "car4d_128x128x64x96"
 STEER = (1.5, math.pi / 18, 0.3)  # Sec. IV-A: a in [-1.5, 1.5], delta in [-pi/18, pi/18], L = 0.3 m
 BYTES_PER_UPDATE = {"f32": 12, "f64": 24, "q527": 12, "f32_bcast": 8}
+KERNEL_NAMES = {1: "generic", 2: "tiled", 3: "resident"}
 PROFILE = os.path.join(ROOT, "profiles", "hj_step_tiled_car4d_128x128x64x96.md")
 KERNEL_SOURCES = ["hj_tiled_kernel.cuh", "hj_tiled_f32.cu", "hj_device.cuh", "hj_tma.cuh", "hj_scaled.cuh",
                   "hj_internal.h"]
@@ -224,6 +225,75 @@ def run_reference(args):
 
 # ------------------------------------------------------------------ our arm
 
+def run_small(hj, scenes, torch, stream):
+    """The small single-instance workloads and the paper's own experiment
+    (all fit in the 129 MB L2, so they are reported as cell-updates/s and
+    solve latency, not against HBM).  Each precision runs the kernel
+    HJ_KERNEL_AUTO picks (the resident kernel for FP32 and Q5.27 grids this
+    small) and, for comparison, the per-step kernel it replaces; every result
+    is held against the FP64 solve (which matches the oracle to 1e-12 in the
+    parity tests): max |difference| and BRT sign flips."""
+    def time_small(wl, prec, kernel, dyn, params, v0d, reps=5):
+        gs = hj.Grid(wl.grid.n, wl.grid.lo, wl.grid.hi, wl.grid.periodic, prec, stream.cuda_stream)
+        gs.set_dynamics(dyn, params)
+        gs.set_kernel(kernel)
+        o = torch.empty(v0d.numel(), dtype=torch.float64, device="cuda")
+        for _ in range(2):
+            hj.hj_set_initial_value_device(gs.handle, v0d)
+            gs.solve_brt(wl.T, wl.cfl)
+        ms_, loops = [], []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            hj.hj_set_initial_value_device(gs.handle, v0d)
+            st_ = gs.solve_brt(wl.T, wl.cfl)
+            e1.record(stream)
+            e1.synchronize()
+            ms_.append(e0.elapsed_time(e1))
+            loops.append(st_.loop_ms)
+        hj.hj_read_value_device(gs.handle, o)
+        kern = gs.info().kernel
+        gs.close()
+        med = float(np.median(ms_))
+        return {"ms_per_solve_median": med, "time_steps": st_.steps,
+                "us_per_step": 1e3 * float(np.median(loops)) / max(st_.steps, 1),
+                "value": v0d.numel() * st_.steps / (med * 1e-3), "unit": UNIT,
+                "kernel": KERNEL_NAMES.get(kern, kern)}, o
+
+    def vs_fp64(o, ref):
+        d = (o - ref).abs()
+        m = ref.abs() >= 1e-3
+        return float(d.max().item()), int((torch.sign(o[m]) != torch.sign(ref[m])).sum().item())
+
+    small = {}
+    cases = [(name, scenes.workload(name), hj.HJ_DYN_CAR4D, None)
+             for name in ("car4d_31x31x11x16", "car4d_60x60x20x36")]
+    cases.append(("paper_room_60x60x20x36_steer", scenes.paper_room(1), hj.HJ_DYN_CAR4D_STEER, scenes.PAPER_STEER))
+    for name, ws_, dyn, params in cases:
+        params = params or (ws_.a_max, ws_.w_max)
+        v0s = torch.from_numpy(scenes.initial_value(ws_.grid, ws_.scene)).to("cuda")
+        res = {}
+        ref = None
+        for pname, pr, per_step in (("f64", hj.HJ_FP64, None), ("f32", hj.HJ_FP32, hj.HJ_KERNEL_TILED),
+                                    ("q527", hj.HJ_Q527, hj.HJ_KERNEL_TILED)):
+            r, o = time_small(ws_, pr, hj.HJ_KERNEL_AUTO, dyn, params, v0s)
+            if ref is None:
+                ref = o
+            else:
+                r["max_abs_vs_fp64"], r["sign_flips_vs_fp64"] = vs_fp64(o, ref)
+            if per_step is not None:
+                rp, _ = time_small(ws_, pr, per_step, dyn, params, v0s)
+                r["per_step_kernel"] = {k: rp[k] for k in ("kernel", "ms_per_solve_median", "us_per_step")}
+            res[pname] = r
+        small[name] = {**res, "l2_resident": True, "T": ws_.T, "cfl": ws_.cfl}
+        if name.startswith("paper_room"):
+            # context only (another machine): Table II, the FPGA's 67 iterations
+            # on its 60x60x20x36 grid in fixed point, 0.176 s
+            small[name]["published_fpga_brt_ms"] = 176.0
+            small[name]["dynamics"] = "steering car, a in [-1.5, 1.5], delta in [-pi/18, pi/18], L = 0.3 m"
+    return small
+
+
 def run_ours(args):
     import torch
     world, rank, local = dist_env()
@@ -236,6 +306,11 @@ def run_ours(args):
     import __graft_entry__
     __graft_entry__.build()
     from paper_2012_04011_gb300 import hj, scenes
+
+    if args.small_only:
+        if rank == 0:
+            print(json.dumps({"small_configs": run_small(hj, scenes, torch, torch.cuda.current_stream())}))
+        return 0
 
     w = scenes.workload(WORKLOAD)
     V0 = scenes.initial_value(w.grid, w.scene)
@@ -363,48 +438,7 @@ def run_ours(args):
                               "frac": qbytes * mq / (qms * 1e-3) / 1e9 / measured_peaks()[0],
                               "bytes_per_query": qbytes}}
 
-    # the small single-instance workloads (both fit in the 129 MB L2, so they
-    # are reported as cell-updates/s only): FP32 (tiled) and FP64 solve times,
-    # and the FP32 result against the FP64 one (which matches the oracle to
-    # 1e-12 in the parity tests): max |difference| and BRT sign flips
-    small = None
-    if not args.no_small:
-        small = {}
-        for name in ("car4d_31x31x11x16", "car4d_60x60x20x36"):
-            ws_ = scenes.workload(name)
-            v0s = torch.from_numpy(scenes.initial_value(ws_.grid, ws_.scene)).to("cuda")
-            res = {}
-            outs = {}
-            for pname, pr in (("f32", hj.HJ_FP32), ("f64", hj.HJ_FP64)):
-                gs = hj.Grid(ws_.grid.n, ws_.grid.lo, ws_.grid.hi, ws_.grid.periodic, pr, stream.cuda_stream)
-                gs.set_dynamics(hj.HJ_DYN_CAR4D, (ws_.a_max, ws_.w_max))
-                o = torch.empty(v0s.numel(), dtype=torch.float64, device="cuda")
-                for _ in range(2):
-                    hj.hj_set_initial_value_device(gs.handle, v0s)
-                    gs.solve_brt(ws_.T, ws_.cfl)
-                ks, ms_, steps, loops = 5, [], 0, []
-                for _ in range(ks):
-                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                    e0.record(stream)
-                    hj.hj_set_initial_value_device(gs.handle, v0s)
-                    st_ = gs.solve_brt(ws_.T, ws_.cfl)
-                    e1.record(stream)
-                    e1.synchronize()
-                    ms_.append(e0.elapsed_time(e1))
-                    steps = st_.steps
-                    loops.append(st_.loop_ms)
-                hj.hj_read_value_device(gs.handle, o)
-                outs[pname] = o
-                res[pname] = {"ms_per_solve_median": float(np.median(ms_)), "time_steps": steps,
-                              "avg_step_ms": float(np.median(loops)) / max(steps, 1),
-                              "value": v0s.numel() * steps / (float(np.median(ms_)) * 1e-3), "unit": UNIT,
-                              "kernel": gs.info().kernel}
-                gs.close()
-            d = (outs["f32"] - outs["f64"]).abs()
-            m = outs["f64"].abs() >= 1e-3
-            flips = int((torch.sign(outs["f32"][m]) != torch.sign(outs["f64"][m])).sum().item())
-            small[name] = {**res, "l2_resident": True, "max_abs_fp32_vs_fp64": float(d.max().item()),
-                           "sign_flips_fp32_vs_fp64": flips}
+    small = None if args.no_small else run_small(hj, scenes, torch, stream)
 
     # batched solves: the 64-instance workload (uneven grids, own obstacles,
     # T = 1.5 s), V0 already on the device, one persistent kernel per batch step
@@ -637,6 +671,8 @@ def main():
     ap.add_argument("--no-steer", action="store_true")
     ap.add_argument("--no-query", action="store_true")
     ap.add_argument("--no-small", action="store_true")
+    ap.add_argument("--small-only", action="store_true",
+                    help="time only the small workloads and the paper's room (prints their JSON; not a bench line)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")

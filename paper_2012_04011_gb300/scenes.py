@@ -21,6 +21,13 @@ Domain for all: x, y in [-5, 5], v in [0, 4], theta in [-pi, pi) periodic;
 a_max = 1.5, w_max = 1.0, CFL 0.8.  Circles: centres uniform in [-4, 4]^2,
 radii uniform in [0.3, 1.0].  Rectangles: centres uniform in [-4, 4]^2,
 half-sizes uniform in [0.2, 1.0].
+
+The paper's own experiment (Sec. IV-A) is paper_room(): the 6 m x 4 m room
+on 60x60x20x36 points at 0.1 m, 0.067 m, 0.2 m/s and 2 pi/36 rad, the
+steering car (a in [-1.5, 1.5], delta in [-pi/18, pi/18], L = 0.3 m), cones
+inflated to R = 0.75 m, horizon 0.5 s in steps of the reported 0.007497 s
+(67 steps).  The cone placements are not published: seeded positions in the
+room stand in for its three environments.
 """
 from __future__ import annotations
 
@@ -153,6 +160,41 @@ def custom_workload(n, n_circles: int = 4, n_rects: int = 0, T: float = 0.5, see
     rng = np.random.default_rng(seed)
     return Workload(f"custom{tuple(n)}", GridSpec(tuple(int(x) for x in n)), random_scene(rng, n_circles, n_rects),
                     T, seed, a_max, w_max, cfl)
+
+
+# ---------------------------------------------------------------- the paper's room
+
+PAPER_ROOM_N = (60, 60, 20, 36)
+PAPER_ROOM_LO = (0.0, 0.0, 0.0, -math.pi)
+PAPER_ROOM_HI = (59 * 0.1, 59 * 0.067, 19 * 0.2, math.pi)  # x 6 m, y 4 m, v up to 3.8 m/s
+PAPER_STEER = (1.5, math.pi / 18, 0.3)                        # a_max, delta_max, L
+PAPER_CONE_R = 0.75
+PAPER_T = 0.5
+PAPER_DT = 0.007497  # the largest stable step the paper reports for its grid
+
+
+def paper_room_cfl(grid: GridSpec, steer=PAPER_STEER, dt: float = PAPER_DT) -> float:
+    """Courant number at which the CFL step of the grid is dt: the step is
+    CFL / sum_d alpha_d^max / dx_d with alpha^max = (v_max, v_max, a_max,
+    v_max tan(delta_max) / L) (cos and sin reach 1 on this theta grid)."""
+    h = [(grid.hi[d] - grid.lo[d]) / (grid.n[d] if (grid.periodic >> d) & 1 else grid.n[d] - 1) for d in range(4)]
+    vmax = max(abs(grid.lo[2]), abs(grid.hi[2]))
+    a_max, d_max, L = steer
+    s = vmax / h[0] + vmax / h[1] + a_max / h[2] + vmax * math.tan(d_max) / L / h[3]
+    return dt * s
+
+
+def paper_room(env: int = 1, n_cones: int = 3) -> Workload:
+    """The room of Sec. IV-A with n_cones seeded cones (env selects the
+    seed; the paper's three environments are not published)."""
+    rng = np.random.default_rng(SEED_BASE + 10 + env)
+    cones = np.empty((n_cones, 3))
+    cones[:, 0] = rng.uniform(0.8, PAPER_ROOM_HI[0] - 0.8, n_cones)
+    cones[:, 1] = rng.uniform(0.8, PAPER_ROOM_HI[1] - 0.8, n_cones)
+    cones[:, 2] = PAPER_CONE_R
+    grid = GridSpec(PAPER_ROOM_N, PAPER_ROOM_LO, PAPER_ROOM_HI)
+    return Workload(f"paper_room_env{env}", grid, Scene(cones), PAPER_T, SEED_BASE + 10 + env,
+                    a_max=PAPER_STEER[0], w_max=0.0, cfl=paper_room_cfl(grid))
 
 
 # ---------------------------------------------------------------- serving trace
