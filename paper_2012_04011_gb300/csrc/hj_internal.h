@@ -267,6 +267,26 @@ __device__ __forceinline__ int32_t hj_q527_update_interior(int32_t vc, int32_t v
     return (int32_t)(vn < -2147483648LL ? -2147483648LL : vn);
 }
 
+// The same interior update when the weights sum to at most 2^30 (nsum >=
+// -2^30; a Courant number below 1 guarantees it).  Then the increment
+// floor((sum W_d (u_d - V_c) + 2^29) / 2^30) lies between the smallest and
+// the largest of u_d - V_c and 0, so V_c plus it lies between the smallest and
+// the largest of V_c and the u_d: it fits int32, needs no saturation, and
+// the low 32 bits of the shifted sum, added to V_c modulo 2^32, are exact.
+__device__ __forceinline__ int32_t hj_q527_update_interior32(int32_t vc, int32_t v0, int32_t u1, int32_t u2,
+                                                             int32_t u3, int32_t u4, int32_t w1, int32_t w2,
+                                                             int32_t w3, int32_t w4, int32_t nsum)
+{
+    long long acc = (long long)nsum * vc + (1LL << 29);
+    acc += (long long)w1 * u1;
+    acc += (long long)w2 * u2;
+    acc += (long long)w3 * u3;
+    acc += (long long)w4 * u4;
+    const uint32_t inc = __funnelshift_r((uint32_t)acc, (uint32_t)((unsigned long long)acc >> 32), 30);
+    const int32_t vn = (int32_t)((uint32_t)vc + inc);
+    return vn < v0 ? vn : v0;
+}
+
 // One fixed-point cell update from the upwind differences d_d = V_up,d - V_c
 // (exact, int64) and the weight magnitudes: V_c + floor((sum W_d d_d + 2^29)
 // / 2^30), then the BRT min with V0 and saturation below.

@@ -728,8 +728,10 @@ __global__ void __launch_bounds__(RES_THREADS, res_min_blocks<T>()) hj_step_resi
                         const int32_t u2 = w2 >= 0 ? ay.p.v[L] : ay.m.v[L];
                         const int32_t u3 = q_upwind_value(av.m.v[L], av.p.v[L], g.mode3);
                         const int32_t u4 = q_upwind_value(mraw, praw, g.mode4);
-                        vn = hj_q527_update_interior(vc, Z.v[L], u1, u2, u3, u4, a1, a2, w3, w4,
-                                                     -(a1 + a2 + w3 + w4));
+                        const int32_t nsum = -(a1 + a2 + w3 + w4);
+                        vn = nsum >= -(1 << 30)
+                                 ? hj_q527_update_interior32(vc, Z.v[L], u1, u2, u3, u4, a1, a2, w3, w4, nsum)
+                                 : hj_q527_update_interior(vc, Z.v[L], u1, u2, u3, u4, a1, a2, w3, w4, nsum);
                     } else {
                         const bool gm4 = l == 0 && !per4, gp4 = l == N4 - 1 && !per4;
                         vn = q_cell_value(vc, Z.v[L], lane_qdiff(ax.m.v[L], ax.p.v[L], ax.gm, ax.gp, vc),

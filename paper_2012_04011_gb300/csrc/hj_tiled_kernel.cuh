@@ -324,6 +324,7 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
             // per lane: weight magnitudes, upwind sides and -(sum of the four weights)
             int32_t aw1[4], aw2[4], nsum[4];
             bool xpos[4], ypos[4];
+            bool wsmall = true;  // every lane's weights sum to at most 2^30 (hj_q527_update_interior32)
             if (FIXED) {
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
@@ -334,6 +335,7 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
                     aw1[e] = abs(w1);
                     aw2[e] = abs(w2);
                     nsum[e] = -(aw1[e] + aw2[e] + qw3 + qw4);
+                    wsmall = wsmall && nsum[e] >= -(1 << 30);
                 }
             }
             float v0next = 0.f;  // broadcast V0 of the next plane (loaded one plane ahead)
@@ -418,7 +420,7 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
                         // ghost flags: x-1 (x = 0), x+1 (x = N1-1), y-1, y+1, v-1, v+1
                         const bool gxm = s_prev < 0, gxp = x == N1 - 1;
                         const bool gym = gmask & 1u, gyp = gmask & 2u, gvm = gmask & 4u, gvp = gmask & 8u;
-                        if (!(gxm || gxp || gmask)) {  // interior row: int32 operands throughout
+                        if (!(gxm || gxp || gmask) && wsmall) {  // interior row: int32 operands throughout
 #pragma unroll
                             for (int e = 0; e < 4; ++e) {
                                 const int32_t vc = f4geti(cur, e);
@@ -428,15 +430,16 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
                                 const int32_t u1 = xpos[e] ? f4geti(nxt, e) : f4geti(prev, e);
                                 const int32_t u2 = ypos[e] ? f4geti(yp, e) : f4geti(ym, e);
                                 const int32_t u3 = max(f4geti(vp, e), f4geti(vm, e));
-                                int32_t vn = hj_q527_update_interior(vc, f4geti(v0c, e), u1, u2, u3, max(tp, tm),
-                                                                     aw1[e], aw2[e], qw3, qw4, nsum[e]);
+                                int32_t vn = hj_q527_update_interior32(vc, f4geti(v0c, e), u1, u2, u3, max(tp, tm),
+                                                                       aw1[e], aw2[e], qw3, qw4, nsum[e]);
                                 if (PADDED && e >= lreal) vn = 0;
                                 f4set(out, e, __int_as_float(vn));
                             }
                         } else {
                             // an extrapolated ghost on some axis (Sec. II-B): the ghost
                             // 2 V_c - V_o enters as -W on V_o and +2W on V_c, so the
-                            // operands stay int32 and the sum stays exact
+                            // operands stay int32 and the sum stays exact (this form
+                            // also takes interior rows whose weights sum above 2^30)
 #pragma unroll
                             for (int e = 0; e < 4; ++e) {
                                 const int32_t vc = f4geti(cur, e);
