@@ -455,7 +455,7 @@ struct hj_batch {
     BatchCtl *d_ctl = nullptr;
     CUtensorMap *d_maps = nullptr;
     int nconsumer_req = 0;  // 0: automatic
-    int xc_mode = 0;        // 0: one chunk per column, k > 0: about n1 / k planes per chunk
+    int xc_mode = 0;        // 0: automatic, k > 0: about n1 / k planes per chunk
     BatchParams bp = {0, 0, 0};
     int ctas = 0;
     int nitems = 0;
@@ -573,11 +573,28 @@ hj_status rebuild(hj_batch *b)
     std::vector<BatchItem> items;
     int stage_bytes = 128;
     int max_cons = 32;
+    // x chunks: the requested count, or automatically whole columns while the
+    // batch has at least one (y, v) column per SM; with fewer (a lone request
+    // of the serving loop) enough chunks to give every SM an item, since a
+    // column's planes are streamed one after another by one CTA
+    long long columns = 0;
+    int min_n1 = 1 << 30;
     for (int i = 0; i < b->max_slots; ++i) {
         SlotHost &s = b->slots[i];
         if (!s.used) continue;
         choose_tile(s, nc, &s.ty, &s.tv);
-        const int nchunk = b->xc_mode > 0 ? b->xc_mode : 1;
+        columns += (long long)((s.n[1] + s.ty - 1) / s.ty) * ((s.n[2] + s.tv - 1) / s.tv);
+        if (s.n[0] < min_n1) min_n1 = s.n[0];
+    }
+    int nchunk = b->xc_mode > 0 ? b->xc_mode : 1;
+    if (b->xc_mode == 0 && columns > 0 && columns < b->sms) {
+        nchunk = (int)((b->sms + columns - 1) / columns);
+        const int most = min_n1 / 4 > 1 ? min_n1 / 4 : 1;  // chunks of at least 4 planes
+        if (nchunk > most) nchunk = most;
+    }
+    for (int i = 0; i < b->max_slots; ++i) {
+        SlotHost &s = b->slots[i];
+        if (!s.used) continue;
         s.xc = (s.n[0] + nchunk - 1) / nchunk;
         if (s.xc < 4) s.xc = s.n[0] < 4 ? s.n[0] : 4;
         BatchInst &I = insts[i];

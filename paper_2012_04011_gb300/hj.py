@@ -637,7 +637,7 @@ REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = range(4)
 class Server:
     """Owns one hj_server (continuous batching of BRT re-solve requests)."""
 
-    def __init__(self, max_slots=64, memory_budget=0, steps_per_tick=8, cuda_stream=None):
+    def __init__(self, max_slots=64, memory_budget=0, steps_per_tick=32, cuda_stream=None):
         out = _VP()
         stream = None if cuda_stream is None else ctypes.c_void_p(int(cuda_stream))
         _check(lib.hj_server_create(int(max_slots), int(memory_budget), int(steps_per_tick), stream,

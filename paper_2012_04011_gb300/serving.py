@@ -28,7 +28,7 @@ def _percentiles(lat_ms):
             "mean": float(a.mean())}
 
 
-def run_server(trace, max_slots: int = 64, memory_budget: int = 0, steps_per_tick: int = 8, fetch: bool = True,
+def run_server(trace, max_slots: int = 64, memory_budget: int = 0, steps_per_tick: int = 32, fetch: bool = True,
                cuda_stream=None, keep_results: bool = False):
     """Replays the trace through an hj.Server.  Returns stats (and results by
     request index when keep_results)."""
