@@ -206,3 +206,44 @@ def test_resident_zero_steps_and_done_grid(hj):
         assert np.array_equal(g.read_value(), V)
         st3 = g.advance_brt(w.T + 0.5, w.cfl, 0)
         assert st3.steps == 0 and np.array_equal(g.read_value(), V)
+
+
+def test_resident_solves_on_two_streams_at_once(hj):
+    """Two grids whose resident launches overlap on two streams (each launch
+    sized to fill the GPU): each cooperative launch waits until all its CTAs
+    can be resident, so neither barrier runs out (HJ_ERR_TIMEOUT otherwise) and
+    each result equals the same solve alone."""
+    import threading
+
+    import torch
+    runs = [("fp32", scenes.workload("car4d_60x60x20x36")), ("q527", scenes.workload("car4d_31x31x11x16"))]
+    solo = {}
+    for prec, w in runs:
+        solo[prec], _ = run(hj, w, prec, hj.HJ_KERNEL_RESIDENT, scenes.initial_value(w.grid, w.scene))
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    out, errors = {}, []
+
+    def worker(idx):
+        prec, w = runs[idx]
+        try:
+            V0 = scenes.initial_value(w.grid, w.scene)
+            with hj.Grid(w.grid.n, w.grid.lo, w.grid.hi, w.grid.periodic, prec_code(hj, prec),
+                         streams[idx].cuda_stream) as g:
+                g.set_dynamics(hj.HJ_DYN_CAR4D, (w.a_max, w.w_max))
+                g.set_kernel(hj.HJ_KERNEL_RESIDENT)
+                g.set_initial_value(V0)
+                for _ in range(3):
+                    g.set_initial_value(V0)
+                    g.solve_brt(w.T, w.cfl)
+                out[prec] = read_raw(hj, g, prec)
+        except Exception as e:  # reported below
+            errors.append(repr(e))
+
+    threads = [threading.Thread(target=worker, args=(i,)) for i in range(2)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    assert not errors, errors
+    for prec, _ in runs:
+        assert np.array_equal(out[prec], solo[prec]), prec
