@@ -742,6 +742,21 @@ static hj_status finish_ingest(hj_grid *g)
     return HJ_OK;
 }
 
+// Device address of a host buffer the grid's device can reach directly
+// (pinned host memory, mapped into the device's address space), else NULL.
+// The ingest and readback kernels then read or write it over the host link
+// in one pass instead of staging it through device memory with a copy.
+static void *device_view(const hj_grid *g, const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type != cudaMemoryTypeHost || !a.devicePointer) return nullptr;
+    return a.device == g->device ? a.devicePointer : nullptr;
+}
+
 hj_status hj_set_initial_value(hj_grid *g, const double *v0, size_t count)
 {
     g_err[0] = 0;
@@ -752,9 +767,13 @@ hj_status hj_set_initial_value(hj_grid *g, const double *v0, size_t count)
         return set_err(HJ_ERR_INVALID_ARG, "count %zu != N1*N2*N3*N4 = %lld", count, g->ncell);
     if ((s = activate(g)) != HJ_OK) return s;
     if ((s = reset_state(g)) != HJ_OK) return s;
-    // stage the dense FP64 array in the ping-pong region (2 * nint * esize >= ncell * 8 bytes)
-    double *staging = (double *)g->buf;
-    HJ_CUDA(cudaMemcpyAsync(staging, v0, sizeof(double) * (size_t)g->ncell, cudaMemcpyHostToDevice, g->stream));
+    // pinned host memory: the ingest kernel reads it directly; otherwise stage
+    // the dense FP64 array in the ping-pong region (2 * nint * esize >= ncell * 8 bytes)
+    const double *staging = (const double *)device_view(g, v0);
+    if (!staging) {
+        staging = (const double *)g->buf;
+        HJ_CUDA(cudaMemcpyAsync(g->buf, v0, sizeof(double) * (size_t)g->ncell, cudaMemcpyHostToDevice, g->stream));
+    }
     long long nrows = (long long)g->n[0] * g->n[1] * g->n[2];
     int *flag = &g->dstate->nonfinite;
     int blocks = grid_blocks(g->nint, 256);
@@ -955,6 +974,18 @@ hj_status hj_read_value(const hj_grid *gc, double *out, size_t count)
     if ((s = pull_state(g)) != HJ_OK) return s;
     const long long n = g->hstate->n;
     const void *src = hj_value_ptr(g, n);
+    const long long nrows = (long long)g->n[0] * g->n[1] * g->n[2];
+    // pinned host memory: the readback kernel writes it directly, in one pass
+    if (double *dv = (double *)device_view(g, out)) {
+        with_elem(g->prec, [&](auto e) {
+            using T = decltype(e);
+            readback_kernel<T, double><<<grid_blocks(nrows * g->n[3], 256), 256, 0, g->stream>>>(
+                (const T *)src, dv, g->n[3], g->p4, 0, nrows);
+        });
+        HJ_CUDA(cudaGetLastError());
+        HJ_CUDA(cudaStreamSynchronize(g->stream));
+        return HJ_OK;
+    }
     if (g->prec == HJ_FP64 && g->p4 == g->n[3]) {
         HJ_CUDA(cudaMemcpyAsync(out, src, sizeof(double) * (size_t)g->ncell, cudaMemcpyDeviceToHost, g->stream));
         HJ_CUDA(cudaStreamSynchronize(g->stream));
@@ -970,7 +1001,6 @@ hj_status hj_read_value(const hj_grid *gc, double *out, size_t count)
         free_buf = (char *)g->buf + (size_t)(n & 1) * g->nint * g->esize;  // the buffer the next step writes
         free_bytes = (size_t)g->nint * g->esize;
     }
-    const long long nrows = (long long)g->n[0] * g->n[1] * g->n[2];
     long long rows_per_chunk = (long long)(free_bytes / (sizeof(double) * (size_t)g->n[3]));
     if (rows_per_chunk < 1) return set_err(HJ_ERR_STATE, "no room to stage the readback");
     for (long long r0 = 0; r0 < nrows; r0 += rows_per_chunk) {

@@ -256,6 +256,37 @@ def test_device_ingest_and_readback(hj):
             assert np.array_equal(g.read_value(), Vh)
 
 
+def test_pinned_host_buffers_equal_pageable(hj):
+    """V0 from pinned host memory (read by the ingest kernel over the host
+    link) and V into pinned host memory (written by the readback kernel) give
+    the same bytes as the staged copies of pageable buffers."""
+    import torch
+    w = scenes.workload("car4d_31x31x11x16")
+    V0 = scenes.initial_value(w.grid, w.scene)
+    V0p = torch.from_numpy(V0.copy()).pin_memory().numpy()
+    for prec in (hj.HJ_FP64, hj.HJ_FP32, hj.HJ_Q527):
+        outs = []
+        for src in (V0, V0p):
+            with hj.Grid(w.grid.n, w.grid.lo, w.grid.hi, w.grid.periodic, prec) as g:
+                g.set_dynamics(hj.HJ_DYN_CAR4D, (w.a_max, w.w_max))
+                g.set_initial_value(src)
+                assert np.array_equal(g.read_value(), g.read_value(torch.empty(V0.shape, dtype=torch.float64)
+                                                                  .pin_memory().numpy()))
+                g.solve_brt(w.T, w.cfl)
+                pinned = torch.empty(V0.shape, dtype=torch.float64).pin_memory().numpy()
+                g.read_value(pinned)
+                assert np.array_equal(pinned, g.read_value())
+                outs.append(pinned.copy())
+        assert np.array_equal(outs[0], outs[1]), prec
+    # a NaN in pinned V0 is rejected as in pageable memory
+    bad = torch.from_numpy(V0.copy()).pin_memory().numpy()
+    bad[1, 2, 3, 4] = np.nan
+    with hj.Grid.for_workload(w, hj.HJ_FP32) as g:
+        with pytest.raises(hj.HjError) as e:
+            g.set_initial_value(bad)
+        assert e.value.status == hj.HJ_ERR_INVALID_ARG
+
+
 def test_errors_on_device(hj):
     w = scenes.workload("car4d_31x31x11x16")
     V0 = scenes.initial_value(w.grid, w.scene)
