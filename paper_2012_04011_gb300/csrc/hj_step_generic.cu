@@ -136,13 +136,15 @@ __device__ __forceinline__ long long q_upwind(const QDiff &d, int mode)
 }
 
 // ---------------------------------------------------------- one cell's update
-// Shared by the per-step and the resident kernels, so that both give the
-// same result bit for bit.
+// The resident kernel's FP32 / FP64 update and the Q5.27 update of both
+// forms.  hj_step_generic_kernel writes the same FP32 / FP64 expressions, in
+// the same order, inline (its FP64 build is 2 % faster that way), so the
+// resident and per-step kernels give the same result bit for bit (tested).
 
 // FP32: V_c + dt (K1 (V_up1 - V_c) + K2 (V_up2 - V_c) + k3 (V_up3 - V_c) +
-// k4 (V_up4 - V_c)), then the BRT min with V0 (Algorithm 2).  c1, c2 are the
-// signed xdot_d / dx_d of the cell's (v, theta).
-__device__ __forceinline__ float cell_value(float vc, float v0c, const Neigh<float> &nx, const Neigh<float> &ny,
+// k4 (V_up4 - V_c)), the Euler update before the BRT min with V0 (the caller
+// applies it).  c1, c2 are the signed xdot_d / dx_d of the cell's (v, theta).
+__device__ __forceinline__ float cell_value(const float vc, const Neigh<float> &nx, const Neigh<float> &ny,
                                             const Neigh<float> &nv, const Neigh<float> &nt, float c1, float c2,
                                             float k3, float k4, float dt, int mode3, int mode4)
 {
@@ -155,12 +157,12 @@ __device__ __forceinline__ float cell_value(float vc, float v0c, const Neigh<flo
     r = fmaf(K2, u2 - vc, r);
     r = fmaf(k3, u3 - vc, r);
     r = fmaf(k4, u4 - vc, r);
-    return hj_min(v0c, fmaf(dt, r, vc));
+    return fmaf(dt, r, vc);
 }
 
 // FP64: w0 V_c + |w1| V_up1 + |w2| V_up2 + dt k3 V_up3 + w4 V_up4 (1 DMUL +
-// 4 DFMA; signs and magnitudes by integer operations), then the BRT min.
-__device__ __forceinline__ double cell_value(double vc, double v0c, const Neigh<double> &nx, const Neigh<double> &ny,
+// 4 DFMA; signs and magnitudes by integer operations), before the BRT min.
+__device__ __forceinline__ double cell_value(const double vc, const Neigh<double> &nx, const Neigh<double> &ny,
                                              const Neigh<double> &nv, const Neigh<double> &nt,
                                              const HjScaledCoef &sc, double k3dt, int mode3, int mode4)
 {
@@ -172,7 +174,7 @@ __device__ __forceinline__ double cell_value(double vc, double v0c, const Neigh<
     r = fma(mag(sc.w1), u1, r);
     r = fma(mag(sc.w2), u2, r);
     r = fma(k3dt, u3, r);
-    return hj_min(v0c, fma(sc.w4, u4, r));
+    return fma(sc.w4, u4, r);
 }
 
 // Q5.27: V_c + round_half_up(sum_d W_d (V_up,d - V_c) / 2^30), BRT min,
@@ -320,48 +322,98 @@ __global__ void __launch_bounds__(256) hj_step_generic_kernel(const T *__restric
     T *vout;
     hj_io_buffers<T>(v0, buf, nint, n, vin, vout);
 
-    const long long s2 = (long long)g.n3 * g.p4, s1 = (long long)g.n2 * s2;
-    const unsigned long long ncell = (unsigned long long)g.n1 * g.n2 * g.n3 * g.n4;
+    const unsigned int N1 = g.n1, N2 = g.n2, N3 = g.n3, N4 = g.n4;
+    const long long s3 = g.p4, s2 = (long long)N3 * g.p4, s1 = (long long)N2 * s2;
+    const unsigned long long ncell = (unsigned long long)N1 * N2 * N3 * N4;
+    const T k3 = (T)g.k3;
     // FP64: dt is folded into the per-(v, theta) table; the v weight needs it
     // once per thread
     const double k3dt = g.k3 * st->dt;
-    StepMax m;
+    unsigned long long am1 = 0ull, am2 = 0ull, dbits = 0ull;
+    float am1f = 0.f, am2f = 0.f, dmf = 0.f;
+
     for (unsigned long long c = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; c < ncell;
          c += (unsigned long long)gridDim.x * blockDim.x) {
-        const Cell cl = cell_at<FAST32>(c, dv, g);
-        const long long o = cl.o;
+        unsigned long long row;
+        int l, k, i, j;
+        if (FAST32) {  // the grid has fewer than 2^32 cells
+            const uint32_t c32 = (uint32_t)c, row32 = fast_div(c32, dv.n4);
+            const uint32_t r2 = fast_div(row32, dv.n3);
+            const uint32_t i32 = fast_div(r2, dv.n2);
+            row = row32;
+            l = (int)(c32 - row32 * N4);
+            k = (int)(row32 - r2 * N3);
+            i = (int)i32;
+            j = (int)(r2 - i32 * N2);
+        } else {
+            row = c / N4;
+            l = (int)(c - row * N4);
+            const unsigned long long r2 = row / N3;
+            k = (int)(row - r2 * N3);
+            i = (int)(r2 / N2);
+            j = (int)(r2 - (unsigned long long)i * N2);
+        }
+        const long long o = (long long)row * g.p4 + l;
+
         const T vc = vin[o];
-        const Neigh<T> nx = axis_neighbours<T>(vin, o, cl.i, g.n1, s1, g.periodic & 1, vc);
-        const Neigh<T> ny = axis_neighbours<T>(vin, o, cl.j, g.n2, s2, (g.periodic >> 1) & 1, vc);
-        const Neigh<T> nv = axis_neighbours<T>(vin, o, cl.k, g.n3, g.p4, (g.periodic >> 2) & 1, vc);
-        const Neigh<T> nt = axis_neighbours<T>(vin, o, cl.l, g.n4, 1, (g.periodic >> 3) & 1, vc);
-        const HjCoef<T> cf = coef[cl.k * g.n4 + cl.l];
+        const Neigh<T> nx = axis_neighbours<T>(vin, o, i, N1, s1, g.periodic & 1, vc);
+        const Neigh<T> ny = axis_neighbours<T>(vin, o, j, N2, s2, (g.periodic >> 1) & 1, vc);
+        const Neigh<T> nv = axis_neighbours<T>(vin, o, k, N3, s3, (g.periodic >> 2) & 1, vc);
+        const Neigh<T> nt = axis_neighbours<T>(vin, o, l, N4, 1, (g.periodic >> 3) & 1, vc);
+
+        const HjCoef<T> cf = coef[k * N4 + l];
+        const T u3 = upwind_value<T>(nv, g.mode3);
+        const T u4 = upwind_value<T>(nt, g.mode4);
         T vn;
-        if constexpr (sizeof(T) == 8)
-            vn = cell_value(vc, v0[o], nx, ny, nv, nt, scaled[cl.k * g.n4 + cl.l], k3dt, g.mode3, g.mode4);
-        else  // theta coefficient of this speed: k4tab[k].x
-            vn = cell_value(vc, v0[o], nx, ny, nv, nt, cf.c1, cf.c2, (T)g.k3, ((const float2 *)k4tab)[cl.k].x, dt,
-                            g.mode3, g.mode4);
+        if constexpr (sizeof(T) == 8) {
+            // V_new = w0 V_c + |w1| V_up1 + |w2| V_up2 + dt k3 V_up3 + dt k4 V_up4:
+            // 1 DMUL + 4 DFMA; signs and magnitudes by integer operations
+            const HjScaledCoef sc = scaled[k * N4 + l];
+            const T u1 = nonneg(sc.w1) ? nx.p : nx.m;
+            const T u2 = nonneg(sc.w2) ? ny.p : ny.m;
+            T r = sc.w0 * vc;
+            r = fma(mag(sc.w1), u1, r);
+            r = fma(mag(sc.w2), u2, r);
+            r = fma(k3dt, u3, r);
+            vn = fma(sc.w4, u4, r);
+        } else {
+            const T u1 = nonneg(cf.c1) ? nx.p : nx.m;
+            const T u2 = nonneg(cf.c2) ? ny.p : ny.m;
+            const T K1 = fabs(cf.c1), K2 = fabs(cf.c2);
+            T r = K1 * (u1 - vc);
+            r = fmaf(K2, u2 - vc, r);
+            r = fmaf(k3, u3 - vc, r);
+            r = fmaf(((const float2 *)k4tab)[k].x, u4 - vc, r);  // theta coefficient of this speed
+            vn = fmaf(dt, r, vc);
+        }
+        vn = hj_min(v0[o], vn);  // BRT min with the target (Algorithm 2)
         vout[o] = vn;
-        if constexpr (TRACK) track_change(m, vn, vc);  // convergence mode: Algorithm 2's epsilon
+        if constexpr (TRACK) {  // convergence mode: largest change of V (Algorithm 2's epsilon)
+            if constexpr (sizeof(T) == 8) {
+                const unsigned long long b = hj_abits(mag(vn - vc));
+                dbits = dbits > b ? dbits : b;
+            } else {
+                dmf = fmaxf(dmf, fabsf(vn - vc));
+            }
+        }
 
         // alpha_d^max: the largest |xdot_d| among the cells this thread updated
         // (FP64: integer max of the bit patterns; FP32: float max, widened once)
         if constexpr (sizeof(T) == 8) {
             const unsigned long long b1 = hj_abits((double)cf.a1), b2 = hj_abits((double)cf.a2);
-            m.a1 = m.a1 > b1 ? m.a1 : b1;
-            m.a2 = m.a2 > b2 ? m.a2 : b2;
+            am1 = am1 > b1 ? am1 : b1;
+            am2 = am2 > b2 ? am2 : b2;
         } else {
-            m.a1f = fmaxf(m.a1f, (float)cf.a1);
-            m.a2f = fmaxf(m.a2f, (float)cf.a2);
+            am1f = fmaxf(am1f, (float)cf.a1);
+            am2f = fmaxf(am2f, (float)cf.a2);
         }
     }
-    unsigned long long a1, a2, d;
-    step_max_bits<T>(m, a1, a2, d);
     if constexpr (sizeof(T) == 4) {
-        hj_step_epilogue(st, g, a1, a2, d, scratch);
+        am1 = hj_abits((double)am1f);
+        am2 = hj_abits((double)am2f);
+        hj_step_epilogue(st, g, am1, am2, hj_abits((double)dmf), scratch);
     } else {
-        hj_step_epilogue_scaled(st, g, a1, a2, d, scratch, scaled, nullptr, (const HjCoef<double> *)coef,
+        hj_step_epilogue_scaled(st, g, am1, am2, dbits, scratch, scaled, nullptr, (const HjCoef<double> *)coef,
                                 (const double *)k4tab);
     }
 }
@@ -746,11 +798,11 @@ __global__ void __launch_bounds__(RES_THREADS, res_min_blocks<T>()) hj_step_resi
                     const Neigh<T> nvv = {av.m.v[L], av.p.v[L]};
                     const Neigh<T> nt = {mraw, praw};
                     if constexpr (F32) {
-                        vn = cell_value(vc, Z.v[L], nx, ny, nvv, nt, cq1.v[L], cq2.v[L], (float)g.k3, k4s[k], dt,
-                                        g.mode3, g.mode4);
+                        vn = hj_min(Z.v[L], cell_value(vc, nx, ny, nvv, nt, cq1.v[L], cq2.v[L], (float)g.k3,
+                                                       k4s[k], dt, g.mode3, g.mode4));
                     } else {
                         const HjScaledCoef sc = {wq1.v[L], wq2.v[L], wq0.v[L], w4t[k]};
-                        vn = cell_value(vc, Z.v[L], nx, ny, nvv, nt, sc, k3dt, g.mode3, g.mode4);
+                        vn = hj_min(Z.v[L], cell_value(vc, nx, ny, nvv, nt, sc, k3dt, g.mode3, g.mode4));
                     }
                 }
                 out.v[L] = vn;
