@@ -247,3 +247,24 @@ def test_resident_solves_on_two_streams_at_once(hj):
     assert not errors, errors
     for prec, _ in runs:
         assert np.array_equal(out[prec], solo[prec]), prec
+
+
+def test_paper_room_experiment_matches_oracle(hj):
+    """The bench's reconstruction of the paper's experiment (Sec. IV-A: the
+    60x60x20x36 room, the steering car, R = 0.75 m cones, 0.5 s in steps of
+    0.007497 s) through HJ_KERNEL_AUTO: Q5.27 codes bit for bit against the
+    fixed-point oracle with the 67 steps of Table II, FP64 within 1e-12, FP32
+    within the FP32 tolerance."""
+    w = scenes.paper_room(1)
+    V0 = scenes.initial_value(w.grid, w.scene)
+    P = oracle.Problem(w.grid.n, w.grid.lo, w.grid.hi, w.grid.periodic, oracle.DYN_CAR4D_STEER,
+                       scenes.PAPER_STEER)
+    for prec in ("q527", "fp64", "fp32"):
+        with hj.Grid(w.grid.n, w.grid.lo, w.grid.hi, w.grid.periodic, prec_code(hj, prec)) as g:
+            g.set_dynamics(hj.HJ_DYN_CAR4D_STEER, scenes.PAPER_STEER)
+            g.set_initial_value(V0)
+            st = g.solve_brt(w.T, w.cfl)
+            V = read_raw(hj, g, prec)
+        assert st.steps == 67
+        assert st.kernel == (hj.HJ_KERNEL_GENERIC if prec == "fp64" else hj.HJ_KERNEL_RESIDENT)
+        check_oracle(prec, V, V0, P, w.T, w.cfl, st)
