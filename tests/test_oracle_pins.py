@@ -355,6 +355,31 @@ def test_paper_iteration_count():
     assert 0 < dts[-1] < dt_target
 
 
+def test_paper_room_workload(oracle_mod):
+    """The paper's experiment as the bench rebuilds it (Sec. IV-A): spacings
+    0.1 m, 0.067 m, 0.2 m/s and 2 pi/36 rad on 60x60x20x36 points, the
+    steering car, and the Courant number that makes the oracle's CFL step the
+    reported 0.007497 s, so the 0.5 s horizon takes the 67 iterations of
+    Tables II-III."""
+    with open(os.path.join(GOLDEN, "paper_numbers.json")) as f:
+        g = json.load(f)
+    w = scenes.paper_room(1)
+    assert tuple(w.grid.n) == tuple(g["grid"]) and w.T == g["horizon_s"]
+    h = [(w.grid.hi[d] - w.grid.lo[d]) / (w.grid.n[d] - 1) for d in range(3)]
+    assert h == pytest.approx([0.1, 0.067, 0.2], rel=1e-12)
+    assert (w.grid.hi[3] - w.grid.lo[3]) / w.grid.n[3] == pytest.approx(2 * math.pi / 36, rel=1e-15)
+    P = steer_problem(w.grid)
+    V0 = scenes.initial_value(w.grid, w.scene)
+    _, am = oracle.rate(P, V0)
+    assert oracle.cfl_dt(P, am, w.cfl) == pytest.approx(g["max_stable_dt_s"], rel=1e-12)
+    _, _, dts = oracle.advance(P, V0, V0, 0.0, w.T, w.cfl, max_steps=2)
+    assert dts[0] == pytest.approx(g["max_stable_dt_s"], rel=1e-12)
+    assert math.ceil(w.T / dts[0]) == g["iterations"]
+    # the cones lie in the room and V0 is the distance to the nearest inflated cone
+    assert np.all(w.scene.circles[:, 2] == 0.75)
+    assert float(V0.min()) < 0 < float(V0.max()) < 16.0  # inside the Q5.27 range (Sec. IV-B)
+
+
 @pytest.mark.parametrize("name,steps", [("car4d_31x31x11x16", 38), ("car4d_60x60x20x36", 151)])
 def test_car_cfl_step(oracle_mod, name, steps):
     """For the car on [-5,5]^2 x [0,4] x [-pi,pi): alpha^max = (max|v cos th|,
