@@ -561,13 +561,32 @@ __device__ __forceinline__ int32_t q_upwind_value(int32_t m, int32_t p, int mode
     return mode == HJ_AXIS_PLUS ? p : m;
 }
 
-// Q5.27: lane L's differences with the ghosts of q_axis.
-__device__ __forceinline__ QDiff lane_qdiff(int32_t mraw, int32_t praw, bool gm, bool gp, int32_t vc)
+// Q5.27 upwind neighbour of an axis with possibly one extrapolated side (gm:
+// index - 1, gp: index + 1): the grid value u to weigh and whether it stands
+// for the ghost 2 V_c - u (ghost set; the caller then weighs u by -W and V_c
+// by +2W).  The side is the one q_upwind takes from the differences.
+__device__ __forceinline__ int32_t q_upwind_ghost(int32_t m, int32_t p, bool gm, bool gp, int32_t vc, int mode,
+                                                  bool &ghost)
 {
-    QDiff d;
-    d.dm = gm ? (long long)vc - praw : (long long)mraw - vc;
-    d.dp = gp ? (long long)vc - mraw : (long long)praw - vc;
-    return d;
+    if (mode == HJ_AXIS_CONTROL) {
+        // the larger neighbour; a ghost 2 V_c - V_o is the larger one when V_c >= V_o
+        if (gp) {
+            ghost = vc >= m;
+            return m;
+        }
+        if (gm) {
+            ghost = p < vc;
+            return p;
+        }
+        ghost = false;
+        return p > m ? p : m;
+    }
+    if (mode == HJ_AXIS_PLUS) {
+        ghost = gp;
+        return gp ? m : p;
+    }
+    ghost = gm;
+    return gm ? p : m;
 }
 
 // Shared-memory bytes of a CTA's coefficient tables: per (v, theta) arrays
@@ -617,11 +636,13 @@ __device__ __forceinline__ void resident_table64(double *w1t, double *w2t, doubl
     for (int k = threadIdx.x; k < n3; k += blockDim.x) w4t[k] = hj_scaled_entry(coef[k * n4], k4[k], dt).w4;
 }
 
-// CTAs per SM the register budget is set for (FP32 quads need fewer registers)
+// CTAs per SM the register budget is set for: 3 for the 4-byte types (FP32
+// and Q5.27 at 80 registers; Q5.27 with a few spills, still faster than 2),
+// 2 for FP64
 template <typename T>
 constexpr int res_min_blocks()
 {
-    return std::is_same<T, float>::value ? 3 : 2;
+    return std::is_same<T, double>::value ? 2 : 3;
 }
 
 template <typename T, bool TRACK>
@@ -785,12 +806,22 @@ __global__ void __launch_bounds__(RES_THREADS, res_min_blocks<T>()) hj_step_resi
                                  ? hj_q527_update_interior32(vc, Z.v[L], u1, u2, u3, u4, a1, a2, w3, w4, nsum)
                                  : hj_q527_update_interior(vc, Z.v[L], u1, u2, u3, u4, a1, a2, w3, w4, nsum);
                     } else {
+                        // an extrapolated ghost on some axis: the ghost 2 V_c - V_o of an upwind
+                        // side enters as -W on V_o and +2W on V_c (the operands stay int32; the
+                        // sum, exact, is the one of hj_q527_update)
                         const bool gm4 = l == 0 && !per4, gp4 = l == N4 - 1 && !per4;
-                        vn = q_cell_value(vc, Z.v[L], lane_qdiff(ax.m.v[L], ax.p.v[L], ax.gm, ax.gp, vc),
-                                          lane_qdiff(ay.m.v[L], ay.p.v[L], ay.gm, ay.gp, vc),
-                                          lane_qdiff(av.m.v[L], av.p.v[L], av.gm, av.gp, vc),
-                                          lane_qdiff(mraw, praw, gm4, gp4, vc), qq1.v[L], qq2.v[L], w3, w4, g.mode3,
-                                          g.mode4);
+                        const int32_t w1 = qq1.v[L], w2 = qq2.v[L], a1 = abs(w1), a2 = abs(w2);
+                        const bool xpos = w1 >= 0, ypos = w2 >= 0;
+                        const bool hx = xpos ? ax.gp : ax.gm, hy = ypos ? ay.gp : ay.gm;
+                        const int32_t ux = (xpos != hx) ? ax.p.v[L] : ax.m.v[L];
+                        const int32_t uy = (ypos != hy) ? ay.p.v[L] : ay.m.v[L];
+                        bool hv, ht;
+                        const int32_t uv = q_upwind_ghost(av.m.v[L], av.p.v[L], av.gm, av.gp, vc, g.mode3, hv);
+                        const int32_t ut = q_upwind_ghost(mraw, praw, gm4, gp4, vc, g.mode4, ht);
+                        const int32_t c0 = -(a1 + a2 + w3 + w4) + (hx ? 2 * a1 : 0) + (hy ? 2 * a2 : 0) +
+                                           (hv ? 2 * w3 : 0) + (ht ? 2 * w4 : 0);
+                        vn = hj_q527_update_interior(vc, Z.v[L], ux, uy, uv, ut, hx ? -a1 : a1, hy ? -a2 : a2,
+                                                     hv ? -w3 : w3, ht ? -w4 : w4, c0);
                     }
                 } else {
                     const Neigh<T> nx = {ax.m.v[L], ax.p.v[L]};
