@@ -98,15 +98,19 @@ typedef enum {
     HJ_DYN_CAR4D_STEER = 2
 } hj_dynamics;
 
-/* Step-kernel selection (HJ_KERNEL_AUTO picks the fastest one that supports
- * the grid). */
+/* Step-kernel selection.  HJ_KERNEL_AUTO picks, by measured speed:
+ * HJ_KERNEL_RESIDENT for FP32 grids of up to 4 M cells and Q5.27 grids of up
+ * to 8 M cells, else HJ_KERNEL_TILED where it supports the grid, else
+ * HJ_KERNEL_GENERIC (always for FP64 grids). */
 typedef enum {
     HJ_KERNEL_AUTO = 0,
     HJ_KERNEL_GENERIC = 1, /* one thread per cell, loads through L1/L2 */
     HJ_KERNEL_TILED = 2,   /* FP32, Q5.27: TMA-staged 4D tiles streamed along x */
-    HJ_KERNEL_RESIDENT = 3 /* the generic per-cell update, many steps per cooperative launch
-                            * with a grid barrier between steps (small grids); any
-                            * precision, identical results to HJ_KERNEL_GENERIC */
+    HJ_KERNEL_RESIDENT = 3 /* the per-cell update of HJ_KERNEL_GENERIC (identical results, any
+                            * precision and grid of fewer than 2^32 values whose coefficient
+                            * tables fit in shared memory), the whole time loop in one
+                            * cooperative launch with a grid barrier between steps; a barrier
+                            * wait that runs out (2 s) ends the call with HJ_ERR_TIMEOUT */
 } hj_kernel;
 
 typedef struct {
