@@ -26,6 +26,7 @@ struct QueryGeom {
     int p4;
     unsigned int periodic;
     double lo[4], h[4], inv_h[4];
+    double span[4], inv_span[4];  // periodic axes: N h and its inverse
     int dyn;
     double p[3];
 };
@@ -37,23 +38,30 @@ __device__ __forceinline__ double value_at(const T *__restrict__ V, long long o)
     else return (double)V[o];
 }
 
-// Cell index and fraction of coordinate z on axis d.
+// Cell index and fraction of coordinate z on axis d.  The coordinate is
+// scaled by the reciprocal spacing and a periodic axis is wrapped with one
+// floor (no FP64 division or fmod: both are long FP64 sequences, and the FP64
+// unit bounds this kernel); the fraction then differs from the quotient by a
+// few ulps at most.
 __device__ __forceinline__ void query_cell(const QueryGeom &q, int d, double z, int &i0, double &f)
 {
     const int N = q.n[d];
-    const double h = q.h[d], lo = q.lo[d];
+    const double lo = q.lo[d];
     if ((q.periodic >> d) & 1u) {
-        const double span = h * (double)N;
-        double u = fmod(z - lo, span);
+        const double span = q.span[d];
+        double u = z - lo;
+        u = fma(-floor(u * q.inv_span[d]), span, u);
         if (u < 0.0) u += span;
-        const double r = u / h;
+        if (u >= span) u -= span;
+        const double r = u * q.inv_h[d];
         int i = (int)floor(r);
         if (i >= N) i = N - 1;
+        if (i < 0) i = 0;
         i0 = i;
         f = r - (double)i;
         return;
     }
-    const double r = (z - lo) / h;
+    const double r = (z - lo) * q.inv_h[d];
     if (!(r > 0.0)) {  // also NaN: clamp to the lower end
         i0 = 0;
         f = 0.0;
@@ -155,6 +163,8 @@ QueryGeom make_geom(const hj_grid *g)
         q.lo[d] = g->lo[d];
         q.h[d] = g->h[d];
         q.inv_h[d] = 1.0 / g->h[d];
+        q.span[d] = g->h[d] * (double)g->n[d];
+        q.inv_span[d] = 1.0 / q.span[d];
     }
     q.p4 = g->p4;
     q.periodic = g->periodic;
