@@ -268,3 +268,28 @@ def test_paper_room_experiment_matches_oracle(hj):
         assert st.steps == 67
         assert st.kernel == (hj.HJ_KERNEL_GENERIC if prec == "fp64" else hj.HJ_KERNEL_RESIDENT)
         check_oracle(prec, V, V0, P, w.T, w.cfl, st)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "q527"])
+def test_resident_many_quads_per_thread(hj, prec):
+    """100x100x30x48 (14.4 M cells: about 20 theta quads per thread and step)
+    equals the generic kernel bit for bit."""
+    w = scenes.custom_workload((100, 100, 30, 48), n_circles=8, T=0.15, seed=77)
+    V0 = scenes.initial_value(w.grid, w.scene)
+    V, st = run(hj, w, prec, hj.HJ_KERNEL_RESIDENT, V0)
+    Vg, sg = run(hj, w, prec, hj.HJ_KERNEL_GENERIC, V0)
+    assert st.steps == sg.steps > 3
+    assert np.array_equal(V, Vg)
+
+
+def test_resident_rejected_when_tables_do_not_fit(hj):
+    """An FP64 grid whose per-(v, theta) tables exceed the shared memory the
+    resident kernel keeps them in: HJ_KERNEL_RESIDENT is refused and AUTO
+    keeps the generic kernel."""
+    w = scenes.custom_workload((4, 4, 200, 256), n_circles=2, T=0.05, seed=5)
+    with hj.Grid(w.grid.n, w.grid.lo, w.grid.hi, w.grid.periodic, hj.HJ_FP64) as g:
+        g.set_dynamics(hj.HJ_DYN_CAR4D, (w.a_max, w.w_max))
+        with pytest.raises(hj.HjError) as e:
+            g.set_kernel(hj.HJ_KERNEL_RESIDENT)
+        assert e.value.status == hj.HJ_ERR_UNSUPPORTED
+        assert g.info().kernel == hj.HJ_KERNEL_GENERIC
