@@ -36,6 +36,13 @@
  * different host threads.  All device work of a grid runs on the grid's
  * stream.  The calls below block until their device work is complete unless
  * stated otherwise.
+ *
+ * Caller-owned device arrays (the *_device calls, of grids and batches): on a
+ * caller's stream they are ordered by that stream.  A grid or batch on its own
+ * stream first waits, without blocking the host, for the work already queued
+ * on the legacy default stream (where PyTorch's default stream and callers
+ * that name no stream run); work on any other stream that writes or reads
+ * such an array must be complete before the call.
  */
 #ifndef HJ_H
 #define HJ_H

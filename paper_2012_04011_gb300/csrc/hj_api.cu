@@ -460,6 +460,7 @@ void free_grid(hj_grid *g)
     if (g->hstate) cudaFreeHost(g->hstate);
     for (int i = 0; i < 4; ++i)
         if (g->ev[i]) cudaEventDestroy(g->ev[i]);
+    if (g->ev_in) cudaEventDestroy(g->ev_in);
     for (int i = 0; i < 4; ++i)
         if (g->graphs[i].exec) cudaGraphExecDestroy(g->graphs[i].exec);
     if (g->own_stream && g->stream) cudaStreamDestroy(g->stream);
@@ -592,6 +593,7 @@ hj_status hj_create_grid(const int32_t n[4], const double lo[4], const double hi
     if (e == cudaSuccess) e = cudaMalloc(&g->dstate, sizeof(HjDevState));
     if (e == cudaSuccess) e = cudaHostAlloc(&g->hstate, sizeof(HjDevState), cudaHostAllocDefault);
     for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaEventCreate(&g->ev[i]);
+    if (e == cudaSuccess && g->own_stream) e = cudaEventCreateWithFlags(&g->ev_in, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         hj_status s = set_err(e == cudaErrorMemoryAllocation ? HJ_ERR_OOM : HJ_ERR_CUDA, "hj_create_grid: %s",
                               cudaGetErrorString(e));
@@ -757,6 +759,18 @@ static void *device_view(const hj_grid *g, const void *p)
     return a.device == g->device ? a.devicePointer : nullptr;
 }
 
+// A grid on its own (non-blocking) stream reads caller-owned device arrays
+// only after the work already queued on the legacy default stream, where a
+// caller that names no stream (PyTorch's default stream included) wrote them.
+// A grid on a caller's stream is ordered by that stream.
+static hj_status follow_default_stream(hj_grid *g)
+{
+    if (!g->own_stream) return HJ_OK;
+    HJ_CUDA(cudaEventRecord(g->ev_in, cudaStreamLegacy));
+    HJ_CUDA(cudaStreamWaitEvent(g->stream, g->ev_in, 0));
+    return HJ_OK;
+}
+
 hj_status hj_set_initial_value(hj_grid *g, const double *v0, size_t count)
 {
     g_err[0] = 0;
@@ -810,6 +824,7 @@ hj_status hj_set_initial_value_xy_device(hj_grid *g, const void *v0_xy_device, h
     const long long nxy = (long long)g->n[0] * g->n[1];
     if (count != (size_t)nxy) return set_err(HJ_ERR_INVALID_ARG, "count %zu != N1*N2 = %lld", count, nxy);
     if ((s = activate(g)) != HJ_OK) return s;
+    if ((s = follow_default_stream(g)) != HJ_OK) return s;
     if ((s = reset_state(g)) != HJ_OK) return s;
     return ingest_xy(g, v0_xy_device, dtype, nxy);
 }
@@ -824,6 +839,7 @@ hj_status hj_set_initial_value_device(hj_grid *g, const void *v0_device, hj_prec
     if (count != (size_t)g->ncell)
         return set_err(HJ_ERR_INVALID_ARG, "count %zu != N1*N2*N3*N4 = %lld", count, g->ncell);
     if ((s = activate(g)) != HJ_OK) return s;
+    if ((s = follow_default_stream(g)) != HJ_OK) return s;
     if ((s = reset_state(g)) != HJ_OK) return s;
     long long nrows = (long long)g->n[0] * g->n[1] * g->n[2];
     int *flag = &g->dstate->nonfinite;
@@ -1031,6 +1047,7 @@ hj_status hj_query_device(const hj_grid *gc, const double *states, int64_t m, do
     if (!g->has_value) return set_err(HJ_ERR_STATE, "no initial value (hj_set_initial_value)");
     if (control && !g->has_dyn) return set_err(HJ_ERR_STATE, "the control needs the dynamics (hj_set_dynamics)");
     if ((s = activate(g)) != HJ_OK) return s;
+    if ((s = follow_default_stream(g)) != HJ_OK) return s;
     if ((s = pull_state(g)) != HJ_OK) return s;
     HJ_CUDA(hj_launch_query(g, hj_value_ptr(g, g->hstate->n), states, m, value, grad, control));
     HJ_CUDA(cudaStreamSynchronize(g->stream));
@@ -1092,6 +1109,7 @@ hj_status hj_read_value_device(const hj_grid *gc, void *out_device, hj_precision
         return set_err(HJ_ERR_INVALID_ARG, "count %zu != N1*N2*N3*N4 = %lld", count, g->ncell);
     if (!g->has_value) return set_err(HJ_ERR_STATE, "no initial value (hj_set_initial_value)");
     if ((s = activate(g)) != HJ_OK) return s;
+    if ((s = follow_default_stream(g)) != HJ_OK) return s;  // the output array too
     if ((s = pull_state(g)) != HJ_OK) return s;
     const void *src = hj_value_ptr(g, g->hstate->n);
     const long long nrows = (long long)g->n[0] * g->n[1] * g->n[2];

@@ -462,6 +462,7 @@ struct hj_batch {
     bool dirty = true;
     std::vector<std::pair<long long, cudaGraphExec_t>> graphs;
     cudaEvent_t ev[2] = {nullptr, nullptr};
+    cudaEvent_t ev_in = nullptr;  // own stream: orders device inputs after the legacy default stream
 };
 
 namespace {
@@ -777,6 +778,7 @@ hj_status hj_batch_create(int32_t max_slots, size_t memory_budget, void *cuda_st
     if (e == cudaSuccess) e = cudaMalloc(&b->d_ctl, sizeof(BatchCtl));
     if (e == cudaSuccess) e = cudaMalloc(&b->d_maps, sizeof(CUtensorMap) * 4 * max_slots);
     for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaEventCreate(&b->ev[i]);
+    if (e == cudaSuccess && b->own_stream) e = cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming);
     if (e == cudaSuccess) {
         memset(b->h_slots, 0, sizeof(BatchSlot) * max_slots);
         for (int i = 0; i < max_slots; ++i) b->h_slots[i].st.done = 1;
@@ -809,6 +811,7 @@ void hj_batch_destroy(hj_batch *b)
     if (b->d_maps) cudaFree(b->d_maps);
     for (int i = 0; i < 2; ++i)
         if (b->ev[i]) cudaEventDestroy(b->ev[i]);
+    if (b->ev_in) cudaEventDestroy(b->ev_in);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
     delete b;
 }
@@ -947,6 +950,12 @@ static hj_status batch_ingest(hj_batch *b, int32_t slot, const void *src, hj_pre
     b->h_slots[slot].st.status = HJ_OK;
     if ((s = push_slot(b, slot)) != HJ_OK) return s;
     const void *dsrc = src;
+    if (!on_host && b->own_stream) {
+        // a batch on its own (non-blocking) stream reads a caller's device array
+        // only after the work already queued on the legacy default stream
+        HJB_CUDA(cudaEventRecord(b->ev_in, cudaStreamLegacy));
+        HJB_CUDA(cudaStreamWaitEvent(b->stream, b->ev_in, 0));
+    }
     if (on_host) {  // stage the FP64 array in the slot's A|B region (2 nint floats >= ncell doubles)
         HJB_CUDA(cudaMemcpyAsync(sl.buf, src, sizeof(double) * (size_t)sl.ncell, cudaMemcpyHostToDevice, b->stream));
         dsrc = sl.buf;
@@ -1120,6 +1129,10 @@ static hj_status batch_read(hj_batch *b, int32_t slot, void *out, hj_precision d
     const float *src = n == 0 ? sl.v0 : sl.buf + ((n - 1) & 1) * sl.nint;
     const long long nrows = (long long)sl.n[0] * sl.n[1] * sl.n[2];
     if (!to_host) {
+        if (b->own_stream) {  // the caller's array may still be in use on the legacy default stream
+            HJB_CUDA(cudaEventRecord(b->ev_in, cudaStreamLegacy));
+            HJB_CUDA(cudaStreamWaitEvent(b->stream, b->ev_in, 0));
+        }
         HJB_CUDA(hj_launch_readback_f32(src, out, dtype, sl.n[3], sl.p4, 0, nrows, b->stream));
         HJB_CUDA(cudaStreamSynchronize(b->stream));
         return HJ_OK;

@@ -89,6 +89,7 @@ struct hj_grid {
     long long nint;        // n1*n2*n3*p4 (internal values per array)
     cudaStream_t stream;
     bool own_stream;
+    cudaEvent_t ev_in;  // own stream: orders device inputs after the legacy default stream
     int device;
 
     void *v0;              // V0 (internal layout)

@@ -256,6 +256,40 @@ def test_device_ingest_and_readback(hj):
             assert np.array_equal(g.read_value(), Vh)
 
 
+def test_device_arrays_follow_the_default_stream(hj):
+    """A grid or batch on its own stream touches a caller's device array only
+    after the work already queued on the default stream: an input whose copy
+    still waits behind a long kernel arrives whole, and an output that a queued
+    fill would overwrite receives the values.  (torch.cuda._sleep is a spin of
+    a fixed cycle count: it ends by itself.)"""
+    import torch
+    w = scenes.workload("car4d_31x31x11x16")
+    V0 = scenes.initial_value(w.grid, w.scene)
+    src = torch.from_numpy(V0.ravel().copy()).cuda()
+    torch.cuda.synchronize()
+    with hj.Grid.for_workload(w, hj.HJ_FP64) as g:
+        dst = torch.zeros_like(src)
+        torch.cuda._sleep(200_000_000)  # about 0.1 s
+        dst.copy_(src)
+        hj.hj_set_initial_value_device(g.handle, dst)
+        out = torch.empty_like(src)
+        torch.cuda._sleep(200_000_000)
+        out.fill_(-7.0)
+        g.read_value_device(out)
+        assert np.array_equal(out.cpu().numpy(), V0.ravel())
+    with hj.Batch(2) as b:
+        slot = b.add_workload(w)
+        dst = torch.zeros_like(src)
+        torch.cuda._sleep(200_000_000)
+        dst.copy_(src)
+        b.set_initial_value(slot, dst)
+        out = torch.empty(V0.size, dtype=torch.float32, device="cuda")
+        torch.cuda._sleep(200_000_000)
+        out.fill_(-7.0)
+        b.read_value(slot, out)
+        assert np.array_equal(out.cpu().numpy(), V0.ravel().astype(np.float32))
+
+
 def test_pinned_host_buffers_equal_pageable(hj):
     """V0 from pinned host memory (read by the ingest kernel over the host
     link) and V into pinned host memory (written by the readback kernel) give
