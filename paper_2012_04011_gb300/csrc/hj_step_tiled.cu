@@ -143,7 +143,7 @@ bool hj_tiled_setup(hj_grid *g, char *why, size_t why_len)
     if (!g->has_dyn || (g->dyn != HJ_DYN_CAR4D && g->dyn != HJ_DYN_CAR4D_STEER))
         return fail("tiled kernel needs the car dynamics");
     if (g->p4 > 256) return fail("theta rows longer than 256 points");
-    if (g->nint >= (1LL << 31)) return fail("grid too large for 32-bit offsets");
+    if (g->nint >= (1LL << 34)) return fail("grid of 2^34 stored values or more (32-bit float4 indices)");
     EncodeTiledFn enc = get_encode_fn();
     if (!enc) return fail("cuTensorMapEncodeTiled unavailable");
 

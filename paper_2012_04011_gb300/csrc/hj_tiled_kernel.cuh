@@ -207,7 +207,9 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
         const bool inrow = r < P.ty * P.tv;
         const int rsm = inrow ? ((jy + 1) * srow + (kv + 1)) * P4 + 4 * q : (srow + 1) * P4;
         const int r0sm = P.halo_floats + (inrow ? (jy * P.tv + kv) * P4 + 4 * q : 0);  // V0 in the stage
-        const uint32_t s1 = (uint32_t)N2 * N3 * P4;  // plane stride (the grid has < 2^31 values)
+        // V_{n+1} is addressed in float4 units (P4 is a multiple of 4): 32-bit
+        // indices then reach 2^34 values, more than any grid the API accepts
+        const uint32_t s1q = (uint32_t)N2 * N3 * (P4 / 4);  // plane stride in float4 units
 
         // x and y upwind weights of this quad: xdot_1/dx_1 = v cos(th)/dx_1
         // takes V(x+1) where cos >= 0 and V(x-1) where cos < 0; likewise y.
@@ -291,7 +293,7 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
             const bool edge = it.y0 == 0 || it.y0 + P.ty >= N2 || it.v0 == 0 || it.v0 + P.tv >= N3;
             const int y = it.y0 + jy, v = it.v0 + kv;
             const bool rok = inrow && y < N2 && v < N3;
-            const uint32_t rbase = rok ? ((uint32_t)y * N3 + v) * P4 + 4 * q : 0u;
+            const uint32_t rbq = rok ? ((uint32_t)y * N3 + v) * (P4 / 4) + q : 0u;  // row quad, float4 units
             // xdot_1 = v cos(th), xdot_2 = v sin(th): in the general form a
             // negative speed flips the upwind sides and the weights take |v|
             float vk = (rok && !FIXED) ? tab[v] : 0.f;
@@ -498,7 +500,7 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
                         f4set(out, e, vn);
                     }
                     }
-                    *(float4 *)(vout + (uint32_t)x * s1 + rbase) = out;
+                    ((float4 *)vout)[(uint32_t)x * s1q + rbq] = out;
                     if constexpr (TRACK) {
 #pragma unroll
                         for (int e = 0; e < 4; ++e) {

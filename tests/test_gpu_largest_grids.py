@@ -1,10 +1,13 @@
 """The largest grids: more values than 32-bit offsets reach.
 
-A grid with 2^31 or more stored values is refused by the tiled kernel (its
-offsets are 32-bit), so AUTO runs the generic kernel; from 2^32 cells on that
-kernel splits cell indices with 64-bit divisions instead of the 32-bit
-multiply-high ones.  Each case takes V0 from its (x, y) field (Eq. init_V
-depends on the position only), runs two steps and checks each against the
+Past 2^31 stored values the tiled kernel still stores V_{n+1} through 32-bit
+indices, counted in float4 units (they reach 2^34 values), and from 2^32
+cells on the generic kernel splits cell indices with 64-bit divisions instead
+of the 32-bit multiply-high ones.  Each case takes
+V0 from its (x, y) field (Eq. init_V depends on the position only), given as
+that field (the broadcast-V0 variants) or replicated in 4D on the device, runs
+two steps with the kernel AUTO picks (the tiled one for FP32 and Q5.27, the
+generic one for FP64) or the generic one, and checks each step against the
 oracle's step at sampled cells: random cells, every face, edge and corner
 class, and the cells on both sides of the 2^31 and 2^32 flat indices.
 
@@ -16,7 +19,8 @@ memory (a few hundred MB at most).  The device values are read back into a
 device buffer and gathered there.
 
 Device memory: the FP64 case holds 3 x 38.7 GB of grid buffers plus a 35 GB
-read-back buffer (about 151 GB of the 288 GB).
+read-back buffer (about 151 GB of the 288 GB); a 4D V0 input (FP32, 17.7 GB)
+is freed before the read-back buffer is taken.
 """
 import mmap
 
@@ -28,11 +32,17 @@ from paper_2012_04011_gb300 import scenes
 
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
-CASES = [
-    ("fp32", (1536, 1536, 32, 33)),  # 2.49e9 cells: 32-bit cell indices, 64-bit offsets
-    ("fp32", (2048, 2048, 32, 33)),  # 4.43e9 cells: 64-bit cell indices
-    ("q527", (2048, 2048, 32, 33)),
-    ("fp64", (2048, 2048, 32, 33)),
+CASES = [  # precision, grid, kernel ("auto" or "generic"), V0 given as its (x, y) field or in 4D
+    ("fp32", (1536, 1536, 32, 33), "auto", "xy"),  # 2.49e9 cells, 2.7e9 stored values
+    ("fp32", (1536, 1536, 32, 33), "generic", "xy"),  # 32-bit cell indices above 2^31
+    ("fp32", (2048, 2048, 32, 33), "auto", "xy"),  # 4.43e9 cells, 4.8e9 stored values
+    ("fp32", (2048, 2048, 32, 33), "auto", "4d"),
+    ("fp32", (2048, 2048, 32, 33), "generic", "xy"),  # 64-bit cell indices
+    ("q527", (2048, 2048, 32, 33), "auto", "xy"),
+    ("q527", (2048, 2048, 32, 33), "auto", "4d"),
+    ("q527", (2048, 2048, 32, 33), "generic", "xy"),
+    ("fp64", (2048, 2048, 32, 33), "auto", "xy"),  # generic (the FP64 path)
+    ("fp32", (8, 4096, 4096, 36), "auto", "4d"),  # x planes of 6e8 values
 ]
 
 
@@ -93,8 +103,8 @@ def host_view(torch, dev, where, like):
     return h
 
 
-@pytest.mark.parametrize("prec,n", CASES)
-def test_sampled_steps_on_grids_past_32_bit_offsets(hj, prec, n):
+@pytest.mark.parametrize("prec,n,kernel,v0form", CASES)
+def test_sampled_steps_on_grids_past_32_bit_offsets(hj, prec, n, kernel, v0form):
     torch = pytest.importorskip("torch")
     p = {"fp32": hj.HJ_FP32, "fp64": hj.HJ_FP64, "q527": hj.HJ_Q527}[prec]
     tdt = {"fp32": torch.float32, "fp64": torch.float64, "q527": torch.int32}[prec]
@@ -111,8 +121,19 @@ def test_sampled_steps_on_grids_past_32_bit_offsets(hj, prec, n):
     try:
         with hj.Grid(n, grid.lo, grid.hi, grid.periodic, p) as g:
             g.set_dynamics(hj.HJ_DYN_CAR4D, (scenes.A_MAX, scenes.W_MAX))
-            g.set_initial_value_xy(v0_xy)
-            assert g.info().kernel == hj.HJ_KERNEL_GENERIC
+            if v0form == "xy":
+                src = v0_xy
+                g.set_initial_value_xy(v0_xy)
+            else:  # the field replicated over v and theta on the device, in FP32
+                src = v0_xy.astype(np.float32).astype(np.float64)
+                v4 = torch.from_numpy(v0_xy).to("cuda", torch.float32)[:, :, None, None].expand(*n).contiguous()
+                hj.hj_set_initial_value_device(g.handle, v4)
+                del v4
+                torch.cuda.empty_cache()
+            if kernel == "generic":
+                g.set_kernel(hj.HJ_KERNEL_GENERIC)
+            want_kernel = hj.HJ_KERNEL_TILED if kernel == "auto" and prec != "fp64" else hj.HJ_KERNEL_GENERIC
+            assert g.info().kernel == want_kernel
             out = torch.empty(ncell, dtype=tdt, device="cuda")
             g.read_value_device(out)  # V0 as stored (n = 0)
             Vn = host_view(torch, out, star, ndt)
@@ -120,12 +141,12 @@ def test_sampled_steps_on_grids_past_32_bit_offsets(hj, prec, n):
             # V0 is the (x, y) field replicated over v and theta, in the grid's precision
             i, j = np.unravel_index(cells, n)[:2]
             want0 = {"fp32": lambda a: a.astype(np.float32), "fp64": lambda a: a, "q527": oracle.to_q527}[prec]
-            assert np.array_equal(v0_at, want0(v0_xy[i, j]))
+            assert np.array_equal(v0_at, want0(src[i, j]))
             V0h = lazy_zeros(ncell, ndt)  # the oracle reads V0 only at the sampled cells
             V0h[cells] = v0_at
             for _ in range(2):
                 st = g.advance_brt(T, cfl, 1)
-                assert st.steps == 1
+                assert st.steps == 1 and st.kernel == want_kernel
                 g.read_value_device(out)
                 got = out[torch.from_numpy(cells).to(out.device)].cpu().numpy()
                 if prec == "q527":
