@@ -1186,13 +1186,14 @@ hj_status hj_autotune(hj_grid *g, int32_t steps_per_trial, hj_tile_result *resul
 
     // candidate (ty, tv): one consumer thread per (row, theta quad), at least
     // 8 warps; the 4 shapes with the fewest halo reads per row from each
-    // launch-bound class (<= 384, 512, 640, 768 consumer threads)
+    // launch-bound class of the tiled kernel (hj_tiled_variant)
     struct Cand {
         int ty, tv;
         double halo;
     } cands[17];
     int nc = 0;
-    const int class_hi[4] = {384, 512, 640, 768};
+    int class_hi[4];
+    for (int i = 0; i < 4; ++i) class_hi[i] = hj_tiled_variant(g->prec == HJ_Q527, i);
     for (int cls = 0; cls < 4; ++cls) {
         Cand top[4];
         int nt = 0;

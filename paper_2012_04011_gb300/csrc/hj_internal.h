@@ -148,6 +148,8 @@ bool hj_tiled_setup(hj_grid *g, char *why, size_t why_len);
 // Consumer threads a tile of ty x tv rows needs (one per row and theta quad),
 // and whether that shape can run at all.
 int hj_tiled_threads(const hj_grid *g, int ty, int tv);
+// Consumer threads of the tiled kernel's launch-bound class i (0..3), per precision.
+int hj_tiled_variant(bool fixed, int i);
 
 // cos and sin of grid headings for the FP32 tables: values below 1e-12 are
 // rounding artefacts of theta_l = lo + l dx at +-pi/2, 0, +-pi (the next

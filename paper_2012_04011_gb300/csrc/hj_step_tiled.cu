@@ -127,8 +127,10 @@ bool sign_uniform(const hj_grid *g, float *tab_sign)
 int hj_tiled_threads(const hj_grid *g, int ty, int tv)
 {
     const int nc = ((g->p4 / 4) * ty * tv + 31) / 32 * 32;
-    return nc <= MAX_CONSUMERS ? nc + 32 : 0;
+    return nc <= max_consumers(g->prec == HJ_Q527) ? nc + 32 : 0;
 }
+
+int hj_tiled_variant(bool fixed, int i) { return fixed ? VARIANTS_Q527[i] : VARIANTS_F32[i]; }
 
 bool hj_tiled_setup(hj_grid *g, char *why, size_t why_len)
 {
@@ -162,19 +164,19 @@ bool hj_tiled_setup(hj_grid *g, char *why, size_t why_len)
     free(sgn);
     if (e != cudaSuccess) return fail("sign table upload failed");
 
-    // tile shape: one consumer thread per (row, theta quad), at most
-    // MAX_CONSUMERS (+ the producer warp).  By default the rows of (y, v) with
-    // the fewest halo reads per row among the shapes whose block fits the
-    // largest launch-bound class that runs without spills (640 consumer
-    // threads; 512 in fixed point), discounted by the share of the SMs the
+    // tile shape: one consumer thread per (row, theta quad), at most the
+    // largest launch-bound class (+ the producer warp).  By default the rows
+    // of (y, v) with the fewest halo reads per row among the shapes whose block
+    // fits the largest class that runs without spills (640 consumer threads;
+    // 480 in fixed point), discounted by the share of the SMs the
     // shape can keep busy (a small grid needs small tiles to fill the GPU),
     // and as many stages as fit; hj_autotune measures the candidates instead.
     const int q4 = g->p4 / 4;
-    const int max_rows = MAX_CONSUMERS / q4;
+    const int max_rows = max_consumers(fixed) / q4;
     if (max_rows < 1) return fail("theta rows too long for one CTA");
     int ty = g->tile_req[0], tv = g->tile_req[1];
     if (ty <= 0 || tv <= 0) {
-        const int cap = fixed ? 512 : 640;
+        const int cap = fixed ? VARIANTS_Q527[1] : VARIANTS_F32[2];
         double best = 1e300;
         int bty = 1, btv = 1;
         for (int a = 1; a <= 16 && a <= g->n[1]; ++a)
@@ -208,7 +210,7 @@ bool hj_tiled_setup(hj_grid *g, char *why, size_t why_len)
     }
     if (stages < 4 || stages > MAX_STAGES) return fail("stage count out of range");
     TiledParams P = make_params(g, ty, tv, stages, 0);
-    if (P.nconsumer > MAX_CONSUMERS) return fail("tile needs too many threads");
+    if (P.nconsumer > max_consumers(fixed)) return fail("tile needs too many threads");
     size_t smem = tiled_smem_bytes(P);
     if ((int)smem > maxsmem) return fail("tile does not fit in shared memory");
     const void *fn = (const void *)kernel_fn(fixed, g->p4 != g->n[3], usign, g->v0_bcast, false, P.nconsumer);

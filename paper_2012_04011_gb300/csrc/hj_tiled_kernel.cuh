@@ -53,10 +53,23 @@
 namespace hj_tiled {
 
 constexpr int MAX_STAGES = 8;
-constexpr int MAX_CONSUMERS = 768;  // consumer threads per CTA (+ one producer warp)
-// Launch-bound variants: up to 384, 512, 640 or 768 consumer threads (152,
-// 120, 96 or 80 registers a thread); a shape uses the smallest that holds it.
-constexpr int VARIANTS[4] = {384, 512, 640, 768};
+// Launch-bound variants: a shape uses the smallest that holds its consumer
+// threads.  Each of an SM's four 16K-register files holds a quarter of a
+// CTA's warps (rounded up), which sets the registers a thread may use.
+// FP32: up to 384, 512, 640 or 768 consumers (with the producer warp 13, 17,
+// 21 or 25 warps: 128, 96, 80 or 72 registers); its 4D update compiled under
+// the 80-register cap of the 640 class ran faster than under 96.  Q5.27: up
+// to 352, 480, 608 or 736 (12, 16, 20 or 24 warps: 168, 128, 96 or 80
+// registers), so that its 480-consumer shapes keep the registers of the
+// integer update without spilling.
+constexpr int VARIANTS_F32[4] = {384, 512, 640, 768};
+constexpr int VARIANTS_Q527[4] = {352, 480, 608, 736};
+template <bool FIXED>
+constexpr int variant(int i)
+{
+    return FIXED ? VARIANTS_Q527[i] : VARIANTS_F32[i];
+}
+constexpr int max_consumers(bool fixed) { return fixed ? VARIANTS_Q527[3] : VARIANTS_F32[3]; }
 
 struct TiledParams {
     int ty, tv;          // tile rows along y and v
@@ -571,10 +584,10 @@ KernelFn select_q527(bool padded, bool bcast, bool track, int nconsumer);       
 template <bool FIXED, bool PADDED, bool USIGN, bool BCAST, bool TRACK>
 KernelFn by_bound(int nconsumer)
 {
-    if (nconsumer <= VARIANTS[0]) return hj_step_tiled_kernel<FIXED, PADDED, USIGN, BCAST, TRACK, VARIANTS[0]>;
-    if (nconsumer <= VARIANTS[1]) return hj_step_tiled_kernel<FIXED, PADDED, USIGN, BCAST, TRACK, VARIANTS[1]>;
-    if (nconsumer <= VARIANTS[2]) return hj_step_tiled_kernel<FIXED, PADDED, USIGN, BCAST, TRACK, VARIANTS[2]>;
-    return hj_step_tiled_kernel<FIXED, PADDED, USIGN, BCAST, TRACK, VARIANTS[3]>;
+    if (nconsumer <= variant<FIXED>(0)) return hj_step_tiled_kernel<FIXED, PADDED, USIGN, BCAST, TRACK, variant<FIXED>(0)>;
+    if (nconsumer <= variant<FIXED>(1)) return hj_step_tiled_kernel<FIXED, PADDED, USIGN, BCAST, TRACK, variant<FIXED>(1)>;
+    if (nconsumer <= variant<FIXED>(2)) return hj_step_tiled_kernel<FIXED, PADDED, USIGN, BCAST, TRACK, variant<FIXED>(2)>;
+    return hj_step_tiled_kernel<FIXED, PADDED, USIGN, BCAST, TRACK, variant<FIXED>(3)>;
 }
 
 }  // namespace hj_tiled
