@@ -294,6 +294,41 @@ def run_small(hj, scenes, torch, stream):
     return small
 
 
+LARGE_GRID = (2048, 2048, 32, 33)
+
+
+def run_large(hj, scenes, torch, stream, steps=10):
+    """Grids past 32-bit offsets: the 2048x2048x32x33 car (4.4e9 cells, 4.8e9
+    stored values, 58 GB of FP32 or Q5.27 buffers), V0 from its (x, y) field.
+    Each precision runs the tiled kernel (autotuned) and the generic one;
+    ms per step from the library's CUDA events around `steps` steps, after 3
+    warm-up steps."""
+    n = LARGE_GRID
+    grid = scenes.GridSpec(n)
+    v0_xy = scenes.signed_distance_xy(grid, scenes.random_scene(np.random.default_rng(scenes.SEED_BASE + 7), 12))
+    ncell = int(np.prod(n))
+    peak = measured_peaks()[0]
+    res = {"workload": "car4d_%dx%dx%dx%d" % n, "cells": ncell}
+    for pname, prec in (("f32", hj.HJ_FP32), ("q527", hj.HJ_Q527)):
+        for kname, kern in (("tiled", hj.HJ_KERNEL_TILED), ("generic", hj.HJ_KERNEL_GENERIC)):
+            with hj.Grid(n, grid.lo, grid.hi, grid.periodic, prec, stream.cuda_stream) as g:
+                g.set_dynamics(hj.HJ_DYN_CAR4D, (scenes.A_MAX, scenes.W_MAX))
+                g.set_initial_value_xy(v0_xy)
+                g.set_kernel(kern)
+                if kern == hj.HJ_KERNEL_TILED:
+                    g.autotune(4)
+                g.advance_brt(10.0, scenes.CFL, 3)
+                st = g.advance_brt(10.0, scenes.CFL, steps)
+                ms = st.loop_ms / max(st.steps, 1)
+                res[f"{pname}_{kname}"] = {
+                    "ms_per_step": ms, "value": ncell / (ms * 1e-3), "unit": UNIT,
+                    "hbm_frac": BYTES_PER_UPDATE[pname] * ncell / (ms * 1e-3) / 1e9 / peak,
+                    "kernel": KERNEL_NAMES.get(g.info().kernel, g.info().kernel),
+                    "tile": list(g.info().tile) if kern == hj.HJ_KERNEL_TILED else None}
+            torch.cuda.empty_cache()
+    return res
+
+
 def run_ours(args):
     import torch
     world, rank, local = dist_env()
@@ -310,6 +345,10 @@ def run_ours(args):
     if args.small_only:
         if rank == 0:
             print(json.dumps({"small_configs": run_small(hj, scenes, torch, torch.cuda.current_stream())}))
+        return 0
+    if args.large_only:
+        if rank == 0:
+            print(json.dumps({"large_grid": run_large(hj, scenes, torch, torch.cuda.current_stream())}))
         return 0
 
     w = scenes.workload(WORKLOAD)
@@ -685,6 +724,8 @@ def main():
     ap.add_argument("--no-small", action="store_true")
     ap.add_argument("--small-only", action="store_true",
                     help="time only the small workloads and the paper's room (prints their JSON; not a bench line)")
+    ap.add_argument("--large-only", action="store_true",
+                    help="time only the 2048x2048x32x33 grid, tiled and generic kernels (prints its JSON; not a bench line)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
