@@ -112,7 +112,9 @@ typedef enum {
 typedef enum {
     HJ_KERNEL_AUTO = 0,
     HJ_KERNEL_GENERIC = 1, /* one thread per cell, loads through L1/L2 */
-    HJ_KERNEL_TILED = 2,   /* FP32, Q5.27: TMA-staged 4D tiles streamed along x */
+    HJ_KERNEL_TILED = 2,   /* FP32, Q5.27 car grids (theta periodic, x, y, v not; theta rows of at
+                            * most 256 points; every size the API accepts): TMA-staged 4D tiles
+                            * streamed along x */
     HJ_KERNEL_RESIDENT = 3 /* the per-cell update of HJ_KERNEL_GENERIC (identical results, any
                             * precision and grid of fewer than 2^32 values whose coefficient
                             * tables fit in shared memory), the whole time loop in one
