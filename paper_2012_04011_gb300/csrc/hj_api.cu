@@ -36,9 +36,11 @@ hj_status set_err(hj_status s, const char *fmt, ...)
 #define HJ_CUDA(call)                                                                                 \
     do {                                                                                              \
         cudaError_t e_ = (call);                                                                      \
-        if (e_ != cudaSuccess)                                                                        \
+        if (e_ != cudaSuccess) {                                                                      \
+            cudaGetLastError(); /* a failed call (not a sticky fault) must not fail later checks */   \
             return set_err(e_ == cudaErrorMemoryAllocation ? HJ_ERR_OOM : HJ_ERR_CUDA, "%s: %s (%s:%d)", \
                            #call, cudaGetErrorString(e_), __FILE__, __LINE__);                        \
+        }                                                                                             \
     } while (0)
 
 // ---------------------------------------------------------------- kernels
@@ -357,7 +359,11 @@ hj_status launch_step(hj_grid *g, hj_kernel k)
     cudaError_t e = (k == HJ_KERNEL_TILED)     ? hj_launch_step_tiled(g)
                     : (k == HJ_KERNEL_RESIDENT) ? hj_launch_step_resident(g, 1)
                                                 : hj_launch_step_generic(g);
-    if (e != cudaSuccess) return set_err(HJ_ERR_CUDA, "step launch: %s", cudaGetErrorString(e));
+    if (e != cudaSuccess) {
+        cudaGetLastError();  // a failed call (not a sticky fault) must not fail later checks
+        return set_err(e == cudaErrorMemoryAllocation ? HJ_ERR_OOM : HJ_ERR_CUDA, "step launch: %s",
+                       cudaGetErrorString(e));
+    }
     return HJ_OK;
 }
 
@@ -595,6 +601,7 @@ hj_status hj_create_grid(const int32_t n[4], const double lo[4], const double hi
     for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaEventCreate(&g->ev[i]);
     if (e == cudaSuccess && g->own_stream) e = cudaEventCreateWithFlags(&g->ev_in, cudaEventDisableTiming);
     if (e != cudaSuccess) {
+        cudaGetLastError();  // the failed allocation must not fail later launch checks
         hj_status s = set_err(e == cudaErrorMemoryAllocation ? HJ_ERR_OOM : HJ_ERR_CUDA, "hj_create_grid: %s",
                               cudaGetErrorString(e));
         free_grid(g);

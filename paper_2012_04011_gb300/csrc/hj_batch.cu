@@ -482,9 +482,11 @@ hj_status bfail(hj_status s, const char *fmt, ...)
 #define HJB_CUDA(call)                                                                                   \
     do {                                                                                                 \
         cudaError_t e_ = (call);                                                                         \
-        if (e_ != cudaSuccess)                                                                           \
+        if (e_ != cudaSuccess) {                                                                         \
+            cudaGetLastError(); /* a failed call (not a sticky fault) must not fail later checks */      \
             return bfail(e_ == cudaErrorMemoryAllocation ? HJ_ERR_OOM : HJ_ERR_CUDA, "%s: %s", #call,      \
                          cudaGetErrorString(e_));                                                        \
+        }                                                                                                \
     } while (0)
 
 void drop_graphs(hj_batch *b)
@@ -787,6 +789,7 @@ hj_status hj_batch_create(int32_t max_slots, size_t memory_budget, void *cuda_st
     if (e == cudaSuccess) e = cudaMemset(b->d_insts, 0, sizeof(BatchInst) * max_slots);
     if (e == cudaSuccess) e = cudaMemset(b->d_ctl, 0, sizeof(BatchCtl));
     if (e != cudaSuccess) {
+        cudaGetLastError();  // the failed allocation must not fail later launch checks
         hj_status s = bfail(e == cudaErrorMemoryAllocation ? HJ_ERR_OOM : HJ_ERR_CUDA, "hj_batch_create: %s",
                             cudaGetErrorString(e));
         hj_batch_destroy(b);

@@ -64,6 +64,7 @@ hj_status run_selftest(int64_t limit_ns, int32_t *status, int64_t *waited_ns, Se
     const size_t bytes = 16 + sizeof(HjResidentSync);
     cudaError_t e = cudaMalloc(&d, bytes);
     if (e != cudaSuccess) {
+        cudaGetLastError();  // the failed allocation must not fail later launch checks
         hj_internal_set_error(cudaGetErrorString(e));
         return e == cudaErrorMemoryAllocation ? HJ_ERR_OOM : HJ_ERR_CUDA;
     }

@@ -359,6 +359,28 @@ def test_errors_on_device(hj):
         assert e.value.status == hj.HJ_ERR_UNSUPPORTED
 
 
+def test_grid_larger_than_device_memory(hj):
+    """A grid the API accepts (2^33 cells at most) but the device cannot hold:
+    8.58e9 FP64 cells with theta rows padded from 5 to 8 values need 3 x 110 GB.
+    Creation reports HJ_ERR_OOM, releases what it had allocated, and the
+    context goes on solving."""
+    import torch
+    n = (2048, 2048, 409, 5)
+    assert np.prod(n, dtype=np.int64) <= 1 << 33
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    with pytest.raises(hj.HjError) as e:
+        hj.hj_create_grid(n, scenes.DOMAIN_LO, scenes.DOMAIN_HI, scenes.PERIODIC_THETA, hj.HJ_FP64)
+    assert e.value.status == hj.HJ_ERR_OOM
+    free1, _ = torch.cuda.mem_get_info()
+    assert abs(free1 - free0) < 64 << 20
+    w = scenes.workload("car4d_31x31x11x16")
+    V0 = scenes.initial_value(w.grid, w.scene)
+    Vo, _ = oracle.solve(oracle_problem(w), V0, w.T, w.cfl)
+    V, _ = gpu_solve(hj, w, V0, hj.HJ_FP64, hj.HJ_KERNEL_AUTO)
+    assert float(np.abs(V - Vo).max()) <= 1e-12
+
+
 # ---------------------------------------------------------------- full size (128x128x64x96)
 
 @pytest.mark.slow
