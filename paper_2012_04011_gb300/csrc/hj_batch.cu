@@ -40,7 +40,7 @@
 namespace {
 
 constexpr int B_MAX_STAGES = 8;
-constexpr int B_VARIANTS[4] = {384, 512, 640, 768};
+constexpr int B_VARIANTS[4] = {352, 480, 608, 736};
 
 struct BatchInst {
     int n1, n2, n3, n4, p4, q4;
@@ -1196,7 +1196,7 @@ hj_status hj_batch_autotune(hj_batch *b, int32_t steps_per_trial, int32_t *best_
     const int keep_nc = b->nconsumer_req, keep_ch = b->xc_mode;
     double best = 1e300;
     int best_nc = keep_nc, best_ch = keep_ch;
-    const int ncs[4] = {384, 512, 640, 768};
+    const int ncs[4] = {B_VARIANTS[0], B_VARIANTS[1], B_VARIANTS[2], B_VARIANTS[3]};
     const int chs[3] = {1, 2, 4};
     for (int a = 0; a < 4; ++a)
         for (int c = 0; c < 3; ++c) {
