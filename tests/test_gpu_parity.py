@@ -368,7 +368,9 @@ def test_grid_larger_than_device_memory(hj):
     n = (2048, 2048, 409, 5)
     assert np.prod(n, dtype=np.int64) <= 1 << 33
     torch.cuda.synchronize()
-    free0, _ = torch.cuda.mem_get_info()
+    free0, total = torch.cuda.mem_get_info()
+    if 3 * 8 * 8 * n[0] * n[1] * n[2] <= total:  # V0 and two buffers, 8-value rows of doubles
+        pytest.skip("this device could hold the grid")
     with pytest.raises(hj.HjError) as e:
         hj.hj_create_grid(n, scenes.DOMAIN_LO, scenes.DOMAIN_HI, scenes.PERIODIC_THETA, hj.HJ_FP64)
     assert e.value.status == hj.HJ_ERR_OOM
