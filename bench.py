@@ -40,11 +40,21 @@ KERNEL_NAMES = {1: "generic", 2: "tiled", 3: "resident"}
 PROFILE = os.path.join(ROOT, "profiles", "hj_step_tiled_car4d_128x128x64x96.md")
 KERNEL_SOURCES = ["hj_tiled_kernel.cuh", "hj_tiled_f32.cu", "hj_device.cuh", "hj_tma.cuh", "hj_scaled.cuh",
                   "hj_internal.h"]
-# FP64 path: bound by the FP64 unit.  Algorithmic FP64 flops per cell-update:
-# 1 DMUL + 5 DFMA = 11; nominal GB300 FP64 rate 1.25 TFLOP/s (no measured FP64
-# figure in MEASURED_PEAKS.json).
-FP64_FLOPS_PER_UPDATE = 11
-FP64_PEAK_TFLOPS = 1.25
+# FP64 path: bound by the FP64 unit.  Algorithmic FP64 flops per cell-update
+# of the FP64 step kernel: V_new = w0 V_c + |w1| V_up1 + |w2| V_up2 + dt k3
+# V_up3 + w4 V_up4 with the dt-scaled table, 1 DMUL + 4 DFMA = 9 flops (the
+# BRT min is an integer compare of the bit patterns).  The peak is measured
+# in the run by the library's FP64 FMA probe; the nominal GB300 figure is the
+# fallback only if the probe cannot run.
+FP64_FLOPS_PER_UPDATE = 9
+FP64_NOMINAL_TFLOPS = 1.25
+# Query kernel: FP64 flops per query, counted from its source: the cell
+# search (3 flops on each of the three clamped axes, 6 on the periodic one),
+# 15 linear interpolations for V and 11 for the gradient (a difference and an
+# FMA each: 3 flops) and 4 multiplications by the reciprocal spacings.  The
+# 16 float-to-double conversions and 4 floors also run on the FP64 unit but
+# are not flops.
+QUERY_FP64_FLOPS = 3 * 3 + 6 + 3 * 15 + 3 * 11 + 4
 
 
 # ------------------------------------------------------------------ helpers
@@ -168,6 +178,54 @@ def visible_gpu_index(local_rank: int) -> int:
     return local_rank
 
 
+def measure_fp64_peak(hj, torch, stream, gpu_index, iters=4096, launches=5):
+    """FP64 FMA throughput of this GPU, from the library's probe kernel:
+    CUDA events on the launching stream around `launches` launches after two
+    warm-up launches, SM clocks sampled meanwhile.  2 flops per FMA."""
+    for _ in range(2):
+        hj.hj_fp64_fma_probe(iters, 8, stream.cuda_stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(gpu_index) as cs:
+        e0.record(stream)
+        fmas = 0
+        for _ in range(launches):
+            fmas += hj.hj_fp64_fma_probe(iters, 8, stream.cuda_stream)
+        e1.record(stream)
+        e1.synchronize()
+        time.sleep(0.25)  # let the sampler see the clocks of the run
+    ms = e0.elapsed_time(e1)
+    clk = cs.summary()
+    tflops = 2.0 * fmas / (ms * 1e-3) / 1e12
+    return {"tflops": tflops, "ms_per_launch": ms / launches, "fma_per_launch": fmas // launches,
+            "sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"],
+            "tflops_x_mhz_ratio": (tflops / clk["sm_mhz"] * clk["sm_max_mhz"]) if clk["sm_mhz"] else None,
+            "how": "hj_fp64_fma_probe: 8 CTAs of 256 threads per SM, 8 independent DFMA chains of "
+                   f"{iters} steps per thread, {launches} launches timed with CUDA events"}
+
+
+def oracle_accuracy(w, V0, results_host, nthreads):
+    """Every precision's full-horizon result on the workload against the FP64
+    oracle's solve of the same input: max |V - V_oracle| and the BRT sign
+    flips among cells with |V_oracle| >= 1e-3."""
+    import oracle
+    P = oracle.Problem(w.grid.n, w.grid.lo, w.grid.hi, w.grid.periodic, oracle.DYN_CAR4D, (w.a_max, w.w_max))
+    t0 = time.perf_counter()
+    Vo, dts = oracle.solve(P, V0, w.T, w.cfl, nthreads=nthreads)
+    el = time.perf_counter() - t0
+    band = np.abs(Vo) >= 1e-3
+    out = {"oracle": {"time_steps": len(dts), "dt_first": float(dts[0]), "dt_last": float(dts[-1]),
+                      "seconds": el, "threads": nthreads}, "sign_band": 1e-3,
+           "fp32_tolerance": 1e-4 * float(np.abs(V0).max()), "fp64_tolerance": 1e-12}
+    for name, (V, st) in results_host.items():
+        V = V.reshape(Vo.shape)
+        out[name] = {"max_abs_vs_oracle": float(np.abs(V - Vo).max()),
+                     "sign_flips_vs_oracle": int(np.count_nonzero(np.sign(V[band]) != np.sign(Vo[band]))),
+                     "time_steps_equal": st[0] == len(dts),
+                     "dt_first_last_equal": st[1] == dts[0] and st[2] == dts[-1]}
+    return out
+
+
 # ------------------------------------------------------------------ oracle (CPU baseline)
 
 def oracle_sample(w, V0, steps: int, nthreads: int):
@@ -225,14 +283,16 @@ def run_reference(args):
 
 # ------------------------------------------------------------------ our arm
 
-def run_small(hj, scenes, torch, stream):
+def run_small(hj, scenes, torch, stream, with_oracle=True):
     """The small single-instance workloads and the paper's own experiment
     (all fit in the 129 MB L2, so they are reported as cell-updates/s and
     solve latency, not against HBM).  Each precision runs the kernel
     HJ_KERNEL_AUTO picks (the resident kernel for FP32 and Q5.27 grids this
-    small) and, for comparison, the per-step kernel it replaces; every result
-    is held against the FP64 solve (which matches the oracle to 1e-12 in the
-    parity tests): max |difference| and BRT sign flips."""
+    small) and, for comparison, the per-step kernel it replaces.  With
+    with_oracle, every result is held against the FP64 oracle's solve of the
+    same input (max |difference| and BRT sign flips among cells with
+    |V_oracle| >= 1e-3), and the oracle's own solve is timed on the host
+    cores: all of them, and one thread for the 31x31x11x16 grid."""
     def time_small(wl, prec, kernel, dyn, params, v0d, reps=5):
         gs = hj.Grid(wl.grid.n, wl.grid.lo, wl.grid.hi, wl.grid.periodic, prec, stream.cuda_stream)
         gs.set_dynamics(dyn, params)
@@ -260,10 +320,18 @@ def run_small(hj, scenes, torch, stream):
                 "value": v0d.numel() * st_.steps / (med * 1e-3), "unit": UNIT,
                 "kernel": KERNEL_NAMES.get(kern, kern)}, o
 
-    def vs_fp64(o, ref):
-        d = (o - ref).abs()
-        m = ref.abs() >= 1e-3
-        return float(d.max().item()), int((torch.sign(o[m]) != torch.sign(ref[m])).sum().item())
+    def vs_oracle(o, Vo):
+        V = o.cpu().numpy().reshape(Vo.shape)  # FP64 values (a Q5.27 grid reads back code * 2^-27)
+        m = np.abs(Vo) >= 1e-3
+        return float(np.abs(V - Vo).max()), int(np.count_nonzero(np.sign(V[m]) != np.sign(Vo[m])))
+
+    def oracle_solve(ws_, dyn, params, V0, nthreads):
+        import oracle
+        okind = oracle.DYN_CAR4D_STEER if dyn == hj.HJ_DYN_CAR4D_STEER else oracle.DYN_CAR4D
+        P = oracle.Problem(ws_.grid.n, ws_.grid.lo, ws_.grid.hi, ws_.grid.periodic, okind, params)
+        t0 = time.perf_counter()
+        Vo, dts = oracle.solve(P, V0, ws_.T, ws_.cfl, nthreads=nthreads)
+        return Vo, dts, time.perf_counter() - t0
 
     small = {}
     cases = [(name, scenes.workload(name), hj.HJ_DYN_CAR4D, None)
@@ -271,16 +339,23 @@ def run_small(hj, scenes, torch, stream):
     cases.append(("paper_room_60x60x20x36_steer", scenes.paper_room(1), hj.HJ_DYN_CAR4D_STEER, scenes.PAPER_STEER))
     for name, ws_, dyn, params in cases:
         params = params or (ws_.a_max, ws_.w_max)
-        v0s = torch.from_numpy(scenes.initial_value(ws_.grid, ws_.scene)).to("cuda")
+        V0h = scenes.initial_value(ws_.grid, ws_.scene)
+        v0s = torch.from_numpy(V0h).to("cuda")
         res = {}
-        ref = None
+        Vo = None
+        if with_oracle:
+            nth = cpu_threads()
+            Vo, dts, el = oracle_solve(ws_, dyn, params, V0h, nth)
+            res["oracle"] = {"seconds_per_solve": el, "threads": nth, "time_steps": len(dts),
+                             "value": V0h.size * len(dts) / el, "unit": UNIT}
+            if name == "car4d_31x31x11x16":
+                _, _, el1 = oracle_solve(ws_, dyn, params, V0h, 1)
+                res["oracle"]["seconds_per_solve_one_thread"] = el1
         for pname, pr, per_step in (("f64", hj.HJ_FP64, None), ("f32", hj.HJ_FP32, hj.HJ_KERNEL_TILED),
                                     ("q527", hj.HJ_Q527, hj.HJ_KERNEL_TILED)):
             r, o = time_small(ws_, pr, hj.HJ_KERNEL_AUTO, dyn, params, v0s)
-            if ref is None:
-                ref = o
-            else:
-                r["max_abs_vs_fp64"], r["sign_flips_vs_fp64"] = vs_fp64(o, ref)
+            if Vo is not None:
+                r["max_abs_vs_oracle"], r["sign_flips_vs_oracle"] = vs_oracle(o, Vo)
             if per_step is not None:
                 rp, _ = time_small(ws_, pr, per_step, dyn, params, v0s)
                 r["per_step_kernel"] = {k: rp[k] for k in ("kernel", "ms_per_solve_median", "us_per_step")}
@@ -292,6 +367,37 @@ def run_small(hj, scenes, torch, stream):
             small[name]["published_fpga_brt_ms"] = 176.0
             small[name]["dynamics"] = "steering car, a in [-1.5, 1.5], delta in [-pi/18, pi/18], L = 0.3 m"
     return small
+
+
+DEADLINE_MS = 200.0  # the paper's 5 Hz re-solve rate (Sec. IV-C)
+
+
+def saturation_sweep(srv_mod, scenes, stream, sizes, rates, seconds, seed0):
+    """Poisson traces at rising rates, replayed in real time through the FP32
+    server (continuous batching) and through the plain FP64 path.  An arm
+    stops at the first rate whose p99 latency reaches the deadline; its
+    saturation point is the highest rate it served with p99 below it."""
+    rows, alive, sat = {}, {"fp32_batched": True, "fp64_plain": True}, {"fp32_batched": None, "fp64_plain": None}
+    for rate in rates:
+        if not any(alive.values()):
+            break
+        trs = scenes.serving_trace(rate, seconds, seed=seed0 + int(rate), sizes=sizes)
+        row = {"requests": len(trs)}
+        for arm, fn in (("fp32_batched", srv_mod.run_server), ("fp64_plain", srv_mod.run_plain_fp64)):
+            if not alive[arm]:
+                continue
+            r = fn(trs, cuda_stream=stream.cuda_stream)
+            lat = r["latency_ms"]
+            row[arm] = {"p50": lat["p50"], "p99": lat["p99"], "served_req_per_s": len(trs) / r["wall_s"],
+                        "cell_updates_per_s": r["cell_updates_per_s"]}
+            if lat["p99"] is not None and lat["p99"] < DEADLINE_MS:
+                sat[arm] = {"req_per_s": rate, **row[arm]}
+            else:
+                alive[arm] = False
+        rows[f"{rate:g}"] = row
+    return {"sizes": ["x".join(map(str, s)) for s in sizes], "seconds_per_rate": seconds,
+            "deadline_ms": DEADLINE_MS, "req_per_s": rows, "saturation": sat,
+            "note": "saturation = the highest swept rate whose p99 stayed below the deadline; null = none did"}
 
 
 LARGE_GRID = (2048, 2048, 32, 33)
@@ -381,6 +487,7 @@ def run_ours(args):
 
     results = {}
     accuracy = None
+    results_host = {}  # precision -> (V as FP64 host array, (steps, dt_first, dt_last)) of the 4D-V0 car solves
     for prec_name, prec, out, K, W in (("f32", hj.HJ_FP32, out32, args.steps, args.warmup),
                                        ("f64", hj.HJ_FP64, out64, max(1, min(args.steps, args.fp64_steps)), 1),
                                        ("q527", hj.HJ_Q527, outq, max(1, min(args.steps, args.q527_steps)), 1),
@@ -436,16 +543,9 @@ def run_ours(args):
         ms = max_over_ranks(ev0.elapsed_time(ev1))
         kernel = g.info().kernel
         g.close()
-        if prec_name == "f64" and "f32" in results:
-            # the FP32 result (still in out32) against the FP64 one, which
-            # matches the oracle to 1e-12 in the parity tests
-            d32 = (out32.double() - out64).abs()
-            band = out64.abs() >= 1e-3
-            accuracy = {"max_abs_fp32_vs_fp64": float(d32.max().item()),
-                        "tolerance": 1e-4 * float(V0_dev.abs().max().item()),
-                        "sign_flips_fp32_vs_fp64": int((torch.sign(out32.double()[band]) !=
-                                                        torch.sign(out64[band])).sum().item()),
-                        "sign_band": 1e-3}
+        if prec_name in ("f32", "f64", "q527"):
+            vals = out.double() * (2.0 ** -27) if prec_name == "q527" else out.double()
+            results_host[prec_name] = (vals.cpu().numpy(), (st.steps, st.dt_first, st.dt_last))
         results[prec_name] = {
             "ms_total": ms, "K": K, "value": job_throughput(world, ncell * steps_total, ms * 1e-3), "ms_per_step": ms / K,
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
@@ -483,12 +583,11 @@ def run_ours(args):
         qbytes = 32 + 8 + 32 + 16 + 16 * 4  # state in, value, gradient, control out, 16 grid values
         query = {"workload": f"{mq} random states on the solved {WORKLOAD} FP32 grid: value, gradient, u_opt",
                  "value": job_throughput(world, mq, qms * 1e-3), "unit": "queries/s", "ms_per_call": qms,
-                 "roofline": {"bound": "hbm", "achieved": qbytes * mq / (qms * 1e-3) / 1e9,
-                              "peak": measured_peaks()[0], "unit": "GB/s",
-                              "frac": qbytes * mq / (qms * 1e-3) / 1e9 / measured_peaks()[0],
-                              "bytes_per_query": qbytes}}
+                 "hbm": {"achieved_gbs": qbytes * mq / (qms * 1e-3) / 1e9,
+                         "frac": qbytes * mq / (qms * 1e-3) / 1e9 / measured_peaks()[0], "bytes_per_query": qbytes}}
 
-    small = None if args.no_small else run_small(hj, scenes, torch, stream)
+    small = None if args.no_small else run_small(hj, scenes, torch, stream, with_oracle=world == 1)
+    fp64_peak = measure_fp64_peak(hj, torch, stream, visible_gpu_index(local))
 
     # batched solves: the 64-instance workload (uneven grids, own obstacles,
     # T = 1.5 s), V0 already on the device, one persistent kernel per batch step
@@ -552,18 +651,16 @@ def run_ours(args):
                    "mixed_sizes_fp32_batched": {"sizes": "31x31x11x16, 60x60x20x36, 80x80x25x40, 100x100x30x48",
                                                 **{k: mixed[k] for k in ("requests", "latency_ms",
                                                                          "cell_updates_per_s")}}}
-        # the arrival rates of the serving workload (5-40 req/s), mixed sizes,
-        # FP32 batched against the plain FP64 path, p50 / p99 latency (ms)
-        sweep = {}
-        for rate in args.serving_sweep:
-            trs = scenes.serving_trace(rate, args.serving_sweep_seconds, seed=scenes.SEED_BASE + 40 + int(rate))
-            a = srv_mod.run_server(trs, cuda_stream=stream.cuda_stream)
-            b = srv_mod.run_plain_fp64(trs, cuda_stream=stream.cuda_stream)
-            sweep[f"{rate:g}"] = {"requests": a["requests"],
-                                  "fp32_batched": {k: a["latency_ms"][k] for k in ("p50", "p99")},
-                                  "fp64_plain": {k: b["latency_ms"][k] for k in ("p50", "p99")}}
-        if sweep:
-            serving["rate_sweep_mixed_sizes"] = {"seconds_per_rate": args.serving_sweep_seconds, "req_per_s": sweep}
+        # rising arrival rates, FP32 continuous batching against the plain
+        # FP64 path, each arm until its p99 reaches the 200 ms deadline: the
+        # 60x60x20x36 re-solves, then the mixed sizes
+        if args.serving_sweep:
+            serving["rate_sweep_60x60x20x36"] = saturation_sweep(
+                srv_mod, scenes, stream, ((60, 60, 20, 36),), args.serving_sweep, args.serving_sweep_seconds,
+                scenes.SEED_BASE + 200)
+            serving["rate_sweep_mixed_sizes"] = saturation_sweep(
+                srv_mod, scenes, stream, scenes.SERVING_SIZES, args.serving_sweep, args.serving_sweep_seconds,
+                scenes.SEED_BASE + 40)
 
     # end to end through the C ABI with host buffers (pinned), copies timed
     e2e = None
@@ -634,19 +731,29 @@ def run_ours(args):
     if "f64" in results:
         r64 = results["f64"]
         # the FP64 path is bound by the FP64 ALU on this GPU, not by HBM
+        fpk = fp64_peak["tflops"] if fp64_peak else FP64_NOMINAL_TFLOPS
+        fpk_src = ("measured in this run by hj_fp64_fma_probe (DFMA throughput)" if fp64_peak
+                   else "nominal GB300 FP64 rate (the probe did not run)")
+        a64 = FP64_FLOPS_PER_UPDATE * ncell / (r64["avg_step_kernel_ms"] * 1e-3) / 1e12
         line["fp64_path"] = {
             "value": r64["value"], "unit": UNIT, "ms_per_step": r64["ms_per_step"], "steps": r64["K"],
             "latency_ms": r64["latency_ms"], "avg_step_kernel_ms": r64["avg_step_kernel_ms"],
             "hbm_frac": BYTES_PER_UPDATE["f64"] * ncell / (r64["avg_step_kernel_ms"] * 1e-3) / 1e9 / peak,
-            "roofline": {"bound": "alu", "kernel": "hj_step_generic_kernel<double>",
-                         "achieved": FP64_FLOPS_PER_UPDATE * ncell / (r64["avg_step_kernel_ms"] * 1e-3) / 1e12,
-                         "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": FP64_FLOPS_PER_UPDATE * ncell / (r64["avg_step_kernel_ms"] * 1e-3) / 1e12
-                         / FP64_PEAK_TFLOPS,
-                         "peak_source": "nominal GB300 FP64 rate (profiling recipe table)",
-                         "flops_per_update": FP64_FLOPS_PER_UPDATE},
+            "roofline": {"bound": "alu", "kernel": "hj_step_generic_kernel<double>", "achieved": a64,
+                         "peak": fpk, "unit": "TFLOP/s", "frac": a64 / fpk, "peak_source": fpk_src,
+                         "flops_per_update": FP64_FLOPS_PER_UPDATE,
+                         "flops_counted": "1 DMUL + 4 DFMA per cell-update (dt folded into the coefficient table)"},
             "speedup_fp32_over_fp64": r32["value"] / r64["value"],
         }
+    line["fp64_peak"] = fp64_peak
+    if query is not None:
+        fpk = fp64_peak["tflops"] if fp64_peak else FP64_NOMINAL_TFLOPS
+        aq = QUERY_FP64_FLOPS * query["value"] / world / 1e12
+        query["roofline"] = {"bound": "alu", "kernel": "query_kernel<float>", "achieved": aq, "peak": fpk,
+                             "unit": "TFLOP/s", "frac": aq / fpk, "flops_per_query": QUERY_FP64_FLOPS,
+                             "peak_source": "fp64_peak" if fp64_peak else "nominal GB300 FP64 rate",
+                             "note": "FP64 flops only; 16 float-to-double conversions and 4 floors per query "
+                                     "also occupy the FP64 unit"}
     if "q527" in results:
         rq = results["q527"]
         # Q5.27 codes move like FP32 (4 bytes); Sec. IV-B's error table compares
@@ -686,6 +793,9 @@ def run_ours(args):
                          "bytes_per_update": BYTES_PER_UPDATE["f32"], "peak_source": f"{peak_kind} hbm_gbs"},
             "tile": {k: v for k, v in (rs["tile"] or {}).items() if k != "tried"},
         }
+    if world == 1 and not args.no_oracle_accuracy and results_host:
+        # after every timed region: the oracle's full solve of the same input
+        line["accuracy"] = oracle_accuracy(w, V0, results_host, cpu_threads())
     if world == 1 and not args.no_cpu_baseline:
         nthreads = cpu_threads()
         rate, el, nst = oracle_sample(w, V0, args.cpu_sample_steps, nthreads)
@@ -728,6 +838,8 @@ def main():
                     help="time only the 2048x2048x32x33 grid, tiled and generic kernels (prints its JSON; not a bench line)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-oracle-accuracy", action="store_true",
+                    help="skip the oracle's full solve of the workload (about 75 s on 16 cores)")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--tile", default="", help="fixed tile shape ty,tv,xc,stages instead of autotuning")
     ap.add_argument("--no-batch", action="store_true")
@@ -735,8 +847,10 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serving-rate", type=float, default=40.0)
     ap.add_argument("--serving-seconds", type=float, default=4.0)
-    ap.add_argument("--serving-sweep", type=float, nargs="*", default=[5.0, 10.0, 20.0, 40.0])
-    ap.add_argument("--serving-sweep-seconds", type=float, default=2.0)
+    ap.add_argument("--serving-sweep", type=float, nargs="*",
+                    default=[5.0, 10.0, 20.0, 40.0, 80.0, 120.0, 160.0, 240.0, 320.0, 480.0, 640.0, 960.0, 1280.0,
+                             1920.0, 2560.0, 3840.0, 5120.0])
+    ap.add_argument("--serving-sweep-seconds", type=float, default=1.5)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("note: fewer than 3 warm-up steps", file=sys.stderr)

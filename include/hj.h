@@ -303,9 +303,13 @@ HJ_API hj_status hj_autotune(hj_grid *g, int32_t steps_per_trial, hj_tile_result
  * Computes v_out = min(v0, v_in + dt * rate(v_in)) for every cell: the same
  * step as hj_advance_brt, with the dt the caller gives (>= 0, finite).
  * Arrays are dense [N1][N2][N3][N4] of double (HJ_FP64) or float (HJ_FP32)
- * on the current device; v_out must not overlap v_in.  Grid, periodic mask
- * and dynamics are as for hj_create_grid and hj_set_dynamics (HJ_DYN_CAR4D
- * and HJ_DYN_CONST; other kinds give HJ_ERR_INVALID_ARG).
+ * on the current device, owned by the caller; `bytes` is the size of each of
+ * the three arrays and must equal N1*N2*N3*N4 * sizeof(element), and v_out
+ * must overlap neither v_in nor v0 (HJ_ERR_INVALID_ARG otherwise: the library
+ * cannot see the arrays' real sizes, so a short array would be overrun).
+ * Grid, periodic mask and dynamics are as for hj_create_grid and
+ * hj_set_dynamics (HJ_DYN_CAR4D and HJ_DYN_CONST; other kinds give
+ * HJ_ERR_INVALID_ARG).
  * alpha_max_out (host, may be NULL) receives alpha_d^max over the grid, from
  * which a caller forms the next CFL step (dt = CFL / sum_d alpha_d^max/dx_d).
  *
@@ -318,12 +322,14 @@ HJ_API hj_status hj_autotune(hj_grid *g, int32_t steps_per_trial, hj_tile_result
  * before any stream capture.  All calls share the array and it keeps the
  * last call's contents (each call clears what must start at zero), so calls
  * whose work overlaps on the GPU race with one another: serialise them on
- * one stream.  Runs on cuda_stream (NULL: the legacy default stream) and
- * returns when the step is complete. */
+ * one stream.  Runs on cuda_stream (NULL: the legacy default stream); every
+ * call reads alpha^max back and synchronises cuda_stream before it returns,
+ * so it blocks until the step is complete.  A CUDA error left pending by the
+ * caller's earlier work is cleared at entry and not reported as this call's. */
 HJ_API hj_status hj_step_noalloc(const int32_t n[4], const double lo[4], const double hi[4], uint32_t periodic_mask,
                                  hj_precision prec, hj_dynamics kind, const double *params, int32_t nparams,
-                                 const void *v_in, const void *v0, void *v_out, double dt, void *cuda_stream,
-                                 double alpha_max_out[4]);
+                                 const void *v_in, const void *v0, void *v_out, size_t bytes, double dt,
+                                 void *cuda_stream, double alpha_max_out[4]);
 
 /* ---- Batches: many independent car grids stepped together ---------------
  *
@@ -499,6 +505,17 @@ HJ_API hj_status hj_wait_selftest(int64_t limit_ns, int32_t *status, int64_t *wa
  * the resident kernel reports when a barrier runs out.  Same outputs and
  * side effects as hj_wait_selftest. */
 HJ_API hj_status hj_barrier_selftest(int64_t limit_ns, int32_t *status, int64_t *waited_ns);
+
+/* FP64 fused multiply-add throughput probe.  The paper has no counterpart:
+ * it measures the FP64 rate that the FP64 step kernel and the query kernel
+ * are held against (their roofline).  Launches one kernel on cuda_stream
+ * (NULL: the legacy default stream) of blocks_per_sm (1..64) x SMs CTAs of
+ * 256 threads, each thread running 8 independent chains of `iters`
+ * (1..2^40) dependent FMAs.  *fma_out (may be NULL) = the FMAs issued (2
+ * flops each).  Asynchronous: time it with events on cuda_stream.  Allocates
+ * nothing; HJ_ERR_INVALID_ARG for out-of-range arguments, HJ_ERR_CUDA if the
+ * launch fails. */
+HJ_API hj_status hj_fp64_fma_probe(int64_t iters, int32_t blocks_per_sm, void *cuda_stream, int64_t *fma_out);
 
 /* Free all device and host resources of the grid (NULL is a no-op). */
 HJ_API void hj_destroy_grid(hj_grid *g);

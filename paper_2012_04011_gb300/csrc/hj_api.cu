@@ -135,7 +135,7 @@ __global__ void prologue_kernel(HjDevState *st, const HjGeom g, const HjCoef<T> 
     const bool fresh = st->n == 0 || st->alpha_stale;
     if (fresh)
         for (int i = threadIdx.x; i < ncoef; i += blockDim.x) {
-            unsigned long long b1 = hj_abits((double)coef[i].a1), b2 = hj_abits((double)coef[i].a2);
+            unsigned long long b1 = hj_abits(coef[i].a1), b2 = hj_abits(coef[i].a2);
             a1 = a1 > b1 ? a1 : b1;
             a2 = a2 > b2 ? a2 : b2;
         }
@@ -304,8 +304,8 @@ hj_status upload_tables(hj_grid *g)
             c[i].c1 = (float)c1;
             c[i].c2 = (float)c2;
             c[i].ks = (float)(fabs(c1) + fabs(c2) + k3 + k4v[i / N4]);
-            c[i].a1 = (float)fabs(f1[i]);
-            c[i].a2 = (float)fabs(f2[i]);
+            c[i].a1 = fabs(f1[i]);
+            c[i].a2 = fabs(f2[i]);
         }
         if (c) {
             cudaError_t e = cudaMemcpy(g->coef, c, sizeof(HjCoef<float>) * nco, cudaMemcpyHostToDevice);

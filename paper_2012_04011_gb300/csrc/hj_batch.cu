@@ -334,21 +334,20 @@ __global__ void __launch_bounds__(MAXC + 32, 1)
 
             // alpha^max partials of this warp for the slot, then count the
             // warp done; the warp completing the slot's step finalises it
-            float a1 = 0.f, a2 = 0.f;
+            // (FP64 |xdot_1|, |xdot_2| of the table: the slot's dt is the FP64 one)
+            unsigned long long a1 = 0ull, a2 = 0ull;
             if (rok)
                 for (int e = 0; e < lreal; ++e) {
-                    const HjCoef<float> c = I.coef[v * N4 + 4 * q + e];
-                    a1 = fmaxf(a1, c.a1);
-                    a2 = fmaxf(a2, c.a2);
+                    const unsigned long long b1 = hj_abits(I.coef[v * N4 + 4 * q + e].a1);
+                    const unsigned long long b2 = hj_abits(I.coef[v * N4 + 4 * q + e].a2);
+                    a1 = a1 > b1 ? a1 : b1;
+                    a2 = a2 > b2 ? a2 : b2;
                 }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                a1 = fmaxf(a1, __shfl_xor_sync(0xffffffffu, a1, o));
-                a2 = fmaxf(a2, __shfl_xor_sync(0xffffffffu, a2, o));
-            }
+            a1 = hj_warp_max_u64(a1);
+            a2 = hj_warp_max_u64(a2);
             if (lane == 0) {
-                atomicMax(&sl->st.alpha_bits[0], hj_abits((double)a1));
-                atomicMax(&sl->st.alpha_bits[1], hj_abits((double)a2));
+                atomicMax(&sl->st.alpha_bits[0], a1);
+                atomicMax(&sl->st.alpha_bits[1], a2);
                 __threadfence();
                 const unsigned int per_step = (unsigned int)nconsumer_warps * (unsigned int)I.nitems;
                 const unsigned int prev_done = atomicAdd(&sl->warps_done, 1u);
@@ -537,8 +536,8 @@ hj_status upload_slot_tables(hj_batch *b, SlotHost &s)
             e.c1 = (float)c1;
             e.c2 = (float)c2;
             e.ks = (float)(fabs(c1) + fabs(c2) + k3 + k4);
-            e.a1 = (float)fabs(f1);
-            e.a2 = (float)fabs(f2);
+            e.a1 = fabs(f1);
+            e.a2 = fabs(f2);
         }
     }
     for (int l = 0; l < N4; ++l) {

@@ -72,10 +72,13 @@ struct HjGeom {
 };
 
 // Per-(v, theta) coefficients: c1 = xdot_1/dx_1, c2 = xdot_2/dx_2 (signed),
-// ks = |c1| + |c2| + k3 + k4, a1 = |xdot_1|, a2 = |xdot_2|.
+// ks = |c1| + |c2| + k3 + k4 in the working precision; a1 = |xdot_1|,
+// a2 = |xdot_2| in FP64 for every precision, so that alpha^max, and with it
+// the dt sequence of Algorithm 1, is the FP64 one whatever V is stored in.
 template <typename T>
 struct HjCoef {
-    T c1, c2, ks, a1, a2;
+    T c1, c2, ks;
+    double a1, a2;
 };
 
 struct hj_grid {

@@ -65,8 +65,8 @@ __global__ void noalloc_init_kernel(HjDevState *st, HjCoef<T> *coef, const HjGeo
         c.c1 = (T)q1;
         c.c2 = (T)q2;
         c.ks = (T)(fabs(q1) + fabs(q2) + g.k3 + g.k4);
-        c.a1 = (T)fabs(f1);
-        c.a2 = (T)fabs(f2);
+        c.a1 = fabs(f1);
+        c.a2 = fabs(f2);
         coef[i] = c;
     }
 }
@@ -129,7 +129,7 @@ __global__ void __launch_bounds__(256) noalloc_step_kernel(const T *__restrict__
         r = noalloc_fma(k3, u3 - vc, r);
         r = noalloc_fma(k4, u4 - vc, r);
         vout[o] = hj_min(v0[o], noalloc_fma(dt, r, vc));
-        const unsigned long long b1 = hj_abits((double)cf.a1), b2 = hj_abits((double)cf.a2);
+        const unsigned long long b1 = hj_abits(cf.a1), b2 = hj_abits(cf.a2);
         am1 = am1 > b1 ? am1 : b1;
         am2 = am2 > b2 ? am2 : b2;
     }
@@ -185,10 +185,11 @@ extern "C" {
 
 hj_status hj_step_noalloc(const int32_t n[4], const double lo[4], const double hi[4], uint32_t periodic_mask,
                           hj_precision prec, hj_dynamics kind, const double *params, int32_t nparams,
-                          const void *v_in, const void *v0, void *v_out, double dt, void *cuda_stream,
-                          double alpha_max_out[4])
+                          const void *v_in, const void *v0, void *v_out, size_t bytes, double dt,
+                          void *cuda_stream, double alpha_max_out[4])
 {
     hj_internal_set_error("");
+    (void)cudaGetLastError();  // an error pending from the caller's earlier work is not this call's
     if (!n || !lo || !hi || !params || !v_in || !v0 || !v_out)
         return noalloc_fail(HJ_ERR_INVALID_ARG, "hj_step_noalloc: NULL argument");
     if (prec != HJ_FP64 && prec != HJ_FP32) return noalloc_fail(HJ_ERR_INVALID_ARG, "hj_step_noalloc: unknown precision");
@@ -204,6 +205,17 @@ hj_status hj_step_noalloc(const int32_t n[4], const double lo[4], const double h
         return noalloc_fail(HJ_ERR_INVALID_ARG,
                             "hj_step_noalloc: N3 * N4 exceeds 16384, the size of its fixed working array");
     if (ncell > (1LL << 33)) return noalloc_fail(HJ_ERR_INVALID_ARG, "hj_step_noalloc: grid too large");
+    const size_t want_bytes = (size_t)ncell * (prec == HJ_FP64 ? sizeof(double) : sizeof(float));
+    if (bytes != want_bytes)
+        return noalloc_fail(HJ_ERR_INVALID_ARG,
+                            "hj_step_noalloc: bytes must equal N1*N2*N3*N4 times the element size of prec");
+    {
+        // v_out is written while v_in and v0 are read: the ranges must be disjoint
+        const uintptr_t o0 = (uintptr_t)v_out, o1 = o0 + bytes;
+        const uintptr_t i0 = (uintptr_t)v_in, z0 = (uintptr_t)v0;
+        if ((i0 < o1 && o0 < i0 + bytes) || (z0 < o1 && o0 < z0 + bytes))
+            return noalloc_fail(HJ_ERR_INVALID_ARG, "hj_step_noalloc: v_out overlaps v_in or v0");
+    }
     if (!isfinite(dt) || dt < 0) return noalloc_fail(HJ_ERR_INVALID_ARG, "hj_step_noalloc: dt must be finite and >= 0");
     if (kind == HJ_DYN_CAR4D) {
         if (nparams != 2 || !isfinite(params[0]) || !isfinite(params[1]) || params[0] < 0 || params[1] < 0)

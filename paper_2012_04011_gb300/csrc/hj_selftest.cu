@@ -9,9 +9,37 @@
 // usable.  The grid-barrier self-test does the same for the resident step
 // kernel's barrier (hj_grid_sync): two co-resident CTAs wait for a third
 // arrival that never comes.
+//
+// Also here: the FP64 fused multiply-add throughput probe that the FP64
+// roofline of the FP64 step kernel and of the query kernel is measured
+// against (GB300's FP64 rate is a small fraction of its FP32 rate, so the
+// measured figure, not a nominal one, is the denominator).
 #include "hj_resident.cuh"
 
 namespace {
+
+// Written only when a chain sum is negative, which the probe's inputs never
+// give; the store keeps every chain live without a buffer from the caller.
+__device__ double g_fma_sink;
+
+constexpr int FMA_CHAINS = 8;
+
+// Each thread runs FMA_CHAINS independent DFMA chains x <- x a + b of iters
+// steps (a < 1, b > 0: the chains stay in [0, 1]).
+__global__ void __launch_bounds__(256) fp64_fma_probe_kernel(long long iters, double a, double b)
+{
+    double x[FMA_CHAINS];
+#pragma unroll
+    for (int j = 0; j < FMA_CHAINS; ++j) x[j] = (double)((threadIdx.x + 7 * j) & 255) * (1.0 / 512.0);
+    for (long long i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int j = 0; j < FMA_CHAINS; ++j) x[j] = fma(x[j], a, b);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int j = 0; j < FMA_CHAINS; ++j) s += x[j];
+    if (s < 0.0) g_fma_sink = s;
+}
 
 __global__ void wait_selftest_kernel(unsigned long long limit_ns, int *status, unsigned long long *waited_ns)
 {
@@ -111,4 +139,32 @@ extern "C" hj_status hj_barrier_selftest(int64_t limit_ns, int32_t *status, int6
 extern "C" hj_status hj_wait_selftest(int64_t limit_ns, int32_t *status, int64_t *waited_ns)
 {
     return run_selftest(limit_ns, status, waited_ns, launch_wait);
+}
+
+extern "C" hj_status hj_fp64_fma_probe(int64_t iters, int32_t blocks_per_sm, void *cuda_stream, int64_t *fma_out)
+{
+    hj_internal_set_error("");
+    if (iters < 1 || iters > (1LL << 40) || blocks_per_sm < 1 || blocks_per_sm > 64) {
+        hj_internal_set_error("iters must be in [1, 2^40] and blocks_per_sm in [1, 64]");
+        return HJ_ERR_INVALID_ARG;
+    }
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        hj_internal_set_error(cudaGetErrorString(e));
+        return HJ_ERR_CUDA;
+    }
+    const int blocks = sms * blocks_per_sm, threads = 256;
+    // a = 1 - 2^-20, b = 2^-20: every chain moves toward 1 and stays in [0, 1]
+    fp64_fma_probe_kernel<<<blocks, threads, 0, (cudaStream_t)cuda_stream>>>((long long)iters, 1.0 - 0x1p-20,
+                                                                            0x1p-20);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        hj_internal_set_error(cudaGetErrorString(e));
+        return HJ_ERR_CUDA;
+    }
+    if (fma_out) *fma_out = (int64_t)blocks * threads * FMA_CHAINS * iters;
+    return HJ_OK;
 }

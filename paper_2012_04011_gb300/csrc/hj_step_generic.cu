@@ -225,7 +225,7 @@ __device__ __forceinline__ Cell cell_at(unsigned long long c, const Divisors &dv
 // Per-thread maxima of a step: |xdot_1|, |xdot_2| and the change of V.
 struct StepMax {
     unsigned long long a1 = 0ull, a2 = 0ull, d = 0ull;  // FP64 bit patterns (Q5.27: d in codes)
-    float a1f = 0.f, a2f = 0.f, df = 0.f;               // FP32 kernels
+    float df = 0.f;                                     // FP32 kernels: the change of V
 };
 
 // The maxima as bit patterns of non-negative doubles.
@@ -234,8 +234,8 @@ __device__ __forceinline__ void step_max_bits(const StepMax &m, unsigned long lo
                                               unsigned long long &d)
 {
     if constexpr (std::is_same<T, float>::value) {
-        a1 = hj_abits((double)m.a1f);
-        a2 = hj_abits((double)m.a2f);
+        a1 = m.a1;
+        a2 = m.a2;
         d = hj_abits((double)m.df);
     } else if constexpr (std::is_same<T, double>::value) {
         a1 = m.a1;
@@ -330,7 +330,7 @@ __global__ void __launch_bounds__(256) hj_step_generic_kernel(const T *__restric
     // once per thread
     const double k3dt = g.k3 * st->dt;
     unsigned long long am1 = 0ull, am2 = 0ull, dbits = 0ull;
-    float am1f = 0.f, am2f = 0.f, dmf = 0.f;
+    float dmf = 0.f;
 
     for (unsigned long long c = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; c < ncell;
          c += (unsigned long long)gridDim.x * blockDim.x) {
@@ -398,19 +398,14 @@ __global__ void __launch_bounds__(256) hj_step_generic_kernel(const T *__restric
         }
 
         // alpha_d^max: the largest |xdot_d| among the cells this thread updated
-        // (FP64: integer max of the bit patterns; FP32: float max, widened once)
-        if constexpr (sizeof(T) == 8) {
-            const unsigned long long b1 = hj_abits((double)cf.a1), b2 = hj_abits((double)cf.a2);
+        // (integer max of the FP64 bit patterns, in both precisions)
+        {
+            const unsigned long long b1 = hj_abits(cf.a1), b2 = hj_abits(cf.a2);
             am1 = am1 > b1 ? am1 : b1;
             am2 = am2 > b2 ? am2 : b2;
-        } else {
-            am1f = fmaxf(am1f, (float)cf.a1);
-            am2f = fmaxf(am2f, (float)cf.a2);
         }
     }
     if constexpr (sizeof(T) == 4) {
-        am1 = hj_abits((double)am1f);
-        am2 = hj_abits((double)am2f);
         hj_step_epilogue(st, g, am1, am2, hj_abits((double)dmf), scratch);
     } else {
         hj_step_epilogue_scaled(st, g, am1, am2, dbits, scratch, scaled, nullptr, (const HjCoef<double> *)coef,
@@ -673,7 +668,6 @@ __global__ void __launch_bounds__(RES_THREADS, res_min_blocks<T>()) hj_step_resi
     unsigned long long a1 = 0ull, a2 = 0ull, dz = 0ull;
     if constexpr (F32) {
         const HjCoef<float> *coef = (const HjCoef<float> *)coefp;
-        float m1 = 0.f, m2 = 0.f;
         for (int e = threadIdx.x; e < tot; e += blockDim.x) {
             const int k = e / P4, l = e - k * P4;
             float c1 = 0.f, c2 = 0.f;
@@ -681,15 +675,14 @@ __global__ void __launch_bounds__(RES_THREADS, res_min_blocks<T>()) hj_step_resi
                 const HjCoef<float> c = coef[k * N4 + l];
                 c1 = c.c1;
                 c2 = c.c2;
-                m1 = fmaxf(m1, (float)c.a1);
-                m2 = fmaxf(m2, (float)c.a2);
+                const unsigned long long b1 = hj_abits(c.a1), b2 = hj_abits(c.a2);
+                a1 = a1 > b1 ? a1 : b1;
+                a2 = a2 > b2 ? a2 : b2;
             }
             c1t[e] = c1;
             c2t[e] = c2;
         }
         for (int k = threadIdx.x; k < N3; k += blockDim.x) k4s[k] = ((const float2 *)k4tab)[k].x;
-        a1 = hj_abits((double)m1);
-        a2 = hj_abits((double)m2);
     } else {
         const HjCoef<double> *coef = (const HjCoef<double> *)coefp;
         for (int e = threadIdx.x; e < N3 * N4; e += blockDim.x) {

@@ -121,6 +121,7 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
 {
     const HjCoef<float> *coef = (const HjCoef<float> *)coefv;     // FP32 grids
     const HjCoef<double> *coefd = (const HjCoef<double> *)coefv;  // Q5.27 grids
+    (void)coef;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     if (st->done) return;  // uniform across the grid
 
@@ -151,8 +152,8 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
     }
     __syncthreads();
 
-    float am1 = 0.f, am2 = 0.f;  // this thread's max |xdot_1|, |xdot_2| (non-negative)
-    unsigned long long ab1 = 0ull, ab2 = 0ull;  // the same as FP64 bit patterns (FIXED)
+    // this thread's max |xdot_1|, |xdot_2| (FP64 bit patterns of non-negative values)
+    unsigned long long ab1 = 0ull, ab2 = 0ull;
     // convergence mode (Algorithm 2's epsilon): this thread's largest |V_{n+1} - V_n|
     float dmf = 0.f;
     unsigned int dmq = 0u;  // in codes (FIXED; a change of one step is below 2^32 codes)
@@ -551,16 +552,12 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
             const int y = it.y0 + jy, v = it.v0 + kv;
             if (inrow && y < N2 && v < N3)
                 for (int e = 0; e < lreal; ++e) {
-                    if constexpr (FIXED) {
-                        const HjCoef<double> c = coefd[v * N4 + 4 * q + e];
-                        const unsigned long long b1 = hj_abits(c.a1), b2 = hj_abits(c.a2);
-                        ab1 = ab1 > b1 ? ab1 : b1;
-                        ab2 = ab2 > b2 ? ab2 : b2;
-                    } else {
-                        const HjCoef<float> c = coef[v * N4 + 4 * q + e];
-                        am1 = fmaxf(am1, c.a1);
-                        am2 = fmaxf(am2, c.a2);
-                    }
+                    // the FP64 |xdot_1|, |xdot_2| of the table, in either precision
+                    const double c1 = FIXED ? coefd[v * N4 + 4 * q + e].a1 : coef[v * N4 + 4 * q + e].a1;
+                    const double c2 = FIXED ? coefd[v * N4 + 4 * q + e].a2 : coef[v * N4 + 4 * q + e].a2;
+                    const unsigned long long b1 = hj_abits(c1), b2 = hj_abits(c2);
+                    ab1 = ab1 > b1 ? ab1 : b1;
+                    ab2 = ab2 > b2 ? ab2 : b2;
                 }
         }
     }
@@ -568,7 +565,7 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
         hj_step_epilogue_scaled(st, g, ab1, ab2, hj_abits((double)dmq * (1.0 / HJ_Q527_SCALE)), scratch, nullptr, qw,
                                 coefd, (const double *)k4tab);
     else
-        hj_step_epilogue(st, g, hj_abits((double)am1), hj_abits((double)am2), hj_abits((double)dmf), scratch);
+        hj_step_epilogue(st, g, ab1, ab2, hj_abits((double)dmf), scratch);
 }
 
 typedef void (*KernelFn)(const CUtensorMap, const CUtensorMap, const CUtensorMap, const CUtensorMap, float *,

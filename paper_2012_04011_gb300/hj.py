@@ -162,6 +162,7 @@ _SIGS = {
                                         ctypes.POINTER(ctypes.c_int64)]),
     "hj_barrier_selftest": (ctypes.c_int, [ctypes.c_int64, ctypes.POINTER(ctypes.c_int32),
                                            ctypes.POINTER(ctypes.c_int64)]),
+    "hj_fp64_fma_probe": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, _VP, ctypes.POINTER(ctypes.c_int64)]),
     "hj_read_value": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.c_size_t]),
     "hj_read_value_device": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_size_t]),
     "hj_set_kernel": (ctypes.c_int, [_VP, ctypes.c_int]),
@@ -171,7 +172,7 @@ _SIGS = {
     "hj_step_noalloc": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double),
                                        ctypes.POINTER(ctypes.c_double), ctypes.c_uint32, ctypes.c_int, ctypes.c_int,
                                        ctypes.POINTER(ctypes.c_double), ctypes.c_int32, _VP, _VP, _VP,
-                                       ctypes.c_double, _VP, ctypes.POINTER(ctypes.c_double)]),
+                                       ctypes.c_size_t, ctypes.c_double, _VP, ctypes.POINTER(ctypes.c_double)]),
     "hj_get_info": (ctypes.c_int, [_VP, ctypes.POINTER(hj_grid_info)]),
     "hj_batch_create": (ctypes.c_int, [ctypes.c_int32, ctypes.c_size_t, _VP, ctypes.POINTER(_VP)]),
     "hj_batch_slot_bytes": (ctypes.c_size_t, [ctypes.POINTER(ctypes.c_int32)]),
@@ -352,6 +353,14 @@ def hj_wait_selftest(limit_ns: int):
     return int(st.value), int(waited.value)
 
 
+def hj_fp64_fma_probe(iters: int, blocks_per_sm: int = 8, cuda_stream=None) -> int:
+    """Launches the FP64 FMA throughput probe on cuda_stream; returns the FMAs issued."""
+    n = ctypes.c_int64(0)
+    stream = None if cuda_stream is None else ctypes.c_void_p(int(cuda_stream))
+    _check(lib.hj_fp64_fma_probe(int(iters), int(blocks_per_sm), stream, ctypes.byref(n)))
+    return int(n.value)
+
+
 def hj_barrier_selftest(limit_ns: int):
     """(status, waited_ns) of the bounded grid-barrier self-test."""
     st = ctypes.c_int32(0)
@@ -395,8 +404,29 @@ def hj_autotune(g, steps_per_trial: int = 8, max_results: int = 32):
     return [res[i] for i in range(min(cnt.value, max_results))]
 
 
-def hj_step_noalloc(n, lo, hi, periodic_mask, prec, kind, params, v_in, v0, v_out, dt, cuda_stream=None):
-    """One step on caller-owned device arrays without any allocation; returns alpha^max (4 values)."""
+def hj_step_noalloc(n, lo, hi, periodic_mask, prec, kind, params, v_in, v0, v_out, dt, cuda_stream=None,
+                    want_alpha: bool = True):
+    """One step on caller-owned device arrays without any allocation; returns
+    alpha^max (4 values), or None when want_alpha is false (the C call then
+    gets a NULL alpha_max_out).  v_in, v0 and v_out are contiguous device
+    tensors of the precision's element type (float64 for HJ_FP64, float32 for
+    HJ_FP32) with N1*N2*N3*N4 elements each; v_out may overlap neither
+    input."""
+    import torch
+    want = torch.float64 if int(prec) == HJ_FP64 else torch.float32
+    ncell = int(np.prod([int(v) for v in n], dtype=np.int64))
+    for name, t in (("v_in", v_in), ("v0", v0), ("v_out", v_out)):
+        if not isinstance(t, torch.Tensor) or not t.is_cuda or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous CUDA tensor")
+        if t.dtype != want:
+            raise ValueError(f"{name} has dtype {t.dtype}, the precision needs {want}")
+        if t.numel() != ncell:
+            raise ValueError(f"{name} has {t.numel()} elements, the grid has {ncell}")
+    nbytes = ncell * (8 if want == torch.float64 else 4)
+    o0 = v_out.data_ptr()
+    for name, t in (("v_in", v_in), ("v0", v0)):
+        if t.data_ptr() < o0 + nbytes and o0 < t.data_ptr() + nbytes:
+            raise ValueError(f"v_out overlaps {name}")
     cn = (ctypes.c_int32 * 4)(*[int(v) for v in n])
     clo = (ctypes.c_double * 4)(*[float(v) for v in lo])
     chi = (ctypes.c_double * 4)(*[float(v) for v in hi])
@@ -405,8 +435,8 @@ def hj_step_noalloc(n, lo, hi, periodic_mask, prec, kind, params, v_in, v0, v_ou
     stream = None if cuda_stream is None else ctypes.c_void_p(int(cuda_stream))
     _check(lib.hj_step_noalloc(cn, clo, chi, int(periodic_mask), int(prec), int(kind), p, len(params),
                                ctypes.c_void_p(_dptr(v_in)), ctypes.c_void_p(_dptr(v0)), ctypes.c_void_p(_dptr(v_out)),
-                               float(dt), stream, alpha))
-    return list(alpha)
+                               nbytes, float(dt), stream, alpha if want_alpha else None))
+    return list(alpha) if want_alpha else None
 
 
 def hj_get_info(g) -> hj_grid_info:

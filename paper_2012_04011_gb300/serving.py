@@ -30,9 +30,9 @@ def _percentiles(lat_ms):
 
 def run_server(trace, max_slots: int = 64, memory_budget: int = 0, steps_per_tick: int = 32, fetch: bool = True,
                cuda_stream=None, keep_results: bool = False):
-    """Replays the trace through an hj.Server.  Returns stats (and results by
-    request index when keep_results)."""
-    lat, cell_updates, results = [], 0, {}
+    """Replays the trace through an hj.Server.  Returns stats (and, when
+    keep_results, the results and the time steps taken, by request index)."""
+    lat, cell_updates, results, steps_by_req = [], 0, {}, {}
     with hj.Server(max_slots, memory_budget, steps_per_tick, cuda_stream) as srv:
         t0 = srv.clock()
         pending = list(enumerate(trace))
@@ -61,6 +61,7 @@ def run_server(trace, max_slots: int = 64, memory_budget: int = 0, steps_per_tic
                             v = srv.fetch(rid, r.workload.grid.n)
                             if keep_results:
                                 results[i] = v
+                                steps_by_req[i] = info.steps
                     elif info.state == hj.REQ_FAILED:
                         raise RuntimeError(f"request {rid} failed")
         wall = srv.clock() - t0
@@ -69,6 +70,7 @@ def run_server(trace, max_slots: int = 64, memory_budget: int = 0, steps_per_tic
            "cell_updates_per_s": cell_updates / wall if wall > 0 else None, "ticks": ticks, "batch_steps": steps}
     if keep_results:
         out["results"] = results
+        out["steps"] = steps_by_req
     return out
 
 

@@ -22,7 +22,7 @@ def declared_symbols():
     with open(os.path.join(ROOT, "include", "hj.h")) as f:
         text = f.read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(hj_[a-z_]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(hj_[a-z0-9_]+)\s*\(", text)))
 
 
 def test_header_declares_the_boundary():
@@ -96,3 +96,9 @@ def test_batch_host_checks(hj):
     for fn, args in ((hj.lib.hj_batch_advance, (None, 1, None)), (hj.lib.hj_batch_remove, (None, 0))):
         assert fn(*args) == hj.HJ_ERR_INVALID_ARG
     hj.lib.hj_batch_destroy(None)
+
+
+def test_fp64_probe_rejects_bad_arguments(hj):
+    """Checked before any CUDA call."""
+    for iters, bps in ((0, 8), (1 << 41, 8), (100, 0), (100, 65)):
+        assert hj.lib.hj_fp64_fma_probe(iters, bps, None, None) == hj.HJ_ERR_INVALID_ARG

@@ -1,10 +1,13 @@
 """Re-solve server (continuous batching): requests admitted while others are
 on the GPU, by slot and device-memory budget; each result must be exactly
-what the request gives when it runs alone, and a Poisson trace must meet the
+what the request gives when it runs alone, must match the FP64 oracle's solve
+of the same request within the FP32 tolerance (1e-4 max|V0|, no BRT sign flip
+among cells with |V_oracle| >= 1e-3), and a Poisson trace must meet the
 200 ms (5 Hz) deadline of the paper's real-time use."""
 import numpy as np
 import pytest
 
+import oracle
 from paper_2012_04011_gb300 import scenes
 
 pytestmark = pytest.mark.gpu
@@ -66,6 +69,29 @@ def test_result_same_alone_and_in_the_mix(hj):
         while srv.info(rid).state != hj.REQ_DONE:
             srv.tick()
         assert np.array_equal(srv.fetch(rid, r.workload.grid.n), mixed[2])
+
+
+def test_served_results_match_oracle(hj):
+    """A dense Poisson trace (400 req/s for 40 ms, so requests overlap on the
+    GPU) over all four serving sizes, 31x31x11x16 up to 100x100x30x48, replayed
+    in real time through the server: every served result against the
+    oracle's full solve of its request (T = 0.5 s from that request's V0)."""
+    from paper_2012_04011_gb300 import serving
+    trace = scenes.serving_trace(400.0, 0.04, seed=scenes.SEED_BASE + 60)
+    assert {r.workload.grid.n for r in trace} == set(scenes.SERVING_SIZES)
+    st = serving.run_server(trace, keep_results=True)
+    assert sorted(st["results"]) == list(range(len(trace)))
+    for i, r in enumerate(trace):
+        w = r.workload
+        V0 = scenes.initial_value(w.grid, w.scene)
+        P = oracle.Problem(w.grid.n, w.grid.lo, w.grid.hi, w.grid.periodic, oracle.DYN_CAR4D, (w.a_max, w.w_max))
+        Vo, dts = oracle.solve(P, V0, w.T, w.cfl, nthreads=oracle.max_threads())
+        V = st["results"][i]
+        assert st["steps"][i] == len(dts), (i, w.grid.n)
+        err = float(np.abs(V - Vo).max())
+        assert err <= 1e-4 * float(np.abs(V0).max()), (i, w.grid.n, err)
+        band = np.abs(Vo) >= 1e-3
+        assert int(np.count_nonzero(np.sign(V[band]) != np.sign(Vo[band]))) == 0, (i, w.grid.n)
 
 
 def test_admission_by_memory_budget(hj):

@@ -69,7 +69,7 @@ def test_steer_fp32(hj, name, kernel):
     Vo, dts = oracle.solve(oracle_steer(w), V0, w.T, w.cfl, nthreads=oracle.max_threads())
     k = hj.HJ_KERNEL_TILED if kernel == "tiled" else hj.HJ_KERNEL_GENERIC
     V, st = gpu(hj, w, hj.HJ_FP32, k)
-    assert st.kernel == k and abs(st.steps - len(dts)) <= 1
+    assert st.kernel == k and st.steps == len(dts) and st.dt_first == dts[0] and st.dt_last == dts[-1]
     assert float(np.abs(V - Vo).max()) <= 1e-4 * float(np.abs(V0).max())
     m = np.abs(Vo) >= 1e-3
     assert int(np.count_nonzero(np.sign(V[m]) != np.sign(Vo[m]))) == 0
