@@ -221,8 +221,8 @@ def oracle_accuracy(w, V0, results_host, nthreads):
         V = V.reshape(Vo.shape)
         out[name] = {"max_abs_vs_oracle": float(np.abs(V - Vo).max()),
                      "sign_flips_vs_oracle": int(np.count_nonzero(np.sign(V[band]) != np.sign(Vo[band]))),
-                     "time_steps_equal": st[0] == len(dts),
-                     "dt_first_last_equal": st[1] == dts[0] and st[2] == dts[-1]}
+                     "time_steps_equal": bool(st[0] == len(dts)),
+                     "dt_first_last_equal": bool(st[1] == dts[0] and st[2] == dts[-1])}
     return out
 
 
@@ -277,7 +277,7 @@ def run_reference(args):
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": nthreads, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
-    print(json.dumps(line), flush=True)
+    print(json.dumps(line, default=json_default), flush=True)
     return 0
 
 
@@ -450,11 +450,11 @@ def run_ours(args):
 
     if args.small_only:
         if rank == 0:
-            print(json.dumps({"small_configs": run_small(hj, scenes, torch, torch.cuda.current_stream())}))
+            print(json.dumps({"small_configs": run_small(hj, scenes, torch, torch.cuda.current_stream())}, default=json_default))
         return 0
     if args.large_only:
         if rank == 0:
-            print(json.dumps({"large_grid": run_large(hj, scenes, torch, torch.cuda.current_stream())}))
+            print(json.dumps({"large_grid": run_large(hj, scenes, torch, torch.cuda.current_stream())}, default=json_default))
         return 0
 
     w = scenes.workload(WORKLOAD)
@@ -808,10 +808,19 @@ def run_ours(args):
             "value": rate1, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{nst1} oracle time step of the {WORKLOAD} solve ({nst1 * ncell:.3e} cell-updates, "
                       f"{el1:.1f} s), FP64, one thread"}
-    print(json.dumps(line), flush=True)
+    print(json.dumps(line, default=json_default), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def json_default(o):
+    """numpy scalars and arrays in the result line as plain JSON values."""
+    if isinstance(o, np.generic):
+        return o.item()
+    if isinstance(o, np.ndarray):
+        return o.tolist()
+    raise TypeError(f"not JSON serialisable: {type(o).__name__}")
 
 
 def main():
