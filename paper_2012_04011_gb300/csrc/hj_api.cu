@@ -318,6 +318,27 @@ hj_status upload_tables(hj_grid *g)
                                    cudaMemcpyHostToDevice);
         if (e != cudaSuccess) st = set_err(HJ_ERR_CUDA, "table upload: %s", cudaGetErrorString(e));
     }
+    // the largest |xdot_1|, |xdot_2| over each theta quad's real headings, per speed
+    if (st == HJ_OK) {
+        const int Q4 = P4 / 4;
+        double2 *aq = (double2 *)malloc(sizeof(double2) * (size_t)N3 * Q4);
+        if (!aq) st = set_err(HJ_ERR_OOM, "host allocation failed");
+        for (int k = 0; aq && k < N3; ++k)
+            for (int q = 0; q < Q4; ++q) {
+                double m1 = 0.0, m2 = 0.0;
+                for (int l = 4 * q; l < 4 * q + 4 && l < N4; ++l) {
+                    const double a1 = fabs(f1[(size_t)k * N4 + l]), a2 = fabs(f2[(size_t)k * N4 + l]);
+                    if (a1 > m1) m1 = a1;
+                    if (a2 > m2) m2 = a2;
+                }
+                aq[(size_t)k * Q4 + q] = make_double2(m1, m2);
+            }
+        if (aq) {
+            cudaError_t e = cudaMemcpy(g->amax_q, aq, sizeof(double2) * (size_t)N3 * Q4, cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) st = set_err(HJ_ERR_CUDA, "table upload: %s", cudaGetErrorString(e));
+        }
+        free(aq);
+    }
     free(f1);
     free(f2);
     free(tab);
@@ -457,6 +478,7 @@ void free_grid(hj_grid *g)
     if (g->buf) cudaFree(g->buf);
     if (g->coef) cudaFree(g->coef);
     if (g->tab_tiled) cudaFree(g->tab_tiled);
+    if (g->amax_q) cudaFree(g->amax_q);
     if (g->scaled) cudaFree(g->scaled);
     if (g->qw) cudaFree(g->qw);
     if (g->v0xy) cudaFree(g->v0xy);
@@ -591,6 +613,7 @@ hj_status hj_create_grid(const int32_t n[4], const double lo[4], const double hi
     const size_t k4_bytes = (size_t)n[2] * (prec == HJ_FP32 ? 2 * sizeof(float) : sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&g->coef, coef_bytes);
     if (e == cudaSuccess) e = cudaMalloc(&g->tab_tiled, sizeof(float) * ((size_t)n[2] + 3 * (size_t)g->p4));
+    if (e == cudaSuccess) e = cudaMalloc(&g->amax_q, sizeof(double2) * (size_t)n[2] * (g->p4 / 4));
     if (e == cudaSuccess && prec == HJ_FP64) e = cudaMalloc(&g->scaled, ncoef * sizeof(HjScaledCoef));
     if (e == cudaSuccess && prec == HJ_Q527) e = cudaMalloc(&g->qw, qw_bytes);
     const size_t xy_bytes = (size_t)n[0] * n[1] * g->esize;

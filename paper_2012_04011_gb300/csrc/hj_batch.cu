@@ -52,6 +52,7 @@ struct BatchInst {
     float *buf;                 // buffer A, then buffer B (nint floats each)
     const float *tab;           // v_k [n3], cos/dx1 [p4], sin/dx2 [p4]
     const HjCoef<float> *coef;  // [n3 * n4]
+    const double2 *amaxv;       // [n3]: the largest FP64 |xdot_1|, |xdot_2| over the headings of each speed
     HjGeom geom;
 };
 
@@ -332,26 +333,31 @@ __global__ void __launch_bounds__(MAXC + 32, 1)
             HJ_RELEASE_OLDEST();
             if (x1 <= pl1) HJ_RELEASE_OLDEST();
 
-            // alpha^max partials of this warp for the slot, then count the
-            // warp done; the warp completing the slot's step finalises it
-            // (FP64 |xdot_1|, |xdot_2| of the table: the slot's dt is the FP64 one)
-            unsigned long long a1 = 0ull, a2 = 0ull;
-            if (rok)
-                for (int e = 0; e < lreal; ++e) {
-                    const unsigned long long b1 = hj_abits(I.coef[v * N4 + 4 * q + e].a1);
-                    const unsigned long long b2 = hj_abits(I.coef[v * N4 + 4 * q + e].a2);
+            // count the warp done; the warp completing the slot's step
+            // reduces the slot's alpha^max over its per-speed table (every cell
+            // of the slot was updated in this step, and the car's velocity
+            // depends on v and theta only: the same maxima as over the cells)
+            // and finalises the step
+            unsigned int last = 0u;
+            if (lane == 0) {
+                __threadfence();
+                const unsigned int per_step = (unsigned int)nconsumer_warps * (unsigned int)I.nitems;
+                last = atomicAdd(&sl->warps_done, 1u) + 1 == per_step;
+            }
+            if (__shfl_sync(0xffffffffu, last, 0)) {
+                __threadfence();
+                unsigned long long a1 = 0ull, a2 = 0ull;
+                for (int e = lane; e < N3; e += 32) {
+                    const double2 am = I.amaxv[e];
+                    const unsigned long long b1 = hj_abits(am.x), b2 = hj_abits(am.y);
                     a1 = a1 > b1 ? a1 : b1;
                     a2 = a2 > b2 ? a2 : b2;
                 }
-            a1 = hj_warp_max_u64(a1);
-            a2 = hj_warp_max_u64(a2);
-            if (lane == 0) {
-                atomicMax(&sl->st.alpha_bits[0], a1);
-                atomicMax(&sl->st.alpha_bits[1], a2);
-                __threadfence();
-                const unsigned int per_step = (unsigned int)nconsumer_warps * (unsigned int)I.nitems;
-                const unsigned int prev_done = atomicAdd(&sl->warps_done, 1u);
-                if (prev_done + 1 == per_step) {
+                a1 = hj_warp_max_u64(a1);
+                a2 = hj_warp_max_u64(a2);
+                if (lane == 0) {
+                    atomicMax(&sl->st.alpha_bits[0], a1);
+                    atomicMax(&sl->st.alpha_bits[1], a2);
                     hj_finalise(&sl->st, I.geom);
                     sl->warps_done = 0u;
                     __threadfence();
@@ -431,6 +437,7 @@ struct SlotHost {
     size_t bytes = 0;
     float *v0 = nullptr, *buf = nullptr, *tab = nullptr;
     HjCoef<float> *coef = nullptr;
+    double2 *amaxv = nullptr;
     bool has_value = false;
     double T = 0, cfl = 0.8;
     int ty = 0, tv = 0, xc = 0;
@@ -524,6 +531,7 @@ hj_status upload_slot_tables(hj_batch *b, SlotHost &s)
     const int N3 = s.n[2], N4 = s.n[3], P4 = s.p4;
     std::vector<HjCoef<float>> c((size_t)N3 * N4);
     std::vector<float> tab((size_t)N3 + 2 * P4, 0.f);
+    std::vector<double2> amax((size_t)N3, make_double2(0.0, 0.0));
     const double k3 = s.a_max / s.h[2], k4 = s.w_max / s.h[3];
     for (int k = 0; k < N3; ++k) {
         const double v = s.lo[2] + (double)k * s.h[2];
@@ -538,6 +546,9 @@ hj_status upload_slot_tables(hj_batch *b, SlotHost &s)
             e.ks = (float)(fabs(c1) + fabs(c2) + k3 + k4);
             e.a1 = fabs(f1);
             e.a2 = fabs(f2);
+            double2 &m = amax[k];  // the speed's largest |xdot_1|, |xdot_2|
+            if (e.a1 > m.x) m.x = e.a1;
+            if (e.a2 > m.y) m.y = e.a2;
         }
     }
     for (int l = 0; l < N4; ++l) {
@@ -547,6 +558,7 @@ hj_status upload_slot_tables(hj_batch *b, SlotHost &s)
     }
     HJB_CUDA(cudaMemcpyAsync(s.coef, c.data(), sizeof(HjCoef<float>) * c.size(), cudaMemcpyHostToDevice, b->stream));
     HJB_CUDA(cudaMemcpyAsync(s.tab, tab.data(), sizeof(float) * tab.size(), cudaMemcpyHostToDevice, b->stream));
+    HJB_CUDA(cudaMemcpyAsync(s.amaxv, amax.data(), sizeof(double2) * amax.size(), cudaMemcpyHostToDevice, b->stream));
     HJB_CUDA(cudaStreamSynchronize(b->stream));  // the host vectors go out of scope
     return HJ_OK;
 }
@@ -619,6 +631,7 @@ hj_status rebuild(hj_batch *b)
         I.buf = s.buf;
         I.tab = s.tab;
         I.coef = s.coef;
+        I.amaxv = s.amaxv;
         I.geom = s.geom;
         const int ncv = (s.n[2] + s.tv - 1) / s.tv, ncy = (s.n[1] + s.ty - 1) / s.ty;
         const int nch = (s.n[0] + s.xc - 1) / s.xc;
@@ -820,7 +833,8 @@ void hj_batch_destroy(hj_batch *b)
 
 // Device memory of one slot: V0, buffers A|B (contiguous), coefficient
 // table, tiled tables; each section 256-byte aligned.
-static void slot_layout(const int32_t n[4], size_t *v0_b, size_t *ab_b, size_t *coef_b, size_t *tab_b)
+static void slot_layout(const int32_t n[4], size_t *v0_b, size_t *ab_b, size_t *coef_b, size_t *tab_b,
+                        size_t *amax_b)
 {
     const long long p4 = (n[3] + 3) / 4 * 4;
     const long long nint = (long long)n[0] * n[1] * n[2] * p4;
@@ -828,6 +842,7 @@ static void slot_layout(const int32_t n[4], size_t *v0_b, size_t *ab_b, size_t *
     *ab_b = ((size_t)nint * 8 + 255) / 256 * 256;
     *coef_b = ((size_t)n[2] * n[3] * sizeof(HjCoef<float>) + 255) / 256 * 256;
     *tab_b = (((size_t)n[2] + 2 * (size_t)p4) * 4 + 255) / 256 * 256;
+    *amax_b = ((size_t)n[2] * sizeof(double2) + 255) / 256 * 256;
 }
 
 size_t hj_batch_slot_bytes(const int32_t n[4])
@@ -835,9 +850,9 @@ size_t hj_batch_slot_bytes(const int32_t n[4])
     if (!n) return 0;
     for (int d = 0; d < 4; ++d)
         if (n[d] < 1) return 0;
-    size_t a, b2, c, t;
-    slot_layout(n, &a, &b2, &c, &t);
-    return a + b2 + c + t;
+    size_t a, b2, c, t, am;
+    slot_layout(n, &a, &b2, &c, &t, &am);
+    return a + b2 + c + t + am;
 }
 
 hj_status hj_batch_add(hj_batch *b, const int32_t n[4], const double lo[4], const double hi[4], const double params[2],
@@ -886,13 +901,14 @@ hj_status hj_batch_add(hj_batch *b, const int32_t n[4], const double lo[4], cons
     s.ncell = (long long)n[0] * n[1] * n[2] * n[3];
     HJB_CUDA(cudaMalloc(&s.mem, bytes));
     s.bytes = bytes;
-    size_t sz_v0, sz_ab, sz_coef, sz_tab;
-    slot_layout(n, &sz_v0, &sz_ab, &sz_coef, &sz_tab);
+    size_t sz_v0, sz_ab, sz_coef, sz_tab, sz_amax;
+    slot_layout(n, &sz_v0, &sz_ab, &sz_coef, &sz_tab, &sz_amax);
     char *m = (char *)s.mem;
     s.v0 = (float *)m;
     s.buf = (float *)(m + sz_v0);  // A, then B at buf + nint
     s.coef = (HjCoef<float> *)(m + sz_v0 + sz_ab);
     s.tab = (float *)(m + sz_v0 + sz_ab + sz_coef);
+    s.amaxv = (double2 *)(m + sz_v0 + sz_ab + sz_coef + sz_tab);
     memset(&s.geom, 0, sizeof(s.geom));
     s.geom.n1 = n[0];
     s.geom.n2 = n[1];

@@ -106,6 +106,8 @@ struct hj_grid {
     bool v0_bcast;         // V0 was set from the (x, y) field: the tiled kernel reads v0xy
     bool track;            // a convergence-mode call is running: launch the kernels that reduce the change
     float *tab_tiled;      // tiled-kernel tables: v_k [n3], cos/dx1 [p4], sin/dx2 [p4], quad signs [p4]
+    double2 *amax_q;       // per (v_k, theta quad q) [n3][p4 / 4]: the largest FP64 |xdot_1|, |xdot_2| over the
+                           // quad's headings (the tiled kernel's alpha^max partials, one load per work item)
     HjDevState *dstate;
     HjDevState *hstate;    // pinned host mirror
 

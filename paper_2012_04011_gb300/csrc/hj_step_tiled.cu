@@ -261,6 +261,6 @@ cudaError_t hj_launch_step_tiled(hj_grid *g)
     KernelFn fn = kernel_fn(g->prec == HJ_Q527, g->p4 != g->n[3], g->tiled_usign, g->v0_bcast, g->track, P.nconsumer);
     fn<<<g->tiled_ctas, P.nconsumer + 32, tiled_smem_bytes(P), g->stream>>>(
         g->tmap[0], g->tmap[1], g->tmap[2], g->tmap[3], (float *)g->buf, g->coef, g->tab_tiled, g->qw,
-        (const float *)g->v0xy, g->k4tab, g->dstate, g->geom, P, g->nint);
+        (const float *)g->v0xy, g->k4tab, g->amax_q, g->dstate, g->geom, P, g->nint);
     return cudaGetLastError();
 }

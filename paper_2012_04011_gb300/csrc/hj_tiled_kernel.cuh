@@ -22,9 +22,11 @@
 //   * All CTAs of a step sweep x concurrently, so y/v halo rows of
 //     neighbouring columns are in L2 when they are needed.
 //   * alpha^max partials (|xdot_1|, |xdot_2| over the (v, theta) states of the
-//     cells each thread updates) are reduced by warp shuffles and a block
-//     reduction, and the last CTA computes the next CFL step (fused; no extra
-//     pass over the grid).
+//     cells each thread updates: one FP64 pair per (v, theta quad) of each of
+//     its items, from a small table) are reduced by each consumer thread at
+//     the start, while the first planes are in flight, then by warp shuffles
+//     and shared-memory maxima; the last CTA computes the next CFL step
+//     (fused; no extra pass over the grid, no registers held in the sweep).
 // The Q5.27 variant (FIXED) moves the same 4-byte values through the same
 // ring and evaluates the fixed-point update of hj_q527_update per lane:
 // exact integer upwind differences (ghosts by flag, as minus the difference
@@ -116,12 +118,10 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
     const __grid_constant__ CUtensorMap map_v0, const __grid_constant__ CUtensorMap map_a,
     const __grid_constant__ CUtensorMap map_b, const __grid_constant__ CUtensorMap map_v0_tile,
     float *__restrict__ buf, const void *__restrict__ coefv, const float *__restrict__ tab,
-    int32_t *__restrict__ qw, const float *__restrict__ v0xy, const void *__restrict__ k4tab, HjDevState *st,
-    const HjGeom g, const TiledParams P, long long nint)
+    int32_t *__restrict__ qw, const float *__restrict__ v0xy, const void *__restrict__ k4tab,
+    const double2 *__restrict__ amaxq, HjDevState *st, const HjGeom g, const TiledParams P, long long nint)
 {
-    const HjCoef<float> *coef = (const HjCoef<float> *)coefv;     // FP32 grids
-    const HjCoef<double> *coefd = (const HjCoef<double> *)coefv;  // Q5.27 grids
-    (void)coef;
+    const HjCoef<double> *coefd = (const HjCoef<double> *)coefv;  // Q5.27 grids: the table the weights come from
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     if (st->done) return;  // uniform across the grid
 
@@ -132,6 +132,7 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
     unsigned long long *scratch = (unsigned long long *)(empty + MAX_STAGES);
     volatile int *abort_flag = (volatile int *)(scratch + 96);
     unsigned long long *deadline_p = (unsigned long long *)(scratch + 97);
+    unsigned long long *alpha_s = scratch + 98;  // the CTA's alpha^max partials (FP64 bit patterns)
 
     const long long n = st->n;
     const float dt = (float)st->dt;
@@ -147,13 +148,13 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
         }
         *abort_flag = 0;
         *deadline_p = global_ns() + HJ_WAIT_NS;
+        alpha_s[0] = 0ull;
+        alpha_s[1] = 0ull;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     __syncthreads();
 
-    // this thread's max |xdot_1|, |xdot_2| (FP64 bit patterns of non-negative values)
-    unsigned long long ab1 = 0ull, ab2 = 0ull;
     // convergence mode (Algorithm 2's epsilon): this thread's largest |V_{n+1} - V_n|
     float dmf = 0.f;
     unsigned int dmq = 0u;  // in codes (FIXED; a change of one step is below 2^32 codes)
@@ -219,6 +220,30 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
         const int srow = P.tv + 2;  // smem rows per y row
         const int jy = r / P.tv, kv = r - (r / P.tv) * P.tv;
         const bool inrow = r < P.ty * P.tv;
+        {
+            // alpha^max partials: the FP64 |xdot_1|, |xdot_2| maxima over this
+            // thread's theta quad in the row it owns in each of its items (the
+            // car's velocity depends on v and theta only), reduced while the
+            // producer's first copies are in flight
+            unsigned long long ab1 = 0ull, ab2 = 0ull;
+#pragma unroll 4
+            for (int item = blockIdx.x; item < P.nitems; item += gridDim.x) {
+                const int col = item % P.ncol;
+                const int y = (col / P.ncol_v) * P.ty + jy, v = (col % P.ncol_v) * P.tv + kv;
+                if (inrow && y < g.n2 && v < g.n3) {
+                    const double2 am = amaxq[v * P.q4 + q];
+                    const unsigned long long b1 = hj_abits(am.x), b2 = hj_abits(am.y);
+                    ab1 = ab1 > b1 ? ab1 : b1;
+                    ab2 = ab2 > b2 ? ab2 : b2;
+                }
+            }
+            ab1 = hj_warp_max_u64(ab1);
+            ab2 = hj_warp_max_u64(ab2);
+            if (lane == 0) {
+                atomicMax(&alpha_s[0], ab1);
+                atomicMax(&alpha_s[1], ab2);
+            }
+        }
         const int rsm = inrow ? ((jy + 1) * srow + (kv + 1)) * P4 + 4 * q : (srow + 1) * P4;
         const int r0sm = P.halo_floats + (inrow ? (jy * P.tv + kv) * P4 + 4 * q : 0);  // V0 in the stage
         // V_{n+1} is addressed in float4 units (P4 is a multiple of 4): 32-bit
@@ -545,22 +570,10 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
             st->status = HJ_ERR_TIMEOUT;
             *abort_flag = 1;
         }
-        // alpha^max partials over the (v, theta) states of the cells this
-        // thread updated (the car's xdot_1, xdot_2 depend only on v, theta)
-        for (int item = blockIdx.x; item < P.nitems; item += gridDim.x) {
-            const ItemGeom it = item_geom(P, g, item);
-            const int y = it.y0 + jy, v = it.v0 + kv;
-            if (inrow && y < N2 && v < N3)
-                for (int e = 0; e < lreal; ++e) {
-                    // the FP64 |xdot_1|, |xdot_2| of the table, in either precision
-                    const double c1 = FIXED ? coefd[v * N4 + 4 * q + e].a1 : coef[v * N4 + 4 * q + e].a1;
-                    const double c2 = FIXED ? coefd[v * N4 + 4 * q + e].a2 : coef[v * N4 + 4 * q + e].a2;
-                    const unsigned long long b1 = hj_abits(c1), b2 = hj_abits(c2);
-                    ab1 = ab1 > b1 ? ab1 : b1;
-                    ab2 = ab2 > b2 ? ab2 : b2;
-                }
-        }
     }
+    // the CTA's alpha^max partials enter the block reduction through thread 0
+    __syncthreads();
+    const unsigned long long ab1 = tid == 0 ? alpha_s[0] : 0ull, ab2 = tid == 0 ? alpha_s[1] : 0ull;
     if constexpr (FIXED)
         hj_step_epilogue_scaled(st, g, ab1, ab2, hj_abits((double)dmq * (1.0 / HJ_Q527_SCALE)), scratch, nullptr, qw,
                                 coefd, (const double *)k4tab);
@@ -569,8 +582,8 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
 }
 
 typedef void (*KernelFn)(const CUtensorMap, const CUtensorMap, const CUtensorMap, const CUtensorMap, float *,
-                         const void *, const float *, int32_t *, const float *, const void *, HjDevState *,
-                         const HjGeom, const TiledParams, long long);
+                         const void *, const float *, int32_t *, const float *, const void *, const double2 *,
+                         HjDevState *, const HjGeom, const TiledParams, long long);
 
 // Kernel of a variant, smallest launch bound class that holds nconsumer
 // consumer threads (defined in the instantiating translation units).
