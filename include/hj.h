@@ -393,7 +393,9 @@ HJ_API hj_status hj_batch_set_initial_value_device(hj_batch *b, int32_t slot, co
 /* As hj_set_initial_value_xy, for a slot. */
 HJ_API hj_status hj_batch_set_initial_value_xy(hj_batch *b, int32_t slot, const double *v0_xy, size_t count);
 
-/* Horizon T and Courant number of a slot (computes its first dt). */
+/* Horizon T and Courant number of a slot (computes its first dt on the
+ * device; queued on the batch's stream, ordered before the next batch step,
+ * without waiting for it). */
 HJ_API hj_status hj_batch_set_horizon(hj_batch *b, int32_t slot, double T, double cfl);
 
 /* Take up to max_steps batch steps (each unfinished slot advances one step

@@ -753,6 +753,26 @@ hj_status push_slot(hj_batch *b, int i)
     return HJ_OK;
 }
 
+// Queue the host mirror of slot i to the device without waiting: every later
+// host read of the mirror comes after a stream synchronisation, and the
+// mirror entry is not written again before then.
+hj_status push_slot_async(hj_batch *b, int i)
+{
+    HJB_CUDA(cudaMemcpyAsync(&b->d_slots[i], &b->h_slots[i], sizeof(BatchSlot), cudaMemcpyHostToDevice, b->stream));
+    return HJ_OK;
+}
+
+// Whether the ingest queued on the stream saw a NaN or Inf in slot i's V0
+// (waits for the stream).
+hj_status pull_nonfinite(hj_batch *b, int i, bool *bad)
+{
+    HJB_CUDA(cudaMemcpyAsync(&b->h_slots[i].st.nonfinite, &b->d_slots[i].st.nonfinite, sizeof(int),
+                             cudaMemcpyDeviceToHost, b->stream));
+    HJB_CUDA(cudaStreamSynchronize(b->stream));
+    *bad = b->h_slots[i].st.nonfinite != 0;
+    return HJ_OK;
+}
+
 hj_status check_slot(const hj_batch *b, int slot)
 {
     if (!b) return bfail(HJ_ERR_INVALID_ARG, "batch is NULL");
@@ -962,11 +982,13 @@ static hj_status batch_ingest(hj_batch *b, int32_t slot, const void *src, hj_pre
     SlotHost &sl = b->slots[slot];
     if (!src) return bfail(HJ_ERR_INVALID_ARG, "v0 is NULL");
     if (count != (size_t)sl.ncell) return bfail(HJ_ERR_INVALID_ARG, "count %zu != %lld", count, sl.ncell);
-    HJB_CUDA(cudaStreamSynchronize(b->stream));
+    // (every call of the batch API returns with its stream work done or with
+    // a synchronisation after its last use of the host mirror, so the mirror
+    // entry is free to rewrite; the reset state is queued, not waited for)
     memset(&b->h_slots[slot], 0, sizeof(BatchSlot));
     b->h_slots[slot].st.done = 1;  // until a horizon is set
     b->h_slots[slot].st.status = HJ_OK;
-    if ((s = push_slot(b, slot)) != HJ_OK) return s;
+    if ((s = push_slot_async(b, slot)) != HJ_OK) return s;
     const void *dsrc = src;
     if (!on_host && b->own_stream) {
         // a batch on its own (non-blocking) stream reads a caller's device array
@@ -981,8 +1003,9 @@ static hj_status batch_ingest(hj_batch *b, int32_t slot, const void *src, hj_pre
     int *flag = &b->d_slots[slot].st.nonfinite;
     HJB_CUDA(hj_launch_ingest_f32(dsrc, type, sl.v0, sl.n[3], sl.p4, (long long)sl.n[0] * sl.n[1] * sl.n[2], flag,
                                   b->stream));
-    if ((s = pull_slots(b)) != HJ_OK) return s;
-    if (b->h_slots[slot].st.nonfinite) {
+    bool bad = false;
+    if ((s = pull_nonfinite(b, slot, &bad)) != HJ_OK) return s;
+    if (bad) {
         sl.has_value = false;
         return bfail(HJ_ERR_INVALID_ARG, "V0 contains NaN or Inf");
     }
@@ -999,15 +1022,15 @@ hj_status hj_batch_set_initial_value_xy(hj_batch *b, int32_t slot, const double 
     if (!v0_xy) return bfail(HJ_ERR_INVALID_ARG, "v0_xy is NULL");
     const long long nxy = (long long)sl.n[0] * sl.n[1];
     if (count != (size_t)nxy) return bfail(HJ_ERR_INVALID_ARG, "count %zu != N1*N2 = %lld", count, nxy);
-    HJB_CUDA(cudaStreamSynchronize(b->stream));
     memset(&b->h_slots[slot], 0, sizeof(BatchSlot));
     b->h_slots[slot].st.done = 1;
-    if ((s = push_slot(b, slot)) != HJ_OK) return s;
+    if ((s = push_slot_async(b, slot)) != HJ_OK) return s;
     HJB_CUDA(cudaMemcpyAsync(sl.buf, v0_xy, sizeof(double) * (size_t)nxy, cudaMemcpyHostToDevice, b->stream));
     HJB_CUDA(hj_launch_ingest_xy_f32((const double *)sl.buf, sl.v0, sl.n[2], sl.n[3], sl.p4, nxy,
                                      &b->d_slots[slot].st.nonfinite, b->stream));
-    if ((s = pull_slots(b)) != HJ_OK) return s;
-    if (b->h_slots[slot].st.nonfinite) {
+    bool bad = false;
+    if ((s = pull_nonfinite(b, slot, &bad)) != HJ_OK) return s;
+    if (bad) {
         sl.has_value = false;
         return bfail(HJ_ERR_INVALID_ARG, "V0 contains NaN or Inf");
     }
@@ -1040,8 +1063,9 @@ hj_status hj_batch_set_horizon(hj_batch *b, int32_t slot, double T, double cfl)
     if (!sl.has_value) return bfail(HJ_ERR_STATE, "slot %d has no initial value", slot);
     sl.T = T;
     sl.cfl = cfl;
+    // queued on the batch's stream (ordered before the next batch step); the
+    // calls that read slot states synchronise first
     HJB_CUDA(hj_launch_prologue_f32(&b->d_slots[slot].st, sl.geom, sl.coef, sl.n[2] * sl.n[3], T, cfl, b->stream));
-    HJB_CUDA(cudaStreamSynchronize(b->stream));
     return HJ_OK;
 }
 
