@@ -86,6 +86,157 @@ static __device__ __forceinline__ void tensormap_acquire(const CUtensorMap *m)
     asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"((unsigned long long)m) : "memory");
 }
 
+// What the consumers need of a work item, written into shared memory by the
+// producer (with the item's first plane; the full barrier's arrive releases
+// it), so that an item starts without a chain of dependent global loads.
+struct BatchDesc {
+    int item;                 // -1: no more work
+    int slot;
+    int y0, v0, x0, x1;       // tile origin and the item's x range [x0, x1)
+    int n1, n2, n3, n4, p4, q4, ty, tv;
+    int halo_floats;          // V0 box offset in a stage
+    unsigned int per_step;    // consumer warps x the slot's items: finishes of one slot step
+    float k3, k4, mk34, dt;   // v / theta coefficients and the slot's dt (working precision)
+    float *vout;              // buffer of V_{n+1}
+    const float *tab;         // v_k [n3], cos/dx1 [p4], sin/dx2 [p4]
+};
+
+// The planes of one item for one consumer thread (row r of the tile, theta
+// quad q): waits for each plane, updates the thread's quad, stores V_{n+1},
+// releases plane x-1.  PADDED: N4 is not a multiple of 4 (the last quad of a
+// row has pad lanes: the theta wrap of its last real lane comes from lane 0
+// of the row, and pad lanes are written as 0).  Returns false if a wait ran
+// out.  Plane x-1 is carried in registers from the previous plane.
+template <bool PADDED>
+__device__ __forceinline__ bool batch_item_planes(const BatchDesc &d, int s_first, int q, int jy, int kv, bool rok,
+                                                  const float *stages, int sfl, int nst, uint64_t *full,
+                                                  uint64_t *empty, const unsigned long long *deadline_p, int lane,
+                                                  int &wslot, uint32_t &wphase, int &rslot)
+{
+#define HJ_WAIT_NEXT(slot_out)                                   \
+    do {                                                         \
+        if (!mbar_wait_warp(&full[wslot], wphase, deadline_p)) { \
+            slot_out = -1;                                       \
+        } else {                                                 \
+            slot_out = wslot;                                    \
+            if (++wslot == nst) {                                \
+                wslot = 0;                                       \
+                wphase ^= 1u;                                    \
+            }                                                    \
+        }                                                        \
+    } while (0)
+#define HJ_RELEASE_OLDEST()                            \
+    do {                                               \
+        __syncwarp();                                  \
+        if (lane == 0) mbar_arrive(&empty[rslot]);     \
+        if (++rslot == nst) rslot = 0;                 \
+    } while (0)
+    const int N1 = d.n1, N2 = d.n2, N3 = d.n3, N4 = d.n4, P4 = d.p4, tv = d.tv;
+    const int x0 = d.x0, x1 = d.x1, pl0 = max(x0 - 1, 0), pl1 = min(x1, N1 - 1);
+    const int y = d.y0 + jy, v = d.v0 + kv;
+    const int srow = tv + 2;
+    const int rsm = rok ? ((jy + 1) * srow + (kv + 1)) * P4 + 4 * q : (srow + 1) * P4;
+    const int r0sm = d.halo_floats + (rok ? (jy * tv + kv) * P4 + 4 * q : 0);
+    const uint32_t s1 = (uint32_t)N2 * N3 * P4;
+    const uint32_t rbase = rok ? ((uint32_t)y * N3 + v) * P4 + 4 * q : 0u;
+    const uint32_t gmask = (y == 0 ? 1u : 0u) | (y == N2 - 1 ? 2u : 0u) | (v == 0 ? 4u : 0u) |
+                           (v == N3 - 1 ? 8u : 0u);
+    const int lm = (4 * q - 1 + N4) % N4, lp = (4 * q + 4) % N4, lreal = min(4, N4 - 4 * q);
+    const float k3 = d.k3, k4 = d.k4, mk34 = d.mk34, dt = d.dt;
+    float *const vout = d.vout;
+    float wx[4], wxm[4], wy[4], wym[4], cs[4];
+    float vk = 0.f;
+    if (rok) {
+        // xdot_1 = v cos(th), xdot_2 = v sin(th): a negative speed flips the
+        // upwind sides, and the weights take |v|
+        vk = d.tab[v];
+        const float sg = vk < 0.f ? -1.f : 1.f;
+        vk = fabsf(vk);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const float c = sg * d.tab[N3 + 4 * q + e], sn = sg * d.tab[N3 + P4 + 4 * q + e];
+            wx[e] = fmaxf(c, 0.f);
+            wxm[e] = fmaxf(-c, 0.f);
+            wy[e] = fmaxf(sn, 0.f);
+            wym[e] = fmaxf(-sn, 0.f);
+            cs[e] = fabsf(c) + fabsf(sn);
+        }
+    } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) wx[e] = wxm[e] = wy[e] = wym[e] = cs[e] = 0.f;
+    }
+    int s_x = s_first;
+    if (x0 > pl0) HJ_WAIT_NEXT(s_x);
+    if (s_x < 0) return false;
+    float4 cur = *(const float4 *)(stages + (size_t)s_x * sfl + rsm);
+    int s_prev = x0 > pl0 ? s_first : -1;
+    // centre of plane x-1, carried in registers from the previous plane
+    float4 prevr = s_prev >= 0 ? *(const float4 *)(stages + (size_t)s_first * sfl + rsm) : cur;
+    for (int x = x0; x < x1; ++x) {
+        const float *sx = stages + (size_t)s_x * sfl;
+        int s_n = -1;
+        float4 prev, nxt;
+        if (x + 1 <= N1 - 1) {
+            HJ_WAIT_NEXT(s_n);
+            if (s_n < 0) return false;
+            nxt = *(const float4 *)(stages + (size_t)s_n * sfl + rsm);
+            prev = s_prev >= 0 ? prevr : f4ghost(cur, nxt);
+        } else {
+            prev = s_prev >= 0 ? prevr : cur;
+            nxt = f4ghost(cur, prev);
+        }
+        if (rok) {
+            const float *row = sx + rsm;
+            float4 ym = *(const float4 *)(row - srow * P4);
+            float4 yp = *(const float4 *)(row + srow * P4);
+            float4 vm = *(const float4 *)(row - P4);
+            float4 vp = *(const float4 *)(row + P4);
+            if (gmask) {  // extrapolated points past the y / v ends (Sec. II-B)
+                if (gmask & 1u) ym = f4ghost(cur, yp);
+                if (gmask & 2u) yp = f4ghost(cur, ym);
+                if (gmask & 4u) vm = f4ghost(cur, vp);
+                if (gmask & 8u) vp = f4ghost(cur, vm);
+            }
+            const float *row0 = row - 4 * q;
+            const float tl = row0[lm], tr = row0[lp];
+            float t0 = 0.f;
+            if (PADDED) t0 = row0[0];
+            const float4 v0c = *(const float4 *)(sx + r0sm);
+            float4 out;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const float vc = f4get(cur, e);
+                const float tm = e == 0 ? tl : f4get(cur, e - 1);
+                float tp = e == 3 ? tr : f4get(cur, e + 1);
+                if (PADDED && lreal < 4 && e == lreal - 1) tp = t0;  // wrap of a padded last quad
+                float in = wx[e] * f4get(nxt, e);
+                in = fmaf(wxm[e], f4get(prev, e), in);
+                in = fmaf(wy[e], f4get(yp, e), in);
+                in = fmaf(wym[e], f4get(ym, e), in);
+                in = fmaf(-cs[e], vc, in);
+                float acc = fmaf(k3, fmaxf(f4get(vp, e), f4get(vm, e)), mk34 * vc);
+                acc = fmaf(k4, fmaxf(tp, tm), acc);
+                acc = fmaf(vk, in, acc);
+                float vn = fminf(f4get(v0c, e), fmaf(dt, acc, vc));
+                if (PADDED && e >= lreal) vn = 0.f;
+                f4set(out, e, vn);
+            }
+            *(float4 *)(vout + (uint32_t)x * s1 + rbase) = out;
+        }
+        if (s_prev >= 0) HJ_RELEASE_OLDEST();
+        s_prev = s_x;
+        s_x = s_n;
+        prevr = cur;
+        cur = nxt;
+    }
+    // still held: plane x1-1 and, if loaded, the halo plane x1
+    HJ_RELEASE_OLDEST();
+    if (x1 <= pl1) HJ_RELEASE_OLDEST();
+    return true;
+#undef HJ_WAIT_NEXT
+#undef HJ_RELEASE_OLDEST
+}
+
 template <int MAXC>
 __global__ void __launch_bounds__(MAXC + 32, 1)
     hj_batch_step_kernel(const BatchInst *__restrict__ insts, BatchSlot *slots, const BatchItem *__restrict__ items,
@@ -95,9 +246,9 @@ __global__ void __launch_bounds__(MAXC + 32, 1)
     float *stages = (float *)smem_raw;
     uint64_t *full = (uint64_t *)(smem_raw + (size_t)BP.stages * BP.stage_bytes);
     uint64_t *empty = full + B_MAX_STAGES;
-    int *stage_item = (int *)(empty + B_MAX_STAGES);  // item tag of each stage
-    volatile int *abort_flag = stage_item + B_MAX_STAGES;
-    unsigned long long *deadline_p = (unsigned long long *)(stage_item + B_MAX_STAGES + 2);
+    BatchDesc *desc = (BatchDesc *)(empty + B_MAX_STAGES);  // descriptor of the item whose first plane is in a stage
+    volatile int *abort_flag = (volatile int *)(desc + B_MAX_STAGES);
+    unsigned long long *deadline_p = (unsigned long long *)(abort_flag + 2);
 
     const int tid = threadIdx.x;
     const int nconsumer_warps = BP.nconsumer >> 5;
@@ -153,20 +304,45 @@ __global__ void __launch_bounds__(MAXC + 32, 1)
                         ok = false;
                         break;
                     }
+                    if (p == pl0) {  // the item's descriptor travels with its first plane
+                        BatchDesc &D = desc[slot];
+                        D.item = item;
+                        D.slot = it.slot;
+                        D.y0 = it.y0;
+                        D.v0 = it.v0;
+                        D.x0 = it.x0;
+                        D.x1 = x1;
+                        D.n1 = I.n1;
+                        D.n2 = I.n2;
+                        D.n3 = I.n3;
+                        D.n4 = I.n4;
+                        D.p4 = I.p4;
+                        D.q4 = I.q4;
+                        D.ty = I.ty;
+                        D.tv = I.tv;
+                        D.halo_floats = I.halo_floats;
+                        D.per_step = (unsigned int)nconsumer_warps * (unsigned int)I.nitems;
+                        D.k3 = I.k3;
+                        D.k4 = I.k4;
+                        D.mk34 = I.mk34;
+                        D.dt = (float)sl->st.dt;
+                        D.vout = I.buf + (n & 1) * I.nint;
+                        D.tab = I.tab;
+                    }
                     const bool interior = p >= it.x0 && p < x1;
                     float *dst = stages + (size_t)slot * (BP.stage_bytes / 4);
-                    stage_item[slot] = item;
                     mbar_arrive_expect_tx(&full[slot], tx_halo + (interior ? tx_v0 : 0u));
                     tma_load_4d(dst, m_in, &full[slot], 0, it.v0 - 1, it.y0 - 1, p);
                     if (interior) tma_load_4d(dst + I.halo_floats, m_v0, &full[slot], 0, it.v0, it.y0, p);
                     advance();
                 }
             }
-            // end of work: a stage tagged -1, completed by a plain arrive; it
-            // is that ring slot's last phase, so the drain below waits for it
-            // (a parity wait only tells the current phase from the one before)
+            // end of work: a stage whose descriptor says so, completed by a
+            // plain arrive; it is that ring slot's last phase, so the drain
+            // below waits for it (a parity wait only tells the current phase
+            // from the one before)
             if (ok && next_slot()) {
-                stage_item[slot] = -1;
+                desc[slot].item = -1;
                 mbar_arrive(&full[slot]);
                 advance();
             } else {
@@ -189,165 +365,52 @@ __global__ void __launch_bounds__(MAXC + 32, 1)
         const int nst = BP.stages;
         const int sfl = BP.stage_bytes / 4;
         bool ok = true;
-#define HJ_WAIT_NEXT(slot_out)                                   \
-    do {                                                         \
-        if (!mbar_wait_warp(&full[wslot], wphase, deadline_p)) { \
-            slot_out = -1;                                       \
-        } else {                                                 \
-            slot_out = wslot;                                    \
-            if (++wslot == nst) {                                \
-                wslot = 0;                                       \
-                wphase ^= 1u;                                    \
-            }                                                    \
-        }                                                        \
-    } while (0)
-#define HJ_RELEASE_OLDEST()                            \
-    do {                                               \
-        __syncwarp();                                  \
-        if (lane == 0) mbar_arrive(&empty[rslot]);     \
-        if (++rslot == nst) rslot = 0;                 \
-    } while (0)
         while (ok) {
-            int s_first;
-            HJ_WAIT_NEXT(s_first);
-            if (s_first < 0) {
+            // a producer that gave up stops the consumers at the next item (a
+            // plane that never arrives ends their bounded waits instead)
+            if (__any_sync(0xffffffffu, *abort_flag != 0)) {
                 ok = false;
                 break;
             }
-            const int item = stage_item[s_first];
-            if (item < 0) break;  // no more work
-            const BatchItem it = items[item];
-            const BatchInst &I = insts[it.slot];
-            BatchSlot *sl = &slots[it.slot];
-            const int N1 = I.n1, N2 = I.n2, N3 = I.n3, N4 = I.n4, P4 = I.p4, q4 = I.q4, tv = I.tv;
-            const int x0 = it.x0, x1 = min(it.x0 + I.xc, N1), pl0 = max(x0 - 1, 0), pl1 = min(x1, N1 - 1);
-            const long long n = sl->st.n;
-            const float dt = (float)sl->st.dt;
-            float *vout = I.buf + (n & 1) * I.nint;
-
-            const int q = tid % q4, r = tid / q4;
-            const int srow = tv + 2;
-            const int jy = r / tv, kv = r - (r / tv) * tv;
-            const bool inrow = r < I.ty * tv;
-            const int y = it.y0 + jy, v = it.v0 + kv;
-            const bool rok = inrow && y < N2 && v < N3;
-            const int rsm = rok ? ((jy + 1) * srow + (kv + 1)) * P4 + 4 * q : (srow + 1) * P4;
-            const int r0sm = I.halo_floats + (rok ? (jy * tv + kv) * P4 + 4 * q : 0);
-            const uint32_t s1 = (uint32_t)N2 * N3 * P4;
-            const uint32_t rbase = rok ? ((uint32_t)y * N3 + v) * P4 + 4 * q : 0u;
-            const uint32_t gmask = (y == 0 ? 1u : 0u) | (y == N2 - 1 ? 2u : 0u) | (v == 0 ? 4u : 0u) |
-                                   (v == N3 - 1 ? 8u : 0u);
-            const int lm = (4 * q - 1 + N4) % N4, lp = (4 * q + 4) % N4, lreal = min(4, N4 - 4 * q);
-            float wx[4], wxm[4], wy[4], wym[4], cs[4];
-            float vk = 0.f;
-            if (rok) {
-                // xdot_1 = v cos(th), xdot_2 = v sin(th): a negative speed flips
-                // the upwind sides, and the weights take |v|
-                vk = I.tab[v];
-                const float sg = vk < 0.f ? -1.f : 1.f;
-                vk = fabsf(vk);
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const float c = sg * I.tab[N3 + 4 * q + e], s = sg * I.tab[N3 + P4 + 4 * q + e];
-                    wx[e] = fmaxf(c, 0.f);
-                    wxm[e] = fmaxf(-c, 0.f);
-                    wy[e] = fmaxf(s, 0.f);
-                    wym[e] = fmaxf(-s, 0.f);
-                    cs[e] = fabsf(c) + fabsf(s);
-                }
-            } else {
-#pragma unroll
-                for (int e = 0; e < 4; ++e) wx[e] = wxm[e] = wy[e] = wym[e] = cs[e] = 0.f;
-            }
-
-            int s_x = s_first;
-            if (x0 > pl0) HJ_WAIT_NEXT(s_x);
-            if (s_x < 0) {
+            int s_first = -1;
+            if (!mbar_wait_warp(&full[wslot], wphase, deadline_p)) {
                 ok = false;
                 break;
             }
-            float4 cur = *(const float4 *)(stages + (size_t)s_x * sfl + rsm);
-            int s_prev = x0 > pl0 ? s_first : -1;
-            for (int x = x0; x < x1; ++x) {
-                if (__any_sync(0xffffffffu, *abort_flag != 0)) {
-                    ok = false;
-                    break;
-                }
-                const float *sx = stages + (size_t)s_x * sfl;
-                int s_n = -1;
-                float4 prev, nxt;
-                if (x + 1 <= N1 - 1) {
-                    HJ_WAIT_NEXT(s_n);
-                    if (s_n < 0) {
-                        ok = false;
-                        break;
-                    }
-                    nxt = *(const float4 *)(stages + (size_t)s_n * sfl + rsm);
-                    prev = s_prev >= 0 ? *(const float4 *)(stages + (size_t)s_prev * sfl + rsm) : f4ghost(cur, nxt);
-                } else {
-                    prev = s_prev >= 0 ? *(const float4 *)(stages + (size_t)s_prev * sfl + rsm) : cur;
-                    nxt = f4ghost(cur, prev);
-                }
-                if (rok) {
-                    const float *row = sx + rsm;
-                    float4 ym = *(const float4 *)(row - srow * P4);
-                    float4 yp = *(const float4 *)(row + srow * P4);
-                    float4 vm = *(const float4 *)(row - P4);
-                    float4 vp = *(const float4 *)(row + P4);
-                    if (gmask) {  // extrapolated points past the y / v ends (Sec. II-B)
-                        if (gmask & 1u) ym = f4ghost(cur, yp);
-                        if (gmask & 2u) yp = f4ghost(cur, ym);
-                        if (gmask & 4u) vm = f4ghost(cur, vp);
-                        if (gmask & 8u) vp = f4ghost(cur, vm);
-                    }
-                    const float *row0 = row - 4 * q;
-                    const float tl = row0[lm], tr = row0[lp], t0 = row0[0];
-                    const float4 v0c = *(const float4 *)(sx + r0sm);
-                    float4 out;
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const float vc = f4get(cur, e);
-                        const float tm = e == 0 ? tl : f4get(cur, e - 1);
-                        float tp = e == 3 ? tr : f4get(cur, e + 1);
-                        if (lreal < 4 && e == lreal - 1) tp = t0;  // wrap of a padded last quad
-                        float in = wx[e] * f4get(nxt, e);
-                        in = fmaf(wxm[e], f4get(prev, e), in);
-                        in = fmaf(wy[e], f4get(yp, e), in);
-                        in = fmaf(wym[e], f4get(ym, e), in);
-                        in = fmaf(-cs[e], vc, in);
-                        float acc = fmaf(I.k3, fmaxf(f4get(vp, e), f4get(vm, e)), I.mk34 * vc);
-                        acc = fmaf(I.k4, fmaxf(tp, tm), acc);
-                        acc = fmaf(vk, in, acc);
-                        float vn = fminf(f4get(v0c, e), fmaf(dt, acc, vc));
-                        if (e >= lreal) vn = 0.f;
-                        f4set(out, e, vn);
-                    }
-                    *(float4 *)(vout + (uint32_t)x * s1 + rbase) = out;
-                }
-                if (s_prev >= 0) HJ_RELEASE_OLDEST();
-                s_prev = s_x;
-                s_x = s_n;
-                cur = nxt;
+            s_first = wslot;
+            if (++wslot == nst) {
+                wslot = 0;
+                wphase ^= 1u;
             }
+            const BatchDesc d = desc[s_first];
+            if (d.item < 0) break;  // no more work
+            const int q = tid % d.q4, r = tid / d.q4;
+            const int jy = r / d.tv, kv = r - (r / d.tv) * d.tv;
+            const bool inrow = r < d.ty * d.tv;
+            const bool rok = inrow && d.y0 + jy < d.n2 && d.v0 + kv < d.n3;
+            ok = (d.p4 != d.n4)
+                     ? batch_item_planes<true>(d, s_first, q, jy, kv, rok, stages, sfl, nst, full, empty, deadline_p,
+                                               lane, wslot, wphase, rslot)
+                     : batch_item_planes<false>(d, s_first, q, jy, kv, rok, stages, sfl, nst, full, empty, deadline_p,
+                                                lane, wslot, wphase, rslot);
             if (!ok) break;
-            HJ_RELEASE_OLDEST();
-            if (x1 <= pl1) HJ_RELEASE_OLDEST();
 
             // count the warp done; the warp completing the slot's step
             // reduces the slot's alpha^max over its per-speed table (every cell
             // of the slot was updated in this step, and the car's velocity
             // depends on v and theta only: the same maxima as over the cells)
             // and finalises the step
+            BatchSlot *sl = &slots[d.slot];
             unsigned int last = 0u;
             if (lane == 0) {
                 __threadfence();
-                const unsigned int per_step = (unsigned int)nconsumer_warps * (unsigned int)I.nitems;
-                last = atomicAdd(&sl->warps_done, 1u) + 1 == per_step;
+                last = atomicAdd(&sl->warps_done, 1u) + 1 == d.per_step;
             }
             if (__shfl_sync(0xffffffffu, last, 0)) {
                 __threadfence();
+                const BatchInst &I = insts[d.slot];
                 unsigned long long a1 = 0ull, a2 = 0ull;
-                for (int e = lane; e < N3; e += 32) {
+                for (int e = lane; e < d.n3; e += 32) {
                     const double2 am = I.amaxv[e];
                     const unsigned long long b1 = hj_abits(am.x), b2 = hj_abits(am.y);
                     a1 = a1 > b1 ? a1 : b1;
@@ -364,8 +427,6 @@ __global__ void __launch_bounds__(MAXC + 32, 1)
                 }
             }
         }
-#undef HJ_WAIT_NEXT
-#undef HJ_RELEASE_OLDEST
         if (!ok) {
             ctl->status = HJ_ERR_TIMEOUT;
             *abort_flag = 1;
@@ -382,7 +443,6 @@ __global__ void __launch_bounds__(MAXC + 32, 1)
         }
     }
 }
-
 }  // namespace
 
 // ======================================================================== host
@@ -422,8 +482,9 @@ BatchKernelFn batch_kernel(int nconsumer)
 
 size_t batch_smem(const BatchParams &bp)
 {
-    return (size_t)bp.stages * bp.stage_bytes + 2 * B_MAX_STAGES * sizeof(uint64_t) + (B_MAX_STAGES + 4) * sizeof(int) +
-           2 * sizeof(unsigned long long) + 32;
+    // ring, full / empty barriers, item descriptors, abort flag, deadline
+    return (size_t)bp.stages * bp.stage_bytes + 2 * B_MAX_STAGES * sizeof(uint64_t) + B_MAX_STAGES * sizeof(BatchDesc) +
+           2 * sizeof(int) + sizeof(unsigned long long) + 32;
 }
 
 struct SlotHost {
