@@ -165,6 +165,14 @@ __device__ __forceinline__ bool batch_item_planes(const BatchDesc &d, int s_firs
 #pragma unroll
         for (int e = 0; e < 4; ++e) wx[e] = wxm[e] = wy[e] = wym[e] = cs[e] = 0.f;
     }
+    // the weights as lane pairs (0, 1), (2, 3) and the constants broadcast
+    const float2 wx01 = make_float2(wx[0], wx[1]), wx23 = make_float2(wx[2], wx[3]);
+    const float2 wxm01 = make_float2(wxm[0], wxm[1]), wxm23 = make_float2(wxm[2], wxm[3]);
+    const float2 wy01 = make_float2(wy[0], wy[1]), wy23 = make_float2(wy[2], wy[3]);
+    const float2 wym01 = make_float2(wym[0], wym[1]), wym23 = make_float2(wym[2], wym[3]);
+    const float2 ncs01 = make_float2(-cs[0], -cs[1]), ncs23 = make_float2(-cs[2], -cs[3]);
+    const float2 k3p = make_float2(k3, k3), k4p = make_float2(k4, k4), mk34p = make_float2(mk34, mk34);
+    const float2 vkp = make_float2(vk, vk), dtp = make_float2(dt, dt);
     int s_x = s_first;
     if (x0 > pl0) HJ_WAIT_NEXT(s_x);
     if (s_x < 0) return false;
@@ -202,24 +210,43 @@ __device__ __forceinline__ bool batch_item_planes(const BatchDesc &d, int s_firs
             float t0 = 0.f;
             if (PADDED) t0 = row0[0];
             const float4 v0c = *(const float4 *)(sx + r0sm);
-            float4 out;
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const float vc = f4get(cur, e);
-                const float tm = e == 0 ? tl : f4get(cur, e - 1);
-                float tp = e == 3 ? tr : f4get(cur, e + 1);
-                if (PADDED && lreal < 4 && e == lreal - 1) tp = t0;  // wrap of a padded last quad
-                float in = wx[e] * f4get(nxt, e);
-                in = fmaf(wxm[e], f4get(prev, e), in);
-                in = fmaf(wy[e], f4get(yp, e), in);
-                in = fmaf(wym[e], f4get(ym, e), in);
-                in = fmaf(-cs[e], vc, in);
-                float acc = fmaf(k3, fmaxf(f4get(vp, e), f4get(vm, e)), mk34 * vc);
-                acc = fmaf(k4, fmaxf(tp, tm), acc);
-                acc = fmaf(vk, in, acc);
-                float vn = fminf(f4get(v0c, e), fmaf(dt, acc, vc));
-                if (PADDED && e >= lreal) vn = 0.f;
-                f4set(out, e, vn);
+            // theta neighbours: the larger of the two, per lane
+            float tp3 = tr, tp2 = cur.w, tp1 = cur.z, tp0 = cur.y;
+            if (PADDED && lreal < 4) {  // wrap of a padded last quad
+                if (lreal == 1) tp0 = t0;
+                if (lreal == 2) tp1 = t0;
+                if (lreal == 3) tp2 = t0;
+            }
+            const float2 mt01 = make_float2(fmaxf(tp0, tl), fmaxf(tp1, cur.x));
+            const float2 mt23 = make_float2(fmaxf(tp2, cur.y), fmaxf(tp3, cur.z));
+            const float2 mv01 = make_float2(fmaxf(vp.x, vm.x), fmaxf(vp.y, vm.y));
+            const float2 mv23 = make_float2(fmaxf(vp.z, vm.z), fmaxf(vp.w, vm.w));
+            const float2 c01 = make_float2(cur.x, cur.y), c23 = make_float2(cur.z, cur.w);
+            // lanes (0, 1) and (2, 3) in paired FP32 multiply-adds: the same
+            // operations in the same order as one lane at a time, so the same bits
+            float2 in01 = __fmul2_rn(wx01, make_float2(nxt.x, nxt.y));
+            float2 in23 = __fmul2_rn(wx23, make_float2(nxt.z, nxt.w));
+            in01 = __ffma2_rn(wxm01, make_float2(prev.x, prev.y), in01);
+            in23 = __ffma2_rn(wxm23, make_float2(prev.z, prev.w), in23);
+            in01 = __ffma2_rn(wy01, make_float2(yp.x, yp.y), in01);
+            in23 = __ffma2_rn(wy23, make_float2(yp.z, yp.w), in23);
+            in01 = __ffma2_rn(wym01, make_float2(ym.x, ym.y), in01);
+            in23 = __ffma2_rn(wym23, make_float2(ym.z, ym.w), in23);
+            in01 = __ffma2_rn(ncs01, c01, in01);
+            in23 = __ffma2_rn(ncs23, c23, in23);
+            float2 acc01 = __ffma2_rn(k3p, mv01, __fmul2_rn(mk34p, c01));
+            float2 acc23 = __ffma2_rn(k3p, mv23, __fmul2_rn(mk34p, c23));
+            acc01 = __ffma2_rn(k4p, mt01, acc01);
+            acc23 = __ffma2_rn(k4p, mt23, acc23);
+            acc01 = __ffma2_rn(vkp, in01, acc01);
+            acc23 = __ffma2_rn(vkp, in23, acc23);
+            const float2 u01 = __ffma2_rn(dtp, acc01, c01), u23 = __ffma2_rn(dtp, acc23, c23);
+            float4 out = make_float4(fminf(v0c.x, u01.x), fminf(v0c.y, u01.y), fminf(v0c.z, u23.x),
+                                     fminf(v0c.w, u23.y));
+            if (PADDED && lreal < 4) {  // pad lanes hold 0
+                if (lreal <= 1) out.y = 0.f;
+                if (lreal <= 2) out.z = 0.f;
+                out.w = 0.f;
             }
             *(float4 *)(vout + (uint32_t)x * s1 + rbase) = out;
         }
