@@ -11,14 +11,18 @@
 // neighbouring columns and their halos hit L2), skips items of slots that
 // have reached their horizon, and streams the item's planes (V_n box with a
 // one-cell y/v halo, V0 box without) through the shared-memory ring with
-// TMA, tagging each stage with its item.  Consumers own one (row, theta
-// quad) each, as in the single-grid kernel; the tile shape of each slot is
-// chosen so that its rows x quads fit the block.
+// TMA; the stage of an item's first plane carries the item's descriptor
+// (geometry, the slot's coefficients, dt and output buffer), so consumers
+// start an item from shared memory.  Consumers own one (row, theta quad)
+// each, as in the single-grid kernel, and update lane pairs with paired FP32
+// multiply-adds; the tile shape of each slot is chosen so that its rows x
+// quads fit the block.
 //
 // Time loop: each slot keeps its own FP64 state (t, dt, step count) on the
-// device.  After an item, each consumer warp merges its alpha^max partials
-// into the slot and counts itself done; the warp that completes the slot's
-// last item computes the slot's next CFL step (hj_finalise).  Slots
+// device.  After an item, each consumer warp counts itself done; the warp
+// that completes the slot's last item reduces the slot's alpha^max over its
+// per-speed table of |xdot_1|, |xdot_2| maxima and computes the slot's next
+// CFL step (hj_finalise).  Slots
 // therefore advance independently: a batch step moves every unfinished slot
 // by its own dt, and finished slots cost nothing.
 //
@@ -427,12 +431,12 @@ __global__ void __launch_bounds__(MAXC + 32, 1)
             // of the slot was updated in this step, and the car's velocity
             // depends on v and theta only: the same maxima as over the cells)
             // and finalises the step
+            // (no fence before the count: nothing this launch writes is read in
+            // it by another warp except the count and the slot state, which
+            // only the finalising warp writes; the next launch sees all of it)
             BatchSlot *sl = &slots[d.slot];
             unsigned int last = 0u;
-            if (lane == 0) {
-                __threadfence();
-                last = atomicAdd(&sl->warps_done, 1u) + 1 == d.per_step;
-            }
+            if (lane == 0) last = atomicAdd(&sl->warps_done, 1u) + 1 == d.per_step;
             if (__shfl_sync(0xffffffffu, last, 0)) {
                 __threadfence();
                 const BatchInst &I = insts[d.slot];
