@@ -45,6 +45,10 @@ namespace {
 
 constexpr int B_MAX_STAGES = 8;
 constexpr int B_VARIANTS[4] = {352, 480, 608, 736};
+// Shapes of at most B_DUAL consumers run two CTAs per SM (10 warps each, two
+// independent rings and producers per SM; each CTA gets half the SM's shared
+// memory).
+constexpr int B_DUAL = 288;
 
 struct BatchInst {
     int n1, n2, n3, n4, p4, q4;
@@ -268,8 +272,8 @@ __device__ __forceinline__ bool batch_item_planes(const BatchDesc &d, int s_firs
 #undef HJ_RELEASE_OLDEST
 }
 
-template <int MAXC>
-__global__ void __launch_bounds__(MAXC + 32, 1)
+template <int MAXC, int MINB>
+__global__ void __launch_bounds__(MAXC + 32, MINB)
     hj_batch_step_kernel(const BatchInst *__restrict__ insts, BatchSlot *slots, const BatchItem *__restrict__ items,
                          BatchCtl *ctl, const CUtensorMap *maps, const BatchParams BP)
 {
@@ -505,10 +509,11 @@ typedef void (*BatchKernelFn)(const BatchInst *, BatchSlot *, const BatchItem *,
 
 BatchKernelFn batch_kernel(int nconsumer)
 {
-    if (nconsumer <= B_VARIANTS[0]) return hj_batch_step_kernel<B_VARIANTS[0]>;
-    if (nconsumer <= B_VARIANTS[1]) return hj_batch_step_kernel<B_VARIANTS[1]>;
-    if (nconsumer <= B_VARIANTS[2]) return hj_batch_step_kernel<B_VARIANTS[2]>;
-    return hj_batch_step_kernel<B_VARIANTS[3]>;
+    if (nconsumer <= B_DUAL) return hj_batch_step_kernel<B_DUAL, 2>;
+    if (nconsumer <= B_VARIANTS[0]) return hj_batch_step_kernel<B_VARIANTS[0], 1>;
+    if (nconsumer <= B_VARIANTS[1]) return hj_batch_step_kernel<B_VARIANTS[1], 1>;
+    if (nconsumer <= B_VARIANTS[2]) return hj_batch_step_kernel<B_VARIANTS[2], 1>;
+    return hj_batch_step_kernel<B_VARIANTS[3], 1>;
 }
 
 size_t batch_smem(const BatchParams &bp)
@@ -543,7 +548,7 @@ struct hj_batch {
     size_t budget = 0, used_bytes = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
-    int device = 0, sms = 0, maxsmem = 0;
+    int device = 0, sms = 0, maxsmem = 0, smem_sm = 0;
     std::vector<SlotHost> slots;
     BatchInst *d_insts = nullptr;
     BatchSlot *d_slots = nullptr;
@@ -754,7 +759,10 @@ hj_status rebuild(hj_batch *b)
     BatchParams bp;
     bp.nconsumer = max_cons;
     bp.stage_bytes = stage_bytes;
-    bp.stages = (int)((b->maxsmem - 4096) / stage_bytes);
+    // two CTAs per SM for the smallest shapes: each gets half of the SM's
+    // shared memory, less the 1 KB the runtime reserves per block
+    const int smem_cta = max_cons <= B_DUAL ? b->smem_sm / 2 - 1024 : b->maxsmem;
+    bp.stages = (int)((smem_cta - 4096) / stage_bytes);
     if (bp.stages > B_MAX_STAGES) bp.stages = B_MAX_STAGES;
     if (bp.stages < 4) return bfail(HJ_ERR_UNSUPPORTED, "a slot's tile does not fit four ring stages");
     // device copies
@@ -889,6 +897,8 @@ hj_status hj_batch_create(int32_t max_slots, size_t memory_budget, void *cuda_st
     cudaError_t e = cudaGetDevice(&b->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->maxsmem, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&b->smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, b->device);
     size_t free_b = 0, total_b = 0;
     if (e == cudaSuccess) e = cudaMemGetInfo(&free_b, &total_b);
     b->budget = memory_budget > 0 ? memory_budget : (size_t)(0.9 * (double)free_b);
@@ -1327,9 +1337,9 @@ hj_status hj_batch_autotune(hj_batch *b, int32_t steps_per_trial, int32_t *best_
     const int keep_nc = b->nconsumer_req, keep_ch = b->xc_mode;
     double best = 1e300;
     int best_nc = keep_nc, best_ch = keep_ch;
-    const int ncs[4] = {B_VARIANTS[0], B_VARIANTS[1], B_VARIANTS[2], B_VARIANTS[3]};
+    const int ncs[5] = {B_DUAL, B_VARIANTS[0], B_VARIANTS[1], B_VARIANTS[2], B_VARIANTS[3]};
     const int chs[3] = {1, 2, 4};
-    for (int a = 0; a < 4; ++a)
+    for (int a = 0; a < 5; ++a)
         for (int c = 0; c < 3; ++c) {
             b->nconsumer_req = ncs[a];
             b->xc_mode = chs[c];

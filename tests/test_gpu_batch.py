@@ -108,7 +108,7 @@ def test_batch_shapes_and_autotune_give_identical_bits(hj):
     ws = [scenes.custom_workload(n, n_circles=3, T=0.2, seed=7 + i) for i, n in enumerate(MIXED[:3])]
     v0s = [scenes.initial_value(w.grid, w.scene) for w in ws]
     results = []
-    for shape in ((0, 0), (352, 1), (480, 2), (608, 4), (736, 1), ("tune", 0)):
+    for shape in ((0, 0), (288, 1), (256, 3), (352, 1), (480, 2), (608, 4), (736, 1), ("tune", 0)):
         with hj.Batch(4) as b:
             slots = [b.add_workload(w) for w in ws]
             for s, v0 in zip(slots, v0s):
