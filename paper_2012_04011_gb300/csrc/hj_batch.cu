@@ -36,6 +36,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
 #include <vector>
 
@@ -703,10 +704,29 @@ hj_status rebuild(hj_batch *b)
         const int most = min_n1 / 4 > 1 ? min_n1 / 4 : 1;  // chunks of at least 4 planes
         if (nchunk > most) nchunk = most;
     }
-    for (int i = 0; i < b->max_slots; ++i) {
+    // Item order: slots with the longest columns first.  In the automatic
+    // mode with whole columns, the slots whose items come last in the queue
+    // (about the last two items per SM) are cut into two x chunks, so that
+    // the CTAs of a batch step run out of work at nearly the same time.
+    std::vector<int> order;
+    for (int i = 0; i < b->max_slots; ++i)
+        if (b->slots[i].used) order.push_back(i);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int c) { return b->slots[a].n[0] > b->slots[c].n[0]; });
+    std::vector<int> slot_chunks(b->max_slots, nchunk);
+    if (b->xc_mode == 0 && nchunk == 1) {
+        long long tail = 0;
+        for (int k = (int)order.size() - 1; k >= 0 && tail < 2LL * b->sms; --k) {
+            const SlotHost &s = b->slots[order[k]];
+            if (s.n[0] < 8) break;
+            slot_chunks[order[k]] = 2;
+            tail += 2LL * ((s.n[1] + s.ty - 1) / s.ty) * ((s.n[2] + s.tv - 1) / s.tv);
+        }
+    }
+    for (int oi = 0; oi < (int)order.size(); ++oi) {
+        const int i = order[oi];
         SlotHost &s = b->slots[i];
-        if (!s.used) continue;
-        s.xc = (s.n[0] + nchunk - 1) / nchunk;
+        s.xc = (s.n[0] + slot_chunks[i] - 1) / slot_chunks[i];
         if (s.xc < 4) s.xc = s.n[0] < 4 ? s.n[0] : 4;
         BatchInst &I = insts[i];
         I.n1 = s.n[0];
@@ -1338,9 +1358,9 @@ hj_status hj_batch_autotune(hj_batch *b, int32_t steps_per_trial, int32_t *best_
     double best = 1e300;
     int best_nc = keep_nc, best_ch = keep_ch;
     const int ncs[5] = {B_DUAL, B_VARIANTS[0], B_VARIANTS[1], B_VARIANTS[2], B_VARIANTS[3]};
-    const int chs[3] = {1, 2, 4};
+    const int chs[4] = {0, 1, 2, 4};
     for (int a = 0; a < 5; ++a)
-        for (int c = 0; c < 3; ++c) {
+        for (int c = 0; c < 4; ++c) {
             b->nconsumer_req = ncs[a];
             b->xc_mode = chs[c];
             b->dirty = true;
