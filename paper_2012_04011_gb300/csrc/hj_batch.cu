@@ -124,7 +124,7 @@ __device__ __forceinline__ bool batch_item_planes(const BatchDesc &d, int s_firs
 {
 #define HJ_WAIT_NEXT(slot_out)                                   \
     do {                                                         \
-        if (!mbar_wait_warp(&full[wslot], wphase, deadline_p)) { \
+        if (!mbar_wait_warp<true>(&full[wslot], wphase, deadline_p)) { \
             slot_out = -1;                                       \
         } else {                                                 \
             slot_out = wslot;                                    \
@@ -409,7 +409,7 @@ __global__ void __launch_bounds__(MAXC + 32, MINB)
                 break;
             }
             int s_first = -1;
-            if (!mbar_wait_warp(&full[wslot], wphase, deadline_p)) {
+            if (!mbar_wait_warp<true>(&full[wslot], wphase, deadline_p)) {
                 ok = false;
                 break;
             }

@@ -4,7 +4,8 @@
 // spinning forever.  This kernel exercises exactly that path: one producer
 // thread initialises an mbarrier that expects one arrival and never
 // arrives; the consumer warps wait on it with the same warp-uniform bounded
-// wait (mbar_wait_warp) as the step kernels, give up at the deadline and
+// waits (mbar_wait_warp, with and without the suspend-time hint) as the step
+// kernels, give up at the deadline and
 // record the status.  Nothing faults, traps or hangs; the context stays
 // usable.  The grid-barrier self-test does the same for the resident step
 // kernel's barrier (hj_grid_sync): two co-resident CTAs wait for a third
@@ -53,7 +54,10 @@ __global__ void wait_selftest_kernel(unsigned long long limit_ns, int *status, u
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    const bool ok = mbar_wait_warp(&bar, 0u, &deadline);
+    // warp 0 waits as the HBM-bound step kernels do, warp 1 with the
+    // suspend-time hint of the issue-bound ones
+    const bool ok = (threadIdx.x >> 5) & 1 ? mbar_wait_warp<true>(&bar, 0u, &deadline)
+                                           : mbar_wait_warp<false>(&bar, 0u, &deadline);
     if (!ok && (threadIdx.x & 31) == 0) atomicExch(status, (int)HJ_ERR_TIMEOUT);
     __syncthreads();
     if (threadIdx.x == 0) *waited_ns = global_ns() - t0;

@@ -305,7 +305,7 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
         bool ok = true;
 #define HJ_WAIT_NEXT(slot_out)                                   \
     do {                                                         \
-        if (!mbar_wait_warp(&full[wslot], wphase, deadline_p)) { \
+        if (!mbar_wait_warp<BCAST || FIXED>(&full[wslot], wphase, deadline_p)) { \
             slot_out = -1;                                       \
         } else {                                                 \
             slot_out = wslot;                                    \

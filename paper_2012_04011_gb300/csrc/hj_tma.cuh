@@ -32,6 +32,24 @@ static __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t par
         : "memory");
     return ok != 0;
 }
+// The same try with a suspend-time hint: the thread may sleep until the phase
+// completes or HJ_TRY_WAIT_NS pass, so a waiting warp spins a few times per
+// wait instead of many, leaving issue slots to the warps that compute (the
+// issue-bound kernels gain; the HBM-bound 4D FP32 step, whose warps mostly
+// wait on memory, measured slower with it).
+constexpr uint32_t HJ_TRY_WAIT_NS = 20000u;
+static __device__ __forceinline__ bool mbar_try_wait_hint(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(HJ_TRY_WAIT_NS)
+        : "memory");
+    return ok != 0;
+}
 static __device__ __forceinline__ unsigned long long global_ns()
 {
     unsigned long long t;
@@ -49,10 +67,11 @@ static __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity,
 // Warp-uniform version for consumer warps: every lane observes the phase,
 // and the timeout decision is the same for the whole warp.  The deadline is
 // read (from shared memory) only when the phase is not complete yet.
+template <bool HINT = false>
 static __device__ __forceinline__ bool mbar_wait_warp(uint64_t *bar, uint32_t parity, const unsigned long long *deadline)
 {
     while (true) {
-        bool done = mbar_try_wait(bar, parity);
+        bool done = HINT ? mbar_try_wait_hint(bar, parity) : mbar_try_wait(bar, parity);
         if (__all_sync(0xffffffffu, done)) return true;
         bool late = global_ns() > *deadline;
         if (__any_sync(0xffffffffu, late)) return false;
