@@ -606,9 +606,8 @@ def run_ours(args):
             nc, ch, _ = b.autotune(4)
 
         def batch_solve():
-            for sl, v, bw in zip(slots, v0d, ws):
-                hj.hj_batch_set_initial_value(b.handle, sl, v)
-                b.set_horizon(sl, bw.T, bw.cfl)
+            b.set_initial_values(slots, v0d)  # every slot's V0, one synchronisation
+            b.set_horizons(slots, [bw.T for bw in ws], [bw.cfl for bw in ws])
             return b.advance()
 
         for _ in range(2):

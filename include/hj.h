@@ -390,6 +390,17 @@ HJ_API hj_status hj_batch_set_initial_value(hj_batch *b, int32_t slot, const dou
 HJ_API hj_status hj_batch_set_initial_value_device(hj_batch *b, int32_t slot, const void *v0, hj_precision dtype,
                                                    size_t count);
 
+/* The same for several slots in one call: slots[k] takes the device array
+ * v0[k] of counts[k] values (dtype HJ_FP32 or HJ_FP64; layout as
+ * hj_set_initial_value).  Every argument is checked before anything is
+ * queued; the conversions are queued back to back and one stream
+ * synchronisation covers every slot's NaN / Inf check, so a batch's V0 set
+ * costs one wait instead of one per slot.  A slot whose V0 holds NaN or Inf
+ * is left without a value and the call returns HJ_ERR_INVALID_ARG naming the
+ * first such slot; the others are set. */
+HJ_API hj_status hj_batch_set_initial_values_device(hj_batch *b, int32_t nslots, const int32_t *slots,
+                                                    const void *const *v0, hj_precision dtype, const size_t *counts);
+
 /* As hj_set_initial_value_xy, for a slot. */
 HJ_API hj_status hj_batch_set_initial_value_xy(hj_batch *b, int32_t slot, const double *v0_xy, size_t count);
 
@@ -397,6 +408,11 @@ HJ_API hj_status hj_batch_set_initial_value_xy(hj_batch *b, int32_t slot, const 
  * device; queued on the batch's stream, ordered before the next batch step,
  * without waiting for it). */
 HJ_API hj_status hj_batch_set_horizon(hj_batch *b, int32_t slot, double T, double cfl);
+
+/* The same for several slots in one call (slots[k] takes T[k], cfl[k]);
+ * every argument is checked before anything is queued. */
+HJ_API hj_status hj_batch_set_horizons(hj_batch *b, int32_t nslots, const int32_t *slots, const double *T,
+                                       const double *cfl);
 
 /* Take up to max_steps batch steps (each unfinished slot advances one step
  * per batch step) and return when every slot has reached its horizon or the

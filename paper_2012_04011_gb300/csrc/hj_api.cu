@@ -131,54 +131,7 @@ __global__ void prologue_kernel(HjDevState *st, const HjGeom g, const HjCoef<T> 
                                 const double *k4 = nullptr, double threshold = 0.0)
 {
     __shared__ unsigned long long scratch[64];
-    unsigned long long a1 = 0ull, a2 = 0ull;
-    const bool fresh = st->n == 0 || st->alpha_stale;
-    if (fresh)
-        for (int i = threadIdx.x; i < ncoef; i += blockDim.x) {
-            unsigned long long b1 = hj_abits(coef[i].a1), b2 = hj_abits(coef[i].a2);
-            a1 = a1 > b1 ? a1 : b1;
-            a2 = a2 > b2 ? a2 : b2;
-        }
-    a1 = hj_warp_max_u64(a1);
-    a2 = hj_warp_max_u64(a2);
-    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0) {
-        scratch[warp] = a1;
-        scratch[32 + warp] = a2;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
-            a1 = a1 > scratch[w] ? a1 : scratch[w];
-            a2 = a2 > scratch[32 + w] ? a2 : scratch[32 + w];
-        }
-        st->T = T_end;
-        st->cfl = cfl;
-        // convergence mode (threshold > 0): the steps reduce max |V_{n+1} - V_n|
-        st->track = threshold > 0.0 ? 1 : 0;
-        st->threshold = threshold;
-        st->converged = 0;
-        st->delta_bits = 0ull;
-        st->delta_last = 0.0;
-        double a[4];
-        if (fresh) {
-            a[0] = __longlong_as_double((long long)a1);
-            a[1] = __longlong_as_double((long long)a2);
-            a[2] = g.alpha3;
-            a[3] = g.alpha4;
-            for (int d = 0; d < 4; ++d) st->alpha_prev[d] = a[d];
-            st->alpha_stale = 0;
-        } else {
-            for (int d = 0; d < 4; ++d) a[d] = st->alpha_prev[d];
-        }
-        st->alpha_bits[0] = 0ull;
-        st->alpha_bits[1] = 0ull;
-        st->blocks_done = 0u;
-        if (st->status == HJ_OK)
-            hj_next_dt(st, g, a, st->t);
-        else
-            st->done = 1;
-    }
+    hj_prologue_block(st, g, coef, ncoef, T_end, cfl, threshold, scratch);
     if (scaled || qw) {  // FP64 / Q5.27 grids: the dt-scaled tables must match the first dt
         __syncthreads();
         const volatile HjDevState *vs = st;

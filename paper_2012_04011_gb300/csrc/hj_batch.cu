@@ -95,6 +95,51 @@ static __device__ __forceinline__ void tensormap_acquire(const CUtensorMap *m)
     asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"((unsigned long long)m) : "memory");
 }
 
+// One slot's V0 conversion and first step, for the calls that set up many
+// slots at once (one launch for all of them instead of one per slot).
+struct SlotSetup {
+    const void *src;  // caller's dense V0 (FP64 or FP32)
+    float *dst;       // the slot's V0 in the internal layout
+    HjDevState *st;   // the slot's time-loop state
+    const HjCoef<float> *coef;
+    long long nrows;  // N1 * N2 * N3
+    int n4, p4, ncoef;
+    double T, cfl;
+    HjGeom geom;
+};
+
+// blockIdx.y = entry: dense -> padded rows (pad lanes zero), NaN / Inf flag
+// into the entry's state (the state itself was reset before).
+template <typename Tin>
+__global__ void batch_ingest_many_kernel(const SlotSetup *__restrict__ list)
+{
+    const SlotSetup d = list[blockIdx.y];
+    const Tin *src = (const Tin *)d.src;
+    const long long total = d.nrows * d.p4;
+    int bad = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long row = i / d.p4;
+        const int l = (int)(i - row * d.p4);
+        float v = 0.f;
+        if (l < d.n4) {
+            const double x = (double)src[row * d.n4 + l];
+            if (!isfinite(x)) bad = 1;
+            v = (float)x;
+        }
+        d.dst[i] = v;
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&d.st->nonfinite, 1);
+}
+
+// One block per entry: the solve prologue of the entry's slot.
+__global__ void batch_horizon_many_kernel(const SlotSetup *__restrict__ list)
+{
+    __shared__ unsigned long long scratch[64];
+    const SlotSetup &d = list[blockIdx.x];
+    hj_prologue_block(d.st, d.geom, d.coef, d.ncoef, d.T, d.cfl, 0.0, scratch);
+}
+
 // What the consumers need of a work item, written into shared memory by the
 // producer (with the item's first plane; the full barrier's arrive releases
 // it), so that an item starts without a chain of dependent global loads.
@@ -567,6 +612,9 @@ struct hj_batch {
     std::vector<std::pair<long long, cudaGraphExec_t>> graphs;
     cudaEvent_t ev[2] = {nullptr, nullptr};
     cudaEvent_t ev_in = nullptr;  // own stream: orders device inputs after the legacy default stream
+    SlotSetup *h_setup = nullptr;  // pinned staging of the multi-slot set-up lists (max_slots entries)
+    SlotSetup *d_setup = nullptr;  // their device copy
+    cudaEvent_t ev_setup = nullptr;  // the last staging copy has been read
 };
 
 namespace {
@@ -931,6 +979,9 @@ hj_status hj_batch_create(int32_t max_slots, size_t memory_budget, void *cuda_st
     if (e == cudaSuccess) e = cudaMalloc(&b->d_insts, sizeof(BatchInst) * max_slots);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_slots, sizeof(BatchSlot) * max_slots);
     if (e == cudaSuccess) e = cudaHostAlloc(&b->h_slots, sizeof(BatchSlot) * max_slots, cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaHostAlloc(&b->h_setup, sizeof(SlotSetup) * max_slots, cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_setup, sizeof(SlotSetup) * max_slots);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_setup, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_ctl, sizeof(BatchCtl));
     if (e == cudaSuccess) e = cudaMalloc(&b->d_maps, sizeof(CUtensorMap) * 4 * max_slots);
     for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaEventCreate(&b->ev[i]);
@@ -963,6 +1014,9 @@ void hj_batch_destroy(hj_batch *b)
     if (b->d_insts) cudaFree(b->d_insts);
     if (b->d_slots) cudaFree(b->d_slots);
     if (b->h_slots) cudaFreeHost(b->h_slots);
+    if (b->h_setup) cudaFreeHost(b->h_setup);
+    if (b->d_setup) cudaFree(b->d_setup);
+    if (b->ev_setup) cudaEventDestroy(b->ev_setup);
     if (b->d_items) cudaFree(b->d_items);
     if (b->d_ctl) cudaFree(b->d_ctl);
     if (b->d_maps) cudaFree(b->d_maps);
@@ -1096,28 +1150,31 @@ hj_status hj_batch_remove(hj_batch *b, int32_t slot)
     return HJ_OK;
 }
 
-static hj_status batch_ingest(hj_batch *b, int32_t slot, const void *src, hj_precision type, bool on_host,
-                              size_t count)
+// Checks a slot's V0 arguments.
+static hj_status ingest_check(hj_batch *b, int32_t slot, const void *src, size_t count)
 {
     hj_status s = check_slot(b, slot);
     if (s != HJ_OK) return s;
-    SlotHost &sl = b->slots[slot];
     if (!src) return bfail(HJ_ERR_INVALID_ARG, "v0 is NULL");
-    if (count != (size_t)sl.ncell) return bfail(HJ_ERR_INVALID_ARG, "count %zu != %lld", count, sl.ncell);
+    if (count != (size_t)b->slots[slot].ncell)
+        return bfail(HJ_ERR_INVALID_ARG, "count %zu != %lld", count, b->slots[slot].ncell);
+    return HJ_OK;
+}
+
+// Queues a slot's V0 ingest (reset state, staging copy, conversion kernel
+// with its NaN / Inf flag) on the batch's stream, without waiting.
+static hj_status ingest_queue(hj_batch *b, int32_t slot, const void *src, hj_precision type, bool on_host)
+{
+    SlotHost &sl = b->slots[slot];
     // (every call of the batch API returns with its stream work done or with
     // a synchronisation after its last use of the host mirror, so the mirror
     // entry is free to rewrite; the reset state is queued, not waited for)
     memset(&b->h_slots[slot], 0, sizeof(BatchSlot));
     b->h_slots[slot].st.done = 1;  // until a horizon is set
     b->h_slots[slot].st.status = HJ_OK;
+    hj_status s;
     if ((s = push_slot_async(b, slot)) != HJ_OK) return s;
     const void *dsrc = src;
-    if (!on_host && b->own_stream) {
-        // a batch on its own (non-blocking) stream reads a caller's device array
-        // only after the work already queued on the legacy default stream
-        HJB_CUDA(cudaEventRecord(b->ev_in, cudaStreamLegacy));
-        HJB_CUDA(cudaStreamWaitEvent(b->stream, b->ev_in, 0));
-    }
     if (on_host) {  // stage the FP64 array in the slot's A|B region (2 nint floats >= ncell doubles)
         HJB_CUDA(cudaMemcpyAsync(sl.buf, src, sizeof(double) * (size_t)sl.ncell, cudaMemcpyHostToDevice, b->stream));
         dsrc = sl.buf;
@@ -1125,6 +1182,28 @@ static hj_status batch_ingest(hj_batch *b, int32_t slot, const void *src, hj_pre
     int *flag = &b->d_slots[slot].st.nonfinite;
     HJB_CUDA(hj_launch_ingest_f32(dsrc, type, sl.v0, sl.n[3], sl.p4, (long long)sl.n[0] * sl.n[1] * sl.n[2], flag,
                                   b->stream));
+    return HJ_OK;
+}
+
+// A batch on its own (non-blocking) stream reads a caller's device arrays
+// only after the work already queued on the legacy default stream.
+static hj_status order_after_default_stream(hj_batch *b)
+{
+    if (b->own_stream) {
+        HJB_CUDA(cudaEventRecord(b->ev_in, cudaStreamLegacy));
+        HJB_CUDA(cudaStreamWaitEvent(b->stream, b->ev_in, 0));
+    }
+    return HJ_OK;
+}
+
+static hj_status batch_ingest(hj_batch *b, int32_t slot, const void *src, hj_precision type, bool on_host,
+                              size_t count)
+{
+    hj_status s = ingest_check(b, slot, src, count);
+    if (s != HJ_OK) return s;
+    SlotHost &sl = b->slots[slot];
+    if (!on_host && (s = order_after_default_stream(b)) != HJ_OK) return s;
+    if ((s = ingest_queue(b, slot, src, type, on_host)) != HJ_OK) return s;
     bool bad = false;
     if ((s = pull_nonfinite(b, slot, &bad)) != HJ_OK) return s;
     if (bad) {
@@ -1174,6 +1253,69 @@ hj_status hj_batch_set_initial_value_device(hj_batch *b, int32_t slot, const voi
     return batch_ingest(b, slot, v0, dtype, false, count);
 }
 
+hj_status hj_batch_set_initial_values_device(hj_batch *b, int32_t nslots, const int32_t *slots,
+                                             const void *const *v0, hj_precision dtype, const size_t *counts)
+{
+    hj_internal_set_error("");
+    if (!b) return bfail(HJ_ERR_INVALID_ARG, "batch is NULL");
+    if (nslots < 0 || (nslots > 0 && (!slots || !v0 || !counts)))
+        return bfail(HJ_ERR_INVALID_ARG, "nslots must be >= 0 with non-NULL slots, v0 and counts");
+    if (dtype != HJ_FP64 && dtype != HJ_FP32) return bfail(HJ_ERR_INVALID_ARG, "unknown dtype");
+    hj_status s;
+    for (int32_t k = 0; k < nslots; ++k)  // every argument first: nothing is queued for a bad call
+        if ((s = ingest_check(b, slots[k], v0[k], counts[k])) != HJ_OK) return s;
+    if (nslots == 0) return HJ_OK;
+    if ((s = order_after_default_stream(b)) != HJ_OK) return s;
+    // reset the slots' states: the mirror entries, pushed as runs of
+    // consecutive slots
+    for (int32_t k = 0; k < nslots; ++k) {
+        memset(&b->h_slots[slots[k]], 0, sizeof(BatchSlot));
+        b->h_slots[slots[k]].st.done = 1;  // until a horizon is set
+    }
+    std::vector<int32_t> sorted(slots, slots + nslots);
+    std::sort(sorted.begin(), sorted.end());
+    sorted.erase(std::unique(sorted.begin(), sorted.end()), sorted.end());
+    for (size_t a = 0; a < sorted.size();) {
+        size_t c = a + 1;
+        while (c < sorted.size() && sorted[c] == sorted[c - 1] + 1) ++c;
+        HJB_CUDA(cudaMemcpyAsync(&b->d_slots[sorted[a]], &b->h_slots[sorted[a]], sizeof(BatchSlot) * (c - a),
+                                 cudaMemcpyHostToDevice, b->stream));
+        a = c;
+    }
+    // one conversion launch for all the slots
+    HJB_CUDA(cudaEventSynchronize(b->ev_setup));  // the previous list has been copied
+    long long most = 1;
+    for (int32_t k = 0; k < nslots; ++k) {
+        const SlotHost &sl = b->slots[slots[k]];
+        SlotSetup &e = b->h_setup[k];
+        e.src = v0[k];
+        e.dst = sl.v0;
+        e.st = &b->d_slots[slots[k]].st;
+        e.nrows = (long long)sl.n[0] * sl.n[1] * sl.n[2];
+        e.n4 = sl.n[3];
+        e.p4 = sl.p4;
+        if (e.nrows * e.p4 > most) most = e.nrows * e.p4;
+    }
+    HJB_CUDA(cudaMemcpyAsync(b->d_setup, b->h_setup, sizeof(SlotSetup) * nslots, cudaMemcpyHostToDevice, b->stream));
+    HJB_CUDA(cudaEventRecord(b->ev_setup, b->stream));
+    long long bx = (most + 255) / 256;
+    if (bx > 1024) bx = 1024;
+    const dim3 grid((unsigned)bx, (unsigned)nslots);
+    if (dtype == HJ_FP64) batch_ingest_many_kernel<double><<<grid, 256, 0, b->stream>>>(b->d_setup);
+    else batch_ingest_many_kernel<float><<<grid, 256, 0, b->stream>>>(b->d_setup);
+    HJB_CUDA(cudaGetLastError());
+    // one synchronisation for every slot's NaN / Inf check
+    if ((s = pull_slots(b)) != HJ_OK) return s;
+    int first_bad = -1;
+    for (int32_t k = 0; k < nslots; ++k) {
+        const bool bad = b->h_slots[slots[k]].st.nonfinite != 0;
+        b->slots[slots[k]].has_value = !bad;
+        if (bad && first_bad < 0) first_bad = slots[k];
+    }
+    if (first_bad >= 0) return bfail(HJ_ERR_INVALID_ARG, "slot %d: V0 contains NaN or Inf", first_bad);
+    return HJ_OK;
+}
+
 hj_status hj_batch_set_horizon(hj_batch *b, int32_t slot, double T, double cfl)
 {
     hj_internal_set_error("");
@@ -1188,6 +1330,42 @@ hj_status hj_batch_set_horizon(hj_batch *b, int32_t slot, double T, double cfl)
     // queued on the batch's stream (ordered before the next batch step); the
     // calls that read slot states synchronise first
     HJB_CUDA(hj_launch_prologue_f32(&b->d_slots[slot].st, sl.geom, sl.coef, sl.n[2] * sl.n[3], T, cfl, b->stream));
+    return HJ_OK;
+}
+
+hj_status hj_batch_set_horizons(hj_batch *b, int32_t nslots, const int32_t *slots, const double *T, const double *cfl)
+{
+    hj_internal_set_error("");
+    if (!b) return bfail(HJ_ERR_INVALID_ARG, "batch is NULL");
+    if (nslots < 0 || (nslots > 0 && (!slots || !T || !cfl)))
+        return bfail(HJ_ERR_INVALID_ARG, "nslots must be >= 0 with non-NULL slots, T and cfl");
+    hj_status s;
+    for (int32_t k = 0; k < nslots; ++k) {  // every argument first: nothing is queued for a bad call
+        if ((s = check_slot(b, slots[k])) != HJ_OK) return s;
+        if (!isfinite(T[k]) || T[k] < 0) return bfail(HJ_ERR_INVALID_ARG, "slot %d: T must be finite and >= 0", slots[k]);
+        if (!isfinite(cfl[k]) || !(cfl[k] > 0) || cfl[k] > 1)
+            return bfail(HJ_ERR_INVALID_ARG, "slot %d: cfl must be in (0, 1]", slots[k]);
+        if (!b->slots[slots[k]].has_value) return bfail(HJ_ERR_STATE, "slot %d has no initial value", slots[k]);
+    }
+    if (nslots == 0) return HJ_OK;
+    HJB_CUDA(cudaEventSynchronize(b->ev_setup));  // the previous list has been copied
+    for (int32_t k = 0; k < nslots; ++k) {
+        SlotHost &sl = b->slots[slots[k]];
+        sl.T = T[k];
+        sl.cfl = cfl[k];
+        SlotSetup &e = b->h_setup[k];
+        e.st = &b->d_slots[slots[k]].st;
+        e.geom = sl.geom;
+        e.coef = sl.coef;
+        e.ncoef = sl.n[2] * sl.n[3];
+        e.T = T[k];
+        e.cfl = cfl[k];
+    }
+    // one launch, one block per slot (queued; ordered before the next batch step)
+    HJB_CUDA(cudaMemcpyAsync(b->d_setup, b->h_setup, sizeof(SlotSetup) * nslots, cudaMemcpyHostToDevice, b->stream));
+    HJB_CUDA(cudaEventRecord(b->ev_setup, b->stream));
+    batch_horizon_many_kernel<<<nslots, 256, 0, b->stream>>>(b->d_setup);
+    HJB_CUDA(cudaGetLastError());
     return HJ_OK;
 }
 

@@ -109,6 +109,66 @@ __device__ __forceinline__ void hj_finalise(HjDevState *st, const HjGeom &g)
     __threadfence();
 }
 
+// Start of a solve call, run by one block: horizon, Courant number and the
+// dt of the first step.  Right after V0 is set (n == 0), or after new
+// dynamics, alpha^max is reduced over the (v, theta) coefficient table, which
+// holds |xdot_1|, |xdot_2| of every cell (the car's velocity depends only on
+// v and theta).  scratch holds at least 64 values.
+template <typename T>
+__device__ __forceinline__ void hj_prologue_block(HjDevState *st, const HjGeom &g, const HjCoef<T> *__restrict__ coef,
+                                                  int ncoef, double T_end, double cfl, double threshold,
+                                                  unsigned long long *scratch)
+{
+    unsigned long long a1 = 0ull, a2 = 0ull;
+    const bool fresh = st->n == 0 || st->alpha_stale;
+    if (fresh)
+        for (int i = threadIdx.x; i < ncoef; i += blockDim.x) {
+            unsigned long long b1 = hj_abits(coef[i].a1), b2 = hj_abits(coef[i].a2);
+            a1 = a1 > b1 ? a1 : b1;
+            a2 = a2 > b2 ? a2 : b2;
+        }
+    a1 = hj_warp_max_u64(a1);
+    a2 = hj_warp_max_u64(a2);
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        scratch[warp] = a1;
+        scratch[32 + warp] = a2;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+            a1 = a1 > scratch[w] ? a1 : scratch[w];
+            a2 = a2 > scratch[32 + w] ? a2 : scratch[32 + w];
+        }
+        st->T = T_end;
+        st->cfl = cfl;
+        // convergence mode (threshold > 0): the steps reduce max |V_{n+1} - V_n|
+        st->track = threshold > 0.0 ? 1 : 0;
+        st->threshold = threshold;
+        st->converged = 0;
+        st->delta_bits = 0ull;
+        st->delta_last = 0.0;
+        double a[4];
+        if (fresh) {
+            a[0] = __longlong_as_double((long long)a1);
+            a[1] = __longlong_as_double((long long)a2);
+            a[2] = g.alpha3;
+            a[3] = g.alpha4;
+            for (int d = 0; d < 4; ++d) st->alpha_prev[d] = a[d];
+            st->alpha_stale = 0;
+        } else {
+            for (int d = 0; d < 4; ++d) a[d] = st->alpha_prev[d];
+        }
+        st->alpha_bits[0] = 0ull;
+        st->alpha_bits[1] = 0ull;
+        st->blocks_done = 0u;
+        if (st->status == HJ_OK)
+            hj_next_dt(st, g, a, st->t);
+        else
+            st->done = 1;
+    }
+}
+
 // Block-wide max of the CTA's |xdot_1|, |xdot_2| partials and of its largest
 // change |V_{n+1} - V_n| (bit patterns of non-negative doubles; the change
 // is 0 outside the convergence mode).  Every thread of the block must call

@@ -183,6 +183,11 @@ _SIGS = {
     "hj_batch_set_initial_value": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
                                                   ctypes.c_size_t]),
     "hj_batch_set_initial_value_device": (ctypes.c_int, [_VP, ctypes.c_int32, _VP, ctypes.c_int, ctypes.c_size_t]),
+    "hj_batch_set_horizons": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                                             ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+    "hj_batch_set_initial_values_device": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                                                          ctypes.POINTER(_VP), ctypes.c_int,
+                                                          ctypes.POINTER(ctypes.c_size_t)]),
     "hj_batch_set_horizon": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_double, ctypes.c_double]),
     "hj_batch_advance": (ctypes.c_int, [_VP, ctypes.c_int64, ctypes.POINTER(hj_batch_stats)]),
     "hj_batch_get_slot_info": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.POINTER(hj_batch_slot_info)]),
@@ -555,6 +560,35 @@ def hj_batch_set_initial_value(b, slot: int, v0):
         _check(lib.hj_batch_set_initial_value(b, int(slot), a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), a.size))
 
 
+def hj_batch_set_initial_values_device(b, slots, v0s):
+    """V0 of several slots from CUDA tensors of one dtype (float32 or float64),
+    with one synchronisation for all of them."""
+    n = len(slots)
+    if n != len(v0s):
+        raise ValueError("one V0 tensor per slot")
+    if n == 0:
+        return
+    dtypes = {_dtype_code(v) for v in v0s}
+    if len(dtypes) != 1 or HJ_Q527 in dtypes:
+        raise ValueError("the V0 tensors must all be float32 or all float64")
+    cs = (ctypes.c_int32 * n)(*[int(s) for s in slots])
+    ps = (_VP * n)(*[_dptr(v) for v in v0s])
+    cnt = (ctypes.c_size_t * n)(*[int(v.numel()) for v in v0s])
+    _check(lib.hj_batch_set_initial_values_device(b, n, cs, ps, dtypes.pop(), cnt))
+
+
+def hj_batch_set_horizons(b, slots, T, cfl):
+    """Horizons and Courant numbers of several slots in one call."""
+    n = len(slots)
+    if not (n == len(T) == len(cfl)):
+        raise ValueError("one T and one cfl per slot")
+    if n == 0:
+        return
+    _check(lib.hj_batch_set_horizons(b, n, (ctypes.c_int32 * n)(*[int(s) for s in slots]),
+                                     (ctypes.c_double * n)(*[float(t) for t in T]),
+                                     (ctypes.c_double * n)(*[float(c) for c in cfl])))
+
+
 def hj_batch_set_initial_value_xy(b, slot: int, v0_xy):
     a = np.ascontiguousarray(v0_xy, dtype=np.float64)
     _check(lib.hj_batch_set_initial_value_xy(b, int(slot), a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), a.size))
@@ -619,6 +653,12 @@ class Batch:
 
     def set_initial_value(self, slot, v0):
         hj_batch_set_initial_value(self.handle, slot, v0)
+
+    def set_initial_values(self, slots, v0s):
+        hj_batch_set_initial_values_device(self.handle, slots, v0s)
+
+    def set_horizons(self, slots, T, cfl):
+        hj_batch_set_horizons(self.handle, slots, T, cfl)
 
     def set_initial_value_xy(self, slot, v0_xy):
         hj_batch_set_initial_value_xy(self.handle, slot, v0_xy)

@@ -179,3 +179,42 @@ def test_batch_slot_with_negative_speeds(hj):
     assert np.array_equal(V, ref)
     Vo, _ = oracle.solve(oracle_problem(w), V0, w.T, w.cfl)
     assert float(np.abs(V - Vo).max()) <= 1e-4 * float(np.abs(V0).max())
+
+
+def test_many_slots_set_in_one_call(hj):
+    """hj_batch_set_initial_values_device and hj_batch_set_horizons: the V0
+    and horizons of several slots in one call each (one synchronisation) give
+    the same solve, bit for bit, as one call per slot; a NaN in one slot's V0 is reported with that slot, which is left
+    without a value while the others are set."""
+    import torch
+    ws = [scenes.custom_workload(n, n_circles=3, T=0.25, seed=70 + i) for i, n in enumerate(MIXED[:4])]
+    v0s = [torch.from_numpy(scenes.initial_value(w.grid, w.scene)).cuda().reshape(-1) for w in ws]
+    out = []
+    for together in (False, True):
+        with hj.Batch(len(ws)) as b:
+            slots = [b.add_workload(w) for w in ws]
+            if together:
+                b.set_initial_values(slots, v0s)
+                b.set_horizons(slots, [w.T for w in ws], [w.cfl for w in ws])
+            else:
+                for s, v, w in zip(slots, v0s, ws):
+                    b.set_initial_value(s, v)
+                    b.set_horizon(s, w.T, w.cfl)
+            b.advance()
+            out.append([b.read_value(s) for s in slots])
+    for a, c in zip(*out):
+        assert np.array_equal(a, c)
+    bad = v0s[2].clone()
+    bad[17] = float("nan")
+    with hj.Batch(len(ws)) as b:
+        slots = [b.add_workload(w) for w in ws]
+        with pytest.raises(hj.HjError) as e:
+            b.set_initial_values(slots, [v0s[0], v0s[1], bad, v0s[3]])
+        assert e.value.status == hj.HJ_ERR_INVALID_ARG and f"slot {slots[2]}" in str(e.value)
+        with pytest.raises(hj.HjError) as e:  # that slot has no value
+            b.set_horizon(slots[2], 0.1)
+        assert e.value.status == hj.HJ_ERR_STATE
+        b.set_horizon(slots[0], ws[0].T, ws[0].cfl)  # the others have theirs
+        with pytest.raises(hj.HjError) as e:  # a count that does not match the slot's grid
+            b.set_initial_values(slots[:1], [v0s[1]])
+        assert e.value.status == hj.HJ_ERR_INVALID_ARG
