@@ -115,15 +115,15 @@ __global__ void batch_ingest_many_kernel(const SlotSetup *__restrict__ list)
 {
     const SlotSetup d = list[blockIdx.y];
     const Tin *src = (const Tin *)d.src;
-    const long long total = d.nrows * d.p4;
+    // a slot holds fewer than 2^31 values (hj_batch_add): 32-bit indices
+    const uint32_t total = (uint32_t)(d.nrows * d.p4), p4 = (uint32_t)d.p4, n4 = (uint32_t)d.n4;
     int bad = 0;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-         i += (long long)gridDim.x * blockDim.x) {
-        const long long row = i / d.p4;
-        const int l = (int)(i - row * d.p4);
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+        const uint32_t row = i / p4;
+        const uint32_t l = i - row * p4;
         float v = 0.f;
-        if (l < d.n4) {
-            const double x = (double)src[row * d.n4 + l];
+        if (l < n4) {
+            const double x = (double)src[(size_t)row * n4 + l];
             if (!isfinite(x)) bad = 1;
             v = (float)x;
         }
