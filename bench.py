@@ -505,8 +505,11 @@ def run_ours(args):
         else:
             g.set_dynamics(hj.HJ_DYN_CAR4D, (w.a_max, w.w_max))
         tuned = None
-        if prec != hj.HJ_FP64 and args.tile:
-            g.set_tile_shape([int(v) for v in args.tile.split(",")])
+        tile_arg = {"f32_bcast": args.bcast_tile, "q527": args.q527_tile}.get(prec_name) or args.tile
+        if prec != hj.HJ_FP64 and tile_arg:
+            if xy:  # the tile's room depends on whether V0 comes as a box
+                hj.hj_set_initial_value_xy_device(g.handle, V0xy_dev)
+            g.set_tile_shape([int(v) for v in tile_arg.split(",")])
             tuned = {"shape": list(g.info().tile), "ctas": g.info().tile_ctas, "tried": []}
         elif prec != hj.HJ_FP64 and not args.no_autotune:
             # pick the tile shape by timing candidates (outside the timed region)
@@ -852,6 +855,8 @@ def main():
                     help="skip the oracle's full solve of the workload (about 75 s on 16 cores)")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--tile", default="", help="fixed tile shape ty,tv,xc,stages instead of autotuning")
+    ap.add_argument("--bcast-tile", default="", help="fixed tile shape of the broadcast-V0 variant (default: --tile)")
+    ap.add_argument("--q527-tile", default="", help="fixed tile shape of the Q5.27 variant (default: --tile)")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--batch-shape", default="", help="fixed batch kernel shape nconsumer,chunks instead of autotuning")
     ap.add_argument("--no-serving", action="store_true")
