@@ -754,8 +754,9 @@ hj_status rebuild(hj_batch *b)
     }
     // Item order: slots with the longest columns first.  In the automatic
     // mode with whole columns, the slots whose items come last in the queue
-    // (about the last two items per SM) are cut into two x chunks, so that
-    // the CTAs of a batch step run out of work at nearly the same time.
+    // are cut into x chunks (about the last item per CTA into four, the one
+    // before into two), so that the CTAs of a batch step run out of work at
+    // nearly the same time.
     std::vector<int> order;
     for (int i = 0; i < b->max_slots; ++i)
         if (b->slots[i].used) order.push_back(i);
@@ -763,12 +764,14 @@ hj_status rebuild(hj_batch *b)
                      [&](int a, int c) { return b->slots[a].n[0] > b->slots[c].n[0]; });
     std::vector<int> slot_chunks(b->max_slots, nchunk);
     if (b->xc_mode == 0 && nchunk == 1) {
+        const long long ctas = (long long)b->sms * (nc <= B_DUAL ? 2 : 1);  // resident CTAs of the shape
         long long tail = 0;
-        for (int k = (int)order.size() - 1; k >= 0 && tail < 2LL * b->sms; --k) {
+        for (int k = (int)order.size() - 1; k >= 0 && tail < 2 * ctas; --k) {
             const SlotHost &s = b->slots[order[k]];
             if (s.n[0] < 8) break;
-            slot_chunks[order[k]] = 2;
-            tail += 2LL * ((s.n[1] + s.ty - 1) / s.ty) * ((s.n[2] + s.tv - 1) / s.tv);
+            const int ch = tail < ctas ? 4 : 2;
+            slot_chunks[order[k]] = ch;
+            tail += (long long)ch * ((s.n[1] + s.ty - 1) / s.ty) * ((s.n[2] + s.tv - 1) / s.tv);
         }
     }
     for (int oi = 0; oi < (int)order.size(); ++oi) {
