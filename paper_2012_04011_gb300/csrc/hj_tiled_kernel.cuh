@@ -282,6 +282,7 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
         // per step on 128x128x64x96).
         constexpr bool LEAN = BCAST || FIXED;
         constexpr bool YONE = LEAN && USIGN && !FIXED;
+        constexpr bool XLOAD = YONE;
         // (the sides are those of cos and sin: the host takes the USIGN form
         // only when every speed is >= 0; the general form flips the sides of
         // a negative-speed row, see below)
@@ -395,10 +396,15 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
                 ok = false;
                 break;
             }
-            float4 cur = *(const float4 *)(stages + (size_t)s_x * sfl + rsm);
             int s_prev = it.x0 > it.pl0 ? s_first : -1;  // slot of plane x-1, -1 at x = 0
-            // centre of plane x-1, carried in registers from the previous plane
-            float4 prevr = s_prev >= 0 ? *(const float4 *)(stages + (size_t)s_first * sfl + rsm) : cur;
+            // XLOAD (the broadcast-V0 single-sided form): the centre and the one
+            // upwind x neighbour are loaded from their stages every plane;
+            // otherwise the centres of planes x-1 and x are carried in registers
+            float4 cur = make_float4(0.f, 0.f, 0.f, 0.f), prevr = cur;
+            if (!XLOAD) {
+                cur = *(const float4 *)(stages + (size_t)s_x * sfl + rsm);
+                prevr = s_prev >= 0 ? *(const float4 *)(stages + (size_t)s_first * sfl + rsm) : cur;
+            }
 
             for (int x = it.x0; x < it.x1; ++x) {
                 if (!LEAN && __any_sync(0xffffffffu, *abort_flag != 0)) {
@@ -413,18 +419,31 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
                 }
                 // centre of plane x+1, or the extrapolated ghost past the end
                 int s_n = -1;
-                float4 prev, nxt;
+                float4 prev = make_float4(0.f, 0.f, 0.f, 0.f), nxt = prev;
                 if (x + 1 <= N1 - 1) {
                     HJ_WAIT_NEXT(s_n);
                     if (s_n < 0) {
                         ok = false;
                         break;
                     }
-                    nxt = *(const float4 *)(stages + (size_t)s_n * sfl + rsm);
-                    prev = s_prev >= 0 ? prevr : (FIXED ? cur : f4ghost(cur, nxt));
-                } else {
+                    if (!XLOAD) {
+                        nxt = *(const float4 *)(stages + (size_t)s_n * sfl + rsm);
+                        prev = s_prev >= 0 ? prevr : (FIXED ? cur : f4ghost(cur, nxt));
+                    }
+                } else if (!XLOAD) {
                     prev = s_prev >= 0 ? prevr : cur;
                     nxt = FIXED ? cur : f4ghost(cur, prev);
+                }
+                float4 xl = make_float4(0.f, 0.f, 0.f, 0.f);  // XLOAD: the upwind x neighbour
+                if (XLOAD && rok) {
+                    cur = *(const float4 *)(sx + rsm);
+                    const int s_u = xplus ? s_n : s_prev;
+                    if (s_u >= 0) {
+                        xl = *(const float4 *)(stages + (size_t)s_u * sfl + rsm);
+                    } else {  // past an end: the extrapolated point from the other side
+                        const int s_o = xplus ? s_prev : s_n;
+                        xl = f4ghost(cur, s_o >= 0 ? *(const float4 *)(stages + (size_t)s_o * sfl + rsm) : cur);
+                    }
                 }
                 if (rok) {
                     const float *row = sx + rsm;
@@ -454,7 +473,8 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
                     if (PADDED) t0 = row0[0];
                     const float4 v0c = BCAST ? make_float4(v0s, v0s, v0s, v0s) : *(const float4 *)(sx + r0sm);
                     float4 xu = nxt;  // upwind x / y neighbours (USIGN)
-                    if (USIGN && !xplus) xu = prev;
+                    if (XLOAD) xu = xl;
+                    else if (USIGN && !xplus) xu = prev;
                     if (USIGN && !YONE) yu = yplus ? yp : ym;
                     float4 out;
                     if constexpr (FIXED) {
@@ -556,8 +576,10 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
                 if (s_prev >= 0) HJ_RELEASE_OLDEST();  // plane x-1
                 s_prev = s_x;
                 s_x = s_n;
-                prevr = cur;
-                cur = nxt;
+                if (!XLOAD) {
+                    prevr = cur;
+                    cur = nxt;
+                }
             }
             if (!ok) break;
             // still held: plane x1-1 and, if loaded, the halo plane x1
