@@ -63,3 +63,22 @@ def test_selftest_limits(hj):
             with pytest.raises(hj.HjError) as e:
                 fn(bad)
             assert e.value.status == hj.HJ_ERR_INVALID_ARG
+
+
+def test_fp64_probe_counts_and_runs(hj):
+    """The FP64 rate probe the FP64 rooflines are held against: it issues the
+    FMAs it reports (8 chains x iters per thread, 8 CTAs of 256 threads per
+    SM) and finishes in the time that count allows at a plausible rate."""
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    iters = 512
+    stream = torch.cuda.current_stream()
+    hj.hj_fp64_fma_probe(iters, 8, stream.cuda_stream)  # warm-up
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    n = hj.hj_fp64_fma_probe(iters, 8, stream.cuda_stream)
+    e1.record(stream)
+    e1.synchronize()
+    assert n == sms * 8 * 256 * 8 * iters
+    tflops = 2.0 * n / (e0.elapsed_time(e1) * 1e-3) / 1e12
+    assert 0.05 < tflops < 10.0, tflops
