@@ -6,11 +6,26 @@ using namespace hj_tiled;
 
 namespace {
 
-KernelFn kernel_fn(bool fixed, bool padded, bool usign, bool bcast, bool track, int nconsumer)
+KernelFn kernel_fn(bool fixed, bool padded, bool usign, bool bcast, bool track, int nconsumer, int rpt)
 {
     // the fixed-point variant selects the upwind side per lane (no USIGN form)
     if (fixed) return select_q527(padded, bcast, track, nconsumer);
-    return track ? select_f32_track(padded, usign, bcast, nconsumer) : select_f32(padded, usign, bcast, nconsumer);
+    return track ? select_f32_track(padded, usign, bcast, nconsumer, rpt)
+                 : select_f32(padded, usign, bcast, nconsumer, rpt);
+}
+
+// v rows per consumer thread: two in the broadcast-V0 single-sided FP32 form
+// (issue-bound: the per-plane ring and address work is shared by two rows)
+// when the tile has an even number of v rows, else one.  g->tiled_usign must
+// be current (hj_tiled_setup sets it before it sizes a tile).
+int tiled_rpt(const hj_grid *g, int tv)
+{
+    return g->prec == HJ_FP32 && g->v0_bcast && g->tiled_usign && g->p4 == g->n[3] && tv % 2 == 0 ? 2 : 1;
+}
+
+int consumers_of(const hj_grid *g, int ty, int tv)
+{
+    return ((g->p4 / 4) * ty * (tv / tiled_rpt(g, tv)) + 31) / 32 * 32;
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
@@ -41,7 +56,8 @@ TiledParams make_params(const hj_grid *g, int ty, int tv, int stages, int xc)
     P.tv = tv;
     P.stages = stages;
     P.q4 = g->p4 / 4;
-    P.nconsumer = ((P.q4 * ty * tv + 31) / 32) * 32;
+    P.rpt = tiled_rpt(g, tv);
+    P.nconsumer = consumers_of(g, ty, tv);
     P.ncol_v = (g->n[2] + tv - 1) / tv;
     P.ncol = ((g->n[1] + ty - 1) / ty) * P.ncol_v;
     P.halo_box = g->p4 * (tv + 2) * (ty + 2);
@@ -126,7 +142,7 @@ bool sign_uniform(const hj_grid *g, float *tab_sign)
 
 int hj_tiled_threads(const hj_grid *g, int ty, int tv)
 {
-    const int nc = ((g->p4 / 4) * ty * tv + 31) / 32 * 32;
+    const int nc = consumers_of(g, ty, tv);
     return nc <= max_consumers(g->prec == HJ_Q527) ? nc + 32 : 0;
 }
 
@@ -163,17 +179,18 @@ bool hj_tiled_setup(hj_grid *g, char *why, size_t why_len)
     cudaError_t e = cudaMemcpy(g->tab_tiled + g->n[2] + 2 * g->p4, sgn, sizeof(float) * g->p4, cudaMemcpyHostToDevice);
     free(sgn);
     if (e != cudaSuccess) return fail("sign table upload failed");
+    g->tiled_usign = usign;  // a property of the grid's v and theta ranges (read by tiled_rpt)
 
-    // tile shape: one consumer thread per (row, theta quad), at most the
-    // largest launch-bound class (+ the producer warp).  By default the rows
+    // tile shape: one consumer thread per (row, theta quad) (per pair of v
+    // rows in the two-row form), at most the largest launch-bound class (+
+    // the producer warp).  By default the rows
     // of (y, v) with the fewest halo reads per row among the shapes whose block
     // fits the largest class that runs without spills (640 consumer threads;
     // 480 in fixed point), discounted by the share of the SMs the
     // shape can keep busy (a small grid needs small tiles to fill the GPU),
     // and as many stages as fit; hj_autotune measures the candidates instead.
     const int q4 = g->p4 / 4;
-    const int max_rows = max_consumers(fixed) / q4;
-    if (max_rows < 1) return fail("theta rows too long for one CTA");
+    if (max_consumers(fixed) / q4 < 1) return fail("theta rows too long for one CTA");
     int ty = g->tile_req[0], tv = g->tile_req[1];
     if (ty <= 0 || tv <= 0) {
         const int cap = fixed ? VARIANTS_Q527[1] : VARIANTS_F32[2];
@@ -182,7 +199,7 @@ bool hj_tiled_setup(hj_grid *g, char *why, size_t why_len)
         for (int a = 1; a <= 16 && a <= g->n[1]; ++a)
             for (int b = 1; b <= 16 && b <= g->n[2]; ++b) {
                 if ((ty > 0 && a != ty) || (tv > 0 && b != tv)) continue;
-                const int cons = (a * b * q4 + 31) / 32 * 32;
+                const int cons = consumers_of(g, a, b);
                 if (cons > cap && !(a == 1 && b == 1)) continue;
                 // work items this shape can offer (columns x chunks of >= 4 planes)
                 const double items = (double)((g->n[1] + a - 1) / a) * ((g->n[2] + b - 1) / b) *
@@ -200,8 +217,8 @@ bool hj_tiled_setup(hj_grid *g, char *why, size_t why_len)
     }
     if (tv > g->n[2]) tv = g->n[2];
     if (ty > g->n[1]) ty = g->n[1];
-    while (ty * tv > max_rows && ty > 1) --ty;
-    while (ty * tv > max_rows && tv > 1) --tv;
+    while (consumers_of(g, ty, tv) > max_consumers(fixed) && ty > 1) --ty;
+    while (consumers_of(g, ty, tv) > max_consumers(fixed) && tv > 1) --tv;
     int stages = g->tile_req[3];
     if (stages <= 0) {  // as many as fit in shared memory, up to MAX_STAGES
         TiledParams P1 = make_params(g, ty, tv, 1, 0);
@@ -213,8 +230,9 @@ bool hj_tiled_setup(hj_grid *g, char *why, size_t why_len)
     if (P.nconsumer > max_consumers(fixed)) return fail("tile needs too many threads");
     size_t smem = tiled_smem_bytes(P);
     if ((int)smem > maxsmem) return fail("tile does not fit in shared memory");
-    const void *fn = (const void *)kernel_fn(fixed, g->p4 != g->n[3], usign, g->v0_bcast, false, P.nconsumer);
-    const void *fn_track = (const void *)kernel_fn(fixed, g->p4 != g->n[3], usign, g->v0_bcast, true, P.nconsumer);
+    const void *fn = (const void *)kernel_fn(fixed, g->p4 != g->n[3], usign, g->v0_bcast, false, P.nconsumer, P.rpt);
+    const void *fn_track =
+        (const void *)kernel_fn(fixed, g->p4 != g->n[3], usign, g->v0_bcast, true, P.nconsumer, P.rpt);
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
         cudaFuncSetAttribute(fn_track, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return fail("cannot raise the shared-memory limit");
@@ -258,7 +276,8 @@ bool hj_tiled_setup(hj_grid *g, char *why, size_t why_len)
 cudaError_t hj_launch_step_tiled(hj_grid *g)
 {
     const TiledParams P = make_params(g, g->tile_ty, g->tile_tv, g->tile_stages, g->tile_xc);
-    KernelFn fn = kernel_fn(g->prec == HJ_Q527, g->p4 != g->n[3], g->tiled_usign, g->v0_bcast, g->track, P.nconsumer);
+    KernelFn fn =
+        kernel_fn(g->prec == HJ_Q527, g->p4 != g->n[3], g->tiled_usign, g->v0_bcast, g->track, P.nconsumer, P.rpt);
     fn<<<g->tiled_ctas, P.nconsumer + 32, tiled_smem_bytes(P), g->stream>>>(
         g->tmap[0], g->tmap[1], g->tmap[2], g->tmap[3], (float *)g->buf, g->coef, g->tab_tiled, g->qw,
         (const float *)g->v0xy, g->k4tab, g->amax_q, g->dstate, g->geom, P, g->nint);

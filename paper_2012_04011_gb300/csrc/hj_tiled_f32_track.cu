@@ -4,8 +4,9 @@
 
 namespace hj_tiled {
 
-KernelFn select_f32_track(bool padded, bool usign, bool bcast, int nc)
+KernelFn select_f32_track(bool padded, bool usign, bool bcast, int nc, int rpt)
 {
+    if (rpt == 2 && !padded && usign && bcast) return by_bound<false, false, true, true, true, 2>(nc);
     if (padded) {
         if (usign) return bcast ? by_bound<false, true, true, true, true>(nc) : by_bound<false, true, true, false, true>(nc);
         return bcast ? by_bound<false, true, false, true, true>(nc) : by_bound<false, true, false, false, true>(nc);

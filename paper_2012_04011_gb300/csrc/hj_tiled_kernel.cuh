@@ -14,7 +14,8 @@
 //     Out-of-range halo rows come back zero-filled and are replaced by
 //     extrapolated ghosts.
 //   * Each consumer thread owns one (y, v) row of the tile and one theta quad
-//     (float4) for the whole kernel.  It holds planes x-1, x, x+1 in the ring
+//     (float4) for the whole kernel (two adjacent v rows in the RPT = 2 form
+//     of the broadcast-V0 variant, see below).  It holds planes x-1, x, x+1 in the ring
 //     (x-1 and x+1 give the x neighbours), reads y/v/theta neighbours and V0
 //     from the stage of plane x, and writes V_{n+1} with one float4 store.
 //     Every V and V0 value is read from HBM once per step; halos are served
@@ -35,7 +36,13 @@
 // Broadcast V0 (BCAST): when V0 depends on (x, y) only (Eq. init_V), the
 // grid keeps its N1 x N2 field and the kernel reads V0 from it (one scalar
 // per row and plane, an L1/L2 hit) instead of a V0 box per plane: 8
-// algorithmic bytes per cell-update instead of 12.
+// algorithmic bytes per cell-update instead of 12.  That variant is issue-
+// bound rather than HBM-bound, so in its single-sided form a thread may own
+// two adjacent v rows of one theta quad (RPT = 2): the ring waits, releases,
+// cursors, stage addresses and the V0 load of a plane are shared by the two
+// rows, and the rows' v neighbours overlap (four row loads for two rows'
+// centres and v neighbours instead of six).  Each cell's arithmetic is the
+// one-row form's, in the same order.
 // Every mbarrier wait is bounded by %globaltimer; on timeout the kernel
 // records HJ_ERR_TIMEOUT in the device state, stops issuing work, waits
 // (bounded) for its own copies in flight and returns.
@@ -77,6 +84,7 @@ struct TiledParams {
     int ty, tv;          // tile rows along y and v
     int xc;              // planes per work item
     int q4;              // float4 per theta row (p4 / 4)
+    int rpt;             // v rows per consumer thread (1, or 2 in the broadcast-V0 single-sided form)
     int nconsumer;       // consumer threads (multiple of 32)
     int stages;          // shared-memory ring depth
     int ncol_v, ncol;    // tiles along v; columns in total
@@ -113,7 +121,8 @@ __device__ __forceinline__ int32_t f4geti(const float4 &v, int e) { return __flo
 // across every theta quad, so each thread picks its x and y upwind sides once.
 // BCAST: V0 comes from the N1 x N2 field v0xy.
 // TRACK: convergence mode, the step also reduces max |V_{n+1} - V_n|.
-template <bool FIXED, bool PADDED, bool USIGN, bool BCAST, bool TRACK, int MAXC>
+// RPT: v rows per consumer thread (2 only with BCAST, USIGN, FP32, unpadded).
+template <bool FIXED, bool PADDED, bool USIGN, bool BCAST, bool TRACK, int MAXC, int RPT = 1>
 __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
     const __grid_constant__ CUtensorMap map_v0, const __grid_constant__ CUtensorMap map_a,
     const __grid_constant__ CUtensorMap map_b, const __grid_constant__ CUtensorMap map_v0_tile,
@@ -121,6 +130,7 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
     int32_t *__restrict__ qw, const float *__restrict__ v0xy, const void *__restrict__ k4tab,
     const double2 *__restrict__ amaxq, HjDevState *st, const HjGeom g, const TiledParams P, long long nint)
 {
+    static_assert(RPT == 1 || (RPT == 2 && BCAST && USIGN && !FIXED && !PADDED), "two rows per thread: broadcast V0, single-sided FP32");
     const HjCoef<double> *coefd = (const HjCoef<double> *)coefv;  // Q5.27 grids: the table the weights come from
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     if (st->done) return;  // uniform across the grid
@@ -212,14 +222,16 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
     } else {
         // ------------------------------------------------------------ consumers
         // Thread t owns theta quad q = t % q4 of tile row r = t / q4 (row r is
-        // (y0 + r / tv, v0 + r % tv)) for the whole kernel.
+        // (y0 + r / tv, v0 + r % tv)) for the whole kernel; with RPT = 2, of
+        // the rows (y0 + r / (tv / 2), v0 + 2 (r % (tv / 2)) + {0, 1}).
         const int lane = tid & 31;
         const int q = tid % P.q4;
         const int r = tid / P.q4;
         const int N1 = g.n1, N2 = g.n2, N3 = g.n3, N4 = g.n4, P4 = g.p4;
         const int srow = P.tv + 2;  // smem rows per y row
-        const int jy = r / P.tv, kv = r - (r / P.tv) * P.tv;
-        const bool inrow = r < P.ty * P.tv;
+        const int tvr = RPT == 1 ? P.tv : P.tv / RPT;  // threads along v (the host makes tv a multiple of RPT)
+        const int jy = r / tvr, kv = (r - jy * tvr) * RPT;
+        const bool inrow = r < P.ty * tvr;
         {
             // alpha^max partials: the FP64 |xdot_1|, |xdot_2| maxima over this
             // thread's theta quad in the row it owns in each of its items (the
@@ -230,12 +242,14 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
             for (int item = blockIdx.x; item < P.nitems; item += gridDim.x) {
                 const int col = item % P.ncol;
                 const int y = (col / P.ncol_v) * P.ty + jy, v = (col % P.ncol_v) * P.tv + kv;
-                if (inrow && y < g.n2 && v < g.n3) {
-                    const double2 am = amaxq[v * P.q4 + q];
-                    const unsigned long long b1 = hj_abits(am.x), b2 = hj_abits(am.y);
-                    ab1 = ab1 > b1 ? ab1 : b1;
-                    ab2 = ab2 > b2 ? ab2 : b2;
-                }
+#pragma unroll
+                for (int rr = 0; rr < RPT; ++rr)
+                    if (inrow && y < g.n2 && v + rr < g.n3) {
+                        const double2 am = amaxq[(v + rr) * P.q4 + q];
+                        const unsigned long long b1 = hj_abits(am.x), b2 = hj_abits(am.y);
+                        ab1 = ab1 > b1 ? ab1 : b1;
+                        ab2 = ab2 > b2 ? ab2 : b2;
+                    }
             }
             ab1 = hj_warp_max_u64(ab1);
             ab2 = hj_warp_max_u64(ab2);
@@ -358,6 +372,10 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
                 if (FIXED) qw4 = qw[2 * qtot + HJ_QW_TAIL + v];
                 else k4m = ((const float2 *)k4tab)[v];
             }
+            // RPT = 2: the second row (v + 1) of the pair, if it is in the grid
+            const bool rok1 = RPT == 2 && rok && v + 1 < N3;
+            const float vk1 = rok1 ? tab[v + 1] : 0.f;
+            const float2 k4m1 = rok1 ? ((const float2 *)k4tab)[v + 1] : make_float2(0.f, 0.f);
             int4 qw1 = make_int4(0, 0, 0, 0), qw2 = make_int4(0, 0, 0, 0);  // signed x / y weights of the quad
             if (FIXED && rok) {
                 qw1 = *(const int4 *)(qw + v * P4 + 4 * q);
@@ -385,6 +403,7 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
             // ghosts this row needs: 1 y-1, 2 y+1, 4 v-1, 8 v+1
             const uint32_t gmask = (y == 0 ? 1u : 0u) | (y == N2 - 1 ? 2u : 0u) | (v == 0 ? 4u : 0u) |
                                    (v == N3 - 1 ? 8u : 0u);
+            const uint32_t gmask1 = (gmask & 3u) | (v + 1 == N3 - 1 ? 8u : 0u);  // the second row's (RPT = 2)
 
             // Planes held while plane x is updated: x-1 (if loaded), x and
             // x+1; plane x-1 is released after the update.
@@ -434,141 +453,208 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
                     prev = s_prev >= 0 ? prevr : cur;
                     nxt = FIXED ? cur : f4ghost(cur, prev);
                 }
-                float4 xl = make_float4(0.f, 0.f, 0.f, 0.f);  // XLOAD: the upwind x neighbour
-                if (XLOAD && rok) {
-                    cur = *(const float4 *)(sx + rsm);
-                    const int s_u = xplus ? s_n : s_prev;
-                    if (s_u >= 0) {
-                        xl = *(const float4 *)(stages + (size_t)s_u * sfl + rsm);
-                    } else {  // past an end: the extrapolated point from the other side
-                        const int s_o = xplus ? s_prev : s_n;
-                        xl = f4ghost(cur, s_o >= 0 ? *(const float4 *)(stages + (size_t)s_o * sfl + rsm) : cur);
-                    }
-                }
-                if (rok) {
-                    const float *row = sx + rsm;
-                    float4 ym = make_float4(0.f, 0.f, 0.f, 0.f), yp = ym, yu = ym;
-                    if (YONE) {
-                        yu = *(const float4 *)(row + yoff);
-                    } else {
-                        ym = *(const float4 *)(row - srow * P4);
-                        yp = *(const float4 *)(row + srow * P4);
-                    }
-                    float4 vm = *(const float4 *)(row - P4);
-                    float4 vp = *(const float4 *)(row + P4);
-                    if (!FIXED && edge && gmask) {
-                        // extrapolated points past the y / v ends (Sec. II-B)
-                        if (YONE) {
-                            if (gmask & yghost) yu = f4ghost(cur, *(const float4 *)(row - yoff));
-                        } else {
-                            if (gmask & 1u) ym = f4ghost(cur, yp);
-                            if (gmask & 2u) yp = f4ghost(cur, ym);
+                if constexpr (RPT == 2) {
+                    // two adjacent v rows of one theta quad: the centres c0, c1
+                    // are each other's v neighbours; per cell the arithmetic
+                    // and its order are those of the one-row form below
+                    if (rok) {
+                        const float *row = sx + rsm;
+                        const float4 c0 = *(const float4 *)row, c1 = *(const float4 *)(row + P4);
+                        float4 xl0, xl1;  // the upwind x neighbours
+                        const int s_u = xplus ? s_n : s_prev;
+                        if (s_u >= 0) {
+                            const float *ru = stages + (size_t)s_u * sfl + rsm;
+                            xl0 = *(const float4 *)ru;
+                            xl1 = *(const float4 *)(ru + P4);
+                        } else {  // past an end: the extrapolated point from the other side
+                            const int s_o = xplus ? s_prev : s_n;
+                            const float *ro = stages + (size_t)(s_o >= 0 ? s_o : s_x) * sfl + rsm;
+                            xl0 = f4ghost(c0, *(const float4 *)ro);
+                            xl1 = f4ghost(c1, *(const float4 *)(ro + P4));
                         }
-                        if (gmask & 4u) vm = f4ghost(cur, vp);
-                        if (gmask & 8u) vp = f4ghost(cur, vm);
-                    }
-                    const float *row0 = row - 4 * q;
-                    const float tl = row0[lm], tr = row0[lp];
-                    float t0 = 0.f;
-                    if (PADDED) t0 = row0[0];
-                    const float4 v0c = BCAST ? make_float4(v0s, v0s, v0s, v0s) : *(const float4 *)(sx + r0sm);
-                    float4 xu = nxt;  // upwind x / y neighbours (USIGN)
-                    if (XLOAD) xu = xl;
-                    else if (USIGN && !xplus) xu = prev;
-                    if (USIGN && !YONE) yu = yplus ? yp : ym;
-                    float4 out;
-                    if constexpr (FIXED) {
-                        // ghost flags: x-1 (x = 0), x+1 (x = N1-1), y-1, y+1, v-1, v+1
-                        const bool gxm = s_prev < 0, gxp = x == N1 - 1;
-                        const bool gym = gmask & 1u, gyp = gmask & 2u, gvm = gmask & 4u, gvp = gmask & 8u;
-                        if (!(gxm || gxp || gmask) && wsmall) {  // interior row: int32 operands throughout
-#pragma unroll
-                            for (int e = 0; e < 4; ++e) {
-                                const int32_t vc = f4geti(cur, e);
-                                const int32_t tm = e == 0 ? __float_as_int(tl) : f4geti(cur, e - 1);
-                                int32_t tp = e == 3 ? __float_as_int(tr) : f4geti(cur, e + 1);
-                                if (PADDED && lreal < 4 && e == lreal - 1) tp = __float_as_int(t0);
-                                const int32_t u1 = xpos[e] ? f4geti(nxt, e) : f4geti(prev, e);
-                                const int32_t u2 = ypos[e] ? f4geti(yp, e) : f4geti(ym, e);
-                                const int32_t u3 = max(f4geti(vp, e), f4geti(vm, e));
-                                int32_t vn = hj_q527_update_interior32(vc, f4geti(v0c, e), u1, u2, u3, max(tp, tm),
-                                                                       aw1[e], aw2[e], qw3, qw4, nsum[e]);
-                                if (PADDED && e >= lreal) vn = 0;
-                                f4set(out, e, __int_as_float(vn));
+                        float4 yu0 = *(const float4 *)(row + yoff), yu1 = *(const float4 *)(row + P4 + yoff);
+                        float4 vm0 = *(const float4 *)(row - P4), vp0 = c1, vm1 = c0;
+                        float4 vp1 = *(const float4 *)(row + 2 * P4);
+                        if (edge && (gmask | gmask1)) {
+                            // extrapolated points past the y / v ends (Sec. II-B)
+                            if (gmask & yghost) {
+                                yu0 = f4ghost(c0, *(const float4 *)(row - yoff));
+                                yu1 = f4ghost(c1, *(const float4 *)(row + P4 - yoff));
                             }
-                        } else {
-                            // an extrapolated ghost on some axis (Sec. II-B): the ghost
-                            // 2 V_c - V_o enters as -W on V_o and +2W on V_c, so the
-                            // operands stay int32 and the sum stays exact (this form
-                            // also takes interior rows whose weights sum above 2^30)
-#pragma unroll
-                            for (int e = 0; e < 4; ++e) {
-                                const int32_t vc = f4geti(cur, e);
-                                const int32_t xm = f4geti(prev, e), xp = f4geti(nxt, e);
-                                const int32_t ym_ = f4geti(ym, e), yp_ = f4geti(yp, e);
-                                const int32_t vm_ = f4geti(vm, e), vp_ = f4geti(vp, e);
-                                const int32_t tm = e == 0 ? __float_as_int(tl) : f4geti(cur, e - 1);
-                                int32_t tp = e == 3 ? __float_as_int(tr) : f4geti(cur, e + 1);
-                                if (PADDED && lreal < 4 && e == lreal - 1) tp = __float_as_int(t0);
-                                // x, y: the upwind side, and whether it is a ghost
-                                const bool hx = xpos[e] ? gxp : gxm, hy = ypos[e] ? gyp : gym;
-                                const int32_t ux = (xpos[e] != hx) ? xp : xm, uy = (ypos[e] != hy) ? yp_ : ym_;
-                                // v: the larger of V(v+1), V(v-1), either possibly a ghost
-                                bool hv = false;
-                                int32_t uv = max(vp_, vm_);
-                                if (gvp) {
-                                    uv = vm_;
-                                    hv = vc >= vm_;
-                                } else if (gvm) {
-                                    uv = vp_;
-                                    hv = vp_ < vc;
-                                }
-                                const int32_t c0 = nsum[e] + (hx ? 2 * aw1[e] : 0) + (hy ? 2 * aw2[e] : 0) +
-                                                   (hv ? 2 * qw3 : 0);
-                                int32_t vn = hj_q527_update_interior(vc, f4geti(v0c, e), ux, uy, uv, max(tp, tm),
-                                                                     hx ? -aw1[e] : aw1[e], hy ? -aw2[e] : aw2[e],
-                                                                     hv ? -qw3 : qw3, qw4, c0);
-                                if (PADDED && e >= lreal) vn = 0;
-                                f4set(out, e, __int_as_float(vn));
-                            }
+                            if (gmask & 4u) vm0 = f4ghost(c0, vp0);
+                            if (gmask & 8u) vp0 = f4ghost(c0, vm0);
+                            if (gmask1 & 8u) vp1 = f4ghost(c1, vm1);
                         }
-                    } else {
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const float vc = f4get(cur, e);
-                        const float tm = e == 0 ? tl : f4get(cur, e - 1);
-                        float tp = e == 3 ? tr : f4get(cur, e + 1);
-                        if (PADDED && lreal < 4 && e == lreal - 1) tp = t0;  // wrap of a padded last quad
-                        float in;
-                        if (USIGN) {
-                            in = wx[e] * f4get(xu, e);
-                            in = fmaf(wy[e], f4get(yu, e), in);
-                        } else {  // upwind differences folded into weights (no selects)
-                            in = wx[e] * f4get(nxt, e);
-                            in = fmaf(wxm[e], f4get(prev, e), in);
-                            in = fmaf(wy[e], f4get(yp, e), in);
-                            in = fmaf(wym[e], f4get(ym, e), in);
-                        }
-                        in = fmaf(-cs[e], vc, in);
-                        // v and theta: the bang-bang control takes the larger neighbour
-                        float acc = fmaf(P.k3, fmaxf(f4get(vp, e), f4get(vm, e)), k4m.y * vc);
-                        acc = fmaf(k4m.x, fmaxf(tp, tm), acc);
-                        acc = fmaf(vk, in, acc);
-                        float vn = fminf(f4get(v0c, e), fmaf(dt, acc, vc));
-                        if (PADDED && e >= lreal) vn = 0.f;
-                        f4set(out, e, vn);
-                    }
-                    }
-                    ((float4 *)vout)[(uint32_t)x * s1q + rbq] = out;
-                    if constexpr (TRACK) {
+                        const float *row0 = row - 4 * q;
+                        const float tl0 = row0[lm], tr0 = row0[lp], tl1 = row0[P4 + lm], tr1 = row0[P4 + lp];
+                        float4 out0, out1;
 #pragma unroll
                         for (int e = 0; e < 4; ++e) {
-                            if constexpr (FIXED) {
-                                const long long dd = (long long)f4geti(out, e) - f4geti(cur, e);
-                                const unsigned long long ad = (unsigned long long)(dd < 0 ? -dd : dd);
-                                dmq = max(dmq, (unsigned int)min(ad, 0xffffffffull));
+                            const float a = f4get(c0, e), b = f4get(c1, e);
+                            const float tma = e == 0 ? tl0 : f4get(c0, e - 1), tpa = e == 3 ? tr0 : f4get(c0, e + 1);
+                            const float tmb = e == 0 ? tl1 : f4get(c1, e - 1), tpb = e == 3 ? tr1 : f4get(c1, e + 1);
+                            float ina = wx[e] * f4get(xl0, e), inb = wx[e] * f4get(xl1, e);
+                            ina = fmaf(wy[e], f4get(yu0, e), ina);
+                            inb = fmaf(wy[e], f4get(yu1, e), inb);
+                            ina = fmaf(-cs[e], a, ina);
+                            inb = fmaf(-cs[e], b, inb);
+                            float acca = fmaf(P.k3, fmaxf(f4get(vp0, e), f4get(vm0, e)), k4m.y * a);
+                            float accb = fmaf(P.k3, fmaxf(f4get(vp1, e), f4get(vm1, e)), k4m1.y * b);
+                            acca = fmaf(k4m.x, fmaxf(tpa, tma), acca);
+                            accb = fmaf(k4m1.x, fmaxf(tpb, tmb), accb);
+                            acca = fmaf(vk, ina, acca);
+                            accb = fmaf(vk1, inb, accb);
+                            f4set(out0, e, fminf(v0s, fmaf(dt, acca, a)));
+                            f4set(out1, e, fminf(v0s, fmaf(dt, accb, b)));
+                        }
+                        float4 *dst = (float4 *)vout + ((uint32_t)x * s1q + rbq);
+                        dst[0] = out0;
+                        if (rok1) dst[P4 / 4] = out1;
+                        if constexpr (TRACK) {
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                dmf = fmaxf(dmf, fabsf(f4get(out0, e) - f4get(c0, e)));
+                                if (rok1) dmf = fmaxf(dmf, fabsf(f4get(out1, e) - f4get(c1, e)));
+                            }
+                        }
+                    }
+                } else {
+                    float4 xl = make_float4(0.f, 0.f, 0.f, 0.f);  // XLOAD: the upwind x neighbour
+                    if (XLOAD && rok) {
+                        cur = *(const float4 *)(sx + rsm);
+                        const int s_u = xplus ? s_n : s_prev;
+                        if (s_u >= 0) {
+                            xl = *(const float4 *)(stages + (size_t)s_u * sfl + rsm);
+                        } else {  // past an end: the extrapolated point from the other side
+                            const int s_o = xplus ? s_prev : s_n;
+                            xl = f4ghost(cur, s_o >= 0 ? *(const float4 *)(stages + (size_t)s_o * sfl + rsm) : cur);
+                        }
+                    }
+                    if (rok) {
+                        const float *row = sx + rsm;
+                        float4 ym = make_float4(0.f, 0.f, 0.f, 0.f), yp = ym, yu = ym;
+                        if (YONE) {
+                            yu = *(const float4 *)(row + yoff);
+                        } else {
+                            ym = *(const float4 *)(row - srow * P4);
+                            yp = *(const float4 *)(row + srow * P4);
+                        }
+                        float4 vm = *(const float4 *)(row - P4);
+                        float4 vp = *(const float4 *)(row + P4);
+                        if (!FIXED && edge && gmask) {
+                            // extrapolated points past the y / v ends (Sec. II-B)
+                            if (YONE) {
+                                if (gmask & yghost) yu = f4ghost(cur, *(const float4 *)(row - yoff));
                             } else {
-                                dmf = fmaxf(dmf, fabsf(f4get(out, e) - f4get(cur, e)));
+                                if (gmask & 1u) ym = f4ghost(cur, yp);
+                                if (gmask & 2u) yp = f4ghost(cur, ym);
+                            }
+                            if (gmask & 4u) vm = f4ghost(cur, vp);
+                            if (gmask & 8u) vp = f4ghost(cur, vm);
+                        }
+                        const float *row0 = row - 4 * q;
+                        const float tl = row0[lm], tr = row0[lp];
+                        float t0 = 0.f;
+                        if (PADDED) t0 = row0[0];
+                        const float4 v0c = BCAST ? make_float4(v0s, v0s, v0s, v0s) : *(const float4 *)(sx + r0sm);
+                        float4 xu = nxt;  // upwind x / y neighbours (USIGN)
+                        if (XLOAD) xu = xl;
+                        else if (USIGN && !xplus) xu = prev;
+                        if (USIGN && !YONE) yu = yplus ? yp : ym;
+                        float4 out;
+                        if constexpr (FIXED) {
+                            // ghost flags: x-1 (x = 0), x+1 (x = N1-1), y-1, y+1, v-1, v+1
+                            const bool gxm = s_prev < 0, gxp = x == N1 - 1;
+                            const bool gym = gmask & 1u, gyp = gmask & 2u, gvm = gmask & 4u, gvp = gmask & 8u;
+                            if (!(gxm || gxp || gmask) && wsmall) {  // interior row: int32 operands throughout
+    #pragma unroll
+                                for (int e = 0; e < 4; ++e) {
+                                    const int32_t vc = f4geti(cur, e);
+                                    const int32_t tm = e == 0 ? __float_as_int(tl) : f4geti(cur, e - 1);
+                                    int32_t tp = e == 3 ? __float_as_int(tr) : f4geti(cur, e + 1);
+                                    if (PADDED && lreal < 4 && e == lreal - 1) tp = __float_as_int(t0);
+                                    const int32_t u1 = xpos[e] ? f4geti(nxt, e) : f4geti(prev, e);
+                                    const int32_t u2 = ypos[e] ? f4geti(yp, e) : f4geti(ym, e);
+                                    const int32_t u3 = max(f4geti(vp, e), f4geti(vm, e));
+                                    int32_t vn = hj_q527_update_interior32(vc, f4geti(v0c, e), u1, u2, u3, max(tp, tm),
+                                                                           aw1[e], aw2[e], qw3, qw4, nsum[e]);
+                                    if (PADDED && e >= lreal) vn = 0;
+                                    f4set(out, e, __int_as_float(vn));
+                                }
+                            } else {
+                                // an extrapolated ghost on some axis (Sec. II-B): the ghost
+                                // 2 V_c - V_o enters as -W on V_o and +2W on V_c, so the
+                                // operands stay int32 and the sum stays exact (this form
+                                // also takes interior rows whose weights sum above 2^30)
+    #pragma unroll
+                                for (int e = 0; e < 4; ++e) {
+                                    const int32_t vc = f4geti(cur, e);
+                                    const int32_t xm = f4geti(prev, e), xp = f4geti(nxt, e);
+                                    const int32_t ym_ = f4geti(ym, e), yp_ = f4geti(yp, e);
+                                    const int32_t vm_ = f4geti(vm, e), vp_ = f4geti(vp, e);
+                                    const int32_t tm = e == 0 ? __float_as_int(tl) : f4geti(cur, e - 1);
+                                    int32_t tp = e == 3 ? __float_as_int(tr) : f4geti(cur, e + 1);
+                                    if (PADDED && lreal < 4 && e == lreal - 1) tp = __float_as_int(t0);
+                                    // x, y: the upwind side, and whether it is a ghost
+                                    const bool hx = xpos[e] ? gxp : gxm, hy = ypos[e] ? gyp : gym;
+                                    const int32_t ux = (xpos[e] != hx) ? xp : xm, uy = (ypos[e] != hy) ? yp_ : ym_;
+                                    // v: the larger of V(v+1), V(v-1), either possibly a ghost
+                                    bool hv = false;
+                                    int32_t uv = max(vp_, vm_);
+                                    if (gvp) {
+                                        uv = vm_;
+                                        hv = vc >= vm_;
+                                    } else if (gvm) {
+                                        uv = vp_;
+                                        hv = vp_ < vc;
+                                    }
+                                    const int32_t c0 = nsum[e] + (hx ? 2 * aw1[e] : 0) + (hy ? 2 * aw2[e] : 0) +
+                                                       (hv ? 2 * qw3 : 0);
+                                    int32_t vn = hj_q527_update_interior(vc, f4geti(v0c, e), ux, uy, uv, max(tp, tm),
+                                                                         hx ? -aw1[e] : aw1[e], hy ? -aw2[e] : aw2[e],
+                                                                         hv ? -qw3 : qw3, qw4, c0);
+                                    if (PADDED && e >= lreal) vn = 0;
+                                    f4set(out, e, __int_as_float(vn));
+                                }
+                            }
+                        } else {
+    #pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const float vc = f4get(cur, e);
+                            const float tm = e == 0 ? tl : f4get(cur, e - 1);
+                            float tp = e == 3 ? tr : f4get(cur, e + 1);
+                            if (PADDED && lreal < 4 && e == lreal - 1) tp = t0;  // wrap of a padded last quad
+                            float in;
+                            if (USIGN) {
+                                in = wx[e] * f4get(xu, e);
+                                in = fmaf(wy[e], f4get(yu, e), in);
+                            } else {  // upwind differences folded into weights (no selects)
+                                in = wx[e] * f4get(nxt, e);
+                                in = fmaf(wxm[e], f4get(prev, e), in);
+                                in = fmaf(wy[e], f4get(yp, e), in);
+                                in = fmaf(wym[e], f4get(ym, e), in);
+                            }
+                            in = fmaf(-cs[e], vc, in);
+                            // v and theta: the bang-bang control takes the larger neighbour
+                            float acc = fmaf(P.k3, fmaxf(f4get(vp, e), f4get(vm, e)), k4m.y * vc);
+                            acc = fmaf(k4m.x, fmaxf(tp, tm), acc);
+                            acc = fmaf(vk, in, acc);
+                            float vn = fminf(f4get(v0c, e), fmaf(dt, acc, vc));
+                            if (PADDED && e >= lreal) vn = 0.f;
+                            f4set(out, e, vn);
+                        }
+                        }
+                        ((float4 *)vout)[(uint32_t)x * s1q + rbq] = out;
+                        if constexpr (TRACK) {
+    #pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                if constexpr (FIXED) {
+                                    const long long dd = (long long)f4geti(out, e) - f4geti(cur, e);
+                                    const unsigned long long ad = (unsigned long long)(dd < 0 ? -dd : dd);
+                                    dmq = max(dmq, (unsigned int)min(ad, 0xffffffffull));
+                                } else {
+                                    dmf = fmaxf(dmf, fabsf(f4get(out, e) - f4get(cur, e)));
+                                }
                             }
                         }
                     }
@@ -608,18 +694,20 @@ typedef void (*KernelFn)(const CUtensorMap, const CUtensorMap, const CUtensorMap
                          HjDevState *, const HjGeom, const TiledParams, long long);
 
 // Kernel of a variant, smallest launch bound class that holds nconsumer
-// consumer threads (defined in the instantiating translation units).
-KernelFn select_f32(bool padded, bool usign, bool bcast, int nconsumer);        // hj_tiled_f32.cu
-KernelFn select_f32_track(bool padded, bool usign, bool bcast, int nconsumer);  // hj_tiled_f32_track.cu
-KernelFn select_q527(bool padded, bool bcast, bool track, int nconsumer);       // hj_tiled_q527.cu
+// consumer threads (defined in the instantiating translation units); rpt is
+// the v rows per consumer thread (2 only for the broadcast-V0 single-sided
+// FP32 form, see TiledParams::rpt).
+KernelFn select_f32(bool padded, bool usign, bool bcast, int nconsumer, int rpt);        // hj_tiled_f32.cu
+KernelFn select_f32_track(bool padded, bool usign, bool bcast, int nconsumer, int rpt);  // hj_tiled_f32_track.cu
+KernelFn select_q527(bool padded, bool bcast, bool track, int nconsumer);                // hj_tiled_q527.cu
 
-template <bool FIXED, bool PADDED, bool USIGN, bool BCAST, bool TRACK>
+template <bool FIXED, bool PADDED, bool USIGN, bool BCAST, bool TRACK, int RPT = 1>
 KernelFn by_bound(int nconsumer)
 {
-    if (nconsumer <= variant<FIXED>(0)) return hj_step_tiled_kernel<FIXED, PADDED, USIGN, BCAST, TRACK, variant<FIXED>(0)>;
-    if (nconsumer <= variant<FIXED>(1)) return hj_step_tiled_kernel<FIXED, PADDED, USIGN, BCAST, TRACK, variant<FIXED>(1)>;
-    if (nconsumer <= variant<FIXED>(2)) return hj_step_tiled_kernel<FIXED, PADDED, USIGN, BCAST, TRACK, variant<FIXED>(2)>;
-    return hj_step_tiled_kernel<FIXED, PADDED, USIGN, BCAST, TRACK, variant<FIXED>(3)>;
+    if (nconsumer <= variant<FIXED>(0)) return hj_step_tiled_kernel<FIXED, PADDED, USIGN, BCAST, TRACK, variant<FIXED>(0), RPT>;
+    if (nconsumer <= variant<FIXED>(1)) return hj_step_tiled_kernel<FIXED, PADDED, USIGN, BCAST, TRACK, variant<FIXED>(1), RPT>;
+    if (nconsumer <= variant<FIXED>(2)) return hj_step_tiled_kernel<FIXED, PADDED, USIGN, BCAST, TRACK, variant<FIXED>(2), RPT>;
+    return hj_step_tiled_kernel<FIXED, PADDED, USIGN, BCAST, TRACK, variant<FIXED>(3), RPT>;
 }
 
 }  // namespace hj_tiled

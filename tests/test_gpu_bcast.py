@@ -83,6 +83,36 @@ def test_broadcast_v0_tile_shapes_and_mode_switch(hj):
         assert np.array_equal(g.read_value().astype(np.float32), ref)
 
 
+@pytest.mark.parametrize("n, shape", [((17, 13, 11, 32), [4, 2, 5, 4]), ((12, 10, 9, 16), [3, 4, 0, 0]),
+                                      ((9, 21, 5, 48), [5, 4, 0, 0]), ((10, 7, 3, 16), [2, 2, 3, 4])])
+def test_broadcast_v0_two_rows_per_thread(hj, n, shape):
+    """An even number of v rows per tile on a grid whose theta quads have one
+    sign of cos and of sin takes the two-rows-per-thread form; odd N3 leaves
+    the last pair with its second row outside the grid.  Both solve modes
+    must give the 4D-V0 path's bits (and the one-row form's, odd tv)."""
+    w = scenes.custom_workload(n, n_circles=3, n_rects=1, T=0.4, seed=sum(n) + 7)
+    ref, st_ref, _ = solve(hj, w, hj.HJ_FP32, xy=False, kernel=hj.HJ_KERNEL_TILED)
+    for shp in (shape, [shape[0], shape[1] - 1, shape[2], shape[3]]):
+        b, st, info = solve(hj, w, hj.HJ_FP32, xy=True, kernel=hj.HJ_KERNEL_TILED, shape=shp)
+        assert info.tile[1] == min(shp[1], n[2]), (shp, list(info.tile))
+        assert st.steps == st_ref.steps and st.dt_last == st_ref.dt_last
+        assert np.array_equal(b, ref), shp
+    # convergence mode (the step also reduces max |V_{n+1} - V_n|)
+    outs = []
+    for xy in (False, True):
+        with hj.Grid.for_workload(w, hj.HJ_FP32) as g:
+            g.set_kernel(hj.HJ_KERNEL_TILED)
+            if xy:
+                g.set_initial_value_xy(scenes.signed_distance_xy(w.grid, w.scene))
+                g.set_tile_shape(shape)
+            else:
+                g.set_initial_value(scenes.initial_value(w.grid, w.scene))
+            st = g.solve_converged(1e-3, 0.6, w.cfl)
+            outs.append((g.read_value(), st.steps, st.last_change))
+    assert outs[0][1] == outs[1][1] and outs[0][2] == outs[1][2]
+    assert np.array_equal(outs[0][0], outs[1][0])
+
+
 def test_broadcast_v0_device_field(hj):
     import torch
     w = scenes.workload("car4d_31x31x11x16")
