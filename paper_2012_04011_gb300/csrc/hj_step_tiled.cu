@@ -14,18 +14,23 @@ KernelFn kernel_fn(bool fixed, bool padded, bool usign, bool bcast, bool track, 
                  : select_f32(padded, usign, bcast, nconsumer, rpt);
 }
 
-// v rows per consumer thread: two in the broadcast-V0 single-sided FP32 form
-// (issue-bound: the per-plane ring and address work is shared by two rows)
-// when the tile has an even number of v rows, else one.  g->tiled_usign must
-// be current (hj_tiled_setup sets it before it sizes a tile).
-int tiled_rpt(const hj_grid *g, int tv)
+// v rows per consumer thread in the broadcast-V0 single-sided FP32 form
+// (bound by data movement: several rows a thread let a CTA hold larger tiles,
+// whose halo rows cost less L2 traffic per row, and share the per-plane
+// ring and address work): four when tv is a multiple of 4 and that still
+// leaves at least 8 consumer warps, else two when tv is even; one otherwise
+// and in every other variant.  g->tiled_usign must be current
+// (hj_tiled_setup sets it before it sizes a tile).
+int tiled_rpt(const hj_grid *g, int ty, int tv)
 {
-    return g->prec == HJ_FP32 && g->v0_bcast && g->tiled_usign && g->p4 == g->n[3] && tv % 2 == 0 ? 2 : 1;
+    if (!(g->prec == HJ_FP32 && g->v0_bcast && g->tiled_usign && g->p4 == g->n[3])) return 1;
+    if (tv % 4 == 0 && (g->p4 / 4) * ty * (tv / 4) >= 256) return 4;
+    return tv % 2 == 0 ? 2 : 1;
 }
 
 int consumers_of(const hj_grid *g, int ty, int tv)
 {
-    return ((g->p4 / 4) * ty * (tv / tiled_rpt(g, tv)) + 31) / 32 * 32;
+    return ((g->p4 / 4) * ty * (tv / tiled_rpt(g, ty, tv)) + 31) / 32 * 32;
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
@@ -56,7 +61,7 @@ TiledParams make_params(const hj_grid *g, int ty, int tv, int stages, int xc)
     P.tv = tv;
     P.stages = stages;
     P.q4 = g->p4 / 4;
-    P.rpt = tiled_rpt(g, tv);
+    P.rpt = tiled_rpt(g, ty, tv);
     P.nconsumer = consumers_of(g, ty, tv);
     P.ncol_v = (g->n[2] + tv - 1) / tv;
     P.ncol = ((g->n[1] + ty - 1) / ty) * P.ncol_v;

@@ -5,7 +5,8 @@ namespace hj_tiled {
 
 KernelFn select_f32(bool padded, bool usign, bool bcast, int nc, int rpt)
 {
-    if (rpt == 2 && !padded && usign && bcast) return by_bound<false, false, true, true, false, 2>(nc);
+    if (rpt > 1 && !padded && usign && bcast)
+        return rpt == 4 ? by_bound<false, false, true, true, false, 4>(nc) : by_bound<false, false, true, true, false, 2>(nc);
     if (padded) {
         if (usign) return bcast ? by_bound<false, true, true, true, false>(nc) : by_bound<false, true, true, false, false>(nc);
         return bcast ? by_bound<false, true, false, true, false>(nc) : by_bound<false, true, false, false, false>(nc);

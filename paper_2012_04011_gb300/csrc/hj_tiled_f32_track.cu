@@ -6,7 +6,8 @@ namespace hj_tiled {
 
 KernelFn select_f32_track(bool padded, bool usign, bool bcast, int nc, int rpt)
 {
-    if (rpt == 2 && !padded && usign && bcast) return by_bound<false, false, true, true, true, 2>(nc);
+    if (rpt > 1 && !padded && usign && bcast)
+        return rpt == 4 ? by_bound<false, false, true, true, true, 4>(nc) : by_bound<false, false, true, true, true, 2>(nc);
     if (padded) {
         if (usign) return bcast ? by_bound<false, true, true, true, true>(nc) : by_bound<false, true, true, false, true>(nc);
         return bcast ? by_bound<false, true, false, true, true>(nc) : by_bound<false, true, false, false, true>(nc);

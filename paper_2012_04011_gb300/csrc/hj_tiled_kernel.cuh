@@ -14,8 +14,8 @@
 //     Out-of-range halo rows come back zero-filled and are replaced by
 //     extrapolated ghosts.
 //   * Each consumer thread owns one (y, v) row of the tile and one theta quad
-//     (float4) for the whole kernel (two adjacent v rows in the RPT = 2 form
-//     of the broadcast-V0 variant, see below).  It holds planes x-1, x, x+1 in the ring
+//     (float4) for the whole kernel (two or four adjacent v rows in the
+//     broadcast-V0 variant, see below).  It holds planes x-1, x, x+1 in the ring
 //     (x-1 and x+1 give the x neighbours), reads y/v/theta neighbours and V0
 //     from the stage of plane x, and writes V_{n+1} with one float4 store.
 //     Every V and V0 value is read from HBM once per step; halos are served
@@ -38,11 +38,14 @@
 // per row and plane, an L1/L2 hit) instead of a V0 box per plane: 8
 // algorithmic bytes per cell-update instead of 12.  That variant is issue-
 // bound rather than HBM-bound, so in its single-sided form a thread may own
-// two adjacent v rows of one theta quad (RPT = 2): the ring waits, releases,
-// cursors, stage addresses and the V0 load of a plane are shared by the two
-// rows, and the rows' v neighbours overlap (four row loads for two rows'
-// centres and v neighbours instead of six).  Each cell's arithmetic is the
-// one-row form's, in the same order.
+// RPT = 2 or 4 adjacent v rows of one theta quad: the ring waits, releases,
+// cursors, stage addresses and the V0 load of a plane are shared by the
+// rows, and the rows' v neighbours overlap (RPT + 2 row loads for the
+// centres and v neighbours instead of 3 RPT).  With four rows a thread, a
+// CTA can hold tiles large enough (8 x 8 rows and up) that the y/v halo
+// rows, which each plane re-reads from L2, add about 1.5 instead of 1.8
+// times the tile; that L2 traffic, not the arithmetic, sets the pace of this
+// variant.  Each cell's arithmetic is the one-row form's, in the same order.
 // Every mbarrier wait is bounded by %globaltimer; on timeout the kernel
 // records HJ_ERR_TIMEOUT in the device state, stops issuing work, waits
 // (bounded) for its own copies in flight and returns.
@@ -84,7 +87,7 @@ struct TiledParams {
     int ty, tv;          // tile rows along y and v
     int xc;              // planes per work item
     int q4;              // float4 per theta row (p4 / 4)
-    int rpt;             // v rows per consumer thread (1, or 2 in the broadcast-V0 single-sided form)
+    int rpt;             // v rows per consumer thread (1; 2 or 4 in the broadcast-V0 single-sided form)
     int nconsumer;       // consumer threads (multiple of 32)
     int stages;          // shared-memory ring depth
     int ncol_v, ncol;    // tiles along v; columns in total
@@ -121,7 +124,7 @@ __device__ __forceinline__ int32_t f4geti(const float4 &v, int e) { return __flo
 // across every theta quad, so each thread picks its x and y upwind sides once.
 // BCAST: V0 comes from the N1 x N2 field v0xy.
 // TRACK: convergence mode, the step also reduces max |V_{n+1} - V_n|.
-// RPT: v rows per consumer thread (2 only with BCAST, USIGN, FP32, unpadded).
+// RPT: v rows per consumer thread (2 or 4 only with BCAST, USIGN, FP32, unpadded).
 template <bool FIXED, bool PADDED, bool USIGN, bool BCAST, bool TRACK, int MAXC, int RPT = 1>
 __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
     const __grid_constant__ CUtensorMap map_v0, const __grid_constant__ CUtensorMap map_a,
@@ -130,7 +133,8 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
     int32_t *__restrict__ qw, const float *__restrict__ v0xy, const void *__restrict__ k4tab,
     const double2 *__restrict__ amaxq, HjDevState *st, const HjGeom g, const TiledParams P, long long nint)
 {
-    static_assert(RPT == 1 || (RPT == 2 && BCAST && USIGN && !FIXED && !PADDED), "two rows per thread: broadcast V0, single-sided FP32");
+    static_assert(RPT == 1 || ((RPT == 2 || RPT == 4) && BCAST && USIGN && !FIXED && !PADDED),
+                  "several rows per thread: broadcast V0, single-sided FP32");
     const HjCoef<double> *coefd = (const HjCoef<double> *)coefv;  // Q5.27 grids: the table the weights come from
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     if (st->done) return;  // uniform across the grid
@@ -222,8 +226,8 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
     } else {
         // ------------------------------------------------------------ consumers
         // Thread t owns theta quad q = t % q4 of tile row r = t / q4 (row r is
-        // (y0 + r / tv, v0 + r % tv)) for the whole kernel; with RPT = 2, of
-        // the rows (y0 + r / (tv / 2), v0 + 2 (r % (tv / 2)) + {0, 1}).
+        // (y0 + r / tv, v0 + r % tv)) for the whole kernel; with RPT > 1, of
+        // the rows (y0 + r / (tv / RPT), v0 + RPT (r % (tv / RPT)) + k), k < RPT.
         const int lane = tid & 31;
         const int q = tid % P.q4;
         const int r = tid / P.q4;
@@ -372,10 +376,16 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
                 if (FIXED) qw4 = qw[2 * qtot + HJ_QW_TAIL + v];
                 else k4m = ((const float2 *)k4tab)[v];
             }
-            // RPT = 2: the second row (v + 1) of the pair, if it is in the grid
-            const bool rok1 = RPT == 2 && rok && v + 1 < N3;
-            const float vk1 = rok1 ? tab[v + 1] : 0.f;
-            const float2 k4m1 = rok1 ? ((const float2 *)k4tab)[v + 1] : make_float2(0.f, 0.f);
+            // RPT > 1: rows v + k; in the grid, speed, theta coefficient
+            bool rokv[RPT];
+            float vkv[RPT];
+            float2 k4v[RPT];
+#pragma unroll
+            for (int k = 0; k < RPT; ++k) {
+                rokv[k] = rok && v + k < N3;
+                vkv[k] = (RPT > 1 && rokv[k]) ? tab[v + k] : 0.f;
+                k4v[k] = (RPT > 1 && rokv[k]) ? ((const float2 *)k4tab)[v + k] : make_float2(0.f, 0.f);
+            }
             int4 qw1 = make_int4(0, 0, 0, 0), qw2 = make_int4(0, 0, 0, 0);  // signed x / y weights of the quad
             if (FIXED && rok) {
                 qw1 = *(const int4 *)(qw + v * P4 + 4 * q);
@@ -403,7 +413,9 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
             // ghosts this row needs: 1 y-1, 2 y+1, 4 v-1, 8 v+1
             const uint32_t gmask = (y == 0 ? 1u : 0u) | (y == N2 - 1 ? 2u : 0u) | (v == 0 ? 4u : 0u) |
                                    (v == N3 - 1 ? 8u : 0u);
-            const uint32_t gmask1 = (gmask & 3u) | (v + 1 == N3 - 1 ? 8u : 0u);  // the second row's (RPT = 2)
+            uint32_t gmv[RPT];  // and ghosts (RPT > 1)
+#pragma unroll
+            for (int k = 0; k < RPT; ++k) gmv[k] = (gmask & (k == 0 ? 7u : 3u)) | (v + k == N3 - 1 ? 8u : 0u);
 
             // Planes held while plane x is updated: x-1 (if loaded), x and
             // x+1; plane x-1 is released after the update.
@@ -453,69 +465,56 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
                     prev = s_prev >= 0 ? prevr : cur;
                     nxt = FIXED ? cur : f4ghost(cur, prev);
                 }
-                if constexpr (RPT == 2) {
-                    // two adjacent v rows of one theta quad: the centres c0, c1
-                    // are each other's v neighbours; per cell the arithmetic
-                    // and its order are those of the one-row form below
+                if constexpr (RPT > 1) {
+                    // RPT adjacent v rows of one theta quad, a rolling window
+                    // along v: the centres of rows k - 1 and k + 1 are row k's
+                    // v neighbours; per cell the arithmetic and its order are
+                    // those of the one-row form below
                     if (rok) {
                         const float *row = sx + rsm;
-                        const float4 c0 = *(const float4 *)row, c1 = *(const float4 *)(row + P4);
-                        float4 xl0, xl1;  // the upwind x neighbours
-                        const int s_u = xplus ? s_n : s_prev;
-                        if (s_u >= 0) {
-                            const float *ru = stages + (size_t)s_u * sfl + rsm;
-                            xl0 = *(const float4 *)ru;
-                            xl1 = *(const float4 *)(ru + P4);
-                        } else {  // past an end: the extrapolated point from the other side
-                            const int s_o = xplus ? s_prev : s_n;
-                            const float *ro = stages + (size_t)(s_o >= 0 ? s_o : s_x) * sfl + rsm;
-                            xl0 = f4ghost(c0, *(const float4 *)ro);
-                            xl1 = f4ghost(c1, *(const float4 *)(ro + P4));
-                        }
-                        float4 yu0 = *(const float4 *)(row + yoff), yu1 = *(const float4 *)(row + P4 + yoff);
-                        float4 vm0 = *(const float4 *)(row - P4), vp0 = c1, vm1 = c0;
-                        float4 vp1 = *(const float4 *)(row + 2 * P4);
-                        if (edge && (gmask | gmask1)) {
-                            // extrapolated points past the y / v ends (Sec. II-B)
-                            if (gmask & yghost) {
-                                yu0 = f4ghost(c0, *(const float4 *)(row - yoff));
-                                yu1 = f4ghost(c1, *(const float4 *)(row + P4 - yoff));
-                            }
-                            if (gmask & 4u) vm0 = f4ghost(c0, vp0);
-                            if (gmask & 8u) vp0 = f4ghost(c0, vm0);
-                            if (gmask1 & 8u) vp1 = f4ghost(c1, vm1);
-                        }
-                        const float *row0 = row - 4 * q;
-                        const float tl0 = row0[lm], tr0 = row0[lp], tl1 = row0[P4 + lm], tr1 = row0[P4 + lp];
-                        float4 out0, out1;
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            const float a = f4get(c0, e), b = f4get(c1, e);
-                            const float tma = e == 0 ? tl0 : f4get(c0, e - 1), tpa = e == 3 ? tr0 : f4get(c0, e + 1);
-                            const float tmb = e == 0 ? tl1 : f4get(c1, e - 1), tpb = e == 3 ? tr1 : f4get(c1, e + 1);
-                            float ina = wx[e] * f4get(xl0, e), inb = wx[e] * f4get(xl1, e);
-                            ina = fmaf(wy[e], f4get(yu0, e), ina);
-                            inb = fmaf(wy[e], f4get(yu1, e), inb);
-                            ina = fmaf(-cs[e], a, ina);
-                            inb = fmaf(-cs[e], b, inb);
-                            float acca = fmaf(P.k3, fmaxf(f4get(vp0, e), f4get(vm0, e)), k4m.y * a);
-                            float accb = fmaf(P.k3, fmaxf(f4get(vp1, e), f4get(vm1, e)), k4m1.y * b);
-                            acca = fmaf(k4m.x, fmaxf(tpa, tma), acca);
-                            accb = fmaf(k4m1.x, fmaxf(tpb, tmb), accb);
-                            acca = fmaf(vk, ina, acca);
-                            accb = fmaf(vk1, inb, accb);
-                            f4set(out0, e, fminf(v0s, fmaf(dt, acca, a)));
-                            f4set(out1, e, fminf(v0s, fmaf(dt, accb, b)));
-                        }
+                        // the upwind x plane, or past an end the one to
+                        // extrapolate from (the other side, or the centre)
+                        const int s_u = xplus ? s_n : s_prev, s_o = xplus ? s_prev : s_n;
+                        const float *ru = stages + (size_t)(s_u >= 0 ? s_u : (s_o >= 0 ? s_o : s_x)) * sfl + rsm;
+                        float4 cm = *(const float4 *)(row - P4), c = *(const float4 *)row;
                         float4 *dst = (float4 *)vout + ((uint32_t)x * s1q + rbq);
-                        dst[0] = out0;
-                        if (rok1) dst[P4 / 4] = out1;
-                        if constexpr (TRACK) {
+#pragma unroll
+                        for (int k = 0; k < RPT; ++k) {
+                            const float *rk = row + k * P4;
+                            const float4 cp = *(const float4 *)(rk + P4);
+                            float4 xl = *(const float4 *)(ru + k * P4);
+                            if (s_u < 0) xl = f4ghost(c, xl);
+                            float4 yu = *(const float4 *)(rk + yoff), vm = cm, vp = cp;
+                            if (edge && (gmv[k] & (yghost | 12u))) {
+                                // extrapolated points past the y / v ends (Sec. II-B)
+                                if (gmv[k] & yghost) yu = f4ghost(c, *(const float4 *)(rk - yoff));
+                                if (gmv[k] & 4u) vm = f4ghost(c, vp);
+                                if (gmv[k] & 8u) vp = f4ghost(c, vm);
+                            }
+                            const float *rk0 = rk - 4 * q;
+                            const float tl = rk0[lm], tr = rk0[lp];
+                            float4 out;
 #pragma unroll
                             for (int e = 0; e < 4; ++e) {
-                                dmf = fmaxf(dmf, fabsf(f4get(out0, e) - f4get(c0, e)));
-                                if (rok1) dmf = fmaxf(dmf, fabsf(f4get(out1, e) - f4get(c1, e)));
+                                const float vc = f4get(c, e);
+                                const float tm = e == 0 ? tl : f4get(c, e - 1), tp = e == 3 ? tr : f4get(c, e + 1);
+                                float in = wx[e] * f4get(xl, e);
+                                in = fmaf(wy[e], f4get(yu, e), in);
+                                in = fmaf(-cs[e], vc, in);
+                                float acc = fmaf(P.k3, fmaxf(f4get(vp, e), f4get(vm, e)), k4v[k].y * vc);
+                                acc = fmaf(k4v[k].x, fmaxf(tp, tm), acc);
+                                acc = fmaf(vkv[k], in, acc);
+                                f4set(out, e, fminf(v0s, fmaf(dt, acc, vc)));
                             }
+                            if (rokv[k]) {
+                                dst[k * (P4 / 4)] = out;
+                                if constexpr (TRACK) {
+#pragma unroll
+                                    for (int e = 0; e < 4; ++e) dmf = fmaxf(dmf, fabsf(f4get(out, e) - f4get(c, e)));
+                                }
+                            }
+                            cm = c;
+                            c = cp;
                         }
                     }
                 } else {
@@ -695,8 +694,8 @@ typedef void (*KernelFn)(const CUtensorMap, const CUtensorMap, const CUtensorMap
 
 // Kernel of a variant, smallest launch bound class that holds nconsumer
 // consumer threads (defined in the instantiating translation units); rpt is
-// the v rows per consumer thread (2 only for the broadcast-V0 single-sided
-// FP32 form, see TiledParams::rpt).
+// the v rows per consumer thread (2 or 4 only for the broadcast-V0
+// single-sided FP32 form, see TiledParams::rpt).
 KernelFn select_f32(bool padded, bool usign, bool bcast, int nconsumer, int rpt);        // hj_tiled_f32.cu
 KernelFn select_f32_track(bool padded, bool usign, bool bcast, int nconsumer, int rpt);  // hj_tiled_f32_track.cu
 KernelFn select_q527(bool padded, bool bcast, bool track, int nconsumer);                // hj_tiled_q527.cu

@@ -84,12 +84,16 @@ def test_broadcast_v0_tile_shapes_and_mode_switch(hj):
 
 
 @pytest.mark.parametrize("n, shape", [((17, 13, 11, 32), [4, 2, 5, 4]), ((12, 10, 9, 16), [3, 4, 0, 0]),
-                                      ((9, 21, 5, 48), [5, 4, 0, 0]), ((10, 7, 3, 16), [2, 2, 3, 4])])
-def test_broadcast_v0_two_rows_per_thread(hj, n, shape):
+                                      ((9, 21, 5, 48), [5, 4, 0, 0]), ((10, 7, 3, 16), [2, 2, 3, 4]),
+                                      ((26, 25, 11, 48), [12, 8, 0, 0]), ((10, 17, 19, 16), [16, 16, 4, 4])])
+def test_broadcast_v0_several_rows_per_thread(hj, n, shape):
     """An even number of v rows per tile on a grid whose theta quads have one
-    sign of cos and of sin takes the two-rows-per-thread form; odd N3 leaves
-    the last pair with its second row outside the grid.  Both solve modes
-    must give the 4D-V0 path's bits (and the one-row form's, odd tv)."""
+    sign of cos and of sin takes the form in which a thread updates two
+    adjacent v rows, or four when tv is a multiple of 4 and that leaves at
+    least 8 consumer warps (the last two cases); N3 not a multiple of the
+    rows a thread leaves the last rows of a thread outside the grid.  Both
+    solve modes must give the 4D-V0 path's bits (and those of the one-row
+    or two-row form, tv - 1)."""
     w = scenes.custom_workload(n, n_circles=3, n_rects=1, T=0.4, seed=sum(n) + 7)
     ref, st_ref, _ = solve(hj, w, hj.HJ_FP32, xy=False, kernel=hj.HJ_KERNEL_TILED)
     for shp in (shape, [shape[0], shape[1] - 1, shape[2], shape[3]]):
