@@ -351,7 +351,7 @@ typedef struct {
     double device_ms;   /* device time of the call (CUDA events) */
     int32_t nconsumer;  /* consumer threads per CTA of the batch kernel */
     int32_t ctas;       /* CTAs per batch step */
-    int32_t items;      /* work items per batch step (all slots) */
+    int32_t items;      /* work items per batch step in the last item layout (the running slots) */
 } hj_batch_stats;
 
 typedef struct {

@@ -601,6 +601,9 @@ struct hj_batch {
     BatchSlot *h_slots = nullptr;  // pinned mirror
     BatchItem *d_items = nullptr;
     int items_cap = 0;
+    std::vector<BatchInst> h_insts;  // host copy of d_insts (the item layout rewrites xc and nitems)
+    std::vector<char> lay_active;    // slots the current item layout covers
+    int lay_nitems = 0;              // source of the stream-ordered copy into d_ctl->nitems
     BatchCtl *d_ctl = nullptr;
     CUtensorMap *d_maps = nullptr;
     int nconsumer_req = 0;  // 0: automatic
@@ -709,6 +712,67 @@ hj_status upload_slot_tables(hj_batch *b, SlotHost &s)
     return HJ_OK;
 }
 
+// Item layout of the slots marked in `active` for `ctas` resident CTAs (the
+// tiles chosen by rebuild): x chunks per slot, h_insts' xc and nitems
+// (0 for the others), and the queue in order.  Whole columns while the
+// active slots have at least one (y, v) column per CTA, else enough chunks
+// (of at least 4 planes) to give every CTA an item, since a column's planes
+// are streamed one after another by one CTA.  Slots with the longest columns
+// come first; with whole columns, the slots whose items come last are cut
+// into x chunks (about the last item per CTA into four, the one before into
+// two), so that the CTAs of a batch step run out of work at nearly the same
+// time.  A fixed chunk count (hj_batch_set_shape) replaces both rules.
+void plan_layout(hj_batch *b, const std::vector<char> &active, long long ctas, std::vector<BatchItem> &items)
+{
+    items.clear();
+    long long columns = 0;
+    int min_n1 = 1 << 30;
+    std::vector<int> order;
+    for (int i = 0; i < b->max_slots; ++i) {
+        b->h_insts[i].nitems = 0;
+        if (!b->slots[i].used || !active[i]) continue;
+        const SlotHost &s = b->slots[i];
+        columns += (long long)((s.n[1] + s.ty - 1) / s.ty) * ((s.n[2] + s.tv - 1) / s.tv);
+        if (s.n[0] < min_n1) min_n1 = s.n[0];
+        order.push_back(i);
+    }
+    int nchunk = b->xc_mode > 0 ? b->xc_mode : 1;
+    if (b->xc_mode == 0 && columns > 0 && columns < ctas) {
+        nchunk = (int)((ctas + columns - 1) / columns);
+        const int most = min_n1 / 4 > 1 ? min_n1 / 4 : 1;  // chunks of at least 4 planes
+        if (nchunk > most) nchunk = most;
+    }
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int c) { return b->slots[a].n[0] > b->slots[c].n[0]; });
+    std::vector<int> slot_chunks(b->max_slots, nchunk);
+    if (b->xc_mode == 0 && nchunk == 1) {
+        long long tail = 0;
+        for (int k = (int)order.size() - 1; k >= 0 && tail < 2 * ctas; --k) {
+            const SlotHost &s = b->slots[order[k]];
+            if (s.n[0] < 8) break;
+            const int ch = tail < ctas ? 4 : 2;
+            slot_chunks[order[k]] = ch;
+            tail += (long long)ch * ((s.n[1] + s.ty - 1) / s.ty) * ((s.n[2] + s.tv - 1) / s.tv);
+        }
+    }
+    for (int i : order) {
+        SlotHost &s = b->slots[i];
+        s.xc = (s.n[0] + slot_chunks[i] - 1) / slot_chunks[i];
+        if (s.xc < 4) s.xc = s.n[0] < 4 ? s.n[0] : 4;
+        const int ncv = (s.n[2] + s.tv - 1) / s.tv, ncy = (s.n[1] + s.ty - 1) / s.ty;
+        const int nch = (s.n[0] + s.xc - 1) / s.xc;
+        b->h_insts[i].xc = s.xc;
+        b->h_insts[i].nitems = ncv * ncy * nch;
+        for (int c = 0; c < nch; ++c)
+            for (int yt = 0; yt < ncy; ++yt)
+                for (int vt = 0; vt < ncv; ++vt) items.push_back({i, yt * s.ty, vt * s.tv, c * s.xc});
+    }
+    b->lay_active = active;
+}
+
+// Resident CTAs of a block of nc consumers (before the occupancy query).
+long long resident_ctas(const hj_batch *b, int nc) { return (long long)b->sms * (nc <= B_DUAL ? 2 : 1); }
+
 // Rebuild the per-slot descriptors, tensor maps and item list after slots or
 // the kernel shape changed.
 hj_status rebuild(hj_batch *b)
@@ -726,59 +790,25 @@ hj_status rebuild(hj_batch *b)
                 while (nc < need && nc < B_VARIANTS[3]) nc += 128;
             }
     }
-    std::vector<BatchInst> insts(b->max_slots);
+    b->h_insts.assign(b->max_slots, BatchInst());
+    std::vector<BatchInst> &insts = b->h_insts;
     std::vector<CUtensorMap> maps((size_t)4 * b->max_slots);
     memset(insts.data(), 0, sizeof(BatchInst) * insts.size());
     memset(maps.data(), 0, sizeof(CUtensorMap) * maps.size());
     std::vector<BatchItem> items;
     int stage_bytes = 128;
     int max_cons = 32;
-    // x chunks: the requested count, or automatically whole columns while the
-    // batch has at least one (y, v) column per SM; with fewer (a lone request
-    // of the serving loop) enough chunks to give every SM an item, since a
-    // column's planes are streamed one after another by one CTA
-    long long columns = 0;
-    int min_n1 = 1 << 30;
+    std::vector<char> all(b->max_slots, 0);
     for (int i = 0; i < b->max_slots; ++i) {
         SlotHost &s = b->slots[i];
         if (!s.used) continue;
         choose_tile(s, nc, &s.ty, &s.tv);
-        columns += (long long)((s.n[1] + s.ty - 1) / s.ty) * ((s.n[2] + s.tv - 1) / s.tv);
-        if (s.n[0] < min_n1) min_n1 = s.n[0];
+        all[i] = 1;
     }
-    int nchunk = b->xc_mode > 0 ? b->xc_mode : 1;
-    if (b->xc_mode == 0 && columns > 0 && columns < b->sms) {
-        nchunk = (int)((b->sms + columns - 1) / columns);
-        const int most = min_n1 / 4 > 1 ? min_n1 / 4 : 1;  // chunks of at least 4 planes
-        if (nchunk > most) nchunk = most;
-    }
-    // Item order: slots with the longest columns first.  In the automatic
-    // mode with whole columns, the slots whose items come last in the queue
-    // are cut into x chunks (about the last item per CTA into four, the one
-    // before into two), so that the CTAs of a batch step run out of work at
-    // nearly the same time.
-    std::vector<int> order;
-    for (int i = 0; i < b->max_slots; ++i)
-        if (b->slots[i].used) order.push_back(i);
-    std::stable_sort(order.begin(), order.end(),
-                     [&](int a, int c) { return b->slots[a].n[0] > b->slots[c].n[0]; });
-    std::vector<int> slot_chunks(b->max_slots, nchunk);
-    if (b->xc_mode == 0 && nchunk == 1) {
-        const long long ctas = (long long)b->sms * (nc <= B_DUAL ? 2 : 1);  // resident CTAs of the shape
-        long long tail = 0;
-        for (int k = (int)order.size() - 1; k >= 0 && tail < 2 * ctas; --k) {
-            const SlotHost &s = b->slots[order[k]];
-            if (s.n[0] < 8) break;
-            const int ch = tail < ctas ? 4 : 2;
-            slot_chunks[order[k]] = ch;
-            tail += (long long)ch * ((s.n[1] + s.ty - 1) / s.ty) * ((s.n[2] + s.tv - 1) / s.tv);
-        }
-    }
-    for (int oi = 0; oi < (int)order.size(); ++oi) {
-        const int i = order[oi];
+    plan_layout(b, all, resident_ctas(b, nc), items);
+    for (int i = 0; i < b->max_slots; ++i) {
+        if (!all[i]) continue;
         SlotHost &s = b->slots[i];
-        s.xc = (s.n[0] + slot_chunks[i] - 1) / slot_chunks[i];
-        if (s.xc < 4) s.xc = s.n[0] < 4 ? s.n[0] : 4;
         BatchInst &I = insts[i];
         I.n1 = s.n[0];
         I.n2 = s.n[1];
@@ -788,7 +818,6 @@ hj_status rebuild(hj_batch *b)
         I.q4 = s.p4 / 4;
         I.ty = s.ty;
         I.tv = s.tv;
-        I.xc = s.xc;
         I.halo_box = s.p4 * (s.tv + 2) * (s.ty + 2);
         I.halo_floats = (I.halo_box + 31) / 32 * 32;
         I.v0_floats = s.p4 * s.ty * s.tv;
@@ -801,12 +830,6 @@ hj_status rebuild(hj_batch *b)
         I.coef = s.coef;
         I.amaxv = s.amaxv;
         I.geom = s.geom;
-        const int ncv = (s.n[2] + s.tv - 1) / s.tv, ncy = (s.n[1] + s.ty - 1) / s.ty;
-        const int nch = (s.n[0] + s.xc - 1) / s.xc;
-        I.nitems = ncv * ncy * nch;
-        for (int c = 0; c < nch; ++c)
-            for (int yt = 0; yt < ncy; ++yt)
-                for (int vt = 0; vt < ncv; ++vt) items.push_back({i, yt * s.ty, vt * s.tv, c * s.xc});
         const int sb = ((I.halo_floats + I.v0_floats) * 4 + 127) / 128 * 128;
         if (sb > stage_bytes) stage_bytes = sb;
         const int cons = ((I.q4 * s.ty * s.tv) + 31) / 32 * 32;
@@ -837,11 +860,14 @@ hj_status rebuild(hj_batch *b)
     if (bp.stages > B_MAX_STAGES) bp.stages = B_MAX_STAGES;
     if (bp.stages < 4) return bfail(HJ_ERR_UNSUPPORTED, "a slot's tile does not fit four ring stages");
     // device copies
-    if ((int)items.size() > b->items_cap) {
+    // room for the layouts of the advance loop's later phases too (at most
+    // about four items per resident CTA beyond this layout's count)
+    const int need = (int)items.size() + 4 * (int)resident_ctas(b, nc) + 64;
+    if (need > b->items_cap) {
         if (b->d_items) cudaFree(b->d_items);
         b->d_items = nullptr;
         b->items_cap = 0;
-        const int cap = (int)items.size() * 2 + 64;
+        const int cap = need + (int)items.size();
         HJB_CUDA(cudaMalloc(&b->d_items, sizeof(BatchItem) * cap));
         b->items_cap = cap;
         drop_graphs(b);  // the kernel's item pointer changed
@@ -875,6 +901,37 @@ hj_status launch_batch_step(hj_batch *b)
     fn<<<b->ctas, b->bp.nconsumer + 32, batch_smem(b->bp), b->stream>>>(b->d_insts, b->d_slots, b->d_items, b->d_ctl,
                                                                         b->d_maps, b->bp);
     HJB_CUDA(cudaGetLastError());
+    return HJ_OK;
+}
+
+// Switch the item layout to the slots marked in `active` (a no-op when the
+// layout covers them already).  The item list, the per-slot descriptors and
+// the item count go to the device by copies queued on the batch's stream,
+// so they take effect between batch steps, after every step queued before;
+// the captured step graphs read them at run time and stay valid.  A layout
+// that would not fit the item buffer keeps the current one.
+hj_status apply_layout(hj_batch *b, const std::vector<char> &active)
+{
+    if (active == b->lay_active) return HJ_OK;
+    const std::vector<char> keep = b->lay_active;
+    const std::vector<BatchInst> keep_insts = b->h_insts;
+    std::vector<BatchItem> items;
+    plan_layout(b, active, b->ctas, items);
+    if ((int)items.size() > b->items_cap || items.empty()) {
+        b->h_insts = keep_insts;
+        b->lay_active = keep;
+        for (int i = 0; i < b->max_slots; ++i) b->slots[i].xc = b->h_insts[i].xc;
+        return HJ_OK;
+    }
+    // pageable sources: each copy has taken its data when the call returns
+    HJB_CUDA(cudaMemcpyAsync(b->d_items, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice,
+                             b->stream));
+    HJB_CUDA(cudaMemcpyAsync(b->d_insts, b->h_insts.data(), sizeof(BatchInst) * b->h_insts.size(),
+                             cudaMemcpyHostToDevice, b->stream));
+    b->lay_nitems = (int)items.size();
+    HJB_CUDA(cudaMemcpyAsync((char *)b->d_ctl + offsetof(BatchCtl, nitems), &b->lay_nitems, sizeof(int),
+                             cudaMemcpyHostToDevice, b->stream));
+    b->nitems = b->lay_nitems;
     return HJ_OK;
 }
 
@@ -1384,22 +1441,59 @@ hj_status hj_batch_advance(hj_batch *b, int64_t max_steps, hj_batch_stats *stats
     if ((s = pull_slots(b)) != HJ_OK) return s;
     HJB_CUDA(cudaEventRecord(b->ev[0], b->stream));
     while (taken < max_steps && b->nitems > 0) {
-        // batch steps until the slowest unfinished slot reaches its horizon
+        // batch steps until the slowest unfinished slot reaches its horizon;
+        // ki: the steps slot i has left (exact while its dt stays constant,
+        // as with the car's fixed alpha^max; the loop re-plans otherwise)
         long long k = 0;
+        std::vector<long long> ki(b->max_slots, 0);
         for (int i = 0; i < b->max_slots; ++i) {
             if (!b->slots[i].used) continue;
             const HjDevState &h = b->h_slots[i].st;
             if (h.done || h.status != HJ_OK) continue;
-            long long ki = 1;
+            ki[i] = 1;
             if (!h.last && h.dt > 0) {
                 const double r = ceil((h.T - h.t) / h.dt);
-                ki = r > 1 ? (r < 1e9 ? (long long)r : 1000000000LL) : 1;
+                ki[i] = r > 1 ? (r < 1e9 ? (long long)r : 1000000000LL) : 1;
             }
-            if (ki > k) k = ki;
+            if (ki[i] > k) k = ki[i];
         }
         if (k == 0) break;
         if (k > max_steps - taken) k = max_steps - taken;
-        if ((s = launch_steps(b, k)) != HJ_OK) return s;
+        // Phases: as slots reach their horizons, the remaining ones get a
+        // new item layout (finer x chunks once they have fewer columns than
+        // CTAs) when their columns have fallen below half of those at the
+        // phase's start; otherwise the last steps would each take a whole
+        // column sweep of a few long items.  With a fixed chunk count the
+        // layout only drops the finished slots.
+        long long s0 = 0;
+        while (s0 < k) {
+            std::vector<char> act(b->max_slots, 0);
+            long long cols = 0;
+            auto columns_after = [&](long long st) {  // columns of the slots still running after st steps
+                long long c = 0;
+                for (int i = 0; i < b->max_slots; ++i)
+                    if (ki[i] > st) {
+                        const SlotHost &sl = b->slots[i];
+                        c += (long long)((sl.n[1] + sl.ty - 1) / sl.ty) * ((sl.n[2] + sl.tv - 1) / sl.tv);
+                    }
+                return c;
+            };
+            for (int i = 0; i < b->max_slots; ++i) act[i] = ki[i] > s0;
+            cols = columns_after(s0);
+            long long e = k;
+            std::vector<long long> ends;
+            for (int i = 0; i < b->max_slots; ++i)
+                if (ki[i] > s0 && ki[i] < k) ends.push_back(ki[i]);
+            std::sort(ends.begin(), ends.end());
+            for (long long r : ends)
+                if (2 * columns_after(r) < cols) {
+                    e = r;
+                    break;
+                }
+            if ((s = apply_layout(b, act)) != HJ_OK) return s;
+            if ((s = launch_steps(b, e - s0)) != HJ_OK) return s;
+            s0 = e;
+        }
         started = true;
         launches += k;
         taken += k;

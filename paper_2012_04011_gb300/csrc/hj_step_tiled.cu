@@ -206,6 +206,9 @@ bool hj_tiled_setup(hj_grid *g, char *why, size_t why_len)
                 if ((ty > 0 && a != ty) || (tv > 0 && b != tv)) continue;
                 const int cons = consumers_of(g, a, b);
                 if (cons > cap && !(a == 1 && b == 1)) continue;
+                // room for the smallest ring (4 stages)
+                if (4 * (size_t)make_params(g, a, b, 1, 0).stage_bytes + 2048 > (size_t)maxsmem && !(a == 1 && b == 1))
+                    continue;
                 // work items this shape can offer (columns x chunks of >= 4 planes)
                 const double items = (double)((g->n[1] + a - 1) / a) * ((g->n[2] + b - 1) / b) *
                                      (g->n[0] / 4 > 1 ? g->n[0] / 4 : 1);

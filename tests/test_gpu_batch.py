@@ -127,6 +127,41 @@ def test_batch_shapes_and_autotune_give_identical_bits(hj):
             assert np.array_equal(a, c)
 
 
+@pytest.mark.parametrize("shape, pieces", [((0, 0), 1), ((0, 0), 3), ((288, 2), 1)])
+def test_batch_relayout_as_slots_finish(hj, shape, pieces):
+    """Horizons from 0.1 to 1.2 s: as slots finish, the advance loop gives the
+    remaining ones a new item layout (finer x chunks once they have fewer
+    columns than CTAs).  Every slot still gives its single-grid solve's bits
+    and step count, whether one advance call runs the whole solve or
+    several calls with a step budget split it."""
+    ns = [(44, 40, 16, 24), (30, 36, 12, 32), (50, 26, 18, 28), (24, 24, 10, 16), (40, 48, 20, 36), (36, 30, 14, 24)]
+    Ts = [0.1, 1.2, 0.3, 0.9, 0.6, 1.0]
+    ws = [scenes.custom_workload(n, n_circles=3, n_rects=1, T=T, seed=300 + i) for i, (n, T) in enumerate(zip(ns, Ts))]
+    v0s = [scenes.initial_value(w.grid, w.scene) for w in ws]
+    with hj.Batch(len(ws)) as b:
+        slots = [b.add_workload(w) for w in ws]
+        if shape != (0, 0):
+            b.set_shape(*shape)
+        for s, w, v0 in zip(slots, ws, v0s):
+            b.set_initial_value(s, v0)
+            b.set_horizon(s, w.T, w.cfl)
+        if pieces == 1:
+            st = b.advance()
+        else:
+            total = 0
+            while True:
+                st = b.advance(23)
+                total += st.steps
+                if st.active == 0:
+                    break
+        assert st.active == 0
+        for s, w, v0 in zip(slots, ws, v0s):
+            ref, rst = single_grid(hj, w, v0)
+            info = b.slot_info(s)
+            assert info.steps == rst.steps and info.t == w.T
+            assert np.array_equal(b.read_value(s), ref), (s, w.grid.n)
+
+
 @pytest.mark.slow
 def test_batch64_workload(hj):
     """The 64-instance workload: uneven grids (N1, N2 in {40, 50, 60}, N3 in
