@@ -335,17 +335,18 @@ HJ_API hj_status hj_step_noalloc(const int32_t n[4], const double lo[4], const d
  *
  * A batch holds up to max_slots grids ("slots"), each with its own size,
  * bounds, control bounds, V0, horizon and time loop (Sec. II-B scheme as
- * above, FP32, theta periodic, the other axes not).  One batch step runs one
- * persistent kernel over every slot that has not reached its horizon, each
- * slot advancing by its own CFL step; hj_batch_advance launches batch steps
- * as CUDA graphs.  Slots may be added and removed between calls (admission is
+ * above, FP32, theta periodic, the other axes not).  A batch step advances
+ * every slot that has not reached its horizon by its own CFL step;
+ * hj_batch_advance runs up to 1024 batch steps per launch of one persistent
+ * kernel, in which each slot starts its next step as soon as its own step is
+ * done.  Slots may be added and removed between calls (admission is
  * by device memory: a slot needs hj_batch_slot_bytes(n) of the batch's
  * budget). */
 typedef struct hj_batch hj_batch;
 
 typedef struct {
     int64_t steps;      /* batch steps taken by this call */
-    int64_t launches;   /* step kernels launched */
+    int64_t launches;   /* kernel launches (each runs up to 1024 batch steps) */
     int32_t active;     /* slots with steps left after this call */
     int32_t finished;   /* slots at their horizon */
     double device_ms;   /* device time of the call (CUDA events) */

@@ -1,35 +1,35 @@
 // Batched solves: many independent 4D car instances (each its own grid
-// size, obstacle map V0, horizon and time loop) stepped together by one
-// persistent kernel per time step, with the time loop captured as a CUDA
-// graph.  Same scheme and same per-cell arithmetic as the single-grid tiled
-// kernel (one step of Algorithm 2 of arxiv 2012.04011 in upwind form, see
-// hj_step_generic.cu and hj_step_tiled.cu).
+// size, obstacle map V0, horizon and time loop) stepped by one persistent
+// kernel that runs many batch steps per launch.  Same scheme and same
+// per-cell arithmetic as the single-grid tiled kernel (one step of
+// Algorithm 2 of arxiv 2012.04011 in upwind form, see hj_step_generic.cu and
+// hj_step_tiled.cu).
 //
-// Work: every active slot's grid is cut into items (slot, y-tile, v-tile,
+// Work: every running slot's grid is cut into items (slot, y-tile, v-tile,
 // x-chunk).  A CTA's producer warp takes the next item from a device-side
 // queue (items are ordered slot by slot, so concurrently running CTAs share
-// neighbouring columns and their halos hit L2), skips items of slots that
-// have reached their horizon, and streams the item's planes (V_n box with a
-// one-cell y/v halo, V0 box without) through the shared-memory ring with
-// TMA; the stage of an item's first plane carries the item's descriptor
-// (geometry, the slot's coefficients, dt and output buffer), so consumers
-// start an item from shared memory.  Consumers own one (row, theta quad)
-// each, as in the single-grid kernel, and update lane pairs with paired FP32
-// multiply-adds; the tile shape of each slot is chosen so that its rows x
-// quads fit the block.
+// neighbouring columns and their halos hit L2) and streams the item's planes
+// (V_n box with a one-cell y/v halo, V0 box without) through the
+// shared-memory ring with TMA; the stage of an item's first plane carries the
+// item's descriptor (geometry, the slot's coefficients, dt and output
+// buffer), so consumers start an item from shared memory.  Consumers own one
+// (row, theta quad) each, as in the single-grid kernel, and update lane pairs
+// with paired FP32 multiply-adds; the tile shape of each slot is chosen so
+// that its rows x quads fit the block.
 //
 // Time loop: each slot keeps its own FP64 state (t, dt, step count) on the
 // device.  After an item, each consumer warp counts itself done; the warp
-// that completes the slot's last item reduces the slot's alpha^max over its
-// per-speed table of |xdot_1|, |xdot_2| maxima and computes the slot's next
-// CFL step (hj_finalise).  Slots
-// therefore advance independently: a batch step moves every unfinished slot
-// by its own dt, and finished slots cost nothing.
+// that completes the slot's last item of a step reduces the slot's alpha^max
+// over its per-speed table of |xdot_1|, |xdot_2| maxima and computes the
+// slot's next CFL step (hj_finalise).  A launch runs many such steps as
+// rounds of the queue (round r: the items of every slot with more than r
+// steps to go), and a slot's items of its next step start as soon as its own
+// step is finalised, so the slots do not wait for one another between steps
+// and the GPU stays busy while the slots that finish early drop out.
 //
-// Slots can be added and removed between steps (the serving loop admits
-// requests this way); the item list and tensor maps live in device memory,
-// so a captured graph stays valid while the kernel shape (block size, ring
-// stage size) does not change.
+// Slots can be added and removed between calls (the serving loop admits
+// requests this way); the item list, the per-slot descriptors and the tensor
+// maps live in device memory and are rewritten by stream-ordered copies.
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
@@ -50,6 +50,8 @@ constexpr int B_VARIANTS[4] = {352, 480, 608, 736};
 // independent rings and producers per SM; each CTA gets half the SM's shared
 // memory).
 constexpr int B_DUAL = 288;
+// Batch steps (rounds) per launch at most.
+constexpr int B_MAX_ROUNDS = 1024;
 
 struct BatchInst {
     int n1, n2, n3, n4, p4, q4;
@@ -318,10 +320,24 @@ __device__ __forceinline__ bool batch_item_planes(const BatchDesc &d, int s_firs
 #undef HJ_RELEASE_OLDEST
 }
 
+// One launch runs nrounds batch steps.  Round r holds the items of every
+// slot with more than r steps to go: the first round_start[r + 1] -
+// round_start[r] items of the item list (slots with more steps first), at
+// queue positions round_start[r] onwards.  A slot moves to its next step as
+// soon as its own step is finalised: the producer that takes an item of round
+// r waits (bounded) until rounds_done[slot] (zeroed before the launch, raised
+// by the slot's finalising warp after the slot's state is written and
+// fenced) reaches r, then reads the slot's state.  Every item
+// of the slot's round r - 1 comes earlier in the queue and needs nothing
+// that a waiting producer holds, so the waits end.  Consumers make their
+// stores visible to other SMs' tensor copies (a proxy fence and a release
+// fence) before they count an item done; the producer acquires the finalised
+// step before it issues the item's copies.
 template <int MAXC, int MINB>
 __global__ void __launch_bounds__(MAXC + 32, MINB)
     hj_batch_step_kernel(const BatchInst *__restrict__ insts, BatchSlot *slots, const BatchItem *__restrict__ items,
-                         BatchCtl *ctl, const CUtensorMap *maps, const BatchParams BP)
+                         BatchCtl *ctl, const CUtensorMap *maps, const BatchParams BP,
+                         const int *__restrict__ round_start, int *rounds_done, int nrounds)
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     float *stages = (float *)smem_raw;
@@ -349,7 +365,7 @@ __global__ void __launch_bounds__(MAXC + 32, MINB)
     if (tid >= BP.nconsumer) {
         // ------------------------------------------------------------ producer
         if (tid == BP.nconsumer) {
-            const unsigned long long deadline = *deadline_p;
+            unsigned long long deadline = *deadline_p;
             int slot = 0;
             uint32_t phase = 0, issued = 0, used_mask = 0, last_phase = 0;
             bool ok = true;
@@ -366,14 +382,38 @@ __global__ void __launch_bounds__(MAXC + 32, MINB)
                     phase ^= 1u;
                 }
             };
+            int round = 0;
             while (ok) {
-                const int item = (int)atomicAdd(&ctl->head, 1u);
-                if (item >= nitems) break;
+                const int gi = (int)atomicAdd(&ctl->head, 1u);
+                if (gi >= nitems) break;
+                while (round + 1 < nrounds && round_start[round + 1] <= gi) ++round;  // queue positions only grow
+                const int item = gi - round_start[round];
                 const BatchItem it = items[item];
-                const BatchSlot *sl = &slots[it.slot];
-                if (sl->st.done) continue;
+                BatchSlot *sl = &slots[it.slot];
+                // the slot's steps of the earlier rounds must be finalised
+                // (bounded wait; a slot that reached its horizon has no more)
+                const unsigned long long wdl = global_ns() + HJ_WAIT_NS;
+                bool skip = false;
+                while (*(volatile int *)&rounds_done[it.slot] < round) {
+                    if (*(volatile int *)&sl->st.done) {
+                        skip = true;
+                        break;
+                    }
+                    if (global_ns() > wdl || *abort_flag) {
+                        ok = false;
+                        break;
+                    }
+                    __nanosleep(256);
+                }
+                if (!ok) break;
+                if (skip) continue;
+                __threadfence();  // acquire the slot's state and its V_n
+                asm volatile("fence.proxy.async.global;" ::: "memory");
+                if (*(volatile int *)&sl->st.done) continue;
+                deadline = global_ns() + HJ_WAIT_NS;
+                *deadline_p = deadline;  // the waits of this item: bounded per item
                 const BatchInst &I = insts[it.slot];
-                const long long n = sl->st.n;
+                const long long n = *(volatile long long *)&sl->st.n;
                 const CUtensorMap *m_in = &maps[4 * it.slot + (n == 0 ? 0 : 1 + (int)((n - 1) & 1))];
                 const CUtensorMap *m_v0 = &maps[4 * it.slot + 3];
                 tensormap_acquire(m_in);
@@ -406,7 +446,7 @@ __global__ void __launch_bounds__(MAXC + 32, MINB)
                         D.k3 = I.k3;
                         D.k4 = I.k4;
                         D.mk34 = I.mk34;
-                        D.dt = (float)sl->st.dt;
+                        D.dt = (float)*(volatile double *)&sl->st.dt;
                         D.vout = I.buf + (n & 1) * I.nint;
                         D.tab = I.tab;
                     }
@@ -481,12 +521,16 @@ __global__ void __launch_bounds__(MAXC + 32, MINB)
             // of the slot was updated in this step, and the car's velocity
             // depends on v and theta only: the same maxima as over the cells)
             // and finalises the step
-            // (no fence before the count: nothing this launch writes is read in
-            // it by another warp except the count and the slot state, which
-            // only the finalising warp writes; the next launch sees all of it)
+            // (this warp's stores of V_{n+1} are read by later items' tensor
+            // copies on other SMs: proxy fence, then a release before the count)
             BatchSlot *sl = &slots[d.slot];
+            asm volatile("fence.proxy.async.global;" ::: "memory");
+            __syncwarp();
             unsigned int last = 0u;
-            if (lane == 0) last = atomicAdd(&sl->warps_done, 1u) + 1 == d.per_step;
+            if (lane == 0) {
+                __threadfence();
+                last = atomicAdd(&sl->warps_done, 1u) + 1 == d.per_step;
+            }
             if (__shfl_sync(0xffffffffu, last, 0)) {
                 __threadfence();
                 const BatchInst &I = insts[d.slot];
@@ -505,6 +549,7 @@ __global__ void __launch_bounds__(MAXC + 32, MINB)
                     hj_finalise(&sl->st, I.geom);
                     sl->warps_done = 0u;
                     __threadfence();
+                    atomicAdd(&rounds_done[d.slot], 1);  // publish: the slot's next step may start
                 }
             }
         }
@@ -551,7 +596,7 @@ BEncodeFn batch_encode_fn()
 }
 
 typedef void (*BatchKernelFn)(const BatchInst *, BatchSlot *, const BatchItem *, BatchCtl *, const CUtensorMap *,
-                              const BatchParams);
+                              const BatchParams, const int *, int *, int);
 
 BatchKernelFn batch_kernel(int nconsumer)
 {
@@ -604,6 +649,7 @@ struct hj_batch {
     std::vector<BatchInst> h_insts;  // host copy of d_insts (the item layout rewrites xc and nitems)
     std::vector<char> lay_active;    // slots the current item layout covers
     int lay_nitems = 0;              // source of the stream-ordered copy into d_ctl->nitems
+    int lay_items = 0;               // items of one batch step in the current layout
     BatchCtl *d_ctl = nullptr;
     CUtensorMap *d_maps = nullptr;
     int nconsumer_req = 0;  // 0: automatic
@@ -612,7 +658,10 @@ struct hj_batch {
     int ctas = 0;
     int nitems = 0;
     bool dirty = true;
-    std::vector<std::pair<long long, cudaGraphExec_t>> graphs;
+    int *d_rounds = nullptr;       // queue position of each round of a launch (B_MAX_ROUNDS + 1)
+    int *d_rounds_done = nullptr;  // per slot: steps finalised in the current launch
+    std::vector<int> h_rounds;     // source of the stream-ordered copy into d_rounds
+    std::vector<int> lay_order;   // slot order of the current item layout
     cudaEvent_t ev[2] = {nullptr, nullptr};
     cudaEvent_t ev_in = nullptr;  // own stream: orders device inputs after the legacy default stream
     SlotSetup *h_setup = nullptr;  // pinned staging of the multi-slot set-up lists (max_slots entries)
@@ -644,11 +693,6 @@ hj_status bfail(hj_status s, const char *fmt, ...)
         }                                                                                                \
     } while (0)
 
-void drop_graphs(hj_batch *b)
-{
-    for (auto &kv : b->graphs) cudaGraphExecDestroy(kv.second);
-    b->graphs.clear();
-}
 
 // Tile of one slot for a block of nc consumer threads (ty x tv <= nc / q4).
 // Every item costs the whole block a pass over its planes, whether its rows
@@ -722,7 +766,8 @@ hj_status upload_slot_tables(hj_batch *b, SlotHost &s)
 // into x chunks (about the last item per CTA into four, the one before into
 // two), so that the CTAs of a batch step run out of work at nearly the same
 // time.  A fixed chunk count (hj_batch_set_shape) replaces both rules.
-void plan_layout(hj_batch *b, const std::vector<char> &active, long long ctas, std::vector<BatchItem> &items)
+void plan_layout(hj_batch *b, const std::vector<char> &active, const std::vector<long long> &ki, long long ctas,
+                 std::vector<BatchItem> &items)
 {
     items.clear();
     long long columns = 0;
@@ -742,8 +787,12 @@ void plan_layout(hj_batch *b, const std::vector<char> &active, long long ctas, s
         const int most = min_n1 / 4 > 1 ? min_n1 / 4 : 1;  // chunks of at least 4 planes
         if (nchunk > most) nchunk = most;
     }
-    std::stable_sort(order.begin(), order.end(),
-                     [&](int a, int c) { return b->slots[a].n[0] > b->slots[c].n[0]; });
+    // slots with more steps to go first (a launch's later rounds are then a
+    // prefix of the list), then the longest columns first
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
+        if (ki[a] != ki[c]) return ki[a] > ki[c];
+        return b->slots[a].n[0] > b->slots[c].n[0];
+    });
     std::vector<int> slot_chunks(b->max_slots, nchunk);
     if (b->xc_mode == 0 && nchunk == 1) {
         long long tail = 0;
@@ -768,6 +817,7 @@ void plan_layout(hj_batch *b, const std::vector<char> &active, long long ctas, s
                 for (int vt = 0; vt < ncv; ++vt) items.push_back({i, yt * s.ty, vt * s.tv, c * s.xc});
     }
     b->lay_active = active;
+    b->lay_order = order;
 }
 
 // Resident CTAs of a block of nc consumers (before the occupancy query).
@@ -805,7 +855,7 @@ hj_status rebuild(hj_batch *b)
         choose_tile(s, nc, &s.ty, &s.tv);
         all[i] = 1;
     }
-    plan_layout(b, all, resident_ctas(b, nc), items);
+    plan_layout(b, all, std::vector<long long>(b->max_slots, 1), resident_ctas(b, nc), items);
     for (int i = 0; i < b->max_slots; ++i) {
         if (!all[i]) continue;
         SlotHost &s = b->slots[i];
@@ -870,7 +920,6 @@ hj_status rebuild(hj_batch *b)
         const int cap = need + (int)items.size();
         HJB_CUDA(cudaMalloc(&b->d_items, sizeof(BatchItem) * cap));
         b->items_cap = cap;
-        drop_graphs(b);  // the kernel's item pointer changed
     }
     HJB_CUDA(cudaStreamSynchronize(b->stream));
     if (!items.empty())
@@ -880,8 +929,8 @@ hj_status rebuild(hj_batch *b)
     BatchCtl ctl = {0u, 0u, (int)items.size(), HJ_OK};
     HJB_CUDA(cudaMemcpy(b->d_ctl, &ctl, sizeof(ctl), cudaMemcpyHostToDevice));
     b->nitems = (int)items.size();
+    b->lay_items = b->nitems;
     if (bp.nconsumer != b->bp.nconsumer || bp.stages != b->bp.stages || bp.stage_bytes != b->bp.stage_bytes) {
-        drop_graphs(b);
         b->bp = bp;
         BatchKernelFn fn = batch_kernel(bp.nconsumer);
         const size_t smem = batch_smem(bp);
@@ -895,75 +944,91 @@ hj_status rebuild(hj_batch *b)
     return HJ_OK;
 }
 
-hj_status launch_batch_step(hj_batch *b)
+// Item layout of the slots with ki > 0, ordered by ki (steps to go), for a
+// launch.  The item list, the per-slot descriptors and the item count go to
+// the device by copies queued on the batch's stream, so they take effect
+// after every launch queued before.  A no-op when the layout covers the same
+// slots in the same order.
+hj_status apply_layout(hj_batch *b, const std::vector<long long> &ki)
 {
+    std::vector<char> active(b->max_slots, 0);
+    for (int i = 0; i < b->max_slots; ++i) active[i] = b->slots[i].used && ki[i] > 0;
+    std::vector<int> order;
+    for (int i = 0; i < b->max_slots; ++i)
+        if (active[i]) order.push_back(i);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
+        if (ki[a] != ki[c]) return ki[a] > ki[c];
+        return b->slots[a].n[0] > b->slots[c].n[0];
+    });
+    if (active == b->lay_active && order == b->lay_order) return HJ_OK;
+    std::vector<BatchItem> items;
+    plan_layout(b, active, ki, b->ctas, items);
+    if ((int)items.size() > b->items_cap)
+        return bfail(HJ_ERR_CUDA, "batch item layout of %d items exceeds its buffer (%d)", (int)items.size(),
+                     b->items_cap);
+    // pageable sources: each copy has taken its data when the call returns
+    if (!items.empty())
+        HJB_CUDA(cudaMemcpyAsync(b->d_items, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice,
+                                 b->stream));
+    HJB_CUDA(cudaMemcpyAsync(b->d_insts, b->h_insts.data(), sizeof(BatchInst) * b->h_insts.size(),
+                             cudaMemcpyHostToDevice, b->stream));
+    b->lay_items = (int)items.size();
+    return HJ_OK;
+}
+
+// k batch steps (k <= B_MAX_ROUNDS) as one launch: every slot i takes
+// min(ki[i], k) of them (round r holds the slots with ki > r, a prefix of
+// the layout).
+hj_status run_rounds(hj_batch *b, const std::vector<long long> &ki, long long k)
+{
+    if (k <= 0) return HJ_OK;
+    if (k > B_MAX_ROUNDS) return bfail(HJ_ERR_INVALID_ARG, "at most %d batch steps per launch", B_MAX_ROUNDS);
+    hj_status s = apply_layout(b, ki);
+    if (s != HJ_OK) return s;
+    // round r: the items of the slots with ki > r (a prefix of the layout)
+    std::vector<long long> per_slot(b->max_slots, 0);
+    for (int i = 0; i < b->max_slots; ++i) per_slot[i] = b->h_insts[i].nitems;
+    b->h_rounds.assign((size_t)k + 1, 0);
+    long long pos = 0;
+    for (long long r = 0; r < k; ++r) {
+        b->h_rounds[r] = (int)pos;
+        for (int i : b->lay_order)
+            if (ki[i] > r) pos += per_slot[i];
+    }
+    if (pos >= (1LL << 31)) return bfail(HJ_ERR_INVALID_ARG, "too many work items in one launch");
+    b->h_rounds[k] = (int)pos;
+    HJB_CUDA(cudaMemcpyAsync(b->d_rounds, b->h_rounds.data(), sizeof(int) * (k + 1), cudaMemcpyHostToDevice,
+                             b->stream));
+    HJB_CUDA(cudaMemsetAsync(b->d_rounds_done, 0, sizeof(int) * b->max_slots, b->stream));
+    b->lay_nitems = (int)pos;
+    HJB_CUDA(cudaMemcpyAsync((char *)b->d_ctl + offsetof(BatchCtl, nitems), &b->lay_nitems, sizeof(int),
+                             cudaMemcpyHostToDevice, b->stream));
+    b->nitems = (int)pos;
     BatchKernelFn fn = batch_kernel(b->bp.nconsumer);
     fn<<<b->ctas, b->bp.nconsumer + 32, batch_smem(b->bp), b->stream>>>(b->d_insts, b->d_slots, b->d_items, b->d_ctl,
-                                                                        b->d_maps, b->bp);
+                                                                        b->d_maps, b->bp, b->d_rounds,
+                                                                        b->d_rounds_done, (int)k);
     HJB_CUDA(cudaGetLastError());
     return HJ_OK;
 }
 
-// Switch the item layout to the slots marked in `active` (a no-op when the
-// layout covers them already).  The item list, the per-slot descriptors and
-// the item count go to the device by copies queued on the batch's stream,
-// so they take effect between batch steps, after every step queued before;
-// the captured step graphs read them at run time and stay valid.  A layout
-// that would not fit the item buffer keeps the current one.
-hj_status apply_layout(hj_batch *b, const std::vector<char> &active)
+// Steps to go of every slot: ceil((T - t) / dt) (exact while dt stays
+// constant, as with the car's fixed alpha^max; the advance loop re-plans
+// otherwise), 0 for a slot that is not running.
+std::vector<long long> steps_to_go(const hj_batch *b)
 {
-    if (active == b->lay_active) return HJ_OK;
-    const std::vector<char> keep = b->lay_active;
-    const std::vector<BatchInst> keep_insts = b->h_insts;
-    std::vector<BatchItem> items;
-    plan_layout(b, active, b->ctas, items);
-    if ((int)items.size() > b->items_cap || items.empty()) {
-        b->h_insts = keep_insts;
-        b->lay_active = keep;
-        for (int i = 0; i < b->max_slots; ++i) b->slots[i].xc = b->h_insts[i].xc;
-        return HJ_OK;
-    }
-    // pageable sources: each copy has taken its data when the call returns
-    HJB_CUDA(cudaMemcpyAsync(b->d_items, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice,
-                             b->stream));
-    HJB_CUDA(cudaMemcpyAsync(b->d_insts, b->h_insts.data(), sizeof(BatchInst) * b->h_insts.size(),
-                             cudaMemcpyHostToDevice, b->stream));
-    b->lay_nitems = (int)items.size();
-    HJB_CUDA(cudaMemcpyAsync((char *)b->d_ctl + offsetof(BatchCtl, nitems), &b->lay_nitems, sizeof(int),
-                             cudaMemcpyHostToDevice, b->stream));
-    b->nitems = b->lay_nitems;
-    return HJ_OK;
-}
-
-// k batch steps as one CUDA graph launch (graphs cached by k)
-hj_status launch_steps(hj_batch *b, long long k)
-{
-    if (k <= 0) return HJ_OK;
-    cudaGraphExec_t exec = nullptr;
-    for (auto &kv : b->graphs)
-        if (kv.first == k) exec = kv.second;
-    if (!exec) {
-        cudaGraph_t graph = nullptr;
-        HJB_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
-        hj_status s = HJ_OK;
-        for (long long i = 0; i < k && s == HJ_OK; ++i) s = launch_batch_step(b);
-        cudaError_t e = cudaStreamEndCapture(b->stream, &graph);
-        if (s != HJ_OK) {
-            if (graph) cudaGraphDestroy(graph);
-            return s;
+    std::vector<long long> ki(b->max_slots, 0);
+    for (int i = 0; i < b->max_slots; ++i) {
+        if (!b->slots[i].used) continue;
+        const HjDevState &h = b->h_slots[i].st;
+        if (h.done || h.status != HJ_OK) continue;
+        ki[i] = 1;
+        if (!h.last && h.dt > 0) {
+            const double r = ceil((h.T - h.t) / h.dt);
+            ki[i] = r > 1 ? (r < 1e9 ? (long long)r : 1000000000LL) : 1;
         }
-        if (e != cudaSuccess) return bfail(HJ_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
-        e = cudaGraphInstantiate(&exec, graph, 0);
-        cudaGraphDestroy(graph);
-        if (e != cudaSuccess) return bfail(HJ_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
-        if (b->graphs.size() >= 16) {
-            cudaGraphExecDestroy(b->graphs.front().second);
-            b->graphs.erase(b->graphs.begin());
-        }
-        b->graphs.push_back({k, exec});
     }
-    HJB_CUDA(cudaGraphLaunch(exec, b->stream));
-    return HJ_OK;
+    return ki;
 }
 
 hj_status pull_slots(hj_batch *b)
@@ -1043,6 +1108,8 @@ hj_status hj_batch_create(int32_t max_slots, size_t memory_budget, void *cuda_st
     if (e == cudaSuccess) e = cudaMalloc(&b->d_setup, sizeof(SlotSetup) * max_slots);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_setup, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_ctl, sizeof(BatchCtl));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_rounds, sizeof(int) * (B_MAX_ROUNDS + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_rounds_done, sizeof(int) * max_slots);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_maps, sizeof(CUtensorMap) * 4 * max_slots);
     for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaEventCreate(&b->ev[i]);
     if (e == cudaSuccess && b->own_stream) e = cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming);
@@ -1068,7 +1135,6 @@ void hj_batch_destroy(hj_batch *b)
 {
     if (!b) return;
     if (b->stream) cudaStreamSynchronize(b->stream);
-    drop_graphs(b);
     for (auto &s : b->slots)
         if (s.mem) cudaFree(s.mem);
     if (b->d_insts) cudaFree(b->d_insts);
@@ -1079,6 +1145,8 @@ void hj_batch_destroy(hj_batch *b)
     if (b->ev_setup) cudaEventDestroy(b->ev_setup);
     if (b->d_items) cudaFree(b->d_items);
     if (b->d_ctl) cudaFree(b->d_ctl);
+    if (b->d_rounds) cudaFree(b->d_rounds);
+    if (b->d_rounds_done) cudaFree(b->d_rounds_done);
     if (b->d_maps) cudaFree(b->d_maps);
     for (int i = 0; i < 2; ++i)
         if (b->ev[i]) cudaEventDestroy(b->ev[i]);
@@ -1440,62 +1508,18 @@ hj_status hj_batch_advance(hj_batch *b, int64_t max_steps, hj_batch_stats *stats
     bool started = false;
     if ((s = pull_slots(b)) != HJ_OK) return s;
     HJB_CUDA(cudaEventRecord(b->ev[0], b->stream));
-    while (taken < max_steps && b->nitems > 0) {
-        // batch steps until the slowest unfinished slot reaches its horizon;
-        // ki: the steps slot i has left (exact while its dt stays constant,
-        // as with the car's fixed alpha^max; the loop re-plans otherwise)
+    while (taken < max_steps) {
+        // batch steps until the slowest unfinished slot reaches its horizon,
+        // up to B_MAX_ROUNDS per launch; each slot takes its own steps to go
+        const std::vector<long long> ki = steps_to_go(b);
         long long k = 0;
-        std::vector<long long> ki(b->max_slots, 0);
-        for (int i = 0; i < b->max_slots; ++i) {
-            if (!b->slots[i].used) continue;
-            const HjDevState &h = b->h_slots[i].st;
-            if (h.done || h.status != HJ_OK) continue;
-            ki[i] = 1;
-            if (!h.last && h.dt > 0) {
-                const double r = ceil((h.T - h.t) / h.dt);
-                ki[i] = r > 1 ? (r < 1e9 ? (long long)r : 1000000000LL) : 1;
-            }
-            if (ki[i] > k) k = ki[i];
-        }
+        for (long long v : ki) k = v > k ? v : k;
         if (k == 0) break;
         if (k > max_steps - taken) k = max_steps - taken;
-        // Phases: as slots reach their horizons, the remaining ones get a
-        // new item layout (finer x chunks once they have fewer columns than
-        // CTAs) when their columns have fallen below half of those at the
-        // phase's start; otherwise the last steps would each take a whole
-        // column sweep of a few long items.  With a fixed chunk count the
-        // layout only drops the finished slots.
-        long long s0 = 0;
-        while (s0 < k) {
-            std::vector<char> act(b->max_slots, 0);
-            long long cols = 0;
-            auto columns_after = [&](long long st) {  // columns of the slots still running after st steps
-                long long c = 0;
-                for (int i = 0; i < b->max_slots; ++i)
-                    if (ki[i] > st) {
-                        const SlotHost &sl = b->slots[i];
-                        c += (long long)((sl.n[1] + sl.ty - 1) / sl.ty) * ((sl.n[2] + sl.tv - 1) / sl.tv);
-                    }
-                return c;
-            };
-            for (int i = 0; i < b->max_slots; ++i) act[i] = ki[i] > s0;
-            cols = columns_after(s0);
-            long long e = k;
-            std::vector<long long> ends;
-            for (int i = 0; i < b->max_slots; ++i)
-                if (ki[i] > s0 && ki[i] < k) ends.push_back(ki[i]);
-            std::sort(ends.begin(), ends.end());
-            for (long long r : ends)
-                if (2 * columns_after(r) < cols) {
-                    e = r;
-                    break;
-                }
-            if ((s = apply_layout(b, act)) != HJ_OK) return s;
-            if ((s = launch_steps(b, e - s0)) != HJ_OK) return s;
-            s0 = e;
-        }
+        if (k > B_MAX_ROUNDS) k = B_MAX_ROUNDS;
+        if ((s = run_rounds(b, ki, k)) != HJ_OK) return s;
         started = true;
-        launches += k;
+        launches += 1;
         taken += k;
         if ((s = pull_slots(b)) != HJ_OK) return s;
         BatchCtl ctl;
@@ -1525,7 +1549,7 @@ hj_status hj_batch_advance(hj_batch *b, int64_t max_steps, hj_batch_stats *stats
         stats->device_ms = ms;
         stats->nconsumer = b->bp.nconsumer;
         stats->ctas = b->ctas;
-        stats->items = b->nitems;
+        stats->items = b->lay_items;
     }
     return HJ_OK;
 }
@@ -1648,14 +1672,18 @@ hj_status hj_batch_autotune(hj_batch *b, int32_t steps_per_trial, int32_t *best_
                 if (b->slots[i].used)
                     hj_launch_prologue_f32(&b->d_slots[i].st, b->slots[i].geom, b->slots[i].coef,
                                            b->slots[i].n[2] * b->slots[i].n[3], 1e300, 0.8, b->stream);
-            if ((s = launch_steps(b, 2)) != HJ_OK) break;
+            // (the trial's steps: every slot takes each of them)
+            std::vector<long long> all(b->max_slots, 0);
+            for (int i = 0; i < b->max_slots; ++i) all[i] = b->slots[i].used ? (1LL << 40) : 0;
+            if ((s = run_rounds(b, all, 2)) != HJ_OK) break;
             cudaEventRecord(b->ev[0], b->stream);
-            if ((s = launch_steps(b, steps_per_trial)) != HJ_OK) break;
+            const int kt = steps_per_trial > B_MAX_ROUNDS ? B_MAX_ROUNDS : steps_per_trial;
+            if ((s = run_rounds(b, all, kt)) != HJ_OK) break;
             cudaEventRecord(b->ev[1], b->stream);
             cudaEventSynchronize(b->ev[1]);
             float ms = 0.f;
             cudaEventElapsedTime(&ms, b->ev[0], b->ev[1]);
-            const double per = ms / steps_per_trial;
+            const double per = ms / kt;
             if (per < best) {
                 best = per;
                 best_nc = ncs[a];
