@@ -432,9 +432,9 @@ HJ_API hj_status hj_batch_read_value_device(hj_batch *b, int32_t slot, void *out
 /* Kernel shape: consumer threads per CTA (0: automatic, else a multiple of 32
  * in [128, 736]; shapes of at most 288 run two CTAs per SM, each with half
  * of the SM's shared memory) and x chunks per slot column (1: whole columns; 0:
- * automatic, whole columns unless the batch has fewer (y, v) columns than
- * the GPU has SMs, then as many chunks as fill them, each at least 4 x
- * planes long). */
+ * automatic, whole columns unless the running slots have fewer (y, v)
+ * columns than the kernel has resident CTAs, then as many chunks as fill
+ * them, each at least 4 x planes long). */
 HJ_API hj_status hj_batch_set_shape(hj_batch *b, int32_t nconsumer, int32_t chunks);
 
 /* Time steps_per_trial batch steps for each candidate kernel shape and keep

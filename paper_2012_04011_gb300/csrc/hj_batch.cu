@@ -761,11 +761,12 @@ hj_status upload_slot_tables(hj_batch *b, SlotHost &s)
 // (0 for the others), and the queue in order.  Whole columns while the
 // active slots have at least one (y, v) column per CTA, else enough chunks
 // (of at least 4 planes) to give every CTA an item, since a column's planes
-// are streamed one after another by one CTA.  Slots with the longest columns
-// come first; with whole columns, the slots whose items come last are cut
-// into x chunks (about the last item per CTA into four, the one before into
-// two), so that the CTAs of a batch step run out of work at nearly the same
-// time.  A fixed chunk count (hj_batch_set_shape) replaces both rules.
+// are streamed one after another by one CTA.  (With the steps of a launch
+// overlapping, nothing is gained by cutting some columns shorter: cutting
+// the queue's last slots, or the slots with the most steps, into x chunks
+// measured slower, 19.6-19.7 against 19.4 ms per batch64 solve.)  Slots with
+// more steps to go come first, then the longest columns.  A fixed chunk
+// count (hj_batch_set_shape) replaces the automatic one.
 void plan_layout(hj_batch *b, const std::vector<char> &active, const std::vector<long long> &ki, long long ctas,
                  std::vector<BatchItem> &items)
 {
@@ -794,16 +795,6 @@ void plan_layout(hj_batch *b, const std::vector<char> &active, const std::vector
         return b->slots[a].n[0] > b->slots[c].n[0];
     });
     std::vector<int> slot_chunks(b->max_slots, nchunk);
-    if (b->xc_mode == 0 && nchunk == 1) {
-        long long tail = 0;
-        for (int k = (int)order.size() - 1; k >= 0 && tail < 2 * ctas; --k) {
-            const SlotHost &s = b->slots[order[k]];
-            if (s.n[0] < 8) break;
-            const int ch = tail < ctas ? 4 : 2;
-            slot_chunks[order[k]] = ch;
-            tail += (long long)ch * ((s.n[1] + s.ty - 1) / s.ty) * ((s.n[2] + s.tv - 1) / s.tv);
-        }
-    }
     for (int i : order) {
         SlotHost &s = b->slots[i];
         s.xc = (s.n[0] + slot_chunks[i] - 1) / slot_chunks[i];
