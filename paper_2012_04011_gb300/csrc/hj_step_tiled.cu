@@ -286,8 +286,20 @@ cudaError_t hj_launch_step_tiled(hj_grid *g)
     const TiledParams P = make_params(g, g->tile_ty, g->tile_tv, g->tile_stages, g->tile_xc);
     KernelFn fn =
         kernel_fn(g->prec == HJ_Q527, g->p4 != g->n[3], g->tiled_usign, g->v0_bcast, g->track, P.nconsumer, P.rpt);
-    fn<<<g->tiled_ctas, P.nconsumer + 32, tiled_smem_bytes(P), g->stream>>>(
-        g->tmap[0], g->tmap[1], g->tmap[2], g->tmap[3], (float *)g->buf, g->coef, g->tab_tiled, g->qw,
-        (const float *)g->v0xy, g->k4tab, g->amax_q, g->dstate, g->geom, P, g->nint);
-    return cudaGetLastError();
+    // a programmatic dependent of the previous launch on the stream: the
+    // kernel sets up its ring while the previous step drains and waits for
+    // that step's completion before it reads anything it wrote
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)g->tiled_ctas);
+    cfg.blockDim = dim3((unsigned)(P.nconsumer + 32));
+    cfg.dynamicSmemBytes = tiled_smem_bytes(P);
+    cfg.stream = g->stream;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, fn, g->tmap[0], g->tmap[1], g->tmap[2], g->tmap[3], (float *)g->buf,
+                              (const void *)g->coef, (const float *)g->tab_tiled, g->qw, (const float *)g->v0xy,
+                              (const void *)g->k4tab, (const double2 *)g->amax_q, g->dstate, g->geom, P, g->nint);
 }

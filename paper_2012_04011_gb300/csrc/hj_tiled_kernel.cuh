@@ -137,7 +137,6 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
                   "several rows per thread: broadcast V0, single-sided FP32");
     const HjCoef<double> *coefd = (const HjCoef<double> *)coefv;  // Q5.27 grids: the table the weights come from
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    if (st->done) return;  // uniform across the grid
 
     // ---- shared memory carve-up
     float *stages = (float *)smem_raw;
@@ -147,11 +146,6 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
     volatile int *abort_flag = (volatile int *)(scratch + 96);
     unsigned long long *deadline_p = (unsigned long long *)(scratch + 97);
     unsigned long long *alpha_s = scratch + 98;  // the CTA's alpha^max partials (FP64 bit patterns)
-
-    const long long n = st->n;
-    const float dt = (float)st->dt;
-    float *vout = buf + (n & 1) * nint;
-    const CUtensorMap *map_in = (n == 0) ? &map_v0 : (((n - 1) & 1) ? &map_b : &map_a);
 
     const int tid = threadIdx.x;
     const int nconsumer_warps = P.nconsumer >> 5;
@@ -168,6 +162,18 @@ __global__ void __launch_bounds__(MAXC + 32, 1) hj_step_tiled_kernel(
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     __syncthreads();
+    // Launched as a programmatic dependent of the previous step (the host sets
+    // the launch attribute): everything above overlaps that step's end; from
+    // here on the previous grid has completed and its V_n and finalised state
+    // are visible.  Then the next step may be scheduled as SMs free up (its
+    // CTAs wait here in turn).  Without such a prerequisite both are no-ops.
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    if (st->done) return;  // uniform across the grid
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    const long long n = st->n;
+    const float dt = (float)st->dt;
+    float *vout = buf + (n & 1) * nint;
+    const CUtensorMap *map_in = (n == 0) ? &map_v0 : (((n - 1) & 1) ? &map_b : &map_a);
 
     // convergence mode (Algorithm 2's epsilon): this thread's largest |V_{n+1} - V_n|
     float dmf = 0.f;
