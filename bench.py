@@ -593,7 +593,7 @@ def run_ours(args):
     fp64_peak = measure_fp64_peak(hj, torch, stream, visible_gpu_index(local))
 
     # batched solves: the 64-instance workload (uneven grids, own obstacles,
-    # T = 1.5 s), V0 already on the device, one persistent kernel per batch step
+    # T = 1.5 s), V0 already on the device, one persistent launch per batch solve
     batch = None
     if not args.no_batch:
         ws = scenes.batch_workloads()

@@ -1,5 +1,5 @@
 """Batched solves: many independent car grids stepped by one persistent
-kernel per batch step (CUDA graphs), each slot with its own grid, V0,
+kernel that runs many batch steps per launch, each slot with its own grid, V0,
 horizon and dt.
 
 Each slot must give exactly what a single-grid FP32 solve of the same grid
