@@ -656,7 +656,6 @@ struct hj_batch {
     int xc_mode = 0;        // 0: automatic, k > 0: about n1 / k planes per chunk
     BatchParams bp = {0, 0, 0};
     int ctas = 0;
-    int nitems = 0;
     bool dirty = true;
     int *d_rounds = nullptr;       // queue position of each round of a launch (B_MAX_ROUNDS + 1)
     int *d_rounds_done = nullptr;  // per slot: steps finalised in the current launch
@@ -919,8 +918,7 @@ hj_status rebuild(hj_batch *b)
     HJB_CUDA(cudaMemcpy(b->d_maps, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice));
     BatchCtl ctl = {0u, 0u, (int)items.size(), HJ_OK};
     HJB_CUDA(cudaMemcpy(b->d_ctl, &ctl, sizeof(ctl), cudaMemcpyHostToDevice));
-    b->nitems = (int)items.size();
-    b->lay_items = b->nitems;
+    b->lay_items = (int)items.size();
     if (bp.nconsumer != b->bp.nconsumer || bp.stages != b->bp.stages || bp.stage_bytes != b->bp.stage_bytes) {
         b->bp = bp;
         BatchKernelFn fn = batch_kernel(bp.nconsumer);
@@ -994,7 +992,6 @@ hj_status run_rounds(hj_batch *b, const std::vector<long long> &ki, long long k)
     b->lay_nitems = (int)pos;
     HJB_CUDA(cudaMemcpyAsync((char *)b->d_ctl + offsetof(BatchCtl, nitems), &b->lay_nitems, sizeof(int),
                              cudaMemcpyHostToDevice, b->stream));
-    b->nitems = (int)pos;
     BatchKernelFn fn = batch_kernel(b->bp.nconsumer);
     fn<<<b->ctas, b->bp.nconsumer + 32, batch_smem(b->bp), b->stream>>>(b->d_insts, b->d_slots, b->d_items, b->d_ctl,
                                                                         b->d_maps, b->bp, b->d_rounds,
