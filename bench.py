@@ -407,8 +407,9 @@ def run_large(hj, scenes, torch, stream, steps=10):
     """Grids past 32-bit offsets: the 2048x2048x32x33 car (4.4e9 cells, 4.8e9
     stored values, 58 GB of FP32 or Q5.27 buffers), V0 from its (x, y) field
     (so the tiled kernel is its broadcast-V0 variant, 8 B per update; the
-    generic kernel reads the 4D V0, 12 B).  Each precision runs the tiled
-    kernel (autotuned) and the generic one;
+    generic kernel reads the 4D V0, 12 B), and the tiled kernel once more
+    with the same V0 as a 4D device array (12 B).  Each precision runs the
+    tiled kernel (autotuned) both ways and the generic one;
     ms per step from the library's CUDA events around `steps` steps, after 3
     warm-up steps."""
     n = LARGE_GRID
@@ -418,10 +419,20 @@ def run_large(hj, scenes, torch, stream, steps=10):
     peak = measured_peaks()[0]
     res = {"workload": "car4d_%dx%dx%dx%d" % n, "cells": ncell}
     for pname, prec in (("f32", hj.HJ_FP32), ("q527", hj.HJ_Q527)):
-        for kname, kern in (("tiled", hj.HJ_KERNEL_TILED), ("generic", hj.HJ_KERNEL_GENERIC)):
+        for kname, kern in (("tiled", hj.HJ_KERNEL_TILED), ("tiled_4d", hj.HJ_KERNEL_TILED),
+                            ("generic", hj.HJ_KERNEL_GENERIC)):
             with hj.Grid(n, grid.lo, grid.hi, grid.periodic, prec, stream.cuda_stream) as g:
                 g.set_dynamics(hj.HJ_DYN_CAR4D, (scenes.A_MAX, scenes.W_MAX))
-                g.set_initial_value_xy(v0_xy)
+                if kname == "tiled_4d":
+                    # the same V0 as a 4D array (the field replicated over v and
+                    # theta on the device, 17.7 GB of FP32): the 12-byte kernel
+                    v4 = torch.from_numpy(np.ascontiguousarray(v0_xy, dtype=np.float32)).to("cuda")
+                    v4 = v4[:, :, None, None].expand(n[0], n[1], n[2], n[3]).contiguous().reshape(-1)
+                    hj.hj_set_initial_value_device(g.handle, v4)
+                    del v4
+                    torch.cuda.empty_cache()
+                else:
+                    g.set_initial_value_xy(v0_xy)
                 g.set_kernel(kern)
                 if kern == hj.HJ_KERNEL_TILED:
                     g.autotune(4)
@@ -430,7 +441,7 @@ def run_large(hj, scenes, torch, stream, steps=10):
                 ms = st.loop_ms / max(st.steps, 1)
                 # V0 came as its (x, y) field: the tiled kernel reads that field
                 # (8 B per update), the generic kernel the 4D V0 (12 B)
-                bpu = BYTES_PER_UPDATE["f32_bcast"] if kern == hj.HJ_KERNEL_TILED else BYTES_PER_UPDATE[pname]
+                bpu = BYTES_PER_UPDATE["f32_bcast"] if kname == "tiled" else BYTES_PER_UPDATE[pname]
                 res[f"{pname}_{kname}"] = {
                     "ms_per_step": ms, "value": ncell / (ms * 1e-3), "unit": UNIT, "bytes_per_update": bpu,
                     "hbm_frac": bpu * ncell / (ms * 1e-3) / 1e9 / peak,
