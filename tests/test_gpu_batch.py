@@ -48,6 +48,7 @@ def test_batch_slots_equal_single_grid_solves(hj):
             b.set_horizon(s, w.T, w.cfl)
         st = b.advance()
         assert st.active == 0 and st.finished == len(ws)
+        assert st.launches == 1  # every batch step of the solve in one launch
         for s, w, v0 in zip(slots, ws, v0s):
             ref, rst = single_grid(hj, w, v0)
             info = b.slot_info(s)
@@ -160,6 +161,27 @@ def test_batch_relayout_as_slots_finish(hj, shape, pieces):
             info = b.slot_info(s)
             assert info.steps == rst.steps and info.t == w.T
             assert np.array_equal(b.read_value(s), ref), (s, w.grid.n)
+
+
+def test_batch_advance_longer_than_one_launch(hj):
+    """More batch steps than one launch runs (1024): the advance loop takes
+    several launches, and the slots still give their single-grid solves'
+    bits and step counts (one slot with about 1200 steps, one with a few)."""
+    ws = [scenes.custom_workload((13, 11, 6, 8), n_circles=2, T=T, seed=500 + i) for i, T in enumerate((80.0, 0.5))]
+    v0s = [scenes.initial_value(w.grid, w.scene) for w in ws]
+    with hj.Batch(len(ws)) as b:
+        slots = [b.add_workload(w) for w in ws]
+        for s, w, v0 in zip(slots, ws, v0s):
+            b.set_initial_value(s, v0)
+            b.set_horizon(s, w.T, w.cfl)
+        st = b.advance()
+        assert st.active == 0 and st.launches >= 2, (st.steps, st.launches)
+        for s, w, v0 in zip(slots, ws, v0s):
+            ref, rst = single_grid(hj, w, v0)
+            info = b.slot_info(s)
+            assert info.steps == rst.steps and info.t == w.T
+            assert np.array_equal(b.read_value(s), ref), s
+        assert b.slot_info(slots[0]).steps > 1024
 
 
 @pytest.mark.slow
