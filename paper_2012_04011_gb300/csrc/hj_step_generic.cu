@@ -272,7 +272,11 @@ __global__ void __launch_bounds__(256) hj_step_q527_kernel(const int32_t *__rest
                                                             const HjGeom g, long long nint, const Divisors dv)
 {
     __shared__ unsigned long long scratch[96];
+    // a programmatic dependent of the previous step: wait for its grid (its
+    // V_n and finalised state), then let the next step be scheduled
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     if (st->done) return;
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const long long n = st->n;
     const int32_t *vin;
     int32_t *vout;
@@ -315,7 +319,11 @@ __global__ void __launch_bounds__(256) hj_step_generic_kernel(const T *__restric
                                                                const Divisors dv)
 {
     __shared__ unsigned long long scratch[96];
+    // a programmatic dependent of the previous step: wait for its grid (its
+    // V_n and finalised state), then let the next step be scheduled
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     if (st->done) return;  // uniform: written by the previous kernel on this stream
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const long long n = st->n;
     const T dt = (T)st->dt;
     const T *vin;
@@ -949,6 +957,24 @@ cudaError_t hj_launch_step_resident(hj_grid *g, long long k)
     return g->track ? launch_resident<float, true>(g, k) : launch_resident<float, false>(g, k);
 }
 
+// Launch of a step kernel as a programmatic dependent of the previous launch
+// on the stream (the kernel waits for that grid before it reads its state).
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_dependent(void (*fn)(KArgs...), int blocks, int threads, cudaStream_t stream, Args... args)
+{
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)blocks);
+    cfg.blockDim = dim3((unsigned)threads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = stream;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, fn, (KArgs)args...);
+}
+
 cudaError_t hj_launch_step_generic(hj_grid *g)
 {
     int sms = 0;
@@ -963,14 +989,15 @@ cudaError_t hj_launch_step_generic(hj_grid *g)
     dv.n3 = make_fastdiv((uint32_t)g->n[2]);
     dv.n2 = make_fastdiv((uint32_t)g->n[1]);
     const bool fast = g->ncell < (1LL << 32);
-#define HJ_LAUNCH_Q(F, K)                                                                                     \
-    hj_step_q527_kernel<F, K><<<blocks, threads, 0, g->stream>>>(                                          \
-        (const int32_t *)g->v0, (int32_t *)g->buf, (const HjCoef<double> *)g->coef, g->qw,                  \
-        (const double *)g->k4tab, g->dstate, g->geom, g->nint, dv)
-#define HJ_LAUNCH(T, F, K)                                                                                    \
-    hj_step_generic_kernel<T, F, K><<<blocks, threads, 0, g->stream>>>(                                    \
-        (const T *)g->v0, (T *)g->buf, (const HjCoef<T> *)g->coef, g->scaled, g->k4tab, g->dstate, g->geom, \
-        g->nint, dv)
+    cudaError_t le = cudaSuccess;
+#define HJ_LAUNCH_Q(F, K)                                                                                      \
+    le = launch_dependent(hj_step_q527_kernel<F, K>, blocks, threads, g->stream, (const int32_t *)g->v0,      \
+                          (int32_t *)g->buf, (const HjCoef<double> *)g->coef, g->qw, (const double *)g->k4tab, \
+                          g->dstate, g->geom, g->nint, dv)
+#define HJ_LAUNCH(T, F, K)                                                                                     \
+    le = launch_dependent(hj_step_generic_kernel<T, F, K>, blocks, threads, g->stream, (const T *)g->v0,      \
+                          (T *)g->buf, (const HjCoef<T> *)g->coef, g->scaled, (const void *)g->k4tab, g->dstate, \
+                          g->geom, g->nint, dv)
 #define HJ_LAUNCH2(T, F)          \
     do {                          \
         if (g->track)             \
@@ -996,5 +1023,5 @@ cudaError_t hj_launch_step_generic(hj_grid *g)
 #undef HJ_LAUNCH_Q
 #undef HJ_LAUNCH
 #undef HJ_LAUNCH2
-    return cudaGetLastError();
+    return le != cudaSuccess ? le : cudaGetLastError();
 }
