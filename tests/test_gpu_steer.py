@@ -106,6 +106,39 @@ def test_steer_broadcast_v0_and_zero_angle(hj):
         assert np.array_equal(g.read_value().astype(np.float32), z)
 
 
+@pytest.mark.parametrize("n, shape", [((26, 25, 11, 48), [12, 8, 0, 0]), ((17, 13, 11, 32), [4, 2, 5, 4]),
+                                      ((10, 17, 19, 16), [16, 16, 4, 4])])
+def test_steer_broadcast_v0_several_rows_per_thread(hj, n, shape):
+    """The steering car's theta coefficient grows with the speed, so each of
+    the two or four v rows a thread updates in the broadcast-V0 single-sided
+    form has its own (theta counts a multiple of 16 give every quad one sign
+    of cos and sin).  The results must be the 4D-V0 path's bits, and the
+    oracle's within the FP32 tolerance."""
+    import torch
+    w = scenes.custom_workload(n, n_circles=3, n_rects=1, T=0.5, seed=sum(n) + 11)
+    V0 = scenes.initial_value(w.grid, w.scene)
+    outs = []
+    for xy in (False, True):
+        with hj.Grid(w.grid.n, w.grid.lo, w.grid.hi, w.grid.periodic, hj.HJ_FP32) as g:
+            g.set_dynamics(hj.HJ_DYN_CAR4D_STEER, STEER)
+            g.set_kernel(hj.HJ_KERNEL_TILED)
+            if xy:
+                g.set_initial_value_xy(scenes.signed_distance_xy(w.grid, w.scene))
+                g.set_tile_shape(shape)
+                assert g.info().tile[1] == min(shape[1], n[2])
+            else:
+                g.set_initial_value(V0)
+            st = g.solve_brt(w.T, w.cfl)
+            out = torch.empty(int(np.prod(n)), dtype=torch.float32, device="cuda")
+            g.read_value_device(out)
+            outs.append((out.cpu().numpy().reshape(n), st.steps))
+    assert outs[0][1] == outs[1][1]
+    assert np.array_equal(outs[0][0], outs[1][0])
+    Vo, dts = oracle.solve(oracle_steer(w), V0, w.T, w.cfl)
+    assert outs[1][1] == len(dts)
+    assert float(np.abs(outs[1][0] - Vo).max()) <= 1e-4 * float(np.abs(V0).max())
+
+
 def test_steer_parameter_checks(hj):
     w = scenes.workload("car4d_31x31x11x16")
     with hj.Grid(w.grid.n, w.grid.lo, w.grid.hi, w.grid.periodic, hj.HJ_FP32) as g:
